@@ -1,0 +1,194 @@
+/*
+ * mlmc.h - C ABI of libmlmc, the GB300 (sm_103a) batched coupled MLMC
+ * sample solve.
+ *
+ * Method: Badia, Hampton, Principe, "A massively parallel implementation of
+ * multilevel Monte Carlo for finite element models" (arXiv 2111.11788).
+ * For each level l and sample i the library draws KLE coefficients xi(l, i),
+ * forms kappa = exp(Phi xi) on the level-l and level-(l-1) meshes, solves
+ * -div(kappa grad u) = 1 (Eq. (model), Sec. 2.1) with preconditioned CG on
+ * both meshes, and folds Y_l^i = Q_l - Q_{l-1} (Eq. (mlmc_average)) into
+ * per-level Welford statistics (Eq. (sample_variance)) that drive the
+ * estimator and the sample allocation (Eq. (mlmc_num_samples)).
+ *
+ * Conventions for every entry point:
+ *  - Return codes only; nothing is thrown across the ABI. On error the
+ *    outputs are unspecified.
+ *  - "host" pointers are ordinary CPU memory owned by the caller; "device"
+ *    pointers are CUDA global memory on the current device, owned by the
+ *    caller. The plan owns only its own tables and workspace.
+ *  - `stream` arguments are borrowed cudaStream_t handles (NULL = legacy
+ *    default stream). Device-pointer entry points are asynchronous on the
+ *    plan's stream; host-pointer entry points return after the results are
+ *    in host memory.
+ *  - Mesh m has n_m = coarse_cells * 2^m cells per side (Sec. 2.2, s = 2),
+ *    (n_m + 1)^dim nodes including the boundary, n_m^dim elements.
+ *  - Node arrays hold (n+1)^dim doubles per sample, x fastest, boundary
+ *    entries included (ignored on input, written as 0 on output), samples
+ *    mlmc_node_stride(dim, n) doubles apart. Element arrays hold n^dim
+ *    doubles per sample, x fastest, mlmc_elem_stride(dim, n) apart.
+ *  - A plan is not thread-safe; distinct plans may be used concurrently.
+ */
+#ifndef MLMC_H
+#define MLMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum mlmc_status {
+  MLMC_OK = 0,
+  MLMC_ERR_INVALID = -1,        /* bad argument or configuration */
+  MLMC_ERR_OOM = -2,            /* device allocation failed */
+  MLMC_ERR_NOT_CONVERGED = -3,  /* some sample hit max_iter (its iters = -1) */
+  MLMC_ERR_CUDA = -4,           /* a CUDA runtime call or launch failed */
+  MLMC_ERR_TIMEOUT = -5,        /* reserved: a bounded device wait expired */
+  MLMC_ERR_UNIMPLEMENTED = -6   /* combination not built (e.g. dim 3 + mixed) */
+} mlmc_status;
+
+enum { MLMC_QOI_DOMAIN_MEAN = 0, MLMC_QOI_BOX_MEAN = 1 };
+enum { MLMC_JACOBI_PCG = 0, MLMC_GMG_PCG = 1 };
+enum { MLMC_FP64 = 0, MLMC_MIXED = 1 };
+
+/* Problem and solver description. Fill with mlmc_config_default() first. */
+typedef struct mlmc_config {
+  int32_t dim;             /* 2 or 3 */
+  int32_t n_levels;        /* L + 1, 1..16 */
+  int32_t coarse_cells;    /* n_0 >= 2, cells per side of mesh 0 */
+  int32_t modes_per_dim;   /* m; M = m^dim tensor KLE modes, 1..32 */
+  double sigma2;           /* variance of the Gaussian log-field (> 0) */
+  double corr_len;         /* exponential correlation length (> 0) */
+  int32_t qoi;             /* MLMC_QOI_DOMAIN_MEAN | MLMC_QOI_BOX_MEAN */
+  int32_t solver;          /* MLMC_JACOBI_PCG | MLMC_GMG_PCG */
+  double box_lo, box_hi;   /* QoI box [lo, hi]^dim, node-aligned on every mesh */
+  double rtol;             /* stop when ||r||_2 <= rtol ||b||_2 */
+  int32_t max_iter;        /* CG iteration cap (> 0) */
+  int32_t precision;       /* MLMC_FP64 (MLMC_MIXED reserved) */
+  uint64_t seed;           /* Philox key */
+  uint32_t stream_id;      /* fourth Philox counter word (request id) */
+  int32_t mg_smooth;       /* damped-Jacobi sweeps before and after each coarse correction */
+  double mg_omega;         /* Jacobi damping in the smoother */
+  int32_t mg_coarsest;     /* cells per side of the coarsest multigrid grid (>= 2) */
+  int32_t check_every;     /* CG iterations between convergence polls (0 = auto) */
+  uint64_t workspace_bytes;/* device workspace budget for batching (0 = auto) */
+} mlmc_config;
+
+/* Per-level Welford state (Eq. (sample_variance): V = m2 / n). */
+typedef struct mlmc_level_state {
+  int64_t n;
+  double mean;
+  double m2;
+  double cost_sum;         /* sum of the per-sample cost model C_l */
+} mlmc_level_state;
+
+typedef struct mlmc_plan_s* mlmc_plan;
+
+/* ---- configuration and layout -------------------------------------- */
+
+/* Defaults: 2D, 3 levels, n_0 = 16, m = 4, sigma2 = 1, corr_len = 0.3,
+ * domain-mean QoI, Jacobi-PCG, rtol 1e-10, FP64, seed 0. */
+void mlmc_config_default(mlmc_config* cfg);
+
+/* Doubles between consecutive samples in node / element arrays. */
+int64_t mlmc_node_stride(int dim, int n);
+int64_t mlmc_elem_stride(int dim, int n);
+
+/* Cells per side of mesh `mesh` (n_0 * 2^mesh), or -1 if out of range. */
+int64_t mlmc_mesh_cells(const mlmc_config* cfg, int mesh);
+
+/* Deterministic level cost C_l = interior DOFs of mesh l + of mesh l-1
+ * (the paper measures CPU time per Y_l, Sec. 2.3). */
+double mlmc_level_cost(const mlmc_config* cfg, int level);
+
+const char* mlmc_status_str(mlmc_status s);
+
+/* ---- plan ----------------------------------------------------------- */
+
+/* Validates cfg, solves the 1D KLE eigenproblems (Sec. 5.2 exponential
+ * covariance; Ghanem & Spanos closed form), builds the per-mesh tables on
+ * the device and zeroes the level states. `stream` is borrowed for the
+ * plan's lifetime. Errors: INVALID, OOM, CUDA. */
+mlmc_status mlmc_plan_create(const mlmc_config* cfg, void* stream, mlmc_plan* out);
+mlmc_status mlmc_plan_destroy(mlmc_plan plan);
+
+/* Reset all level states to n = 0. */
+mlmc_status mlmc_reset_stats(mlmc_plan plan);
+
+/* Coupled samples first..first+count-1 of `level` (Eq. (mlmc_average)):
+ * one xi(level, i) per sample, solved on mesh `level` and, for level > 0,
+ * on mesh level-1; Y = Q_f - Q_c is folded into the level state in sample
+ * order. Optional host outputs (each `count` long, may be NULL): q_fine,
+ * q_coarse (0 for level 0), iters (fine-mesh CG iterations, -1 if not
+ * converged). Returns NOT_CONVERGED if any solve hit max_iter (its Y is
+ * still folded). Samples must satisfy 0 <= i < 2^32. */
+mlmc_status mlmc_sample_level(mlmc_plan plan, int level, int64_t first, int64_t count,
+                              double* q_fine, double* q_coarse, int32_t* iters);
+
+/* Host copy of one level state. */
+mlmc_status mlmc_level_stats(mlmc_plan plan, int level, mlmc_level_state* out);
+
+/* Eq. (mlmc_average) and Sec. 2.2: q_hat = sum_l mean_l and
+ * stat_var = sum_l (m2_l / n_l) / n_l over levels with n_l > 0 (host outputs). */
+mlmc_status mlmc_estimate(mlmc_plan plan, double* q_hat, double* stat_var);
+
+/* Eq. (mlmc_num_samples): N_l = ceil(2 eps^-2 sqrt(V_l / C_l) sum_i sqrt(V_i C_i)).
+ * V, C, N_out are host arrays of n_levels entries; evaluated on the device. */
+mlmc_status mlmc_allocate(const double* V, const double* C, int n_levels, double eps,
+                          int64_t* N_out);
+
+/* Adaptive MLMC with L fixed (Sec. 2.3, Algorithm 2): `pilot` samples per
+ * level, then repeat {N_l from Eq. (mlmc_num_samples) with the current
+ * V_l and the cost model; draw the missing samples} until every level has
+ * its N_l. With N_fixed (host, n_levels entries) the counts are fixed and
+ * eps is ignored. Outputs q_hat, stat_var (host, may be NULL); N_out (host,
+ * n_levels, may be NULL) receives the final sample counts. */
+mlmc_status mlmc_run(mlmc_plan plan, double eps, int64_t pilot, const int64_t* N_fixed,
+                     double* q_hat, double* stat_var, int64_t* N_out);
+
+/* ---- device-level steps (device pointers, asynchronous on the plan's stream) */
+
+/* xi[s * n_modes + k] = xi_k(level, first + s), s < count (the plan's seed
+ * and stream_id; Philox4x32-10 counter (k/2, i, level, stream_id)). */
+mlmc_status mlmc_draw_xi(mlmc_plan plan, int level, int64_t first, int64_t count, double* xi);
+
+/* kappa = exp(Phi xi) at the element centroids of mesh `mesh` for `count`
+ * coefficient vectors xi (count x M, contiguous). Output element arrays. */
+mlmc_status mlmc_kappa(mlmc_plan plan, int mesh, const double* xi, int64_t count, double* kappa);
+
+/* y = A(kappa) x on mesh `mesh` (Q1 stiffness, homogeneous Dirichlet):
+ * node arrays in and out, `count` samples. */
+mlmc_status mlmc_apply(mlmc_plan plan, int mesh, const double* kappa, const double* x,
+                       double* y, int64_t count);
+
+/* Solve A(kappa) u = b (b_i = h^dim) with the configured PCG for `count`
+ * samples; u (node arrays, may be NULL), q (QoI, count doubles), iters
+ * (count int32, may be NULL; -1 = not converged). */
+mlmc_status mlmc_solve(mlmc_plan plan, int mesh, const double* kappa, int64_t count,
+                       double* u, double* q, int32_t* iters);
+
+/* ---- tracing: per-kernel CUDA-event timing -------------------------- */
+
+typedef struct mlmc_kernel_stat {
+  int64_t launches;
+  double ms;              /* summed event time of the recorded launches */
+  double bytes;           /* summed algorithmic DRAM bytes of those launches */
+} mlmc_kernel_stat;
+
+int mlmc_kernel_count(void);
+const char* mlmc_kernel_name(int kernel_id);
+/* When on, every launch of a kernel is bracketed by CUDA events on the
+ * plan's stream; stats accumulate until mlmc_profile_reset. */
+mlmc_status mlmc_profile_enable(mlmc_plan plan, int on);
+mlmc_status mlmc_profile_reset(mlmc_plan plan);
+mlmc_status mlmc_kernel_stats(mlmc_plan plan, int kernel_id, mlmc_kernel_stat* out);
+/* Number of kernel launches issued by this plan since creation. */
+int64_t mlmc_launch_count(mlmc_plan plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MLMC_H */

@@ -1,0 +1,215 @@
+// Lognormal coefficient kappa = exp(Phi xi) at element centroids.
+//
+// Phi is the full tensor basis of the 1D exponential-covariance KLE
+// eigenfunctions (Sec. 5.2 "eigenfunctions in each dimension"):
+//   Phi[e, k] = sqrt(sigma^2) prod_a sqrt(theta_{k_a}) f_{k_a}(c_a(e)),
+// k = (k_z m + k_y) m + k_x. Because Phi is a Kronecker product of per-axis
+// tables F[i, k] = sqrt(theta_k) f_k((i + 1/2) h), the contraction Phi xi is
+// evaluated axis by axis (sum factorisation) in FP64: for each sample a
+// small x-contraction into shared memory, then m FMAs per element and one
+// exp. The kernel is bound by the write of kappa (8 B per element).
+#include "mlmc_internal.cuh"
+
+namespace mlmc {
+namespace {
+
+// F[i * m + k] = sqrt(theta_k) f_k(x_i), x_i = (i + 1/2) / n, centred t = x - 1/2:
+// even k: cos(w t) / sqrt(1/2 + sin(w) / (2w)); odd k: sin(w t) / sqrt(1/2 - sin(w) / (2w)).
+__global__ void k_kle_table(int n, int m, const double* __restrict__ omega,
+                            const double* __restrict__ theta, const int32_t* __restrict__ even,
+                            double* __restrict__ table) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * m) return;
+  const int i = idx / m;
+  const int k = idx - i * m;
+  const double w = omega[k];
+  const double t = ((double)i + 0.5) / (double)n - 0.5;
+  const double s2 = sin(w) / (2.0 * w);   // sin(2 w a) / (2 w) with a = 1/2
+  double f;
+  if (even[k]) {
+    f = cos(w * t) / sqrt(0.5 + s2);
+  } else {
+    f = sin(w * t) / sqrt(0.5 - s2);
+  }
+  table[idx] = sqrt(theta[k]) * f;
+}
+
+constexpr int KAP_ROWS = 4;  // element rows per thread in 2D
+
+// 2D: CTA covers 32 x (8 * KAP_ROWS) elements of one sample.
+__global__ void __launch_bounds__(TX2* TY2)
+    k_kappa2d(int n, int m, double sqrt_sigma2, const double* __restrict__ table,
+              const double* __restrict__ xi, int64_t es, double* __restrict__ kappa, Prof prof) {
+  __shared__ double s_xi[MAX_MODES_1D * MAX_MODES_1D];
+  __shared__ double s_t[TX2][MAX_MODES_1D + 1];          // T[ix][k_y]
+  __shared__ double s_fy[TY2 * KAP_ROWS][MAX_MODES_1D + 1];
+  const int b = blockIdx.z;
+  const int tid = threadIdx.y * TX2 + threadIdx.x;
+  const int nthreads = TX2 * TY2;
+  const int x0 = blockIdx.x * TX2;
+  const int y0 = blockIdx.y * TY2 * KAP_ROWS;
+  const int M = m * m;
+  const double* xs = xi + (int64_t)b * M;
+  for (int k = tid; k < M; k += nthreads) s_xi[k] = xs[k];
+  for (int idx = tid; idx < TY2 * KAP_ROWS * m; idx += nthreads) {
+    const int r = idx / m, k = idx - r * m;
+    const int iy = y0 + r;
+    s_fy[r][k] = (iy < n) ? table[iy * m + k] : 0.0;
+  }
+  __syncthreads();
+  // T[ix][ky] = sum_kx F[ix][kx] xi[ky * m + kx]
+  for (int idx = tid; idx < TX2 * m; idx += nthreads) {
+    const int c = idx / m, ky = idx - c * m;
+    const int ix = x0 + c;
+    double acc = 0.0;
+    if (ix < n) {
+      const double* fx = table + ix * m;
+      for (int kx = 0; kx < m; ++kx) acc = fma(fx[kx], s_xi[ky * m + kx], acc);
+    }
+    s_t[c][ky] = acc;
+  }
+  __syncthreads();
+  const int ix = x0 + threadIdx.x;
+  if (ix < n) {
+    double* out = kappa + (int64_t)b * es;
+#pragma unroll
+    for (int r = 0; r < KAP_ROWS; ++r) {
+      const int rl = threadIdx.y + TY2 * r;
+      const int iy = y0 + rl;
+      if (iy >= n) break;
+      double g = 0.0;
+      for (int ky = 0; ky < m; ++ky) g = fma(s_fy[rl][ky], s_t[threadIdx.x][ky], g);
+      out[(int64_t)iy * n + ix] = exp(sqrt_sigma2 * g);
+    }
+  }
+  if (prof.acc && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) atomicAdd(prof.acc, prof.per_sample);
+}
+
+// 3D: CTA covers 32 (x) x 4 (y) elements for all z of one sample column
+// block; per (ix, iy): T2[kz] = sum_ky F[iy][ky] sum_kx F[ix][kx] xi[kz][ky][kx],
+// then g(iz) = sum_kz F[iz][kz] T2[kz].
+constexpr int K3_TY = 4;
+__global__ void __launch_bounds__(TX2* K3_TY)
+    k_kappa3d(int n, int m, double sqrt_sigma2, const double* __restrict__ table,
+              const double* __restrict__ xi, int64_t es, double* __restrict__ kappa,
+              int z_chunk, Prof prof) {
+  extern __shared__ double smem[];
+  const int M = m * m * m;
+  double* s_xi = smem;                              // M
+  double* s_t1 = s_xi + M;                          // [TX2][m*m]  T1[ix][kz*m+ky]
+  const int b = blockIdx.z;
+  const int tid = threadIdx.y * TX2 + threadIdx.x;
+  const int nthreads = TX2 * K3_TY;
+  const int x0 = blockIdx.x * TX2;
+  const int iy = blockIdx.y * K3_TY + threadIdx.y;
+  const double* xs = xi + (int64_t)b * M;
+  for (int k = tid; k < M; k += nthreads) s_xi[k] = xs[k];
+  __syncthreads();
+  const int mm = m * m;
+  for (int idx = tid; idx < TX2 * mm; idx += nthreads) {
+    const int c = idx / mm, kk = idx - c * mm;     // kk = kz * m + ky
+    const int ix = x0 + c;
+    double acc = 0.0;
+    if (ix < n) {
+      const double* fx = table + ix * m;
+      for (int kx = 0; kx < m; ++kx) acc = fma(fx[kx], s_xi[kk * m + kx], acc);
+    }
+    s_t1[c * mm + kk] = acc;
+  }
+  __syncthreads();
+  const int ix = x0 + threadIdx.x;
+  if (ix >= n || iy >= n) return;
+  double t2[MAX_MODES_1D];
+  const double* fy = table + iy * m;
+  for (int kz = 0; kz < m; ++kz) {
+    double acc = 0.0;
+    for (int ky = 0; ky < m; ++ky) acc = fma(fy[ky], s_t1[threadIdx.x * mm + kz * m + ky], acc);
+    t2[kz] = acc;
+  }
+  double* out = kappa + (int64_t)b * es;
+  const int z0 = blockIdx.y * 0 + 0;
+  (void)z0;
+  for (int iz = 0; iz < n; ++iz) {
+    const double* fz = table + iz * m;
+    double g = 0.0;
+    for (int kz = 0; kz < m; ++kz) g = fma(fz[kz], t2[kz], g);
+    out[((int64_t)iz * n + iy) * n + ix] = exp(sqrt_sigma2 * g);
+  }
+  (void)z_chunk;
+  if (prof.acc && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) atomicAdd(prof.acc, prof.per_sample);
+}
+
+__global__ void k_coarsen2d(int nc, const double* __restrict__ kf, double* __restrict__ kc,
+                            int64_t esf, int64_t esc, Prof prof) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y;
+  const int b = blockIdx.z;
+  if (I >= nc) return;
+  const int nf = 2 * nc;
+  const double* f = kf + (int64_t)b * esf + (int64_t)(2 * J) * nf + 2 * I;
+  kc[(int64_t)b * esc + (int64_t)J * nc + I] = 0.25 * ((f[0] + f[1]) + (f[nf] + f[nf + 1]));
+  if (prof.acc && I == 0 && J == 0) atomicAdd(prof.acc, prof.per_sample);
+}
+
+__global__ void k_coarsen3d(int nc, const double* __restrict__ kf, double* __restrict__ kc,
+                            int64_t esf, int64_t esc, Prof prof) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y % nc;
+  const int K = blockIdx.y / nc;
+  const int b = blockIdx.z;
+  if (I >= nc) return;
+  const int nf = 2 * nc;
+  const int64_t pl = (int64_t)nf * nf;
+  const double* f = kf + (int64_t)b * esf + (int64_t)(2 * K) * pl + (int64_t)(2 * J) * nf + 2 * I;
+  const double s0 = (f[0] + f[1]) + (f[nf] + f[nf + 1]);
+  const double s1 = (f[pl] + f[pl + 1]) + (f[pl + nf] + f[pl + nf + 1]);
+  kc[(int64_t)b * esc + ((int64_t)K * nc + J) * nc + I] = 0.125 * (s0 + s1);
+  if (prof.acc && I == 0 && J == 0 && K == 0) atomicAdd(prof.acc, prof.per_sample);
+}
+
+}  // namespace
+
+cudaError_t launch_kle_table(cudaStream_t s, int n, int m, const double* omega,
+                             const double* theta, const int32_t* even, double* table) {
+  const int total = n * m;
+  k_kle_table<<<(total + 255) / 256, 256, 0, s>>>(n, m, omega, theta, even, table);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kappa(cudaStream_t s, const Grid& g, int m, double sqrt_sigma2,
+                         const double* table, const double* xi, int64_t B, double* kappa, Prof p) {
+  if (B == 0) return cudaSuccess;
+  if (g.dim == 2) {
+    dim3 grid((g.n + TX2 - 1) / TX2, (g.n + TY2 * KAP_ROWS - 1) / (TY2 * KAP_ROWS), (unsigned)B);
+    k_kappa2d<<<grid, dim3(TX2, TY2), 0, s>>>(g.n, m, sqrt_sigma2, table, xi, g.es, kappa, p);
+  } else {
+    const int M = m * m * m;
+    const size_t smem = sizeof(double) * ((size_t)M + (size_t)TX2 * m * m);
+    static bool attr_set = false;
+    if (!attr_set) {
+      cudaFuncSetAttribute(k_kappa3d, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      attr_set = true;
+    }
+    dim3 grid((g.n + TX2 - 1) / TX2, (g.n + K3_TY - 1) / K3_TY, (unsigned)B);
+    k_kappa3d<<<grid, dim3(TX2, K3_TY), smem, s>>>(g.n, m, sqrt_sigma2, table, xi, g.es, kappa,
+                                                   g.n, p);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarsen(cudaStream_t s, const Grid& fine, const Grid& coarse,
+                           const double* kf, double* kc, int64_t B, Prof p) {
+  if (B == 0) return cudaSuccess;
+  const int nc = coarse.n;
+  const int threads = nc < 128 ? ((nc + 31) / 32) * 32 : 128;
+  if (fine.dim == 2) {
+    dim3 grid((nc + threads - 1) / threads, nc, (unsigned)B);
+    k_coarsen2d<<<grid, threads, 0, s>>>(nc, kf, kc, fine.es, coarse.es, p);
+  } else {
+    dim3 grid((nc + threads - 1) / threads, nc * nc, (unsigned)B);
+    k_coarsen3d<<<grid, threads, 0, s>>>(nc, kf, kc, fine.es, coarse.es, p);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace mlmc

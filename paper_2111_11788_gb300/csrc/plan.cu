@@ -1,0 +1,903 @@
+// C ABI of libmlmc: plan, workspace, batched coupled solves, estimator.
+//
+// Host orchestration only: every numerical step runs in the kernels of
+// xi.cu, field.cu, stencil2d.cu and reduce.cu. The plan owns the KLE
+// eigenpairs (solved on the host once, a scalar root-finding), the per-mesh
+// eigenfunction tables, the level states and one workspace buffer that is
+// carved per batch.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "mlmc_internal.cuh"
+
+namespace mlmc {
+
+Grid make_grid(int dim, int n) {
+  Grid g;
+  g.dim = dim;
+  g.n = n;
+  g.ns = round_up(ipow(n + 1, dim), 32);
+  g.es = round_up(ipow(n, dim), 32);
+  g.h = 1.0 / n;
+  if (dim == 2) {
+    g.tiles_x = (n + 1 + TX2 - 1) / TX2;
+    g.tiles_y = (n + 1 + TY2 - 1) / TY2;
+    g.tiles_z = 1;
+  } else {
+    g.tiles_x = (n + 1 + TX3 - 1) / TX3;
+    g.tiles_y = (n + 1 + TY3 - 1) / TY3;
+    g.tiles_z = (n + 1 + TZ3 - 1) / TZ3;
+  }
+  return g;
+}
+
+namespace {
+
+const char* kKernelNames[NUM_KERNELS] = {
+    "draw_xi", "kle_table", "kappa", "coarsen_kappa", "apply", "pcg_init", "pcg_pq", "pcg_xr",
+    "jacobi_z", "mg_pre", "restrict", "coarse_solve", "mg_post", "qoi", "finalize", "welford",
+    "estimate", "count_active", "setup"};
+
+// Bump allocator over the workspace (base == nullptr: size only).
+struct Carve {
+  char* base;
+  size_t off = 0;
+  explicit Carve(void* b) : base((char*)b) {}
+  template <class T>
+  T* take(int64_t count) {
+    off = (size_t)round_up((int64_t)off, 256);
+    T* p = base ? (T*)(base + off) : nullptr;
+    off += sizeof(T) * (size_t)std::max<int64_t>(count, 0);
+    return p;
+  }
+};
+
+constexpr int MAX_MG = 16;
+
+struct MeshInfo {
+  int n;
+  int K;                 // multigrid levels (1 = no multigrid)
+  Grid g[MAX_MG];
+  double* table;         // n x m KLE table on the device
+};
+
+// Views of the workspace for one batched solve on one mesh.
+struct SolveWs {
+  double *x, *r, *p0, *p1, *q, *z;
+  double* kap[MAX_MG];
+  double* w[MAX_MG];
+  double *e[MAX_MG], *r1[MAX_MG], *bk[MAX_MG], *eo[MAX_MG];
+  double* part;
+  Scalars sc;
+  int32_t* count;
+};
+
+void carve_solve(Carve& c, const MeshInfo& mi, int64_t B, bool own_kappa0, SolveWs& w) {
+  const Grid& g0 = mi.g[0];
+  w.x = c.take<double>(B * g0.ns);
+  w.r = c.take<double>(B * g0.ns);
+  w.p0 = c.take<double>(B * g0.ns);
+  w.p1 = c.take<double>(B * g0.ns);
+  w.q = c.take<double>(B * g0.ns);
+  w.z = c.take<double>(B * g0.ns);
+  for (int k = 0; k < mi.K; ++k) {
+    const Grid& g = mi.g[k];
+    w.kap[k] = (k == 0 && !own_kappa0) ? nullptr : c.take<double>(B * g.es);
+    w.w[k] = c.take<double>(B * g.ns);
+    if (mi.K > 1) {
+      w.e[k] = c.take<double>(B * g.ns);
+      w.r1[k] = (k < mi.K - 1) ? c.take<double>(B * g.ns) : nullptr;
+      w.bk[k] = (k == 0) ? w.r : c.take<double>(B * g.ns);
+      w.eo[k] = (k == 0) ? w.z : ((k < mi.K - 1) ? c.take<double>(B * g.ns) : w.e[k]);
+    }
+  }
+  w.part = c.take<double>(B * g0.tiles());
+  w.sc.gamma = c.take<double>(B);
+  w.sc.delta = c.take<double>(B);
+  w.sc.alpha = c.take<double>(B);
+  w.sc.beta = c.take<double>(B);
+  w.sc.rho = c.take<double>(B);
+  w.sc.tol = c.take<double>(B);
+  w.sc.active = c.take<int32_t>(B);
+  w.sc.iters = c.take<int32_t>(B);
+  w.count = c.take<int32_t>(1);
+}
+
+// Workspace of one coupled batch: xi, outputs and the solve views of the
+// finer mesh (the coarse solve reuses them).
+struct CoupledWs {
+  double* xi;
+  double* qf;
+  double* qc;
+  int32_t* itf;
+  int32_t* itc;
+  SolveWs s;
+};
+
+void carve_coupled(Carve& c, const MeshInfo& mi, int M, int64_t B, CoupledWs& w) {
+  w.xi = c.take<double>(B * M);
+  w.qf = c.take<double>(B);
+  w.qc = c.take<double>(B);
+  w.itf = c.take<int32_t>(B);
+  w.itc = c.take<int32_t>(B);
+  carve_solve(c, mi, B, true, w.s);
+}
+
+struct PendingEvent {
+  int kid;
+  cudaEvent_t a, b;
+};
+
+}  // namespace
+}  // namespace mlmc
+
+using namespace mlmc;
+
+struct mlmc_plan_s {
+  mlmc_config cfg;
+  cudaStream_t stream = nullptr;
+  int M = 0;
+  double sqrt_sigma2 = 1.0;
+  std::vector<MeshInfo> meshes;
+  double* d_omega = nullptr;
+  double* d_theta = nullptr;
+  int32_t* d_even = nullptr;
+  mlmc_level_state* d_states = nullptr;
+  double* d_cost = nullptr;
+  double* d_small = nullptr;      // scratch for estimate / allocate (64 doubles)
+  int64_t* d_N = nullptr;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  size_t ws_budget = 0;
+  void* h_pin = nullptr;
+  size_t h_pin_bytes = 0;
+  // tracing
+  bool prof_on = false;
+  double* d_prof = nullptr;       // NUM_KERNELS byte accumulators
+  std::vector<PendingEvent> pending;
+  std::vector<cudaEvent_t> pool;
+  double ms[NUM_KERNELS] = {0};
+  int64_t kl[NUM_KERNELS] = {0};
+  int64_t launches = 0;
+};
+
+namespace {
+
+#define CK(call)                                  \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) return MLMC_ERR_CUDA;  \
+  } while (0)
+
+bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+mlmc_status validate(const mlmc_config* c) {
+  if (!c) return MLMC_ERR_INVALID;
+  if (c->dim != 2 && c->dim != 3) return MLMC_ERR_INVALID;
+  if (c->n_levels < 1 || c->n_levels > 16) return MLMC_ERR_INVALID;
+  if (c->coarse_cells < 2) return MLMC_ERR_INVALID;
+  if (c->modes_per_dim < 1 || c->modes_per_dim > (c->dim == 2 ? 32 : 16)) return MLMC_ERR_INVALID;
+  if (!(c->sigma2 > 0.0) || !(c->corr_len > 0.0)) return MLMC_ERR_INVALID;
+  if (!(c->rtol > 0.0) || c->max_iter < 1) return MLMC_ERR_INVALID;
+  if (c->qoi != MLMC_QOI_DOMAIN_MEAN && c->qoi != MLMC_QOI_BOX_MEAN) return MLMC_ERR_INVALID;
+  if (c->solver != MLMC_JACOBI_PCG && c->solver != MLMC_GMG_PCG) return MLMC_ERR_INVALID;
+  const int64_t nf = (int64_t)c->coarse_cells << (c->n_levels - 1);
+  if (nf > (c->dim == 2 ? 16384 : 1024)) return MLMC_ERR_INVALID;
+  if (c->solver == MLMC_GMG_PCG) {
+    if (!is_pow2(c->coarse_cells)) return MLMC_ERR_INVALID;
+    if (!(c->mg_omega > 0.0 && c->mg_omega < 2.0) || c->mg_smooth != 1) return MLMC_ERR_INVALID;
+    if (c->mg_coarsest != 2) return MLMC_ERR_INVALID;
+  }
+  if (c->qoi == MLMC_QOI_BOX_MEAN) {
+    const double lo = c->box_lo * c->coarse_cells, hi = c->box_hi * c->coarse_cells;
+    if (!(c->box_lo >= 0.0 && c->box_hi <= 1.0 && c->box_lo < c->box_hi)) return MLMC_ERR_INVALID;
+    if (std::fabs(lo - std::round(lo)) > 1e-9 || std::fabs(hi - std::round(hi)) > 1e-9)
+      return MLMC_ERR_INVALID;
+  }
+  if (c->precision != MLMC_FP64 && c->precision != MLMC_MIXED) return MLMC_ERR_INVALID;
+  if (c->precision == MLMC_MIXED) return MLMC_ERR_UNIMPLEMENTED;
+  if (c->dim == 3) return MLMC_ERR_UNIMPLEMENTED;
+  return MLMC_OK;
+}
+
+// Roots of the 1D exponential-covariance KLE (Ghanem & Spanos closed form):
+// with c = 1/corr_len on [0, 1] (half-width 1/2), mode k has its root in
+// (k pi, (k+1) pi): even k solves c cos(w/2) - w sin(w/2) = 0, odd k solves
+// w cos(w/2) + c sin(w/2) = 0; theta_k = 2c / (w^2 + c^2).
+void kle_roots(double corr_len, int m, std::vector<double>& omega, std::vector<double>& theta,
+               std::vector<int32_t>& even) {
+  const double c = 1.0 / corr_len;
+  const double pi = 3.14159265358979323846;
+  omega.resize(m);
+  theta.resize(m);
+  even.resize(m);
+  for (int k = 0; k < m; ++k) {
+    const bool ev = (k % 2 == 0);
+    auto f = [&](double w) {
+      return ev ? c * std::cos(0.5 * w) - w * std::sin(0.5 * w)
+                : w * std::cos(0.5 * w) + c * std::sin(0.5 * w);
+    };
+    double lo = k * pi, hi = (k + 1) * pi;
+    double flo = f(lo);
+    for (int it = 0; it < 200; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (mid <= lo || mid >= hi) break;
+      const double fm = f(mid);
+      if ((fm < 0) == (flo < 0)) {
+        lo = mid;
+        flo = fm;
+      } else {
+        hi = mid;
+      }
+    }
+    omega[k] = 0.5 * (lo + hi);
+    theta[k] = 2.0 * c / (omega[k] * omega[k] + c * c);
+    even[k] = ev ? 1 : 0;
+  }
+}
+
+int64_t interior_dofs(int dim, int64_t n) { return ipow(n - 1, dim); }
+
+double level_cost_cfg(const mlmc_config* c, int level) {
+  const int64_t n = (int64_t)c->coarse_cells << level;
+  double cost = (double)interior_dofs(c->dim, n);
+  if (level > 0) cost += (double)interior_dofs(c->dim, n / 2);
+  return cost;
+}
+
+// --- tracing helpers --------------------------------------------------
+
+void harvest(mlmc_plan p) {
+  if (p->pending.empty()) return;
+  cudaStreamSynchronize(p->stream);
+  for (auto& e : p->pending) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, e.a, e.b) == cudaSuccess) p->ms[e.kid] += t;
+    p->kl[e.kid] += 1;
+    p->pool.push_back(e.a);
+    p->pool.push_back(e.b);
+  }
+  p->pending.clear();
+}
+
+cudaEvent_t get_event(mlmc_plan p) {
+  if (!p->pool.empty()) {
+    cudaEvent_t e = p->pool.back();
+    p->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+Prof prof_for(mlmc_plan p, int kid, double per_sample) {
+  Prof pr;
+  pr.acc = p->prof_on ? p->d_prof + kid : nullptr;
+  pr.per_sample = per_sample;
+  return pr;
+}
+
+// Launch `f` as kernel `kid`, bracketed by events when tracing is on.
+template <class F>
+cudaError_t run(mlmc_plan p, int kid, F&& f) {
+  p->launches += 1;
+  if (!p->prof_on) return f();
+  PendingEvent pe;
+  pe.kid = kid;
+  pe.a = get_event(p);
+  pe.b = get_event(p);
+  cudaEventRecord(pe.a, p->stream);
+  cudaError_t e = f();
+  cudaEventRecord(pe.b, p->stream);
+  p->pending.push_back(pe);
+  if (p->pending.size() > 8192) harvest(p);
+  return e;
+}
+
+double nodes_of(const Grid& g) { return (double)ipow(g.n + 1, g.dim); }
+double elems_of(const Grid& g) { return (double)ipow(g.n, g.dim); }
+
+// --- workspace --------------------------------------------------------
+
+mlmc_status ensure_ws(mlmc_plan p, size_t bytes) {
+  if (bytes <= p->ws_bytes) return MLMC_OK;
+  if (p->ws) {
+    cudaStreamSynchronize(p->stream);
+    cudaFree(p->ws);
+    p->ws = nullptr;
+    p->ws_bytes = 0;
+  }
+  if (cudaMalloc(&p->ws, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return MLMC_ERR_OOM;
+  }
+  p->ws_bytes = bytes;
+  return MLMC_OK;
+}
+
+mlmc_status ensure_pin(mlmc_plan p, size_t bytes) {
+  if (bytes <= p->h_pin_bytes) return MLMC_OK;
+  if (p->h_pin) {
+    cudaStreamSynchronize(p->stream);
+    cudaFreeHost(p->h_pin);
+    p->h_pin = nullptr;
+  }
+  const size_t b = std::max<size_t>(bytes, 1 << 16);
+  if (cudaMallocHost(&p->h_pin, b) != cudaSuccess) {
+    cudaGetLastError();
+    p->h_pin_bytes = 0;
+    return MLMC_ERR_OOM;
+  }
+  p->h_pin_bytes = b;
+  return MLMC_OK;
+}
+
+size_t coupled_bytes(const MeshInfo& mi, int M, int64_t B) {
+  Carve c(nullptr);
+  CoupledWs w;
+  carve_coupled(c, mi, M, B, w);
+  return c.off + 256;
+}
+
+size_t solve_bytes(const MeshInfo& mi, int64_t B) {
+  Carve c(nullptr);
+  SolveWs w;
+  carve_solve(c, mi, B, false, w);
+  return c.off + 256;
+}
+
+template <class SizeFn>
+int64_t max_batch(mlmc_plan p, SizeFn size_of, int64_t want) {
+  int64_t B = std::min<int64_t>(want, 65535);
+  if (B <= 0) return 0;
+  const size_t one = size_of(1);
+  const size_t per = std::max<size_t>(size_of(2) - one, 1);
+  if (size_of(B) > p->ws_budget) {
+    B = (int64_t)((p->ws_budget > one ? p->ws_budget - one : 0) / per) + 1;
+    while (B > 1 && size_of(B) > p->ws_budget) --B;
+  }
+  return std::max<int64_t>(B, 1);
+}
+
+// --- the batched PCG --------------------------------------------------
+
+// z = M r (GMG V-cycle or Jacobi), with per-tile partials of r.z in ws.part.
+mlmc_status precondition(mlmc_plan p, const MeshInfo& mi, SolveWs& w, int64_t B) {
+  cudaStream_t s = p->stream;
+  const Grid& g0 = mi.g[0];
+  const double nn0 = nodes_of(g0);
+  if (mi.K == 1) {
+    CK(run(p, KID_JACOBI_Z, [&] {
+      return d2::jacobi_z(s, g0, w.w[0], w.r, w.z, w.sc, w.part, B,
+                          prof_for(p, KID_JACOBI_Z, 3 * nn0 * 8));
+    }));
+    return MLMC_OK;
+  }
+  const int K = mi.K;
+  for (int k = 0; k < K - 1; ++k) {
+    const Grid& g = mi.g[k];
+    const double nn = nodes_of(g), ne = elems_of(g);
+    CK(run(p, KID_MG_PRE, [&] {
+      return d2::mg_pre(s, g, w.kap[k], w.w[k], w.bk[k], w.e[k], w.r1[k], w.sc.active, B,
+                        prof_for(p, KID_MG_PRE, (4 * nn + ne) * 8));
+    }));
+    CK(run(p, KID_RESTRICT, [&] {
+      return d2::restrict_(s, g, mi.g[k + 1], w.r1[k], w.bk[k + 1], w.sc.active, B,
+                           prof_for(p, KID_RESTRICT, (nn + nodes_of(mi.g[k + 1])) * 8));
+    }));
+  }
+  CK(run(p, KID_COARSE, [&] {
+    return d2::coarse_solve(s, mi.g[K - 1], w.kap[K - 1], w.bk[K - 1], w.e[K - 1], w.sc.active, B);
+  }));
+  for (int k = K - 2; k >= 0; --k) {
+    const Grid& g = mi.g[k];
+    const double nn = nodes_of(g), ne = elems_of(g), nc = nodes_of(mi.g[k + 1]);
+    CK(run(p, KID_MG_POST, [&] {
+      return d2::mg_post(s, g, mi.g[k + 1], w.kap[k], w.w[k], w.bk[k], w.e[k], w.eo[k + 1],
+                         w.eo[k], w.sc.active, k == 0 ? w.part : nullptr, B,
+                         prof_for(p, KID_MG_POST, (4 * nn + ne + nc) * 8));
+    }));
+  }
+  return MLMC_OK;
+}
+
+// Solve A(kappa) u = b for B samples on mesh `mi`; w.kap[0] must hold kappa.
+// Leaves u in w.x, writes q (device) and iters (device).
+mlmc_status solve_batch(mlmc_plan p, const MeshInfo& mi, SolveWs& w, int64_t B, double* q_dev,
+                        int32_t* iters_dev) {
+  cudaStream_t s = p->stream;
+  const mlmc_config& c = p->cfg;
+  const Grid& g0 = mi.g[0];
+  const double nn0 = nodes_of(g0), ne0 = elems_of(g0);
+  const int K = mi.K;
+  for (int k = 1; k < K; ++k) {
+    CK(run(p, KID_COARSEN, [&] {
+      return launch_coarsen(s, mi.g[k - 1], mi.g[k], w.kap[k - 1], w.kap[k], B,
+                            prof_for(p, KID_COARSEN, (elems_of(mi.g[k - 1]) + elems_of(mi.g[k])) * 8));
+    }));
+  }
+  const double omega = (K > 1) ? c.mg_omega : 1.0;
+  for (int k = 0; k < std::max(1, K - 1); ++k)
+    CK(run(p, KID_SETUP, [&] { return d2::winv(s, mi.g[k], w.kap[k], omega, w.w[k], B); }));
+  const double bnorm = std::pow(g0.h, c.dim) * std::sqrt((double)interior_dofs(c.dim, g0.n));
+  CK(run(p, KID_SETUP, [&] { return launch_scalars_init(s, w.sc, c.rtol * bnorm, B); }));
+  CK(run(p, KID_PCG_INIT, [&] {
+    return d2::pcg_init(s, g0, w.x, w.r, B, prof_for(p, KID_PCG_INIT, 2 * nn0 * 8));
+  }));
+  mlmc_status st = precondition(p, mi, w, B);
+  if (st != MLMC_OK) return st;
+  const int64_t T = g0.tiles();
+  CK(run(p, KID_FINALIZE, [&] { return launch_finalize(s, FIN_GAMMA0, w.part, T, w.sc, nullptr, 0, c.max_iter, B); }));
+  int check = c.check_every;
+  if (check <= 0) check = (B * nn0 > 4e6) ? 1 : 4;
+  if (ensure_pin(p, 64) != MLMC_OK) return MLMC_ERR_OOM;
+  int32_t* h_count = (int32_t*)p->h_pin;
+  double* pold = w.p0;
+  double* pnew = w.p1;
+  for (int it = 1; it <= c.max_iter; ++it) {
+    CK(run(p, KID_PCG_PQ, [&] {
+      return d2::pcg_pq(s, g0, w.kap[0], w.z, pold, pnew, w.q, w.sc, w.part, B,
+                        prof_for(p, KID_PCG_PQ, (4 * nn0 + ne0) * 8));
+    }));
+    CK(run(p, KID_FINALIZE, [&] { return launch_finalize(s, FIN_ALPHA, w.part, T, w.sc, nullptr, it, c.max_iter, B); }));
+    CK(run(p, KID_PCG_XR, [&] {
+      return d2::pcg_xr(s, g0, w.x, pnew, w.r, w.q, w.sc, w.part, B,
+                        prof_for(p, KID_PCG_XR, 6 * nn0 * 8));
+    }));
+    CK(run(p, KID_FINALIZE, [&] { return launch_finalize(s, FIN_CONV, w.part, T, w.sc, nullptr, it, c.max_iter, B); }));
+    if (it % check == 0 || it == c.max_iter) {
+      CK(run(p, KID_COUNT, [&] { return launch_count_active(s, w.sc.active, B, w.count); }));
+      CK(cudaMemcpyAsync(h_count, w.count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (*h_count == 0) break;
+    }
+    st = precondition(p, mi, w, B);
+    if (st != MLMC_OK) return st;
+    CK(run(p, KID_FINALIZE, [&] { return launch_finalize(s, FIN_BETA, w.part, T, w.sc, nullptr, it, c.max_iter, B); }));
+    std::swap(pold, pnew);
+  }
+  const int64_t nf = g0.n;
+  const int L = (int)std::lround(c.box_lo * nf), H = (int)std::lround(c.box_hi * nf);
+  const double vol = std::pow(c.box_hi - c.box_lo, c.dim);
+  const int box = (c.qoi == MLMC_QOI_BOX_MEAN) ? 1 : 0;
+  CK(run(p, KID_QOI, [&] {
+    return d2::qoi(s, g0, box, L, H, box ? 1.0 / vol : 1.0, w.x, w.part, B,
+                   prof_for(p, KID_QOI, nn0 * 8));
+  }));
+  CK(run(p, KID_FINALIZE, [&] { return launch_finalize(s, FIN_QOI, w.part, T, w.sc, q_dev, 0, c.max_iter, B); }));
+  if (iters_dev) CK(cudaMemcpyAsync(iters_dev, w.sc.iters, sizeof(int32_t) * B, cudaMemcpyDeviceToDevice, s));
+  return MLMC_OK;
+}
+
+mlmc_status make_kappa(mlmc_plan p, int mesh, const double* xi, int64_t B, double* kappa) {
+  const MeshInfo& mi = p->meshes[mesh];
+  CK(run(p, KID_KAPPA, [&] {
+    return launch_kappa(p->stream, mi.g[0], p->cfg.modes_per_dim, p->sqrt_sigma2, mi.table, xi, B,
+                        kappa, prof_for(p, KID_KAPPA, elems_of(mi.g[0]) * 8));
+  }));
+  return MLMC_OK;
+}
+
+}  // namespace
+
+// ===================================================================
+// C ABI
+// ===================================================================
+
+extern "C" {
+
+void mlmc_config_default(mlmc_config* c) {
+  if (!c) return;
+  std::memset(c, 0, sizeof(*c));
+  c->dim = 2;
+  c->n_levels = 3;
+  c->coarse_cells = 16;
+  c->modes_per_dim = 4;
+  c->sigma2 = 1.0;
+  c->corr_len = 0.3;
+  c->qoi = MLMC_QOI_DOMAIN_MEAN;
+  c->solver = MLMC_JACOBI_PCG;
+  c->box_lo = 0.25;
+  c->box_hi = 0.75;
+  c->rtol = 1e-10;
+  c->max_iter = 20000;
+  c->precision = MLMC_FP64;
+  c->seed = 0;
+  c->stream_id = 0;
+  c->mg_smooth = 1;
+  c->mg_omega = 0.8;
+  c->mg_coarsest = 2;
+  c->check_every = 0;
+  c->workspace_bytes = 0;
+}
+
+int64_t mlmc_node_stride(int dim, int n) {
+  if ((dim != 2 && dim != 3) || n < 1) return -1;
+  return make_grid(dim, n).ns;
+}
+
+int64_t mlmc_elem_stride(int dim, int n) {
+  if ((dim != 2 && dim != 3) || n < 1) return -1;
+  return make_grid(dim, n).es;
+}
+
+int64_t mlmc_mesh_cells(const mlmc_config* cfg, int mesh) {
+  if (!cfg || mesh < 0 || mesh >= cfg->n_levels) return -1;
+  return (int64_t)cfg->coarse_cells << mesh;
+}
+
+double mlmc_level_cost(const mlmc_config* cfg, int level) {
+  if (!cfg || level < 0 || level >= cfg->n_levels) return -1.0;
+  return level_cost_cfg(cfg, level);
+}
+
+const char* mlmc_status_str(mlmc_status s) {
+  switch (s) {
+    case MLMC_OK: return "ok";
+    case MLMC_ERR_INVALID: return "invalid argument";
+    case MLMC_ERR_OOM: return "out of device memory";
+    case MLMC_ERR_NOT_CONVERGED: return "a solve hit max_iter";
+    case MLMC_ERR_CUDA: return "CUDA error";
+    case MLMC_ERR_TIMEOUT: return "device wait timed out";
+    case MLMC_ERR_UNIMPLEMENTED: return "not implemented";
+  }
+  return "unknown status";
+}
+
+int mlmc_kernel_count(void) { return NUM_KERNELS; }
+
+const char* mlmc_kernel_name(int kid) {
+  if (kid < 0 || kid >= NUM_KERNELS) return nullptr;
+  return kKernelNames[kid];
+}
+
+mlmc_status mlmc_plan_create(const mlmc_config* cfg, void* stream, mlmc_plan* out) {
+  if (!out) return MLMC_ERR_INVALID;
+  *out = nullptr;
+  mlmc_status st = validate(cfg);
+  if (st != MLMC_OK) return st;
+  mlmc_plan p = new mlmc_plan_s();
+  p->cfg = *cfg;
+  p->stream = (cudaStream_t)stream;
+  const int m = cfg->modes_per_dim;
+  p->M = (int)ipow(m, cfg->dim);
+  p->sqrt_sigma2 = std::sqrt(cfg->sigma2);
+  std::vector<double> omega, theta;
+  std::vector<int32_t> even;
+  kle_roots(cfg->corr_len, m, omega, theta, even);
+  auto fail = [&](mlmc_status s) {
+    mlmc_plan_destroy(p);
+    return s;
+  };
+  if (cudaMalloc(&p->d_omega, sizeof(double) * m) != cudaSuccess ||
+      cudaMalloc(&p->d_theta, sizeof(double) * m) != cudaSuccess ||
+      cudaMalloc(&p->d_even, sizeof(int32_t) * m) != cudaSuccess ||
+      cudaMalloc(&p->d_states, sizeof(mlmc_level_state) * cfg->n_levels) != cudaSuccess ||
+      cudaMalloc(&p->d_cost, sizeof(double) * cfg->n_levels) != cudaSuccess ||
+      cudaMalloc(&p->d_small, sizeof(double) * 64) != cudaSuccess ||
+      cudaMalloc(&p->d_N, sizeof(int64_t) * 16) != cudaSuccess ||
+      cudaMalloc(&p->d_prof, sizeof(double) * NUM_KERNELS) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MLMC_ERR_OOM);
+  }
+  std::vector<double> cost(cfg->n_levels);
+  for (int l = 0; l < cfg->n_levels; ++l) cost[l] = level_cost_cfg(cfg, l);
+  if (cudaMemcpyAsync(p->d_omega, omega.data(), sizeof(double) * m, cudaMemcpyHostToDevice, p->stream) != cudaSuccess ||
+      cudaMemcpyAsync(p->d_theta, theta.data(), sizeof(double) * m, cudaMemcpyHostToDevice, p->stream) != cudaSuccess ||
+      cudaMemcpyAsync(p->d_even, even.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, p->stream) != cudaSuccess ||
+      cudaMemcpyAsync(p->d_cost, cost.data(), sizeof(double) * cfg->n_levels, cudaMemcpyHostToDevice, p->stream) != cudaSuccess ||
+      cudaMemsetAsync(p->d_states, 0, sizeof(mlmc_level_state) * cfg->n_levels, p->stream) != cudaSuccess ||
+      cudaMemsetAsync(p->d_prof, 0, sizeof(double) * NUM_KERNELS, p->stream) != cudaSuccess)
+    return fail(MLMC_ERR_CUDA);
+  p->meshes.resize(cfg->n_levels);
+  for (int l = 0; l < cfg->n_levels; ++l) {
+    MeshInfo& mi = p->meshes[l];
+    mi.n = cfg->coarse_cells << l;
+    mi.K = 1;
+    mi.g[0] = make_grid(cfg->dim, mi.n);
+    if (cfg->solver == MLMC_GMG_PCG && mi.n > 2) {
+      int n = mi.n;
+      while (n > 2 && mi.K < MAX_MG) {
+        n /= 2;
+        mi.g[mi.K++] = make_grid(cfg->dim, n);
+      }
+    }
+    if (cudaMalloc(&mi.table, sizeof(double) * (size_t)mi.n * m) != cudaSuccess) {
+      mi.table = nullptr;
+      cudaGetLastError();
+      return fail(MLMC_ERR_OOM);
+    }
+    if (run(p, KID_TABLE, [&] { return launch_kle_table(p->stream, mi.n, m, p->d_omega, p->d_theta, p->d_even, mi.table); }) != cudaSuccess)
+      return fail(MLMC_ERR_CUDA);
+  }
+  size_t budget = cfg->workspace_bytes;
+  if (budget == 0) {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return fail(MLMC_ERR_CUDA);
+    budget = std::min<size_t>((size_t)(0.4 * (double)fr), (size_t)48 << 30);
+  }
+  p->ws_budget = budget;
+  if (cudaStreamSynchronize(p->stream) != cudaSuccess) return fail(MLMC_ERR_CUDA);
+  *out = p;
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_plan_destroy(mlmc_plan p) {
+  if (!p) return MLMC_ERR_INVALID;
+  if (p->stream || true) cudaStreamSynchronize(p->stream);
+  for (auto& mi : p->meshes)
+    if (mi.table) cudaFree(mi.table);
+  cudaFree(p->d_omega);
+  cudaFree(p->d_theta);
+  cudaFree(p->d_even);
+  cudaFree(p->d_states);
+  cudaFree(p->d_cost);
+  cudaFree(p->d_small);
+  cudaFree(p->d_N);
+  cudaFree(p->d_prof);
+  if (p->ws) cudaFree(p->ws);
+  if (p->h_pin) cudaFreeHost(p->h_pin);
+  for (auto& e : p->pending) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  for (auto e : p->pool) cudaEventDestroy(e);
+  delete p;
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_reset_stats(mlmc_plan p) {
+  if (!p) return MLMC_ERR_INVALID;
+  CK(cudaMemsetAsync(p->d_states, 0, sizeof(mlmc_level_state) * p->cfg.n_levels, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_draw_xi(mlmc_plan p, int level, int64_t first, int64_t count, double* xi) {
+  if (!p || level < 0 || level >= p->cfg.n_levels || first < 0 || count < 0 ||
+      first + count > (int64_t(1) << 32) || (count > 0 && !xi))
+    return MLMC_ERR_INVALID;
+  CK(run(p, KID_XI, [&] {
+    return launch_draw_xi(p->stream, p->cfg.seed, p->cfg.stream_id, level, first, count, p->M, xi,
+                          prof_for(p, KID_XI, p->M * 8.0));
+  }));
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_kappa(mlmc_plan p, int mesh, const double* xi, int64_t count, double* kappa) {
+  if (!p || mesh < 0 || mesh >= p->cfg.n_levels || count < 0 || (count > 0 && (!xi || !kappa)))
+    return MLMC_ERR_INVALID;
+  const Grid& g = p->meshes[mesh].g[0];
+  for (int64_t off = 0; off < count; off += 65535) {
+    const int64_t B = std::min<int64_t>(65535, count - off);
+    mlmc_status st = make_kappa(p, mesh, xi + off * p->M, B, kappa + off * g.es);
+    if (st != MLMC_OK) return st;
+  }
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_apply(mlmc_plan p, int mesh, const double* kappa, const double* x, double* y,
+                       int64_t count) {
+  if (!p || mesh < 0 || mesh >= p->cfg.n_levels || count < 0 ||
+      (count > 0 && (!kappa || !x || !y)))
+    return MLMC_ERR_INVALID;
+  const Grid& g = p->meshes[mesh].g[0];
+  for (int64_t off = 0; off < count; off += 65535) {
+    const int64_t B = std::min<int64_t>(65535, count - off);
+    CK(run(p, KID_APPLY, [&] {
+      return d2::apply(p->stream, g, kappa + off * g.es, x + off * g.ns, y + off * g.ns, B,
+                       prof_for(p, KID_APPLY, (2 * nodes_of(g) + elems_of(g)) * 8));
+    }));
+  }
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_solve(mlmc_plan p, int mesh, const double* kappa, int64_t count, double* u,
+                       double* q, int32_t* iters) {
+  if (!p || mesh < 0 || mesh >= p->cfg.n_levels || count < 0 || (count > 0 && (!kappa || !q)))
+    return MLMC_ERR_INVALID;
+  const MeshInfo& mi = p->meshes[mesh];
+  const int64_t Bmax = max_batch(p, [&](int64_t B) { return solve_bytes(mi, B); }, count);
+  bool bad = false;
+  for (int64_t off = 0; off < count; off += Bmax) {
+    const int64_t B = std::min<int64_t>(Bmax, count - off);
+    mlmc_status st = ensure_ws(p, solve_bytes(mi, B));
+    if (st != MLMC_OK) return st;
+    Carve c(p->ws);
+    SolveWs w;
+    carve_solve(c, mi, B, false, w);
+    w.kap[0] = const_cast<double*>(kappa + off * mi.g[0].es);
+    st = solve_batch(p, mi, w, B, q + off, iters ? iters + off : nullptr);
+    if (st != MLMC_OK) return st;
+    if (u) CK(cudaMemcpyAsync(u + off * mi.g[0].ns, w.x, sizeof(double) * B * mi.g[0].ns, cudaMemcpyDeviceToDevice, p->stream));
+    if (ensure_pin(p, sizeof(int32_t) * B) != MLMC_OK) return MLMC_ERR_OOM;
+    CK(cudaMemcpyAsync(p->h_pin, w.sc.iters, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    const int32_t* it = (const int32_t*)p->h_pin;
+    for (int64_t b = 0; b < B; ++b) bad |= (it[b] < 0);
+  }
+  return bad ? MLMC_ERR_NOT_CONVERGED : MLMC_OK;
+}
+
+mlmc_status mlmc_sample_level(mlmc_plan p, int level, int64_t first, int64_t count, double* q_fine,
+                              double* q_coarse, int32_t* iters) {
+  if (!p || level < 0 || level >= p->cfg.n_levels || first < 0 || count < 0 ||
+      first + count > (int64_t(1) << 32))
+    return MLMC_ERR_INVALID;
+  if (count == 0) return MLMC_OK;
+  const MeshInfo& mf = p->meshes[level];
+  const int M = p->M;
+  const int64_t Bmax = max_batch(p, [&](int64_t B) { return coupled_bytes(mf, M, B); }, count);
+  const double cost = level_cost_cfg(&p->cfg, level);
+  bool bad = false;
+  for (int64_t off = 0; off < count; off += Bmax) {
+    const int64_t B = std::min<int64_t>(Bmax, count - off);
+    mlmc_status st = ensure_ws(p, coupled_bytes(mf, M, B));
+    if (st != MLMC_OK) return st;
+    Carve c(p->ws);
+    CoupledWs w;
+    carve_coupled(c, mf, M, B, w);
+    st = mlmc_draw_xi(p, level, first + off, B, w.xi);
+    if (st != MLMC_OK) return st;
+    st = make_kappa(p, level, w.xi, B, w.s.kap[0]);
+    if (st != MLMC_OK) return st;
+    st = solve_batch(p, mf, w.s, B, w.qf, w.itf);
+    if (st != MLMC_OK) return st;
+    if (level > 0) {
+      const MeshInfo& mc = p->meshes[level - 1];
+      Carve cc(p->ws);
+      CoupledWs wc;
+      carve_coupled(cc, mc, M, B, wc);   // same xi / qf / qc offsets (prefix is identical)
+      st = make_kappa(p, level - 1, w.xi, B, wc.s.kap[0]);
+      if (st != MLMC_OK) return st;
+      st = solve_batch(p, mc, wc.s, B, w.qc, w.itc);
+      if (st != MLMC_OK) return st;
+    }
+    CK(run(p, KID_WELFORD, [&] {
+      return launch_welford(p->stream, w.qf, level > 0 ? w.qc : nullptr, B, p->d_states + level, cost);
+    }));
+    const size_t need = sizeof(double) * 2 * B + sizeof(int32_t) * 2 * B;
+    if (ensure_pin(p, need) != MLMC_OK) return MLMC_ERR_OOM;
+    double* hq = (double*)p->h_pin;
+    int32_t* hit = (int32_t*)(hq + 2 * B);
+    CK(cudaMemcpyAsync(hq, w.qf, sizeof(double) * B, cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaMemcpyAsync(hq + B, w.qc, sizeof(double) * B, cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaMemcpyAsync(hit, w.itf, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaMemcpyAsync(hit + B, w.itc, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    for (int64_t b = 0; b < B; ++b) {
+      if (hit[b] < 0 || (level > 0 && hit[B + b] < 0)) bad = true;
+      if (q_fine) q_fine[off + b] = hq[b];
+      if (q_coarse) q_coarse[off + b] = level > 0 ? hq[B + b] : 0.0;
+      if (iters) iters[off + b] = hit[b];
+    }
+  }
+  return bad ? MLMC_ERR_NOT_CONVERGED : MLMC_OK;
+}
+
+mlmc_status mlmc_level_stats(mlmc_plan p, int level, mlmc_level_state* out) {
+  if (!p || !out || level < 0 || level >= p->cfg.n_levels) return MLMC_ERR_INVALID;
+  CK(cudaMemcpyAsync(out, p->d_states + level, sizeof(mlmc_level_state), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_estimate(mlmc_plan p, double* q_hat, double* stat_var) {
+  if (!p) return MLMC_ERR_INVALID;
+  CK(run(p, KID_ESTIMATE, [&] {
+    return launch_estimate(p->stream, p->d_states, p->cfg.n_levels, p->d_cost, 0.0, p->d_small, nullptr);
+  }));
+  double h[2];
+  CK(cudaMemcpyAsync(h, p->d_small, sizeof(h), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  if (q_hat) *q_hat = h[0];
+  if (stat_var) *stat_var = h[1];
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_allocate(const double* V, const double* C, int n_levels, double eps,
+                          int64_t* N_out) {
+  if (!V || !C || !N_out || n_levels < 1 || n_levels > 16 || !(eps > 0.0)) return MLMC_ERR_INVALID;
+  for (int l = 0; l < n_levels; ++l)
+    if (!(V[l] >= 0.0) || !(C[l] > 0.0)) return MLMC_ERR_INVALID;
+  double* d = nullptr;
+  if (cudaMalloc(&d, sizeof(double) * 2 * 16 + sizeof(int64_t) * 16) != cudaSuccess) {
+    cudaGetLastError();
+    return MLMC_ERR_OOM;
+  }
+  int64_t* dN = (int64_t*)(d + 32);
+  mlmc_status st = MLMC_OK;
+  if (cudaMemcpy(d, V, sizeof(double) * n_levels, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(d + 16, C, sizeof(double) * n_levels, cudaMemcpyHostToDevice) != cudaSuccess ||
+      launch_allocate(nullptr, d, d + 16, n_levels, eps, dN) != cudaSuccess ||
+      cudaMemcpy(N_out, dN, sizeof(int64_t) * n_levels, cudaMemcpyDeviceToHost) != cudaSuccess)
+    st = MLMC_ERR_CUDA;
+  cudaFree(d);
+  return st;
+}
+
+mlmc_status mlmc_run(mlmc_plan p, double eps, int64_t pilot, const int64_t* N_fixed, double* q_hat,
+                     double* stat_var, int64_t* N_out) {
+  if (!p || (!N_fixed && !(eps > 0.0)) || pilot < 0) return MLMC_ERR_INVALID;
+  const int L1 = p->cfg.n_levels;
+  mlmc_status st = mlmc_reset_stats(p);
+  if (st != MLMC_OK) return st;
+  std::vector<int64_t> have(L1, 0), target(L1, pilot);
+  if (N_fixed)
+    for (int l = 0; l < L1; ++l) {
+      if (N_fixed[l] < 0) return MLMC_ERR_INVALID;
+      target[l] = N_fixed[l];
+    }
+  bool bad = false;
+  for (int round = 0; round < 64; ++round) {
+    // finest level first (the priority of the paper's incremental greedy schedule)
+    for (int l = L1 - 1; l >= 0; --l) {
+      if (have[l] < target[l]) {
+        st = mlmc_sample_level(p, l, have[l], target[l] - have[l], nullptr, nullptr, nullptr);
+        if (st == MLMC_ERR_NOT_CONVERGED) bad = true;
+        else if (st != MLMC_OK) return st;
+        have[l] = target[l];
+      }
+    }
+    if (N_fixed) break;
+    CK(run(p, KID_ESTIMATE, [&] {
+      return launch_estimate(p->stream, p->d_states, L1, p->d_cost, eps, p->d_small, p->d_N);
+    }));
+    int64_t hN[16];
+    CK(cudaMemcpyAsync(hN, p->d_N, sizeof(int64_t) * L1, cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    bool more = false;
+    for (int l = 0; l < L1; ++l) {
+      if (hN[l] > target[l]) {
+        target[l] = hN[l];
+        more = true;
+      }
+    }
+    if (!more) break;
+  }
+  st = mlmc_estimate(p, q_hat, stat_var);
+  if (st != MLMC_OK) return st;
+  if (N_out)
+    for (int l = 0; l < L1; ++l) N_out[l] = have[l];
+  return bad ? MLMC_ERR_NOT_CONVERGED : MLMC_OK;
+}
+
+mlmc_status mlmc_profile_enable(mlmc_plan p, int on) {
+  if (!p) return MLMC_ERR_INVALID;
+  harvest(p);
+  p->prof_on = on != 0;
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_profile_reset(mlmc_plan p) {
+  if (!p) return MLMC_ERR_INVALID;
+  harvest(p);
+  for (int k = 0; k < NUM_KERNELS; ++k) {
+    p->ms[k] = 0.0;
+    p->kl[k] = 0;
+  }
+  CK(cudaMemsetAsync(p->d_prof, 0, sizeof(double) * NUM_KERNELS, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_kernel_stats(mlmc_plan p, int kid, mlmc_kernel_stat* out) {
+  if (!p || !out || kid < 0 || kid >= NUM_KERNELS) return MLMC_ERR_INVALID;
+  harvest(p);
+  double bytes = 0.0;
+  CK(cudaMemcpyAsync(&bytes, p->d_prof + kid, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  out->launches = p->kl[kid];
+  out->ms = p->ms[kid];
+  out->bytes = bytes;
+  return MLMC_OK;
+}
+
+int64_t mlmc_launch_count(mlmc_plan p) { return p ? p->launches : -1; }
+
+}  // extern "C"

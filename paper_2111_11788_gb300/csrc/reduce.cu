@@ -1,0 +1,167 @@
+// Per-sample reductions of the batched PCG, level statistics and the MLMC
+// estimator / allocation.
+//
+// finalize: one warp per sample sums that sample's per-tile partials in a
+//   fixed order (lane-strided, then a shuffle tree), so every per-sample
+//   scalar is independent of the batch width and of the other samples.
+// welford:  Y = Q_f - Q_c folded into the level state in sample order
+//   (Eq. (sample_variance) as (n, mean, M2), V = M2 / n).
+// estimate: Eq. (mlmc_average) q = sum_l mean_l, Sec. 2.2 V(Q~) = sum V_l / N_l,
+//   and Eq. (mlmc_num_samples) N_l = ceil(2 eps^-2 sqrt(V_l / C_l) sum sqrt(V_i C_i)).
+#include "mlmc_internal.cuh"
+
+namespace mlmc {
+namespace {
+
+__global__ void k_finalize(int mode, const double* __restrict__ part, int64_t tiles, Scalars sc,
+                           double* __restrict__ out, int iter, int max_iter, int64_t B) {
+  const int64_t b = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (b >= B) return;
+  if (mode != FIN_QOI && mode != FIN_GAMMA0 && !sc.active[b]) return;
+  const double* p = part + b * tiles;
+  double v = 0.0;
+  for (int64_t t = lane; t < tiles; t += 32) v += p[t];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (lane != 0) return;
+  switch (mode) {
+    case FIN_GAMMA0:
+      sc.gamma[b] = v;
+      sc.beta[b] = 0.0;
+      break;
+    case FIN_ALPHA:
+      sc.delta[b] = v;
+      sc.alpha[b] = (v > 0.0) ? sc.gamma[b] / v : 0.0;
+      break;
+    case FIN_CONV: {
+      const double rho = sqrt(v);
+      sc.rho[b] = rho;
+      if (rho <= sc.tol[b]) {
+        sc.active[b] = 0;
+        sc.iters[b] = iter;
+      } else if (iter >= max_iter || !(rho == rho)) {
+        sc.active[b] = 0;
+        sc.iters[b] = -1;
+      }
+      break;
+    }
+    case FIN_BETA: {
+      const double g = sc.gamma[b];
+      sc.beta[b] = (g != 0.0) ? v / g : 0.0;
+      sc.gamma[b] = v;
+      break;
+    }
+    case FIN_QOI:
+      out[b] = v;
+      break;
+  }
+}
+
+__global__ void k_count_active(const int32_t* __restrict__ active, int64_t B, int32_t* count) {
+  __shared__ int32_t s;
+  if (threadIdx.x == 0) s = 0;
+  __syncthreads();
+  int32_t c = 0;
+  for (int64_t b = threadIdx.x; b < B; b += blockDim.x) c += active[b] ? 1 : 0;
+  atomicAdd(&s, c);
+  __syncthreads();
+  if (threadIdx.x == 0) *count = s;
+}
+
+__global__ void k_scalars_init(Scalars sc, double tol, int64_t B) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  sc.tol[b] = tol;
+  sc.active[b] = 1;
+  sc.iters[b] = 0;
+  sc.beta[b] = 0.0;
+  sc.alpha[b] = 0.0;
+  sc.gamma[b] = 0.0;
+}
+
+__global__ void k_welford(const double* __restrict__ qf, const double* __restrict__ qc, int64_t B,
+                          mlmc_level_state* st, double cost) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int64_t n = st->n;
+  double mean = st->mean, m2 = st->m2, cs = st->cost_sum;
+  for (int64_t s = 0; s < B; ++s) {
+    const double y = qc ? qf[s] - qc[s] : qf[s];
+    n += 1;
+    const double d = y - mean;
+    mean += d / (double)n;
+    m2 += d * (y - mean);
+    cs += cost;
+  }
+  st->n = n;
+  st->mean = mean;
+  st->m2 = m2;
+  st->cost_sum = cs;
+}
+
+__device__ void allocate_dev(const double* V, const double* C, int L, double eps, int64_t* N) {
+  double s = 0.0;
+  for (int l = 0; l < L; ++l) s += sqrt(V[l] * C[l]);
+  const double f = 2.0 / (eps * eps);
+  for (int l = 0; l < L; ++l) N[l] = (int64_t)ceil(f * sqrt(V[l] / C[l]) * s);
+}
+
+__global__ void k_estimate(const mlmc_level_state* st, int L, const double* __restrict__ C,
+                           double eps, double* out2, int64_t* N) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double q = 0.0, v = 0.0;
+  double V[16];
+  for (int l = 0; l < L; ++l) {
+    q += st[l].mean;
+    V[l] = st[l].n > 0 ? st[l].m2 / (double)st[l].n : 0.0;
+    if (st[l].n > 0) v += V[l] / (double)st[l].n;
+  }
+  out2[0] = q;
+  out2[1] = v;
+  if (N && eps > 0.0) allocate_dev(V, C, L, eps, N);
+}
+
+__global__ void k_allocate(const double* V, const double* C, int L, double eps, int64_t* N) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  allocate_dev(V, C, L, eps, N);
+}
+
+}  // namespace
+
+cudaError_t launch_finalize(cudaStream_t s, FinMode mode, const double* part, int64_t tiles,
+                            const Scalars& sc, double* out, int iter, int max_iter, int64_t B) {
+  const int warps = 8;
+  k_finalize<<<(unsigned)((B + warps - 1) / warps), warps * 32, 0, s>>>(mode, part, tiles, sc, out,
+                                                                      iter, max_iter, B);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_count_active(cudaStream_t s, const int32_t* active, int64_t B, int32_t* count) {
+  k_count_active<<<1, 256, 0, s>>>(active, B, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scalars_init(cudaStream_t s, const Scalars& sc, double tol, int64_t B) {
+  k_scalars_init<<<(unsigned)((B + 255) / 256), 256, 0, s>>>(sc, tol, B);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_welford(cudaStream_t s, const double* qf, const double* qc, int64_t B,
+                           mlmc_level_state* st, double cost) {
+  k_welford<<<1, 32, 0, s>>>(qf, qc, B, st, cost);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_estimate(cudaStream_t s, const mlmc_level_state* st, int n_levels,
+                            const double* cost, double eps, double* out2, int64_t* N) {
+  k_estimate<<<1, 32, 0, s>>>(st, n_levels, cost, eps, out2, N);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_allocate(cudaStream_t s, const double* V, const double* C, int n_levels,
+                            double eps, int64_t* N) {
+  k_allocate<<<1, 32, 0, s>>>(V, C, n_levels, eps, N);
+  return cudaGetLastError();
+}
+
+}  // namespace mlmc

@@ -1,0 +1,299 @@
+"""ctypes binding of libmlmc (include/mlmc.h): argument marshalling only.
+
+Every numerical step runs in the library's CUDA kernels. There is no CPU
+fallback: if ``libmlmc.so`` is missing or cannot be loaded, importing the
+binding raises. Device buffers are passed as raw pointers (e.g. a torch
+tensor's ``data_ptr()``); streams as raw ``cudaStream_t`` handles.
+"""
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libmlmc.so")
+
+MLMC_OK = 0
+MLMC_ERR_INVALID = -1
+MLMC_ERR_OOM = -2
+MLMC_ERR_NOT_CONVERGED = -3
+MLMC_ERR_CUDA = -4
+MLMC_ERR_TIMEOUT = -5
+MLMC_ERR_UNIMPLEMENTED = -6
+
+QOI_DOMAIN_MEAN = 0
+QOI_BOX_MEAN = 1
+JACOBI_PCG = 0
+GMG_PCG = 1
+FP64 = 0
+MIXED = 1
+
+
+class Config(ctypes.Structure):
+    """Mirror of ``mlmc_config``."""
+    _fields_ = [
+        ("dim", ctypes.c_int32),
+        ("n_levels", ctypes.c_int32),
+        ("coarse_cells", ctypes.c_int32),
+        ("modes_per_dim", ctypes.c_int32),
+        ("sigma2", ctypes.c_double),
+        ("corr_len", ctypes.c_double),
+        ("qoi", ctypes.c_int32),
+        ("solver", ctypes.c_int32),
+        ("box_lo", ctypes.c_double),
+        ("box_hi", ctypes.c_double),
+        ("rtol", ctypes.c_double),
+        ("max_iter", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("seed", ctypes.c_uint64),
+        ("stream_id", ctypes.c_uint32),
+        ("mg_smooth", ctypes.c_int32),
+        ("mg_omega", ctypes.c_double),
+        ("mg_coarsest", ctypes.c_int32),
+        ("check_every", ctypes.c_int32),
+        ("workspace_bytes", ctypes.c_uint64),
+    ]
+
+
+class LevelState(ctypes.Structure):
+    """Mirror of ``mlmc_level_state``."""
+    _fields_ = [("n", ctypes.c_int64), ("mean", ctypes.c_double), ("m2", ctypes.c_double),
+                ("cost_sum", ctypes.c_double)]
+
+
+class KernelStat(ctypes.Structure):
+    """Mirror of ``mlmc_kernel_stat``."""
+    _fields_ = [("launches", ctypes.c_int64), ("ms", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_I64 = ctypes.c_int64
+_D = ctypes.c_double
+_DP = ctypes.POINTER(ctypes.c_double)
+_I32P = ctypes.POINTER(ctypes.c_int32)
+_I64P = ctypes.POINTER(ctypes.c_int64)
+
+# (name, restype, argtypes) for every symbol of include/mlmc.h
+SIGNATURES = [
+    ("mlmc_config_default", None, [ctypes.POINTER(Config)]),
+    ("mlmc_node_stride", _I64, [_I, _I]),
+    ("mlmc_elem_stride", _I64, [_I, _I]),
+    ("mlmc_mesh_cells", _I64, [ctypes.POINTER(Config), _I]),
+    ("mlmc_level_cost", _D, [ctypes.POINTER(Config), _I]),
+    ("mlmc_status_str", ctypes.c_char_p, [_I]),
+    ("mlmc_plan_create", _I, [ctypes.POINTER(Config), _P, ctypes.POINTER(_P)]),
+    ("mlmc_plan_destroy", _I, [_P]),
+    ("mlmc_reset_stats", _I, [_P]),
+    ("mlmc_sample_level", _I, [_P, _I, _I64, _I64, _DP, _DP, _I32P]),
+    ("mlmc_level_stats", _I, [_P, _I, ctypes.POINTER(LevelState)]),
+    ("mlmc_estimate", _I, [_P, _DP, _DP]),
+    ("mlmc_allocate", _I, [_DP, _DP, _I, _D, _I64P]),
+    ("mlmc_run", _I, [_P, _D, _I64, _I64P, _DP, _DP, _I64P]),
+    ("mlmc_draw_xi", _I, [_P, _I, _I64, _I64, _P]),
+    ("mlmc_kappa", _I, [_P, _I, _P, _I64, _P]),
+    ("mlmc_apply", _I, [_P, _I, _P, _P, _P, _I64]),
+    ("mlmc_solve", _I, [_P, _I, _P, _I64, _P, _P, _P]),
+    ("mlmc_kernel_count", _I, []),
+    ("mlmc_kernel_name", ctypes.c_char_p, [_I]),
+    ("mlmc_profile_enable", _I, [_P, _I]),
+    ("mlmc_profile_reset", _I, [_P]),
+    ("mlmc_kernel_stats", _I, [_P, _I, ctypes.POINTER(KernelStat)]),
+    ("mlmc_launch_count", _I64, [_P]),
+]
+
+
+def load(path=LIB_PATH):
+    """Load libmlmc.so and declare every entry point. Raises if it is missing."""
+    if not os.path.exists(path):
+        raise ImportError("libmlmc.so not built (run __graft_entry__.build()): " + path)
+    lib = ctypes.CDLL(path)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = load()
+    return _lib
+
+
+class MLMCError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        msg = lib().mlmc_status_str(status).decode()
+        super().__init__("%s: %s (%d)" % (what, msg, status))
+
+
+def check(status, what, allow=()):
+    if status != MLMC_OK and status not in allow:
+        raise MLMCError(status, what)
+    return status
+
+
+def _dp(arr):
+    return None if arr is None else arr.ctypes.data_as(_DP)
+
+
+def config(dim=2, n_levels=3, coarse_cells=16, modes_per_dim=4, sigma2=1.0, corr_len=0.3,
+           qoi="domain", solver="jacobi", box=(0.25, 0.75), rtol=1e-10, max_iter=None,
+           precision="fp64", seed=0, stream_id=0, mg_omega=None, check_every=0,
+           workspace_bytes=0):
+    """Build a Config from plain values (defaults from mlmc_config_default)."""
+    c = Config()
+    lib().mlmc_config_default(ctypes.byref(c))
+    c.dim, c.n_levels, c.coarse_cells, c.modes_per_dim = dim, n_levels, coarse_cells, modes_per_dim
+    c.sigma2, c.corr_len = sigma2, corr_len
+    c.qoi = {"domain": QOI_DOMAIN_MEAN, "box": QOI_BOX_MEAN}[qoi]
+    c.solver = {"jacobi": JACOBI_PCG, "gmg": GMG_PCG}[solver]
+    c.box_lo, c.box_hi = box
+    c.rtol = rtol
+    if max_iter is not None:
+        c.max_iter = max_iter
+    elif solver == "gmg":
+        c.max_iter = 500
+    c.precision = {"fp64": FP64, "mixed": MIXED}[precision]
+    c.seed, c.stream_id = seed, stream_id
+    if mg_omega is not None:
+        c.mg_omega = mg_omega
+    c.check_every = check_every
+    c.workspace_bytes = workspace_bytes
+    return c
+
+
+def config_from_workload(wl, **over):
+    """Config from a workload dictionary (see synth.workloads)."""
+    args = dict(dim=wl["dim"], n_levels=wl["levels"], coarse_cells=wl["n0"],
+                modes_per_dim=wl["m"], sigma2=wl["sigma2"], corr_len=wl["corr_len"],
+                qoi=wl.get("qoi", "domain"), solver=wl.get("solver", "jacobi"),
+                box=tuple(wl.get("box", (0.25, 0.75))), rtol=wl["rtol"],
+                seed=wl.get("seed", 0), stream_id=wl.get("stream_id", 0),
+                precision=wl.get("precision", "fp64"))
+    args.update(over)
+    return config(**args)
+
+
+def node_stride(dim, n):
+    return lib().mlmc_node_stride(dim, n)
+
+
+def elem_stride(dim, n):
+    return lib().mlmc_elem_stride(dim, n)
+
+
+class Plan:
+    """An mlmc_plan: KLE tables, level states and workspace on one device."""
+
+    def __init__(self, cfg, stream=0):
+        self.cfg = cfg
+        self._h = _P()
+        check(lib().mlmc_plan_create(ctypes.byref(cfg), _P(stream), ctypes.byref(self._h)),
+              "mlmc_plan_create")
+
+    def close(self):
+        if self._h:
+            check(lib().mlmc_plan_destroy(self._h), "mlmc_plan_destroy")
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # --- plan-level API (host outputs) ---
+    def mesh_cells(self, mesh):
+        return lib().mlmc_mesh_cells(ctypes.byref(self.cfg), mesh)
+
+    def sample_level(self, level, first, count, want=True, allow_not_converged=False):
+        import numpy as np
+        qf = np.zeros(count) if want else None
+        qc = np.zeros(count) if want else None
+        it = np.zeros(count, dtype=np.int32) if want else None
+        st = lib().mlmc_sample_level(self._h, level, first, count, _dp(qf), _dp(qc),
+                                     None if it is None else it.ctypes.data_as(_I32P))
+        check(st, "mlmc_sample_level",
+              allow=(MLMC_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+        return qf, qc, it
+
+    def level_stats(self, level):
+        s = LevelState()
+        check(lib().mlmc_level_stats(self._h, level, ctypes.byref(s)), "mlmc_level_stats")
+        return s.n, s.mean, s.m2, s.cost_sum
+
+    def estimate(self):
+        q, v = ctypes.c_double(), ctypes.c_double()
+        check(lib().mlmc_estimate(self._h, ctypes.byref(q), ctypes.byref(v)), "mlmc_estimate")
+        return q.value, v.value
+
+    def reset_stats(self):
+        check(lib().mlmc_reset_stats(self._h), "mlmc_reset_stats")
+
+    def run(self, eps=None, pilot=0, N=None):
+        import numpy as np
+        L1 = self.cfg.n_levels
+        q, v = ctypes.c_double(), ctypes.c_double()
+        Nout = np.zeros(L1, dtype=np.int64)
+        Nfix = None if N is None else np.ascontiguousarray(N, dtype=np.int64)
+        st = lib().mlmc_run(self._h, eps or 0.0, pilot,
+                            None if Nfix is None else Nfix.ctypes.data_as(_I64P),
+                            ctypes.byref(q), ctypes.byref(v), Nout.ctypes.data_as(_I64P))
+        check(st, "mlmc_run")
+        return q.value, v.value, Nout
+
+    # --- device-level API (raw device pointers) ---
+    def draw_xi(self, level, first, count, xi_ptr):
+        check(lib().mlmc_draw_xi(self._h, level, first, count, _P(xi_ptr)), "mlmc_draw_xi")
+
+    def kappa(self, mesh, xi_ptr, count, kappa_ptr):
+        check(lib().mlmc_kappa(self._h, mesh, _P(xi_ptr), count, _P(kappa_ptr)), "mlmc_kappa")
+
+    def apply(self, mesh, kappa_ptr, x_ptr, y_ptr, count):
+        check(lib().mlmc_apply(self._h, mesh, _P(kappa_ptr), _P(x_ptr), _P(y_ptr), count),
+              "mlmc_apply")
+
+    def solve(self, mesh, kappa_ptr, count, u_ptr, q_ptr, iters_ptr, allow_not_converged=False):
+        st = lib().mlmc_solve(self._h, mesh, _P(kappa_ptr), count, _P(u_ptr or None),
+                              _P(q_ptr), _P(iters_ptr or None))
+        return check(st, "mlmc_solve",
+                     allow=(MLMC_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+
+    # --- tracing ---
+    def profile(self, on=True):
+        check(lib().mlmc_profile_enable(self._h, 1 if on else 0), "mlmc_profile_enable")
+
+    def profile_reset(self):
+        check(lib().mlmc_profile_reset(self._h), "mlmc_profile_reset")
+
+    def kernel_stats(self):
+        out = {}
+        for k in range(lib().mlmc_kernel_count()):
+            s = KernelStat()
+            check(lib().mlmc_kernel_stats(self._h, k, ctypes.byref(s)), "mlmc_kernel_stats")
+            out[lib().mlmc_kernel_name(k).decode()] = (s.launches, s.ms, s.bytes)
+        return out
+
+    def launch_count(self):
+        return lib().mlmc_launch_count(self._h)
+
+
+def allocate(V, C, eps):
+    """Eq. (mlmc_num_samples) evaluated by the library (on the device)."""
+    import numpy as np
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    C = np.ascontiguousarray(C, dtype=np.float64)
+    N = np.zeros(V.size, dtype=np.int64)
+    check(lib().mlmc_allocate(_dp(V), _dp(C), V.size, eps, N.ctypes.data_as(_I64P)),
+          "mlmc_allocate")
+    return N
