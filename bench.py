@@ -1,0 +1,326 @@
+"""Benchmark: MLMC to RMSE eps on the 2D-at-scale workload, one JSON line.
+
+Workload (default): 2D -div(kappa grad u) = 1 on the unit square, Q1 on
+32^2..1024^2 elements (6 levels), lognormal KLE field sigma^2 = 1,
+correlation length 0.1, M = 64 tensor modes, GMG-preconditioned CG rtol
+1e-10, domain-mean QoI, adaptive sample counts for RMSE eps = 1e-3 from 100
+pilot samples per level. One step = one whole MLMC run to eps (pilot,
+allocation rounds, estimate) through mlmc_run.
+
+Metric: coupled DOF-solves/s = sum over completed coupled samples of the
+interior DOFs of both meshes, per second (higher is better); the step time
+is the time to RMSE eps.
+
+--impl reference times the CPU FP64 oracle (the only reference this method
+has) on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synth import workload  # noqa: E402
+
+WORKLOAD = "2d-scale"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def interior_dofs(dim, n):
+    return (n - 1) ** dim
+
+
+def coupled_dofs(wl, level):
+    n = wl["n0"] << level
+    d = interior_dofs(wl["dim"], n)
+    if level > 0:
+        d += interior_dofs(wl["dim"], n // 2)
+    return d
+
+
+def workload_desc(wl):
+    nf = wl["n0"] << (wl["levels"] - 1)
+    return ("%dD Q1 %d^%d..%d^%d elements (%d levels), sigma2=%g, corr_len=%g, M=%d, %s-PCG "
+            "rtol %g, %s QoI, eps=%g, pilot %d" % (
+                wl["dim"], wl["n0"], wl["dim"], nf, wl["dim"], wl["levels"], wl["sigma2"],
+                wl["corr_len"], wl["m"] ** wl["dim"], wl["solver"].upper(), wl["rtol"],
+                wl["qoi"], wl["eps"], wl["pilot"]))
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ CPU oracle
+
+def oracle_sample_code(name, levels):
+    return (
+        "import sys, time, json; sys.path.insert(0, %r)\n"
+        "from synth import workload\n"
+        "from oracle import mlmc\n"
+        "wl = workload(%r)\n"
+        "t = time.perf_counter(); dofs = 0\n"
+        "for l in %r:\n"
+        "    mlmc.coupled_sample(wl, l, 0)\n"
+        "    n = wl['n0'] << l; d = (n - 1) ** wl['dim']\n"
+        "    dofs += d + ((n // 2 - 1) ** wl['dim'] if l > 0 else 0)\n"
+        "dt = time.perf_counter() - t\n"
+        "print(json.dumps({'dofs': dofs, 'seconds': dt}))\n" % (ROOT, name, list(levels)))
+
+
+def run_oracle_sample(name, levels):
+    """One coupled sample per listed level with the oracle, single-threaded BLAS."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    res = subprocess.run([sys.executable, "-c", oracle_sample_code(name, levels)], env=env,
+                         capture_output=True, text=True, timeout=1800)
+    if res.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + res.stderr[-2000:])
+    out = json.loads(res.stdout.strip().splitlines()[-1])
+    return out["dofs"], out["seconds"]
+
+
+def cpu_baseline(name, levels):
+    dofs, sec = run_oracle_sample(name, levels)
+    return {"value": dofs / sec, "unit": "coupled DOF-solves/s", "cores": 1, "kind": "oracle",
+            "sample": "one coupled sample (sample 0) on each of levels %s of the %s workload: "
+                      "dense KLE, assembled Q1 matrix, sparse LU solve with refinement; "
+                      "%d coupled DOFs in %.1f s" % (list(levels), name, dofs, sec)}
+
+
+def bench_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = workload(args.workload)
+    levels = list(range(min(wl["levels"], 5)))
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        run_oracle_sample(args.workload, levels[:2])
+    t_dofs, t_sec = 0, 0.0
+    for _ in range(args.steps):
+        d, s = run_oracle_sample(args.workload, levels)
+        t_dofs += d
+        t_sec += s
+    value = t_dofs / t_sec
+    line = {"impl": "reference", "metric": "coupled DOF-solves/s", "value": value,
+            "unit": "coupled DOF-solves/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_sec / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload + ": " + workload_desc(wl),
+                       "sample": "levels %s, sample 0 each" % levels},
+            "cpu_baseline": {"value": value, "unit": "coupled DOF-solves/s", "cores": 1,
+                             "kind": "oracle",
+                             "sample": "one coupled sample per level %s per step" % levels},
+            "e2e": {"value": value, "unit": "coupled DOF-solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------- GPU
+
+def bench_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+
+    from paper_2111_11788_gb300.build import build_library
+    build_library()
+    import paper_2111_11788_gb300.mlmc as m
+
+    wl = workload(args.workload)
+    # replicas: each rank runs an independent MLMC estimate on its own Philox stream
+    cfg = m.config_from_workload(wl, stream_id=rank)
+    stream = torch.cuda.Stream()
+    sh = stream.cuda_stream
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    with torch.cuda.stream(stream):
+        plan = m.Plan(cfg, sh)
+        # warm-up steps (also fix the sample counts of a step)
+        N = None
+        for _ in range(max(args.warmup, 1)):
+            q, v, N = plan.run(eps=wl["eps"], pilot=wl["pilot"])
+        dofs_step = sum(int(N[l]) * coupled_dofs(wl, l) for l in range(wl["levels"]))
+        # pick the dominant kernel from a traced step
+        plan.profile(-1)
+        plan.profile_reset()
+        plan.run(eps=wl["eps"], pilot=wl["pilot"])
+        stats = plan.kernel_stats()
+        plan.profile(0)
+        total_ms = sum(s[1] for s in stats.values())
+        dom = max(stats, key=lambda k: stats[k][1])
+        shares = {k: round(s[1] / total_ms, 4) for k, s in stats.items() if s[1] > 0}
+
+        # timed region: device events, dominant kernel traced live
+        plan.profile_reset()
+        plan.profile(1 << m.Plan.kernel_id(dom))
+        clocks = ClockSampler(local)
+        barrier()
+        torch.cuda.synchronize()
+        clocks.start()
+        l0 = plan.launch_count()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            q, v, N = plan.run(eps=wl["eps"], pilot=wl["pilot"])
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        clk = clocks.stop()
+        launches = plan.launch_count() - l0
+        ms = ev0.elapsed_time(ev1)
+        dstat = plan.kernel_stats()[dom]
+        plan.profile(0)
+
+        # end to end through the public API: plan creation (host KLE roots,
+        # table upload), the run, results back to host, plan destruction
+        wall = []
+        h2d = 8 * 2 * wl["m"] + 4 * wl["m"] + 8 * wl["levels"]
+        d2h = 8 * 2 + 8 * wl["levels"]
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            p2 = m.Plan(cfg, sh)
+            q2, v2, N2 = p2.run(eps=wl["eps"], pilot=wl["pilot"])
+            p2.close()
+            torch.cuda.synchronize()
+            wall.append(time.perf_counter() - t0)
+        plan.close()
+
+    ms_t = torch.tensor([ms], device="cuda")
+    e2e_t = torch.tensor([sum(wall)], device="cuda")
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    ms = float(ms_t.item())
+    e2e_s = float(e2e_t.item())
+    value = world * dofs_step * args.steps / (ms / 1e3)
+    e2e_value = world * dofs_step * args.steps / e2e_s
+
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = json.load(open(pk_path))
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    d_launches, d_ms, d_bytes = dstat
+    achieved = (d_bytes / (d_ms / 1e3)) / 1e9 if d_ms > 0 else 0.0
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
+                "peak": hbm_peak, "peak_source": peak_src, "unit": "GB/s",
+                "frac": round(achieved / hbm_peak, 4), "traffic": None,
+                "launches": d_launches, "avg_launch_us": round(1e3 * d_ms / max(d_launches, 1), 2),
+                "time_shares": shares}
+
+    if rank == 0:
+        line = {"metric": "coupled DOF-solves/s", "value": value, "unit": "coupled DOF-solves/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms / args.steps, "time_to_eps_s": ms / args.steps / 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic",
+                "config": {"workload": args.workload + ": " + workload_desc(wl),
+                           "form": "plain FP64",
+                           "samples_per_level": [int(x) for x in N],
+                           "q_hat": q, "stat_var": v,
+                           "l2": "working set of the 512^2/1024^2 levels (GBs) exceeds the 129 MB L2",
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "roofline": roofline, "clocks": clk, "gpu_launches": int(launches),
+                "e2e": {"value": e2e_value, "unit": "coupled DOF-solves/s",
+                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}}
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args.workload, list(range(min(wl["levels"], 5))))
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_ours(args)
+
+
+if __name__ == "__main__":
+    main()

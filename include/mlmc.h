@@ -179,9 +179,11 @@ typedef struct mlmc_kernel_stat {
 
 int mlmc_kernel_count(void);
 const char* mlmc_kernel_name(int kernel_id);
-/* When on, every launch of a kernel is bracketed by CUDA events on the
- * plan's stream; stats accumulate until mlmc_profile_reset. */
-mlmc_status mlmc_profile_enable(mlmc_plan plan, int on);
+/* `mask` selects kernels by bit (1 << kernel_id; -1 = all, 0 = off). Every
+ * launch of a selected kernel is bracketed by CUDA events on the plan's
+ * stream and its algorithmic bytes are accumulated on the device; stats
+ * accumulate until mlmc_profile_reset. */
+mlmc_status mlmc_profile_enable(mlmc_plan plan, int mask);
 mlmc_status mlmc_profile_reset(mlmc_plan plan);
 mlmc_status mlmc_kernel_stats(mlmc_plan plan, int kernel_id, mlmc_kernel_stat* out);
 /* Number of kernel launches issued by this plan since creation. */

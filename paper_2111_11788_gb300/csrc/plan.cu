@@ -157,6 +157,7 @@ struct mlmc_plan_s {
   size_t h_pin_bytes = 0;
   // tracing
   bool prof_on = false;
+  uint32_t prof_mask = 0;
   double* d_prof = nullptr;       // NUM_KERNELS byte accumulators
   std::vector<PendingEvent> pending;
   std::vector<cudaEvent_t> pool;
@@ -277,7 +278,7 @@ cudaEvent_t get_event(mlmc_plan p) {
 
 Prof prof_for(mlmc_plan p, int kid, double per_sample) {
   Prof pr;
-  pr.acc = p->prof_on ? p->d_prof + kid : nullptr;
+  pr.acc = (p->prof_on && (p->prof_mask >> kid & 1u)) ? p->d_prof + kid : nullptr;
   pr.per_sample = per_sample;
   return pr;
 }
@@ -286,7 +287,7 @@ Prof prof_for(mlmc_plan p, int kid, double per_sample) {
 template <class F>
 cudaError_t run(mlmc_plan p, int kid, F&& f) {
   p->launches += 1;
-  if (!p->prof_on) return f();
+  if (!p->prof_on || !(p->prof_mask >> kid & 1u)) return f();
   PendingEvent pe;
   pe.kid = kid;
   pe.a = get_event(p);
@@ -867,10 +868,11 @@ mlmc_status mlmc_run(mlmc_plan p, double eps, int64_t pilot, const int64_t* N_fi
   return bad ? MLMC_ERR_NOT_CONVERGED : MLMC_OK;
 }
 
-mlmc_status mlmc_profile_enable(mlmc_plan p, int on) {
+mlmc_status mlmc_profile_enable(mlmc_plan p, int mask) {
   if (!p) return MLMC_ERR_INVALID;
   harvest(p);
-  p->prof_on = on != 0;
+  p->prof_mask = (uint32_t)mask;
+  p->prof_on = mask != 0;
   return MLMC_OK;
 }
 

@@ -270,8 +270,9 @@ class Plan:
                      allow=(MLMC_ERR_NOT_CONVERGED,) if allow_not_converged else ())
 
     # --- tracing ---
-    def profile(self, on=True):
-        check(lib().mlmc_profile_enable(self._h, 1 if on else 0), "mlmc_profile_enable")
+    def profile(self, mask=-1):
+        """Trace kernels selected by bit mask (1 << kernel id; -1 all, 0 off)."""
+        check(lib().mlmc_profile_enable(self._h, int(mask)), "mlmc_profile_enable")
 
     def profile_reset(self):
         check(lib().mlmc_profile_reset(self._h), "mlmc_profile_reset")
@@ -283,6 +284,13 @@ class Plan:
             check(lib().mlmc_kernel_stats(self._h, k, ctypes.byref(s)), "mlmc_kernel_stats")
             out[lib().mlmc_kernel_name(k).decode()] = (s.launches, s.ms, s.bytes)
         return out
+
+    @staticmethod
+    def kernel_id(name):
+        for k in range(lib().mlmc_kernel_count()):
+            if lib().mlmc_kernel_name(k).decode() == name:
+                return k
+        raise KeyError(name)
 
     def launch_count(self):
         return lib().mlmc_launch_count(self._h)

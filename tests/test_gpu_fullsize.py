@@ -1,0 +1,44 @@
+"""Full-size parity on the 2D-at-scale workload (32^2..1024^2, M = 64, GMG-PCG
+rtol 1e-10), in the launch configuration the benchmark times: the whole
+100-sample pilot batch of a level in one call, with sampled outputs checked
+one by one against the oracle (sparse LU with refinement) and properties
+that hold for every sample."""
+import numpy as np
+import pytest
+
+from oracle import mlmc as omlmc
+from synth import workload
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def m():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2111_11788_gb300.build import build_library
+    build_library()
+    import paper_2111_11788_gb300.mlmc as mod
+    mod.lib()
+    return mod
+
+
+@pytest.mark.parametrize("level,checked", [(5, (0, 57)), (3, (0, 99))])
+def test_pilot_batch_full_size(m, level, checked):
+    wl = workload("2d-scale")
+    cfg = m.config_from_workload(wl)
+    with m.Plan(cfg, torch.cuda.current_stream().cuda_stream) as plan:
+        qf, qc, it = plan.sample_level(level, 0, 100)
+        n, mean, m2, _ = plan.level_stats(level)
+    assert n == 100
+    assert np.all(it > 0) and np.all(it < 100)
+    assert np.all(qf > 0) and np.all(qc > 0)
+    y = qf - qc
+    # the coupled difference is a discretisation error: far below the QoI itself
+    assert np.max(np.abs(y)) < 0.05 * np.min(qf)
+    assert abs(mean - y.mean()) <= 1e-12 * abs(y.mean()) + 1e-18
+    for i in checked:
+        rf, rc = omlmc.coupled_sample(wl, level, i)
+        assert abs(qf[i] - rf) <= 1e-9 * abs(rf)
+        assert abs(qc[i] - rc) <= 1e-9 * abs(rc)
