@@ -40,6 +40,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-level", type=int, default=None,
+                    help="profiling case: only run this level's coupled batch twice, then exit")
+    ap.add_argument("--profile-batch", type=int, default=64)
     return ap.parse_args()
 
 
@@ -314,9 +317,27 @@ def bench_ours(args):
         dist.destroy_process_group()
 
 
+def profile_case(args):
+    """Small case for ncu: one level's coupled batch, twice, no timing."""
+    import torch
+    from paper_2111_11788_gb300.build import build_library
+    build_library()
+    import paper_2111_11788_gb300.mlmc as m
+    wl = workload(args.workload)
+    cfg = m.config_from_workload(wl)
+    with m.Plan(cfg, torch.cuda.current_stream().cuda_stream) as plan:
+        for rep in range(2):
+            plan.sample_level(args.profile_level, rep * args.profile_batch, args.profile_batch,
+                              want=False)
+    torch.cuda.synchronize()
+    print("profile case done: level %d, batch %d" % (args.profile_level, args.profile_batch))
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.profile_level is not None:
+        profile_case(args)
+    elif args.impl == "reference":
         bench_reference(args)
     else:
         bench_ours(args)
