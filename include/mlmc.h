@@ -169,6 +169,38 @@ mlmc_status mlmc_apply(mlmc_plan plan, int mesh, const double* kappa, const doub
 mlmc_status mlmc_solve(mlmc_plan plan, int mesh, const double* kappa, int64_t count,
                        double* u, double* q, int32_t* iters);
 
+/* ---- solve without device allocation -------------------------------- */
+
+/* Bytes of the static device scratch used by mlmc_solve_noalloc. */
+#define MLMC_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
+
+/* The batched PCG solve of mlmc_solve (same kernels, same results) for
+ * callers that must not allocate device memory: code living inside another
+ * framework's memory arena, latency-critical loops that cannot afford the
+ * device synchronisation of cudaMalloc/cudaFree, and hosts that forbid
+ * device allocation. The paper has no counterpart; it is a deployment
+ * convenience of this library.
+ *  - No plan is needed and nothing is allocated: the scratch is a static
+ *    device array of MLMC_NOALLOC_SCRATCH_BYTES inside the library, held by
+ *    every GPU that loads it until the process exits.
+ *  - cfg: dim 2, FP64, Jacobi- or GMG-PCG (as for mlmc_plan_create); mesh
+ *    m has n = coarse_cells * 2^m cells per side.
+ *  - kappa: device element arrays (count x mlmc_elem_stride(2, n));
+ *    q: device, count doubles (QoI per sample); iters: device, count int32
+ *    (may be NULL; -1 = not converged). stream: borrowed cudaStream_t.
+ *  - Returns MLMC_ERR_INVALID when count samples of this mesh need more
+ *    scratch than MLMC_NOALLOC_SCRATCH_BYTES (e.g. about 40 GMG samples of
+ *    128^2 cells, 10 of 256^2), or count > 65535; NOT_CONVERGED if a sample
+ *    hit max_iter. Blocks until the results are on the device.
+ *  - The first call on a device looks up the array's device address on
+ *    that device (make it before any stream capture).
+ *  - Every call shares the one array, and the array keeps the last call's
+ *    contents (each call writes every scratch entry it reads before reading
+ *    it). Calls that overlap on the GPU (other streams, other host threads)
+ *    race on it: the caller must serialise them. */
+mlmc_status mlmc_solve_noalloc(const mlmc_config* cfg, int mesh, const double* kappa,
+                               int64_t count, double* q, int32_t* iters, void* stream);
+
 /* ---- tracing: per-kernel CUDA-event timing -------------------------- */
 
 typedef struct mlmc_kernel_stat {

@@ -98,6 +98,7 @@ SIGNATURES = [
     ("mlmc_profile_reset", _I, [_P]),
     ("mlmc_kernel_stats", _I, [_P, _I, ctypes.POINTER(KernelStat)]),
     ("mlmc_launch_count", _I64, [_P]),
+    ("mlmc_solve_noalloc", _I, [ctypes.POINTER(Config), _I, _P, _I64, _P, _P, _P]),
 ]
 
 
