@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--profile-level", type=int, default=None,
                     help="profiling case: only run this level's coupled batch twice, then exit")
     ap.add_argument("--profile-batch", type=int, default=64)
+    ap.add_argument("--form", default="fp64", choices=["fp64", "mixed"],
+                    help="form of the headline line (the other form is measured alongside)")
+    ap.add_argument("--single-form", action="store_true")
     return ap.parse_args()
 
 
@@ -191,53 +194,29 @@ def bench_reference(args):
 
 # ------------------------------------------------------------------- GPU
 
-def bench_ours(args):
-    import numpy as np
+def measure_form(m, wl, cfg, stream, args, world, barrier, with_e2e):
+    """Warm up, trace one run, then time args.steps MLMC runs of one form."""
     import torch
-    import torch.distributed as dist
-
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-
-    from paper_2111_11788_gb300.build import build_library
-    build_library()
-    import paper_2111_11788_gb300.mlmc as m
-
-    wl = workload(args.workload)
-    # replicas: each rank runs an independent MLMC estimate on its own Philox stream
-    cfg = m.config_from_workload(wl, stream_id=rank)
-    stream = torch.cuda.Stream()
     sh = stream.cuda_stream
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
     with torch.cuda.stream(stream):
         plan = m.Plan(cfg, sh)
-        # warm-up steps (also fix the sample counts of a step)
         N = None
         for _ in range(max(args.warmup, 1)):
             q, v, N = plan.run(eps=wl["eps"], pilot=wl["pilot"])
         dofs_step = sum(int(N[l]) * coupled_dofs(wl, l) for l in range(wl["levels"]))
-        # pick the dominant kernel from a traced step
+        # pick the dominant kernel from a traced run
         plan.profile(-1)
         plan.profile_reset()
         plan.run(eps=wl["eps"], pilot=wl["pilot"])
         stats = plan.kernel_stats()
         plan.profile(0)
-        total_ms = sum(s[1] for s in stats.values())
+        total_ms = sum(st[1] for st in stats.values())
         dom = max(stats, key=lambda k: stats[k][1])
-        shares = {k: round(s[1] / total_ms, 4) for k, s in stats.items() if s[1] > 0}
-
-        # timed region: device events, dominant kernel traced live
+        shares = {k: round(st[1] / total_ms, 4) for k, st in stats.items() if st[1] > 0}
+        # timed region: device events; only the dominant kernel is traced live
         plan.profile_reset()
         plan.profile(1 << m.Plan.kernel_id(dom))
-        clocks = ClockSampler(local)
+        clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
         barrier()
         torch.cuda.synchronize()
         clocks.start()
@@ -255,61 +234,116 @@ def bench_ours(args):
         ms = ev0.elapsed_time(ev1)
         dstat = plan.kernel_stats()[dom]
         plan.profile(0)
-
-        # end to end through the public API: plan creation (host KLE roots,
-        # table upload), the run, results back to host, plan destruction
         wall = []
-        h2d = 8 * 2 * wl["m"] + 4 * wl["m"] + 8 * wl["levels"]
-        d2h = 8 * 2 + 8 * wl["levels"]
-        for _ in range(args.steps):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            p2 = m.Plan(cfg, sh)
-            q2, v2, N2 = p2.run(eps=wl["eps"], pilot=wl["pilot"])
-            p2.close()
-            torch.cuda.synchronize()
-            wall.append(time.perf_counter() - t0)
+        if with_e2e:
+            # end to end through the public API: plan creation (host KLE roots,
+            # table upload), the run, results back to host, plan destruction
+            for _ in range(args.steps):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                p2 = m.Plan(cfg, sh)
+                p2.run(eps=wl["eps"], pilot=wl["pilot"])
+                p2.close()
+                torch.cuda.synchronize()
+                wall.append(time.perf_counter() - t0)
         plan.close()
+    return dict(ms=ms, N=[int(x) for x in N], dofs_step=dofs_step, q=q, v=v, dom=dom,
+                dstat=dstat, shares=shares, clocks=clk, launches=launches, wall=wall)
 
-    ms_t = torch.tensor([ms], device="cuda")
-    e2e_t = torch.tensor([sum(wall)], device="cuda")
+
+def roofline_of(res, peaks, fp64_alu):
+    d_launches, d_ms, d_bytes = res["dstat"]
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    src = "measured" if "hbm_gbs" in peaks else "fallback"
+    achieved = (d_bytes / (d_ms / 1e3)) / 1e9 if d_ms > 0 else 0.0
+    r = {"bound": "alu" if fp64_alu else "hbm", "kernel": res["dom"],
+         "achieved": round(achieved, 1), "peak": hbm_peak, "peak_source": src, "unit": "GB/s",
+         "frac": round(achieved / hbm_peak, 4), "traffic": None, "launches": d_launches,
+         "avg_launch_us": round(1e3 * d_ms / max(d_launches, 1), 2),
+         "time_shares": res["shares"]}
+    if fp64_alu:
+        r["note"] = ("FP64 form: the kernel is bound by the FP64 pipe (2 DFMA/SM/cycle on GB300, "
+                     "1.26 TFLOP/s at 2.07 GHz); achieved/peak/frac here are its HBM bytes "
+                     "against the measured copy bandwidth")
+    return r
+
+
+def bench_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    ms = float(ms_t.item())
-    e2e_s = float(e2e_t.item())
-    value = world * dofs_step * args.steps / (ms / 1e3)
-    e2e_value = world * dofs_step * args.steps / e2e_s
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+
+    from paper_2111_11788_gb300.build import build_library
+    build_library()
+    import paper_2111_11788_gb300.mlmc as m
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    wl = workload(args.workload)
+    stream = torch.cuda.Stream()
+    # replicas: each rank runs an independent MLMC estimate on its own Philox stream
+    forms = {}
+    for form in (args.form, "mixed" if args.form == "fp64" else "fp64"):
+        if form != args.form and args.single_form:
+            continue
+        cfg = m.config_from_workload(wl, stream_id=rank, precision=form)
+        forms[form] = measure_form(m, wl, cfg, stream, args, world, barrier,
+                                   with_e2e=(form == args.form))
+
+    def reduce_max(x):
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
 
     peaks = {}
     pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pk_path):
         peaks = json.load(open(pk_path))
-    hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    d_launches, d_ms, d_bytes = dstat
-    achieved = (d_bytes / (d_ms / 1e3)) / 1e9 if d_ms > 0 else 0.0
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
-                "peak": hbm_peak, "peak_source": peak_src, "unit": "GB/s",
-                "frac": round(achieved / hbm_peak, 4), "traffic": None,
-                "launches": d_launches, "avg_launch_us": round(1e3 * d_ms / max(d_launches, 1), 2),
-                "time_shares": shares}
-
+    main = forms[args.form]
+    ms = reduce_max(main["ms"])
+    e2e_s = reduce_max(sum(main["wall"]))
+    value = world * main["dofs_step"] * args.steps / (ms / 1e3)
+    e2e_value = world * main["dofs_step"] * args.steps / e2e_s
+    h2d = 8 * 2 * wl["m"] + 4 * wl["m"] + 8 * wl["levels"]
+    d2h = 8 * 2 + 8 * wl["levels"]
+    other = {}
+    for form, res in forms.items():
+        if form == args.form:
+            continue
+        oms = reduce_max(res["ms"])
+        other[form] = {"value": world * res["dofs_step"] * args.steps / (oms / 1e3),
+                       "unit": "coupled DOF-solves/s", "ms_per_step": oms / args.steps,
+                       "time_to_eps_s": oms / args.steps / 1e3,
+                       "samples_per_level": res["N"], "q_hat": res["q"], "stat_var": res["v"],
+                       "gpu_launches": int(res["launches"]), "clocks": res["clocks"],
+                       "roofline": roofline_of(res, peaks, fp64_alu=(form == "fp64"))}
     if rank == 0:
+        names = {"fp64": "plain FP64", "mixed": "mixed: FP32 inner PCG + FP64 refinement"}
         line = {"metric": "coupled DOF-solves/s", "value": value, "unit": "coupled DOF-solves/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": ms / args.steps, "time_to_eps_s": ms / args.steps / 1e3,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64", "data": "synthetic",
+                "dtype": "f64" if args.form == "fp64" else "f32+f64", "data": "synthetic",
                 "config": {"workload": args.workload + ": " + workload_desc(wl),
-                           "form": "plain FP64",
-                           "samples_per_level": [int(x) for x in N],
-                           "q_hat": q, "stat_var": v,
+                           "form": names[args.form],
+                           "samples_per_level": main["N"],
+                           "q_hat": main["q"], "stat_var": main["v"],
                            "l2": "working set of the 512^2/1024^2 levels (GBs) exceeds the 129 MB L2",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
-                "roofline": roofline, "clocks": clk, "gpu_launches": int(launches),
+                "roofline": roofline_of(main, peaks, fp64_alu=(args.form == "fp64")),
+                "clocks": main["clocks"], "gpu_launches": int(main["launches"]),
                 "e2e": {"value": e2e_value, "unit": "coupled DOF-solves/s",
-                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}}
+                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "other_forms": {names[k]: v for k, v in other.items()}}
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.workload, list(range(min(wl["levels"], 5))))
         print(json.dumps(line), flush=True)
@@ -324,7 +358,7 @@ def profile_case(args):
     build_library()
     import paper_2111_11788_gb300.mlmc as m
     wl = workload(args.workload)
-    cfg = m.config_from_workload(wl)
+    cfg = m.config_from_workload(wl, precision=args.form)
     with m.Plan(cfg, torch.cuda.current_stream().cuda_stream) as plan:
         for rep in range(2):
             plan.sample_level(args.profile_level, rep * args.profile_batch, args.profile_batch,

@@ -66,7 +66,7 @@ typedef struct mlmc_config {
   double box_lo, box_hi;   /* QoI box [lo, hi]^dim, node-aligned on every mesh */
   double rtol;             /* stop when ||r||_2 <= rtol ||b||_2 */
   int32_t max_iter;        /* CG iteration cap (> 0) */
-  int32_t precision;       /* MLMC_FP64 (MLMC_MIXED reserved) */
+  int32_t precision;       /* MLMC_FP64 | MLMC_MIXED (FP32 inner PCG + FP64 refinement) */
   uint64_t seed;           /* Philox key */
   uint32_t stream_id;      /* fourth Philox counter word (request id) */
   int32_t mg_smooth;       /* damped-Jacobi sweeps before and after each coarse correction */
@@ -74,6 +74,9 @@ typedef struct mlmc_config {
   int32_t mg_coarsest;     /* cells per side of the coarsest multigrid grid (>= 2) */
   int32_t check_every;     /* CG iterations between convergence polls (0 = auto) */
   uint64_t workspace_bytes;/* device workspace budget for batching (0 = auto) */
+  double inner_rtol;       /* MLMC_MIXED: relative tolerance of each FP32 inner solve */
+  int32_t inner_max_iter;  /* MLMC_MIXED: iteration cap of each inner solve */
+  int32_t outer_max_iter;  /* MLMC_MIXED: cap on FP64 refinement steps */
 } mlmc_config;
 
 /* Per-level Welford state (Eq. (sample_variance): V = m2 / n). */
@@ -89,7 +92,14 @@ typedef struct mlmc_plan_s* mlmc_plan;
 /* ---- configuration and layout -------------------------------------- */
 
 /* Defaults: 2D, 3 levels, n_0 = 16, m = 4, sigma2 = 1, corr_len = 0.3,
- * domain-mean QoI, Jacobi-PCG, rtol 1e-10, FP64, seed 0. */
+ * domain-mean QoI, Jacobi-PCG, rtol 1e-10, FP64, seed 0; mixed form:
+ * inner_rtol 1e-5, inner_max_iter 60, outer_max_iter 12.
+ *
+ * MLMC_MIXED (iterative refinement, the precision pattern the method admits
+ * on GB300): u = 0, r = b; repeat { d = A32^-1 (r / s) by FP32 PCG with
+ * kappa32 = (float) kappa to inner_rtol; u += s d; r = b - A(kappa) u in
+ * FP64; s = ||r|| } until ||r||_2 <= rtol ||b||_2 (the FP64 true residual).
+ * iters then counts all inner iterations; -1 if outer_max_iter was hit. */
 void mlmc_config_default(mlmc_config* cfg);
 
 /* Doubles between consecutive samples in node / element arrays. */

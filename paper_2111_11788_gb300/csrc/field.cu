@@ -8,6 +8,8 @@
 // evaluated axis by axis (sum factorisation) in FP64: for each sample a
 // small x-contraction into shared memory, then m FMAs per element and one
 // exp. The kernel is bound by the write of kappa (8 B per element).
+#include <algorithm>
+
 #include "mlmc_internal.cuh"
 
 namespace mlmc {
@@ -127,8 +129,6 @@ __global__ void __launch_bounds__(TX2* K3_TY)
     t2[kz] = acc;
   }
   double* out = kappa + (int64_t)b * es;
-  const int z0 = blockIdx.y * 0 + 0;
-  (void)z0;
   for (int iz = 0; iz < n; ++iz) {
     const double* fz = table + iz * m;
     double g = 0.0;
@@ -139,19 +139,21 @@ __global__ void __launch_bounds__(TX2* K3_TY)
   if (prof.acc && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) atomicAdd(prof.acc, prof.per_sample);
 }
 
-__global__ void k_coarsen2d(int nc, const double* __restrict__ kf, double* __restrict__ kc,
+template <class T>
+__global__ void k_coarsen2d(int nc, const T* __restrict__ kf, T* __restrict__ kc,
                             int64_t esf, int64_t esc, Prof prof) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y;
   const int b = blockIdx.z;
   if (I >= nc) return;
   const int nf = 2 * nc;
-  const double* f = kf + (int64_t)b * esf + (int64_t)(2 * J) * nf + 2 * I;
-  kc[(int64_t)b * esc + (int64_t)J * nc + I] = 0.25 * ((f[0] + f[1]) + (f[nf] + f[nf + 1]));
+  const T* f = kf + (int64_t)b * esf + (int64_t)(2 * J) * nf + 2 * I;
+  kc[(int64_t)b * esc + (int64_t)J * nc + I] = T(0.25) * ((f[0] + f[1]) + (f[nf] + f[nf + 1]));
   if (prof.acc && I == 0 && J == 0) atomicAdd(prof.acc, prof.per_sample);
 }
 
-__global__ void k_coarsen3d(int nc, const double* __restrict__ kf, double* __restrict__ kc,
+template <class T>
+__global__ void k_coarsen3d(int nc, const T* __restrict__ kf, T* __restrict__ kc,
                             int64_t esf, int64_t esc, Prof prof) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y % nc;
@@ -160,14 +162,31 @@ __global__ void k_coarsen3d(int nc, const double* __restrict__ kf, double* __res
   if (I >= nc) return;
   const int nf = 2 * nc;
   const int64_t pl = (int64_t)nf * nf;
-  const double* f = kf + (int64_t)b * esf + (int64_t)(2 * K) * pl + (int64_t)(2 * J) * nf + 2 * I;
-  const double s0 = (f[0] + f[1]) + (f[nf] + f[nf + 1]);
-  const double s1 = (f[pl] + f[pl + 1]) + (f[pl + nf] + f[pl + nf + 1]);
-  kc[(int64_t)b * esc + ((int64_t)K * nc + J) * nc + I] = 0.125 * (s0 + s1);
+  const T* f = kf + (int64_t)b * esf + (int64_t)(2 * K) * pl + (int64_t)(2 * J) * nf + 2 * I;
+  const T s0 = (f[0] + f[1]) + (f[nf] + f[nf + 1]);
+  const T s1 = (f[pl] + f[pl + 1]) + (f[pl + nf] + f[pl + nf + 1]);
+  kc[(int64_t)b * esc + ((int64_t)K * nc + J) * nc + I] = T(0.125) * (s0 + s1);
   if (prof.acc && I == 0 && J == 0 && K == 0) atomicAdd(prof.acc, prof.per_sample);
 }
 
+__global__ void k_cast_kappa(int64_t ne, int64_t es, const double* __restrict__ k64,
+                             float* __restrict__ k32) {
+  const int64_t b = blockIdx.y;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne;
+       e += (int64_t)gridDim.x * blockDim.x)
+    k32[b * es + e] = (float)k64[b * es + e];
+}
+
 }  // namespace
+
+cudaError_t launch_cast_kappa(cudaStream_t s, const Grid& g, const double* k64, float* k32,
+                              int64_t B) {
+  if (B == 0) return cudaSuccess;
+  const int64_t ne = ipow(g.n, g.dim);
+  const int64_t blocks = std::min<int64_t>((ne + 255) / 256, 4096);
+  k_cast_kappa<<<dim3((unsigned)blocks, (unsigned)B), 256, 0, s>>>(ne, g.es, k64, k32);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_kle_table(cudaStream_t s, int n, int m, const double* omega,
                              const double* theta, const int32_t* even, double* table) {
@@ -197,19 +216,25 @@ cudaError_t launch_kappa(cudaStream_t s, const Grid& g, int m, double sqrt_sigma
   return cudaGetLastError();
 }
 
+template <class T>
 cudaError_t launch_coarsen(cudaStream_t s, const Grid& fine, const Grid& coarse,
-                           const double* kf, double* kc, int64_t B, Prof p) {
+                           const T* kf, T* kc, int64_t B, Prof p) {
   if (B == 0) return cudaSuccess;
   const int nc = coarse.n;
   const int threads = nc < 128 ? ((nc + 31) / 32) * 32 : 128;
   if (fine.dim == 2) {
     dim3 grid((nc + threads - 1) / threads, nc, (unsigned)B);
-    k_coarsen2d<<<grid, threads, 0, s>>>(nc, kf, kc, fine.es, coarse.es, p);
+    k_coarsen2d<T><<<grid, threads, 0, s>>>(nc, kf, kc, fine.es, coarse.es, p);
   } else {
     dim3 grid((nc + threads - 1) / threads, nc * nc, (unsigned)B);
-    k_coarsen3d<<<grid, threads, 0, s>>>(nc, kf, kc, fine.es, coarse.es, p);
+    k_coarsen3d<T><<<grid, threads, 0, s>>>(nc, kf, kc, fine.es, coarse.es, p);
   }
   return cudaGetLastError();
 }
+
+template cudaError_t launch_coarsen<double>(cudaStream_t, const Grid&, const Grid&, const double*,
+                                            double*, int64_t, Prof);
+template cudaError_t launch_coarsen<float>(cudaStream_t, const Grid&, const Grid&, const float*,
+                                           float*, int64_t, Prof);
 
 }  // namespace mlmc

@@ -8,7 +8,15 @@
 
 namespace mlmc {
 
-// 2D tiles: 32 x 8 threads, one node per thread.
+// 2D stencil kernels: CTAs of SWARPS warps, each warp a strip of 30 output
+// columns streamed over SROWS rows.
+constexpr int SWARPS = 4;
+constexpr int SROWS = 32;
+// Flat (pointwise) kernels: FLAT_THREADS threads per CTA, FLAT_ELEMS
+// elements of one sample per CTA.
+constexpr int FLAT_THREADS = 256;
+constexpr int FLAT_ELEMS = 4096;
+// KLE kernel tiles.
 constexpr int TX2 = 32;
 constexpr int TY2 = 8;
 // 3D tiles: 32 x 4 x 2 threads.
@@ -39,6 +47,8 @@ enum KernelId {
   KID_ESTIMATE,
   KID_COUNT,
   KID_SETUP,
+  KID_REFINE,
+  KID_RESID64,
   NUM_KERNELS
 };
 
@@ -56,15 +66,18 @@ inline int64_t ipow(int64_t b, int e) {
   return r;
 }
 
-// Geometry of one (multigrid) grid level for a batch.
+// Geometry of one (multigrid) grid level and its launch shapes.
 struct Grid {
   int dim;
-  int n;          // cells per side
-  int64_t ns;     // node stride (doubles per sample)
-  int64_t es;     // element stride
+  int n;            // cells per side
+  int64_t ns;       // node stride (values per sample)
+  int64_t es;       // element stride
   double h;
-  int tiles_x, tiles_y, tiles_z;  // CTA tiles per sample
-  int64_t tiles() const { return (int64_t)tiles_x * tiles_y * tiles_z; }
+  int sx, sy;       // stencil CTAs per sample (strip groups x row chunks)
+  int64_t tiles_s;  // partials per sample written by stencil kernels (one per warp)
+  int fx;           // flat CTAs per sample
+  int64_t tiles_f;  // partials per sample written by flat kernels (one per CTA)
+  int64_t tiles() const { return tiles_s > tiles_f ? tiles_s : tiles_f; }
 };
 
 Grid make_grid(int dim, int n);
@@ -79,9 +92,22 @@ struct Scalars {
   double* tol;      // rtol * ||b||
   int32_t* active;
   int32_t* iters;
+  double* scale;    // mixed form: scale of the inner right-hand side (outer scalars only)
+  int32_t* total;   // mixed form: inner iterations so far (outer scalars only)
 };
 
 enum FinMode { FIN_GAMMA0 = 0, FIN_ALPHA = 1, FIN_CONV = 2, FIN_BETA = 3, FIN_QOI = 4 };
+
+// Mixed form: close one outer refinement step. With rho = ||r|| from the
+// partials: converged (rho <= tol) -> inactive, iters = total inner iterations;
+// outer_it == outer_max -> inactive, iters = -1; else scale = rho. Inner
+// iterations (inner.iters, -1 = hit inner max) are added to the total.
+cudaError_t launch_outer_step(cudaStream_t s, const double* part, int64_t tiles,
+                              const Scalars& outer, const int32_t* inner_iters, int inner_max,
+                              int outer_it, int outer_max, int64_t B);
+// inner.active = outer.active, inner.tol = tol, inner.iters = 0, beta = 0.
+cudaError_t launch_inner_init(cudaStream_t s, const Scalars& inner, const Scalars& outer,
+                              double tol, int64_t B);
 
 // ---- launchers (return cudaGetLastError()) -----------------------------
 
@@ -94,35 +120,55 @@ cudaError_t launch_kle_table(cudaStream_t s, int n, int m, const double* omega,
 cudaError_t launch_kappa(cudaStream_t s, const Grid& g, int m, double sqrt_sigma2,
                          const double* table, const double* xi, int64_t B, double* kappa, Prof p);
 
+template <class T>
 cudaError_t launch_coarsen(cudaStream_t s, const Grid& fine, const Grid& coarse,
-                           const double* kf, double* kc, int64_t B, Prof p);
+                           const T* kf, T* kc, int64_t B, Prof p);
 
-// 2D FP64 operator / PCG / multigrid kernels (stencil2d.cu).
+// kappa32 = (float) kappa64, element arrays.
+cudaError_t launch_cast_kappa(cudaStream_t s, const Grid& g, const double* k64, float* k32,
+                              int64_t B);
+
+// 2D operator / PCG / multigrid kernels (stencil2d.cu), T = double or float.
 namespace d2 {
-cudaError_t apply(cudaStream_t s, const Grid& g, const double* kappa, const double* x, double* y,
-                  int64_t B, Prof p);
-cudaError_t winv(cudaStream_t s, const Grid& g, const double* kappa, double omega, double* w,
-                 int64_t B);
-cudaError_t pcg_init(cudaStream_t s, const Grid& g, double* x, double* r, int64_t B, Prof p);
-cudaError_t pcg_pq(cudaStream_t s, const Grid& g, const double* kappa, const double* z,
-                   const double* p_old, double* p_new, double* q, const Scalars& sc,
-                   double* part, int64_t B, Prof p);
-cudaError_t pcg_xr(cudaStream_t s, const Grid& g, double* x, const double* pv, double* r,
-                   const double* q, const Scalars& sc, double* part, int64_t B, Prof p);
-cudaError_t jacobi_z(cudaStream_t s, const Grid& g, const double* winv, const double* r,
-                     double* z, const Scalars& sc, double* part, int64_t B, Prof p);
-cudaError_t mg_pre(cudaStream_t s, const Grid& g, const double* kappa, const double* w,
-                   const double* b, double* e, double* r1, const int32_t* active, int64_t B,
-                   Prof p);
-cudaError_t restrict_(cudaStream_t s, const Grid& fine, const Grid& coarse, const double* r1,
-                      double* bc, const int32_t* active, int64_t B, Prof p);
-cudaError_t coarse_solve(cudaStream_t s, const Grid& g, const double* kappa, const double* b,
-                         double* e, const int32_t* active, int64_t B);
-cudaError_t mg_post(cudaStream_t s, const Grid& g, const Grid& coarse, const double* kappa,
-                    const double* w, const double* b, const double* e, const double* ec,
-                    double* out, const int32_t* active, double* part, int64_t B, Prof p);
-cudaError_t qoi(cudaStream_t s, const Grid& g, int box, int L, int H, double inv_vol,
-                const double* x, double* part, int64_t B, Prof p);
+template <class T>
+cudaError_t apply(cudaStream_t s, const Grid& g, const T* kappa, const T* x, T* y, int64_t B, Prof p);
+template <class T>
+cudaError_t winv(cudaStream_t s, const Grid& g, const T* kappa, double omega, T* w, int64_t B);
+// x = 0; if r != nullptr, r = b (b_i = h^2 at interior nodes).
+template <class T>
+cudaError_t pcg_init(cudaStream_t s, const Grid& g, T* x, T* r, int64_t B, Prof p);
+template <class T>
+cudaError_t pcg_pq(cudaStream_t s, const Grid& g, const T* kappa, const T* z, const T* p_old,
+                   T* p_new, T* q, const Scalars& sc, double* part, int64_t B, Prof p);
+template <class T>
+cudaError_t pcg_xr(cudaStream_t s, const Grid& g, T* x, const T* pv, T* r, const T* q,
+                   const Scalars& sc, double* part, int64_t B, Prof p);
+template <class T>
+cudaError_t jacobi_z(cudaStream_t s, const Grid& g, const T* winv, const T* r, T* z,
+                     const Scalars& sc, double* part, int64_t B, Prof p);
+template <class T>
+cudaError_t mg_pre(cudaStream_t s, const Grid& g, const T* kappa, const T* w, const T* b, T* e,
+                   T* r1, const int32_t* active, int64_t B, Prof p);
+template <class T>
+cudaError_t restrict_(cudaStream_t s, const Grid& fine, const Grid& coarse, const T* r1, T* bc,
+                      const int32_t* active, int64_t B, Prof p);
+template <class T>
+cudaError_t coarse_solve(cudaStream_t s, const Grid& g, const T* kappa, const T* b, T* e,
+                         const int32_t* active, int64_t B);
+template <class T>
+cudaError_t mg_post(cudaStream_t s, const Grid& g, const Grid& coarse, const T* kappa, const T* w,
+                    const T* b, const T* e, const T* ec, T* out, const int32_t* active,
+                    double* part, int64_t B, Prof p);
+template <class T>
+cudaError_t qoi(cudaStream_t s, const Grid& g, int box, int L, int H, double inv_vol, const T* x,
+                double* part, int64_t B, Prof p);
+// mixed form (FP64 outer refinement around the FP32 inner solve)
+cudaError_t resid64(cudaStream_t s, const Grid& g, const double* kappa, const double* u,
+                    double* r, const int32_t* active, double* part, int64_t B, Prof p);
+cudaError_t to_rhs32(cudaStream_t s, const Grid& g, const double* r, const double* scale,
+                     float* r32, const int32_t* active, int64_t B, Prof p);
+cudaError_t add_correction(cudaStream_t s, const Grid& g, double* u, const float* d32,
+                           const double* scale, const int32_t* active, int64_t B, Prof p);
 }  // namespace d2
 
 cudaError_t launch_finalize(cudaStream_t s, FinMode mode, const double* part, int64_t tiles,
@@ -130,7 +176,10 @@ cudaError_t launch_finalize(cudaStream_t s, FinMode mode, const double* part, in
 
 cudaError_t launch_count_active(cudaStream_t s, const int32_t* active, int64_t B, int32_t* count);
 
-cudaError_t launch_scalars_init(cudaStream_t s, const Scalars& sc, double tol, int64_t B);
+// active = 1, iters = 0, tol = tol, beta = alpha = gamma = 0; total = 0 and
+// scale = scale0 when those arrays are present.
+cudaError_t launch_scalars_init(cudaStream_t s, const Scalars& sc, double tol, double scale0,
+                                int64_t B);
 
 cudaError_t launch_welford(cudaStream_t s, const double* qf, const double* qc, int64_t B,
                            mlmc_level_state* st, double cost);

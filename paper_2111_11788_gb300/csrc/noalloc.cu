@@ -94,6 +94,8 @@ size_t na_layout(char* base, const Grid* g, int K, int64_t B, NaWs& w) {
   w.sc.active = (int32_t*)take(sizeof(int32_t) * (size_t)B);
   w.sc.iters = (int32_t*)take(sizeof(int32_t) * (size_t)B);
   w.count = (int32_t*)take(sizeof(int32_t));
+  w.sc.scale = nullptr;
+  w.sc.total = nullptr;
   return off;
 }
 
@@ -113,10 +115,12 @@ __global__ void k_na_count_failed(const int32_t* __restrict__ iters, int64_t B, 
     if ((call) != cudaSuccess) return MLMC_ERR_CUDA; \
   } while (0)
 
-mlmc_status na_precondition(cudaStream_t s, const Grid* g, int K, NaWs& w, int64_t B) {
+mlmc_status na_precondition(cudaStream_t s, const Grid* g, int K, NaWs& w, int64_t B,
+                            int64_t* tiles) {
   const Prof off{nullptr, 0.0};
   if (K == 1) {
     NA_CK(d2::jacobi_z(s, g[0], w.w[0], w.r, w.z, w.sc, w.part, B, off));
+    *tiles = g[0].tiles_f;
     return MLMC_OK;
   }
   for (int k = 0; k < K - 1; ++k) {
@@ -127,6 +131,7 @@ mlmc_status na_precondition(cudaStream_t s, const Grid* g, int K, NaWs& w, int64
   for (int k = K - 2; k >= 0; --k)
     NA_CK(d2::mg_post(s, g[k], g[k + 1], w.kap[k], w.w[k], w.bk[k], w.e[k], w.eo[k + 1], w.eo[k],
                       w.sc.active, k == 0 ? w.part : nullptr, B, off));
+  *tiles = g[0].tiles_s;
   return MLMC_OK;
 }
 
@@ -173,30 +178,30 @@ extern "C" mlmc_status mlmc_solve_noalloc(const mlmc_config* c, int mesh, const 
   const double omega = (K > 1) ? c->mg_omega : 1.0;
   for (int k = 0; k < (K > 1 ? K - 1 : 1); ++k) NA_CK(d2::winv(s, g[k], w.kap[k], omega, w.w[k], count));
   const double bnorm = g[0].h * g[0].h * (double)(n - 1);
-  NA_CK(launch_scalars_init(s, w.sc, c->rtol * bnorm, count));
+  NA_CK(launch_scalars_init(s, w.sc, c->rtol * bnorm, 0.0, count));
   NA_CK(d2::pcg_init(s, g[0], w.x, w.r, count, off));
-  mlmc_status st = na_precondition(s, g, K, w, count);
+  int64_t Tp = 0;
+  mlmc_status st = na_precondition(s, g, K, w, count, &Tp);
   if (st != MLMC_OK) return st;
-  const int64_t T = g[0].tiles();
-  NA_CK(launch_finalize(s, FIN_GAMMA0, w.part, T, w.sc, nullptr, 0, c->max_iter, count));
+  NA_CK(launch_finalize(s, FIN_GAMMA0, w.part, Tp, w.sc, nullptr, 0, c->max_iter, count));
   const int check = c->check_every > 0 ? c->check_every : 4;
   double* pold = w.p0;
   double* pnew = w.p1;
   int32_t h_count = 0;
   for (int it = 1; it <= c->max_iter; ++it) {
     NA_CK(d2::pcg_pq(s, g[0], w.kap[0], w.z, pold, pnew, w.q, w.sc, w.part, count, off));
-    NA_CK(launch_finalize(s, FIN_ALPHA, w.part, T, w.sc, nullptr, it, c->max_iter, count));
+    NA_CK(launch_finalize(s, FIN_ALPHA, w.part, g[0].tiles_s, w.sc, nullptr, it, c->max_iter, count));
     NA_CK(d2::pcg_xr(s, g[0], w.x, pnew, w.r, w.q, w.sc, w.part, count, off));
-    NA_CK(launch_finalize(s, FIN_CONV, w.part, T, w.sc, nullptr, it, c->max_iter, count));
+    NA_CK(launch_finalize(s, FIN_CONV, w.part, g[0].tiles_f, w.sc, nullptr, it, c->max_iter, count));
     if (it % check == 0 || it == c->max_iter) {
       NA_CK(launch_count_active(s, w.sc.active, count, w.count));
       NA_CK(cudaMemcpyAsync(&h_count, w.count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
       NA_CK(cudaStreamSynchronize(s));
       if (h_count == 0) break;
     }
-    st = na_precondition(s, g, K, w, count);
+    st = na_precondition(s, g, K, w, count, &Tp);
     if (st != MLMC_OK) return st;
-    NA_CK(launch_finalize(s, FIN_BETA, w.part, T, w.sc, nullptr, it, c->max_iter, count));
+    NA_CK(launch_finalize(s, FIN_BETA, w.part, Tp, w.sc, nullptr, it, c->max_iter, count));
     double* t = pold;
     pold = pnew;
     pnew = t;
@@ -205,7 +210,7 @@ extern "C" mlmc_status mlmc_solve_noalloc(const mlmc_config* c, int mesh, const 
   const int box = (c->qoi == MLMC_QOI_BOX_MEAN) ? 1 : 0;
   const double vol = (c->box_hi - c->box_lo) * (c->box_hi - c->box_lo);
   NA_CK(d2::qoi(s, g[0], box, L, H, box ? 1.0 / vol : 1.0, w.x, w.part, count, off));
-  NA_CK(launch_finalize(s, FIN_QOI, w.part, T, w.sc, q, 0, c->max_iter, count));
+  NA_CK(launch_finalize(s, FIN_QOI, w.part, g[0].tiles_f, w.sc, q, 0, c->max_iter, count));
   if (iters) NA_CK(cudaMemcpyAsync(iters, w.sc.iters, sizeof(int32_t) * count, cudaMemcpyDeviceToDevice, s));
   // number of samples that hit max_iter (iteration count -1)
   k_na_count_failed<<<1, 256, 0, s>>>(w.sc.iters, count, w.count);

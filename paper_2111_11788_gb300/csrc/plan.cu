@@ -23,15 +23,12 @@ Grid make_grid(int dim, int n) {
   g.ns = round_up(ipow(n + 1, dim), 32);
   g.es = round_up(ipow(n, dim), 32);
   g.h = 1.0 / n;
-  if (dim == 2) {
-    g.tiles_x = (n + 1 + TX2 - 1) / TX2;
-    g.tiles_y = (n + 1 + TY2 - 1) / TY2;
-    g.tiles_z = 1;
-  } else {
-    g.tiles_x = (n + 1 + TX3 - 1) / TX3;
-    g.tiles_y = (n + 1 + TY3 - 1) / TY3;
-    g.tiles_z = (n + 1 + TZ3 - 1) / TZ3;
-  }
+  const int strips = (n + 1 + 29) / 30;
+  g.sx = (strips + SWARPS - 1) / SWARPS;
+  g.sy = (n + 1 + SROWS - 1) / SROWS;
+  g.tiles_s = (int64_t)g.sx * g.sy * SWARPS;
+  g.fx = (int)((g.ns + FLAT_ELEMS - 1) / FLAT_ELEMS);
+  g.tiles_f = g.fx;
   return g;
 }
 
@@ -40,7 +37,7 @@ namespace {
 const char* kKernelNames[NUM_KERNELS] = {
     "draw_xi", "kle_table", "kappa", "coarsen_kappa", "apply", "pcg_init", "pcg_pq", "pcg_xr",
     "jacobi_z", "mg_pre", "restrict", "coarse_solve", "mg_post", "qoi", "finalize", "welford",
-    "estimate", "count_active", "setup"};
+    "estimate", "count_active", "setup", "refine", "resid64"};
 
 // Bump allocator over the workspace (base == nullptr: size only).
 struct Carve {
@@ -65,34 +62,36 @@ struct MeshInfo {
   double* table;         // n x m KLE table on the device
 };
 
-// Views of the workspace for one batched solve on one mesh.
+// Views of the workspace for one batched PCG solve on one mesh, value type T.
+template <class T>
 struct SolveWs {
-  double *x, *r, *p0, *p1, *q, *z;
-  double* kap[MAX_MG];
-  double* w[MAX_MG];
-  double *e[MAX_MG], *r1[MAX_MG], *bk[MAX_MG], *eo[MAX_MG];
+  T *x, *r, *p0, *p1, *q, *z;
+  T* kap[MAX_MG];
+  T* w[MAX_MG];
+  T *e[MAX_MG], *r1[MAX_MG], *bk[MAX_MG], *eo[MAX_MG];
   double* part;
   Scalars sc;
   int32_t* count;
 };
 
-void carve_solve(Carve& c, const MeshInfo& mi, int64_t B, bool own_kappa0, SolveWs& w) {
+template <class T>
+void carve_solve(Carve& c, const MeshInfo& mi, int64_t B, bool own_kappa0, SolveWs<T>& w) {
   const Grid& g0 = mi.g[0];
-  w.x = c.take<double>(B * g0.ns);
-  w.r = c.take<double>(B * g0.ns);
-  w.p0 = c.take<double>(B * g0.ns);
-  w.p1 = c.take<double>(B * g0.ns);
-  w.q = c.take<double>(B * g0.ns);
-  w.z = c.take<double>(B * g0.ns);
+  w.x = c.take<T>(B * g0.ns);
+  w.r = c.take<T>(B * g0.ns);
+  w.p0 = c.take<T>(B * g0.ns);
+  w.p1 = c.take<T>(B * g0.ns);
+  w.q = c.take<T>(B * g0.ns);
+  w.z = c.take<T>(B * g0.ns);
   for (int k = 0; k < mi.K; ++k) {
     const Grid& g = mi.g[k];
-    w.kap[k] = (k == 0 && !own_kappa0) ? nullptr : c.take<double>(B * g.es);
-    w.w[k] = c.take<double>(B * g.ns);
+    w.kap[k] = (k == 0 && !own_kappa0) ? nullptr : c.take<T>(B * g.es);
+    w.w[k] = c.take<T>(B * g.ns);
     if (mi.K > 1) {
-      w.e[k] = c.take<double>(B * g.ns);
-      w.r1[k] = (k < mi.K - 1) ? c.take<double>(B * g.ns) : nullptr;
-      w.bk[k] = (k == 0) ? w.r : c.take<double>(B * g.ns);
-      w.eo[k] = (k == 0) ? w.z : ((k < mi.K - 1) ? c.take<double>(B * g.ns) : w.e[k]);
+      w.e[k] = c.take<T>(B * g.ns);
+      w.r1[k] = (k < mi.K - 1) ? c.take<T>(B * g.ns) : nullptr;
+      w.bk[k] = (k == 0) ? w.r : c.take<T>(B * g.ns);
+      w.eo[k] = (k == 0) ? w.z : ((k < mi.K - 1) ? c.take<T>(B * g.ns) : w.e[k]);
     }
   }
   w.part = c.take<double>(B * g0.tiles());
@@ -104,7 +103,38 @@ void carve_solve(Carve& c, const MeshInfo& mi, int64_t B, bool own_kappa0, Solve
   w.sc.tol = c.take<double>(B);
   w.sc.active = c.take<int32_t>(B);
   w.sc.iters = c.take<int32_t>(B);
+  w.sc.scale = nullptr;
+  w.sc.total = nullptr;
   w.count = c.take<int32_t>(1);
+}
+
+// Mixed form: FP64 solution / residual / kappa plus the FP32 inner solve.
+struct MixedWs {
+  double* u;
+  double* r;
+  double* kap64;
+  Scalars outer;
+  SolveWs<float> in;
+};
+
+void carve_mixed(Carve& c, const MeshInfo& mi, int64_t B, MixedWs& w) {
+  const Grid& g0 = mi.g[0];
+  w.u = c.take<double>(B * g0.ns);
+  w.r = c.take<double>(B * g0.ns);
+  w.kap64 = c.take<double>(B * g0.es);
+  w.outer.gamma = w.outer.delta = w.outer.alpha = w.outer.beta = nullptr;
+  w.outer.rho = c.take<double>(B);
+  w.outer.tol = c.take<double>(B);
+  w.outer.scale = c.take<double>(B);
+  w.outer.active = c.take<int32_t>(B);
+  w.outer.iters = c.take<int32_t>(B);
+  w.outer.total = c.take<int32_t>(B);
+  // the outer scalars' gamma..beta are written by the scalar-init kernel: give them storage
+  w.outer.gamma = c.take<double>(B);
+  w.outer.delta = c.take<double>(B);
+  w.outer.alpha = c.take<double>(B);
+  w.outer.beta = c.take<double>(B);
+  carve_solve(c, mi, B, true, w.in);
 }
 
 // Workspace of one coupled batch: xi, outputs and the solve views of the
@@ -115,16 +145,24 @@ struct CoupledWs {
   double* qc;
   int32_t* itf;
   int32_t* itc;
-  SolveWs s;
+  double* kap;          // FP64 kappa of the mesh being solved
+  SolveWs<double> s;    // FP64 form
+  MixedWs mx;           // mixed form
 };
 
-void carve_coupled(Carve& c, const MeshInfo& mi, int M, int64_t B, CoupledWs& w) {
+void carve_coupled(Carve& c, const MeshInfo& mi, int M, int64_t B, bool mixed, CoupledWs& w) {
   w.xi = c.take<double>(B * M);
   w.qf = c.take<double>(B);
   w.qc = c.take<double>(B);
   w.itf = c.take<int32_t>(B);
   w.itc = c.take<int32_t>(B);
-  carve_solve(c, mi, B, true, w.s);
+  if (mixed) {
+    carve_mixed(c, mi, B, w.mx);
+    w.kap = w.mx.kap64;
+  } else {
+    carve_solve(c, mi, B, true, w.s);
+    w.kap = w.s.kap[0];
+  }
 }
 
 struct PendingEvent {
@@ -200,7 +238,9 @@ mlmc_status validate(const mlmc_config* c) {
       return MLMC_ERR_INVALID;
   }
   if (c->precision != MLMC_FP64 && c->precision != MLMC_MIXED) return MLMC_ERR_INVALID;
-  if (c->precision == MLMC_MIXED) return MLMC_ERR_UNIMPLEMENTED;
+  if (c->precision == MLMC_MIXED &&
+      (!(c->inner_rtol > 0.0 && c->inner_rtol < 1.0) || c->inner_max_iter < 1 || c->outer_max_iter < 1))
+    return MLMC_ERR_INVALID;
   if (c->dim == 3) return MLMC_ERR_UNIMPLEMENTED;
   return MLMC_OK;
 }
@@ -338,17 +378,24 @@ mlmc_status ensure_pin(mlmc_plan p, size_t bytes) {
   return MLMC_OK;
 }
 
-size_t coupled_bytes(const MeshInfo& mi, int M, int64_t B) {
+bool is_mixed(mlmc_plan p) { return p->cfg.precision == MLMC_MIXED; }
+
+size_t coupled_bytes(const MeshInfo& mi, int M, int64_t B, bool mixed) {
   Carve c(nullptr);
   CoupledWs w;
-  carve_coupled(c, mi, M, B, w);
+  carve_coupled(c, mi, M, B, mixed, w);
   return c.off + 256;
 }
 
-size_t solve_bytes(const MeshInfo& mi, int64_t B) {
+size_t solve_bytes(const MeshInfo& mi, int64_t B, bool mixed) {
   Carve c(nullptr);
-  SolveWs w;
-  carve_solve(c, mi, B, false, w);
+  if (mixed) {
+    MixedWs w;
+    carve_mixed(c, mi, B, w);
+  } else {
+    SolveWs<double> w;
+    carve_solve(c, mi, B, false, w);
+  }
   return c.off + 256;
 }
 
@@ -367,16 +414,20 @@ int64_t max_batch(mlmc_plan p, SizeFn size_of, int64_t want) {
 
 // --- the batched PCG --------------------------------------------------
 
-// z = M r (GMG V-cycle or Jacobi), with per-tile partials of r.z in ws.part.
-mlmc_status precondition(mlmc_plan p, const MeshInfo& mi, SolveWs& w, int64_t B) {
+// z = M r (GMG V-cycle or Jacobi), with per-tile partials of r.z in w.part.
+template <class T>
+mlmc_status precondition(mlmc_plan p, const MeshInfo& mi, SolveWs<T>& w, int64_t B,
+                         int64_t* tiles) {
   cudaStream_t s = p->stream;
   const Grid& g0 = mi.g[0];
+  const double vb = (double)sizeof(T);
   const double nn0 = nodes_of(g0);
   if (mi.K == 1) {
     CK(run(p, KID_JACOBI_Z, [&] {
-      return d2::jacobi_z(s, g0, w.w[0], w.r, w.z, w.sc, w.part, B,
-                          prof_for(p, KID_JACOBI_Z, 3 * nn0 * 8));
+      return d2::jacobi_z<T>(s, g0, w.w[0], w.r, w.z, w.sc, w.part, B,
+                             prof_for(p, KID_JACOBI_Z, 3 * nn0 * vb));
     }));
+    *tiles = g0.tiles_f;
     return MLMC_OK;
   }
   const int K = mi.K;
@@ -384,94 +435,181 @@ mlmc_status precondition(mlmc_plan p, const MeshInfo& mi, SolveWs& w, int64_t B)
     const Grid& g = mi.g[k];
     const double nn = nodes_of(g), ne = elems_of(g);
     CK(run(p, KID_MG_PRE, [&] {
-      return d2::mg_pre(s, g, w.kap[k], w.w[k], w.bk[k], w.e[k], w.r1[k], w.sc.active, B,
-                        prof_for(p, KID_MG_PRE, (4 * nn + ne) * 8));
+      return d2::mg_pre<T>(s, g, w.kap[k], w.w[k], w.bk[k], w.e[k], w.r1[k], w.sc.active, B,
+                           prof_for(p, KID_MG_PRE, (4 * nn + ne) * vb));
     }));
     CK(run(p, KID_RESTRICT, [&] {
-      return d2::restrict_(s, g, mi.g[k + 1], w.r1[k], w.bk[k + 1], w.sc.active, B,
-                           prof_for(p, KID_RESTRICT, (nn + nodes_of(mi.g[k + 1])) * 8));
+      return d2::restrict_<T>(s, g, mi.g[k + 1], w.r1[k], w.bk[k + 1], w.sc.active, B,
+                              prof_for(p, KID_RESTRICT, (nn + nodes_of(mi.g[k + 1])) * vb));
     }));
   }
   CK(run(p, KID_COARSE, [&] {
-    return d2::coarse_solve(s, mi.g[K - 1], w.kap[K - 1], w.bk[K - 1], w.e[K - 1], w.sc.active, B);
+    return d2::coarse_solve<T>(s, mi.g[K - 1], w.kap[K - 1], w.bk[K - 1], w.e[K - 1], w.sc.active, B);
   }));
   for (int k = K - 2; k >= 0; --k) {
     const Grid& g = mi.g[k];
     const double nn = nodes_of(g), ne = elems_of(g), nc = nodes_of(mi.g[k + 1]);
     CK(run(p, KID_MG_POST, [&] {
-      return d2::mg_post(s, g, mi.g[k + 1], w.kap[k], w.w[k], w.bk[k], w.e[k], w.eo[k + 1],
-                         w.eo[k], w.sc.active, k == 0 ? w.part : nullptr, B,
-                         prof_for(p, KID_MG_POST, (4 * nn + ne + nc) * 8));
+      return d2::mg_post<T>(s, g, mi.g[k + 1], w.kap[k], w.w[k], w.bk[k], w.e[k], w.eo[k + 1],
+                            w.eo[k], w.sc.active, k == 0 ? w.part : nullptr, B,
+                            prof_for(p, KID_MG_POST, (4 * nn + ne + nc) * vb));
     }));
   }
+  *tiles = g0.tiles_s;
   return MLMC_OK;
 }
 
-// Solve A(kappa) u = b for B samples on mesh `mi`; w.kap[0] must hold kappa.
-// Leaves u in w.x, writes q (device) and iters (device).
-mlmc_status solve_batch(mlmc_plan p, const MeshInfo& mi, SolveWs& w, int64_t B, double* q_dev,
-                        int32_t* iters_dev) {
+// Multigrid kappa hierarchy and W = omega / D per level (w.kap[0] given).
+template <class T>
+mlmc_status setup_levels(mlmc_plan p, const MeshInfo& mi, SolveWs<T>& w, int64_t B) {
   cudaStream_t s = p->stream;
-  const mlmc_config& c = p->cfg;
-  const Grid& g0 = mi.g[0];
-  const double nn0 = nodes_of(g0), ne0 = elems_of(g0);
   const int K = mi.K;
+  const double vb = (double)sizeof(T);
   for (int k = 1; k < K; ++k) {
     CK(run(p, KID_COARSEN, [&] {
-      return launch_coarsen(s, mi.g[k - 1], mi.g[k], w.kap[k - 1], w.kap[k], B,
-                            prof_for(p, KID_COARSEN, (elems_of(mi.g[k - 1]) + elems_of(mi.g[k])) * 8));
+      return launch_coarsen<T>(s, mi.g[k - 1], mi.g[k], w.kap[k - 1], w.kap[k], B,
+                               prof_for(p, KID_COARSEN, (elems_of(mi.g[k - 1]) + elems_of(mi.g[k])) * vb));
     }));
   }
-  const double omega = (K > 1) ? c.mg_omega : 1.0;
+  const double omega = (K > 1) ? p->cfg.mg_omega : 1.0;
   for (int k = 0; k < std::max(1, K - 1); ++k)
-    CK(run(p, KID_SETUP, [&] { return d2::winv(s, mi.g[k], w.kap[k], omega, w.w[k], B); }));
-  const double bnorm = std::pow(g0.h, c.dim) * std::sqrt((double)interior_dofs(c.dim, g0.n));
-  CK(run(p, KID_SETUP, [&] { return launch_scalars_init(s, w.sc, c.rtol * bnorm, B); }));
-  CK(run(p, KID_PCG_INIT, [&] {
-    return d2::pcg_init(s, g0, w.x, w.r, B, prof_for(p, KID_PCG_INIT, 2 * nn0 * 8));
-  }));
-  mlmc_status st = precondition(p, mi, w, B);
+    CK(run(p, KID_SETUP, [&] { return d2::winv<T>(s, mi.g[k], w.kap[k], omega, w.w[k], B); }));
+  return MLMC_OK;
+}
+
+// PCG iterations on w (scalars, x and r already initialised). Stops when no
+// sample is active or after max_iter iterations.
+template <class T>
+mlmc_status pcg_loop(mlmc_plan p, const MeshInfo& mi, SolveWs<T>& w, int64_t B, int max_iter) {
+  cudaStream_t s = p->stream;
+  const Grid& g0 = mi.g[0];
+  const double vb = (double)sizeof(T);
+  const double nn0 = nodes_of(g0), ne0 = elems_of(g0);
+  int64_t Tp = 0;
+  mlmc_status st = precondition<T>(p, mi, w, B, &Tp);
   if (st != MLMC_OK) return st;
-  const int64_t T = g0.tiles();
-  CK(run(p, KID_FINALIZE, [&] { return launch_finalize(s, FIN_GAMMA0, w.part, T, w.sc, nullptr, 0, c.max_iter, B); }));
-  int check = c.check_every;
+  CK(run(p, KID_FINALIZE, [&] { return launch_finalize(s, FIN_GAMMA0, w.part, Tp, w.sc, nullptr, 0, max_iter, B); }));
+  int check = p->cfg.check_every;
   if (check <= 0) check = (B * nn0 > 4e6) ? 1 : 4;
   if (ensure_pin(p, 64) != MLMC_OK) return MLMC_ERR_OOM;
   int32_t* h_count = (int32_t*)p->h_pin;
-  double* pold = w.p0;
-  double* pnew = w.p1;
-  for (int it = 1; it <= c.max_iter; ++it) {
+  T* pold = w.p0;
+  T* pnew = w.p1;
+  for (int it = 1; it <= max_iter; ++it) {
     CK(run(p, KID_PCG_PQ, [&] {
-      return d2::pcg_pq(s, g0, w.kap[0], w.z, pold, pnew, w.q, w.sc, w.part, B,
-                        prof_for(p, KID_PCG_PQ, (4 * nn0 + ne0) * 8));
+      return d2::pcg_pq<T>(s, g0, w.kap[0], w.z, pold, pnew, w.q, w.sc, w.part, B,
+                           prof_for(p, KID_PCG_PQ, (4 * nn0 + ne0) * vb));
     }));
-    CK(run(p, KID_FINALIZE, [&] { return launch_finalize(s, FIN_ALPHA, w.part, T, w.sc, nullptr, it, c.max_iter, B); }));
+    CK(run(p, KID_FINALIZE, [&] { return launch_finalize(s, FIN_ALPHA, w.part, g0.tiles_s, w.sc, nullptr, it, max_iter, B); }));
     CK(run(p, KID_PCG_XR, [&] {
-      return d2::pcg_xr(s, g0, w.x, pnew, w.r, w.q, w.sc, w.part, B,
-                        prof_for(p, KID_PCG_XR, 6 * nn0 * 8));
+      return d2::pcg_xr<T>(s, g0, w.x, pnew, w.r, w.q, w.sc, w.part, B,
+                           prof_for(p, KID_PCG_XR, 6 * nn0 * vb));
     }));
-    CK(run(p, KID_FINALIZE, [&] { return launch_finalize(s, FIN_CONV, w.part, T, w.sc, nullptr, it, c.max_iter, B); }));
-    if (it % check == 0 || it == c.max_iter) {
+    CK(run(p, KID_FINALIZE, [&] { return launch_finalize(s, FIN_CONV, w.part, g0.tiles_f, w.sc, nullptr, it, max_iter, B); }));
+    if (it % check == 0 || it == max_iter) {
       CK(run(p, KID_COUNT, [&] { return launch_count_active(s, w.sc.active, B, w.count); }));
       CK(cudaMemcpyAsync(h_count, w.count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
       if (*h_count == 0) break;
     }
-    st = precondition(p, mi, w, B);
+    st = precondition<T>(p, mi, w, B, &Tp);
     if (st != MLMC_OK) return st;
-    CK(run(p, KID_FINALIZE, [&] { return launch_finalize(s, FIN_BETA, w.part, T, w.sc, nullptr, it, c.max_iter, B); }));
+    CK(run(p, KID_FINALIZE, [&] { return launch_finalize(s, FIN_BETA, w.part, Tp, w.sc, nullptr, it, max_iter, B); }));
     std::swap(pold, pnew);
   }
+  return MLMC_OK;
+}
+
+double b_norm(const mlmc_config& c, const Grid& g0) {
+  return std::pow(g0.h, c.dim) * std::sqrt((double)interior_dofs(c.dim, g0.n));
+}
+
+// QoI of the FP64 solution u into q_dev (Sec. 2.1; exact Q1 integral mean).
+mlmc_status qoi_of(mlmc_plan p, const Grid& g0, const double* u, double* part, const Scalars& sc,
+                   double* q_dev, int64_t B) {
+  const mlmc_config& c = p->cfg;
   const int64_t nf = g0.n;
   const int L = (int)std::lround(c.box_lo * nf), H = (int)std::lround(c.box_hi * nf);
   const double vol = std::pow(c.box_hi - c.box_lo, c.dim);
   const int box = (c.qoi == MLMC_QOI_BOX_MEAN) ? 1 : 0;
   CK(run(p, KID_QOI, [&] {
-    return d2::qoi(s, g0, box, L, H, box ? 1.0 / vol : 1.0, w.x, w.part, B,
-                   prof_for(p, KID_QOI, nn0 * 8));
+    return d2::qoi<double>(p->stream, g0, box, L, H, box ? 1.0 / vol : 1.0, u, part, B,
+                           prof_for(p, KID_QOI, nodes_of(g0) * 8));
   }));
-  CK(run(p, KID_FINALIZE, [&] { return launch_finalize(s, FIN_QOI, w.part, T, w.sc, q_dev, 0, c.max_iter, B); }));
+  CK(run(p, KID_FINALIZE, [&] { return launch_finalize(p->stream, FIN_QOI, part, g0.tiles_f, sc, q_dev, 0, c.max_iter, B); }));
+  return MLMC_OK;
+}
+
+// FP64 form: solve A(kappa) u = b for B samples; w.kap[0] holds kappa.
+// Leaves u in w.x, writes q (device) and iters (device).
+mlmc_status solve_fp64(mlmc_plan p, const MeshInfo& mi, SolveWs<double>& w, int64_t B,
+                       double* q_dev, int32_t* iters_dev) {
+  cudaStream_t s = p->stream;
+  const mlmc_config& c = p->cfg;
+  const Grid& g0 = mi.g[0];
+  mlmc_status st = setup_levels<double>(p, mi, w, B);
+  if (st != MLMC_OK) return st;
+  CK(run(p, KID_SETUP, [&] { return launch_scalars_init(s, w.sc, c.rtol * b_norm(c, g0), 0.0, B); }));
+  CK(run(p, KID_PCG_INIT, [&] {
+    return d2::pcg_init<double>(s, g0, w.x, w.r, B, prof_for(p, KID_PCG_INIT, 2 * nodes_of(g0) * 8));
+  }));
+  st = pcg_loop<double>(p, mi, w, B, c.max_iter);
+  if (st != MLMC_OK) return st;
+  st = qoi_of(p, g0, w.x, w.part, w.sc, q_dev, B);
+  if (st != MLMC_OK) return st;
   if (iters_dev) CK(cudaMemcpyAsync(iters_dev, w.sc.iters, sizeof(int32_t) * B, cudaMemcpyDeviceToDevice, s));
+  return MLMC_OK;
+}
+
+// Mixed form: FP64 iterative refinement around FP32 GMG/Jacobi-PCG
+// (kappa32 = rounded kappa64). w.kap64 holds kappa. Leaves u in w.u.
+mlmc_status solve_mixed(mlmc_plan p, const MeshInfo& mi, MixedWs& w, int64_t B, double* q_dev,
+                        int32_t* iters_dev) {
+  cudaStream_t s = p->stream;
+  const mlmc_config& c = p->cfg;
+  const Grid& g0 = mi.g[0];
+  const double nn0 = nodes_of(g0), ne0 = elems_of(g0);
+  CK(run(p, KID_SETUP, [&] { return launch_cast_kappa(s, g0, w.kap64, w.in.kap[0], B); }));
+  mlmc_status st = setup_levels<float>(p, mi, w.in, B);
+  if (st != MLMC_OK) return st;
+  const double bn = b_norm(c, g0);
+  CK(run(p, KID_SETUP, [&] { return launch_scalars_init(s, w.outer, c.rtol * bn, bn, B); }));
+  CK(run(p, KID_PCG_INIT, [&] {
+    return d2::pcg_init<double>(s, g0, w.u, w.r, B, prof_for(p, KID_PCG_INIT, 2 * nn0 * 8));
+  }));
+  if (ensure_pin(p, 64) != MLMC_OK) return MLMC_ERR_OOM;
+  int32_t* h_count = (int32_t*)p->h_pin;
+  for (int outer = 1; outer <= c.outer_max_iter; ++outer) {
+    CK(run(p, KID_REFINE, [&] {
+      return d2::to_rhs32(s, g0, w.r, w.outer.scale, w.in.r, w.outer.active, B,
+                          prof_for(p, KID_REFINE, nn0 * (8 + 4)));
+    }));
+    CK(run(p, KID_SETUP, [&] { return launch_inner_init(s, w.in.sc, w.outer, c.inner_rtol, B); }));
+    CK(run(p, KID_PCG_INIT, [&] {
+      return d2::pcg_init<float>(s, g0, w.in.x, nullptr, B, prof_for(p, KID_PCG_INIT, nn0 * 4));
+    }));
+    st = pcg_loop<float>(p, mi, w.in, B, c.inner_max_iter);
+    if (st != MLMC_OK) return st;
+    CK(run(p, KID_REFINE, [&] {
+      return d2::add_correction(s, g0, w.u, w.in.x, w.outer.scale, w.outer.active, B,
+                                prof_for(p, KID_REFINE, nn0 * (8 + 4 + 8)));
+    }));
+    CK(run(p, KID_RESID64, [&] {
+      return d2::resid64(s, g0, w.kap64, w.u, w.r, w.outer.active, w.in.part, B,
+                         prof_for(p, KID_RESID64, (2 * nn0 + ne0) * 8));
+    }));
+    CK(run(p, KID_FINALIZE, [&] {
+      return launch_outer_step(s, w.in.part, g0.tiles_s, w.outer, w.in.sc.iters, c.inner_max_iter, outer,
+                               c.outer_max_iter, B);
+    }));
+    CK(run(p, KID_COUNT, [&] { return launch_count_active(s, w.outer.active, B, w.in.count); }));
+    CK(cudaMemcpyAsync(h_count, w.in.count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (*h_count == 0) break;
+  }
+  st = qoi_of(p, g0, w.u, w.in.part, w.outer, q_dev, B);
+  if (st != MLMC_OK) return st;
+  if (iters_dev) CK(cudaMemcpyAsync(iters_dev, w.outer.iters, sizeof(int32_t) * B, cudaMemcpyDeviceToDevice, s));
   return MLMC_OK;
 }
 
@@ -515,6 +653,9 @@ void mlmc_config_default(mlmc_config* c) {
   c->mg_coarsest = 2;
   c->check_every = 0;
   c->workspace_bytes = 0;
+  c->inner_rtol = 1e-5;
+  c->inner_max_iter = 60;
+  c->outer_max_iter = 12;
 }
 
 int64_t mlmc_node_stride(int dim, int n) {
@@ -703,21 +844,36 @@ mlmc_status mlmc_solve(mlmc_plan p, int mesh, const double* kappa, int64_t count
   if (!p || mesh < 0 || mesh >= p->cfg.n_levels || count < 0 || (count > 0 && (!kappa || !q)))
     return MLMC_ERR_INVALID;
   const MeshInfo& mi = p->meshes[mesh];
-  const int64_t Bmax = max_batch(p, [&](int64_t B) { return solve_bytes(mi, B); }, count);
+  const bool mixed = is_mixed(p);
+  const int64_t Bmax = max_batch(p, [&](int64_t B) { return solve_bytes(mi, B, mixed); }, count);
   bool bad = false;
   for (int64_t off = 0; off < count; off += Bmax) {
     const int64_t B = std::min<int64_t>(Bmax, count - off);
-    mlmc_status st = ensure_ws(p, solve_bytes(mi, B));
+    mlmc_status st = ensure_ws(p, solve_bytes(mi, B, mixed));
     if (st != MLMC_OK) return st;
     Carve c(p->ws);
-    SolveWs w;
-    carve_solve(c, mi, B, false, w);
-    w.kap[0] = const_cast<double*>(kappa + off * mi.g[0].es);
-    st = solve_batch(p, mi, w, B, q + off, iters ? iters + off : nullptr);
+    const double* kap = kappa + off * mi.g[0].es;
+    int32_t* it_dev = nullptr;
+    const double* x = nullptr;
+    if (mixed) {
+      MixedWs w;
+      carve_mixed(c, mi, B, w);
+      CK(cudaMemcpyAsync(w.kap64, kap, sizeof(double) * B * mi.g[0].es, cudaMemcpyDeviceToDevice, p->stream));
+      st = solve_mixed(p, mi, w, B, q + off, iters ? iters + off : nullptr);
+      it_dev = w.outer.iters;
+      x = w.u;
+    } else {
+      SolveWs<double> w;
+      carve_solve(c, mi, B, false, w);
+      w.kap[0] = const_cast<double*>(kap);
+      st = solve_fp64(p, mi, w, B, q + off, iters ? iters + off : nullptr);
+      it_dev = w.sc.iters;
+      x = w.x;
+    }
     if (st != MLMC_OK) return st;
-    if (u) CK(cudaMemcpyAsync(u + off * mi.g[0].ns, w.x, sizeof(double) * B * mi.g[0].ns, cudaMemcpyDeviceToDevice, p->stream));
+    if (u) CK(cudaMemcpyAsync(u + off * mi.g[0].ns, x, sizeof(double) * B * mi.g[0].ns, cudaMemcpyDeviceToDevice, p->stream));
     if (ensure_pin(p, sizeof(int32_t) * B) != MLMC_OK) return MLMC_ERR_OOM;
-    CK(cudaMemcpyAsync(p->h_pin, w.sc.iters, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaMemcpyAsync(p->h_pin, it_dev, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, p->stream));
     CK(cudaStreamSynchronize(p->stream));
     const int32_t* it = (const int32_t*)p->h_pin;
     for (int64_t b = 0; b < B; ++b) bad |= (it[b] < 0);
@@ -733,32 +889,36 @@ mlmc_status mlmc_sample_level(mlmc_plan p, int level, int64_t first, int64_t cou
   if (count == 0) return MLMC_OK;
   const MeshInfo& mf = p->meshes[level];
   const int M = p->M;
-  const int64_t Bmax = max_batch(p, [&](int64_t B) { return coupled_bytes(mf, M, B); }, count);
+  const bool mixed = is_mixed(p);
+  const int64_t Bmax = max_batch(p, [&](int64_t B) { return coupled_bytes(mf, M, B, mixed); }, count);
   const double cost = level_cost_cfg(&p->cfg, level);
   bool bad = false;
   for (int64_t off = 0; off < count; off += Bmax) {
     const int64_t B = std::min<int64_t>(Bmax, count - off);
-    mlmc_status st = ensure_ws(p, coupled_bytes(mf, M, B));
+    mlmc_status st = ensure_ws(p, coupled_bytes(mf, M, B, mixed));
     if (st != MLMC_OK) return st;
-    Carve c(p->ws);
-    CoupledWs w;
-    carve_coupled(c, mf, M, B, w);
-    st = mlmc_draw_xi(p, level, first + off, B, w.xi);
-    if (st != MLMC_OK) return st;
-    st = make_kappa(p, level, w.xi, B, w.s.kap[0]);
-    if (st != MLMC_OK) return st;
-    st = solve_batch(p, mf, w.s, B, w.qf, w.itf);
-    if (st != MLMC_OK) return st;
-    if (level > 0) {
-      const MeshInfo& mc = p->meshes[level - 1];
-      Carve cc(p->ws);
-      CoupledWs wc;
-      carve_coupled(cc, mc, M, B, wc);   // same xi / qf / qc offsets (prefix is identical)
-      st = make_kappa(p, level - 1, w.xi, B, wc.s.kap[0]);
+    for (int side = 0; side < (level > 0 ? 2 : 1); ++side) {
+      // side 0: mesh `level` (fine), side 1: mesh `level - 1` (coarse); the
+      // carve prefix (xi, q_f, q_c, iteration counts) is identical for both.
+      const int mesh = level - side;
+      const MeshInfo& mi = p->meshes[mesh];
+      Carve c(p->ws);
+      CoupledWs w;
+      carve_coupled(c, mi, M, B, mixed, w);
+      if (side == 0) {
+        st = mlmc_draw_xi(p, level, first + off, B, w.xi);
+        if (st != MLMC_OK) return st;
+      }
+      st = make_kappa(p, mesh, w.xi, B, w.kap);
       if (st != MLMC_OK) return st;
-      st = solve_batch(p, mc, wc.s, B, w.qc, w.itc);
+      double* qd = side == 0 ? w.qf : w.qc;
+      int32_t* itd = side == 0 ? w.itf : w.itc;
+      st = mixed ? solve_mixed(p, mi, w.mx, B, qd, itd) : solve_fp64(p, mi, w.s, B, qd, itd);
       if (st != MLMC_OK) return st;
     }
+    Carve c(p->ws);
+    CoupledWs w;
+    carve_coupled(c, mf, M, B, mixed, w);
     CK(run(p, KID_WELFORD, [&] {
       return launch_welford(p->stream, w.qf, level > 0 ? w.qc : nullptr, B, p->d_states + level, cost);
     }));

@@ -69,7 +69,7 @@ __global__ void k_count_active(const int32_t* __restrict__ active, int64_t B, in
   if (threadIdx.x == 0) *count = s;
 }
 
-__global__ void k_scalars_init(Scalars sc, double tol, int64_t B) {
+__global__ void k_scalars_init(Scalars sc, double tol, double scale0, int64_t B) {
   const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
   sc.tol[b] = tol;
@@ -78,6 +78,50 @@ __global__ void k_scalars_init(Scalars sc, double tol, int64_t B) {
   sc.beta[b] = 0.0;
   sc.alpha[b] = 0.0;
   sc.gamma[b] = 0.0;
+  if (sc.total) sc.total[b] = 0;
+  if (sc.scale) sc.scale[b] = scale0;
+}
+
+__global__ void k_outer_step(const double* __restrict__ part, int64_t tiles, Scalars so,
+                             const int32_t* __restrict__ inner_iters, int inner_max, int outer_it,
+                             int outer_max, int64_t B) {
+  const int64_t b = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (b >= B || !so.active[b]) return;
+  const double* p = part + b * tiles;
+  double v = 0.0;
+  for (int64_t t = lane; t < tiles; t += 32) v += p[t];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (lane != 0) return;
+  const double rho = sqrt(v);
+  so.rho[b] = rho;
+  int32_t tot = so.total[b];
+  if (inner_iters) {
+    const int32_t it = inner_iters[b];
+    tot += (it > 0) ? it : inner_max;
+  }
+  so.total[b] = tot;
+  if (rho <= so.tol[b]) {
+    so.active[b] = 0;
+    so.iters[b] = tot;
+  } else if (outer_it >= outer_max || !(rho == rho)) {
+    so.active[b] = 0;
+    so.iters[b] = -1;
+  } else {
+    so.scale[b] = rho;
+  }
+}
+
+__global__ void k_inner_init(Scalars si, Scalars so, double tol, int64_t B) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  si.active[b] = so.active[b];
+  si.tol[b] = tol;
+  si.iters[b] = 0;
+  si.beta[b] = 0.0;
+  si.alpha[b] = 0.0;
+  si.gamma[b] = 0.0;
 }
 
 __global__ void k_welford(const double* __restrict__ qf, const double* __restrict__ qc, int64_t B,
@@ -141,8 +185,24 @@ cudaError_t launch_count_active(cudaStream_t s, const int32_t* active, int64_t B
   return cudaGetLastError();
 }
 
-cudaError_t launch_scalars_init(cudaStream_t s, const Scalars& sc, double tol, int64_t B) {
-  k_scalars_init<<<(unsigned)((B + 255) / 256), 256, 0, s>>>(sc, tol, B);
+cudaError_t launch_scalars_init(cudaStream_t s, const Scalars& sc, double tol, double scale0,
+                                int64_t B) {
+  k_scalars_init<<<(unsigned)((B + 255) / 256), 256, 0, s>>>(sc, tol, scale0, B);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_outer_step(cudaStream_t s, const double* part, int64_t tiles,
+                              const Scalars& outer, const int32_t* inner_iters, int inner_max,
+                              int outer_it, int outer_max, int64_t B) {
+  const int warps = 8;
+  k_outer_step<<<(unsigned)((B + warps - 1) / warps), warps * 32, 0, s>>>(
+      part, tiles, outer, inner_iters, inner_max, outer_it, outer_max, B);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inner_init(cudaStream_t s, const Scalars& inner, const Scalars& outer,
+                              double tol, int64_t B) {
+  k_inner_init<<<(unsigned)((B + 255) / 256), 256, 0, s>>>(inner, outer, tol, B);
   return cudaGetLastError();
 }
 

@@ -1,459 +1,755 @@
 // 2D matrix-free Q1 operator, batched PCG vector kernels and geometric
-// multigrid kernels (FP64).
+// multigrid kernels, templated on the value type (double: the FP64 form and
+// the FP64 residual of the mixed form; float: the FP32 inner solve).
 //
 // Operator (Eq. (model), Sec. 2.1, Q1 on a uniform grid, kappa constant per
 // element, homogeneous Dirichlet): at an interior node c with surrounding
 // elements SW, SE, NW, NE (kappa values kSW..kNE) the row of A is
-//   diagonal          2/3 (kSW + kSE + kNW + kNE)
-//   edge neighbours  -1/6 (sum of kappa of the two elements sharing the edge)
+//   diagonal           2/3 (kSW + kSE + kNW + kNE)
+//   edge neighbours   -1/6 (sum of kappa of the two elements sharing the edge)
 //   corner neighbours -1/3 kappa of the one element shared.
-// Node arrays carry the boundary nodes (always 0), so no neighbour needs a
-// bounds test. One thread per node, CTA tiles of 32 x 8 nodes; per-sample
-// reductions go to one partial per (sample, tile), summed in a fixed order.
+//
+// Stencil kernels stream: each warp owns a strip of 32 node columns (30
+// outputs; the two edge lanes only supply neighbours) and walks down SROWS
+// rows, keeping a 3-row window of the field and a 2-row window of kappa in
+// registers; x-neighbours come from warp shuffles. The field the stencil
+// acts on (p = z + beta p_old, e = W b, e + P e_c, ...) is formed once per
+// node as its row enters the window, and the next row is fetched before the
+// current one is consumed. No shared memory, no barriers.
+//
+// Pointwise kernels treat each sample's node array as a flat vector
+// (boundary entries are 0 and stay 0) with 16-byte vector accesses.
+//
+// Node arrays carry the boundary nodes (always 0). Per-sample reductions
+// write one FP64 partial per warp (stencil kernels, g.tiles_s per sample)
+// or per CTA (flat kernels, g.tiles_f per sample), summed in a fixed order
+// by k_finalize.
 #include "mlmc_internal.cuh"
 
 namespace mlmc {
 namespace {
 
-constexpr double C23 = 2.0 / 3.0;
-constexpr double C16 = 1.0 / 6.0;
-constexpr double C13 = 1.0 / 3.0;
-
-struct Node2 {
-  int i, j;        // node coordinates in 0..n
-  bool valid;      // inside the (n+1)^2 node grid
-  bool interior;
-  int64_t idx;     // j * (n + 1) + i
+template <class T>
+struct Consts {
+  static constexpr T c23 = T(2) / T(3);
+  static constexpr T c16 = T(1) / T(6);
+  static constexpr T c13 = T(1) / T(3);
 };
 
-__device__ __forceinline__ Node2 node2(int n, int tiles_x) {
-  Node2 q;
-  const int t = blockIdx.x;
-  const int ty = t / tiles_x;
-  const int tx = t - ty * tiles_x;
-  q.i = tx * TX2 + threadIdx.x;
-  q.j = ty * TY2 + threadIdx.y;
-  q.valid = (q.i <= n) && (q.j <= n);
-  q.interior = (q.i > 0) && (q.i < n) && (q.j > 0) && (q.j < n);
-  q.idx = (int64_t)q.j * (n + 1) + q.i;
-  return q;
+__device__ __forceinline__ bool interior2(int n, int i, int j) {
+  return i > 0 && i < n && j > 0 && j < n;
 }
 
-// Sum over the 256 threads of the CTA; result valid in thread (0, 0).
-__device__ __forceinline__ double block_sum(double v) {
-  __shared__ double s_w[TY2];
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  if (threadIdx.x == 0) s_w[threadIdx.y] = v;
-  __syncthreads();
-  double r = 0.0;
-  if (threadIdx.x == 0 && threadIdx.y == 0) {
-#pragma unroll
-    for (int w = 0; w < TY2; ++w) r += s_w[w];
-  }
-  return r;
+  return v;
+}
+
+// ------------------------------------------------------------ warp strips
+
+struct Strip {
+  int n;        // cells per side
+  int N1;       // nodes per row
+  int c;        // node column of this lane (may be -1 or > n)
+  bool out;     // this lane produces outputs (lanes 1..30, column <= n)
+  int y0, y1;   // output rows [y0, y1)
+  int64_t part_idx;
+};
+
+__device__ __forceinline__ Strip strip_of(const Grid& g) {
+  Strip s;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int strip = blockIdx.x * SWARPS + warp;
+  s.n = g.n;
+  s.N1 = g.n + 1;
+  s.c = strip * 30 - 1 + lane;
+  s.out = (lane >= 1) && (lane <= 30) && (s.c <= g.n);
+  s.y0 = blockIdx.y * SROWS;
+  s.y1 = min(s.y0 + SROWS, g.n + 1);
+  s.part_idx = (int64_t)blockIdx.z * g.tiles_s + ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * SWARPS + warp;
+  return s;
+}
+
+__device__ __forceinline__ bool first_thread() {
+  return blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0;
 }
 
 __device__ __forceinline__ void prof_tick(const Prof& p) {
-  if (p.acc && blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) atomicAdd(p.acc, p.per_sample);
+  if (p.acc && first_thread()) atomicAdd(p.acc, p.per_sample);
 }
 
-// kappa of the four elements around interior node (i, j)
-struct K4 {
-  double sw, se, nw, ne;
+// kappa of element (e, r) of one sample, 0 outside the grid.
+template <class T>
+__device__ __forceinline__ T kap_at(const T* __restrict__ k, int n, int e, int r) {
+  return (e >= 0 && e < n && r >= 0 && r < n) ? __ldg(k + (int64_t)r * n + e) : T(0);
+}
+
+// Field rows j-1, j, j+1 at columns c-1, c, c+1 and kappa of the elements
+// (c-1, j-1), (c, j-1), (c-1, j), (c, j) around node (c, j).
+template <class T>
+struct Win {
+  T vm, v0, vp;
+  T lm, l0, lp;
+  T rm, r0, rp;
+  T ka, kb, kal, kbl;
 };
-__device__ __forceinline__ K4 load_k4(const double* __restrict__ K, int n, int i, int j) {
-  K4 k;
-  const double* r0 = K + (int64_t)(j - 1) * n + (i - 1);
-  k.sw = __ldg(r0);
-  k.se = __ldg(r0 + 1);
-  k.nw = __ldg(r0 + n);
-  k.ne = __ldg(r0 + n + 1);
-  return k;
+
+template <class T>
+__device__ __forceinline__ T stencil_win(const Win<T>& w) {
+  const T ksw = w.kal, kse = w.ka, knw = w.kbl, kne = w.kb;
+  const T kS = ksw + kse, kN = knw + kne, kW = ksw + knw, kE = kse + kne;
+  const T edge = kE * w.r0 + kW * w.l0 + kN * w.vp + kS * w.vm;
+  const T corner = kne * w.rp + knw * w.lp + kse * w.rm + ksw * w.lm;
+  return Consts<T>::c23 * (kS + kN) * w.v0 - Consts<T>::c16 * edge - Consts<T>::c13 * corner;
 }
 
-__device__ __forceinline__ double diag2(const K4& k) { return C23 * ((k.sw + k.se) + (k.nw + k.ne)); }
-
-// (A v)(c) from the 3x3 values v[dj+1][di+1] around c.
-__device__ __forceinline__ double stencil2(const K4& k, const double v[3][3]) {
-  const double edge = (k.se + k.ne) * v[1][2] + (k.sw + k.nw) * v[1][0] +
-                      (k.nw + k.ne) * v[2][1] + (k.sw + k.se) * v[0][1];
-  const double corner = k.ne * v[2][2] + k.nw * v[2][0] + k.se * v[0][2] + k.sw * v[0][0];
-  return diag2(k) * v[1][1] - C16 * edge - C13 * corner;
-}
-
-__device__ __forceinline__ void load9(const double* __restrict__ X, int n, int64_t idx,
-                                      double v[3][3]) {
-  const int N1 = n + 1;
-#pragma unroll
-  for (int dj = -1; dj <= 1; ++dj)
-#pragma unroll
-    for (int di = -1; di <= 1; ++di) v[dj + 1][di + 1] = __ldg(X + idx + dj * N1 + di);
-}
-
-__global__ void __launch_bounds__(256) k_apply2d(int n, int tiles_x, int64_t ns, int64_t es,
-                                                 const double* __restrict__ K,
-                                                 const double* __restrict__ X,
-                                                 double* __restrict__ Y, Prof prof) {
-  const int b = blockIdx.y;
-  const Node2 q = node2(n, tiles_x);
-  if (!q.valid) return;
-  K += (int64_t)b * es;
-  X += (int64_t)b * ns;
-  double y = 0.0;
-  if (q.interior) {
-    double v[3][3];
-    load9(X, n, q.idx, v);
-    y = stencil2(load_k4(K, n, q.i, q.j), v);
-  }
-  Y[(int64_t)b * ns + q.idx] = y;
-  prof_tick(prof);
-}
-
-// W = omega / D at interior nodes, 0 on the boundary.
-__global__ void __launch_bounds__(256) k_winv2d(int n, int tiles_x, int64_t ns, int64_t es,
-                                                const double* __restrict__ K, double omega,
-                                                double* __restrict__ W) {
-  const int b = blockIdx.y;
-  const Node2 q = node2(n, tiles_x);
-  if (!q.valid) return;
-  double w = 0.0;
-  if (q.interior) w = omega / diag2(load_k4(K + (int64_t)b * es, n, q.i, q.j));
-  W[(int64_t)b * ns + q.idx] = w;
-}
-
-__global__ void __launch_bounds__(256) k_pcg_init2d(int n, int tiles_x, int64_t ns, double h2,
-                                                    double* __restrict__ X,
-                                                    double* __restrict__ R, Prof prof) {
-  const int b = blockIdx.y;
-  const Node2 q = node2(n, tiles_x);
-  if (!q.valid) return;
-  X[(int64_t)b * ns + q.idx] = 0.0;
-  R[(int64_t)b * ns + q.idx] = q.interior ? h2 : 0.0;
-  prof_tick(prof);
-}
-
-// p_new = z + beta p_old (beta == 0: p_new = z), q = A p_new, partial p.q
-__global__ void __launch_bounds__(256) k_pq2d(int n, int tiles_x, int64_t ns, int64_t es,
-                                              const double* __restrict__ K,
-                                              const double* __restrict__ Z,
-                                              const double* __restrict__ Pold,
-                                              double* __restrict__ Pnew, double* __restrict__ Q,
-                                              const double* __restrict__ beta,
-                                              const int32_t* __restrict__ active,
-                                              double* __restrict__ part, Prof prof) {
-  const int b = blockIdx.y;
-  if (!active[b]) return;
-  const Node2 q = node2(n, tiles_x);
-  const double bb = beta[b];
-  const int64_t off = (int64_t)b * ns;
-  double dot = 0.0;
-  if (q.valid) {
-    double pv = 0.0, qv = 0.0;
-    if (q.interior) {
-      const int N1 = n + 1;
-      double v[3][3];
-#pragma unroll
-      for (int dj = -1; dj <= 1; ++dj)
-#pragma unroll
-        for (int di = -1; di <= 1; ++di) {
-          const int64_t o = off + q.idx + dj * N1 + di;
-          const double zz = __ldg(Z + o);
-          v[dj + 1][di + 1] = (bb == 0.0) ? zz : fma(bb, __ldg(Pold + o), zz);
-        }
-      pv = v[1][1];
-      qv = stencil2(load_k4(K + (int64_t)b * es, n, q.i, q.j), v);
-      dot = pv * qv;
+// Streams one warp strip. field(c, j) is the stencilled field at an interior
+// node; out(j, w) runs for each output row j of an output lane with the
+// window centred on (c, j). Every lane executes the loads and shuffles.
+template <class T, class FieldF, class OutF>
+__device__ __forceinline__ void stream_strip(const Strip& s, const T* __restrict__ kap,
+                                             FieldF&& field, OutF&& out) {
+  const int n = s.n;
+  auto fld = [&](int j) -> T { return interior2(n, s.c, j) ? field(s.c, j) : T(0); };
+  Win<T> w;
+  w.v0 = fld(s.y0 - 1);
+  w.vp = fld(s.y0);
+  w.l0 = __shfl_up_sync(0xffffffffu, w.v0, 1);
+  w.r0 = __shfl_down_sync(0xffffffffu, w.v0, 1);
+  w.lp = __shfl_up_sync(0xffffffffu, w.vp, 1);
+  w.rp = __shfl_down_sync(0xffffffffu, w.vp, 1);
+  w.kb = kap_at(kap, n, s.c, s.y0 - 1);
+  w.kbl = __shfl_up_sync(0xffffffffu, w.kb, 1);
+  T vn = fld(s.y0 + 1);
+  T kn = kap_at(kap, n, s.c, s.y0);
+  for (int j = s.y0; j < s.y1; ++j) {
+    w.vm = w.v0; w.lm = w.l0; w.rm = w.r0;
+    w.v0 = w.vp; w.l0 = w.lp; w.r0 = w.rp;
+    w.vp = vn;
+    w.lp = __shfl_up_sync(0xffffffffu, vn, 1);
+    w.rp = __shfl_down_sync(0xffffffffu, vn, 1);
+    w.ka = w.kb; w.kal = w.kbl;
+    w.kb = kn;
+    w.kbl = __shfl_up_sync(0xffffffffu, kn, 1);
+    if (j + 1 < s.y1) {          // fetch the next rows before consuming this one
+      vn = fld(j + 2);
+      kn = kap_at(kap, n, s.c, j + 1);
     }
-    Pnew[off + q.idx] = pv;
-    Q[off + q.idx] = qv;
+    if (s.out) out(j, w);
   }
-  dot = block_sum(dot);
-  if (threadIdx.x == 0 && threadIdx.y == 0) part[(int64_t)b * gridDim.x + blockIdx.x] = dot;
+}
+
+// This warp's partial: per-lane sums (in T) are added across the warp in FP64.
+template <class T>
+__device__ __forceinline__ void warp_partial(T v, double* __restrict__ part, int64_t idx) {
+  const double d = warp_sum((double)v);
+  if ((threadIdx.x & 31) == 0) part[idx] = d;
+}
+
+inline dim3 sgrid(const Grid& g, int64_t B) { return dim3((unsigned)g.sx, (unsigned)g.sy, (unsigned)B); }
+constexpr int SBLOCK = SWARPS * 32;
+
+template <class T>
+__global__ void __launch_bounds__(SBLOCK) k_apply2(Grid g, const T* __restrict__ K,
+                                                   const T* __restrict__ X, T* __restrict__ Y,
+                                                   Prof prof) {
+  const Strip s = strip_of(g);
+  const int64_t b = blockIdx.z;
+  const T* x = X + b * g.ns;
+  T* y = Y + b * g.ns;
+  stream_strip<T>(s, K + b * g.es,
+                  [&](int c, int j) { return __ldg(x + (int64_t)j * s.N1 + c); },
+                  [&](int j, const Win<T>& w) {
+                    y[(int64_t)j * s.N1 + s.c] = interior2(s.n, s.c, j) ? stencil_win(w) : T(0);
+                  });
   prof_tick(prof);
 }
 
-// x += alpha p, r -= alpha q, partial r.r
-__global__ void __launch_bounds__(256) k_xr2d(int n, int tiles_x, int64_t ns,
-                                              double* __restrict__ X,
-                                              const double* __restrict__ P,
-                                              double* __restrict__ R,
-                                              const double* __restrict__ Q,
-                                              const double* __restrict__ alpha,
-                                              const int32_t* __restrict__ active,
-                                              double* __restrict__ part, Prof prof) {
-  const int b = blockIdx.y;
+// p_new = z + beta p_old (beta == 0: p_new = z), q = A p_new, partials of p.q
+template <class T>
+__global__ void __launch_bounds__(SBLOCK) k_pq2(Grid g, const T* __restrict__ K,
+                                                const T* __restrict__ Z, const T* __restrict__ Pold,
+                                                T* __restrict__ Pnew, T* __restrict__ Q,
+                                                const double* __restrict__ beta,
+                                                const int32_t* __restrict__ active,
+                                                double* __restrict__ part, Prof prof) {
+  const int64_t b = blockIdx.z;
   if (!active[b]) return;
-  const Node2 q = node2(n, tiles_x);
-  const double a = alpha[b];
-  double dot = 0.0;
-  if (q.valid) {
-    const int64_t o = (int64_t)b * ns + q.idx;
-    const double xv = fma(a, P[o], X[o]);
-    const double rv = fma(-a, Q[o], R[o]);
-    X[o] = xv;
-    R[o] = rv;
-    dot = rv * rv;
+  const Strip s = strip_of(g);
+  const T bb = (T)beta[b];
+  const T* z = Z + b * g.ns;
+  const T* po = Pold + b * g.ns;
+  T* pn = Pnew + b * g.ns;
+  T* q = Q + b * g.ns;
+  T dot = T(0);
+  auto out = [&](int j, const Win<T>& w) {
+    const int64_t o = (int64_t)j * s.N1 + s.c;
+    T qv = T(0);
+    if (interior2(s.n, s.c, j)) {
+      qv = stencil_win(w);
+      dot = fma(w.v0, qv, dot);
+    }
+    pn[o] = w.v0;
+    q[o] = qv;
+  };
+  if (bb == T(0)) {
+    stream_strip<T>(s, K + b * g.es, [&](int c, int j) { return __ldg(z + (int64_t)j * s.N1 + c); }, out);
+  } else {
+    stream_strip<T>(s, K + b * g.es, [&](int c, int j) {
+      const int64_t o = (int64_t)j * s.N1 + c;
+      return fma(bb, __ldg(po + o), __ldg(z + o));
+    }, out);
   }
-  dot = block_sum(dot);
-  if (threadIdx.x == 0 && threadIdx.y == 0) part[(int64_t)b * gridDim.x + blockIdx.x] = dot;
-  prof_tick(prof);
-}
-
-// z = Dinv r, partial r.z
-__global__ void __launch_bounds__(256) k_jz2d(int n, int tiles_x, int64_t ns,
-                                              const double* __restrict__ Winv,
-                                              const double* __restrict__ R,
-                                              double* __restrict__ Z,
-                                              const int32_t* __restrict__ active,
-                                              double* __restrict__ part, Prof prof) {
-  const int b = blockIdx.y;
-  if (!active[b]) return;
-  const Node2 q = node2(n, tiles_x);
-  double dot = 0.0;
-  if (q.valid) {
-    const int64_t o = (int64_t)b * ns + q.idx;
-    const double rv = R[o];
-    const double zv = Winv[o] * rv;
-    Z[o] = zv;
-    dot = rv * zv;
-  }
-  dot = block_sum(dot);
-  if (threadIdx.x == 0 && threadIdx.y == 0) part[(int64_t)b * gridDim.x + blockIdx.x] = dot;
+  warp_partial(dot, part, s.part_idx);
   prof_tick(prof);
 }
 
 // Pre-smoothing from zero and residual: e = W b, r1 = b - A e.
-__global__ void __launch_bounds__(256) k_mgpre2d(int n, int tiles_x, int64_t ns, int64_t es,
-                                                 const double* __restrict__ K,
-                                                 const double* __restrict__ W,
-                                                 const double* __restrict__ Bv,
-                                                 double* __restrict__ E,
-                                                 double* __restrict__ R1,
-                                                 const int32_t* __restrict__ active, Prof prof) {
-  const int b = blockIdx.y;
+template <class T>
+__global__ void __launch_bounds__(SBLOCK) k_mgpre2(Grid g, const T* __restrict__ K,
+                                                   const T* __restrict__ W,
+                                                   const T* __restrict__ Bv, T* __restrict__ E,
+                                                   T* __restrict__ R1,
+                                                   const int32_t* __restrict__ active, Prof prof) {
+  const int64_t b = blockIdx.z;
   if (!active[b]) return;
-  const Node2 q = node2(n, tiles_x);
-  if (!q.valid) return;
-  const int64_t off = (int64_t)b * ns;
-  double ev = 0.0, rv = 0.0;
-  if (q.interior) {
-    const int N1 = n + 1;
-    double v[3][3];
-#pragma unroll
-    for (int dj = -1; dj <= 1; ++dj)
-#pragma unroll
-      for (int di = -1; di <= 1; ++di) {
-        const int64_t o = off + q.idx + dj * N1 + di;
-        v[dj + 1][di + 1] = __ldg(W + o) * __ldg(Bv + o);   // W = 0 on the boundary
-      }
-    ev = v[1][1];
-    rv = __ldg(Bv + off + q.idx) - stencil2(load_k4(K + (int64_t)b * es, n, q.i, q.j), v);
-  }
-  E[off + q.idx] = ev;
-  R1[off + q.idx] = rv;
+  const Strip s = strip_of(g);
+  const T* w_ = W + b * g.ns;
+  const T* bv = Bv + b * g.ns;
+  T* e = E + b * g.ns;
+  T* r1 = R1 + b * g.ns;
+  stream_strip<T>(s, K + b * g.es,
+                  [&](int c, int j) {
+                    const int64_t o = (int64_t)j * s.N1 + c;
+                    return __ldg(w_ + o) * __ldg(bv + o);
+                  },
+                  [&](int j, const Win<T>& w) {
+                    const int64_t o = (int64_t)j * s.N1 + s.c;
+                    T ev = T(0), rv = T(0);
+                    if (interior2(s.n, s.c, j)) {
+                      ev = w.v0;
+                      rv = __ldg(bv + o) - stencil_win(w);
+                    }
+                    e[o] = ev;
+                    r1[o] = rv;
+                  });
   prof_tick(prof);
-}
-
-// Full-weighting restriction (transpose of bilinear prolongation):
-// bc(I, J) = sum_{di,dj in -1..1} w(di) w(dj) r1(2I + di, 2J + dj), w(0) = 1, w(+-1) = 1/2.
-__global__ void __launch_bounds__(256) k_restrict2d(int nc, int tiles_x, int64_t nsf,
-                                                    int64_t nsc,
-                                                    const double* __restrict__ R1,
-                                                    double* __restrict__ Bc,
-                                                    const int32_t* __restrict__ active,
-                                                    Prof prof) {
-  const int b = blockIdx.y;
-  if (!active[b]) return;
-  const Node2 q = node2(nc, tiles_x);
-  if (!q.valid) return;
-  double v = 0.0;
-  if (q.interior) {
-    const int nf = 2 * nc;
-    const int N1 = nf + 1;
-    const double* r = R1 + (int64_t)b * nsf + (int64_t)(2 * q.j) * N1 + 2 * q.i;
-    const double rows0 = 0.5 * __ldg(r - N1 - 1) + __ldg(r - N1) + 0.5 * __ldg(r - N1 + 1);
-    const double rows1 = 0.5 * __ldg(r - 1) + __ldg(r) + 0.5 * __ldg(r + 1);
-    const double rows2 = 0.5 * __ldg(r + N1 - 1) + __ldg(r + N1) + 0.5 * __ldg(r + N1 + 1);
-    v = 0.5 * (rows0 + rows2) + rows1;
-  }
-  Bc[(int64_t)b * nsc + q.idx] = v;
-  prof_tick(prof);
-}
-
-// Coarsest grid (n = 2, one unknown): e = b / D exactly.
-__global__ void k_coarse2d(int64_t ns, int64_t es, const double* __restrict__ K,
-                           const double* __restrict__ Bv, double* __restrict__ E,
-                           const int32_t* __restrict__ active, int64_t B) {
-  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= B || !active[b]) return;
-  const int64_t off = b * ns;
-  const double* k = K + b * es;
-  const double d = C23 * ((k[0] + k[1]) + (k[2] + k[3]));
-  for (int t = 0; t < 9; ++t) E[off + t] = 0.0;
-  E[off + 4] = Bv[off + 4] / d;
 }
 
 // Bilinear prolongation of the coarse correction at fine node (i, j).
-__device__ __forceinline__ double prolong2(const double* __restrict__ Ec, int nc, int i, int j) {
+template <class T>
+__device__ __forceinline__ T prolong2(const T* __restrict__ Ec, int nc, int i, int j) {
   const int N1c = nc + 1;
-  const int I = i >> 1, J = j >> 1;
-  const double* e = Ec + (int64_t)J * N1c + I;
+  const T* e = Ec + (int64_t)(j >> 1) * N1c + (i >> 1);
   const bool ox = i & 1, oy = j & 1;
-  double v0 = __ldg(e);
-  if (ox) v0 = 0.5 * (v0 + __ldg(e + 1));
+  T v0 = __ldg(e);
+  if (ox) v0 = T(0.5) * (v0 + __ldg(e + 1));
   if (!oy) return v0;
-  double v1 = __ldg(e + N1c);
-  if (ox) v1 = 0.5 * (v1 + __ldg(e + N1c + 1));
-  return 0.5 * (v0 + v1);
+  T v1 = __ldg(e + N1c);
+  if (ox) v1 = T(0.5) * (v1 + __ldg(e + N1c + 1));
+  return T(0.5) * (v0 + v1);
 }
 
-// out = e' + W (b - A e'), e' = e + P ec; partial b.out when part != nullptr.
-__global__ void __launch_bounds__(256) k_mgpost2d(int n, int tiles_x, int64_t ns, int64_t es,
-                                                  int64_t nsc, const double* __restrict__ K,
-                                                  const double* __restrict__ W,
-                                                  const double* __restrict__ Bv,
-                                                  const double* __restrict__ E,
-                                                  const double* __restrict__ Ec,
-                                                  double* __restrict__ Out,
-                                                  const int32_t* __restrict__ active,
-                                                  double* __restrict__ part, Prof prof) {
-  const int b = blockIdx.y;
+// out = e' + W (b - A e'), e' = e + P ec; partials of b.out when part != nullptr.
+template <class T>
+__global__ void __launch_bounds__(SBLOCK) k_mgpost2(Grid g, int64_t nsc, const T* __restrict__ K,
+                                                    const T* __restrict__ W,
+                                                    const T* __restrict__ Bv,
+                                                    const T* __restrict__ E,
+                                                    const T* __restrict__ Ec, T* __restrict__ Out,
+                                                    const int32_t* __restrict__ active,
+                                                    double* __restrict__ part, Prof prof) {
+  const int64_t b = blockIdx.z;
   if (!active[b]) return;
-  const Node2 q = node2(n, tiles_x);
-  const int64_t off = (int64_t)b * ns;
-  const int nc = n / 2;
-  const double* ec = Ec + (int64_t)b * nsc;
-  double dot = 0.0;
-  if (q.valid) {
-    double ov = 0.0;
-    if (q.interior) {
-      const int N1 = n + 1;
-      double v[3][3];
-#pragma unroll
-      for (int dj = -1; dj <= 1; ++dj)
-#pragma unroll
-        for (int di = -1; di <= 1; ++di)
-          v[dj + 1][di + 1] =
-              __ldg(E + off + q.idx + dj * N1 + di) + prolong2(ec, nc, q.i + di, q.j + dj);
-      const double bv = __ldg(Bv + off + q.idx);
-      const double av = stencil2(load_k4(K + (int64_t)b * es, n, q.i, q.j), v);
-      ov = fma(__ldg(W + off + q.idx), bv - av, v[1][1]);
-      dot = bv * ov;
-    }
-    Out[off + q.idx] = ov;
-  }
-  if (part) {
-    dot = block_sum(dot);
-    if (threadIdx.x == 0 && threadIdx.y == 0) part[(int64_t)b * gridDim.x + blockIdx.x] = dot;
-  }
+  const Strip s = strip_of(g);
+  const int nc = g.n / 2;
+  const T* ec = Ec + b * nsc;
+  const T* e = E + b * g.ns;
+  const T* w_ = W + b * g.ns;
+  const T* bv = Bv + b * g.ns;
+  T* out = Out + b * g.ns;
+  T dot = T(0);
+  stream_strip<T>(s, K + b * g.es,
+                  [&](int c, int j) {
+                    return __ldg(e + (int64_t)j * s.N1 + c) + prolong2(ec, nc, c, j);
+                  },
+                  [&](int j, const Win<T>& w) {
+                    const int64_t o = (int64_t)j * s.N1 + s.c;
+                    T ov = T(0);
+                    if (interior2(s.n, s.c, j)) {
+                      const T bval = __ldg(bv + o);
+                      ov = fma(__ldg(w_ + o), bval - stencil_win(w), w.v0);
+                      dot = fma(bval, ov, dot);
+                    }
+                    out[o] = ov;
+                  });
+  if (part) warp_partial(dot, part, s.part_idx);
   prof_tick(prof);
 }
 
-// Per-tile partial sums of w_i x_i for the QoI weights (exact Q1 integral
-// mean): domain: w = h^2 at interior nodes; box [lo, hi]^2 (node indices
-// L, H): w = h^2 chi_x chi_y / |box|, chi = 1 strictly inside, 1/2 on a face.
-__global__ void __launch_bounds__(256) k_qoi2d(int n, int tiles_x, int64_t ns, double h2,
-                                               int box, int L, int H, double inv_vol,
-                                               const double* __restrict__ X,
-                                               double* __restrict__ part, Prof prof) {
-  const int b = blockIdx.y;
-  const Node2 q = node2(n, tiles_x);
+// Mixed form, outer FP64 residual: r = b - A(kappa) u (b_i = h^2), partials of r.r.
+__global__ void __launch_bounds__(SBLOCK) k_resid2(Grid g, const double* __restrict__ K,
+                                                   const double* __restrict__ U,
+                                                   double* __restrict__ R,
+                                                   const int32_t* __restrict__ active,
+                                                   double* __restrict__ part, Prof prof) {
+  const int64_t b = blockIdx.z;
+  if (!active[b]) return;
+  const Strip s = strip_of(g);
+  const double h2 = g.h * g.h;
+  const double* u = U + b * g.ns;
+  double* r = R + b * g.ns;
+  double dot = 0.0;
+  stream_strip<double>(s, K + b * g.es,
+                       [&](int c, int j) { return __ldg(u + (int64_t)j * s.N1 + c); },
+                       [&](int j, const Win<double>& w) {
+                         double rv = 0.0;
+                         if (interior2(s.n, s.c, j)) {
+                           rv = h2 - stencil_win(w);
+                           dot = fma(rv, rv, dot);
+                         }
+                         r[(int64_t)j * s.N1 + s.c] = rv;
+                       });
+  warp_partial(dot, part, s.part_idx);
+  prof_tick(prof);
+}
+
+// ------------------------------------------------------------ flat kernels
+
+template <class T>
+struct Vec;
+template <>
+struct Vec<float> {
+  using V = float4;
+  static constexpr int L = 4;
+};
+template <>
+struct Vec<double> {
+  using V = double2;
+  static constexpr int L = 2;
+};
+
+// 16-byte vector viewed as an array of lanes (kept in registers).
+template <class T>
+union Pack {
+  typename Vec<T>::V v;
+  T a[Vec<T>::L];
+};
+
+// CTA-wide sum of per-thread partials into part[b * tiles_f + blockIdx.x].
+__device__ __forceinline__ void cta_partial(double v, double* __restrict__ part, int64_t tiles_f) {
+  __shared__ double s_w[FLAT_THREADS / 32];
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+#pragma unroll
+    for (int w = 0; w < FLAT_THREADS / 32; ++w) r += s_w[w];
+    part[(int64_t)blockIdx.y * tiles_f + blockIdx.x] = r;
+  }
+}
+
+inline dim3 fgrid(const Grid& g, int64_t B) { return dim3((unsigned)g.fx, (unsigned)B, 1); }
+
+// Nodes of one sample: (n+1)^d. Entries between that and the sample stride
+// are padding that no kernel reads or writes.
+__device__ __forceinline__ int64_t nodes_of(const Grid& g) {
+  const int64_t N1 = g.n + 1;
+  return g.dim == 2 ? N1 * N1 : N1 * N1 * N1;
+}
+
+// Range of whole 16-byte vectors of this CTA within one sample's nodes, and
+// the scalar tail [tail0, nn) that the last CTA handles element by element.
+template <class T>
+__device__ __forceinline__ void flat_range(const Grid& g, int64_t& v0, int64_t& v1, int64_t& tail0,
+                                           int64_t& nn) {
+  nn = nodes_of(g);
+  const int64_t nv = nn / Vec<T>::L;
+  const int64_t per = FLAT_ELEMS / Vec<T>::L;
+  v0 = (int64_t)blockIdx.x * per;
+  v1 = min(v0 + per, nv);
+  tail0 = (blockIdx.x == gridDim.x - 1) ? nv * Vec<T>::L : nn;
+}
+
+// x += alpha p, r -= alpha q, partials of r.r
+template <class T>
+__global__ void __launch_bounds__(FLAT_THREADS) k_xr_flat(Grid g, T* __restrict__ X,
+                                                          const T* __restrict__ P, T* __restrict__ R,
+                                                          const T* __restrict__ Q,
+                                                          const double* __restrict__ alpha,
+                                                          const int32_t* __restrict__ active,
+                                                          double* __restrict__ part, Prof prof) {
+  using V = typename Vec<T>::V;
+  const int64_t b = blockIdx.y;
+  if (!active[b]) return;
+  const T a = (T)alpha[b];
+  int64_t v0, v1, t0, nn;
+  flat_range<T>(g, v0, v1, t0, nn);
+  V* x = reinterpret_cast<V*>(X + b * g.ns);
+  const V* p = reinterpret_cast<const V*>(P + b * g.ns);
+  V* r = reinterpret_cast<V*>(R + b * g.ns);
+  const V* q = reinterpret_cast<const V*>(Q + b * g.ns);
+  T dot = T(0);
+  for (int64_t v = v0 + threadIdx.x; v < v1; v += FLAT_THREADS) {
+    Pack<T> xv, pv, rv, qv;
+    xv.v = x[v];
+    pv.v = p[v];
+    rv.v = r[v];
+    qv.v = q[v];
+#pragma unroll
+    for (int i = 0; i < Vec<T>::L; ++i) {
+      xv.a[i] = fma(a, pv.a[i], xv.a[i]);
+      rv.a[i] = fma(-a, qv.a[i], rv.a[i]);
+      dot = fma(rv.a[i], rv.a[i], dot);
+    }
+    x[v] = xv.v;
+    r[v] = rv.v;
+  }
+  for (int64_t e = t0 + threadIdx.x; e < nn; e += FLAT_THREADS) {
+    T* xs = X + b * g.ns;
+    T* rs = R + b * g.ns;
+    xs[e] = fma(a, P[b * g.ns + e], xs[e]);
+    rs[e] = fma(-a, Q[b * g.ns + e], rs[e]);
+    dot = fma(rs[e], rs[e], dot);
+  }
+  cta_partial((double)dot, part, g.tiles_f);
+  if (prof.acc && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(prof.acc, prof.per_sample);
+}
+
+// z = Winv r, partials of r.z
+template <class T>
+__global__ void __launch_bounds__(FLAT_THREADS) k_jz_flat(Grid g, const T* __restrict__ Wv,
+                                                          const T* __restrict__ R, T* __restrict__ Z,
+                                                          const int32_t* __restrict__ active,
+                                                          double* __restrict__ part, Prof prof) {
+  using V = typename Vec<T>::V;
+  const int64_t b = blockIdx.y;
+  if (!active[b]) return;
+  int64_t v0, v1, t0, nn;
+  flat_range<T>(g, v0, v1, t0, nn);
+  const V* w = reinterpret_cast<const V*>(Wv + b * g.ns);
+  const V* r = reinterpret_cast<const V*>(R + b * g.ns);
+  V* z = reinterpret_cast<V*>(Z + b * g.ns);
+  T dot = T(0);
+  for (int64_t v = v0 + threadIdx.x; v < v1; v += FLAT_THREADS) {
+    Pack<T> wv, rv, zv;
+    wv.v = w[v];
+    rv.v = r[v];
+#pragma unroll
+    for (int i = 0; i < Vec<T>::L; ++i) {
+      zv.a[i] = wv.a[i] * rv.a[i];
+      dot = fma(rv.a[i], zv.a[i], dot);
+    }
+    z[v] = zv.v;
+  }
+  for (int64_t e = t0 + threadIdx.x; e < nn; e += FLAT_THREADS) {
+    const T rv = R[b * g.ns + e];
+    const T zv = Wv[b * g.ns + e] * rv;
+    Z[b * g.ns + e] = zv;
+    dot = fma(rv, zv, dot);
+  }
+  cta_partial((double)dot, part, g.tiles_f);
+  if (prof.acc && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(prof.acc, prof.per_sample);
+}
+
+// x = 0 and, if R != nullptr, r = h^2 at interior nodes (b_i = int phi_i for f = 1).
+template <class T>
+__global__ void __launch_bounds__(FLAT_THREADS) k_init_flat(Grid g, T* __restrict__ X,
+                                                            T* __restrict__ R, Prof prof) {
+  const int64_t b = blockIdx.y;
+  const int64_t e0 = (int64_t)blockIdx.x * FLAT_ELEMS;
+  const int64_t e1 = min(e0 + (int64_t)FLAT_ELEMS, g.ns);
+  const int N1 = g.n + 1;
+  const int64_t nn = (int64_t)N1 * N1;
+  const T h2 = T(g.h * g.h);
+  for (int64_t e = e0 + threadIdx.x; e < e1; e += FLAT_THREADS) {
+    X[b * g.ns + e] = T(0);
+    if (R) {
+      T v = T(0);
+      if (e < nn) {
+        const int j = (int)(e / N1), i = (int)(e - (int64_t)j * N1);
+        if (interior2(g.n, i, j)) v = h2;
+      }
+      R[b * g.ns + e] = v;
+    }
+  }
+  if (prof.acc && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(prof.acc, prof.per_sample);
+}
+
+// Partials of w_i x_i for the QoI weights (exact Q1 integral mean):
+// domain: w = h^2 at interior nodes; box [L, H]^2 in node indices:
+// w = h^2 chi_x chi_y / |box|, chi = 1 strictly inside, 1/2 on a face.
+template <class T>
+__global__ void __launch_bounds__(FLAT_THREADS) k_qoi_flat(Grid g, int box, int L, int H,
+                                                           double inv_vol,
+                                                           const T* __restrict__ X,
+                                                           double* __restrict__ part, Prof prof) {
+  const int64_t b = blockIdx.y;
+  const int64_t e0 = (int64_t)blockIdx.x * FLAT_ELEMS;
+  const int64_t e1 = min(e0 + (int64_t)FLAT_ELEMS, g.ns);
+  const int N1 = g.n + 1;
+  const int64_t nn = (int64_t)N1 * N1;
+  const double h2 = g.h * g.h;
   double v = 0.0;
-  if (q.valid && q.interior) {
+  for (int64_t e = e0 + threadIdx.x; e < e1 && e < nn; e += FLAT_THREADS) {
+    const int j = (int)(e / N1), i = (int)(e - (int64_t)j * N1);
+    if (!interior2(g.n, i, j)) continue;
     double w = h2;
     if (box) {
-      const double cx = (q.i > L && q.i < H) ? 1.0 : ((q.i == L || q.i == H) ? 0.5 : 0.0);
-      const double cy = (q.j > L && q.j < H) ? 1.0 : ((q.j == L || q.j == H) ? 0.5 : 0.0);
+      const double cx = (i > L && i < H) ? 1.0 : ((i == L || i == H) ? 0.5 : 0.0);
+      const double cy = (j > L && j < H) ? 1.0 : ((j == L || j == H) ? 0.5 : 0.0);
       w = h2 * cx * cy * inv_vol;
     }
-    v = w * X[(int64_t)b * ns + q.idx];
+    v += w * (double)X[b * g.ns + e];
   }
-  v = block_sum(v);
-  if (threadIdx.x == 0 && threadIdx.y == 0) part[(int64_t)b * gridDim.x + blockIdx.x] = v;
-  prof_tick(prof);
+  cta_partial(v, part, g.tiles_f);
+  if (prof.acc && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(prof.acc, prof.per_sample);
 }
 
-inline dim3 grid2(const Grid& g, int64_t B) { return dim3((unsigned)g.tiles(), (unsigned)B, 1); }
-inline dim3 block2() { return dim3(TX2, TY2, 1); }
+// Mixed form, pointwise refinement steps per active sample:
+//   mode 0: rhs32 = r / scale   (unit-norm right-hand side of the inner solve)
+//   mode 1: u += scale * d32    (apply the inner correction)
+__global__ void __launch_bounds__(FLAT_THREADS) k_refine_flat(Grid g, int mode,
+                                                              double* __restrict__ Dbl,
+                                                              float* __restrict__ Flt,
+                                                              const double* __restrict__ scale,
+                                                              const int32_t* __restrict__ active,
+                                                              Prof prof) {
+  const int64_t b = blockIdx.y;
+  if (!active[b]) return;
+  const double sc = scale[b];
+  const double inv = 1.0 / sc;
+  int64_t v0, v1, t0, nn;
+  flat_range<float>(g, v0, v1, t0, nn);
+  double2* d = reinterpret_cast<double2*>(Dbl + b * g.ns);
+  float4* f = reinterpret_cast<float4*>(Flt + b * g.ns);
+  for (int64_t v = v0 + threadIdx.x; v < v1; v += FLAT_THREADS) {
+    double2 a = d[2 * v], c = d[2 * v + 1];
+    if (mode == 0) {
+      f[v] = make_float4((float)(a.x * inv), (float)(a.y * inv), (float)(c.x * inv),
+                         (float)(c.y * inv));
+    } else {
+      const float4 fv = f[v];
+      a.x = fma(sc, (double)fv.x, a.x);
+      a.y = fma(sc, (double)fv.y, a.y);
+      c.x = fma(sc, (double)fv.z, c.x);
+      c.y = fma(sc, (double)fv.w, c.y);
+      d[2 * v] = a;
+      d[2 * v + 1] = c;
+    }
+  }
+  for (int64_t e = t0 + threadIdx.x; e < nn; e += FLAT_THREADS) {
+    if (mode == 0) {
+      Flt[b * g.ns + e] = (float)(Dbl[b * g.ns + e] * inv);
+    } else {
+      Dbl[b * g.ns + e] = fma(sc, (double)Flt[b * g.ns + e], Dbl[b * g.ns + e]);
+    }
+  }
+  if (prof.acc && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(prof.acc, prof.per_sample);
+}
+
+// --------------------------------------------------------- per-node kernels
+
+// W = omega / D at every node (0 on the boundary).
+template <class T>
+__global__ void __launch_bounds__(FLAT_THREADS) k_winv2(Grid g, const T* __restrict__ K,
+                                                        double omega, T* __restrict__ W) {
+  const int64_t b = blockIdx.y;
+  const int N1 = g.n + 1;
+  const int64_t nn = (int64_t)N1 * N1;
+  const T* k = K + b * g.es;
+  const int64_t e0 = (int64_t)blockIdx.x * FLAT_ELEMS;
+  const int64_t e1 = min(e0 + (int64_t)FLAT_ELEMS, g.ns);
+  for (int64_t e = e0 + threadIdx.x; e < e1; e += FLAT_THREADS) {
+    T w = T(0);
+    if (e < nn) {
+      const int j = (int)(e / N1), i = (int)(e - (int64_t)j * N1);
+      if (interior2(g.n, i, j)) {
+        const T* r0 = k + (int64_t)(j - 1) * g.n + (i - 1);
+        const T d = Consts<T>::c23 * ((r0[0] + r0[1]) + (r0[g.n] + r0[g.n + 1]));
+        w = T(omega) / d;
+      }
+    }
+    W[b * g.ns + e] = w;
+  }
+}
+
+// Full weighting (transpose of bilinear prolongation), one thread per coarse node:
+// bc(I, J) = sum_{di,dj in -1..1} w(di) w(dj) r1(2I + di, 2J + dj), w(0) = 1, w(+-1) = 1/2.
+template <class T>
+__global__ void __launch_bounds__(FLAT_THREADS) k_restrict2(Grid gc, int64_t nsf,
+                                                            const T* __restrict__ R1,
+                                                            T* __restrict__ Bc,
+                                                            const int32_t* __restrict__ active,
+                                                            Prof prof) {
+  const int64_t b = blockIdx.y;
+  if (!active[b]) return;
+  const int nc = gc.n;
+  const int N1c = nc + 1;
+  const int N1 = 2 * nc + 1;
+  const int64_t nn = (int64_t)N1c * N1c;
+  const int64_t e0 = (int64_t)blockIdx.x * FLAT_ELEMS;
+  const int64_t e1 = min(e0 + (int64_t)FLAT_ELEMS, gc.ns);
+  for (int64_t e = e0 + threadIdx.x; e < e1; e += FLAT_THREADS) {
+    T v = T(0);
+    if (e < nn) {
+      const int J = (int)(e / N1c), I = (int)(e - (int64_t)J * N1c);
+      if (interior2(nc, I, J)) {
+        const T* r = R1 + b * nsf + (int64_t)(2 * J) * N1 + 2 * I;
+        const T h = T(0.5);
+        const T row0 = h * __ldg(r - N1 - 1) + __ldg(r - N1) + h * __ldg(r - N1 + 1);
+        const T row1 = h * __ldg(r - 1) + __ldg(r) + h * __ldg(r + 1);
+        const T row2 = h * __ldg(r + N1 - 1) + __ldg(r + N1) + h * __ldg(r + N1 + 1);
+        v = h * (row0 + row2) + row1;
+      }
+    }
+    Bc[b * gc.ns + e] = v;
+  }
+  if (prof.acc && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(prof.acc, prof.per_sample);
+}
+
+// Coarsest grid (n = 2, one unknown): e = b / D exactly.
+template <class T>
+__global__ void k_coarse2(int64_t ns, int64_t es, const T* __restrict__ K, const T* __restrict__ Bv,
+                          T* __restrict__ E, const int32_t* __restrict__ active, int64_t B) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B || !active[b]) return;
+  const int64_t off = b * ns;
+  const T* k = K + b * es;
+  const T d = Consts<T>::c23 * ((k[0] + k[1]) + (k[2] + k[3]));
+  for (int q = 0; q < 9; ++q) E[off + q] = T(0);
+  E[off + 4] = Bv[off + 4] / d;
+}
 
 }  // namespace
 
+// ------------------------------------------------------------- launchers
+
 namespace d2 {
 
-cudaError_t apply(cudaStream_t s, const Grid& g, const double* kappa, const double* x, double* y,
-                  int64_t B, Prof p) {
-  k_apply2d<<<grid2(g, B), block2(), 0, s>>>(g.n, g.tiles_x, g.ns, g.es, kappa, x, y, p);
+template <class T>
+cudaError_t apply(cudaStream_t s, const Grid& g, const T* kappa, const T* x, T* y, int64_t B, Prof p) {
+  k_apply2<T><<<sgrid(g, B), SBLOCK, 0, s>>>(g, kappa, x, y, p);
   return cudaGetLastError();
 }
 
-cudaError_t winv(cudaStream_t s, const Grid& g, const double* kappa, double omega, double* w,
-                 int64_t B) {
-  k_winv2d<<<grid2(g, B), block2(), 0, s>>>(g.n, g.tiles_x, g.ns, g.es, kappa, omega, w);
+template <class T>
+cudaError_t winv(cudaStream_t s, const Grid& g, const T* kappa, double omega, T* w, int64_t B) {
+  k_winv2<T><<<fgrid(g, B), FLAT_THREADS, 0, s>>>(g, kappa, omega, w);
   return cudaGetLastError();
 }
 
-cudaError_t pcg_init(cudaStream_t s, const Grid& g, double* x, double* r, int64_t B, Prof p) {
-  k_pcg_init2d<<<grid2(g, B), block2(), 0, s>>>(g.n, g.tiles_x, g.ns, g.h * g.h, x, r, p);
+template <class T>
+cudaError_t pcg_init(cudaStream_t s, const Grid& g, T* x, T* r, int64_t B, Prof p) {
+  k_init_flat<T><<<fgrid(g, B), FLAT_THREADS, 0, s>>>(g, x, r, p);
   return cudaGetLastError();
 }
 
-cudaError_t pcg_pq(cudaStream_t s, const Grid& g, const double* kappa, const double* z,
-                   const double* p_old, double* p_new, double* q, const Scalars& sc,
-                   double* part, int64_t B, Prof p) {
-  k_pq2d<<<grid2(g, B), block2(), 0, s>>>(g.n, g.tiles_x, g.ns, g.es, kappa, z, p_old, p_new, q,
-                                          sc.beta, sc.active, part, p);
+template <class T>
+cudaError_t pcg_pq(cudaStream_t s, const Grid& g, const T* kappa, const T* z, const T* p_old,
+                   T* p_new, T* q, const Scalars& sc, double* part, int64_t B, Prof p) {
+  k_pq2<T><<<sgrid(g, B), SBLOCK, 0, s>>>(g, kappa, z, p_old, p_new, q, sc.beta, sc.active, part, p);
   return cudaGetLastError();
 }
 
-cudaError_t pcg_xr(cudaStream_t s, const Grid& g, double* x, const double* pv, double* r,
-                   const double* q, const Scalars& sc, double* part, int64_t B, Prof p) {
-  k_xr2d<<<grid2(g, B), block2(), 0, s>>>(g.n, g.tiles_x, g.ns, x, pv, r, q, sc.alpha, sc.active,
-                                          part, p);
+template <class T>
+cudaError_t pcg_xr(cudaStream_t s, const Grid& g, T* x, const T* pv, T* r, const T* q,
+                   const Scalars& sc, double* part, int64_t B, Prof p) {
+  k_xr_flat<T><<<fgrid(g, B), FLAT_THREADS, 0, s>>>(g, x, pv, r, q, sc.alpha, sc.active, part, p);
   return cudaGetLastError();
 }
 
-cudaError_t jacobi_z(cudaStream_t s, const Grid& g, const double* winv, const double* r,
-                     double* z, const Scalars& sc, double* part, int64_t B, Prof p) {
-  k_jz2d<<<grid2(g, B), block2(), 0, s>>>(g.n, g.tiles_x, g.ns, winv, r, z, sc.active, part, p);
+template <class T>
+cudaError_t jacobi_z(cudaStream_t s, const Grid& g, const T* winv, const T* r, T* z,
+                     const Scalars& sc, double* part, int64_t B, Prof p) {
+  k_jz_flat<T><<<fgrid(g, B), FLAT_THREADS, 0, s>>>(g, winv, r, z, sc.active, part, p);
   return cudaGetLastError();
 }
 
-cudaError_t mg_pre(cudaStream_t s, const Grid& g, const double* kappa, const double* w,
-                   const double* b, double* e, double* r1, const int32_t* active, int64_t B,
-                   Prof p) {
-  k_mgpre2d<<<grid2(g, B), block2(), 0, s>>>(g.n, g.tiles_x, g.ns, g.es, kappa, w, b, e, r1,
-                                             active, p);
+template <class T>
+cudaError_t mg_pre(cudaStream_t s, const Grid& g, const T* kappa, const T* w, const T* b, T* e,
+                   T* r1, const int32_t* active, int64_t B, Prof p) {
+  k_mgpre2<T><<<sgrid(g, B), SBLOCK, 0, s>>>(g, kappa, w, b, e, r1, active, p);
   return cudaGetLastError();
 }
 
-cudaError_t restrict_(cudaStream_t s, const Grid& fine, const Grid& coarse, const double* r1,
-                      double* bc, const int32_t* active, int64_t B, Prof p) {
-  k_restrict2d<<<grid2(coarse, B), block2(), 0, s>>>(coarse.n, coarse.tiles_x, fine.ns, coarse.ns,
-                                                     r1, bc, active, p);
+template <class T>
+cudaError_t restrict_(cudaStream_t s, const Grid& fine, const Grid& coarse, const T* r1, T* bc,
+                      const int32_t* active, int64_t B, Prof p) {
+  k_restrict2<T><<<fgrid(coarse, B), FLAT_THREADS, 0, s>>>(coarse, fine.ns, r1, bc, active, p);
   return cudaGetLastError();
 }
 
-cudaError_t coarse_solve(cudaStream_t s, const Grid& g, const double* kappa, const double* b,
-                         double* e, const int32_t* active, int64_t B) {
-  k_coarse2d<<<(unsigned)((B + 127) / 128), 128, 0, s>>>(g.ns, g.es, kappa, b, e, active, B);
+template <class T>
+cudaError_t coarse_solve(cudaStream_t s, const Grid& g, const T* kappa, const T* b, T* e,
+                         const int32_t* active, int64_t B) {
+  k_coarse2<T><<<(unsigned)((B + 127) / 128), 128, 0, s>>>(g.ns, g.es, kappa, b, e, active, B);
   return cudaGetLastError();
 }
 
-cudaError_t mg_post(cudaStream_t s, const Grid& g, const Grid& coarse, const double* kappa,
-                    const double* w, const double* b, const double* e, const double* ec,
-                    double* out, const int32_t* active, double* part, int64_t B, Prof p) {
-  k_mgpost2d<<<grid2(g, B), block2(), 0, s>>>(g.n, g.tiles_x, g.ns, g.es, coarse.ns, kappa, w, b,
-                                              e, ec, out, active, part, p);
+template <class T>
+cudaError_t mg_post(cudaStream_t s, const Grid& g, const Grid& coarse, const T* kappa, const T* w,
+                    const T* b, const T* e, const T* ec, T* out, const int32_t* active,
+                    double* part, int64_t B, Prof p) {
+  k_mgpost2<T><<<sgrid(g, B), SBLOCK, 0, s>>>(g, coarse.ns, kappa, w, b, e, ec, out, active, part, p);
   return cudaGetLastError();
 }
 
-cudaError_t qoi(cudaStream_t s, const Grid& g, int box, int L, int H, double inv_vol,
-                const double* x, double* part, int64_t B, Prof p) {
-  k_qoi2d<<<grid2(g, B), block2(), 0, s>>>(g.n, g.tiles_x, g.ns, g.h * g.h, box, L, H, inv_vol, x,
-                                           part, p);
+template <class T>
+cudaError_t qoi(cudaStream_t s, const Grid& g, int box, int L, int H, double inv_vol, const T* x,
+                double* part, int64_t B, Prof p) {
+  k_qoi_flat<T><<<fgrid(g, B), FLAT_THREADS, 0, s>>>(g, box, L, H, inv_vol, x, part, p);
   return cudaGetLastError();
 }
+
+cudaError_t resid64(cudaStream_t s, const Grid& g, const double* kappa, const double* u,
+                    double* r, const int32_t* active, double* part, int64_t B, Prof p) {
+  k_resid2<<<sgrid(g, B), SBLOCK, 0, s>>>(g, kappa, u, r, active, part, p);
+  return cudaGetLastError();
+}
+
+cudaError_t to_rhs32(cudaStream_t s, const Grid& g, const double* r, const double* scale,
+                     float* r32, const int32_t* active, int64_t B, Prof p) {
+  k_refine_flat<<<fgrid(g, B), FLAT_THREADS, 0, s>>>(g, 0, const_cast<double*>(r), r32, scale,
+                                                     active, p);
+  return cudaGetLastError();
+}
+
+cudaError_t add_correction(cudaStream_t s, const Grid& g, double* u, const float* d32,
+                           const double* scale, const int32_t* active, int64_t B, Prof p) {
+  k_refine_flat<<<fgrid(g, B), FLAT_THREADS, 0, s>>>(g, 1, u, const_cast<float*>(d32), scale,
+                                                     active, p);
+  return cudaGetLastError();
+}
+
+#define MLMC_INST2(T)                                                                              \
+  template cudaError_t apply<T>(cudaStream_t, const Grid&, const T*, const T*, T*, int64_t, Prof); \
+  template cudaError_t winv<T>(cudaStream_t, const Grid&, const T*, double, T*, int64_t);          \
+  template cudaError_t pcg_init<T>(cudaStream_t, const Grid&, T*, T*, int64_t, Prof);              \
+  template cudaError_t pcg_pq<T>(cudaStream_t, const Grid&, const T*, const T*, const T*, T*, T*,  \
+                                 const Scalars&, double*, int64_t, Prof);                          \
+  template cudaError_t pcg_xr<T>(cudaStream_t, const Grid&, T*, const T*, T*, const T*,            \
+                                 const Scalars&, double*, int64_t, Prof);                          \
+  template cudaError_t jacobi_z<T>(cudaStream_t, const Grid&, const T*, const T*, T*,              \
+                                   const Scalars&, double*, int64_t, Prof);                        \
+  template cudaError_t mg_pre<T>(cudaStream_t, const Grid&, const T*, const T*, const T*, T*, T*,  \
+                                 const int32_t*, int64_t, Prof);                                   \
+  template cudaError_t restrict_<T>(cudaStream_t, const Grid&, const Grid&, const T*, T*,          \
+                                    const int32_t*, int64_t, Prof);                                \
+  template cudaError_t coarse_solve<T>(cudaStream_t, const Grid&, const T*, const T*, T*,          \
+                                       const int32_t*, int64_t);                                   \
+  template cudaError_t mg_post<T>(cudaStream_t, const Grid&, const Grid&, const T*, const T*,      \
+                                  const T*, const T*, const T*, T*, const int32_t*, double*,       \
+                                  int64_t, Prof);                                                  \
+  template cudaError_t qoi<T>(cudaStream_t, const Grid&, int, int, int, double, const T*, double*, \
+                              int64_t, Prof);
+
+MLMC_INST2(double)
+MLMC_INST2(float)
 
 }  // namespace d2
 }  // namespace mlmc

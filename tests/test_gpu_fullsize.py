@@ -3,6 +3,8 @@ rtol 1e-10), in the launch configuration the benchmark times: the whole
 100-sample pilot batch of a level in one call, with sampled outputs checked
 one by one against the oracle (sparse LU with refinement) and properties
 that hold for every sample."""
+import functools
+
 import numpy as np
 import pytest
 
@@ -24,9 +26,15 @@ def m():
     return mod
 
 
-@pytest.mark.parametrize("level,checked", [(5, (0, 57)), (3, (0, 99))])
-def test_pilot_batch_full_size(m, level, checked):
-    wl = workload("2d-scale")
+@functools.lru_cache(maxsize=None)
+def oracle_sample(level, i):
+    return omlmc.coupled_sample(workload("2d-scale"), level, i)
+
+
+@pytest.mark.parametrize("precision,level,checked", [("fp64", 5, (0, 57)), ("fp64", 3, (0, 99)),
+                                                     ("mixed", 5, (0, 57)), ("mixed", 2, (3,))])
+def test_pilot_batch_full_size(m, precision, level, checked):
+    wl = workload("2d-scale", precision=precision)
     cfg = m.config_from_workload(wl)
     with m.Plan(cfg, torch.cuda.current_stream().cuda_stream) as plan:
         qf, qc, it = plan.sample_level(level, 0, 100)
@@ -39,6 +47,6 @@ def test_pilot_batch_full_size(m, level, checked):
     assert np.max(np.abs(y)) < 0.05 * np.min(qf)
     assert abs(mean - y.mean()) <= 1e-12 * abs(y.mean()) + 1e-18
     for i in checked:
-        rf, rc = omlmc.coupled_sample(wl, level, i)
+        rf, rc = oracle_sample(level, i)
         assert abs(qf[i] - rf) <= 1e-9 * abs(rf)
         assert abs(qc[i] - rc) <= 1e-9 * abs(rc)

@@ -131,11 +131,13 @@ def test_apply_parity(m, n):
 
 # ----------------------------------------------------------- A6/A7: solve
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("solver,n", [("jacobi", 16), ("jacobi", 48), ("gmg", 32), ("gmg", 128),
                                       ("gmg", 4), ("jacobi", 2)])
-def test_solve_parity(m, solver, n):
+def test_solve_parity(m, solver, n, precision):
     count = 6
-    cfg = m.config(dim=2, n_levels=1, coarse_cells=n, solver=solver, rtol=1e-11)
+    cfg = m.config(dim=2, n_levels=1, coarse_cells=n, solver=solver, rtol=1e-11,
+                   precision=precision)
     kap = random_element_field(2, n, count, seed=7 * n, spread=1.0)
     with m.Plan(cfg, stream()) as plan:
         kd = elem_arrays_to_device(m, 2, n, kap)
@@ -160,8 +162,9 @@ def test_solve_parity(m, solver, n):
 
 # ------------------------------------------------- A1/A8: coupled samples
 
-def test_coupled_samples_and_level_state(m):
-    wl = small_case(2, n0=8, levels=3, corr_len=0.3, m=4, rtol=1e-11)
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_coupled_samples_and_level_state(m, precision):
+    wl = small_case(2, n0=8, levels=3, corr_len=0.3, m=4, rtol=1e-11, precision=precision)
     cfg = m.config_from_workload(wl)
     with m.Plan(cfg, stream()) as plan:
         for level in range(3):
@@ -183,9 +186,10 @@ def test_coupled_samples_and_level_state(m):
             assert cost == 9 * omlmc.level_cost(wl, level)
 
 
-def test_batching_is_bitwise_invariant(m):
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batching_is_bitwise_invariant(m, precision):
     """Y(l, i) and the level state do not depend on how samples are batched."""
-    wl = small_case(2, n0=8, levels=3, m=4)
+    wl = small_case(2, n0=8, levels=3, m=4, solver="gmg", precision=precision)
     cfg = m.config_from_workload(wl)
     with m.Plan(cfg, stream()) as plan:
         qa, qca, _ = plan.sample_level(2, 0, 12)
