@@ -77,6 +77,9 @@ typedef struct mlmc_config {
   double inner_rtol;       /* MLMC_MIXED: relative tolerance of each FP32 inner solve */
   int32_t inner_max_iter;  /* MLMC_MIXED: iteration cap of each inner solve */
   int32_t outer_max_iter;  /* MLMC_MIXED: cap on FP64 refinement steps */
+  int32_t use_graphs;      /* 1: each batched solve runs as one CUDA graph whose
+                              while-nodes iterate on the device (no host polls);
+                              0: host-driven iterations. Same results either way. */
 } mlmc_config;
 
 /* Per-level Welford state (Eq. (sample_variance): V = m2 / n). */
@@ -92,8 +95,9 @@ typedef struct mlmc_plan_s* mlmc_plan;
 /* ---- configuration and layout -------------------------------------- */
 
 /* Defaults: 2D, 3 levels, n_0 = 16, m = 4, sigma2 = 1, corr_len = 0.3,
- * domain-mean QoI, Jacobi-PCG, rtol 1e-10, FP64, seed 0; mixed form:
- * inner_rtol 1e-5, inner_max_iter 60, outer_max_iter 12.
+ * domain-mean QoI, Jacobi-PCG, rtol 1e-10, FP64, seed 0, mg_omega 0.9,
+ * CUDA graphs on; mixed form: inner_rtol 3e-3, inner_max_iter 60,
+ * outer_max_iter 16.
  *
  * MLMC_MIXED (iterative refinement, the precision pattern the method admits
  * on GB300): u = 0, r = b; repeat { d = A32^-1 (r / s) by FP32 PCG with

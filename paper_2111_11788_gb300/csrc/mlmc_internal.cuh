@@ -104,7 +104,8 @@ enum FinMode { FIN_GAMMA0 = 0, FIN_ALPHA = 1, FIN_CONV = 2, FIN_BETA = 3, FIN_QO
 // iterations (inner.iters, -1 = hit inner max) are added to the total.
 cudaError_t launch_outer_step(cudaStream_t s, const double* part, int64_t tiles,
                               const Scalars& outer, const int32_t* inner_iters, int inner_max,
-                              int outer_it, int outer_max, int64_t B);
+                              int outer_it, int outer_max, int64_t B,
+                              const int32_t* outer_it_dev = nullptr);
 // inner.active = outer.active, inner.tol = tol, inner.iters = 0, beta = 0.
 cudaError_t launch_inner_init(cudaStream_t s, const Scalars& inner, const Scalars& outer,
                               double tol, int64_t B);
@@ -171,8 +172,19 @@ cudaError_t add_correction(cudaStream_t s, const Grid& g, double* u, const float
                            const double* scale, const int32_t* active, int64_t B, Prof p);
 }  // namespace d2
 
+// iter_dev (may be null) overrides iter with a device-side iteration counter.
 cudaError_t launch_finalize(cudaStream_t s, FinMode mode, const double* part, int64_t tiles,
-                            const Scalars& sc, double* out, int iter, int max_iter, int64_t B);
+                            const Scalars& sc, double* out, int iter, int max_iter, int64_t B,
+                            const int32_t* iter_dev = nullptr);
+
+// Graph loop control: count = #active; cond = count > 0 && *it_dev < max_iter;
+// ++*it_dev; ++*execs (if given).
+cudaError_t launch_loop_ctl(cudaStream_t s, const int32_t* active, int64_t B, int32_t* it_dev,
+                            int max_iter, int32_t* count, int32_t* execs,
+                            cudaGraphConditionalHandle h);
+cudaError_t launch_set_int(cudaStream_t s, int32_t* p, int32_t v);
+// Sets a graph conditional (re-arms a nested while-node before it is reached).
+cudaError_t launch_set_cond(cudaStream_t s, cudaGraphConditionalHandle h, unsigned v);
 
 cudaError_t launch_count_active(cudaStream_t s, const int32_t* active, int64_t B, int32_t* count);
 

@@ -10,6 +10,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <tuple>
 #include <vector>
 
 #include "mlmc_internal.cuh"
@@ -72,6 +74,8 @@ struct SolveWs {
   double* part;
   Scalars sc;
   int32_t* count;
+  int32_t* it;       // device iteration counter (graph-driven loop)
+  int32_t* execs;    // device count of loop-body executions (graph-driven loop)
 };
 
 template <class T>
@@ -106,6 +110,8 @@ void carve_solve(Carve& c, const MeshInfo& mi, int64_t B, bool own_kappa0, Solve
   w.sc.scale = nullptr;
   w.sc.total = nullptr;
   w.count = c.take<int32_t>(1);
+  w.it = c.take<int32_t>(1);
+  w.execs = c.take<int32_t>(1);
 }
 
 // Mixed form: FP64 solution / residual / kappa plus the FP32 inner solve.
@@ -114,6 +120,9 @@ struct MixedWs {
   double* r;
   double* kap64;
   Scalars outer;
+  int32_t* outer_count;
+  int32_t* outer_it;
+  int32_t* outer_execs;
   SolveWs<float> in;
 };
 
@@ -134,6 +143,9 @@ void carve_mixed(Carve& c, const MeshInfo& mi, int64_t B, MixedWs& w) {
   w.outer.delta = c.take<double>(B);
   w.outer.alpha = c.take<double>(B);
   w.outer.beta = c.take<double>(B);
+  w.outer_count = c.take<int32_t>(1);
+  w.outer_it = c.take<int32_t>(1);
+  w.outer_execs = c.take<int32_t>(1);
   carve_solve(c, mi, B, true, w.in);
 }
 
@@ -173,6 +185,19 @@ struct PendingEvent {
 }  // namespace
 }  // namespace mlmc
 
+// An instantiated solve graph and the kernel counts of its parts (for the
+// launch counter: setup + body * executions + epilogue).
+struct GraphRec {
+  cudaGraphExec_t exec = nullptr;
+  int64_t n_setup = 0, n_body = 0, n_outer = 0, n_epi = 0;
+};
+
+namespace mlmc {
+namespace {
+
+}  // namespace
+}  // namespace mlmc
+
 using namespace mlmc;
 
 struct mlmc_plan_s {
@@ -202,6 +227,12 @@ struct mlmc_plan_s {
   double ms[NUM_KERNELS] = {0};
   int64_t kl[NUM_KERNELS] = {0};
   int64_t launches = 0;
+  // graph-captured solves, keyed by (form, mesh, batch, workspace)
+  std::map<std::tuple<int, int, int64_t, const void*, const void*, const void*, const void*>,
+           struct GraphRec> graphs;
+  cudaStream_t cap_stream = nullptr;   // private stream the solve graphs are captured on
+  // executed graphs whose kernel counts are settled at the next sync point
+  std::vector<std::tuple<const GraphRec*, int32_t*, int32_t*>> pending_graphs;
 };
 
 namespace {
@@ -345,10 +376,15 @@ double elems_of(const Grid& g) { return (double)ipow(g.n, g.dim); }
 
 // --- workspace --------------------------------------------------------
 
+void clear_graphs(mlmc_plan p);
+mlmc_status settle_graph_launches(mlmc_plan p);
+
 mlmc_status ensure_ws(mlmc_plan p, size_t bytes) {
   if (bytes <= p->ws_bytes) return MLMC_OK;
   if (p->ws) {
     cudaStreamSynchronize(p->stream);
+    if (settle_graph_launches(p) != MLMC_OK) return MLMC_ERR_CUDA;
+    clear_graphs(p);
     cudaFree(p->ws);
     p->ws = nullptr;
     p->ws_bytes = 0;
@@ -477,48 +513,186 @@ mlmc_status setup_levels(mlmc_plan p, const MeshInfo& mi, SolveWs<T>& w, int64_t
   return MLMC_OK;
 }
 
-// PCG iterations on w (scalars, x and r already initialised). Stops when no
-// sample is active or after max_iter iterations.
+// First preconditioning and gamma = r.z; sets the device iteration counter to 1.
 template <class T>
-mlmc_status pcg_loop(mlmc_plan p, const MeshInfo& mi, SolveWs<T>& w, int64_t B, int max_iter) {
+mlmc_status pcg_prologue(mlmc_plan p, const MeshInfo& mi, SolveWs<T>& w, int64_t B, int max_iter) {
+  int64_t Tp = 0;
+  mlmc_status st = precondition<T>(p, mi, w, B, &Tp);
+  if (st != MLMC_OK) return st;
+  CK(run(p, KID_FINALIZE, [&] { return launch_finalize(p->stream, FIN_GAMMA0, w.part, Tp, w.sc, nullptr, 0, max_iter, B); }));
+  CK(run(p, KID_SETUP, [&] { return launch_set_int(p->stream, w.it, 1); }));
+  return MLMC_OK;
+}
+
+// One PCG iteration with p_old -> p_new; with a graph handle, the loop
+// control kernel advances the device counter and sets the while-condition.
+template <class T>
+mlmc_status pcg_iteration(mlmc_plan p, const MeshInfo& mi, SolveWs<T>& w, int64_t B, int max_iter,
+                          int it, T* pold, T* pnew, const cudaGraphConditionalHandle* h,
+                          bool* done) {
   cudaStream_t s = p->stream;
   const Grid& g0 = mi.g[0];
   const double vb = (double)sizeof(T);
   const double nn0 = nodes_of(g0), ne0 = elems_of(g0);
-  int64_t Tp = 0;
-  mlmc_status st = precondition<T>(p, mi, w, B, &Tp);
-  if (st != MLMC_OK) return st;
-  CK(run(p, KID_FINALIZE, [&] { return launch_finalize(s, FIN_GAMMA0, w.part, Tp, w.sc, nullptr, 0, max_iter, B); }));
-  int check = p->cfg.check_every;
-  if (check <= 0) check = (B * nn0 > 4e6) ? 1 : 4;
-  if (ensure_pin(p, 64) != MLMC_OK) return MLMC_ERR_OOM;
-  int32_t* h_count = (int32_t*)p->h_pin;
-  T* pold = w.p0;
-  T* pnew = w.p1;
-  for (int it = 1; it <= max_iter; ++it) {
-    CK(run(p, KID_PCG_PQ, [&] {
-      return d2::pcg_pq<T>(s, g0, w.kap[0], w.z, pold, pnew, w.q, w.sc, w.part, B,
-                           prof_for(p, KID_PCG_PQ, (4 * nn0 + ne0) * vb));
-    }));
-    CK(run(p, KID_FINALIZE, [&] { return launch_finalize(s, FIN_ALPHA, w.part, g0.tiles_s, w.sc, nullptr, it, max_iter, B); }));
-    CK(run(p, KID_PCG_XR, [&] {
-      return d2::pcg_xr<T>(s, g0, w.x, pnew, w.r, w.q, w.sc, w.part, B,
-                           prof_for(p, KID_PCG_XR, 6 * nn0 * vb));
-    }));
-    CK(run(p, KID_FINALIZE, [&] { return launch_finalize(s, FIN_CONV, w.part, g0.tiles_f, w.sc, nullptr, it, max_iter, B); }));
+  const int32_t* itd = h ? w.it : nullptr;
+  CK(run(p, KID_PCG_PQ, [&] {
+    return d2::pcg_pq<T>(s, g0, w.kap[0], w.z, pold, pnew, w.q, w.sc, w.part, B,
+                         prof_for(p, KID_PCG_PQ, (4 * nn0 + ne0) * vb));
+  }));
+  CK(run(p, KID_FINALIZE, [&] { return launch_finalize(s, FIN_ALPHA, w.part, g0.tiles_s, w.sc, nullptr, it, max_iter, B, itd); }));
+  CK(run(p, KID_PCG_XR, [&] {
+    return d2::pcg_xr<T>(s, g0, w.x, pnew, w.r, w.q, w.sc, w.part, B,
+                         prof_for(p, KID_PCG_XR, 6 * nn0 * vb));
+  }));
+  CK(run(p, KID_FINALIZE, [&] { return launch_finalize(s, FIN_CONV, w.part, g0.tiles_f, w.sc, nullptr, it, max_iter, B, itd); }));
+  if (h) {
+    CK(run(p, KID_COUNT, [&] { return launch_loop_ctl(s, w.sc.active, B, w.it, max_iter, w.count, w.execs, *h); }));
+  } else {
+    int check = p->cfg.check_every;
+    if (check <= 0) check = (B * nn0 > 4e6) ? 1 : 4;
     if (it % check == 0 || it == max_iter) {
+      int32_t* h_count = (int32_t*)p->h_pin;
       CK(run(p, KID_COUNT, [&] { return launch_count_active(s, w.sc.active, B, w.count); }));
       CK(cudaMemcpyAsync(h_count, w.count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
-      if (*h_count == 0) break;
+      if (*h_count == 0) {
+        *done = true;
+        return MLMC_OK;
+      }
     }
-    st = precondition<T>(p, mi, w, B, &Tp);
+  }
+  int64_t Tp = 0;
+  mlmc_status st = precondition<T>(p, mi, w, B, &Tp);
+  if (st != MLMC_OK) return st;
+  CK(run(p, KID_FINALIZE, [&] { return launch_finalize(s, FIN_BETA, w.part, Tp, w.sc, nullptr, it, max_iter, B, itd); }));
+  return MLMC_OK;
+}
+
+// Host-driven PCG iterations (scalars, x and r initialised; prologue done).
+template <class T>
+mlmc_status pcg_loop(mlmc_plan p, const MeshInfo& mi, SolveWs<T>& w, int64_t B, int max_iter) {
+  if (ensure_pin(p, 64) != MLMC_OK) return MLMC_ERR_OOM;
+  T* pold = w.p0;
+  T* pnew = w.p1;
+  for (int it = 1; it <= max_iter; ++it) {
+    bool done = false;
+    mlmc_status st = pcg_iteration<T>(p, mi, w, B, max_iter, it, pold, pnew, nullptr, &done);
     if (st != MLMC_OK) return st;
-    CK(run(p, KID_FINALIZE, [&] { return launch_finalize(s, FIN_BETA, w.part, Tp, w.sc, nullptr, it, max_iter, B); }));
+    if (done) break;
     std::swap(pold, pnew);
   }
   return MLMC_OK;
 }
+
+// Body of the graph-driven loop: two iterations (p0 -> p1, p1 -> p0), each
+// followed by the loop control; iterations after convergence are no-ops
+// because every kernel skips inactive samples.
+template <class T>
+mlmc_status pcg_graph_body(mlmc_plan p, const MeshInfo& mi, SolveWs<T>& w, int64_t B, int max_iter,
+                           cudaGraphConditionalHandle h) {
+  bool done = false;
+  mlmc_status st = pcg_iteration<T>(p, mi, w, B, max_iter, 0, w.p0, w.p1, &h, &done);
+  if (st != MLMC_OK) return st;
+  return pcg_iteration<T>(p, mi, w, B, max_iter, 0, w.p1, w.p0, &h, &done);
+}
+
+// --- CUDA-graph capture -----------------------------------------------
+//
+// A solve is captured on the plan's private stream into one graph. Loops are
+// while-nodes inserted into the graph being captured; every kernel that sets
+// a loop condition is a direct node of the body of that loop, or an upstream
+// node of the same graph (to re-arm a nested loop).
+
+// Launches issued while capturing go to the plan's private capture stream.
+struct CaptureStream {
+  mlmc_plan p;
+  cudaStream_t saved;
+  explicit CaptureStream(mlmc_plan pp) : p(pp), saved(pp->stream) { p->stream = p->cap_stream; }
+  ~CaptureStream() { p->stream = saved; }
+};
+
+// Runs f while capturing into `graph` (new graph if *graph == nullptr).
+template <class F>
+mlmc_status capture(mlmc_plan p, cudaGraph_t* graph, F&& f) {
+  CaptureStream cs(p);
+  const int64_t l0 = p->launches;
+  cudaError_t e = (*graph == nullptr)
+                      ? cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal)
+                      : cudaStreamBeginCaptureToGraph(p->stream, *graph, nullptr, nullptr, 0,
+                                                      cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return MLMC_ERR_CUDA;
+  mlmc_status st = f();
+  cudaGraph_t g = *graph;
+  e = cudaStreamEndCapture(p->stream, &g);
+  p->launches = l0;   // captured launches are counted when the graph executes
+  if (st != MLMC_OK || e != cudaSuccess) {
+    if (g && *graph == nullptr) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return st != MLMC_OK ? st : MLMC_ERR_CUDA;
+  }
+  *graph = g;
+  return MLMC_OK;
+}
+
+// Graph being captured on p->stream.
+mlmc_status capture_graph(mlmc_plan p, cudaGraph_t* g) {
+  cudaStreamCaptureStatus cs;
+  if (cudaStreamGetCaptureInfo(p->stream, &cs, nullptr, g, nullptr, nullptr, nullptr) != cudaSuccess ||
+      cs != cudaStreamCaptureStatusActive)
+    return MLMC_ERR_CUDA;
+  return MLMC_OK;
+}
+
+// Inserts a while-node after everything captured so far on p->stream; later
+// launches depend on it. Creates its handle (default 1 at graph launch)
+// unless have_handle. *body receives the (empty) body graph.
+mlmc_status insert_while(mlmc_plan p, cudaGraphConditionalHandle* h, cudaGraph_t* body,
+                         bool have_handle) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* ed = nullptr;
+  size_t nd = 0;
+  if (cudaStreamGetCaptureInfo(p->stream, &cs, nullptr, &g, &deps, &ed, &nd) != cudaSuccess ||
+      cs != cudaStreamCaptureStatusActive)
+    return MLMC_ERR_CUDA;
+  if (!have_handle && cudaGraphConditionalHandleCreate(h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess)
+    return MLMC_ERR_CUDA;
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = *h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (cudaGraphAddNode(&node, g, deps, ed, nd, &np) != cudaSuccess) return MLMC_ERR_CUDA;
+  if (cudaStreamUpdateCaptureDependencies(p->stream, &node, nullptr, 1,
+                                          cudaStreamSetCaptureDependencies) != cudaSuccess)
+    return MLMC_ERR_CUDA;
+  *body = np.conditional.phGraph_out[0];
+  return MLMC_OK;
+}
+
+void clear_graphs(mlmc_plan p) {
+  for (auto& kv : p->graphs)
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  p->graphs.clear();
+  p->pending_graphs.clear();
+}
+
+// Adds the kernels executed by graphs launched since the last sync point.
+mlmc_status settle_graph_launches(mlmc_plan p) {
+  for (auto& t : p->pending_graphs) {
+    const GraphRec* r = std::get<0>(t);
+    int32_t ex[2] = {0, 0};
+    CK(cudaMemcpy(&ex[0], std::get<1>(t), sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (std::get<2>(t)) CK(cudaMemcpy(&ex[1], std::get<2>(t), sizeof(int32_t), cudaMemcpyDeviceToHost));
+    p->launches += r->n_setup + r->n_epi + (int64_t)ex[0] * r->n_body + (int64_t)ex[1] * r->n_outer;
+  }
+  p->pending_graphs.clear();
+  return MLMC_OK;
+}
+
+bool graphs_on(mlmc_plan p) { return p->cfg.use_graphs != 0 && !p->prof_on && p->cap_stream; }
 
 double b_norm(const mlmc_config& c, const Grid& g0) {
   return std::pow(g0.h, c.dim) * std::sqrt((double)interior_dofs(c.dim, g0.n));
@@ -540,76 +714,235 @@ mlmc_status qoi_of(mlmc_plan p, const Grid& g0, const double* u, double* part, c
   return MLMC_OK;
 }
 
-// FP64 form: solve A(kappa) u = b for B samples; w.kap[0] holds kappa.
-// Leaves u in w.x, writes q (device) and iters (device).
-mlmc_status solve_fp64(mlmc_plan p, const MeshInfo& mi, SolveWs<double>& w, int64_t B,
-                       double* q_dev, int32_t* iters_dev) {
+// FP64 form, launch sequences.
+mlmc_status fp64_setup(mlmc_plan p, const MeshInfo& mi, SolveWs<double>& w, int64_t B) {
   cudaStream_t s = p->stream;
   const mlmc_config& c = p->cfg;
   const Grid& g0 = mi.g[0];
   mlmc_status st = setup_levels<double>(p, mi, w, B);
   if (st != MLMC_OK) return st;
   CK(run(p, KID_SETUP, [&] { return launch_scalars_init(s, w.sc, c.rtol * b_norm(c, g0), 0.0, B); }));
+  CK(run(p, KID_SETUP, [&] { return launch_set_int(s, w.execs, 0); }));
   CK(run(p, KID_PCG_INIT, [&] {
     return d2::pcg_init<double>(s, g0, w.x, w.r, B, prof_for(p, KID_PCG_INIT, 2 * nodes_of(g0) * 8));
   }));
-  st = pcg_loop<double>(p, mi, w, B, c.max_iter);
+  return pcg_prologue<double>(p, mi, w, B, c.max_iter);
+}
+
+mlmc_status fp64_epilogue(mlmc_plan p, const MeshInfo& mi, SolveWs<double>& w, int64_t B,
+                          double* q_dev, int32_t* iters_dev) {
+  mlmc_status st = qoi_of(p, mi.g[0], w.x, w.part, w.sc, q_dev, B);
   if (st != MLMC_OK) return st;
-  st = qoi_of(p, g0, w.x, w.part, w.sc, q_dev, B);
-  if (st != MLMC_OK) return st;
-  if (iters_dev) CK(cudaMemcpyAsync(iters_dev, w.sc.iters, sizeof(int32_t) * B, cudaMemcpyDeviceToDevice, s));
+  if (iters_dev) CK(cudaMemcpyAsync(iters_dev, w.sc.iters, sizeof(int32_t) * B, cudaMemcpyDeviceToDevice, p->stream));
   return MLMC_OK;
 }
 
-// Mixed form: FP64 iterative refinement around FP32 GMG/Jacobi-PCG
-// (kappa32 = rounded kappa64). w.kap64 holds kappa. Leaves u in w.u.
-mlmc_status solve_mixed(mlmc_plan p, const MeshInfo& mi, MixedWs& w, int64_t B, double* q_dev,
-                        int32_t* iters_dev) {
+// FP64 form: solve A(kappa) u = b for B samples; w.kap[0] holds kappa.
+// Leaves u in w.x, writes q (device) and iters (device). With graphs on,
+// the whole solve is one graph: setup -> while(two PCG iterations) -> QoI.
+mlmc_status solve_fp64(mlmc_plan p, int mesh, const MeshInfo& mi, SolveWs<double>& w, int64_t B,
+                       double* q_dev, int32_t* iters_dev) {
+  const mlmc_config& c = p->cfg;
+  if (!graphs_on(p)) {
+    mlmc_status st = fp64_setup(p, mi, w, B);
+    if (st != MLMC_OK) return st;
+    st = pcg_loop<double>(p, mi, w, B, c.max_iter);
+    if (st != MLMC_OK) return st;
+    return fp64_epilogue(p, mi, w, B, q_dev, iters_dev);
+  }
+  const auto key = std::make_tuple(0, mesh, B, (const void*)p->ws, (const void*)w.kap[0],
+                                   (const void*)q_dev, (const void*)iters_dev);
+  auto it = p->graphs.find(key);
+  if (it == p->graphs.end()) {
+    // setup -> while(two PCG iterations + loop control) -> QoI epilogue
+    GraphRec rec;
+    cudaGraph_t P = nullptr, body = nullptr;
+    cudaGraphConditionalHandle h;
+    int64_t l1 = 0, l2 = 0;
+    mlmc_status st = capture(p, &P, [&] {
+      const int64_t l0 = p->launches;
+      mlmc_status s2 = fp64_setup(p, mi, w, B);
+      if (s2 != MLMC_OK) return s2;
+      l1 = p->launches - l0;
+      if ((s2 = insert_while(p, &h, &body, false)) != MLMC_OK) return s2;
+      const int64_t l3 = p->launches;
+      s2 = fp64_epilogue(p, mi, w, B, q_dev, iters_dev);
+      l2 = p->launches - l3;
+      return s2;
+    });
+    if (st != MLMC_OK) return st;
+    rec.n_setup = l1;
+    rec.n_epi = l2;
+    int64_t nb = 0;
+    st = capture(p, &body, [&] {
+      const int64_t l0 = p->launches;
+      mlmc_status s2 = pcg_graph_body<double>(p, mi, w, B, c.max_iter, h);
+      nb = p->launches - l0;
+      return s2;
+    });
+    if (st != MLMC_OK || cudaGraphInstantiate(&rec.exec, P, 0) != cudaSuccess) {
+      cudaGraphDestroy(P);
+      cudaGetLastError();
+      return st != MLMC_OK ? st : MLMC_ERR_CUDA;
+    }
+    cudaGraphDestroy(P);
+    rec.n_body = nb / 2;
+    it = p->graphs.emplace(key, rec).first;
+  }
+  CK(cudaGraphLaunch(it->second.exec, p->stream));
+  p->pending_graphs.emplace_back(&it->second, w.execs, nullptr);
+  return MLMC_OK;
+}
+
+// Mixed form, launch sequences.
+mlmc_status mixed_setup(mlmc_plan p, const MeshInfo& mi, MixedWs& w, int64_t B) {
   cudaStream_t s = p->stream;
   const mlmc_config& c = p->cfg;
   const Grid& g0 = mi.g[0];
-  const double nn0 = nodes_of(g0), ne0 = elems_of(g0);
   CK(run(p, KID_SETUP, [&] { return launch_cast_kappa(s, g0, w.kap64, w.in.kap[0], B); }));
   mlmc_status st = setup_levels<float>(p, mi, w.in, B);
   if (st != MLMC_OK) return st;
   const double bn = b_norm(c, g0);
   CK(run(p, KID_SETUP, [&] { return launch_scalars_init(s, w.outer, c.rtol * bn, bn, B); }));
+  CK(run(p, KID_SETUP, [&] { return launch_set_int(s, w.outer_it, 1); }));
+  CK(run(p, KID_SETUP, [&] { return launch_set_int(s, w.outer_execs, 0); }));
+  CK(run(p, KID_SETUP, [&] { return launch_set_int(s, w.in.execs, 0); }));
   CK(run(p, KID_PCG_INIT, [&] {
-    return d2::pcg_init<double>(s, g0, w.u, w.r, B, prof_for(p, KID_PCG_INIT, 2 * nn0 * 8));
+    return d2::pcg_init<double>(s, g0, w.u, w.r, B, prof_for(p, KID_PCG_INIT, 2 * nodes_of(g0) * 8));
   }));
-  if (ensure_pin(p, 64) != MLMC_OK) return MLMC_ERR_OOM;
-  int32_t* h_count = (int32_t*)p->h_pin;
-  for (int outer = 1; outer <= c.outer_max_iter; ++outer) {
-    CK(run(p, KID_REFINE, [&] {
-      return d2::to_rhs32(s, g0, w.r, w.outer.scale, w.in.r, w.outer.active, B,
-                          prof_for(p, KID_REFINE, nn0 * (8 + 4)));
-    }));
-    CK(run(p, KID_SETUP, [&] { return launch_inner_init(s, w.in.sc, w.outer, c.inner_rtol, B); }));
-    CK(run(p, KID_PCG_INIT, [&] {
-      return d2::pcg_init<float>(s, g0, w.in.x, nullptr, B, prof_for(p, KID_PCG_INIT, nn0 * 4));
-    }));
-    st = pcg_loop<float>(p, mi, w.in, B, c.inner_max_iter);
-    if (st != MLMC_OK) return st;
-    CK(run(p, KID_REFINE, [&] {
-      return d2::add_correction(s, g0, w.u, w.in.x, w.outer.scale, w.outer.active, B,
-                                prof_for(p, KID_REFINE, nn0 * (8 + 4 + 8)));
-    }));
-    CK(run(p, KID_RESID64, [&] {
-      return d2::resid64(s, g0, w.kap64, w.u, w.r, w.outer.active, w.in.part, B,
-                         prof_for(p, KID_RESID64, (2 * nn0 + ne0) * 8));
-    }));
-    CK(run(p, KID_FINALIZE, [&] {
-      return launch_outer_step(s, w.in.part, g0.tiles_s, w.outer, w.in.sc.iters, c.inner_max_iter, outer,
-                               c.outer_max_iter, B);
-    }));
-    CK(run(p, KID_COUNT, [&] { return launch_count_active(s, w.outer.active, B, w.in.count); }));
-    CK(cudaMemcpyAsync(h_count, w.in.count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    if (*h_count == 0) break;
-  }
-  st = qoi_of(p, g0, w.u, w.in.part, w.outer, q_dev, B);
+  return MLMC_OK;
+}
+
+// Before each inner solve: unit-norm FP32 right-hand side, inner scalars, d = 0, prologue.
+mlmc_status mixed_pre_inner(mlmc_plan p, const MeshInfo& mi, MixedWs& w, int64_t B) {
+  cudaStream_t s = p->stream;
+  const mlmc_config& c = p->cfg;
+  const Grid& g0 = mi.g[0];
+  const double nn0 = nodes_of(g0);
+  CK(run(p, KID_REFINE, [&] {
+    return d2::to_rhs32(s, g0, w.r, w.outer.scale, w.in.r, w.outer.active, B,
+                        prof_for(p, KID_REFINE, nn0 * (8 + 4)));
+  }));
+  CK(run(p, KID_SETUP, [&] { return launch_inner_init(s, w.in.sc, w.outer, c.inner_rtol, B); }));
+  CK(run(p, KID_PCG_INIT, [&] {
+    return d2::pcg_init<float>(s, g0, w.in.x, nullptr, B, prof_for(p, KID_PCG_INIT, nn0 * 4));
+  }));
+  return pcg_prologue<float>(p, mi, w.in, B, c.inner_max_iter);
+}
+
+// After each inner solve: u += s d, FP64 residual, outer convergence test.
+mlmc_status mixed_post_inner(mlmc_plan p, const MeshInfo& mi, MixedWs& w, int64_t B, int outer,
+                             const int32_t* outer_it_dev) {
+  cudaStream_t s = p->stream;
+  const mlmc_config& c = p->cfg;
+  const Grid& g0 = mi.g[0];
+  const double nn0 = nodes_of(g0), ne0 = elems_of(g0);
+  CK(run(p, KID_REFINE, [&] {
+    return d2::add_correction(s, g0, w.u, w.in.x, w.outer.scale, w.outer.active, B,
+                              prof_for(p, KID_REFINE, nn0 * (8 + 4 + 8)));
+  }));
+  CK(run(p, KID_RESID64, [&] {
+    return d2::resid64(s, g0, w.kap64, w.u, w.r, w.outer.active, w.in.part, B,
+                       prof_for(p, KID_RESID64, (2 * nn0 + ne0) * 8));
+  }));
+  CK(run(p, KID_FINALIZE, [&] {
+    return launch_outer_step(s, w.in.part, g0.tiles_s, w.outer, w.in.sc.iters, c.inner_max_iter,
+                             outer, c.outer_max_iter, B, outer_it_dev);
+  }));
+  return MLMC_OK;
+}
+
+mlmc_status mixed_epilogue(mlmc_plan p, const MeshInfo& mi, MixedWs& w, int64_t B, double* q_dev,
+                           int32_t* iters_dev) {
+  mlmc_status st = qoi_of(p, mi.g[0], w.u, w.in.part, w.outer, q_dev, B);
   if (st != MLMC_OK) return st;
-  if (iters_dev) CK(cudaMemcpyAsync(iters_dev, w.outer.iters, sizeof(int32_t) * B, cudaMemcpyDeviceToDevice, s));
+  if (iters_dev) CK(cudaMemcpyAsync(iters_dev, w.outer.iters, sizeof(int32_t) * B, cudaMemcpyDeviceToDevice, p->stream));
+  return MLMC_OK;
+}
+
+// Mixed form: FP64 iterative refinement around FP32 GMG/Jacobi-PCG
+// (kappa32 = rounded kappa64). w.kap64 holds kappa. Leaves u in w.u. With
+// graphs on: setup -> while_outer(pre -> while_inner(PCG) -> post) -> QoI.
+mlmc_status solve_mixed(mlmc_plan p, int mesh, const MeshInfo& mi, MixedWs& w, int64_t B,
+                        double* q_dev, int32_t* iters_dev) {
+  cudaStream_t s = p->stream;
+  const mlmc_config& c = p->cfg;
+  if (!graphs_on(p)) {
+    mlmc_status st = mixed_setup(p, mi, w, B);
+    if (st != MLMC_OK) return st;
+    if (ensure_pin(p, 64) != MLMC_OK) return MLMC_ERR_OOM;
+    int32_t* h_count = (int32_t*)p->h_pin;
+    for (int outer = 1; outer <= c.outer_max_iter; ++outer) {
+      if ((st = mixed_pre_inner(p, mi, w, B)) != MLMC_OK) return st;
+      if ((st = pcg_loop<float>(p, mi, w.in, B, c.inner_max_iter)) != MLMC_OK) return st;
+      if ((st = mixed_post_inner(p, mi, w, B, outer, nullptr)) != MLMC_OK) return st;
+      CK(run(p, KID_COUNT, [&] { return launch_count_active(s, w.outer.active, B, w.outer_count); }));
+      CK(cudaMemcpyAsync(h_count, w.outer_count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (*h_count == 0) break;
+    }
+    return mixed_epilogue(p, mi, w, B, q_dev, iters_dev);
+  }
+  const auto key = std::make_tuple(1, mesh, B, (const void*)p->ws, (const void*)w.kap64,
+                                   (const void*)q_dev, (const void*)iters_dev);
+  auto it = p->graphs.find(key);
+  if (it == p->graphs.end()) {
+    // setup -> while_outer(pre, re-arm inner, while_inner(PCG), post, outer control) -> QoI
+    GraphRec rec;
+    cudaGraph_t P = nullptr, obody = nullptr, ibody = nullptr;
+    cudaGraphConditionalHandle ho, hi;
+    int64_t l1 = 0, l2 = 0, lo = 0, nb = 0;
+    mlmc_status st = capture(p, &P, [&] {
+      const int64_t l0 = p->launches;
+      mlmc_status s2 = mixed_setup(p, mi, w, B);
+      if (s2 != MLMC_OK) return s2;
+      l1 = p->launches - l0;
+      if ((s2 = insert_while(p, &ho, &obody, false)) != MLMC_OK) return s2;
+      const int64_t l3 = p->launches;
+      s2 = mixed_epilogue(p, mi, w, B, q_dev, iters_dev);
+      l2 = p->launches - l3;
+      return s2;
+    });
+    if (st != MLMC_OK) return st;
+    st = capture(p, &obody, [&] {
+      const int64_t l0 = p->launches;
+      mlmc_status s2 = mixed_pre_inner(p, mi, w, B);
+      if (s2 != MLMC_OK) return s2;
+      cudaGraph_t g = nullptr;
+      if ((s2 = capture_graph(p, &g)) != MLMC_OK) return s2;
+      if (cudaGraphConditionalHandleCreate(&hi, g, 1, cudaGraphCondAssignDefault) != cudaSuccess)
+        return MLMC_ERR_CUDA;
+      CK(run(p, KID_SETUP, [&] { return launch_set_cond(p->stream, hi, 1u); }));
+      if ((s2 = insert_while(p, &hi, &ibody, true)) != MLMC_OK) return s2;
+      if ((s2 = mixed_post_inner(p, mi, w, B, 0, w.outer_it)) != MLMC_OK) return s2;
+      CK(run(p, KID_COUNT, [&] {
+        return launch_loop_ctl(p->stream, w.outer.active, B, w.outer_it, c.outer_max_iter,
+                               w.outer_count, w.outer_execs, ho);
+      }));
+      lo = p->launches - l0;
+      return MLMC_OK;
+    });
+    if (st == MLMC_OK)
+      st = capture(p, &ibody, [&] {
+        const int64_t l0 = p->launches;
+        mlmc_status s2 = pcg_graph_body<float>(p, mi, w.in, B, c.inner_max_iter, hi);
+        nb = p->launches - l0;
+        return s2;
+      });
+    if (st != MLMC_OK || cudaGraphInstantiate(&rec.exec, P, 0) != cudaSuccess) {
+      cudaGraphDestroy(P);
+      cudaGetLastError();
+      return st != MLMC_OK ? st : MLMC_ERR_CUDA;
+    }
+    cudaGraphDestroy(P);
+    rec.n_setup = l1;
+    rec.n_epi = l2;
+    rec.n_outer = lo;
+    rec.n_body = nb / 2;
+    it = p->graphs.emplace(key, rec).first;
+  }
+  CK(cudaGraphLaunch(it->second.exec, p->stream));
+  p->pending_graphs.emplace_back(&it->second, w.in.execs, w.outer_execs);
   return MLMC_OK;
 }
 
@@ -649,13 +982,14 @@ void mlmc_config_default(mlmc_config* c) {
   c->seed = 0;
   c->stream_id = 0;
   c->mg_smooth = 1;
-  c->mg_omega = 0.8;
+  c->mg_omega = 0.9;
   c->mg_coarsest = 2;
   c->check_every = 0;
   c->workspace_bytes = 0;
-  c->inner_rtol = 1e-5;
+  c->inner_rtol = 3e-3;
   c->inner_max_iter = 60;
-  c->outer_max_iter = 12;
+  c->outer_max_iter = 16;
+  c->use_graphs = 1;
 }
 
 int64_t mlmc_node_stride(int dim, int n) {
@@ -757,6 +1091,10 @@ mlmc_status mlmc_plan_create(const mlmc_config* cfg, void* stream, mlmc_plan* ou
     if (run(p, KID_TABLE, [&] { return launch_kle_table(p->stream, mi.n, m, p->d_omega, p->d_theta, p->d_even, mi.table); }) != cudaSuccess)
       return fail(MLMC_ERR_CUDA);
   }
+  if (cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    p->cap_stream = nullptr;
+    return fail(MLMC_ERR_CUDA);
+  }
   size_t budget = cfg->workspace_bytes;
   if (budget == 0) {
     size_t fr = 0, tot = 0;
@@ -771,7 +1109,9 @@ mlmc_status mlmc_plan_create(const mlmc_config* cfg, void* stream, mlmc_plan* ou
 
 mlmc_status mlmc_plan_destroy(mlmc_plan p) {
   if (!p) return MLMC_ERR_INVALID;
-  if (p->stream || true) cudaStreamSynchronize(p->stream);
+  cudaStreamSynchronize(p->stream);
+  clear_graphs(p);
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   for (auto& mi : p->meshes)
     if (mi.table) cudaFree(mi.table);
   cudaFree(p->d_omega);
@@ -859,14 +1199,14 @@ mlmc_status mlmc_solve(mlmc_plan p, int mesh, const double* kappa, int64_t count
       MixedWs w;
       carve_mixed(c, mi, B, w);
       CK(cudaMemcpyAsync(w.kap64, kap, sizeof(double) * B * mi.g[0].es, cudaMemcpyDeviceToDevice, p->stream));
-      st = solve_mixed(p, mi, w, B, q + off, iters ? iters + off : nullptr);
+      st = solve_mixed(p, mesh, mi, w, B, q + off, iters ? iters + off : nullptr);
       it_dev = w.outer.iters;
       x = w.u;
     } else {
       SolveWs<double> w;
       carve_solve(c, mi, B, false, w);
       w.kap[0] = const_cast<double*>(kap);
-      st = solve_fp64(p, mi, w, B, q + off, iters ? iters + off : nullptr);
+      st = solve_fp64(p, mesh, mi, w, B, q + off, iters ? iters + off : nullptr);
       it_dev = w.sc.iters;
       x = w.x;
     }
@@ -875,6 +1215,7 @@ mlmc_status mlmc_solve(mlmc_plan p, int mesh, const double* kappa, int64_t count
     if (ensure_pin(p, sizeof(int32_t) * B) != MLMC_OK) return MLMC_ERR_OOM;
     CK(cudaMemcpyAsync(p->h_pin, it_dev, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, p->stream));
     CK(cudaStreamSynchronize(p->stream));
+    if (settle_graph_launches(p) != MLMC_OK) return MLMC_ERR_CUDA;
     const int32_t* it = (const int32_t*)p->h_pin;
     for (int64_t b = 0; b < B; ++b) bad |= (it[b] < 0);
   }
@@ -913,7 +1254,7 @@ mlmc_status mlmc_sample_level(mlmc_plan p, int level, int64_t first, int64_t cou
       if (st != MLMC_OK) return st;
       double* qd = side == 0 ? w.qf : w.qc;
       int32_t* itd = side == 0 ? w.itf : w.itc;
-      st = mixed ? solve_mixed(p, mi, w.mx, B, qd, itd) : solve_fp64(p, mi, w.s, B, qd, itd);
+      st = mixed ? solve_mixed(p, mesh, mi, w.mx, B, qd, itd) : solve_fp64(p, mesh, mi, w.s, B, qd, itd);
       if (st != MLMC_OK) return st;
     }
     Carve c(p->ws);
@@ -931,6 +1272,7 @@ mlmc_status mlmc_sample_level(mlmc_plan p, int level, int64_t first, int64_t cou
     CK(cudaMemcpyAsync(hit, w.itf, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, p->stream));
     CK(cudaMemcpyAsync(hit + B, w.itc, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, p->stream));
     CK(cudaStreamSynchronize(p->stream));
+    if (settle_graph_launches(p) != MLMC_OK) return MLMC_ERR_CUDA;
     for (int64_t b = 0; b < B; ++b) {
       if (hit[b] < 0 || (level > 0 && hit[B + b] < 0)) bad = true;
       if (q_fine) q_fine[off + b] = hq[b];
@@ -1060,6 +1402,11 @@ mlmc_status mlmc_kernel_stats(mlmc_plan p, int kid, mlmc_kernel_stat* out) {
   return MLMC_OK;
 }
 
-int64_t mlmc_launch_count(mlmc_plan p) { return p ? p->launches : -1; }
+int64_t mlmc_launch_count(mlmc_plan p) {
+  if (!p) return -1;
+  cudaStreamSynchronize(p->stream);
+  settle_graph_launches(p);
+  return p->launches;
+}
 
 }  // extern "C"

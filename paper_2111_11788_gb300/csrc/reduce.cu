@@ -14,7 +14,9 @@ namespace mlmc {
 namespace {
 
 __global__ void k_finalize(int mode, const double* __restrict__ part, int64_t tiles, Scalars sc,
-                           double* __restrict__ out, int iter, int max_iter, int64_t B) {
+                           double* __restrict__ out, int iter, const int32_t* __restrict__ iter_dev,
+                           int max_iter, int64_t B) {
+  if (iter_dev) iter = *iter_dev;
   const int64_t b = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (b >= B) return;
@@ -69,6 +71,36 @@ __global__ void k_count_active(const int32_t* __restrict__ active, int64_t B, in
   if (threadIdx.x == 0) *count = s;
 }
 
+// Loop control of a graph-captured iteration: count the active samples,
+// advance the device iteration counter and set the while-condition to
+// (some sample active and the cap not reached).
+__global__ void k_loop_ctl(const int32_t* __restrict__ active, int64_t B, int32_t* it_dev,
+                           int max_iter, int32_t* count, int32_t* execs,
+                           cudaGraphConditionalHandle h) {
+  __shared__ int32_t s;
+  if (threadIdx.x == 0) s = 0;
+  __syncthreads();
+  int32_t c = 0;
+  for (int64_t b = threadIdx.x; b < B; b += blockDim.x) c += active[b] ? 1 : 0;
+  atomicAdd(&s, c);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int32_t it = *it_dev;
+    *count = s;
+    *it_dev = it + 1;
+    if (execs) *execs += 1;
+    cudaGraphSetConditional(h, (s > 0 && it < max_iter) ? 1u : 0u);
+  }
+}
+
+__global__ void k_set_cond(cudaGraphConditionalHandle h, unsigned v) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(h, v);
+}
+
+__global__ void k_set_int(int32_t* p, int32_t v) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *p = v;
+}
+
 __global__ void k_scalars_init(Scalars sc, double tol, double scale0, int64_t B) {
   const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
@@ -84,7 +116,8 @@ __global__ void k_scalars_init(Scalars sc, double tol, double scale0, int64_t B)
 
 __global__ void k_outer_step(const double* __restrict__ part, int64_t tiles, Scalars so,
                              const int32_t* __restrict__ inner_iters, int inner_max, int outer_it,
-                             int outer_max, int64_t B) {
+                             const int32_t* __restrict__ outer_it_dev, int outer_max, int64_t B) {
+  if (outer_it_dev) outer_it = *outer_it_dev;
   const int64_t b = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (b >= B || !so.active[b]) return;
@@ -173,15 +206,33 @@ __global__ void k_allocate(const double* V, const double* C, int L, double eps, 
 }  // namespace
 
 cudaError_t launch_finalize(cudaStream_t s, FinMode mode, const double* part, int64_t tiles,
-                            const Scalars& sc, double* out, int iter, int max_iter, int64_t B) {
+                            const Scalars& sc, double* out, int iter, int max_iter, int64_t B,
+                            const int32_t* iter_dev) {
   const int warps = 8;
   k_finalize<<<(unsigned)((B + warps - 1) / warps), warps * 32, 0, s>>>(mode, part, tiles, sc, out,
-                                                                      iter, max_iter, B);
+                                                                      iter, iter_dev, max_iter, B);
   return cudaGetLastError();
 }
 
 cudaError_t launch_count_active(cudaStream_t s, const int32_t* active, int64_t B, int32_t* count) {
   k_count_active<<<1, 256, 0, s>>>(active, B, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loop_ctl(cudaStream_t s, const int32_t* active, int64_t B, int32_t* it_dev,
+                            int max_iter, int32_t* count, int32_t* execs,
+                            cudaGraphConditionalHandle h) {
+  k_loop_ctl<<<1, 256, 0, s>>>(active, B, it_dev, max_iter, count, execs, h);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_cond(cudaStream_t s, cudaGraphConditionalHandle h, unsigned v) {
+  k_set_cond<<<1, 32, 0, s>>>(h, v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_int(cudaStream_t s, int32_t* p, int32_t v) {
+  k_set_int<<<1, 32, 0, s>>>(p, v);
   return cudaGetLastError();
 }
 
@@ -193,10 +244,10 @@ cudaError_t launch_scalars_init(cudaStream_t s, const Scalars& sc, double tol, d
 
 cudaError_t launch_outer_step(cudaStream_t s, const double* part, int64_t tiles,
                               const Scalars& outer, const int32_t* inner_iters, int inner_max,
-                              int outer_it, int outer_max, int64_t B) {
+                              int outer_it, int outer_max, int64_t B, const int32_t* outer_it_dev) {
   const int warps = 8;
   k_outer_step<<<(unsigned)((B + warps - 1) / warps), warps * 32, 0, s>>>(
-      part, tiles, outer, inner_iters, inner_max, outer_it, outer_max, B);
+      part, tiles, outer, inner_iters, inner_max, outer_it, outer_it_dev, outer_max, B);
   return cudaGetLastError();
 }
 

@@ -53,6 +53,7 @@ class Config(ctypes.Structure):
         ("inner_rtol", ctypes.c_double),
         ("inner_max_iter", ctypes.c_int32),
         ("outer_max_iter", ctypes.c_int32),
+        ("use_graphs", ctypes.c_int32),
     ]
 
 
@@ -147,7 +148,8 @@ def _dp(arr):
 def config(dim=2, n_levels=3, coarse_cells=16, modes_per_dim=4, sigma2=1.0, corr_len=0.3,
            qoi="domain", solver="jacobi", box=(0.25, 0.75), rtol=1e-10, max_iter=None,
            precision="fp64", seed=0, stream_id=0, mg_omega=None, check_every=0,
-           workspace_bytes=0, inner_rtol=None, inner_max_iter=None, outer_max_iter=None):
+           workspace_bytes=0, inner_rtol=None, inner_max_iter=None, outer_max_iter=None,
+           use_graphs=None):
     """Build a Config from plain values (defaults from mlmc_config_default)."""
     c = Config()
     lib().mlmc_config_default(ctypes.byref(c))
@@ -173,6 +175,8 @@ def config(dim=2, n_levels=3, coarse_cells=16, modes_per_dim=4, sigma2=1.0, corr
         c.inner_max_iter = inner_max_iter
     if outer_max_iter is not None:
         c.outer_max_iter = outer_max_iter
+    if use_graphs is not None:
+        c.use_graphs = int(use_graphs)
     return c
 
 

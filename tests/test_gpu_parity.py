@@ -282,3 +282,40 @@ def test_adaptive_run_reaches_tolerance(m):
         ref.append(st)
     qref, _ = omlmc.estimate(ref)
     assert abs(q - qref) <= RTOL_Q * abs(qref)
+
+
+# ------------------------------------------- graph-driven vs host-driven
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("solver", ["gmg", "jacobi"])
+def test_graph_and_host_driven_solves_agree_bitwise(m, precision, solver):
+    """The CUDA-graph solve (device while-loops) equals the host-driven loop bit for bit."""
+    wl = small_case(2, n0=8, levels=3, m=4, solver=solver, precision=precision)
+    res = []
+    for graphs in (0, 1):
+        cfg = m.config_from_workload(wl, use_graphs=graphs)
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            with m.Plan(cfg, s.cuda_stream) as plan:
+                out = [plan.sample_level(l, 0, 7) for l in range(3)]
+                out.append(plan.sample_level(2, 7, 5))       # second call reuses the cached graph
+                stats = [plan.level_stats(l) for l in range(3)]
+                launches = plan.launch_count()
+        res.append((out, stats, launches))
+    (oa, sa, la), (ob, sb, lb) = res
+    for (qa, ca, ia), (qb, cb, ib) in zip(oa, ob):
+        assert np.array_equal(qa, qb) and np.array_equal(ca, cb) and np.array_equal(ia, ib)
+    assert sa == sb
+    # the graph path executes every body kernel of the converged iterations plus
+    # at most one trailing no-op iteration, so its kernel count is close to the host loop's
+    assert lb > 0 and la > 0 and lb < 2 * la
+
+
+def test_graph_solve_on_legacy_default_stream(m):
+    wl = small_case(2, n0=8, levels=2, m=4, solver="gmg")
+    cfg = m.config_from_workload(wl, use_graphs=1)
+    with m.Plan(cfg, 0) as plan:
+        qf, qc, it = plan.sample_level(1, 0, 4)
+    ref = [omlmc.coupled_sample(wl, 1, i) for i in range(4)]
+    for s in range(4):
+        assert abs(qf[s] - ref[s][0]) <= RTOL_Q * abs(ref[s][0])
