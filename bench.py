@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--form", default="fp64", choices=["fp64", "mixed"],
                     help="form of the headline line (the other form is measured alongside)")
     ap.add_argument("--single-form", action="store_true")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="host-driven solver loops (same kernels; ncu cannot profile kernels "
+                         "inside graphs with conditional nodes)")
     return ap.parse_args()
 
 
@@ -361,7 +364,7 @@ def profile_case(args):
     build_library()
     import paper_2111_11788_gb300.mlmc as m
     wl = workload(args.workload)
-    cfg = m.config_from_workload(wl, precision=args.form)
+    cfg = m.config_from_workload(wl, precision=args.form, use_graphs=0 if args.no_graphs else 1)
     with m.Plan(cfg, torch.cuda.current_stream().cuda_stream) as plan:
         for rep in range(2):
             plan.sample_level(args.profile_level, rep * args.profile_batch, args.profile_batch,
