@@ -47,7 +47,7 @@ def solve_qoi(cfg, mesh, xi):
     kap = kle.kappa(d, n, cfg['corr_len'], cfg['sigma2'], cfg['m'], xi)[0]
     A = fem.assemble_fast(d, n, kap)
     b = fem.load_vector(d, n)
-    u = fem.solve_direct(A, b)
+    u = fem.solve(A, b, d)
     w = fem.qoi_weights(d, n, cfg.get('qoi', 'domain'), tuple(cfg.get('box', (0.25, 0.75))))
     return float(w @ u)
 

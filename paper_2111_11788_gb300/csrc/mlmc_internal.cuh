@@ -173,6 +173,114 @@ cudaError_t add_correction(cudaStream_t s, const Grid& g, double* u, const float
 }  // namespace d2
 
 // iter_dev (may be null) overrides iter with a device-side iteration counter.
+// 3D operator / PCG / multigrid kernels (stencil3d.cu); the pointwise PCG
+// kernels (pcg_xr, jacobi_z, to_rhs32, add_correction) are the flat d2 ones.
+namespace d3 {
+template <class T>
+cudaError_t apply(cudaStream_t s, const Grid& g, const T* kappa, const T* x, T* y, int64_t B, Prof p);
+template <class T>
+cudaError_t winv(cudaStream_t s, const Grid& g, const T* kappa, double omega, T* w, int64_t B);
+template <class T>
+cudaError_t pcg_init(cudaStream_t s, const Grid& g, T* x, T* r, int64_t B, Prof p);
+template <class T>
+cudaError_t pcg_pq(cudaStream_t s, const Grid& g, const T* kappa, const T* z, const T* p_old,
+                   T* p_new, T* q, const Scalars& sc, double* part, int64_t B, Prof p);
+template <class T>
+cudaError_t mg_pre(cudaStream_t s, const Grid& g, const T* kappa, const T* w, const T* b, T* e,
+                   T* r1, const int32_t* active, int64_t B, Prof p);
+template <class T>
+cudaError_t restrict_(cudaStream_t s, const Grid& fine, const Grid& coarse, const T* r1, T* bc,
+                      const int32_t* active, int64_t B, Prof p);
+template <class T>
+cudaError_t coarse_solve(cudaStream_t s, const Grid& g, const T* kappa, const T* b, T* e,
+                         const int32_t* active, int64_t B);
+template <class T>
+cudaError_t mg_post(cudaStream_t s, const Grid& g, const Grid& coarse, const T* kappa, const T* w,
+                    const T* b, const T* e, const T* ec, T* out, const int32_t* active,
+                    double* part, int64_t B, Prof p);
+template <class T>
+cudaError_t qoi(cudaStream_t s, const Grid& g, int box, int L, int H, double inv_vol, const T* x,
+                double* part, int64_t B, Prof p);
+cudaError_t resid64(cudaStream_t s, const Grid& g, const double* kappa, const double* u,
+                    double* r, const int32_t* active, double* part, int64_t B, Prof p);
+}  // namespace d3
+
+// Dimension dispatch used by the plan.
+namespace op {
+template <class T>
+inline cudaError_t apply(cudaStream_t s, const Grid& g, const T* kappa, const T* x, T* y, int64_t B, Prof p) {
+  return g.dim == 2 ? d2::apply<T>(s, g, kappa, x, y, B, p) : d3::apply<T>(s, g, kappa, x, y, B, p);
+}
+template <class T>
+inline cudaError_t winv(cudaStream_t s, const Grid& g, const T* kappa, double omega, T* w, int64_t B) {
+  return g.dim == 2 ? d2::winv<T>(s, g, kappa, omega, w, B) : d3::winv<T>(s, g, kappa, omega, w, B);
+}
+template <class T>
+inline cudaError_t pcg_init(cudaStream_t s, const Grid& g, T* x, T* r, int64_t B, Prof p) {
+  return g.dim == 2 ? d2::pcg_init<T>(s, g, x, r, B, p) : d3::pcg_init<T>(s, g, x, r, B, p);
+}
+template <class T>
+inline cudaError_t pcg_pq(cudaStream_t s, const Grid& g, const T* kappa, const T* z, const T* p_old,
+                          T* p_new, T* q, const Scalars& sc, double* part, int64_t B, Prof p) {
+  return g.dim == 2 ? d2::pcg_pq<T>(s, g, kappa, z, p_old, p_new, q, sc, part, B, p)
+                    : d3::pcg_pq<T>(s, g, kappa, z, p_old, p_new, q, sc, part, B, p);
+}
+template <class T>
+inline cudaError_t pcg_xr(cudaStream_t s, const Grid& g, T* x, const T* pv, T* r, const T* q,
+                          const Scalars& sc, double* part, int64_t B, Prof p) {
+  return d2::pcg_xr<T>(s, g, x, pv, r, q, sc, part, B, p);
+}
+template <class T>
+inline cudaError_t jacobi_z(cudaStream_t s, const Grid& g, const T* winv, const T* r, T* z,
+                            const Scalars& sc, double* part, int64_t B, Prof p) {
+  return d2::jacobi_z<T>(s, g, winv, r, z, sc, part, B, p);
+}
+template <class T>
+inline cudaError_t mg_pre(cudaStream_t s, const Grid& g, const T* kappa, const T* w, const T* b, T* e,
+                          T* r1, const int32_t* active, int64_t B, Prof p) {
+  return g.dim == 2 ? d2::mg_pre<T>(s, g, kappa, w, b, e, r1, active, B, p)
+                    : d3::mg_pre<T>(s, g, kappa, w, b, e, r1, active, B, p);
+}
+template <class T>
+inline cudaError_t restrict_(cudaStream_t s, const Grid& fine, const Grid& coarse, const T* r1, T* bc,
+                             const int32_t* active, int64_t B, Prof p) {
+  return fine.dim == 2 ? d2::restrict_<T>(s, fine, coarse, r1, bc, active, B, p)
+                       : d3::restrict_<T>(s, fine, coarse, r1, bc, active, B, p);
+}
+template <class T>
+inline cudaError_t coarse_solve(cudaStream_t s, const Grid& g, const T* kappa, const T* b, T* e,
+                                const int32_t* active, int64_t B) {
+  return g.dim == 2 ? d2::coarse_solve<T>(s, g, kappa, b, e, active, B)
+                    : d3::coarse_solve<T>(s, g, kappa, b, e, active, B);
+}
+template <class T>
+inline cudaError_t mg_post(cudaStream_t s, const Grid& g, const Grid& coarse, const T* kappa, const T* w,
+                           const T* b, const T* e, const T* ec, T* out, const int32_t* active,
+                           double* part, int64_t B, Prof p) {
+  return g.dim == 2 ? d2::mg_post<T>(s, g, coarse, kappa, w, b, e, ec, out, active, part, B, p)
+                    : d3::mg_post<T>(s, g, coarse, kappa, w, b, e, ec, out, active, part, B, p);
+}
+template <class T>
+inline cudaError_t qoi(cudaStream_t s, const Grid& g, int box, int L, int H, double inv_vol, const T* x,
+                       double* part, int64_t B, Prof p) {
+  return g.dim == 2 ? d2::qoi<T>(s, g, box, L, H, inv_vol, x, part, B, p)
+                    : d3::qoi<T>(s, g, box, L, H, inv_vol, x, part, B, p);
+}
+inline cudaError_t resid64(cudaStream_t s, const Grid& g, const double* kappa, const double* u,
+                           double* r, const int32_t* active, double* part, int64_t B, Prof p) {
+  return g.dim == 2 ? d2::resid64(s, g, kappa, u, r, active, part, B, p)
+                    : d3::resid64(s, g, kappa, u, r, active, part, B, p);
+}
+inline cudaError_t to_rhs32(cudaStream_t s, const Grid& g, const double* r, const double* scale,
+                            float* r32, const int32_t* active, int64_t B, Prof p) {
+  return d2::to_rhs32(s, g, r, scale, r32, active, B, p);
+}
+inline cudaError_t add_correction(cudaStream_t s, const Grid& g, double* u, const float* d32,
+                                  const double* scale, const int32_t* active, int64_t B, Prof p) {
+  return d2::add_correction(s, g, u, d32, scale, active, B, p);
+}
+}  // namespace op
+
 cudaError_t launch_finalize(cudaStream_t s, FinMode mode, const double* part, int64_t tiles,
                             const Scalars& sc, double* out, int iter, int max_iter, int64_t B,
                             const int32_t* iter_dev = nullptr);

@@ -25,10 +25,17 @@ Grid make_grid(int dim, int n) {
   g.ns = round_up(ipow(n + 1, dim), 32);
   g.es = round_up(ipow(n, dim), 32);
   g.h = 1.0 / n;
-  const int strips = (n + 1 + 29) / 30;
-  g.sx = (strips + SWARPS - 1) / SWARPS;
-  g.sy = (n + 1 + SROWS - 1) / SROWS;
-  g.tiles_s = (int64_t)g.sx * g.sy * SWARPS;
+  if (dim == 2) {
+    const int strips = (n + 1 + 29) / 30;
+    g.sx = (strips + SWARPS - 1) / SWARPS;
+    g.sy = (n + 1 + SROWS - 1) / SROWS;
+    g.tiles_s = (int64_t)g.sx * g.sy * SWARPS;
+  } else {
+    // one CTA per 32 x 8 node tile of each z-plane, one partial per CTA
+    g.sx = ((n + 1 + 31) / 32) * ((n + 1 + 7) / 8) * (n + 1);
+    g.sy = 1;
+    g.tiles_s = g.sx;
+  }
   g.fx = (int)((g.ns + FLAT_ELEMS - 1) / FLAT_ELEMS);
   g.tiles_f = g.fx;
   return g;
@@ -272,7 +279,6 @@ mlmc_status validate(const mlmc_config* c) {
   if (c->precision == MLMC_MIXED &&
       (!(c->inner_rtol > 0.0 && c->inner_rtol < 1.0) || c->inner_max_iter < 1 || c->outer_max_iter < 1))
     return MLMC_ERR_INVALID;
-  if (c->dim == 3) return MLMC_ERR_UNIMPLEMENTED;
   return MLMC_OK;
 }
 
@@ -460,7 +466,7 @@ mlmc_status precondition(mlmc_plan p, const MeshInfo& mi, SolveWs<T>& w, int64_t
   const double nn0 = nodes_of(g0);
   if (mi.K == 1) {
     CK(run(p, KID_JACOBI_Z, [&] {
-      return d2::jacobi_z<T>(s, g0, w.w[0], w.r, w.z, w.sc, w.part, B,
+      return op::jacobi_z<T>(s, g0, w.w[0], w.r, w.z, w.sc, w.part, B,
                              prof_for(p, KID_JACOBI_Z, 3 * nn0 * vb));
     }));
     *tiles = g0.tiles_f;
@@ -471,22 +477,22 @@ mlmc_status precondition(mlmc_plan p, const MeshInfo& mi, SolveWs<T>& w, int64_t
     const Grid& g = mi.g[k];
     const double nn = nodes_of(g), ne = elems_of(g);
     CK(run(p, KID_MG_PRE, [&] {
-      return d2::mg_pre<T>(s, g, w.kap[k], w.w[k], w.bk[k], w.e[k], w.r1[k], w.sc.active, B,
+      return op::mg_pre<T>(s, g, w.kap[k], w.w[k], w.bk[k], w.e[k], w.r1[k], w.sc.active, B,
                            prof_for(p, KID_MG_PRE, (4 * nn + ne) * vb));
     }));
     CK(run(p, KID_RESTRICT, [&] {
-      return d2::restrict_<T>(s, g, mi.g[k + 1], w.r1[k], w.bk[k + 1], w.sc.active, B,
+      return op::restrict_<T>(s, g, mi.g[k + 1], w.r1[k], w.bk[k + 1], w.sc.active, B,
                               prof_for(p, KID_RESTRICT, (nn + nodes_of(mi.g[k + 1])) * vb));
     }));
   }
   CK(run(p, KID_COARSE, [&] {
-    return d2::coarse_solve<T>(s, mi.g[K - 1], w.kap[K - 1], w.bk[K - 1], w.e[K - 1], w.sc.active, B);
+    return op::coarse_solve<T>(s, mi.g[K - 1], w.kap[K - 1], w.bk[K - 1], w.e[K - 1], w.sc.active, B);
   }));
   for (int k = K - 2; k >= 0; --k) {
     const Grid& g = mi.g[k];
     const double nn = nodes_of(g), ne = elems_of(g), nc = nodes_of(mi.g[k + 1]);
     CK(run(p, KID_MG_POST, [&] {
-      return d2::mg_post<T>(s, g, mi.g[k + 1], w.kap[k], w.w[k], w.bk[k], w.e[k], w.eo[k + 1],
+      return op::mg_post<T>(s, g, mi.g[k + 1], w.kap[k], w.w[k], w.bk[k], w.e[k], w.eo[k + 1],
                             w.eo[k], w.sc.active, k == 0 ? w.part : nullptr, B,
                             prof_for(p, KID_MG_POST, (4 * nn + ne + nc) * vb));
     }));
@@ -509,7 +515,7 @@ mlmc_status setup_levels(mlmc_plan p, const MeshInfo& mi, SolveWs<T>& w, int64_t
   }
   const double omega = (K > 1) ? p->cfg.mg_omega : 1.0;
   for (int k = 0; k < std::max(1, K - 1); ++k)
-    CK(run(p, KID_SETUP, [&] { return d2::winv<T>(s, mi.g[k], w.kap[k], omega, w.w[k], B); }));
+    CK(run(p, KID_SETUP, [&] { return op::winv<T>(s, mi.g[k], w.kap[k], omega, w.w[k], B); }));
   return MLMC_OK;
 }
 
@@ -536,12 +542,12 @@ mlmc_status pcg_iteration(mlmc_plan p, const MeshInfo& mi, SolveWs<T>& w, int64_
   const double nn0 = nodes_of(g0), ne0 = elems_of(g0);
   const int32_t* itd = h ? w.it : nullptr;
   CK(run(p, KID_PCG_PQ, [&] {
-    return d2::pcg_pq<T>(s, g0, w.kap[0], w.z, pold, pnew, w.q, w.sc, w.part, B,
+    return op::pcg_pq<T>(s, g0, w.kap[0], w.z, pold, pnew, w.q, w.sc, w.part, B,
                          prof_for(p, KID_PCG_PQ, (4 * nn0 + ne0) * vb));
   }));
   CK(run(p, KID_FINALIZE, [&] { return launch_finalize(s, FIN_ALPHA, w.part, g0.tiles_s, w.sc, nullptr, it, max_iter, B, itd); }));
   CK(run(p, KID_PCG_XR, [&] {
-    return d2::pcg_xr<T>(s, g0, w.x, pnew, w.r, w.q, w.sc, w.part, B,
+    return op::pcg_xr<T>(s, g0, w.x, pnew, w.r, w.q, w.sc, w.part, B,
                          prof_for(p, KID_PCG_XR, 6 * nn0 * vb));
   }));
   CK(run(p, KID_FINALIZE, [&] { return launch_finalize(s, FIN_CONV, w.part, g0.tiles_f, w.sc, nullptr, it, max_iter, B, itd); }));
@@ -707,10 +713,12 @@ mlmc_status qoi_of(mlmc_plan p, const Grid& g0, const double* u, double* part, c
   const double vol = std::pow(c.box_hi - c.box_lo, c.dim);
   const int box = (c.qoi == MLMC_QOI_BOX_MEAN) ? 1 : 0;
   CK(run(p, KID_QOI, [&] {
-    return d2::qoi<double>(p->stream, g0, box, L, H, box ? 1.0 / vol : 1.0, u, part, B,
+    return op::qoi<double>(p->stream, g0, box, L, H, box ? 1.0 / vol : 1.0, u, part, B,
                            prof_for(p, KID_QOI, nodes_of(g0) * 8));
   }));
-  CK(run(p, KID_FINALIZE, [&] { return launch_finalize(p->stream, FIN_QOI, part, g0.tiles_f, sc, q_dev, 0, c.max_iter, B); }));
+  // the 2D QoI kernel is flat (one partial per flat CTA), the 3D one tiled
+  const int64_t tq = g0.dim == 2 ? g0.tiles_f : g0.tiles_s;
+  CK(run(p, KID_FINALIZE, [&] { return launch_finalize(p->stream, FIN_QOI, part, tq, sc, q_dev, 0, c.max_iter, B); }));
   return MLMC_OK;
 }
 
@@ -724,7 +732,7 @@ mlmc_status fp64_setup(mlmc_plan p, const MeshInfo& mi, SolveWs<double>& w, int6
   CK(run(p, KID_SETUP, [&] { return launch_scalars_init(s, w.sc, c.rtol * b_norm(c, g0), 0.0, B); }));
   CK(run(p, KID_SETUP, [&] { return launch_set_int(s, w.execs, 0); }));
   CK(run(p, KID_PCG_INIT, [&] {
-    return d2::pcg_init<double>(s, g0, w.x, w.r, B, prof_for(p, KID_PCG_INIT, 2 * nodes_of(g0) * 8));
+    return op::pcg_init<double>(s, g0, w.x, w.r, B, prof_for(p, KID_PCG_INIT, 2 * nodes_of(g0) * 8));
   }));
   return pcg_prologue<double>(p, mi, w, B, c.max_iter);
 }
@@ -808,7 +816,7 @@ mlmc_status mixed_setup(mlmc_plan p, const MeshInfo& mi, MixedWs& w, int64_t B) 
   CK(run(p, KID_SETUP, [&] { return launch_set_int(s, w.outer_execs, 0); }));
   CK(run(p, KID_SETUP, [&] { return launch_set_int(s, w.in.execs, 0); }));
   CK(run(p, KID_PCG_INIT, [&] {
-    return d2::pcg_init<double>(s, g0, w.u, w.r, B, prof_for(p, KID_PCG_INIT, 2 * nodes_of(g0) * 8));
+    return op::pcg_init<double>(s, g0, w.u, w.r, B, prof_for(p, KID_PCG_INIT, 2 * nodes_of(g0) * 8));
   }));
   return MLMC_OK;
 }
@@ -820,12 +828,12 @@ mlmc_status mixed_pre_inner(mlmc_plan p, const MeshInfo& mi, MixedWs& w, int64_t
   const Grid& g0 = mi.g[0];
   const double nn0 = nodes_of(g0);
   CK(run(p, KID_REFINE, [&] {
-    return d2::to_rhs32(s, g0, w.r, w.outer.scale, w.in.r, w.outer.active, B,
+    return op::to_rhs32(s, g0, w.r, w.outer.scale, w.in.r, w.outer.active, B,
                         prof_for(p, KID_REFINE, nn0 * (8 + 4)));
   }));
   CK(run(p, KID_SETUP, [&] { return launch_inner_init(s, w.in.sc, w.outer, c.inner_rtol, B); }));
   CK(run(p, KID_PCG_INIT, [&] {
-    return d2::pcg_init<float>(s, g0, w.in.x, nullptr, B, prof_for(p, KID_PCG_INIT, nn0 * 4));
+    return op::pcg_init<float>(s, g0, w.in.x, nullptr, B, prof_for(p, KID_PCG_INIT, nn0 * 4));
   }));
   return pcg_prologue<float>(p, mi, w.in, B, c.inner_max_iter);
 }
@@ -838,11 +846,11 @@ mlmc_status mixed_post_inner(mlmc_plan p, const MeshInfo& mi, MixedWs& w, int64_
   const Grid& g0 = mi.g[0];
   const double nn0 = nodes_of(g0), ne0 = elems_of(g0);
   CK(run(p, KID_REFINE, [&] {
-    return d2::add_correction(s, g0, w.u, w.in.x, w.outer.scale, w.outer.active, B,
+    return op::add_correction(s, g0, w.u, w.in.x, w.outer.scale, w.outer.active, B,
                               prof_for(p, KID_REFINE, nn0 * (8 + 4 + 8)));
   }));
   CK(run(p, KID_RESID64, [&] {
-    return d2::resid64(s, g0, w.kap64, w.u, w.r, w.outer.active, w.in.part, B,
+    return op::resid64(s, g0, w.kap64, w.u, w.r, w.outer.active, w.in.part, B,
                        prof_for(p, KID_RESID64, (2 * nn0 + ne0) * 8));
   }));
   CK(run(p, KID_FINALIZE, [&] {
@@ -1172,7 +1180,7 @@ mlmc_status mlmc_apply(mlmc_plan p, int mesh, const double* kappa, const double*
   for (int64_t off = 0; off < count; off += 65535) {
     const int64_t B = std::min<int64_t>(65535, count - off);
     CK(run(p, KID_APPLY, [&] {
-      return d2::apply(p->stream, g, kappa + off * g.es, x + off * g.ns, y + off * g.ns, B,
+      return op::apply(p->stream, g, kappa + off * g.es, x + off * g.ns, y + off * g.ns, B,
                        prof_for(p, KID_APPLY, (2 * nodes_of(g) + elems_of(g)) * 8));
     }));
   }

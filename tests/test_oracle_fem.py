@@ -171,3 +171,15 @@ def test_cg_qoi_is_monotone_energy_error():
     qs, gaps = np.array(qs), np.array(gaps)
     assert np.all(np.diff(qs) >= -4 * np.finfo(float).eps * qs[-1])   # up to rounding
     assert np.allclose(b @ u - qs, gaps, rtol=1e-6, atol=8 * np.finfo(float).eps * qs[-1])
+
+
+def test_solve_dispatch_pcg_branch_matches_direct():
+    """fem.solve switches to Jacobi-PCG (rtol 1e-13) on large 3D meshes; both branches agree."""
+    n = 12
+    kap = random_element_field(3, n, 1, seed=21)[0]
+    A = fem.assemble_fast(3, n, kap)
+    b = fem.load_vector(3, n)
+    u_lu = fem.solve_direct(A, b)
+    u_cg = fem.pcg_jacobi(A, b, rtol=1e-13)[0]
+    assert np.abs(u_cg - u_lu).max() <= 1e-11 * np.abs(u_lu).max()
+    assert np.array_equal(fem.solve(A, b, 3), u_lu)          # small: the LU branch
