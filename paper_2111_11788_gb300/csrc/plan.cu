@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <tuple>
 #include <vector>
@@ -196,7 +197,17 @@ struct PendingEvent {
 // launch counter: setup + body * executions + epilogue).
 struct GraphRec {
   cudaGraphExec_t exec = nullptr;
-  int64_t n_setup = 0, n_body = 0, n_outer = 0, n_epi = 0;
+  int64_t n_static = 0;   // kernels outside every loop
+  // per loop: device count of loop-control calls and kernels per call
+  std::vector<std::pair<int32_t*, int64_t>> loops;
+};
+
+// A loop body to be captured after the graph that contains its while-node.
+struct Deferred {
+  cudaGraph_t body;
+  std::function<mlmc_status()> fill;
+  int32_t* execs;   // incremented by the loop control kernel(s) of the body
+  int halves;       // loop-control calls per body execution
 };
 
 namespace mlmc {
@@ -237,9 +248,15 @@ struct mlmc_plan_s {
   // graph-captured solves, keyed by (form, mesh, batch, workspace)
   std::map<std::tuple<int, int, int64_t, const void*, const void*, const void*, const void*>,
            struct GraphRec> graphs;
+  // whole allocation rounds (one branch per level), keyed by form, batch
+  // counts and first sample indices
+  std::map<std::vector<int64_t>, struct GraphRec> round_graphs;
+  std::vector<struct Deferred>* todo = nullptr;      // set while a graph is built
+  std::vector<cudaStream_t> branch;                  // capture streams of round branches
+  std::vector<cudaEvent_t> branch_ev;
   cudaStream_t cap_stream = nullptr;   // private stream the solve graphs are captured on
   // executed graphs whose kernel counts are settled at the next sync point
-  std::vector<std::tuple<const GraphRec*, int32_t*, int32_t*>> pending_graphs;
+  std::vector<const GraphRec*> pending_graphs;
 };
 
 namespace {
@@ -619,7 +636,7 @@ struct CaptureStream {
 
 // Runs f while capturing into `graph` (new graph if *graph == nullptr).
 template <class F>
-mlmc_status capture(mlmc_plan p, cudaGraph_t* graph, F&& f) {
+mlmc_status capture(mlmc_plan p, cudaGraph_t* graph, F&& f, int64_t* nk = nullptr) {
   CaptureStream cs(p);
   const int64_t l0 = p->launches;
   cudaError_t e = (*graph == nullptr)
@@ -630,6 +647,7 @@ mlmc_status capture(mlmc_plan p, cudaGraph_t* graph, F&& f) {
   mlmc_status st = f();
   cudaGraph_t g = *graph;
   e = cudaStreamEndCapture(p->stream, &g);
+  if (nk) *nk = p->launches - l0;
   p->launches = l0;   // captured launches are counted when the graph executes
   if (st != MLMC_OK || e != cudaSuccess) {
     if (g && *graph == nullptr) cudaGraphDestroy(g);
@@ -681,18 +699,66 @@ mlmc_status insert_while(mlmc_plan p, cudaGraphConditionalHandle* h, cudaGraph_t
 void clear_graphs(mlmc_plan p) {
   for (auto& kv : p->graphs)
     if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  for (auto& kv : p->round_graphs)
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
   p->graphs.clear();
+  p->round_graphs.clear();
   p->pending_graphs.clear();
+}
+
+// Inserts a while-node (see insert_while) whose body is captured later by
+// build_graph through body_fn(handle). With `given`, that handle is used.
+template <class F>
+mlmc_status issue_loop(mlmc_plan p, int32_t* execs, int halves, F body_fn,
+                       const cudaGraphConditionalHandle* given = nullptr) {
+  cudaGraphConditionalHandle h;
+  if (given) h = *given;
+  cudaGraph_t body = nullptr;
+  mlmc_status st = insert_while(p, &h, &body, given != nullptr);
+  if (st != MLMC_OK) return st;
+  if (!p->todo) return MLMC_ERR_CUDA;
+  p->todo->push_back(Deferred{body, [h, body_fn]() mutable { return body_fn(h); }, execs, halves});
+  return MLMC_OK;
+}
+
+// Captures issue() into a new graph, then every loop body it (recursively)
+// deferred, and instantiates it.
+mlmc_status build_graph(mlmc_plan p, const std::function<mlmc_status()>& issue, GraphRec* out) {
+  std::vector<Deferred> todo;
+  p->todo = &todo;
+  GraphRec rec;
+  cudaGraph_t P = nullptr;
+  mlmc_status st = capture(p, &P, issue, &rec.n_static);
+  for (size_t i = 0; st == MLMC_OK && i < todo.size(); ++i) {
+    Deferred d = todo[i];
+    int64_t nk = 0;
+    st = capture(p, &d.body, d.fill, &nk);
+    rec.loops.emplace_back(d.execs, nk / d.halves);
+  }
+  p->todo = nullptr;
+  if (st != MLMC_OK) {
+    if (P) cudaGraphDestroy(P);
+    return st;
+  }
+  if (cudaGraphInstantiate(&rec.exec, P, 0) != cudaSuccess) {
+    cudaGraphDestroy(P);
+    cudaGetLastError();
+    return MLMC_ERR_CUDA;
+  }
+  cudaGraphDestroy(P);
+  *out = rec;
+  return MLMC_OK;
 }
 
 // Adds the kernels executed by graphs launched since the last sync point.
 mlmc_status settle_graph_launches(mlmc_plan p) {
-  for (auto& t : p->pending_graphs) {
-    const GraphRec* r = std::get<0>(t);
-    int32_t ex[2] = {0, 0};
-    CK(cudaMemcpy(&ex[0], std::get<1>(t), sizeof(int32_t), cudaMemcpyDeviceToHost));
-    if (std::get<2>(t)) CK(cudaMemcpy(&ex[1], std::get<2>(t), sizeof(int32_t), cudaMemcpyDeviceToHost));
-    p->launches += r->n_setup + r->n_epi + (int64_t)ex[0] * r->n_body + (int64_t)ex[1] * r->n_outer;
+  for (const GraphRec* r : p->pending_graphs) {
+    p->launches += r->n_static;
+    for (const auto& lp : r->loops) {
+      int32_t ex = 0;
+      CK(cudaMemcpy(&ex, lp.first, sizeof(int32_t), cudaMemcpyDeviceToHost));
+      p->launches += (int64_t)ex * lp.second;
+    }
   }
   p->pending_graphs.clear();
   return MLMC_OK;
@@ -745,6 +811,22 @@ mlmc_status fp64_epilogue(mlmc_plan p, const MeshInfo& mi, SolveWs<double>& w, i
   return MLMC_OK;
 }
 
+// FP64 solve issued into the graph being captured: setup -> while(two PCG
+// iterations + loop control) -> QoI epilogue.
+mlmc_status issue_fp64(mlmc_plan p, const MeshInfo& mi, SolveWs<double>& w, int64_t B,
+                       double* q_dev, int32_t* iters_dev) {
+  mlmc_status st = fp64_setup(p, mi, w, B);
+  if (st != MLMC_OK) return st;
+  const MeshInfo* mip = &mi;
+  SolveWs<double> wc = w;   // copied into the deferred body (mutable lambda)
+  const int maxit = p->cfg.max_iter;
+  st = issue_loop(p, w.execs, 2, [p, mip, wc, B, maxit](cudaGraphConditionalHandle h) mutable {
+    return pcg_graph_body<double>(p, *mip, wc, B, maxit, h);
+  });
+  if (st != MLMC_OK) return st;
+  return fp64_epilogue(p, mi, w, B, q_dev, iters_dev);
+}
+
 // FP64 form: solve A(kappa) u = b for B samples; w.kap[0] holds kappa.
 // Leaves u in w.x, writes q (device) and iters (device). With graphs on,
 // the whole solve is one graph: setup -> while(two PCG iterations) -> QoI.
@@ -762,43 +844,13 @@ mlmc_status solve_fp64(mlmc_plan p, int mesh, const MeshInfo& mi, SolveWs<double
                                    (const void*)q_dev, (const void*)iters_dev);
   auto it = p->graphs.find(key);
   if (it == p->graphs.end()) {
-    // setup -> while(two PCG iterations + loop control) -> QoI epilogue
     GraphRec rec;
-    cudaGraph_t P = nullptr, body = nullptr;
-    cudaGraphConditionalHandle h;
-    int64_t l1 = 0, l2 = 0;
-    mlmc_status st = capture(p, &P, [&] {
-      const int64_t l0 = p->launches;
-      mlmc_status s2 = fp64_setup(p, mi, w, B);
-      if (s2 != MLMC_OK) return s2;
-      l1 = p->launches - l0;
-      if ((s2 = insert_while(p, &h, &body, false)) != MLMC_OK) return s2;
-      const int64_t l3 = p->launches;
-      s2 = fp64_epilogue(p, mi, w, B, q_dev, iters_dev);
-      l2 = p->launches - l3;
-      return s2;
-    });
+    mlmc_status st = build_graph(p, [&] { return issue_fp64(p, mi, w, B, q_dev, iters_dev); }, &rec);
     if (st != MLMC_OK) return st;
-    rec.n_setup = l1;
-    rec.n_epi = l2;
-    int64_t nb = 0;
-    st = capture(p, &body, [&] {
-      const int64_t l0 = p->launches;
-      mlmc_status s2 = pcg_graph_body<double>(p, mi, w, B, c.max_iter, h);
-      nb = p->launches - l0;
-      return s2;
-    });
-    if (st != MLMC_OK || cudaGraphInstantiate(&rec.exec, P, 0) != cudaSuccess) {
-      cudaGraphDestroy(P);
-      cudaGetLastError();
-      return st != MLMC_OK ? st : MLMC_ERR_CUDA;
-    }
-    cudaGraphDestroy(P);
-    rec.n_body = nb / 2;
     it = p->graphs.emplace(key, rec).first;
   }
   CK(cudaGraphLaunch(it->second.exec, p->stream));
-  p->pending_graphs.emplace_back(&it->second, w.execs, nullptr);
+  p->pending_graphs.push_back(&it->second);
   return MLMC_OK;
 }
 
@@ -868,9 +920,43 @@ mlmc_status mixed_epilogue(mlmc_plan p, const MeshInfo& mi, MixedWs& w, int64_t 
   return MLMC_OK;
 }
 
+// Mixed solve issued into the graph being captured: setup ->
+// while_outer(pre, re-arm inner, while_inner(PCG), post, outer control) -> QoI.
+mlmc_status issue_mixed(mlmc_plan p, const MeshInfo& mi, MixedWs& w, int64_t B, double* q_dev,
+                        int32_t* iters_dev) {
+  mlmc_status st = mixed_setup(p, mi, w, B);
+  if (st != MLMC_OK) return st;
+  const MeshInfo* mip = &mi;
+  MixedWs wc = w;           // copied into the deferred bodies (mutable lambdas)
+  const int imax = p->cfg.inner_max_iter, omax = p->cfg.outer_max_iter;
+  st = issue_loop(p, w.outer_execs, 1, [p, mip, wc, B, imax, omax](cudaGraphConditionalHandle ho) mutable {
+    mlmc_status s2 = mixed_pre_inner(p, *mip, wc, B);
+    if (s2 != MLMC_OK) return s2;
+    // the inner loop's condition is re-armed before every inner while-node
+    cudaGraph_t g = nullptr;
+    if ((s2 = capture_graph(p, &g)) != MLMC_OK) return s2;
+    cudaGraphConditionalHandle hi;
+    if (cudaGraphConditionalHandleCreate(&hi, g, 1, cudaGraphCondAssignDefault) != cudaSuccess)
+      return MLMC_ERR_CUDA;
+    CK(run(p, KID_SETUP, [&] { return launch_set_cond(p->stream, hi, 1u); }));
+    s2 = issue_loop(p, wc.in.execs, 2, [p, mip, wc, B, imax](cudaGraphConditionalHandle h) mutable {
+      return pcg_graph_body<float>(p, *mip, wc.in, B, imax, h);
+    }, &hi);
+    if (s2 != MLMC_OK) return s2;
+    if ((s2 = mixed_post_inner(p, *mip, wc, B, 0, wc.outer_it)) != MLMC_OK) return s2;
+    CK(run(p, KID_COUNT, [&] {
+      return launch_loop_ctl(p->stream, wc.outer.active, B, wc.outer_it, omax, wc.outer_count,
+                             wc.outer_execs, ho);
+    }));
+    return MLMC_OK;
+  });
+  if (st != MLMC_OK) return st;
+  return mixed_epilogue(p, mi, w, B, q_dev, iters_dev);
+}
+
 // Mixed form: FP64 iterative refinement around FP32 GMG/Jacobi-PCG
 // (kappa32 = rounded kappa64). w.kap64 holds kappa. Leaves u in w.u. With
-// graphs on: setup -> while_outer(pre -> while_inner(PCG) -> post) -> QoI.
+// graphs on the whole solve is one graph (issue_mixed).
 mlmc_status solve_mixed(mlmc_plan p, int mesh, const MeshInfo& mi, MixedWs& w, int64_t B,
                         double* q_dev, int32_t* iters_dev) {
   cudaStream_t s = p->stream;
@@ -895,62 +981,13 @@ mlmc_status solve_mixed(mlmc_plan p, int mesh, const MeshInfo& mi, MixedWs& w, i
                                    (const void*)q_dev, (const void*)iters_dev);
   auto it = p->graphs.find(key);
   if (it == p->graphs.end()) {
-    // setup -> while_outer(pre, re-arm inner, while_inner(PCG), post, outer control) -> QoI
     GraphRec rec;
-    cudaGraph_t P = nullptr, obody = nullptr, ibody = nullptr;
-    cudaGraphConditionalHandle ho, hi;
-    int64_t l1 = 0, l2 = 0, lo = 0, nb = 0;
-    mlmc_status st = capture(p, &P, [&] {
-      const int64_t l0 = p->launches;
-      mlmc_status s2 = mixed_setup(p, mi, w, B);
-      if (s2 != MLMC_OK) return s2;
-      l1 = p->launches - l0;
-      if ((s2 = insert_while(p, &ho, &obody, false)) != MLMC_OK) return s2;
-      const int64_t l3 = p->launches;
-      s2 = mixed_epilogue(p, mi, w, B, q_dev, iters_dev);
-      l2 = p->launches - l3;
-      return s2;
-    });
+    mlmc_status st = build_graph(p, [&] { return issue_mixed(p, mi, w, B, q_dev, iters_dev); }, &rec);
     if (st != MLMC_OK) return st;
-    st = capture(p, &obody, [&] {
-      const int64_t l0 = p->launches;
-      mlmc_status s2 = mixed_pre_inner(p, mi, w, B);
-      if (s2 != MLMC_OK) return s2;
-      cudaGraph_t g = nullptr;
-      if ((s2 = capture_graph(p, &g)) != MLMC_OK) return s2;
-      if (cudaGraphConditionalHandleCreate(&hi, g, 1, cudaGraphCondAssignDefault) != cudaSuccess)
-        return MLMC_ERR_CUDA;
-      CK(run(p, KID_SETUP, [&] { return launch_set_cond(p->stream, hi, 1u); }));
-      if ((s2 = insert_while(p, &hi, &ibody, true)) != MLMC_OK) return s2;
-      if ((s2 = mixed_post_inner(p, mi, w, B, 0, w.outer_it)) != MLMC_OK) return s2;
-      CK(run(p, KID_COUNT, [&] {
-        return launch_loop_ctl(p->stream, w.outer.active, B, w.outer_it, c.outer_max_iter,
-                               w.outer_count, w.outer_execs, ho);
-      }));
-      lo = p->launches - l0;
-      return MLMC_OK;
-    });
-    if (st == MLMC_OK)
-      st = capture(p, &ibody, [&] {
-        const int64_t l0 = p->launches;
-        mlmc_status s2 = pcg_graph_body<float>(p, mi, w.in, B, c.inner_max_iter, hi);
-        nb = p->launches - l0;
-        return s2;
-      });
-    if (st != MLMC_OK || cudaGraphInstantiate(&rec.exec, P, 0) != cudaSuccess) {
-      cudaGraphDestroy(P);
-      cudaGetLastError();
-      return st != MLMC_OK ? st : MLMC_ERR_CUDA;
-    }
-    cudaGraphDestroy(P);
-    rec.n_setup = l1;
-    rec.n_epi = l2;
-    rec.n_outer = lo;
-    rec.n_body = nb / 2;
     it = p->graphs.emplace(key, rec).first;
   }
   CK(cudaGraphLaunch(it->second.exec, p->stream));
-  p->pending_graphs.emplace_back(&it->second, w.in.execs, w.outer_execs);
+  p->pending_graphs.push_back(&it->second);
   return MLMC_OK;
 }
 
@@ -960,6 +997,106 @@ mlmc_status make_kappa(mlmc_plan p, int mesh, const double* xi, int64_t B, doubl
     return launch_kappa(p->stream, mi.g[0], p->cfg.modes_per_dim, p->sqrt_sigma2, mi.table, xi, B,
                         kappa, prof_for(p, KID_KAPPA, elems_of(mi.g[0]) * 8));
   }));
+  return MLMC_OK;
+}
+
+// --- one allocation round as one graph ----------------------------------
+
+// Coupled batch of `level` issued into the graph being captured on p->stream,
+// in the workspace region at `region`: xi, kappa and solve on mesh `level`,
+// kappa and solve on mesh `level - 1`, Welford fold in sample order.
+mlmc_status issue_level(mlmc_plan p, int level, int64_t first, int64_t B, void* region) {
+  const bool mixed = is_mixed(p);
+  const int M = p->M;
+  mlmc_status st;
+  for (int side = 0; side < (level > 0 ? 2 : 1); ++side) {
+    const int mesh = level - side;
+    const MeshInfo& mi = p->meshes[mesh];
+    Carve c(region);
+    CoupledWs w;
+    carve_coupled(c, mi, M, B, mixed, w);
+    if (side == 0 && (st = mlmc_draw_xi(p, level, first, B, w.xi)) != MLMC_OK) return st;
+    if ((st = make_kappa(p, mesh, w.xi, B, w.kap)) != MLMC_OK) return st;
+    double* qd = side == 0 ? w.qf : w.qc;
+    int32_t* itd = side == 0 ? w.itf : w.itc;
+    st = mixed ? issue_mixed(p, mi, w.mx, B, qd, itd) : issue_fp64(p, mi, w.s, B, qd, itd);
+    if (st != MLMC_OK) return st;
+  }
+  Carve c(region);
+  CoupledWs w;
+  carve_coupled(c, p->meshes[level], M, B, mixed, w);
+  const double cost = level_cost_cfg(&p->cfg, level);
+  CK(run(p, KID_WELFORD, [&] {
+    return launch_welford(p->stream, w.qf, level > 0 ? w.qc : nullptr, B, p->d_states + level, cost);
+  }));
+  return MLMC_OK;
+}
+
+// Samples first[l] .. first[l] + count[l] - 1 of every level in one graph
+// with one branch per level (finest first), so the latency-bound coarse
+// levels run beside the fine ones. Returns MLMC_ERR_UNIMPLEMENTED when the
+// batches do not fit the workspace together (the caller then samples level
+// by level). *bad is set when a solve hit its iteration cap.
+mlmc_status run_round(mlmc_plan p, const std::vector<int64_t>& first,
+                      const std::vector<int64_t>& count, bool* bad) {
+  const int L1 = p->cfg.n_levels;
+  const bool mixed = is_mixed(p);
+  std::vector<size_t> off(L1, 0);
+  size_t total = 0;
+  for (int l = 0; l < L1; ++l) {
+    if (count[l] <= 0) continue;
+    if (count[l] > 65535) return MLMC_ERR_UNIMPLEMENTED;
+    off[l] = total;
+    total += (size_t)round_up((int64_t)coupled_bytes(p->meshes[l], p->M, count[l], mixed), 256);
+  }
+  if (total == 0) return MLMC_OK;
+  if (total > p->ws_budget || (int)p->branch.size() < L1) return MLMC_ERR_UNIMPLEMENTED;
+  mlmc_status st = ensure_ws(p, total);
+  if (st != MLMC_OK) return st;
+  std::vector<int64_t> key = {mixed ? 1 : 0, (int64_t)(uintptr_t)p->ws};
+  key.insert(key.end(), first.begin(), first.end());
+  key.insert(key.end(), count.begin(), count.end());
+  auto it = p->round_graphs.find(key);
+  if (it == p->round_graphs.end()) {
+    GraphRec rec;
+    st = build_graph(p, [&]() -> mlmc_status {
+      cudaStream_t origin = p->stream;
+      CK(cudaEventRecord(p->branch_ev[0], origin));
+      int nb = 0;
+      mlmc_status s2 = MLMC_OK;
+      for (int l = L1 - 1; l >= 0 && s2 == MLMC_OK; --l) {
+        if (count[l] <= 0) continue;
+        cudaStream_t S = p->branch[nb];
+        CK(cudaStreamWaitEvent(S, p->branch_ev[0], 0));
+        p->stream = S;
+        s2 = issue_level(p, l, first[l], count[l], (char*)p->ws + off[l]);
+        p->stream = origin;
+        if (s2 == MLMC_OK) CK(cudaEventRecord(p->branch_ev[1 + nb], S));
+        ++nb;
+      }
+      for (int i = 0; i < nb && s2 == MLMC_OK; ++i) CK(cudaStreamWaitEvent(origin, p->branch_ev[1 + i], 0));
+      return s2;
+    }, &rec);
+    if (st != MLMC_OK) return st;
+    it = p->round_graphs.emplace(key, rec).first;
+  }
+  CK(cudaGraphLaunch(it->second.exec, p->stream));
+  p->pending_graphs.push_back(&it->second);
+  CK(cudaStreamSynchronize(p->stream));
+  if ((st = settle_graph_launches(p)) != MLMC_OK) return st;
+  // iteration caps: read back the per-sample counts of both meshes
+  std::vector<int32_t> h;
+  for (int l = 0; l < L1; ++l) {
+    if (count[l] <= 0) continue;
+    Carve c((char*)p->ws + off[l]);
+    CoupledWs w;
+    carve_coupled(c, p->meshes[l], p->M, count[l], mixed, w);
+    h.resize(2 * count[l]);
+    CK(cudaMemcpy(h.data(), w.itf, sizeof(int32_t) * count[l], cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(h.data() + count[l], w.itc, sizeof(int32_t) * count[l], cudaMemcpyDeviceToHost));
+    for (int64_t b = 0; b < count[l]; ++b)
+      if (h[b] < 0 || (l > 0 && h[count[l] + b] < 0)) *bad = true;
+  }
   return MLMC_OK;
 }
 
@@ -1103,6 +1240,16 @@ mlmc_status mlmc_plan_create(const mlmc_config* cfg, void* stream, mlmc_plan* ou
     p->cap_stream = nullptr;
     return fail(MLMC_ERR_CUDA);
   }
+  for (int l = 0; l < cfg->n_levels; ++l) {
+    cudaStream_t bs;
+    if (cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking) != cudaSuccess) return fail(MLMC_ERR_CUDA);
+    p->branch.push_back(bs);
+  }
+  for (int l = 0; l <= cfg->n_levels; ++l) {
+    cudaEvent_t ev;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return fail(MLMC_ERR_CUDA);
+    p->branch_ev.push_back(ev);
+  }
   size_t budget = cfg->workspace_bytes;
   if (budget == 0) {
     size_t fr = 0, tot = 0;
@@ -1120,6 +1267,8 @@ mlmc_status mlmc_plan_destroy(mlmc_plan p) {
   cudaStreamSynchronize(p->stream);
   clear_graphs(p);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+  for (auto bs : p->branch) cudaStreamDestroy(bs);
+  for (auto ev : p->branch_ev) cudaEventDestroy(ev);
   for (auto& mi : p->meshes)
     if (mi.table) cudaFree(mi.table);
   cudaFree(p->d_omega);
@@ -1346,15 +1495,24 @@ mlmc_status mlmc_run(mlmc_plan p, double eps, int64_t pilot, const int64_t* N_fi
     }
   bool bad = false;
   for (int round = 0; round < 64; ++round) {
-    // finest level first (the priority of the paper's incremental greedy schedule)
-    for (int l = L1 - 1; l >= 0; --l) {
-      if (have[l] < target[l]) {
-        st = mlmc_sample_level(p, l, have[l], target[l] - have[l], nullptr, nullptr, nullptr);
-        if (st == MLMC_ERR_NOT_CONVERGED) bad = true;
-        else if (st != MLMC_OK) return st;
-        have[l] = target[l];
+    // one graph per round with a branch per level when the batches fit the
+    // workspace together; otherwise level by level, finest first (the
+    // priority of the paper's incremental greedy schedule)
+    std::vector<int64_t> count(L1);
+    for (int l = 0; l < L1; ++l) count[l] = std::max<int64_t>(0, target[l] - have[l]);
+    st = graphs_on(p) ? run_round(p, have, count, &bad) : MLMC_ERR_UNIMPLEMENTED;
+    if (st == MLMC_ERR_UNIMPLEMENTED) {
+      for (int l = L1 - 1; l >= 0; --l) {
+        if (count[l] > 0) {
+          st = mlmc_sample_level(p, l, have[l], count[l], nullptr, nullptr, nullptr);
+          if (st == MLMC_ERR_NOT_CONVERGED) bad = true;
+          else if (st != MLMC_OK) return st;
+        }
       }
+    } else if (st != MLMC_OK) {
+      return st;
     }
+    for (int l = 0; l < L1; ++l) have[l] = std::max(have[l], target[l]);
     if (N_fixed) break;
     CK(run(p, KID_ESTIMATE, [&] {
       return launch_estimate(p->stream, p->d_states, L1, p->d_cost, eps, p->d_small, p->d_N);

@@ -319,3 +319,20 @@ def test_graph_solve_on_legacy_default_stream(m):
     ref = [omlmc.coupled_sample(wl, 1, i) for i in range(4)]
     for s in range(4):
         assert abs(qf[s] - ref[s][0]) <= RTOL_Q * abs(ref[s][0])
+
+
+@pytest.mark.parametrize("dim,precision", [(2, "fp64"), (2, "mixed"), (3, "fp64")])
+def test_round_graph_run_matches_level_by_level(m, dim, precision):
+    """mlmc_run with one graph per round (a branch per level) equals the level-by-level run bit for bit."""
+    if dim == 2:
+        wl = small_case(2, n0=8, levels=3, m=4, solver="gmg", precision=precision)
+    else:
+        wl = small_case(3, n0=4, levels=3, m=3, solver="gmg", qoi="box", precision=precision)
+    out = []
+    for graphs in (0, 1):
+        cfg = m.config_from_workload(wl, use_graphs=graphs)
+        with m.Plan(cfg, stream()) as plan:
+            q, v, N = plan.run(eps=2e-3, pilot=6)
+            out.append((q, v, list(N), [plan.level_stats(l) for l in range(3)], plan.launch_count()))
+    assert out[0][:4] == out[1][:4]
+    assert out[1][4] > 0
