@@ -66,11 +66,15 @@ def coupled_dofs(wl, level):
 
 def workload_desc(wl):
     nf = wl["n0"] << (wl["levels"] - 1)
+    if wl.get("N") is not None:
+        tail = "fixed N=%s" % (list(wl["N"]),)
+    else:
+        tail = "eps=%g, pilot %d" % (wl["eps"], wl["pilot"])
     return ("%dD Q1 %d^%d..%d^%d elements (%d levels), sigma2=%g, corr_len=%g, M=%d, %s-PCG "
-            "rtol %g, %s QoI, eps=%g, pilot %d" % (
+            "rtol %g, %s QoI, %s" % (
                 wl["dim"], wl["n0"], wl["dim"], nf, wl["dim"], wl["levels"], wl["sigma2"],
                 wl["corr_len"], wl["m"] ** wl["dim"], wl["solver"].upper(), wl["rtol"],
-                wl["qoi"], wl["eps"], wl["pilot"]))
+                wl["qoi"], tail))
 
 
 # ----------------------------------------------------------------- clocks
@@ -204,13 +208,17 @@ def measure_form(m, wl, cfg, stream, args, world, barrier, with_e2e):
     with torch.cuda.stream(stream):
         plan = m.Plan(cfg, sh)
         N = None
+        def one_run():
+            if wl.get("N") is not None:
+                return plan.run(N=list(wl["N"]))
+            return plan.run(eps=wl["eps"], pilot=wl["pilot"])
         for _ in range(max(args.warmup, 1)):
-            q, v, N = plan.run(eps=wl["eps"], pilot=wl["pilot"])
+            q, v, N = one_run()
         dofs_step = sum(int(N[l]) * coupled_dofs(wl, l) for l in range(wl["levels"]))
         # pick the dominant kernel from a traced run
         plan.profile(-1)
         plan.profile_reset()
-        plan.run(eps=wl["eps"], pilot=wl["pilot"])
+        one_run()
         stats = plan.kernel_stats()
         plan.profile(0)
         total_ms = sum(st[1] for st in stats.values())
@@ -226,7 +234,7 @@ def measure_form(m, wl, cfg, stream, args, world, barrier, with_e2e):
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
         for _ in range(args.steps):
-            q, v, N = plan.run(eps=wl["eps"], pilot=wl["pilot"])
+            q, v, N = one_run()
         ev1.record(stream)
         torch.cuda.synchronize()
         barrier()
@@ -237,7 +245,7 @@ def measure_form(m, wl, cfg, stream, args, world, barrier, with_e2e):
         # stream, over a repeat of the same step (host-driven launches of the same kernels)
         plan.profile_reset()
         plan.profile(1 << m.Plan.kernel_id(dom))
-        plan.run(eps=wl["eps"], pilot=wl["pilot"])
+        one_run()
         dstat = plan.kernel_stats()[dom]
         plan.profile(0)
         wall = []
@@ -248,7 +256,10 @@ def measure_form(m, wl, cfg, stream, args, world, barrier, with_e2e):
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 p2 = m.Plan(cfg, sh)
-                p2.run(eps=wl["eps"], pilot=wl["pilot"])
+                if wl.get("N") is not None:
+                    p2.run(N=list(wl["N"]))
+                else:
+                    p2.run(eps=wl["eps"], pilot=wl["pilot"])
                 p2.close()
                 torch.cuda.synchronize()
                 wall.append(time.perf_counter() - t0)

@@ -194,9 +194,10 @@ cudaError_t restrict_(cudaStream_t s, const Grid& fine, const Grid& coarse, cons
 template <class T>
 cudaError_t coarse_solve(cudaStream_t s, const Grid& g, const T* kappa, const T* b, T* e,
                          const int32_t* active, int64_t B);
+// tmp: a node vector of this level used for e + P ec
 template <class T>
 cudaError_t mg_post(cudaStream_t s, const Grid& g, const Grid& coarse, const T* kappa, const T* w,
-                    const T* b, const T* e, const T* ec, T* out, const int32_t* active,
+                    const T* b, const T* e, const T* ec, T* out, T* tmp, const int32_t* active,
                     double* part, int64_t B, Prof p);
 template <class T>
 cudaError_t qoi(cudaStream_t s, const Grid& g, int box, int L, int H, double inv_vol, const T* x,
@@ -253,12 +254,13 @@ inline cudaError_t coarse_solve(cudaStream_t s, const Grid& g, const T* kappa, c
   return g.dim == 2 ? d2::coarse_solve<T>(s, g, kappa, b, e, active, B)
                     : d3::coarse_solve<T>(s, g, kappa, b, e, active, B);
 }
+// tmp: scratch node vector of this level (3D only)
 template <class T>
 inline cudaError_t mg_post(cudaStream_t s, const Grid& g, const Grid& coarse, const T* kappa, const T* w,
-                           const T* b, const T* e, const T* ec, T* out, const int32_t* active,
+                           const T* b, const T* e, const T* ec, T* out, T* tmp, const int32_t* active,
                            double* part, int64_t B, Prof p) {
   return g.dim == 2 ? d2::mg_post<T>(s, g, coarse, kappa, w, b, e, ec, out, active, part, B, p)
-                    : d3::mg_post<T>(s, g, coarse, kappa, w, b, e, ec, out, active, part, B, p);
+                    : d3::mg_post<T>(s, g, coarse, kappa, w, b, e, ec, out, tmp, active, part, B, p);
 }
 template <class T>
 inline cudaError_t qoi(cudaStream_t s, const Grid& g, int box, int L, int H, double inv_vol, const T* x,

@@ -509,8 +509,9 @@ mlmc_status precondition(mlmc_plan p, const MeshInfo& mi, SolveWs<T>& w, int64_t
     const Grid& g = mi.g[k];
     const double nn = nodes_of(g), ne = elems_of(g), nc = nodes_of(mi.g[k + 1]);
     CK(run(p, KID_MG_POST, [&] {
+      // r1[k] is dead once restricted: it serves as the 3D scratch for e + P e_c
       return op::mg_post<T>(s, g, mi.g[k + 1], w.kap[k], w.w[k], w.bk[k], w.e[k], w.eo[k + 1],
-                            w.eo[k], w.sc.active, k == 0 ? w.part : nullptr, B,
+                            w.eo[k], w.r1[k], w.sc.active, k == 0 ? w.part : nullptr, B,
                             prof_for(p, KID_MG_POST, (4 * nn + ne + nc) * vb));
     }));
   }

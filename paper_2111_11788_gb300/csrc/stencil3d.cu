@@ -14,7 +14,9 @@
 // and no face coupling.
 //
 // One thread per node, CTA tiles of 32 x 8 nodes in one z-plane; neighbour
-// values come through the L1 cache. Node arrays carry the boundary nodes
+// values come through the L1 cache. Fields that the stencil acts on (p = z +
+// beta p_old, e = W b, e + P e_c) are first formed by a pointwise pass, so
+// every stencil kernel gathers one stored vector. Node arrays carry the boundary nodes
 // (always 0). Partials: one per CTA (g.tiles_s per sample).
 #include "mlmc_internal.cuh"
 
@@ -187,62 +189,75 @@ __global__ void __launch_bounds__(256) k_init3(Grid g, T* __restrict__ X, T* __r
   prof_tick3(prof);
 }
 
-// p_new = z + beta p_old, q = A p_new, partials of p.q
+// Pointwise: p_new = z + beta p_old (beta == 0: p_new = z; p_old unread).
 template <class T>
-__global__ void __launch_bounds__(256) k_pq3(Grid g, const T* __restrict__ K, const T* __restrict__ Z,
-                                             const T* __restrict__ Pold, T* __restrict__ Pnew,
-                                             T* __restrict__ Q, const double* __restrict__ beta,
-                                             const int32_t* __restrict__ active,
+__global__ void __launch_bounds__(256) k_pupd3(Grid g, const T* __restrict__ Z, const T* __restrict__ Pold,
+                                               T* __restrict__ Pnew, const double* __restrict__ beta,
+                                               const int32_t* __restrict__ active) {
+  const int64_t b = blockIdx.y;
+  if (!active[b]) return;
+  const Node3 q = node3(g.n);
+  if (!q.valid) return;
+  const T bb = (T)beta[b];
+  const int64_t o = b * g.ns + q.idx;
+  const T zv = Z[o];
+  Pnew[o] = (bb == T(0)) ? zv : fma(bb, Pold[o], zv);
+}
+
+// q = A p, partials of p.q
+template <class T>
+__global__ void __launch_bounds__(256) k_aq3(Grid g, const T* __restrict__ K, const T* __restrict__ P,
+                                             T* __restrict__ Q, const int32_t* __restrict__ active,
                                              double* __restrict__ part, Prof prof) {
   const int64_t b = blockIdx.y;
   if (!active[b]) return;
   const Node3 q = node3(g.n);
-  const T bb = (T)beta[b];
-  const bool first = (bb == T(0));
-  const T* z = Z + b * g.ns;
-  const T* po = Pold + b * g.ns;
+  const T* p = P + b * g.ns;
   double dot = 0.0;
   if (q.valid) {
-    T pv = T(0), qv = T(0);
+    T qv = T(0);
     if (q.interior) {
       T v[3][3][3], kk[2][2][2];
-      gather27<T>(q, g.n, [&](int64_t o, int, int, int) {
-        const T zv = __ldg(z + o);
-        return first ? zv : fma(bb, __ldg(po + o), zv);
-      }, v);
+      gather27<T>(q, g.n, [&](int64_t o, int, int, int) { return __ldg(p + o); }, v);
       load_k8(K + b * g.es, g.n, q, kk);
-      pv = v[1][1][1];
       qv = stencil3(kk, v, g.h);
-      dot = (double)(pv * qv);
+      dot = (double)(v[1][1][1] * qv);
     }
-    Pnew[b * g.ns + q.idx] = pv;
     Q[b * g.ns + q.idx] = qv;
   }
   cta_partial3(dot, part, g.tiles_s);
   prof_tick3(prof);
 }
 
-// e = W b, r1 = b - A e
+// Pointwise: out = W b (the pre-smoothing step from zero).
 template <class T>
-__global__ void __launch_bounds__(256) k_mgpre3(Grid g, const T* __restrict__ K, const T* __restrict__ W,
-                                                const T* __restrict__ Bv, T* __restrict__ E,
-                                                T* __restrict__ R1, const int32_t* __restrict__ active,
-                                                Prof prof) {
+__global__ void __launch_bounds__(256) k_wb3(Grid g, const T* __restrict__ W, const T* __restrict__ Bv,
+                                             T* __restrict__ E, const int32_t* __restrict__ active) {
   const int64_t b = blockIdx.y;
   if (!active[b]) return;
   const Node3 q = node3(g.n);
   if (!q.valid) return;
-  const T* w = W + b * g.ns;
-  const T* bv = Bv + b * g.ns;
-  T ev = T(0), rv = T(0);
+  const int64_t o = b * g.ns + q.idx;
+  E[o] = W[o] * Bv[o];
+}
+
+// r1 = b - A e
+template <class T>
+__global__ void __launch_bounds__(256) k_mgres3(Grid g, const T* __restrict__ K, const T* __restrict__ Bv,
+                                                const T* __restrict__ E, T* __restrict__ R1,
+                                                const int32_t* __restrict__ active, Prof prof) {
+  const int64_t b = blockIdx.y;
+  if (!active[b]) return;
+  const Node3 q = node3(g.n);
+  if (!q.valid) return;
+  const T* e = E + b * g.ns;
+  T rv = T(0);
   if (q.interior) {
     T v[3][3][3], kk[2][2][2];
-    gather27<T>(q, g.n, [&](int64_t o, int, int, int) { return __ldg(w + o) * __ldg(bv + o); }, v);
+    gather27<T>(q, g.n, [&](int64_t o, int, int, int) { return __ldg(e + o); }, v);
     load_k8(K + b * g.es, g.n, q, kk);
-    ev = v[1][1][1];
-    rv = __ldg(bv + q.idx) - stencil3(kk, v, g.h);
+    rv = __ldg(Bv + b * g.ns + q.idx) - stencil3(kk, v, g.h);
   }
-  E[b * g.ns + q.idx] = ev;
   R1[b * g.ns + q.idx] = rv;
   prof_tick3(prof);
 }
@@ -305,27 +320,37 @@ __device__ __forceinline__ T prolong3(const T* __restrict__ Ec, int nc, int i, i
   return acc * scale;
 }
 
-// out = e' + W (b - A e'), e' = e + P ec; partials of b.out when part != nullptr.
+// Pointwise: tmp = e + P ec (trilinear prolongation of the coarse correction).
 template <class T>
-__global__ void __launch_bounds__(256) k_mgpost3(Grid g, int64_t nsc, const T* __restrict__ K,
+__global__ void __launch_bounds__(256) k_prolong3(Grid g, int64_t nsc, const T* __restrict__ E,
+                                                  const T* __restrict__ Ec, T* __restrict__ Tmp,
+                                                  const int32_t* __restrict__ active) {
+  const int64_t b = blockIdx.y;
+  if (!active[b]) return;
+  const Node3 q = node3(g.n);
+  if (!q.valid) return;
+  T v = T(0);
+  if (q.interior) v = E[b * g.ns + q.idx] + prolong3(Ec + b * nsc, g.n / 2, q.i, q.j, q.k);
+  Tmp[b * g.ns + q.idx] = v;
+}
+
+// out = e' + W (b - A e') with e' = tmp; partials of b.out when part != nullptr.
+template <class T>
+__global__ void __launch_bounds__(256) k_mgpost3(Grid g, const T* __restrict__ K,
                                                  const T* __restrict__ W, const T* __restrict__ Bv,
-                                                 const T* __restrict__ E, const T* __restrict__ Ec,
-                                                 T* __restrict__ Out, const int32_t* __restrict__ active,
+                                                 const T* __restrict__ Tmp, T* __restrict__ Out,
+                                                 const int32_t* __restrict__ active,
                                                  double* __restrict__ part, Prof prof) {
   const int64_t b = blockIdx.y;
   if (!active[b]) return;
   const Node3 q = node3(g.n);
-  const int nc = g.n / 2;
-  const T* ec = Ec + b * nsc;
-  const T* e = E + b * g.ns;
+  const T* e = Tmp + b * g.ns;
   double dot = 0.0;
   if (q.valid) {
     T ov = T(0);
     if (q.interior) {
       T v[3][3][3], kk[2][2][2];
-      gather27<T>(q, g.n, [&](int64_t o, int i, int j, int k) {
-        return __ldg(e + o) + prolong3(ec, nc, i, j, k);
-      }, v);
+      gather27<T>(q, g.n, [&](int64_t o, int, int, int) { return __ldg(e + o); }, v);
       load_k8(K + b * g.es, g.n, q, kk);
       const T bval = __ldg(Bv + b * g.ns + q.idx);
       ov = fma(__ldg(W + b * g.ns + q.idx), bval - stencil3(kk, v, g.h), v[1][1][1]);
@@ -407,13 +432,15 @@ cudaError_t pcg_init(cudaStream_t s, const Grid& g, T* x, T* r, int64_t B, Prof 
 template <class T>
 cudaError_t pcg_pq(cudaStream_t s, const Grid& g, const T* kappa, const T* z, const T* p_old, T* p_new,
                    T* q, const Scalars& sc, double* part, int64_t B, Prof p) {
-  k_pq3<T><<<grid3(g, B), block3(), 0, s>>>(g, kappa, z, p_old, p_new, q, sc.beta, sc.active, part, p);
+  k_pupd3<T><<<grid3(g, B), block3(), 0, s>>>(g, z, p_old, p_new, sc.beta, sc.active);
+  k_aq3<T><<<grid3(g, B), block3(), 0, s>>>(g, kappa, p_new, q, sc.active, part, p);
   return cudaGetLastError();
 }
 template <class T>
 cudaError_t mg_pre(cudaStream_t s, const Grid& g, const T* kappa, const T* w, const T* b, T* e, T* r1,
                    const int32_t* active, int64_t B, Prof p) {
-  k_mgpre3<T><<<grid3(g, B), block3(), 0, s>>>(g, kappa, w, b, e, r1, active, p);
+  k_wb3<T><<<grid3(g, B), block3(), 0, s>>>(g, w, b, e, active);
+  k_mgres3<T><<<grid3(g, B), block3(), 0, s>>>(g, kappa, b, e, r1, active, p);
   return cudaGetLastError();
 }
 template <class T>
@@ -430,9 +457,10 @@ cudaError_t coarse_solve(cudaStream_t s, const Grid& g, const T* kappa, const T*
 }
 template <class T>
 cudaError_t mg_post(cudaStream_t s, const Grid& g, const Grid& coarse, const T* kappa, const T* w,
-                    const T* b, const T* e, const T* ec, T* out, const int32_t* active, double* part,
-                    int64_t B, Prof p) {
-  k_mgpost3<T><<<grid3(g, B), block3(), 0, s>>>(g, coarse.ns, kappa, w, b, e, ec, out, active, part, p);
+                    const T* b, const T* e, const T* ec, T* out, T* tmp, const int32_t* active,
+                    double* part, int64_t B, Prof p) {
+  k_prolong3<T><<<grid3(g, B), block3(), 0, s>>>(g, coarse.ns, e, ec, tmp, active);
+  k_mgpost3<T><<<grid3(g, B), block3(), 0, s>>>(g, kappa, w, b, tmp, out, active, part, p);
   return cudaGetLastError();
 }
 template <class T>
@@ -460,7 +488,7 @@ cudaError_t resid64(cudaStream_t s, const Grid& g, const double* kappa, const do
   template cudaError_t coarse_solve<T>(cudaStream_t, const Grid&, const T*, const T*, T*,          \
                                        const int32_t*, int64_t);                                   \
   template cudaError_t mg_post<T>(cudaStream_t, const Grid&, const Grid&, const T*, const T*,      \
-                                  const T*, const T*, const T*, T*, const int32_t*, double*,       \
+                                  const T*, const T*, const T*, T*, T*, const int32_t*, double*,   \
                                   int64_t, Prof);                                                  \
   template cudaError_t qoi<T>(cudaStream_t, const Grid&, int, int, int, double, const T*, double*, \
                               int64_t, Prof);

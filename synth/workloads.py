@@ -33,9 +33,12 @@ WORKLOADS = {
                        qoi='box', box=(0.25, 0.75), solver='gmg', rtol=1e-10,
                        seed=0, stream_id=0, eps=5e-4, pilot=100, N=None),
     # 3D mixed precision: 5 levels 16^3..256^3, corr 0.1, M = 343.
+    # No target RMSE or sample counts are given for it: a fixed-N run with
+    # N_l halving per level (64 .. 4) is used.
     "3d-mixed": dict(dim=3, n0=16, levels=5, sigma2=1.0, corr_len=0.1, m=7,
                      qoi='box', box=(0.25, 0.75), solver='gmg', rtol=1e-10,
-                     seed=0, stream_id=0, eps=None, pilot=0, N=None),
+                     seed=0, stream_id=0, eps=None, pilot=0, N=(64, 32, 16, 8, 4),
+                     precision='mixed'),
 }
 
 
