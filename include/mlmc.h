@@ -128,6 +128,28 @@ const char* mlmc_status_str(mlmc_status s);
 mlmc_status mlmc_plan_create(const mlmc_config* cfg, void* stream, mlmc_plan* out);
 mlmc_status mlmc_plan_destroy(mlmc_plan plan);
 
+/* Re-target an idle plan to a configuration of the same shape (dim,
+ * n_levels, coarse_cells, modes_per_dim, solver, precision): field
+ * parameters, seed, stream id, tolerances and QoI may change. Rebuilds the
+ * KLE tables in place, drops cached graphs and resets the level states;
+ * allocates nothing (no device synchronisation from cudaFree). A nonzero
+ * workspace_bytes sets the batching budget unless the workspace is
+ * borrowed. INVALID for a different shape or while a round is in flight. */
+mlmc_status mlmc_plan_retarget(mlmc_plan plan, const mlmc_config* cfg);
+
+/* Give the plan a caller-owned device workspace of `bytes` bytes at `ws`
+ * (256-byte aligned) for its batches and rounds; the plan then never
+ * allocates or grows a workspace, and the batching budget becomes `bytes`.
+ * A plan's own previous workspace is freed; cached graphs are dropped. `ws`
+ * must stay valid until the plan is destroyed or given another workspace;
+ * NULL returns the plan to its own (lazily allocated) workspace. INVALID
+ * while a round is in flight or for a misaligned pointer. */
+mlmc_status mlmc_plan_set_workspace(mlmc_plan plan, void* ws, uint64_t bytes);
+
+/* Device workspace bytes of one round with count[l] samples per level
+ * (host array of n_levels entries), or -1 for an invalid configuration. */
+int64_t mlmc_round_bytes(const mlmc_config* cfg, const int64_t* count);
+
 /* Reset all level states to n = 0. */
 mlmc_status mlmc_reset_stats(mlmc_plan plan);
 
@@ -161,6 +183,24 @@ mlmc_status mlmc_allocate(const double* V, const double* C, int n_levels, double
  * n_levels, may be NULL) receives the final sample counts. */
 mlmc_status mlmc_run(mlmc_plan plan, double eps, int64_t pilot, const int64_t* N_fixed,
                      double* q_hat, double* stat_var, int64_t* N_out);
+
+/* ---- asynchronous allocation rounds ----------------------------------- */
+
+/* Launch samples first[l] .. first[l] + count[l] - 1 of every level l
+ * (host arrays of n_levels entries; count 0 skips a level) as one CUDA
+ * graph with a branch per level, asynchronously on the plan's stream. The
+ * level states are updated when the round completes; at most one round per
+ * plan is in flight. Returns UNIMPLEMENTED when graphs are off (use_graphs
+ * = 0 or tracing on) or the batches do not fit the workspace budget
+ * together (the caller then uses mlmc_sample_level level by level). */
+mlmc_status mlmc_round_begin(mlmc_plan plan, const int64_t* first, const int64_t* count);
+/* 1 when the launched round (if any) has completed, 0 if not yet, -1 on error. */
+int mlmc_round_ready(mlmc_plan plan);
+/* Waits for the round; NOT_CONVERGED if a solve hit its iteration cap. */
+mlmc_status mlmc_round_end(mlmc_plan plan);
+/* Eq. (mlmc_num_samples) from the current level states (V_l = m2_l / n_l)
+ * and the cost model: N_out (host, n_levels entries). */
+mlmc_status mlmc_allocation(mlmc_plan plan, double eps, int64_t* N_out);
 
 /* ---- device-level steps (device pointers, asynchronous on the plan's stream) */
 

@@ -35,7 +35,8 @@ def sources():
 
 def _deps():
     hdr = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
-    hdr.append(os.path.join(ROOT, "include", "mlmc.h"))
+    inc = os.path.join(ROOT, "include")
+    hdr += [os.path.join(inc, f) for f in os.listdir(inc) if f.endswith(".h")]
     return hdr
 
 

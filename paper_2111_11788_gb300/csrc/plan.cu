@@ -234,6 +234,7 @@ struct mlmc_plan_s {
   void* ws = nullptr;
   size_t ws_bytes = 0;
   size_t ws_budget = 0;
+  bool ws_borrowed = false;       // ws belongs to the caller (mlmc_plan_set_workspace)
   void* h_pin = nullptr;
   size_t h_pin_bytes = 0;
   // tracing
@@ -254,6 +255,9 @@ struct mlmc_plan_s {
   std::vector<struct Deferred>* todo = nullptr;      // set while a graph is built
   std::vector<cudaStream_t> branch;                  // capture streams of round branches
   std::vector<cudaEvent_t> branch_ev;
+  cudaEvent_t round_done = nullptr;                  // recorded after a launched round
+  std::vector<size_t> round_off;                     // workspace regions of the launched round
+  std::vector<int64_t> round_count;
   cudaStream_t cap_stream = nullptr;   // private stream the solve graphs are captured on
   // executed graphs whose kernel counts are settled at the next sync point
   std::vector<const GraphRec*> pending_graphs;
@@ -404,6 +408,7 @@ mlmc_status settle_graph_launches(mlmc_plan p);
 
 mlmc_status ensure_ws(mlmc_plan p, size_t bytes) {
   if (bytes <= p->ws_bytes) return MLMC_OK;
+  if (p->ws_borrowed) return MLMC_ERR_OOM;   // a borrowed workspace never grows
   if (p->ws) {
     cudaStreamSynchronize(p->stream);
     if (settle_graph_launches(p) != MLMC_OK) return MLMC_ERR_CUDA;
@@ -1038,8 +1043,8 @@ mlmc_status issue_level(mlmc_plan p, int level, int64_t first, int64_t B, void* 
 // levels run beside the fine ones. Returns MLMC_ERR_UNIMPLEMENTED when the
 // batches do not fit the workspace together (the caller then samples level
 // by level). *bad is set when a solve hit its iteration cap.
-mlmc_status run_round(mlmc_plan p, const std::vector<int64_t>& first,
-                      const std::vector<int64_t>& count, bool* bad) {
+mlmc_status round_launch(mlmc_plan p, const std::vector<int64_t>& first,
+                         const std::vector<int64_t>& count) {
   const int L1 = p->cfg.n_levels;
   const bool mixed = is_mixed(p);
   std::vector<size_t> off(L1, 0);
@@ -1050,6 +1055,8 @@ mlmc_status run_round(mlmc_plan p, const std::vector<int64_t>& first,
     off[l] = total;
     total += (size_t)round_up((int64_t)coupled_bytes(p->meshes[l], p->M, count[l], mixed), 256);
   }
+  p->round_off = off;
+  p->round_count = count;
   if (total == 0) return MLMC_OK;
   if (total > p->ws_budget || (int)p->branch.size() < L1) return MLMC_ERR_UNIMPLEMENTED;
   mlmc_status st = ensure_ws(p, total);
@@ -1082,23 +1089,48 @@ mlmc_status run_round(mlmc_plan p, const std::vector<int64_t>& first,
     it = p->round_graphs.emplace(key, rec).first;
   }
   CK(cudaGraphLaunch(it->second.exec, p->stream));
+  CK(cudaEventRecord(p->round_done, p->stream));
   p->pending_graphs.push_back(&it->second);
-  CK(cudaStreamSynchronize(p->stream));
-  if ((st = settle_graph_launches(p)) != MLMC_OK) return st;
-  // iteration caps: read back the per-sample counts of both meshes
-  std::vector<int32_t> h;
-  for (int l = 0; l < L1; ++l) {
-    if (count[l] <= 0) continue;
-    Carve c((char*)p->ws + off[l]);
-    CoupledWs w;
-    carve_coupled(c, p->meshes[l], p->M, count[l], mixed, w);
-    h.resize(2 * count[l]);
-    CK(cudaMemcpy(h.data(), w.itf, sizeof(int32_t) * count[l], cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(h.data() + count[l], w.itc, sizeof(int32_t) * count[l], cudaMemcpyDeviceToHost));
-    for (int64_t b = 0; b < count[l]; ++b)
-      if (h[b] < 0 || (l > 0 && h[count[l] + b] < 0)) *bad = true;
-  }
   return MLMC_OK;
+}
+
+// Waits for the launched round, settles the launch count and checks the
+// per-sample iteration counts of both meshes of every level.
+mlmc_status round_finish(mlmc_plan p, bool* bad) {
+  CK(cudaStreamSynchronize(p->stream));
+  mlmc_status st = settle_graph_launches(p);
+  if (st != MLMC_OK) return st;
+  const int L1 = p->cfg.n_levels;
+  const bool mixed = is_mixed(p);
+  std::vector<int32_t> h;
+  for (int l = 0; l < L1 && l < (int)p->round_count.size(); ++l) {
+    const int64_t n = p->round_count[l];
+    if (n <= 0) continue;
+    Carve c((char*)p->ws + p->round_off[l]);
+    CoupledWs w;
+    carve_coupled(c, p->meshes[l], p->M, n, mixed, w);
+    h.resize(2 * n);
+    // on the plan's stream: other plans' rounds keep running meanwhile
+    CK(cudaMemcpyAsync(h.data(), w.itf, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaMemcpyAsync(h.data() + n, w.itc, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    for (int64_t b = 0; b < n; ++b)
+      if (h[b] < 0 || (l > 0 && h[n + b] < 0)) *bad = true;
+  }
+  p->round_count.clear();
+  return MLMC_OK;
+}
+
+// Samples first[l] .. first[l] + count[l] - 1 of every level in one graph
+// with one branch per level (finest first), so the latency-bound coarse
+// levels run beside the fine ones. Returns MLMC_ERR_UNIMPLEMENTED when the
+// batches do not fit the workspace together (the caller then samples level
+// by level). *bad is set when a solve hit its iteration cap.
+mlmc_status run_round(mlmc_plan p, const std::vector<int64_t>& first,
+                      const std::vector<int64_t>& count, bool* bad) {
+  mlmc_status st = round_launch(p, first, count);
+  if (st != MLMC_OK) return st;
+  return round_finish(p, bad);
 }
 
 }  // namespace
@@ -1251,6 +1283,10 @@ mlmc_status mlmc_plan_create(const mlmc_config* cfg, void* stream, mlmc_plan* ou
     if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return fail(MLMC_ERR_CUDA);
     p->branch_ev.push_back(ev);
   }
+  if (cudaEventCreateWithFlags(&p->round_done, cudaEventDisableTiming) != cudaSuccess) {
+    p->round_done = nullptr;
+    return fail(MLMC_ERR_CUDA);
+  }
   size_t budget = cfg->workspace_bytes;
   if (budget == 0) {
     size_t fr = 0, tot = 0;
@@ -1263,6 +1299,77 @@ mlmc_status mlmc_plan_create(const mlmc_config* cfg, void* stream, mlmc_plan* ou
   return MLMC_OK;
 }
 
+mlmc_status mlmc_plan_retarget(mlmc_plan p, const mlmc_config* cfg) {
+  if (!p) return MLMC_ERR_INVALID;
+  mlmc_status st = validate(cfg);
+  if (st != MLMC_OK) return st;
+  const mlmc_config& o = p->cfg;
+  if (cfg->dim != o.dim || cfg->n_levels != o.n_levels || cfg->coarse_cells != o.coarse_cells ||
+      cfg->modes_per_dim != o.modes_per_dim || cfg->solver != o.solver ||
+      cfg->precision != o.precision)
+    return MLMC_ERR_INVALID;
+  if (!p->round_count.empty()) return MLMC_ERR_INVALID;
+  CK(cudaStreamSynchronize(p->stream));
+  if (settle_graph_launches(p) != MLMC_OK) return MLMC_ERR_CUDA;
+  clear_graphs(p);   // graphs bake field parameters, seeds and tolerances
+  const int m = cfg->modes_per_dim;
+  std::vector<double> omega, theta;
+  std::vector<int32_t> even;
+  kle_roots(cfg->corr_len, m, omega, theta, even);
+  if (ensure_pin(p, sizeof(double) * 2 * m + sizeof(int32_t) * m) != MLMC_OK) return MLMC_ERR_OOM;
+  double* hp = (double*)p->h_pin;
+  std::memcpy(hp, omega.data(), sizeof(double) * m);
+  std::memcpy(hp + m, theta.data(), sizeof(double) * m);
+  std::memcpy(hp + 2 * m, even.data(), sizeof(int32_t) * m);
+  CK(cudaMemcpyAsync(p->d_omega, hp, sizeof(double) * m, cudaMemcpyHostToDevice, p->stream));
+  CK(cudaMemcpyAsync(p->d_theta, hp + m, sizeof(double) * m, cudaMemcpyHostToDevice, p->stream));
+  CK(cudaMemcpyAsync(p->d_even, hp + 2 * m, sizeof(int32_t) * m, cudaMemcpyHostToDevice, p->stream));
+  for (auto& mi : p->meshes)
+    CK(run(p, KID_TABLE, [&] { return launch_kle_table(p->stream, mi.n, m, p->d_omega, p->d_theta, p->d_even, mi.table); }));
+  p->cfg = *cfg;
+  p->sqrt_sigma2 = std::sqrt(cfg->sigma2);
+  if (cfg->workspace_bytes && !p->ws_borrowed) p->ws_budget = cfg->workspace_bytes;
+  CK(cudaMemsetAsync(p->d_states, 0, sizeof(mlmc_level_state) * cfg->n_levels, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_plan_set_workspace(mlmc_plan p, void* ws, uint64_t bytes) {
+  if (!p || (ws && (bytes == 0 || ((uintptr_t)ws & 255) != 0))) return MLMC_ERR_INVALID;
+  if (!p->round_count.empty()) return MLMC_ERR_INVALID;
+  CK(cudaStreamSynchronize(p->stream));
+  if (settle_graph_launches(p) != MLMC_OK) return MLMC_ERR_CUDA;
+  clear_graphs(p);   // graphs bake workspace addresses
+  if (p->ws && !p->ws_borrowed) cudaFree(p->ws);
+  p->ws = ws;
+  p->ws_bytes = ws ? (size_t)bytes : 0;
+  p->ws_borrowed = ws != nullptr;
+  if (ws) p->ws_budget = (size_t)bytes;
+  return MLMC_OK;
+}
+
+int64_t mlmc_round_bytes(const mlmc_config* cfg, const int64_t* count) {
+  if (!cfg || !count || validate(cfg) != MLMC_OK) return -1;
+  const int M = (int)ipow(cfg->modes_per_dim, cfg->dim);
+  int64_t total = 0;
+  for (int l = 0; l < cfg->n_levels; ++l) {
+    if (count[l] <= 0) continue;
+    MeshInfo mi;
+    mi.n = cfg->coarse_cells << l;
+    mi.K = 1;
+    mi.g[0] = make_grid(cfg->dim, mi.n);
+    if (cfg->solver == MLMC_GMG_PCG && mi.n > 2) {
+      int n = mi.n;
+      while (n > 2 && mi.K < MAX_MG) {
+        n /= 2;
+        mi.g[mi.K++] = make_grid(cfg->dim, n);
+      }
+    }
+    total += round_up((int64_t)coupled_bytes(mi, M, count[l], cfg->precision == MLMC_MIXED), 256);
+  }
+  return total;
+}
+
 mlmc_status mlmc_plan_destroy(mlmc_plan p) {
   if (!p) return MLMC_ERR_INVALID;
   cudaStreamSynchronize(p->stream);
@@ -1270,6 +1377,7 @@ mlmc_status mlmc_plan_destroy(mlmc_plan p) {
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   for (auto bs : p->branch) cudaStreamDestroy(bs);
   for (auto ev : p->branch_ev) cudaEventDestroy(ev);
+  if (p->round_done) cudaEventDestroy(p->round_done);
   for (auto& mi : p->meshes)
     if (mi.table) cudaFree(mi.table);
   cudaFree(p->d_omega);
@@ -1280,7 +1388,7 @@ mlmc_status mlmc_plan_destroy(mlmc_plan p) {
   cudaFree(p->d_small);
   cudaFree(p->d_N);
   cudaFree(p->d_prof);
-  if (p->ws) cudaFree(p->ws);
+  if (p->ws && !p->ws_borrowed) cudaFree(p->ws);
   if (p->h_pin) cudaFreeHost(p->h_pin);
   for (auto& e : p->pending) {
     cudaEventDestroy(e.a);
@@ -1566,6 +1674,49 @@ mlmc_status mlmc_kernel_stats(mlmc_plan p, int kid, mlmc_kernel_stat* out) {
   out->launches = p->kl[kid];
   out->ms = p->ms[kid];
   out->bytes = bytes;
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_round_begin(mlmc_plan p, const int64_t* first, const int64_t* count) {
+  if (!p || !first || !count) return MLMC_ERR_INVALID;
+  if (!graphs_on(p)) return MLMC_ERR_UNIMPLEMENTED;
+  if (!p->round_count.empty()) return MLMC_ERR_INVALID;   // a round is in flight
+  const int L1 = p->cfg.n_levels;
+  std::vector<int64_t> f(first, first + L1), c(count, count + L1);
+  for (int l = 0; l < L1; ++l)
+    if (f[l] < 0 || c[l] < 0 || f[l] + c[l] > (int64_t(1) << 32)) return MLMC_ERR_INVALID;
+  mlmc_status st = round_launch(p, f, c);
+  if (st != MLMC_OK) p->round_count.clear();
+  return st;
+}
+
+int mlmc_round_ready(mlmc_plan p) {
+  if (!p) return -1;
+  if (p->round_count.empty()) return 1;
+  const cudaError_t e = cudaEventQuery(p->round_done);
+  if (e == cudaSuccess) return 1;
+  if (e == cudaErrorNotReady) return 0;
+  cudaGetLastError();
+  return -1;
+}
+
+mlmc_status mlmc_round_end(mlmc_plan p) {
+  if (!p) return MLMC_ERR_INVALID;
+  if (p->round_count.empty()) return MLMC_OK;
+  bool bad = false;
+  mlmc_status st = round_finish(p, &bad);
+  if (st != MLMC_OK) return st;
+  return bad ? MLMC_ERR_NOT_CONVERGED : MLMC_OK;
+}
+
+mlmc_status mlmc_allocation(mlmc_plan p, double eps, int64_t* N_out) {
+  if (!p || !N_out || !(eps > 0.0)) return MLMC_ERR_INVALID;
+  const int L1 = p->cfg.n_levels;
+  CK(run(p, KID_ESTIMATE, [&] {
+    return launch_estimate(p->stream, p->d_states, L1, p->d_cost, eps, p->d_small, p->d_N);
+  }));
+  CK(cudaMemcpyAsync(N_out, p->d_N, sizeof(int64_t) * L1, cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
   return MLMC_OK;
 }
 

@@ -68,6 +68,22 @@ class KernelStat(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("ms", ctypes.c_double), ("bytes", ctypes.c_double)]
 
 
+class ServerConfig(ctypes.Structure):
+    """Mirror of ``mlmc_server_config``."""
+    _fields_ = [("hbm_budget", ctypes.c_uint64), ("max_slots", ctypes.c_int32),
+                ("pilot", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("max_rounds", ctypes.c_int32)]
+
+
+class RequestResult(ctypes.Structure):
+    """Mirror of ``mlmc_request_result``."""
+    _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int32), ("rounds", ctypes.c_int32),
+                ("q_hat", ctypes.c_double), ("stat_var", ctypes.c_double),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("dof_solves", ctypes.c_double),
+                ("N", ctypes.c_int64 * 16)]
+
+
 _P = ctypes.c_void_p
 _I = ctypes.c_int
 _I64 = ctypes.c_int64
@@ -76,7 +92,7 @@ _DP = ctypes.POINTER(ctypes.c_double)
 _I32P = ctypes.POINTER(ctypes.c_int32)
 _I64P = ctypes.POINTER(ctypes.c_int64)
 
-# (name, restype, argtypes) for every symbol of include/mlmc.h
+# (name, restype, argtypes) for every symbol of include/mlmc.h and include/mlmc_server.h
 SIGNATURES = [
     ("mlmc_config_default", None, [ctypes.POINTER(Config)]),
     ("mlmc_node_stride", _I64, [_I, _I]),
@@ -103,6 +119,20 @@ SIGNATURES = [
     ("mlmc_kernel_stats", _I, [_P, _I, ctypes.POINTER(KernelStat)]),
     ("mlmc_launch_count", _I64, [_P]),
     ("mlmc_solve_noalloc", _I, [ctypes.POINTER(Config), _I, _P, _I64, _P, _P, _P]),
+    ("mlmc_round_begin", _I, [_P, _I64P, _I64P]),
+    ("mlmc_round_ready", _I, [_P]),
+    ("mlmc_round_end", _I, [_P]),
+    ("mlmc_allocation", _I, [_P, _D, _I64P]),
+    ("mlmc_plan_retarget", _I, [_P, ctypes.POINTER(Config)]),
+    ("mlmc_round_bytes", _I64, [ctypes.POINTER(Config), _I64P]),
+    ("mlmc_plan_set_workspace", _I, [_P, _P, ctypes.c_uint64]),
+    # include/mlmc_server.h
+    ("mlmc_server_create", _I, [ctypes.POINTER(ServerConfig), ctypes.POINTER(_P)]),
+    ("mlmc_server_submit", _I, [_P, ctypes.POINTER(Config), _D, ctypes.POINTER(ctypes.c_uint64)]),
+    ("mlmc_server_poll", _I, [_P, ctypes.c_uint64, ctypes.POINTER(_I), ctypes.POINTER(RequestResult)]),
+    ("mlmc_server_drain", _I, [_P, _D]),
+    ("mlmc_server_clock", _D, [_P]),
+    ("mlmc_server_destroy", _I, [_P]),
 ]
 
 
@@ -308,6 +338,62 @@ class Plan:
 
     def launch_count(self):
         return lib().mlmc_launch_count(self._h)
+
+
+class Server:
+    """An mlmc_server: continuous-batching MLMC estimation requests.
+
+    ``submit(cfg, eps)`` queues one adaptive estimation and returns its id;
+    ``poll(id)`` returns None while it runs, else a dict of its result
+    (times in seconds on the server clock)."""
+
+    def __init__(self, hbm_budget=0, max_slots=8, pilot=32, device=0, max_rounds=0):
+        sc = ServerConfig(hbm_budget=int(hbm_budget), max_slots=int(max_slots), pilot=int(pilot),
+                          device=int(device), max_rounds=int(max_rounds))
+        self._h = _P()
+        check(lib().mlmc_server_create(ctypes.byref(sc), ctypes.byref(self._h)),
+              "mlmc_server_create")
+
+    def submit(self, cfg, eps):
+        rid = ctypes.c_uint64()
+        check(lib().mlmc_server_submit(self._h, ctypes.byref(cfg), float(eps), ctypes.byref(rid)),
+              "mlmc_server_submit")
+        return rid.value
+
+    def poll(self, rid):
+        done = ctypes.c_int()
+        r = RequestResult()
+        check(lib().mlmc_server_poll(self._h, rid, ctypes.byref(done), ctypes.byref(r)),
+              "mlmc_server_poll")
+        if not done.value:
+            return None
+        n = [int(x) for x in r.N]
+        return dict(id=r.id, status=r.status, rounds=r.rounds, q_hat=r.q_hat,
+                    stat_var=r.stat_var, t_submit=r.t_submit, t_admit=r.t_admit,
+                    t_done=r.t_done, dof_solves=r.dof_solves, N=n)
+
+    def drain(self, timeout=600.0):
+        check(lib().mlmc_server_drain(self._h, float(timeout)), "mlmc_server_drain")
+
+    def clock(self):
+        return lib().mlmc_server_clock(self._h)
+
+    def close(self):
+        if self._h:
+            check(lib().mlmc_server_destroy(self._h), "mlmc_server_destroy")
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def allocate(V, C, eps):

@@ -10,6 +10,8 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "mlmc.h")
+HEADERS = sorted(os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include"))
+                 if f.endswith(".h"))
 
 
 @pytest.fixture(scope="module")
@@ -22,9 +24,11 @@ def m():
 
 
 def declared_functions():
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(mlmc_[a-z0-9_]+)\s*\(", text)))
+    names = set()
+    for h in HEADERS:
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"\b(mlmc_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
 
 
 def test_every_declared_symbol_is_exported_and_bound(m):
@@ -41,11 +45,13 @@ def test_struct_layout_matches_header(m):
     src = r'''
     #include <stdio.h>
     #include <stddef.h>
-    #include "mlmc.h"
+    #include "mlmc_server.h"
     int main(void) {
-      printf("%zu %zu %zu %zu %zu %zu\n", sizeof(mlmc_config), offsetof(mlmc_config, seed),
+      printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(mlmc_config), offsetof(mlmc_config, seed),
              offsetof(mlmc_config, mg_omega), offsetof(mlmc_config, workspace_bytes),
-             sizeof(mlmc_level_state), sizeof(mlmc_kernel_stat));
+             sizeof(mlmc_level_state), sizeof(mlmc_kernel_stat), sizeof(mlmc_server_config),
+             sizeof(mlmc_request_result), offsetof(mlmc_request_result, dof_solves),
+             offsetof(mlmc_request_result, N));
       return 0;
     }'''
     with tempfile.TemporaryDirectory() as d:
@@ -56,7 +62,9 @@ def test_struct_layout_matches_header(m):
         out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
     got = [ctypes.sizeof(m.Config), m.Config.seed.offset, m.Config.mg_omega.offset,
            m.Config.workspace_bytes.offset, ctypes.sizeof(m.LevelState),
-           ctypes.sizeof(m.KernelStat)]
+           ctypes.sizeof(m.KernelStat), ctypes.sizeof(m.ServerConfig),
+           ctypes.sizeof(m.RequestResult), m.RequestResult.dof_solves.offset,
+           m.RequestResult.N.offset]
     assert [int(x) for x in out] == got
 
 
@@ -101,3 +109,34 @@ def test_allocate_rejects_bad_input(m):
     st = m.lib().mlmc_allocate(V.ctypes.data_as(m._DP), C.ctypes.data_as(m._DP), 2, 0.1,
                                N.ctypes.data_as(m._I64P))
     assert st == m.MLMC_ERR_INVALID
+
+
+def test_server_entry_points_reject_bad_arguments_without_a_device(m):
+    L = m.lib()
+    h = ctypes.c_void_p()
+    for sc in (m.ServerConfig(max_slots=0, pilot=8), m.ServerConfig(max_slots=4, pilot=1),
+               m.ServerConfig(max_slots=1000, pilot=8), m.ServerConfig(max_slots=4, pilot=8, device=-1)):
+        assert L.mlmc_server_create(ctypes.byref(sc), ctypes.byref(h)) == m.MLMC_ERR_INVALID
+        assert not h.value
+    cfg = m.config()
+    rid = ctypes.c_uint64()
+    assert L.mlmc_server_submit(None, ctypes.byref(cfg), 1e-3, ctypes.byref(rid)) == m.MLMC_ERR_INVALID
+    done = ctypes.c_int()
+    assert L.mlmc_server_poll(None, 1, ctypes.byref(done), None) == m.MLMC_ERR_INVALID
+    assert L.mlmc_server_drain(None, 1.0) == m.MLMC_ERR_INVALID
+    assert L.mlmc_server_clock(None) == -1.0
+    assert L.mlmc_server_destroy(None) == m.MLMC_ERR_INVALID
+
+
+def test_round_bytes_grows_with_counts(m):
+    L = m.lib()
+    cfg = m.config(dim=2, n_levels=3, coarse_cells=8, solver="gmg")
+    arr = lambda xs: (ctypes.c_int64 * 3)(*xs)
+    zero = L.mlmc_round_bytes(ctypes.byref(cfg), arr([0, 0, 0]))
+    one = L.mlmc_round_bytes(ctypes.byref(cfg), arr([1, 1, 1]))
+    two = L.mlmc_round_bytes(ctypes.byref(cfg), arr([2, 2, 2]))
+    fine = L.mlmc_round_bytes(ctypes.byref(cfg), arr([0, 0, 4]))
+    coarse = L.mlmc_round_bytes(ctypes.byref(cfg), arr([4, 0, 0]))
+    assert zero == 0 and 0 < one < two and fine > coarse > 0
+    cfg.dim = 7
+    assert L.mlmc_round_bytes(ctypes.byref(cfg), arr([1, 1, 1])) == -1
