@@ -27,7 +27,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from synth import workload  # noqa: E402
+from synth import serving_request, serving_stream, workload  # noqa: E402
 
 WORKLOAD = "2d-scale"
 
@@ -46,6 +46,12 @@ def parse():
     ap.add_argument("--form", default="fp64", choices=["fp64", "mixed"],
                     help="form of the headline line (the other form is measured alongside)")
     ap.add_argument("--single-form", action="store_true")
+    ap.add_argument("--serve", type=float, default=0.0,
+                    help="also run the serving stream for this many seconds of Poisson arrivals")
+    ap.add_argument("--serve-only", action="store_true")
+    ap.add_argument("--serve-rate", type=float, default=20.0)
+    ap.add_argument("--serve-slots", type=int, default=24)
+    ap.add_argument("--serve-pilot", type=int, default=32)
     ap.add_argument("--no-graphs", action="store_true",
                     help="host-driven solver loops (same kernels; ncu cannot profile kernels "
                          "inside graphs with conditional nodes)")
@@ -268,6 +274,67 @@ def measure_form(m, wl, cfg, stream, args, world, barrier, with_e2e):
                 dstat=dstat, shares=shares, clocks=clk, launches=launches, wall=wall)
 
 
+def serving_run(m, args, device=0):
+    """The serving stream: Poisson arrivals submitted at their arrival times to
+    one server; returns latency percentiles and aggregate throughput."""
+    import numpy as np
+    import torch
+    n_req = max(1, int(round(args.serve * args.serve_rate)))
+    stream = serving_stream(n_req, rate=args.serve_rate, seed=1)
+    srv = m.Server(max_slots=args.serve_slots, pilot=args.serve_pilot, device=device)
+    try:
+        # warm-up: every plan shape the stream can ask for, a slot's worth each
+        warm = []
+        for dim, modes in ((2, (5, 6, 7, 8)), (3, (5, 6, 7))):
+            for mm in modes:
+                for j in range(3):
+                    wl = serving_request(dim, 1.0, 1.5 / (mm - 0.5), 10 ** 6 + len(warm))
+                    warm.append(srv.submit(m.config_from_workload(wl), 5e-3))
+        srv.drain(timeout=900.0)
+        clocks = ClockSampler(device)
+        torch.cuda.synchronize()
+        clocks.start()
+        t0 = srv.clock()
+        ids = []
+        for (ta, wl, eps) in stream:
+            delay = t0 + ta - srv.clock()
+            if delay > 0:
+                time.sleep(delay)
+            ids.append(srv.submit(m.config_from_workload(wl), eps))
+        srv.drain(timeout=3600.0)
+        clk = clocks.stop()
+        res = [srv.poll(i) for i in ids]
+    finally:
+        srv.close()
+    bad = [r for r in res if r["status"] not in (0,)]
+    lat = np.array([r["t_done"] - r["t_submit"] for r in res])
+    wait = np.array([r["t_admit"] - r["t_submit"] for r in res])
+    span = max(r["t_done"] for r in res) - min(r["t_submit"] for r in res)
+    dofs = sum(r["dof_solves"] for r in res)
+    by_dim = {}
+    for (ta, wl, eps), r in zip(stream, res):
+        by_dim.setdefault(wl["dim"], []).append(r["t_done"] - r["t_submit"])
+    # most requests in flight at once
+    ev = sorted([(r["t_admit"], 1) for r in res] + [(r["t_done"], -1) for r in res])
+    cur = peak = 0
+    for _, d in ev:
+        cur += d
+        peak = max(peak, cur)
+    return {"requests": n_req, "rate_per_s": args.serve_rate, "arrival_seed": 1,
+            "slots": args.serve_slots, "pilot": args.serve_pilot, "failed": len(bad),
+            "p50_time_to_eps_s": float(np.percentile(lat, 50)),
+            "p99_time_to_eps_s": float(np.percentile(lat, 99)),
+            "mean_time_to_eps_s": float(lat.mean()),
+            "p50_by_dim_s": {str(d): float(np.percentile(v, 50)) for d, v in sorted(by_dim.items())},
+            "p99_admission_wait_s": float(np.percentile(wait, 99)),
+            "aggregate_dof_solves_per_s": dofs / span, "span_s": span,
+            "max_in_flight": peak, "rounds": int(sum(r["rounds"] for r in res)),
+            "clocks": clk,
+            "mix": "eps~U[5e-4,5e-3], dim 2|3 (p=1/2), sigma2~U[0.5,2], corr_len~U[0.05,0.3]; "
+                   "2D 32^2..1024^2 domain-mean QoI, 3D 8^3..128^3 box QoI; m=ceil(1.5/corr_len) "
+                   "capped 8 (2D) / 7 (3D); GMG-PCG rtol 1e-10, FP32 inner + FP64 refinement"}
+
+
 def roofline_of(res, peaks, fp64_alu):
     d_launches, d_ms, d_bytes = res["dstat"]
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
@@ -304,6 +371,10 @@ def bench_ours(args):
         if world > 1:
             dist.barrier()
 
+    if args.serve_only:
+        if rank == 0:
+            print(json.dumps({"serving": serving_run(m, args, local)}), flush=True)
+        return
     wl = workload(args.workload)
     stream = torch.cuda.Stream()
     # replicas: each rank runs an independent MLMC estimate on its own Philox stream
@@ -361,6 +432,8 @@ def bench_ours(args):
                 "e2e": {"value": e2e_value, "unit": "coupled DOF-solves/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "other_forms": {names[k]: v for k, v in other.items()}}
+        if args.serve > 0:
+            line["serving"] = serving_run(m, args, local)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.workload, list(range(min(wl["levels"], 5))))
         print(json.dumps(line), flush=True)

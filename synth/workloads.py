@@ -17,6 +17,9 @@ Keys:
   N          fixed sample counts (None -> adaptive)
 """
 import copy
+import math
+
+import numpy as np
 
 WORKLOADS = {
     # 2D plain FP64, 16^2..64^2, Jacobi-PCG, fixed N = (200, 50, 20).
@@ -57,3 +60,35 @@ def small_case(dim=2, **overrides):
                 stream_id=0, eps=None, pilot=0, N=(8, 4, 2))
     base.update(overrides)
     return base
+
+
+def serving_request(dim, sigma2, corr_len, stream_id):
+    """One request of the serving stream: 32^2..1024^2 (2D, domain-mean QoI)
+    or 8^3..128^3 (3D, box QoI) elements, GMG-PCG rtol 1e-10, mixed form,
+    m = ceil(1.5 / corr_len) modes per axis capped at 8 (2D) or 7 (3D); the
+    request index is the Philox stream word."""
+    m = min(int(math.ceil(1.5 / corr_len)), 8 if dim == 2 else 7)
+    if dim == 2:
+        return dict(dim=2, n0=32, levels=6, sigma2=sigma2, corr_len=corr_len, m=m,
+                    qoi='domain', box=(0.25, 0.75), solver='gmg', rtol=1e-10, seed=0,
+                    stream_id=stream_id, eps=None, pilot=0, N=None, precision='mixed')
+    return dict(dim=3, n0=8, levels=5, sigma2=sigma2, corr_len=corr_len, m=m,
+                qoi='box', box=(0.25, 0.75), solver='gmg', rtol=1e-10, seed=0,
+                stream_id=stream_id, eps=None, pilot=0, N=None, precision='mixed')
+
+
+def serving_stream(n_requests, rate=20.0, seed=1):
+    """Poisson arrivals at `rate` per second: a list of (arrival time in s,
+    workload, eps) with eps ~ U[5e-4, 5e-3], dim 2 or 3 with probability 1/2,
+    sigma2 ~ U[0.5, 2], corr_len ~ U[0.05, 0.3]."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for k in range(n_requests):
+        t += rng.exponential(1.0 / rate)
+        eps = rng.uniform(5e-4, 5e-3)
+        dim = 2 if rng.random() < 0.5 else 3
+        sigma2 = rng.uniform(0.5, 2.0)
+        corr = rng.uniform(0.05, 0.3)
+        out.append((t, serving_request(dim, sigma2, corr, k), eps))
+    return out
