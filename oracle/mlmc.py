@@ -18,6 +18,12 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 * Sec. 2.3 / Algorithm 2 with L fixed: pilot samples, then repeat
   {update N_l from the current V_l, C_l; draw the missing samples} until no
   level needs more samples.
+* Sec. 2.3 / Algorithm 2 with L adapted: the discretisation error is modelled
+  as |E(Q_l - Q)| = c s^(-alpha l) (s = 2, c absorbing h_0^alpha), so
+  |E(Y_l)| = c (s^alpha - 1) s^(-alpha l) for l >= 1; alpha and c are fitted
+  from the level means |Ybar_l|, l = 1..L, and Eq. (mlmc_num_levels)
+  L = ceil(log_s(sqrt(2) c / eps) / alpha) gives the level that brings the
+  bias below eps / sqrt(2). Levels that appear get pilot samples first.
 """
 import math
 
@@ -94,6 +100,78 @@ def allocate(V, C, eps):
     C = np.asarray(C, dtype=np.float64)
     s = float(np.sum(np.sqrt(V * C)))
     return [int(math.ceil(2.0 / eps ** 2 * math.sqrt(v / c) * s)) for v, c in zip(V, C)]
+
+
+ALPHA_DEFAULT = 2.0          # the linear-FE rate quoted in Sec. 2.2, used with one difference level
+ALPHA_RANGE = (0.5, 4.0)     # clamp of the fitted rate
+
+
+def fit_bias(means):
+    """(alpha, c) of |E(Q_l - Q)| = c 2^(-alpha l) from the level means.
+
+    Least squares of y_l = log2|Ybar_l| = log2(c (2^alpha - 1)) - alpha l over
+    the levels l >= 1 with a nonzero mean; alpha clamped to ALPHA_RANGE, then
+    the intercept a = mean(y_l + alpha l) and c = 2^a / (2^alpha - 1).
+    One usable level: alpha = ALPHA_DEFAULT. None: (None, None)."""
+    pts = [(l, math.log2(abs(means[l]))) for l in range(1, len(means)) if means[l] != 0.0]
+    if not pts:
+        return None, None
+    if len(pts) == 1:
+        alpha = ALPHA_DEFAULT
+    else:
+        lbar = sum(l for l, _ in pts) / len(pts)
+        ybar = sum(y for _, y in pts) / len(pts)
+        sxy = sum((l - lbar) * (y - ybar) for l, y in pts)
+        sxx = sum((l - lbar) * (l - lbar) for l, _ in pts)
+        alpha = -sxy / sxx
+    alpha = min(max(alpha, ALPHA_RANGE[0]), ALPHA_RANGE[1])
+    a = sum(y + alpha * l for l, y in pts) / len(pts)
+    c = 2.0 ** a / (2.0 ** alpha - 1.0)
+    return alpha, c
+
+
+def num_levels(alpha, c, eps):
+    """Eq. (mlmc_num_levels) with s = 2: L = ceil(log2(sqrt(2) c / eps) / alpha)."""
+    return int(math.ceil(math.log2(math.sqrt(2.0) * c / eps) / alpha))
+
+
+def run_adaptive_levels(cfg, eps, pilot, L0, max_rounds=20, sampler=None):
+    """Adaptive MLMC with L updated by Eq. (mlmc_num_levels) (Sec. 2.3, Algorithm 2).
+
+    Starts on levels 0..L0; after every sampling phase the sample counts of
+    the active levels follow Eq. (mlmc_num_samples) and L grows (never
+    shrinks, never beyond the hierarchy) to the level the bias fit asks for;
+    new levels get `pilot` samples. Stops when neither changes.
+    Returns (q_hat, stat_var, states, L)."""
+    sampler = sampler or (lambda l, i: coupled_sample(cfg, l, i))
+    Lmax = cfg['levels'] - 1
+    L = min(L0, Lmax)
+    states = [Welford() for _ in range(Lmax + 1)]
+    target = [pilot] * (L + 1) + [0] * (Lmax - L)
+    for _ in range(max_rounds):
+        for l in range(L + 1):
+            while states[l].n < target[l]:
+                qf, qc = sampler(l, states[l].n)
+                states[l].add(qf - qc)
+        V = [states[l].var() for l in range(L + 1)]
+        C = [level_cost(cfg, l) for l in range(L + 1)]
+        need = allocate(V, C, eps)
+        alpha, c = fit_bias([states[l].mean for l in range(L + 1)])
+        Lnew = L if alpha is None else min(max(num_levels(alpha, c, eps), L), Lmax)
+        more = False
+        for l in range(L + 1):
+            if need[l] > target[l]:
+                target[l] = need[l]
+                more = True
+        if Lnew > L:
+            for l in range(L + 1, Lnew + 1):
+                target[l] = pilot
+            L = Lnew
+            more = True
+        if not more:
+            break
+    q, v = estimate(states[:L + 1])
+    return q, v, states, L
 
 
 def estimate(states):

@@ -6,6 +6,12 @@ Chan merges of any partition equal the whole; the allocation of Eq.
 sum V_l / N_l <= eps^2 / 2; Table 1 against Eq. (sample_scaling); the
 coupling (both meshes of a pair see xi(l, i)); the telescoping identity of
 Eq. (mlmc_average); level variances decay with the mesh (Sec. 2.2).
+Adaptive L (Sec. 2.3, Eq. (mlmc_num_levels)): the bias fit recovers (alpha,
+c) from level means built as differences of Q_l = Q + c 2^(-alpha l); the
+level rule returns the smallest L with c 2^(-alpha L) <= eps / sqrt(2) (brute
+force); the adaptive run on a synthetic sampler with a known bias ends with
+both the bias and the statistical error within their eps^2 / 2 shares, and
+reduces to the fixed-L run when it starts on every level.
 """
 import json
 import math
@@ -134,3 +140,80 @@ def test_cost_model():
     assert mlmc.level_cost(cfg, 0) == 1
     assert mlmc.level_cost(cfg, 1) == 27 + 1
     assert mlmc.level_cost(cfg, 2) == 343 + 27
+
+
+# ---------------------------------------------------------- adaptive L
+
+def model_means(q_inf, c, alpha, L):
+    """Level means of Y_0 = Q_0, Y_l = Q_l - Q_{l-1} for Q_l = q_inf + c 2^(-alpha l)."""
+    Q = [q_inf + c * 2.0 ** (-alpha * l) for l in range(L + 1)]
+    return [Q[0]] + [Q[l] - Q[l - 1] for l in range(1, L + 1)]
+
+
+@pytest.mark.parametrize("alpha,c,q_inf", [(2.0, 0.3, 0.7), (1.0, 5e-3, 0.7), (1.37, 2.0, 0.7),
+                                           (3.5, 1e-4, 0.0)])
+def test_bias_fit_recovers_rate_and_constant(alpha, c, q_inf):
+    # (q_inf = 0 where the differences would lose digits to cancellation)
+    a, cc = mlmc.fit_bias(model_means(q_inf, c, alpha, 5))
+    assert abs(a - alpha) < 1e-10 and abs(cc - c) < 1e-10 * c
+
+
+def test_bias_fit_single_level_uses_default_rate_and_clamps():
+    # one difference level: the default rate, c from that level
+    a, c = mlmc.fit_bias(model_means(1.0, 0.2, 2.0, 1))
+    assert a == mlmc.ALPHA_DEFAULT and abs(c - 0.2) < 1e-12
+    # a mean that grows with l (noise) is clamped to the smallest rate
+    a, _ = mlmc.fit_bias([1.0, 1e-3, 4e-3, 1.6e-2])
+    assert a == mlmc.ALPHA_RANGE[0]
+    assert mlmc.fit_bias([1.0]) == (None, None)
+
+
+def test_level_rule_is_smallest_level_meeting_bias_share():
+    rng = np.random.default_rng(3)
+    for _ in range(500):
+        alpha = rng.uniform(0.5, 4.0)
+        c = 10 ** rng.uniform(-4, 1)
+        eps = 10 ** rng.uniform(-5, -1)
+        L = mlmc.num_levels(alpha, c, eps)
+        ok = [l for l in range(-60, 200) if c * 2.0 ** (-alpha * l) <= eps / math.sqrt(2.0)]
+        brute = min(ok)
+        # equal unless the bias sits on the boundary to rounding
+        if L != brute:
+            edge = c * 2.0 ** (-alpha * brute) / (eps / math.sqrt(2.0))
+            assert abs(edge - 1.0) < 1e-12
+        assert c * 2.0 ** (-alpha * L) <= eps / math.sqrt(2.0) * (1 + 1e-12)
+
+
+def synthetic_sampler(q_inf, c, alpha, noise, seed=0):
+    """Coupled pairs with a known bias c 2^(-alpha l) and noise shrinking with l."""
+    def sample(level, i):
+        r = np.random.default_rng([seed, level, i]).standard_normal(2)
+        qf = q_inf + c * 2.0 ** (-alpha * level) + noise * r[0] + noise * 2.0 ** (-level) * r[1]
+        if level == 0:
+            return qf, 0.0
+        qc = q_inf + c * 2.0 ** (-alpha * (level - 1)) + noise * r[0]
+        return qf, qc
+    return sample
+
+
+@pytest.mark.parametrize("eps", [3e-3, 1e-3, 3e-4])
+def test_adaptive_levels_meet_both_error_shares(eps):
+    cfg = dict(dim=2, n0=4, levels=9)
+    q_inf, c, alpha = 0.5, 0.2, 2.0
+    q, v, states, L = mlmc.run_adaptive_levels(
+        cfg, eps, pilot=20, L0=2, sampler=synthetic_sampler(q_inf, c, alpha, 0.01))
+    # the bias at the final level is within its share (up to the fit's noise)
+    assert c * 2.0 ** (-alpha * L) <= eps / math.sqrt(2.0) * 1.5
+    assert L < 8 and L >= 2
+    assert v <= eps ** 2 / 2 * (1 + 1e-12)
+    assert all(s.n == 0 for s in states[L + 1:])
+    assert abs(q - q_inf) < 4 * math.sqrt(v) + c * 2.0 ** (-alpha * L)
+
+
+def test_adaptive_levels_reduce_to_fixed_run_when_starting_on_every_level():
+    cfg = small_case(2, n0=4, levels=3)
+    smp = synthetic_sampler(0.3, 0.05, 2.0, 0.02, seed=4)
+    q1, v1, s1, _ = mlmc.run(cfg, 1e-3, 10, sampler=smp)
+    q2, v2, s2, L = mlmc.run_adaptive_levels(cfg, 1e-3, 10, L0=2, sampler=smp)
+    assert L == 2 and (q1, v1) == (q2, v2)
+    assert [s.n for s in s1] == [s.n for s in s2]
