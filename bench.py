@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--serve-slots", type=int, default=24)
     ap.add_argument("--serve-pilot", type=int, default=32)
+    ap.add_argument("--serve-adapt", type=int, default=2,
+                    help="requests start on levels 0..K and adapt L (0: all levels, L fixed)")
     ap.add_argument("--no-graphs", action="store_true",
                     help="host-driven solver loops (same kernels; ncu cannot profile kernels "
                          "inside graphs with conditional nodes)")
@@ -281,7 +283,8 @@ def serving_run(m, args, device=0):
     import torch
     n_req = max(1, int(round(args.serve * args.serve_rate)))
     stream = serving_stream(n_req, rate=args.serve_rate, seed=1)
-    srv = m.Server(max_slots=args.serve_slots, pilot=args.serve_pilot, device=device)
+    srv = m.Server(max_slots=args.serve_slots, pilot=args.serve_pilot, device=device,
+                   adapt_from=args.serve_adapt)
     try:
         # warm-up: every plan shape the stream can ask for, a slot's worth each
         warm = []
@@ -322,6 +325,10 @@ def serving_run(m, args, device=0):
         peak = max(peak, cur)
     return {"requests": n_req, "rate_per_s": args.serve_rate, "arrival_seed": 1,
             "slots": args.serve_slots, "pilot": args.serve_pilot, "failed": len(bad),
+            "levels": ("adaptive from levels 0..%d (Eq. mlmc_num_levels)" % args.serve_adapt
+                       if args.serve_adapt > 0 else "all levels of the range"),
+            "levels_used_hist": {str(k): sum(1 for r in res if r["levels"] == k)
+                                 for k in sorted(set(r["levels"] for r in res))},
             "p50_time_to_eps_s": float(np.percentile(lat, 50)),
             "p99_time_to_eps_s": float(np.percentile(lat, 99)),
             "mean_time_to_eps_s": float(lat.mean()),

@@ -184,6 +184,29 @@ mlmc_status mlmc_allocate(const double* V, const double* C, int n_levels, double
 mlmc_status mlmc_run(mlmc_plan plan, double eps, int64_t pilot, const int64_t* N_fixed,
                      double* q_hat, double* stat_var, int64_t* N_out);
 
+/* Adaptive MLMC with the number of levels adapted as well (Sec. 2.3,
+ * Algorithm 2): start on levels 0..L0 with `pilot` (>= 1) samples each;
+ * after every sampling phase run mlmc_adapt and take its sample counts
+ * (never lowering one) and its level (new levels get `pilot` samples), until
+ * neither changes. The plan's n_levels - 1 is the largest level it may
+ * reach; L0 >= 1 is needed for the level to move (the fit needs a level
+ * difference). Outputs: estimate and sum_l V_l / N_l over the active levels,
+ * N_out (host, n_levels entries, 0 beyond the final level), *L_out the final
+ * level. NOT_CONVERGED as for mlmc_run. */
+mlmc_status mlmc_run_adaptive(mlmc_plan plan, double eps, int64_t pilot, int32_t L0,
+                              double* q_hat, double* stat_var, int64_t* N_out, int32_t* L_out);
+
+/* One adaptive step at a phase boundary, from the device level states of
+ * levels 0..L_active: N_out[0..L_active] (host) per Eq. (mlmc_num_samples)
+ * and *L_out per Eq. (mlmc_num_levels) with s = 2 and the bias model
+ * |E(Q_l - Q)| = c 2^(-alpha l), alpha and c fitted by least squares on
+ * log2 |mean(Y_l)| over l = 1..L_active (levels with a zero mean skipped;
+ * one level: alpha = 2; alpha clamped to [0.5, 4]). *L_out lies in
+ * [L_active, n_levels - 1]; it equals L_active when no level l >= 1 has a
+ * nonzero mean. fit_out (host, nullable) receives {alpha, c}. */
+mlmc_status mlmc_adapt(mlmc_plan plan, int32_t L_active, double eps, int64_t* N_out,
+                       int32_t* L_out, double* fit_out);
+
 /* ---- asynchronous allocation rounds ----------------------------------- */
 
 /* Launch samples first[l] .. first[l] + count[l] - 1 of every level l

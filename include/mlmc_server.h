@@ -2,15 +2,16 @@
  * mlmc_server.h - continuous-batching MLMC estimation server on top of the
  * plan API of mlmc.h.
  *
- * A request is one adaptive MLMC estimation (Sec. 2.3 with the number of
- * levels fixed): a problem description (mlmc_config: field parameters,
+ * A request is one adaptive MLMC estimation (Sec. 2.3): a problem description (mlmc_config: field parameters,
  * hierarchy, solver, precision, seed) and a target RMSE eps. The server runs
  * it exactly like mlmc_run(plan, eps, pilot, NULL, ...): pilot samples on
  * every level, then the sample counts of Eq. (mlmc_num_samples) from the
  * request's own device-resident Welford variances (Eq. (sample_variance)),
- * then the missing samples, until no level needs more. Its estimate and
- * variance are bitwise those of mlmc_run with the same configuration and
- * pilot, whatever other requests run beside it: a sample's result depends
+ * then the missing samples, until no level needs more; or, with adapt_from
+ * = k >= 1, like mlmc_run_adaptive(plan, eps, pilot, k, ...), which also
+ * raises the number of levels by Eq. (mlmc_num_levels). Its estimate and
+ * variance are bitwise those of that plan call with the same configuration
+ * and pilot, whatever other requests run beside it: a sample's result depends
  * only on (config, level, sample index) and every level folds its samples
  * into its Welford state in sample order.
  *
@@ -49,12 +50,18 @@ typedef struct mlmc_server_config {
   int32_t pilot;         /* pilot samples per level (>= 2) */
   int32_t device;        /* CUDA device ordinal */
   int32_t max_rounds;    /* cap on allocation rounds per request (0 = 64) */
+  int32_t adapt_from;    /* 0: every request samples all its levels (L fixed,
+                            as mlmc_run); k >= 1: requests start on levels
+                            0..k and adapt L (as mlmc_run_adaptive, L0 = k) */
+  int32_t reserved;      /* 0 */
 } mlmc_server_config;
 
 typedef struct mlmc_request_result {
   uint64_t id;
   int32_t status;        /* mlmc_status of the request (OK, NOT_CONVERGED, ...) */
   int32_t rounds;        /* rounds of sampling launched */
+  int32_t levels;        /* levels sampled: final L + 1 */
+  int32_t reserved;
   double q_hat;          /* Eq. (mlmc_average) */
   double stat_var;       /* sum_l V_l / N_l */
   double t_submit;       /* seconds on the server clock */

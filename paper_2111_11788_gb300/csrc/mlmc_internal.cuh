@@ -309,6 +309,8 @@ cudaError_t launch_welford(cudaStream_t s, const double* qf, const double* qc, i
 cudaError_t launch_estimate(cudaStream_t s, const mlmc_level_state* st, int n_levels,
                             const double* cost, double eps, double* out2, int64_t* N);
 
+cudaError_t launch_adapt(cudaStream_t s, const mlmc_level_state* st, int La, int Lmax,
+                         const double* cost, double eps, int64_t* N, double* out3);
 cudaError_t launch_allocate(cudaStream_t s, const double* V, const double* C, int n_levels,
                             double eps, int64_t* N);
 

@@ -1133,6 +1133,31 @@ mlmc_status run_round(mlmc_plan p, const std::vector<int64_t>& first,
   return round_finish(p, bad);
 }
 
+// Draws the samples have[l] .. target[l] - 1 of every level and sets have
+// to target: one graph per round with a branch per level when the batches
+// fit the workspace together, otherwise level by level, finest first (the
+// priority of the paper's incremental greedy schedule).
+mlmc_status sample_phase(mlmc_plan p, std::vector<int64_t>& have, const std::vector<int64_t>& target,
+                         bool* bad) {
+  const int L1 = p->cfg.n_levels;
+  std::vector<int64_t> count(L1);
+  for (int l = 0; l < L1; ++l) count[l] = std::max<int64_t>(0, target[l] - have[l]);
+  mlmc_status st = graphs_on(p) ? run_round(p, have, count, bad) : MLMC_ERR_UNIMPLEMENTED;
+  if (st == MLMC_ERR_UNIMPLEMENTED) {
+    for (int l = L1 - 1; l >= 0; --l) {
+      if (count[l] > 0) {
+        st = mlmc_sample_level(p, l, have[l], count[l], nullptr, nullptr, nullptr);
+        if (st == MLMC_ERR_NOT_CONVERGED) *bad = true;
+        else if (st != MLMC_OK) return st;
+      }
+    }
+  } else if (st != MLMC_OK) {
+    return st;
+  }
+  for (int l = 0; l < L1; ++l) have[l] = std::max(have[l], target[l]);
+  return MLMC_OK;
+}
+
 }  // namespace
 
 // ===================================================================
@@ -1604,24 +1629,8 @@ mlmc_status mlmc_run(mlmc_plan p, double eps, int64_t pilot, const int64_t* N_fi
     }
   bool bad = false;
   for (int round = 0; round < 64; ++round) {
-    // one graph per round with a branch per level when the batches fit the
-    // workspace together; otherwise level by level, finest first (the
-    // priority of the paper's incremental greedy schedule)
-    std::vector<int64_t> count(L1);
-    for (int l = 0; l < L1; ++l) count[l] = std::max<int64_t>(0, target[l] - have[l]);
-    st = graphs_on(p) ? run_round(p, have, count, &bad) : MLMC_ERR_UNIMPLEMENTED;
-    if (st == MLMC_ERR_UNIMPLEMENTED) {
-      for (int l = L1 - 1; l >= 0; --l) {
-        if (count[l] > 0) {
-          st = mlmc_sample_level(p, l, have[l], count[l], nullptr, nullptr, nullptr);
-          if (st == MLMC_ERR_NOT_CONVERGED) bad = true;
-          else if (st != MLMC_OK) return st;
-        }
-      }
-    } else if (st != MLMC_OK) {
-      return st;
-    }
-    for (int l = 0; l < L1; ++l) have[l] = std::max(have[l], target[l]);
+    st = sample_phase(p, have, target, &bad);
+    if (st != MLMC_OK) return st;
     if (N_fixed) break;
     CK(run(p, KID_ESTIMATE, [&] {
       return launch_estimate(p->stream, p->d_states, L1, p->d_cost, eps, p->d_small, p->d_N);
@@ -1642,6 +1651,65 @@ mlmc_status mlmc_run(mlmc_plan p, double eps, int64_t pilot, const int64_t* N_fi
   if (st != MLMC_OK) return st;
   if (N_out)
     for (int l = 0; l < L1; ++l) N_out[l] = have[l];
+  return bad ? MLMC_ERR_NOT_CONVERGED : MLMC_OK;
+}
+
+mlmc_status mlmc_adapt(mlmc_plan p, int32_t L_active, double eps, int64_t* N_out, int32_t* L_out,
+                       double* fit_out) {
+  if (!p || !N_out || !L_out || !(eps > 0.0) || L_active < 0 || L_active >= p->cfg.n_levels)
+    return MLMC_ERR_INVALID;
+  CK(run(p, KID_ESTIMATE, [&] {
+    return launch_adapt(p->stream, p->d_states, L_active, p->cfg.n_levels - 1, p->d_cost, eps,
+                        p->d_N, p->d_small + 8);
+  }));
+  double h[3];
+  CK(cudaMemcpyAsync(N_out, p->d_N, sizeof(int64_t) * (L_active + 1), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaMemcpyAsync(h, p->d_small + 8, sizeof(h), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  *L_out = (int32_t)h[0];
+  if (fit_out) {
+    fit_out[0] = h[1];
+    fit_out[1] = h[2];
+  }
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_run_adaptive(mlmc_plan p, double eps, int64_t pilot, int32_t L0, double* q_hat,
+                              double* stat_var, int64_t* N_out, int32_t* L_out) {
+  if (!p || !(eps > 0.0) || pilot < 1 || L0 < 0) return MLMC_ERR_INVALID;
+  const int L1 = p->cfg.n_levels;
+  int32_t L = std::min<int32_t>(L0, L1 - 1);
+  mlmc_status st = mlmc_reset_stats(p);
+  if (st != MLMC_OK) return st;
+  std::vector<int64_t> have(L1, 0), target(L1, 0);
+  for (int l = 0; l <= L; ++l) target[l] = pilot;
+  bool bad = false;
+  for (int round = 0; round < 64; ++round) {
+    st = sample_phase(p, have, target, &bad);
+    if (st != MLMC_OK) return st;
+    if (round == 63) break;   // no more phases: keep L the last sampled level
+    int64_t N[16];
+    int32_t Lnew = L;
+    st = mlmc_adapt(p, L, eps, N, &Lnew, nullptr);
+    if (st != MLMC_OK) return st;
+    bool more = false;
+    for (int l = 0; l <= L; ++l)
+      if (N[l] > target[l]) {
+        target[l] = N[l];
+        more = true;
+      }
+    if (Lnew > L) {
+      for (int l = L + 1; l <= Lnew; ++l) target[l] = pilot;
+      L = Lnew;
+      more = true;
+    }
+    if (!more) break;
+  }
+  st = mlmc_estimate(p, q_hat, stat_var);
+  if (st != MLMC_OK) return st;
+  if (N_out)
+    for (int l = 0; l < L1; ++l) N_out[l] = have[l];
+  if (L_out) *L_out = L;
   return bad ? MLMC_ERR_NOT_CONVERGED : MLMC_OK;
 }
 

@@ -198,6 +198,59 @@ __global__ void k_estimate(const mlmc_level_state* st, int L, const double* __re
   if (N && eps > 0.0) allocate_dev(V, C, L, eps, N);
 }
 
+// One adaptive step over the active levels 0..La (Sec. 2.3): the sample
+// counts of Eq. (mlmc_num_samples), and the level of Eq. (mlmc_num_levels)
+// from the bias model |E(Q_l - Q)| = c 2^(-alpha l): least squares of
+// log2|Ybar_l| on l over the levels l >= 1 with a nonzero mean (rate 2 with
+// one such level), alpha clamped to [0.5, 4], intercept mean(y + alpha l),
+// c = 2^a / (2^alpha - 1). The new level never drops below La nor exceeds
+// Lmax. Products and sums are rounded one by one (no contraction), in the
+// order a plain sequential evaluation takes them.
+__global__ void k_adapt(const mlmc_level_state* st, int La, int Lmax, const double* __restrict__ C,
+                        double eps, int64_t* N, double* out3) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double V[16];
+  for (int l = 0; l <= La; ++l) V[l] = st[l].n > 0 ? st[l].m2 / (double)st[l].n : 0.0;
+  allocate_dev(V, C, La + 1, eps, N);
+  double ls[16], ys[16];
+  int np = 0;
+  for (int l = 1; l <= La; ++l) {
+    if (st[l].mean != 0.0) {
+      ls[np] = (double)l;
+      ys[np] = log2(fabs(st[l].mean));
+      ++np;
+    }
+  }
+  double Lnew = (double)La, alpha = 0.0, c = 0.0;
+  if (np > 0) {
+    if (np == 1) {
+      alpha = 2.0;
+    } else {
+      double lbar = 0.0, ybar = 0.0;
+      for (int k = 0; k < np; ++k) lbar = __dadd_rn(lbar, ls[k]);
+      lbar = __ddiv_rn(lbar, (double)np);
+      for (int k = 0; k < np; ++k) ybar = __dadd_rn(ybar, ys[k]);
+      ybar = __ddiv_rn(ybar, (double)np);
+      double sxy = 0.0, sxx = 0.0;
+      for (int k = 0; k < np; ++k)
+        sxy = __dadd_rn(sxy, __dmul_rn(__dsub_rn(ls[k], lbar), __dsub_rn(ys[k], ybar)));
+      for (int k = 0; k < np; ++k)
+        sxx = __dadd_rn(sxx, __dmul_rn(__dsub_rn(ls[k], lbar), __dsub_rn(ls[k], lbar)));
+      alpha = -__ddiv_rn(sxy, sxx);
+    }
+    alpha = fmin(fmax(alpha, 0.5), 4.0);
+    double a = 0.0;
+    for (int k = 0; k < np; ++k) a = __dadd_rn(a, __dadd_rn(ys[k], __dmul_rn(alpha, ls[k])));
+    a = __ddiv_rn(a, (double)np);
+    c = __ddiv_rn(exp2(a), __dsub_rn(exp2(alpha), 1.0));
+    const double Lr = ceil(__ddiv_rn(log2(__ddiv_rn(__dmul_rn(sqrt(2.0), c), eps)), alpha));
+    Lnew = fmin(fmax(Lr, (double)La), (double)Lmax);
+  }
+  out3[0] = Lnew;
+  out3[1] = alpha;
+  out3[2] = c;
+}
+
 __global__ void k_allocate(const double* V, const double* C, int L, double eps, int64_t* N) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   allocate_dev(V, C, L, eps, N);
@@ -266,6 +319,12 @@ cudaError_t launch_welford(cudaStream_t s, const double* qf, const double* qc, i
 cudaError_t launch_estimate(cudaStream_t s, const mlmc_level_state* st, int n_levels,
                             const double* cost, double eps, double* out2, int64_t* N) {
   k_estimate<<<1, 32, 0, s>>>(st, n_levels, cost, eps, out2, N);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adapt(cudaStream_t s, const mlmc_level_state* st, int La, int Lmax,
+                         const double* cost, double eps, int64_t* N, double* out3) {
+  k_adapt<<<1, 32, 0, s>>>(st, La, Lmax, cost, eps, N, out3);
   return cudaGetLastError();
 }
 

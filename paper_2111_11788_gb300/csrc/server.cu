@@ -53,6 +53,7 @@ struct Request {
   int64_t target[kMaxLevels] = {};
   int64_t inflight[kMaxLevels] = {};
   int phases = 0;   // completed sampling phases (each ends with an allocation)
+  int L = 0;        // highest active level
   bool bad = false;
   bool finished = false;
 };
@@ -240,6 +241,7 @@ void mlmc_server_s::finish(Request& r, mlmc_status st) {
     dofs += (double)r.have[l] * mlmc_level_cost(&r.cfg, l);
   }
   r.res.dof_solves = dofs;
+  r.res.levels = r.L + 1;
   r.res.status = st;
   r.res.t_done = now();
   // a plan whose last call failed is not reused
@@ -281,17 +283,24 @@ void mlmc_server_s::advance(Request& r) {
       return;
     }
     int64_t N[kMaxLevels];
-    const mlmc_status st = mlmc_allocation(r.slot->plan, r.eps, N);
+    int32_t Lnew = r.L;
+    const mlmc_status st = cfg.adapt_from > 0 ? mlmc_adapt(r.slot->plan, r.L, r.eps, N, &Lnew, nullptr)
+                                              : mlmc_allocation(r.slot->plan, r.eps, N);
     if (st != MLMC_OK) {
       finish(r, st);
       return;
     }
     bool more = false;
-    for (int l = 0; l < L1; ++l)
+    for (int l = 0; l <= r.L; ++l)
       if (N[l] > r.target[l]) {
         r.target[l] = N[l];
         more = true;
       }
+    if (Lnew > r.L) {
+      for (int l = r.L + 1; l <= Lnew; ++l) r.target[l] = cfg.pilot;
+      r.L = Lnew;
+      more = true;
+    }
     if (!more) {
       finish(r, MLMC_OK);
       return;
@@ -330,9 +339,11 @@ bool mlmc_server_s::admit() {
       finish(*owned, st);
       continue;
     }
-    for (int l = 0; l < owned->cfg.n_levels; ++l) {
+    const int Lmax = owned->cfg.n_levels - 1;
+    owned->L = cfg.adapt_from > 0 ? std::min(cfg.adapt_from, Lmax) : Lmax;
+    for (int l = 0; l <= Lmax; ++l) {
       owned->have[l] = 0;
-      owned->target[l] = cfg.pilot;
+      owned->target[l] = l <= owned->L ? cfg.pilot : 0;
     }
     advance(*owned);
     if (!owned->finished) active.push_back(std::move(owned));
@@ -396,7 +407,7 @@ mlmc_status mlmc_server_create(const mlmc_server_config* cfg, mlmc_server* out) 
   if (!out) return MLMC_ERR_INVALID;
   *out = nullptr;
   if (!cfg || cfg->max_slots < 1 || cfg->max_slots > 256 || cfg->pilot < 2 || cfg->device < 0 ||
-      cfg->max_rounds < 0)
+      cfg->max_rounds < 0 || cfg->adapt_from < 0)
     return MLMC_ERR_INVALID;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device >= ndev) {

@@ -72,12 +72,14 @@ class ServerConfig(ctypes.Structure):
     """Mirror of ``mlmc_server_config``."""
     _fields_ = [("hbm_budget", ctypes.c_uint64), ("max_slots", ctypes.c_int32),
                 ("pilot", ctypes.c_int32), ("device", ctypes.c_int32),
-                ("max_rounds", ctypes.c_int32)]
+                ("max_rounds", ctypes.c_int32), ("adapt_from", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class RequestResult(ctypes.Structure):
     """Mirror of ``mlmc_request_result``."""
     _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int32), ("rounds", ctypes.c_int32),
+                ("levels", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("q_hat", ctypes.c_double), ("stat_var", ctypes.c_double),
                 ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
                 ("t_done", ctypes.c_double), ("dof_solves", ctypes.c_double),
@@ -126,6 +128,8 @@ SIGNATURES = [
     ("mlmc_plan_retarget", _I, [_P, ctypes.POINTER(Config)]),
     ("mlmc_round_bytes", _I64, [ctypes.POINTER(Config), _I64P]),
     ("mlmc_plan_set_workspace", _I, [_P, _P, ctypes.c_uint64]),
+    ("mlmc_run_adaptive", _I, [_P, _D, _I64, ctypes.c_int32, _DP, _DP, _I64P, _I32P]),
+    ("mlmc_adapt", _I, [_P, ctypes.c_int32, _D, _I64P, _I32P, _DP]),
     # include/mlmc_server.h
     ("mlmc_server_create", _I, [ctypes.POINTER(ServerConfig), ctypes.POINTER(_P)]),
     ("mlmc_server_submit", _I, [_P, ctypes.POINTER(Config), _D, ctypes.POINTER(ctypes.c_uint64)]),
@@ -296,6 +300,27 @@ class Plan:
         check(st, "mlmc_run")
         return q.value, v.value, Nout
 
+    def run_adaptive(self, eps, pilot, L0):
+        """mlmc_run_adaptive: returns (q_hat, stat_var, N per level, final level)."""
+        import numpy as np
+        q, v = ctypes.c_double(), ctypes.c_double()
+        Nout = np.zeros(self.cfg.n_levels, dtype=np.int64)
+        L = ctypes.c_int32()
+        check(lib().mlmc_run_adaptive(self._h, float(eps), int(pilot), int(L0), ctypes.byref(q),
+                                      ctypes.byref(v), Nout.ctypes.data_as(_I64P), ctypes.byref(L)),
+              "mlmc_run_adaptive")
+        return q.value, v.value, Nout, L.value
+
+    def adapt(self, L_active, eps):
+        """mlmc_adapt: (N for levels 0..L_active, new level, (alpha, c))."""
+        import numpy as np
+        N = np.zeros(L_active + 1, dtype=np.int64)
+        L = ctypes.c_int32()
+        fit = (ctypes.c_double * 2)()
+        check(lib().mlmc_adapt(self._h, int(L_active), float(eps), N.ctypes.data_as(_I64P),
+                               ctypes.byref(L), fit), "mlmc_adapt")
+        return N, L.value, (fit[0], fit[1])
+
     # --- device-level API (raw device pointers) ---
     def draw_xi(self, level, first, count, xi_ptr):
         check(lib().mlmc_draw_xi(self._h, level, first, count, _P(xi_ptr)), "mlmc_draw_xi")
@@ -347,9 +372,10 @@ class Server:
     ``poll(id)`` returns None while it runs, else a dict of its result
     (times in seconds on the server clock)."""
 
-    def __init__(self, hbm_budget=0, max_slots=8, pilot=32, device=0, max_rounds=0):
+    def __init__(self, hbm_budget=0, max_slots=8, pilot=32, device=0, max_rounds=0, adapt_from=0):
         sc = ServerConfig(hbm_budget=int(hbm_budget), max_slots=int(max_slots), pilot=int(pilot),
-                          device=int(device), max_rounds=int(max_rounds))
+                          device=int(device), max_rounds=int(max_rounds),
+                          adapt_from=int(adapt_from))
         self._h = _P()
         check(lib().mlmc_server_create(ctypes.byref(sc), ctypes.byref(self._h)),
               "mlmc_server_create")
@@ -368,7 +394,7 @@ class Server:
         if not done.value:
             return None
         n = [int(x) for x in r.N]
-        return dict(id=r.id, status=r.status, rounds=r.rounds, q_hat=r.q_hat,
+        return dict(id=r.id, status=r.status, rounds=r.rounds, levels=r.levels, q_hat=r.q_hat,
                     stat_var=r.stat_var, t_submit=r.t_submit, t_admit=r.t_admit,
                     t_done=r.t_done, dof_solves=r.dof_solves, N=n)
 
