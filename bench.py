@@ -46,8 +46,9 @@ def parse():
     ap.add_argument("--form", default="fp64", choices=["fp64", "mixed"],
                     help="form of the headline line (the other form is measured alongside)")
     ap.add_argument("--single-form", action="store_true")
-    ap.add_argument("--serve", type=float, default=0.0,
-                    help="also run the serving stream for this many seconds of Poisson arrivals")
+    ap.add_argument("--serve", type=float, default=5.0,
+                    help="also run the serving stream for this many seconds of Poisson arrivals "
+                         "(0: skip)")
     ap.add_argument("--serve-only", action="store_true")
     ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--serve-slots", type=int, default=24)
@@ -276,7 +277,19 @@ def measure_form(m, wl, cfg, stream, args, world, barrier, with_e2e):
                 dstat=dstat, shares=shares, clocks=clk, launches=launches, wall=wall)
 
 
-def serving_run(m, args, device=0):
+def serving_both(m, args, device=0):
+    """The serving stream with adaptive levels (headline) and with every level
+    of the ranges sampled (L fixed)."""
+    res = serving_run(m, args, device, args.serve_adapt)
+    if args.serve_adapt > 0:
+        fixed = serving_run(m, args, device, 0)
+        keep = ("p50_time_to_eps_s", "p99_time_to_eps_s", "mean_time_to_eps_s",
+                "aggregate_dof_solves_per_s", "span_s", "max_in_flight", "failed", "rounds")
+        res["fixed_levels"] = {k: fixed[k] for k in keep}
+    return res
+
+
+def serving_run(m, args, device=0, adapt=0):
     """The serving stream: Poisson arrivals submitted at their arrival times to
     one server; returns latency percentiles and aggregate throughput."""
     import numpy as np
@@ -284,7 +297,7 @@ def serving_run(m, args, device=0):
     n_req = max(1, int(round(args.serve * args.serve_rate)))
     stream = serving_stream(n_req, rate=args.serve_rate, seed=1)
     srv = m.Server(max_slots=args.serve_slots, pilot=args.serve_pilot, device=device,
-                   adapt_from=args.serve_adapt)
+                   adapt_from=adapt)
     try:
         # warm-up: every plan shape the stream can ask for, a slot's worth each
         warm = []
@@ -325,8 +338,8 @@ def serving_run(m, args, device=0):
         peak = max(peak, cur)
     return {"requests": n_req, "rate_per_s": args.serve_rate, "arrival_seed": 1,
             "slots": args.serve_slots, "pilot": args.serve_pilot, "failed": len(bad),
-            "levels": ("adaptive from levels 0..%d (Eq. mlmc_num_levels)" % args.serve_adapt
-                       if args.serve_adapt > 0 else "all levels of the range"),
+            "levels": ("adaptive from levels 0..%d (Eq. mlmc_num_levels)" % adapt
+                       if adapt > 0 else "all levels of the range"),
             "levels_used_hist": {str(k): sum(1 for r in res if r["levels"] == k)
                                  for k in sorted(set(r["levels"] for r in res))},
             "p50_time_to_eps_s": float(np.percentile(lat, 50)),
@@ -380,7 +393,7 @@ def bench_ours(args):
 
     if args.serve_only:
         if rank == 0:
-            print(json.dumps({"serving": serving_run(m, args, local)}), flush=True)
+            print(json.dumps({"serving": serving_both(m, args, local)}), flush=True)
         return
     wl = workload(args.workload)
     stream = torch.cuda.Stream()
@@ -440,7 +453,7 @@ def bench_ours(args):
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "other_forms": {names[k]: v for k, v in other.items()}}
         if args.serve > 0:
-            line["serving"] = serving_run(m, args, local)
+            line["serving"] = serving_both(m, args, local)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.workload, list(range(min(wl["levels"], 5))))
         print(json.dumps(line), flush=True)
