@@ -73,11 +73,18 @@ struct Grid {
   int64_t ns;       // node stride (values per sample)
   int64_t es;       // element stride
   double h;
-  int sx, sy;       // stencil CTAs per sample (strip groups x row chunks)
-  int64_t tiles_s;  // partials per sample written by stencil kernels (one per warp)
+  int sx, sy;       // 2D: stencil CTAs per sample (strip groups x row chunks);
+                    // 3D: node-tile CTAs per sample of the pointwise kernels (sx)
+  int zc;           // 3D: z-planes per CTA of the z-marching stencil kernels
+  int zx;           // 3D: z-marching CTAs per sample
+  int64_t tiles_s;  // partials per sample written by stencil kernels
   int fx;           // flat CTAs per sample
   int64_t tiles_f;  // partials per sample written by flat kernels (one per CTA)
-  int64_t tiles() const { return tiles_s > tiles_f ? tiles_s : tiles_f; }
+  int64_t tiles_q;  // partials per sample written by the QoI kernel
+  int64_t tiles() const {
+    int64_t t = tiles_s > tiles_f ? tiles_s : tiles_f;
+    return t > tiles_q ? t : tiles_q;
+  }
 };
 
 Grid make_grid(int dim, int n);

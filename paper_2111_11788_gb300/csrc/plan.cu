@@ -20,7 +20,7 @@
 namespace mlmc {
 
 Grid make_grid(int dim, int n) {
-  Grid g;
+  Grid g{};
   g.dim = dim;
   g.n = n;
   g.ns = round_up(ipow(n + 1, dim), 32);
@@ -32,13 +32,18 @@ Grid make_grid(int dim, int n) {
     g.sy = (n + 1 + SROWS - 1) / SROWS;
     g.tiles_s = (int64_t)g.sx * g.sy * SWARPS;
   } else {
-    // one CTA per 32 x 8 node tile of each z-plane, one partial per CTA
+    // pointwise kernels: one CTA per 32 x 8 node tile of each z-plane;
+    // stencil kernels: one CTA per 32 x 8 column tile and chunk of zc planes
     g.sx = ((n + 1 + 31) / 32) * ((n + 1 + 7) / 8) * (n + 1);
     g.sy = 1;
-    g.tiles_s = g.sx;
+    g.zc = (n + 1 <= 24) ? n + 1 : 16;
+    g.zx = ((n + 31) / 32) * ((n + 7) / 8) * ((n + 1 + g.zc - 1) / g.zc);
+    g.tiles_s = g.zx;
   }
   g.fx = (int)((g.ns + FLAT_ELEMS - 1) / FLAT_ELEMS);
   g.tiles_f = g.fx;
+  // the 2D QoI kernel is flat, the 3D one runs on the node tiles
+  g.tiles_q = dim == 2 ? g.tiles_f : (int64_t)g.sx;
   return g;
 }
 
@@ -788,8 +793,7 @@ mlmc_status qoi_of(mlmc_plan p, const Grid& g0, const double* u, double* part, c
     return op::qoi<double>(p->stream, g0, box, L, H, box ? 1.0 / vol : 1.0, u, part, B,
                            prof_for(p, KID_QOI, nodes_of(g0) * 8));
   }));
-  // the 2D QoI kernel is flat (one partial per flat CTA), the 3D one tiled
-  const int64_t tq = g0.dim == 2 ? g0.tiles_f : g0.tiles_s;
+  const int64_t tq = g0.tiles_q;
   CK(run(p, KID_FINALIZE, [&] { return launch_finalize(p->stream, FIN_QOI, part, tq, sc, q_dev, 0, c.max_iter, B); }));
   return MLMC_OK;
 }

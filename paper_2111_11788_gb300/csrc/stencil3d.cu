@@ -13,11 +13,19 @@
 //   8 corner neighbours   -h/12 * (the 1 shared kappa)
 // and no face coupling.
 //
-// One thread per node, CTA tiles of 32 x 8 nodes in one z-plane; neighbour
-// values come through the L1 cache. Fields that the stencil acts on (p = z +
-// beta p_old, e = W b, e + P e_c) are first formed by a pointwise pass, so
-// every stencil kernel gathers one stored vector. Node arrays carry the boundary nodes
-// (always 0). Partials: one per CTA (g.tiles_s per sample).
+// Stencil kernels march along z: a CTA owns a 32 x 8 tile of node columns
+// and a chunk of zc planes. Each step stages one plane of the input vector
+// (34 x 10 with the halo) and one layer of kappa (33 x 9 elements) in shared
+// memory, double buffered, while the next plane is fetched into registers.
+// A plane p feeds three outputs of a column: p - 1 (the 8 couplings across
+// layer p - 1, after which output p - 1 is complete and goes to the
+// epilogue), p (the centre and its 4 in-plane diagonal edge neighbours) and
+// p + 1 (the 8 couplings across layer p). So a node costs one coalesced load
+// of the vector and of kappa, 13 shared-memory reads and one store, instead
+// of 27 + 8 cached global loads. Pointwise kernels run one thread per node
+// on 32 x 8 tiles of each plane. Node arrays carry the boundary nodes
+// (always 0). Partials: one per CTA (g.tiles_s per sample for the stencil
+// kernels, g.tiles_q for the QoI).
 #include "mlmc_internal.cuh"
 
 namespace mlmc {
@@ -94,75 +102,225 @@ __device__ __forceinline__ T diag3(const T kk[2][2][2], double h) {
   return T(h / 3.0) * s;
 }
 
-// (A v)(c) given v at the 27 nodes around c (v[dz+1][dy+1][dx+1]).
+// ---------------------------------------------------------------- z-march
+
+constexpr int ZTX = 32, ZTY = 8;
+constexpr int ZSX = ZTX + 2, ZSY = ZTY + 2, ZNV = ZSX * ZSY;   // vector plane + halo
+constexpr int ZKX = ZTX + 1, ZKY = ZTY + 1, ZNK = ZKX * ZKY;   // kappa layer + halo
+constexpr int ZTHREADS = ZTX * ZTY;
+static_assert(ZNV <= 2 * ZTHREADS && ZNK <= 2 * ZTHREADS, "two staging slots per thread");
+static_assert(ZTX == BX && ZTY == BY, "the z-march CTA shape is the node-tile shape");
+
+// Couplings of output node c with the 8 nodes of an adjacent plane across
+// the kappa layer K between them (K[b][a]: element at x-offset a - 1, y-offset
+// b - 1 from c): edge neighbours (one in-plane offset zero) take the two
+// shared kappa, corners the one; the face neighbour (0, 0) is not coupled.
+// Returns the sum without the -h/12 factor.
 template <class T>
-__device__ __forceinline__ T stencil3(const T kk[2][2][2], const T v[3][3][3], double h) {
-  T edges = T(0), corners = T(0);
-  // edge neighbours: exactly one zero component; sum kappa over the free axis
-#pragma unroll
-  for (int dy = -1; dy <= 1; dy += 2)
-#pragma unroll
-    for (int dx = -1; dx <= 1; dx += 2) {
-      const int a = dx > 0, b = dy > 0;
-      edges += (kk[0][b][a] + kk[1][b][a]) * v[1][dy + 1][dx + 1];            // dz = 0
-    }
-#pragma unroll
-  for (int dz = -1; dz <= 1; dz += 2)
-#pragma unroll
-    for (int dx = -1; dx <= 1; dx += 2) {
-      const int a = dx > 0, c = dz > 0;
-      edges += (kk[c][0][a] + kk[c][1][a]) * v[dz + 1][1][dx + 1];            // dy = 0
-    }
-#pragma unroll
-  for (int dz = -1; dz <= 1; dz += 2)
-#pragma unroll
-    for (int dy = -1; dy <= 1; dy += 2) {
-      const int b = dy > 0, c = dz > 0;
-      edges += (kk[c][b][0] + kk[c][b][1]) * v[dz + 1][dy + 1][1];            // dx = 0
-    }
-#pragma unroll
-  for (int dz = -1; dz <= 1; dz += 2)
-#pragma unroll
-    for (int dy = -1; dy <= 1; dy += 2)
-#pragma unroll
-      for (int dx = -1; dx <= 1; dx += 2)
-        corners += kk[dz > 0][dy > 0][dx > 0] * v[dz + 1][dy + 1][dx + 1];
-  return diag3(kk, h) * v[1][1][1] - T(h / 12.0) * (edges + corners);
+__device__ __forceinline__ T across3(const T K[2][2], const T v[3][3]) {
+  const T edges = ((K[0][0] + K[1][0]) * v[1][0] + (K[0][1] + K[1][1]) * v[1][2]) +
+                  ((K[0][0] + K[0][1]) * v[0][1] + (K[1][0] + K[1][1]) * v[2][1]);
+  const T corners = (K[0][0] * v[0][0] + K[0][1] * v[0][2]) + (K[1][0] * v[2][0] + K[1][1] * v[2][2]);
+  return edges + corners;
 }
 
-template <class T, class F>
-__device__ __forceinline__ void gather27(const Node3& q, int n, F&& f, T v[3][3][3]) {
-  const int64_t N1 = n + 1, P = N1 * N1;
-#pragma unroll
-  for (int dz = -1; dz <= 1; ++dz)
-#pragma unroll
-    for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-      for (int dx = -1; dx <= 1; ++dx)
-        v[dz + 1][dy + 1][dx + 1] = f(q.idx + dz * P + dy * N1 + dx, q.i + dx, q.j + dy, q.k + dz);
+// In-plane part for output c from its own plane, between layers Kb (below)
+// and Ka (above): the diagonal h/3 sum(8 kappa) and the 4 diagonal edge
+// neighbours (free axis z: one kappa of each layer):
+// h/3 S v_c - h/12 E.
+template <class T>
+__device__ __forceinline__ T inplane3(const T Kb[2][2], const T Ka[2][2], const T v[3][3], T c3, T c12) {
+  const T s = ((Kb[0][0] + Kb[0][1]) + (Kb[1][0] + Kb[1][1])) + ((Ka[0][0] + Ka[0][1]) + (Ka[1][0] + Ka[1][1]));
+  const T e = ((Kb[0][0] + Ka[0][0]) * v[0][0] + (Kb[0][1] + Ka[0][1]) * v[0][2]) +
+              ((Kb[1][0] + Ka[1][0]) * v[2][0] + (Kb[1][1] + Ka[1][1]) * v[2][2]);
+  return c3 * s * v[1][1] - c12 * e;
 }
 
-template <class T>
-__global__ void __launch_bounds__(256) k_apply3(Grid g, const T* __restrict__ K,
-                                                const T* __restrict__ X, T* __restrict__ Y, Prof prof) {
+struct ZTile {
+  int tx0, ty0, z0, z1;   // column origin; output planes [z0, z1)
+};
+
+__device__ __forceinline__ ZTile ztile(const Grid& g) {
+  const int txn = (g.n + ZTX - 1) / ZTX, tyn = (g.n + ZTY - 1) / ZTY;
+  int t = blockIdx.x;
+  const int zq = t / (txn * tyn);
+  t -= zq * txn * tyn;
+  const int ty = t / txn;
+  ZTile z;
+  z.tx0 = (t - ty * txn) * ZTX;
+  z.ty0 = ty * ZTY;
+  z.z0 = zq * g.zc;
+  z.z1 = min(z.z0 + g.zc, g.n + 1);
+  return z;
+}
+
+// Generic z-marching stencil kernel: y = A(kappa) x at every node of the
+// CTA's columns and planes, handed to the epilogue with the centre value of
+// x; the epilogue's returned values are summed into one partial per CTA
+// (part may be null). Tiles cover node columns [0, 32 ceil(n/32)) x
+// [0, 8 ceil(n/8)); when n is a multiple of the tile width, the column n
+// (boundary) is written by the thread of column n - 1 (epi.zero).
+template <class T, class Epi>
+__global__ void __launch_bounds__(ZTHREADS) k_zm3(Grid g, const T* __restrict__ Kap,
+                                                  const T* __restrict__ X,
+                                                  const int32_t* __restrict__ active, Epi epi,
+                                                  double* __restrict__ part, Prof prof) {
   const int64_t b = blockIdx.y;
-  const Node3 q = node3(g.n);
-  if (!q.valid) return;
-  T y = T(0);
-  if (q.interior) {
-    const T* x = X + b * g.ns;
-    const int n = g.n;
-    T v[3][3][3], kk[2][2][2];
-    // the caller's x may carry boundary values: they are ignored
-    gather27<T>(q, n, [&](int64_t o, int i, int j, int k) {
-      return (i > 0 && i < n && j > 0 && j < n && k > 0 && k < n) ? __ldg(x + o) : T(0);
-    }, v);
-    load_k8(K + b * g.es, n, q, kk);
-    y = stencil3(kk, v, g.h);
+  if (active && !active[b]) return;
+  __shared__ T sv[2][ZNV];
+  __shared__ T sk[2][ZNK];
+  const ZTile t = ztile(g);
+  const int n = g.n;
+  const int64_t N1 = n + 1;
+  const int tid = threadIdx.y * ZTX + threadIdx.x;
+  const T* __restrict__ x = X + b * g.ns;
+  const T* __restrict__ kp = Kap + b * g.es;
+  // staging slots of this thread: plane entries tid and tid + 256
+  const bool v1 = tid + ZTHREADS < ZNV, k1 = tid + ZTHREADS < ZNK;
+  const int vx0 = t.tx0 - 1 + tid % ZSX, vy0 = t.ty0 - 1 + tid / ZSX;
+  const int vx1 = t.tx0 - 1 + (tid + ZTHREADS) % ZSX, vy1 = t.ty0 - 1 + (tid + ZTHREADS) / ZSX;
+  const int kx0 = t.tx0 - 1 + tid % ZKX, ky0 = t.ty0 - 1 + tid / ZKX;
+  const int kx1 = t.tx0 - 1 + (tid + ZTHREADS) % ZKX, ky1 = t.ty0 - 1 + (tid + ZTHREADS) / ZKX;
+  // interior nodes only (the caller's boundary values are ignored); kappa
+  // outside the mesh reads as 0
+  auto ldv = [&](int i, int j, int p) -> T {
+    return (i >= 1 && i < n && j >= 1 && j < n && p >= 1 && p < n) ? __ldg(x + ((int64_t)p * N1 + j) * N1 + i)
+                                                                   : T(0);
+  };
+  auto ldk = [&](int i, int j, int p) -> T {
+    return (i >= 0 && i < n && j >= 0 && j < n && p >= 0 && p < n) ? __ldg(kp + ((int64_t)p * n + j) * n + i)
+                                                                   : T(0);
+  };
+  int p = t.z0 - 1;
+  T rv0 = ldv(vx0, vy0, p), rv1 = v1 ? ldv(vx1, vy1, p) : T(0);
+  T rk0 = ldk(kx0, ky0, p), rk1 = k1 ? ldk(kx1, ky1, p) : T(0);
+
+  const int i = t.tx0 + threadIdx.x, j = t.ty0 + threadIdx.y;
+  const bool col_valid = i <= n && j <= n;
+  const bool col_int = i >= 1 && i < n && j >= 1 && j < n;
+  const bool ex = i == n - 1 && n % ZTX == 0, ey = j == n - 1 && n % ZTY == 0;
+  const T c3 = T(g.h / 3.0), c12 = T(g.h / 12.0);
+  T a0 = T(0), a1 = T(0);                      // outputs of planes p - 1 and p so far
+  T kb[2][2] = {{T(0), T(0)}, {T(0), T(0)}};   // kappa layer p - 1
+  T vc = T(0);                                 // x at (i, j, p - 1)
+  double dot = 0.0;
+  int buf = 0;
+  for (; p <= t.z1; ++p) {
+    sv[buf][tid] = rv0;
+    if (v1) sv[buf][tid + ZTHREADS] = rv1;
+    sk[buf][tid] = rk0;
+    if (k1) sk[buf][tid + ZTHREADS] = rk1;
+    __syncthreads();
+    if (p < t.z1) {   // fetch plane p + 1 while plane p is used
+      rv0 = ldv(vx0, vy0, p + 1);
+      if (v1) rv1 = ldv(vx1, vy1, p + 1);
+      rk0 = ldk(kx0, ky0, p + 1);
+      if (k1) rk1 = ldk(kx1, ky1, p + 1);
+    }
+    const T* V = sv[buf] + (threadIdx.y + 1) * ZSX + threadIdx.x + 1;
+    const T* KK = sk[buf] + threadIdx.y * ZKX + threadIdx.x;
+    T v[3][3], ka[2][2];
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 3; ++dx) v[dy][dx] = V[(dy - 1) * ZSX + (dx - 1)];
+#pragma unroll
+    for (int bq = 0; bq < 2; ++bq)
+#pragma unroll
+      for (int a = 0; a < 2; ++a) ka[bq][a] = KK[bq * ZKX + a];
+    // output p - 1 is complete
+    a0 -= c12 * across3(kb, v);
+    const int m = p - 1;
+    if (col_valid && m >= t.z0) {
+      const int64_t o = ((int64_t)m * N1 + j) * N1 + i;
+      dot += epi(b, o, col_int && m >= 1 && m < n, a0, vc);
+      if (ex) epi.zero(b, o + 1);
+      if (ey) epi.zero(b, o + N1);
+      if (ex && ey) epi.zero(b, o + N1 + 1);
+    }
+    a0 = a1 + inplane3(kb, ka, v, c3, c12);
+    a1 = -c12 * across3(ka, v);
+#pragma unroll
+    for (int bq = 0; bq < 2; ++bq)
+#pragma unroll
+      for (int a = 0; a < 2; ++a) kb[bq][a] = ka[bq][a];
+    vc = v[1][1];
+    buf ^= 1;
   }
-  Y[b * g.ns + q.idx] = y;
+  if (part) cta_partial3(dot, part, g.tiles_s);
   prof_tick3(prof);
 }
+
+// Epilogues: (sample, node offset, interior?, (A x) at the node, x at the
+// node) -> contribution to the CTA partial; zero() writes a boundary node.
+template <class T>
+struct EpiApply {   // y = A x
+  T* Y;
+  int64_t ns;
+  __device__ double operator()(int64_t b, int64_t o, bool in, T ax, T) const {
+    Y[b * ns + o] = in ? ax : T(0);
+    return 0.0;
+  }
+  __device__ void zero(int64_t b, int64_t o) const { Y[b * ns + o] = T(0); }
+};
+
+template <class T>
+struct EpiAq {   // q = A p, partial of p.q
+  T* Q;
+  int64_t ns;
+  __device__ double operator()(int64_t b, int64_t o, bool in, T ax, T xc) const {
+    const T qv = in ? ax : T(0);
+    Q[b * ns + o] = qv;
+    return in ? (double)(xc * qv) : 0.0;
+  }
+  __device__ void zero(int64_t b, int64_t o) const { Q[b * ns + o] = T(0); }
+};
+
+template <class T>
+struct EpiMgRes {   // residual of the pre-smoothed iterate: b - A e
+  const T* Bv;
+  T* R1;
+  int64_t ns;
+  __device__ double operator()(int64_t b, int64_t o, bool in, T ax, T) const {
+    R1[b * ns + o] = in ? __ldg(Bv + b * ns + o) - ax : T(0);
+    return 0.0;
+  }
+  __device__ void zero(int64_t b, int64_t o) const { R1[b * ns + o] = T(0); }
+};
+
+template <class T>
+struct EpiMgPost {   // post-smoothing: e + W (b - A e), partial of b.out
+  const T* W;
+  const T* Bv;
+  T* Out;
+  int64_t ns;
+  __device__ double operator()(int64_t b, int64_t o, bool in, T ax, T ec) const {
+    if (!in) {
+      Out[b * ns + o] = T(0);
+      return 0.0;
+    }
+    const T bval = __ldg(Bv + b * ns + o);
+    const T ov = fma(__ldg(W + b * ns + o), bval - ax, ec);
+    Out[b * ns + o] = ov;
+    return (double)(bval * ov);
+  }
+  __device__ void zero(int64_t b, int64_t o) const { Out[b * ns + o] = T(0); }
+};
+
+struct EpiResid {   // outer FP64 residual h^3 - A u, partial of its square
+  double* R;
+  int64_t ns;
+  double h3;
+  __device__ double operator()(int64_t b, int64_t o, bool in, double ax, double) const {
+    const double rv = in ? h3 - ax : 0.0;
+    R[b * ns + o] = rv;
+    return rv * rv;
+  }
+  __device__ void zero(int64_t b, int64_t o) const { R[b * ns + o] = 0.0; }
+};
+
+inline dim3 gridz(const Grid& g, int64_t B) { return dim3((unsigned)g.zx, (unsigned)B, 1); }
+
 
 template <class T>
 __global__ void __launch_bounds__(256) k_winv3(Grid g, const T* __restrict__ K, double omega,
@@ -204,31 +362,6 @@ __global__ void __launch_bounds__(256) k_pupd3(Grid g, const T* __restrict__ Z, 
   Pnew[o] = (bb == T(0)) ? zv : fma(bb, Pold[o], zv);
 }
 
-// q = A p, partials of p.q
-template <class T>
-__global__ void __launch_bounds__(256) k_aq3(Grid g, const T* __restrict__ K, const T* __restrict__ P,
-                                             T* __restrict__ Q, const int32_t* __restrict__ active,
-                                             double* __restrict__ part, Prof prof) {
-  const int64_t b = blockIdx.y;
-  if (!active[b]) return;
-  const Node3 q = node3(g.n);
-  const T* p = P + b * g.ns;
-  double dot = 0.0;
-  if (q.valid) {
-    T qv = T(0);
-    if (q.interior) {
-      T v[3][3][3], kk[2][2][2];
-      gather27<T>(q, g.n, [&](int64_t o, int, int, int) { return __ldg(p + o); }, v);
-      load_k8(K + b * g.es, g.n, q, kk);
-      qv = stencil3(kk, v, g.h);
-      dot = (double)(v[1][1][1] * qv);
-    }
-    Q[b * g.ns + q.idx] = qv;
-  }
-  cta_partial3(dot, part, g.tiles_s);
-  prof_tick3(prof);
-}
-
 // Pointwise: out = W b (the pre-smoothing step from zero).
 template <class T>
 __global__ void __launch_bounds__(256) k_wb3(Grid g, const T* __restrict__ W, const T* __restrict__ Bv,
@@ -239,27 +372,6 @@ __global__ void __launch_bounds__(256) k_wb3(Grid g, const T* __restrict__ W, co
   if (!q.valid) return;
   const int64_t o = b * g.ns + q.idx;
   E[o] = W[o] * Bv[o];
-}
-
-// r1 = b - A e
-template <class T>
-__global__ void __launch_bounds__(256) k_mgres3(Grid g, const T* __restrict__ K, const T* __restrict__ Bv,
-                                                const T* __restrict__ E, T* __restrict__ R1,
-                                                const int32_t* __restrict__ active, Prof prof) {
-  const int64_t b = blockIdx.y;
-  if (!active[b]) return;
-  const Node3 q = node3(g.n);
-  if (!q.valid) return;
-  const T* e = E + b * g.ns;
-  T rv = T(0);
-  if (q.interior) {
-    T v[3][3][3], kk[2][2][2];
-    gather27<T>(q, g.n, [&](int64_t o, int, int, int) { return __ldg(e + o); }, v);
-    load_k8(K + b * g.es, g.n, q, kk);
-    rv = __ldg(Bv + b * g.ns + q.idx) - stencil3(kk, v, g.h);
-  }
-  R1[b * g.ns + q.idx] = rv;
-  prof_tick3(prof);
 }
 
 // Full weighting: bc(I) = sum_{d in {-1,0,1}^3} w(dx) w(dy) w(dz) r1(2I + d).
@@ -334,34 +446,6 @@ __global__ void __launch_bounds__(256) k_prolong3(Grid g, int64_t nsc, const T* 
   Tmp[b * g.ns + q.idx] = v;
 }
 
-// out = e' + W (b - A e') with e' = tmp; partials of b.out when part != nullptr.
-template <class T>
-__global__ void __launch_bounds__(256) k_mgpost3(Grid g, const T* __restrict__ K,
-                                                 const T* __restrict__ W, const T* __restrict__ Bv,
-                                                 const T* __restrict__ Tmp, T* __restrict__ Out,
-                                                 const int32_t* __restrict__ active,
-                                                 double* __restrict__ part, Prof prof) {
-  const int64_t b = blockIdx.y;
-  if (!active[b]) return;
-  const Node3 q = node3(g.n);
-  const T* e = Tmp + b * g.ns;
-  double dot = 0.0;
-  if (q.valid) {
-    T ov = T(0);
-    if (q.interior) {
-      T v[3][3][3], kk[2][2][2];
-      gather27<T>(q, g.n, [&](int64_t o, int, int, int) { return __ldg(e + o); }, v);
-      load_k8(K + b * g.es, g.n, q, kk);
-      const T bval = __ldg(Bv + b * g.ns + q.idx);
-      ov = fma(__ldg(W + b * g.ns + q.idx), bval - stencil3(kk, v, g.h), v[1][1][1]);
-      dot = (double)(bval * ov);
-    }
-    Out[b * g.ns + q.idx] = ov;
-  }
-  if (part) cta_partial3(dot, part, g.tiles_s);
-  prof_tick3(prof);
-}
-
 // QoI partials: domain: w = h^3 at interior nodes; box [L, H]^3 in node
 // indices: w = h^3 chi_x chi_y chi_z / |box|, chi = 1 inside, 1/2 on a face.
 template <class T>
@@ -378,32 +462,7 @@ __global__ void __launch_bounds__(256) k_qoi3(Grid g, int box, int L, int H, dou
     }
     v = w * (double)X[b * g.ns + q.idx];
   }
-  cta_partial3(v, part, g.tiles_s);
-  prof_tick3(prof);
-}
-
-// Mixed form, outer FP64 residual r = b - A u (b_i = h^3), partials of r.r.
-__global__ void __launch_bounds__(256) k_resid3(Grid g, const double* __restrict__ K,
-                                                const double* __restrict__ U, double* __restrict__ R,
-                                                const int32_t* __restrict__ active,
-                                                double* __restrict__ part, Prof prof) {
-  const int64_t b = blockIdx.y;
-  if (!active[b]) return;
-  const Node3 q = node3(g.n);
-  const double* u = U + b * g.ns;
-  double dot = 0.0;
-  if (q.valid) {
-    double rv = 0.0;
-    if (q.interior) {
-      double v[3][3][3], kk[2][2][2];
-      gather27<double>(q, g.n, [&](int64_t o, int, int, int) { return __ldg(u + o); }, v);
-      load_k8(K + b * g.es, g.n, q, kk);
-      rv = g.h * g.h * g.h - stencil3(kk, v, g.h);
-      dot = rv * rv;
-    }
-    R[b * g.ns + q.idx] = rv;
-  }
-  cta_partial3(dot, part, g.tiles_s);
+  cta_partial3(v, part, g.tiles_q);
   prof_tick3(prof);
 }
 
@@ -416,7 +475,8 @@ namespace d3 {
 
 template <class T>
 cudaError_t apply(cudaStream_t s, const Grid& g, const T* kappa, const T* x, T* y, int64_t B, Prof p) {
-  k_apply3<T><<<grid3(g, B), block3(), 0, s>>>(g, kappa, x, y, p);
+  k_zm3<T, EpiApply<T>><<<gridz(g, B), block3(), 0, s>>>(g, kappa, x, nullptr, EpiApply<T>{y, g.ns},
+                                                        nullptr, p);
   return cudaGetLastError();
 }
 template <class T>
@@ -433,14 +493,16 @@ template <class T>
 cudaError_t pcg_pq(cudaStream_t s, const Grid& g, const T* kappa, const T* z, const T* p_old, T* p_new,
                    T* q, const Scalars& sc, double* part, int64_t B, Prof p) {
   k_pupd3<T><<<grid3(g, B), block3(), 0, s>>>(g, z, p_old, p_new, sc.beta, sc.active);
-  k_aq3<T><<<grid3(g, B), block3(), 0, s>>>(g, kappa, p_new, q, sc.active, part, p);
+  k_zm3<T, EpiAq<T>><<<gridz(g, B), block3(), 0, s>>>(g, kappa, p_new, sc.active, EpiAq<T>{q, g.ns},
+                                                     part, p);
   return cudaGetLastError();
 }
 template <class T>
 cudaError_t mg_pre(cudaStream_t s, const Grid& g, const T* kappa, const T* w, const T* b, T* e, T* r1,
                    const int32_t* active, int64_t B, Prof p) {
   k_wb3<T><<<grid3(g, B), block3(), 0, s>>>(g, w, b, e, active);
-  k_mgres3<T><<<grid3(g, B), block3(), 0, s>>>(g, kappa, b, e, r1, active, p);
+  k_zm3<T, EpiMgRes<T>><<<gridz(g, B), block3(), 0, s>>>(g, kappa, e, active,
+                                                        EpiMgRes<T>{b, r1, g.ns}, nullptr, p);
   return cudaGetLastError();
 }
 template <class T>
@@ -460,7 +522,8 @@ cudaError_t mg_post(cudaStream_t s, const Grid& g, const Grid& coarse, const T* 
                     const T* b, const T* e, const T* ec, T* out, T* tmp, const int32_t* active,
                     double* part, int64_t B, Prof p) {
   k_prolong3<T><<<grid3(g, B), block3(), 0, s>>>(g, coarse.ns, e, ec, tmp, active);
-  k_mgpost3<T><<<grid3(g, B), block3(), 0, s>>>(g, kappa, w, b, tmp, out, active, part, p);
+  k_zm3<T, EpiMgPost<T>><<<gridz(g, B), block3(), 0, s>>>(g, kappa, tmp, active,
+                                                         EpiMgPost<T>{w, b, out, g.ns}, part, p);
   return cudaGetLastError();
 }
 template <class T>
@@ -471,7 +534,8 @@ cudaError_t qoi(cudaStream_t s, const Grid& g, int box, int L, int H, double inv
 }
 cudaError_t resid64(cudaStream_t s, const Grid& g, const double* kappa, const double* u, double* r,
                     const int32_t* active, double* part, int64_t B, Prof p) {
-  k_resid3<<<grid3(g, B), block3(), 0, s>>>(g, kappa, u, r, active, part, p);
+  k_zm3<double, EpiResid><<<gridz(g, B), block3(), 0, s>>>(g, kappa, u, active,
+                                                          EpiResid{r, g.ns, g.h * g.h * g.h}, part, p);
   return cudaGetLastError();
 }
 
