@@ -233,6 +233,10 @@ def measure_form(m, wl, cfg, stream, args, world, barrier, with_e2e):
         total_ms = sum(st[1] for st in stats.values())
         dom = max(stats, key=lambda k: stats[k][1])
         shares = {k: round(st[1] / total_ms, 4) for k, st in stats.items() if st[1] > 0}
+        # per kernel: launches, traced time, algorithmic GB/s (event-timed launch by launch)
+        per_kernel = {k: {"launches": int(st[0]), "ms": round(st[1], 3),
+                          "gbs": round(st[2] / (st[1] / 1e3) / 1e9, 1) if st[1] > 0 and st[2] > 0 else None}
+                      for k, st in stats.items() if st[1] > 0}
         # timed region: device events around whole MLMC runs (solves run as CUDA graphs)
         clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
         barrier()
@@ -274,7 +278,8 @@ def measure_form(m, wl, cfg, stream, args, world, barrier, with_e2e):
                 wall.append(time.perf_counter() - t0)
         plan.close()
     return dict(ms=ms, N=[int(x) for x in N], dofs_step=dofs_step, q=q, v=v, dom=dom,
-                dstat=dstat, shares=shares, clocks=clk, launches=launches, wall=wall)
+                dstat=dstat, shares=shares, per_kernel=per_kernel, clocks=clk, launches=launches,
+                wall=wall)
 
 
 def serving_both(m, args, device=0):
@@ -364,7 +369,7 @@ def roofline_of(res, peaks, fp64_alu):
          "achieved": round(achieved, 1), "peak": hbm_peak, "peak_source": src, "unit": "GB/s",
          "frac": round(achieved / hbm_peak, 4), "traffic": None, "launches": d_launches,
          "avg_launch_us": round(1e3 * d_ms / max(d_launches, 1), 2),
-         "time_shares": res["shares"]}
+         "time_shares": res["shares"], "per_kernel": res["per_kernel"]}
     if fp64_alu:
         r["note"] = ("FP64 form: the kernel is bound by the FP64 pipe (2 DFMA/SM/cycle on GB300, "
                      "1.26 TFLOP/s at 2.07 GHz); achieved/peak/frac here are its HBM bytes "

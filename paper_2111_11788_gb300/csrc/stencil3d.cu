@@ -159,7 +159,8 @@ __device__ __forceinline__ ZTile ztile(const Grid& g) {
 // x; the epilogue's returned values are summed into one partial per CTA
 // (part may be null). Tiles cover node columns [0, 32 ceil(n/32)) x
 // [0, 8 ceil(n/8)); when n is a multiple of the tile width, the column n
-// (boundary) is written by the thread of column n - 1 (epi.zero).
+// (boundary) is written by the thread of column n - 1 (epi.zero). Offsets
+// inside one sample fit 32 bits ((n + 1)^3 < 2^31 for n <= 1000).
 template <class T, class Epi>
 __global__ void __launch_bounds__(ZTHREADS) k_zm3(Grid g, const T* __restrict__ Kap,
                                                   const T* __restrict__ X,
@@ -170,55 +171,63 @@ __global__ void __launch_bounds__(ZTHREADS) k_zm3(Grid g, const T* __restrict__ 
   __shared__ T sv[2][ZNV];
   __shared__ T sk[2][ZNK];
   const ZTile t = ztile(g);
-  const int n = g.n;
-  const int64_t N1 = n + 1;
+  const int n = g.n, N1 = n + 1, P = N1 * N1, KP = n * n;
   const int tid = threadIdx.y * ZTX + threadIdx.x;
   const T* __restrict__ x = X + b * g.ns;
   const T* __restrict__ kp = Kap + b * g.es;
-  // staging slots of this thread: plane entries tid and tid + 256
+  epi.bind(b);
+  // staging slots of this thread: plane entries tid and tid + 256, with
+  // their in-plane offsets and whether they lie inside (interior nodes for
+  // x, whose boundary values are ignored; mesh elements for kappa)
+  int vo[2], ko[2];
+  bool vok[2], kok[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int sidx = tid + q * ZTHREADS;
+    const int vx = t.tx0 - 1 + sidx % ZSX, vy = t.ty0 - 1 + sidx / ZSX;
+    vok[q] = sidx < ZNV && vx >= 1 && vx < n && vy >= 1 && vy < n;
+    vo[q] = vok[q] ? vy * N1 + vx : 0;
+    const int kx = t.tx0 - 1 + sidx % ZKX, ky = t.ty0 - 1 + sidx / ZKX;
+    kok[q] = sidx < ZNK && kx >= 0 && kx < n && ky >= 0 && ky < n;
+    ko[q] = kok[q] ? ky * n + kx : 0;
+  }
   const bool v1 = tid + ZTHREADS < ZNV, k1 = tid + ZTHREADS < ZNK;
-  const int vx0 = t.tx0 - 1 + tid % ZSX, vy0 = t.ty0 - 1 + tid / ZSX;
-  const int vx1 = t.tx0 - 1 + (tid + ZTHREADS) % ZSX, vy1 = t.ty0 - 1 + (tid + ZTHREADS) / ZSX;
-  const int kx0 = t.tx0 - 1 + tid % ZKX, ky0 = t.ty0 - 1 + tid / ZKX;
-  const int kx1 = t.tx0 - 1 + (tid + ZTHREADS) % ZKX, ky1 = t.ty0 - 1 + (tid + ZTHREADS) / ZKX;
-  // interior nodes only (the caller's boundary values are ignored); kappa
-  // outside the mesh reads as 0
-  auto ldv = [&](int i, int j, int p) -> T {
-    return (i >= 1 && i < n && j >= 1 && j < n && p >= 1 && p < n) ? __ldg(x + ((int64_t)p * N1 + j) * N1 + i)
-                                                                   : T(0);
-  };
-  auto ldk = [&](int i, int j, int p) -> T {
-    return (i >= 0 && i < n && j >= 0 && j < n && p >= 0 && p < n) ? __ldg(kp + ((int64_t)p * n + j) * n + i)
-                                                                   : T(0);
-  };
   int p = t.z0 - 1;
-  T rv0 = ldv(vx0, vy0, p), rv1 = v1 ? ldv(vx1, vy1, p) : T(0);
-  T rk0 = ldk(kx0, ky0, p), rk1 = k1 ? ldk(kx1, ky1, p) : T(0);
+  T rv[2], rk[2];
+  auto fetch = [&](int pp) {
+    const bool pv = pp >= 1 && pp < n, pk = pp >= 0 && pp < n;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      rv[q] = (pv && vok[q]) ? __ldg(x + pp * P + vo[q]) : T(0);
+      rk[q] = (pk && kok[q]) ? __ldg(kp + pp * KP + ko[q]) : T(0);
+    }
+  };
+  fetch(p);
 
   const int i = t.tx0 + threadIdx.x, j = t.ty0 + threadIdx.y;
   const bool col_valid = i <= n && j <= n;
   const bool col_int = i >= 1 && i < n && j >= 1 && j < n;
   const bool ex = i == n - 1 && n % ZTX == 0, ey = j == n - 1 && n % ZTY == 0;
+  const int ocol = j * N1 + i;
   const T c3 = T(g.h / 3.0), c12 = T(g.h / 12.0);
   T a0 = T(0), a1 = T(0);                      // outputs of planes p - 1 and p so far
   T kb[2][2] = {{T(0), T(0)}, {T(0), T(0)}};   // kappa layer p - 1
   T vc = T(0);                                 // x at (i, j, p - 1)
   double dot = 0.0;
   int buf = 0;
+  const T* V0 = &sv[0][(threadIdx.y + 1) * ZSX + threadIdx.x + 1];
+  const T* K0 = &sk[0][threadIdx.y * ZKX + threadIdx.x];
   for (; p <= t.z1; ++p) {
-    sv[buf][tid] = rv0;
-    if (v1) sv[buf][tid + ZTHREADS] = rv1;
-    sk[buf][tid] = rk0;
-    if (k1) sk[buf][tid + ZTHREADS] = rk1;
+    T* svb = sv[buf];
+    T* skb = sk[buf];
+    svb[tid] = rv[0];
+    if (v1) svb[tid + ZTHREADS] = rv[1];
+    skb[tid] = rk[0];
+    if (k1) skb[tid + ZTHREADS] = rk[1];
     __syncthreads();
-    if (p < t.z1) {   // fetch plane p + 1 while plane p is used
-      rv0 = ldv(vx0, vy0, p + 1);
-      if (v1) rv1 = ldv(vx1, vy1, p + 1);
-      rk0 = ldk(kx0, ky0, p + 1);
-      if (k1) rk1 = ldk(kx1, ky1, p + 1);
-    }
-    const T* V = sv[buf] + (threadIdx.y + 1) * ZSX + threadIdx.x + 1;
-    const T* KK = sk[buf] + threadIdx.y * ZKX + threadIdx.x;
+    if (p < t.z1) fetch(p + 1);   // the next plane is in flight while this one is used
+    const T* V = V0 + buf * ZNV;
+    const T* KK = K0 + buf * ZNK;
     T v[3][3], ka[2][2];
 #pragma unroll
     for (int dy = 0; dy < 3; ++dy)
@@ -232,11 +241,11 @@ __global__ void __launch_bounds__(ZTHREADS) k_zm3(Grid g, const T* __restrict__ 
     a0 -= c12 * across3(kb, v);
     const int m = p - 1;
     if (col_valid && m >= t.z0) {
-      const int64_t o = ((int64_t)m * N1 + j) * N1 + i;
-      dot += epi(b, o, col_int && m >= 1 && m < n, a0, vc);
-      if (ex) epi.zero(b, o + 1);
-      if (ey) epi.zero(b, o + N1);
-      if (ex && ey) epi.zero(b, o + N1 + 1);
+      const int o = m * P + ocol;
+      dot += epi(o, col_int && m >= 1 && m < n, a0, vc);
+      if (ex) epi.zero(o + 1);
+      if (ey) epi.zero(o + N1);
+      if (ex && ey) epi.zero(o + N1 + 1);
     }
     a0 = a1 + inplane3(kb, ka, v, c3, c12);
     a1 = -c12 * across3(ka, v);
@@ -251,29 +260,32 @@ __global__ void __launch_bounds__(ZTHREADS) k_zm3(Grid g, const T* __restrict__ 
   prof_tick3(prof);
 }
 
-// Epilogues: (sample, node offset, interior?, (A x) at the node, x at the
-// node) -> contribution to the CTA partial; zero() writes a boundary node.
+// Epilogues: bind(sample) offsets their arrays to the sample; then
+// (node offset, interior?, (A x) at the node, x at the node) -> contribution
+// to the CTA partial; zero() writes a boundary node.
 template <class T>
 struct EpiApply {   // y = A x
   T* Y;
   int64_t ns;
-  __device__ double operator()(int64_t b, int64_t o, bool in, T ax, T) const {
-    Y[b * ns + o] = in ? ax : T(0);
+  __device__ void bind(int64_t b) { Y += b * ns; }
+  __device__ double operator()(int o, bool in, T ax, T) const {
+    Y[o] = in ? ax : T(0);
     return 0.0;
   }
-  __device__ void zero(int64_t b, int64_t o) const { Y[b * ns + o] = T(0); }
+  __device__ void zero(int o) const { Y[o] = T(0); }
 };
 
 template <class T>
 struct EpiAq {   // q = A p, partial of p.q
   T* Q;
   int64_t ns;
-  __device__ double operator()(int64_t b, int64_t o, bool in, T ax, T xc) const {
+  __device__ void bind(int64_t b) { Q += b * ns; }
+  __device__ double operator()(int o, bool in, T ax, T xc) const {
     const T qv = in ? ax : T(0);
-    Q[b * ns + o] = qv;
+    Q[o] = qv;
     return in ? (double)(xc * qv) : 0.0;
   }
-  __device__ void zero(int64_t b, int64_t o) const { Q[b * ns + o] = T(0); }
+  __device__ void zero(int o) const { Q[o] = T(0); }
 };
 
 template <class T>
@@ -281,11 +293,15 @@ struct EpiMgRes {   // residual of the pre-smoothed iterate: b - A e
   const T* Bv;
   T* R1;
   int64_t ns;
-  __device__ double operator()(int64_t b, int64_t o, bool in, T ax, T) const {
-    R1[b * ns + o] = in ? __ldg(Bv + b * ns + o) - ax : T(0);
+  __device__ void bind(int64_t b) {
+    Bv += b * ns;
+    R1 += b * ns;
+  }
+  __device__ double operator()(int o, bool in, T ax, T) const {
+    R1[o] = in ? __ldg(Bv + o) - ax : T(0);
     return 0.0;
   }
-  __device__ void zero(int64_t b, int64_t o) const { R1[b * ns + o] = T(0); }
+  __device__ void zero(int o) const { R1[o] = T(0); }
 };
 
 template <class T>
@@ -294,29 +310,35 @@ struct EpiMgPost {   // post-smoothing: e + W (b - A e), partial of b.out
   const T* Bv;
   T* Out;
   int64_t ns;
-  __device__ double operator()(int64_t b, int64_t o, bool in, T ax, T ec) const {
+  __device__ void bind(int64_t b) {
+    W += b * ns;
+    Bv += b * ns;
+    Out += b * ns;
+  }
+  __device__ double operator()(int o, bool in, T ax, T ec) const {
     if (!in) {
-      Out[b * ns + o] = T(0);
+      Out[o] = T(0);
       return 0.0;
     }
-    const T bval = __ldg(Bv + b * ns + o);
-    const T ov = fma(__ldg(W + b * ns + o), bval - ax, ec);
-    Out[b * ns + o] = ov;
+    const T bval = __ldg(Bv + o);
+    const T ov = fma(__ldg(W + o), bval - ax, ec);
+    Out[o] = ov;
     return (double)(bval * ov);
   }
-  __device__ void zero(int64_t b, int64_t o) const { Out[b * ns + o] = T(0); }
+  __device__ void zero(int o) const { Out[o] = T(0); }
 };
 
 struct EpiResid {   // outer FP64 residual h^3 - A u, partial of its square
   double* R;
   int64_t ns;
   double h3;
-  __device__ double operator()(int64_t b, int64_t o, bool in, double ax, double) const {
+  __device__ void bind(int64_t b) { R += b * ns; }
+  __device__ double operator()(int o, bool in, double ax, double) const {
     const double rv = in ? h3 - ax : 0.0;
-    R[b * ns + o] = rv;
+    R[o] = rv;
     return rv * rv;
   }
-  __device__ void zero(int64_t b, int64_t o) const { R[b * ns + o] = 0.0; }
+  __device__ void zero(int o) const { R[o] = 0.0; }
 };
 
 inline dim3 gridz(const Grid& g, int64_t B) { return dim3((unsigned)g.zx, (unsigned)B, 1); }
