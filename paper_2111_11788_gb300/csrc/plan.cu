@@ -33,11 +33,11 @@ Grid make_grid(int dim, int n) {
     g.tiles_s = (int64_t)g.sx * g.sy * SWARPS;
   } else {
     // pointwise kernels: one CTA per 32 x 8 node tile of each z-plane;
-    // stencil kernels: one CTA per 32 x 8 column tile and chunk of zc planes
+    // stencil kernels: one CTA per 32 x 16 column tile and chunk of zc planes
     g.sx = ((n + 1 + 31) / 32) * ((n + 1 + 7) / 8) * (n + 1);
     g.sy = 1;
     g.zc = (n + 1 <= 24) ? n + 1 : 16;
-    g.zx = ((n + 31) / 32) * ((n + 7) / 8) * ((n + 1 + g.zc - 1) / g.zc);
+    g.zx = ((n + 31) / 32) * ((n + 15) / 16) * ((n + 1 + g.zc - 1) / g.zc);
     g.tiles_s = g.zx;
   }
   g.fx = (int)((g.ns + FLAT_ELEMS - 1) / FLAT_ELEMS);

@@ -104,36 +104,39 @@ __device__ __forceinline__ T diag3(const T kk[2][2][2], double h) {
 
 // ---------------------------------------------------------------- z-march
 
-constexpr int ZTX = 32, ZTY = 8;
+constexpr int ZTX = 32, ZTY = 16;          // node columns per CTA (x, y)
+constexpr int ZRY = 2;                     // y-rows per thread
+constexpr int ZTHREADS = ZTX * (ZTY / ZRY);
 constexpr int ZSX = ZTX + 2, ZSY = ZTY + 2, ZNV = ZSX * ZSY;   // vector plane + halo
 constexpr int ZKX = ZTX + 1, ZKY = ZTY + 1, ZNK = ZKX * ZKY;   // kappa layer + halo
-constexpr int ZTHREADS = ZTX * ZTY;
-static_assert(ZNV <= 2 * ZTHREADS && ZNK <= 2 * ZTHREADS, "two staging slots per thread");
-static_assert(ZTX == BX && ZTY == BY, "the z-march CTA shape is the node-tile shape");
+constexpr int ZSLOTS = ((ZNV > ZNK ? ZNV : ZNK) + ZTHREADS - 1) / ZTHREADS;
+static_assert(ZNV <= ZSLOTS * ZTHREADS && ZNK <= ZSLOTS * ZTHREADS, "staging slots per thread");
+static_assert(ZTHREADS == BX * BY, "the z-march CTA has the node-tile thread count");
 
 // Couplings of output node c with the 8 nodes of an adjacent plane across
 // the kappa layer K between them (K[b][a]: element at x-offset a - 1, y-offset
-// b - 1 from c): edge neighbours (one in-plane offset zero) take the two
-// shared kappa, corners the one; the face neighbour (0, 0) is not coupled.
-// Returns the sum without the -h/12 factor.
+// b - 1 from c; v[dy + 1][dx + 1]): edge neighbours (one in-plane offset
+// zero) take the two shared kappa, corners the one; the face neighbour
+// (0, 0) is not coupled. Returns the sum without the -h/12 factor.
 template <class T>
-__device__ __forceinline__ T across3(const T K[2][2], const T v[3][3]) {
-  const T edges = ((K[0][0] + K[1][0]) * v[1][0] + (K[0][1] + K[1][1]) * v[1][2]) +
-                  ((K[0][0] + K[0][1]) * v[0][1] + (K[1][0] + K[1][1]) * v[2][1]);
-  const T corners = (K[0][0] * v[0][0] + K[0][1] * v[0][2]) + (K[1][0] * v[2][0] + K[1][1] * v[2][2]);
+__device__ __forceinline__ T across3(const T* K0, const T* K1, const T* v0, const T* v1, const T* v2) {
+  const T edges = ((K0[0] + K1[0]) * v1[0] + (K0[1] + K1[1]) * v1[2]) +
+                  ((K0[0] + K0[1]) * v0[1] + (K1[0] + K1[1]) * v2[1]);
+  const T corners = (K0[0] * v0[0] + K0[1] * v0[2]) + (K1[0] * v2[0] + K1[1] * v2[2]);
   return edges + corners;
 }
 
-// In-plane part for output c from its own plane, between layers Kb (below)
-// and Ka (above): the diagonal h/3 sum(8 kappa) and the 4 diagonal edge
-// neighbours (free axis z: one kappa of each layer):
+// In-plane part for output c from its own plane, between the layers below
+// (B0, B1: rows b = 0, 1) and above (A0, A1): the diagonal h/3 sum(8 kappa)
+// and the 4 diagonal edge neighbours (free axis z: one kappa of each layer):
 // h/3 S v_c - h/12 E.
 template <class T>
-__device__ __forceinline__ T inplane3(const T Kb[2][2], const T Ka[2][2], const T v[3][3], T c3, T c12) {
-  const T s = ((Kb[0][0] + Kb[0][1]) + (Kb[1][0] + Kb[1][1])) + ((Ka[0][0] + Ka[0][1]) + (Ka[1][0] + Ka[1][1]));
-  const T e = ((Kb[0][0] + Ka[0][0]) * v[0][0] + (Kb[0][1] + Ka[0][1]) * v[0][2]) +
-              ((Kb[1][0] + Ka[1][0]) * v[2][0] + (Kb[1][1] + Ka[1][1]) * v[2][2]);
-  return c3 * s * v[1][1] - c12 * e;
+__device__ __forceinline__ T inplane3(const T* B0, const T* B1, const T* A0, const T* A1, const T* v0,
+                                      const T* v1, const T* v2, T c3, T c12) {
+  const T s = ((B0[0] + B0[1]) + (B1[0] + B1[1])) + ((A0[0] + A0[1]) + (A1[0] + A1[1]));
+  const T e = ((B0[0] + A0[0]) * v0[0] + (B0[1] + A0[1]) * v0[2]) +
+              ((B1[0] + A1[0]) * v2[0] + (B1[1] + A1[1]) * v2[2]);
+  return c3 * s * v1[1] - c12 * e;
 }
 
 struct ZTile {
@@ -156,11 +159,13 @@ __device__ __forceinline__ ZTile ztile(const Grid& g) {
 
 // Generic z-marching stencil kernel: y = A(kappa) x at every node of the
 // CTA's columns and planes, handed to the epilogue with the centre value of
-// x; the epilogue's returned values are summed into one partial per CTA
-// (part may be null). Tiles cover node columns [0, 32 ceil(n/32)) x
-// [0, 8 ceil(n/8)); when n is a multiple of the tile width, the column n
-// (boundary) is written by the thread of column n - 1 (epi.zero). Offsets
-// inside one sample fit 32 bits ((n + 1)^3 < 2^31 for n <= 1000).
+// x; the epilogue's returned values are summed (in T per thread, in FP64
+// across the CTA) into one partial per CTA (part may be null). A thread owns
+// two adjacent y-rows of one x-column. The epilogue's own inputs for a node
+// are fetched one plane ahead (Epi::Pre). Tiles cover node columns
+// [0, 32 ceil(n/32)) x [0, 16 ceil(n/16)); when n is a multiple of the tile
+// width, the column n (boundary) is written by the thread of column n - 1
+// (epi.zero). Offsets inside one sample fit 32 bits ((n + 1)^3 < 2^31).
 template <class T, class Epi>
 __global__ void __launch_bounds__(ZTHREADS) k_zm3(Grid g, const T* __restrict__ Kap,
                                                   const T* __restrict__ X,
@@ -176,120 +181,154 @@ __global__ void __launch_bounds__(ZTHREADS) k_zm3(Grid g, const T* __restrict__ 
   const T* __restrict__ x = X + b * g.ns;
   const T* __restrict__ kp = Kap + b * g.es;
   epi.bind(b);
-  // staging slots of this thread: plane entries tid and tid + 256, with
-  // their in-plane offsets and whether they lie inside (interior nodes for
-  // x, whose boundary values are ignored; mesh elements for kappa)
-  int vo[2], ko[2];
-  bool vok[2], kok[2];
+  // staging slots: plane entries tid + q * ZTHREADS, with their in-plane
+  // offsets and whether they lie inside (interior nodes for x, whose
+  // boundary values are ignored; mesh elements for kappa)
+  int vo[ZSLOTS], ko[ZSLOTS];
+  bool vok[ZSLOTS], kok[ZSLOTS], vin[ZSLOTS], kin[ZSLOTS];
 #pragma unroll
-  for (int q = 0; q < 2; ++q) {
+  for (int q = 0; q < ZSLOTS; ++q) {
     const int sidx = tid + q * ZTHREADS;
+    vin[q] = sidx < ZNV;
+    kin[q] = sidx < ZNK;
     const int vx = t.tx0 - 1 + sidx % ZSX, vy = t.ty0 - 1 + sidx / ZSX;
-    vok[q] = sidx < ZNV && vx >= 1 && vx < n && vy >= 1 && vy < n;
+    vok[q] = vin[q] && vx >= 1 && vx < n && vy >= 1 && vy < n;
     vo[q] = vok[q] ? vy * N1 + vx : 0;
     const int kx = t.tx0 - 1 + sidx % ZKX, ky = t.ty0 - 1 + sidx / ZKX;
-    kok[q] = sidx < ZNK && kx >= 0 && kx < n && ky >= 0 && ky < n;
+    kok[q] = kin[q] && kx >= 0 && kx < n && ky >= 0 && ky < n;
     ko[q] = kok[q] ? ky * n + kx : 0;
   }
-  const bool v1 = tid + ZTHREADS < ZNV, k1 = tid + ZTHREADS < ZNK;
-  int p = t.z0 - 1;
-  T rv[2], rk[2];
+  T rv[ZSLOTS], rk[ZSLOTS];
   auto fetch = [&](int pp) {
     const bool pv = pp >= 1 && pp < n, pk = pp >= 0 && pp < n;
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < ZSLOTS; ++q) {
       rv[q] = (pv && vok[q]) ? __ldg(x + pp * P + vo[q]) : T(0);
       rk[q] = (pk && kok[q]) ? __ldg(kp + pp * KP + ko[q]) : T(0);
     }
   };
+  int p = t.z0 - 1;
   fetch(p);
 
-  const int i = t.tx0 + threadIdx.x, j = t.ty0 + threadIdx.y;
-  const bool col_valid = i <= n && j <= n;
-  const bool col_int = i >= 1 && i < n && j >= 1 && j < n;
-  const bool ex = i == n - 1 && n % ZTX == 0, ey = j == n - 1 && n % ZTY == 0;
-  const int ocol = j * N1 + i;
+  const int i = t.tx0 + threadIdx.x;
+  const int j0 = t.ty0 + ZRY * threadIdx.y;
+  bool cvalid[ZRY], cint[ZRY], ey[ZRY];
+  int ocol[ZRY];
+#pragma unroll
+  for (int r = 0; r < ZRY; ++r) {
+    const int j = j0 + r;
+    cvalid[r] = i <= n && j <= n;
+    cint[r] = i >= 1 && i < n && j >= 1 && j < n;
+    ey[r] = j == n - 1 && n % ZTY == 0;
+    ocol[r] = j * N1 + i;
+  }
+  const bool ex = i == n - 1 && n % ZTX == 0;
   const T c3 = T(g.h / 3.0), c12 = T(g.h / 12.0);
-  T a0 = T(0), a1 = T(0);                      // outputs of planes p - 1 and p so far
-  T kb[2][2] = {{T(0), T(0)}, {T(0), T(0)}};   // kappa layer p - 1
-  T vc = T(0);                                 // x at (i, j, p - 1)
-  double dot = 0.0;
+  T a0[ZRY], a1[ZRY], vc[ZRY];   // outputs of planes p - 1 and p so far; x at plane p - 1
+  typename Epi::Pre pre[ZRY];    // epilogue inputs of plane p - 1
+#pragma unroll
+  for (int r = 0; r < ZRY; ++r) a0[r] = a1[r] = vc[r] = T(0);
+  T kb[ZRY + 1][2];              // kappa layer p - 1, element rows j0 - 1 .. j0 + ZRY - 1
+#pragma unroll
+  for (int r = 0; r <= ZRY; ++r) kb[r][0] = kb[r][1] = T(0);
+  T dot = T(0);
+  const int vbase = (ZRY * threadIdx.y + 1) * ZSX + threadIdx.x + 1;
+  const int kbase = ZRY * threadIdx.y * ZKX + threadIdx.x;
   int buf = 0;
-  const T* V0 = &sv[0][(threadIdx.y + 1) * ZSX + threadIdx.x + 1];
-  const T* K0 = &sk[0][threadIdx.y * ZKX + threadIdx.x];
   for (; p <= t.z1; ++p) {
     T* svb = sv[buf];
     T* skb = sk[buf];
-    svb[tid] = rv[0];
-    if (v1) svb[tid + ZTHREADS] = rv[1];
-    skb[tid] = rk[0];
-    if (k1) skb[tid + ZTHREADS] = rk[1];
+#pragma unroll
+    for (int q = 0; q < ZSLOTS; ++q) {
+      if (vin[q]) svb[tid + q * ZTHREADS] = rv[q];
+      if (kin[q]) skb[tid + q * ZTHREADS] = rk[q];
+    }
     __syncthreads();
     if (p < t.z1) fetch(p + 1);   // the next plane is in flight while this one is used
-    const T* V = V0 + buf * ZNV;
-    const T* KK = K0 + buf * ZNK;
-    T v[3][3], ka[2][2];
+    typename Epi::Pre nxt[ZRY];
 #pragma unroll
-    for (int dy = 0; dy < 3; ++dy)
+    for (int r = 0; r < ZRY; ++r)
+      if (cint[r] && p >= t.z0 && p < t.z1 && p >= 1 && p < n) nxt[r] = epi.load(p * P + ocol[r]);
+    T v[ZRY + 2][3], ka[ZRY + 1][2];
 #pragma unroll
-      for (int dx = 0; dx < 3; ++dx) v[dy][dx] = V[(dy - 1) * ZSX + (dx - 1)];
+    for (int r = 0; r < ZRY + 2; ++r)
 #pragma unroll
-    for (int bq = 0; bq < 2; ++bq)
+      for (int dx = 0; dx < 3; ++dx) v[r][dx] = svb[vbase + (r - 1) * ZSX + (dx - 1)];
 #pragma unroll
-      for (int a = 0; a < 2; ++a) ka[bq][a] = KK[bq * ZKX + a];
-    // output p - 1 is complete
-    a0 -= c12 * across3(kb, v);
+    for (int r = 0; r <= ZRY; ++r)
+#pragma unroll
+      for (int a = 0; a < 2; ++a) ka[r][a] = skb[kbase + r * ZKX + a];
     const int m = p - 1;
-    if (col_valid && m >= t.z0) {
-      const int o = m * P + ocol;
-      dot += epi(o, col_int && m >= 1 && m < n, a0, vc);
-      if (ex) epi.zero(o + 1);
-      if (ey) epi.zero(o + N1);
-      if (ex && ey) epi.zero(o + N1 + 1);
+#pragma unroll
+    for (int r = 0; r < ZRY; ++r) {
+      // output (i, j0 + r, p - 1) is complete
+      const T done = a0[r] - c12 * across3(kb[r], kb[r + 1], v[r], v[r + 1], v[r + 2]);
+      if (cvalid[r] && m >= t.z0) {
+        const int o = m * P + ocol[r];
+        dot += epi(o, cint[r] && m >= 1 && m < n, done, vc[r], pre[r]);
+        if (ex) epi.zero(o + 1);
+        if (ey[r]) epi.zero(o + N1);
+        if (ex && ey[r]) epi.zero(o + N1 + 1);
+      }
+      a0[r] = a1[r] + inplane3(kb[r], kb[r + 1], ka[r], ka[r + 1], v[r], v[r + 1], v[r + 2], c3, c12);
+      a1[r] = -c12 * across3(ka[r], ka[r + 1], v[r], v[r + 1], v[r + 2]);
+      vc[r] = v[r + 1][1];
+      pre[r] = nxt[r];
     }
-    a0 = a1 + inplane3(kb, ka, v, c3, c12);
-    a1 = -c12 * across3(ka, v);
 #pragma unroll
-    for (int bq = 0; bq < 2; ++bq)
-#pragma unroll
-      for (int a = 0; a < 2; ++a) kb[bq][a] = ka[bq][a];
-    vc = v[1][1];
+    for (int r = 0; r <= ZRY; ++r) {
+      kb[r][0] = ka[r][0];
+      kb[r][1] = ka[r][1];
+    }
     buf ^= 1;
   }
-  if (part) cta_partial3(dot, part, g.tiles_s);
+  if (part) cta_partial3((double)dot, part, g.tiles_s);
   prof_tick3(prof);
 }
 
-// Epilogues: bind(sample) offsets their arrays to the sample; then
-// (node offset, interior?, (A x) at the node, x at the node) -> contribution
-// to the CTA partial; zero() writes a boundary node.
+// Epilogues: bind(sample) offsets their arrays to the sample; load(node)
+// fetches the node's own inputs (Pre) one plane ahead; then (node offset,
+// interior?, (A x) at the node, x at the node, Pre) -> contribution to the
+// CTA partial; zero() writes a boundary node.
+struct NoPre {};
+
 template <class T>
 struct EpiApply {   // y = A x
+  using Pre = NoPre;
   T* Y;
   int64_t ns;
   __device__ void bind(int64_t b) { Y += b * ns; }
-  __device__ double operator()(int o, bool in, T ax, T) const {
+  __device__ Pre load(int) const { return Pre{}; }
+  __device__ T operator()(int o, bool in, T ax, T, const Pre&) const {
     Y[o] = in ? ax : T(0);
-    return 0.0;
+    return T(0);
   }
   __device__ void zero(int o) const { Y[o] = T(0); }
 };
 
 template <class T>
 struct EpiAq {   // q = A p, partial of p.q
+  using Pre = NoPre;
   T* Q;
   int64_t ns;
   __device__ void bind(int64_t b) { Q += b * ns; }
-  __device__ double operator()(int o, bool in, T ax, T xc) const {
+  __device__ Pre load(int) const { return Pre{}; }
+  __device__ T operator()(int o, bool in, T ax, T xc, const Pre&) const {
     const T qv = in ? ax : T(0);
     Q[o] = qv;
-    return in ? (double)(xc * qv) : 0.0;
+    return xc * qv;
   }
   __device__ void zero(int o) const { Q[o] = T(0); }
 };
 
 template <class T>
+struct PreB {
+  T b;
+};
+
+template <class T>
 struct EpiMgRes {   // residual of the pre-smoothed iterate: b - A e
+  using Pre = PreB<T>;
   const T* Bv;
   T* R1;
   int64_t ns;
@@ -297,15 +336,22 @@ struct EpiMgRes {   // residual of the pre-smoothed iterate: b - A e
     Bv += b * ns;
     R1 += b * ns;
   }
-  __device__ double operator()(int o, bool in, T ax, T) const {
-    R1[o] = in ? __ldg(Bv + o) - ax : T(0);
-    return 0.0;
+  __device__ Pre load(int o) const { return Pre{__ldg(Bv + o)}; }
+  __device__ T operator()(int o, bool in, T ax, T, const Pre& pr) const {
+    R1[o] = in ? pr.b - ax : T(0);
+    return T(0);
   }
   __device__ void zero(int o) const { R1[o] = T(0); }
 };
 
 template <class T>
+struct PreBW {
+  T b, w;
+};
+
+template <class T>
 struct EpiMgPost {   // post-smoothing: e + W (b - A e), partial of b.out
+  using Pre = PreBW<T>;
   const T* W;
   const T* Bv;
   T* Out;
@@ -315,25 +361,23 @@ struct EpiMgPost {   // post-smoothing: e + W (b - A e), partial of b.out
     Bv += b * ns;
     Out += b * ns;
   }
-  __device__ double operator()(int o, bool in, T ax, T ec) const {
-    if (!in) {
-      Out[o] = T(0);
-      return 0.0;
-    }
-    const T bval = __ldg(Bv + o);
-    const T ov = fma(__ldg(W + o), bval - ax, ec);
+  __device__ Pre load(int o) const { return Pre{__ldg(Bv + o), __ldg(W + o)}; }
+  __device__ T operator()(int o, bool in, T ax, T ec, const Pre& pr) const {
+    const T ov = in ? fma(pr.w, pr.b - ax, ec) : T(0);
     Out[o] = ov;
-    return (double)(bval * ov);
+    return in ? pr.b * ov : T(0);
   }
   __device__ void zero(int o) const { Out[o] = T(0); }
 };
 
 struct EpiResid {   // outer FP64 residual h^3 - A u, partial of its square
+  using Pre = NoPre;
   double* R;
   int64_t ns;
   double h3;
   __device__ void bind(int64_t b) { R += b * ns; }
-  __device__ double operator()(int o, bool in, double ax, double) const {
+  __device__ Pre load(int) const { return Pre{}; }
+  __device__ double operator()(int o, bool in, double ax, double, const Pre&) const {
     const double rv = in ? h3 - ax : 0.0;
     R[o] = rv;
     return rv * rv;
