@@ -163,6 +163,14 @@ mlmc_status mlmc_reset_stats(mlmc_plan plan);
 mlmc_status mlmc_sample_level(mlmc_plan plan, int level, int64_t first, int64_t count,
                               double* q_fine, double* q_coarse, int32_t* iters);
 
+/* Fold coupled sample values computed elsewhere (e.g. on other GPUs) into
+ * the level's device Welford state (Eq. (sample_variance)), in the order
+ * given: Y = qf[s] - qc[s] (qc NULL: Y = qf[s]), each sample adding the
+ * level cost C_l to cost_sum. qf, qc: host arrays of `count` doubles. Folding
+ * a level's samples in index order reproduces bit for bit the state that
+ * mlmc_sample_level builds. Synchronous; may allocate a staging buffer. */
+mlmc_status mlmc_level_fold(mlmc_plan plan, int level, const double* qf, const double* qc, int64_t count);
+
 /* Host copy of one level state. */
 mlmc_status mlmc_level_stats(mlmc_plan plan, int level, mlmc_level_state* out);
 

@@ -240,6 +240,8 @@ struct mlmc_plan_s {
   size_t ws_bytes = 0;
   size_t ws_budget = 0;
   bool ws_borrowed = false;       // ws belongs to the caller (mlmc_plan_set_workspace)
+  double* d_fold = nullptr;       // staging of mlmc_level_fold
+  int64_t fold_cap = 0;
   void* h_pin = nullptr;
   size_t h_pin_bytes = 0;
   // tracing
@@ -1418,6 +1420,7 @@ mlmc_status mlmc_plan_destroy(mlmc_plan p) {
   cudaFree(p->d_N);
   cudaFree(p->d_prof);
   if (p->ws && !p->ws_borrowed) cudaFree(p->ws);
+  if (p->d_fold) cudaFree(p->d_fold);
   if (p->h_pin) cudaFreeHost(p->h_pin);
   for (auto& e : p->pending) {
     cudaEventDestroy(e.a);
@@ -1576,6 +1579,30 @@ mlmc_status mlmc_sample_level(mlmc_plan p, int level, int64_t first, int64_t cou
     }
   }
   return bad ? MLMC_ERR_NOT_CONVERGED : MLMC_OK;
+}
+
+mlmc_status mlmc_level_fold(mlmc_plan p, int level, const double* qf, const double* qc, int64_t count) {
+  if (!p || level < 0 || level >= p->cfg.n_levels || count < 0 || (count > 0 && !qf)) return MLMC_ERR_INVALID;
+  if (count == 0) return MLMC_OK;
+  if (count > p->fold_cap) {
+    CK(cudaStreamSynchronize(p->stream));
+    if (p->d_fold) cudaFree(p->d_fold);
+    p->d_fold = nullptr;
+    p->fold_cap = 0;
+    if (cudaMalloc(&p->d_fold, sizeof(double) * 2 * (size_t)count) != cudaSuccess) {
+      cudaGetLastError();
+      return MLMC_ERR_OOM;
+    }
+    p->fold_cap = count;
+  }
+  double* dqf = p->d_fold;
+  double* dqc = qc ? p->d_fold + count : nullptr;
+  CK(cudaMemcpyAsync(dqf, qf, sizeof(double) * count, cudaMemcpyHostToDevice, p->stream));
+  if (qc) CK(cudaMemcpyAsync(dqc, qc, sizeof(double) * count, cudaMemcpyHostToDevice, p->stream));
+  const double cost = level_cost_cfg(&p->cfg, level);
+  CK(run(p, KID_WELFORD, [&] { return launch_welford(p->stream, dqf, dqc, count, p->d_states + level, cost); }));
+  CK(cudaStreamSynchronize(p->stream));
+  return MLMC_OK;
 }
 
 mlmc_status mlmc_level_stats(mlmc_plan p, int level, mlmc_level_state* out) {

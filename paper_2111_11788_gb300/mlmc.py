@@ -86,6 +86,13 @@ class RequestResult(ctypes.Structure):
                 ("N", ctypes.c_int64 * 16)]
 
 
+class SchedResult(ctypes.Structure):
+    """Mirror of ``mlmc_sched_result``."""
+    _fields_ = [("makespan", ctypes.c_double), ("work_total", ctypes.c_double),
+                ("work_lb", ctypes.c_double), ("last_start", ctypes.c_double),
+                ("idle_before_last", ctypes.c_double), ("batches", ctypes.c_int64)]
+
+
 _P = ctypes.c_void_p
 _I = ctypes.c_int
 _I64 = ctypes.c_int64
@@ -129,6 +136,11 @@ SIGNATURES = [
     ("mlmc_round_bytes", _I64, [ctypes.POINTER(Config), _I64P]),
     ("mlmc_plan_set_workspace", _I, [_P, _P, ctypes.c_uint64]),
     ("mlmc_run_adaptive", _I, [_P, _D, _I64, ctypes.c_int32, _DP, _DP, _I64P, _I32P]),
+    ("mlmc_level_fold", _I, [_P, _I, _DP, _DP, _I64]),
+    # include/mlmc_sched.h
+    ("mlmc_batch_size", _I64, [_I64, _I64, _I64, _D, _D]),
+    ("mlmc_schedule_greedy", _I, [_I, _I64P, _I64P, _DP, _I64, _I, _D, _D, _D,
+                                  ctypes.POINTER(SchedResult), _DP]),
     ("mlmc_adapt", _I, [_P, ctypes.c_int32, _D, _I64P, _I32P, _DP]),
     # include/mlmc_server.h
     ("mlmc_server_create", _I, [ctypes.POINTER(ServerConfig), ctypes.POINTER(_P)]),
@@ -300,6 +312,14 @@ class Plan:
         check(st, "mlmc_run")
         return q.value, v.value, Nout
 
+    def level_fold(self, level, qf, qc=None):
+        """mlmc_level_fold: fold host sample values into the level state, in order."""
+        import numpy as np
+        qf = np.ascontiguousarray(qf, dtype=np.float64)
+        qc = None if qc is None else np.ascontiguousarray(qc, dtype=np.float64)
+        check(lib().mlmc_level_fold(self._h, int(level), _dp(qf), _dp(qc), int(qf.size)),
+              "mlmc_level_fold")
+
     def run_adaptive(self, eps, pilot, L0):
         """mlmc_run_adaptive: returns (q_hat, stat_var, N per level, final level)."""
         import numpy as np
@@ -420,6 +440,30 @@ class Server:
 
     def __exit__(self, *a):
         self.close()
+
+
+def batch_size(N, n, parts, min_frac=0.01, max_frac=0.6180339887498949):
+    """mlmc_batch_size: the next batch of a level by Eq. (batch) (-1: invalid)."""
+    return lib().mlmc_batch_size(int(N), int(n), int(parts), float(min_frac), float(max_frac))
+
+
+def schedule_greedy(q, n_tasks, w, p, batch=False, min_frac=0.01, max_frac=0.6180339887498949,
+                    dispatch_cost=0.0, want_starts=False):
+    """mlmc_schedule_greedy: simulate Algorithm 1; returns (result dict, starts or None)."""
+    import numpy as np
+    L = len(q)
+    qa = np.ascontiguousarray(q, dtype=np.int64)
+    na = np.ascontiguousarray(n_tasks, dtype=np.int64)
+    wa = np.ascontiguousarray(w, dtype=np.float64)
+    st = np.zeros(wa.size) if want_starts else None
+    r = SchedResult()
+    check(lib().mlmc_schedule_greedy(L, qa.ctypes.data_as(_I64P), na.ctypes.data_as(_I64P),
+                                     _dp(wa), int(p), int(bool(batch)), float(min_frac),
+                                     float(max_frac), float(dispatch_cost), ctypes.byref(r),
+                                     _dp(st)), "mlmc_schedule_greedy")
+    return (dict(makespan=r.makespan, work_total=r.work_total, work_lb=r.work_lb,
+                 last_start=r.last_start, idle_before_last=r.idle_before_last,
+                 batches=r.batches), st)
 
 
 def allocate(V, C, eps):
