@@ -312,6 +312,13 @@ class Plan:
         check(st, "mlmc_run")
         return q.value, v.value, Nout
 
+    def allocation(self, eps):
+        """mlmc_allocation: N_l of Eq. (mlmc_num_samples) from the device level states."""
+        import numpy as np
+        N = np.zeros(self.cfg.n_levels, dtype=np.int64)
+        check(lib().mlmc_allocation(self._h, float(eps), N.ctypes.data_as(_I64P)), "mlmc_allocation")
+        return N
+
     def level_fold(self, level, qf, qc=None):
         """mlmc_level_fold: fold host sample values into the level state, in order."""
         import numpy as np
