@@ -80,6 +80,11 @@ typedef struct mlmc_config {
   int32_t use_graphs;      /* 1: each batched solve runs as one CUDA graph whose
                               while-nodes iterate on the device (no host polls);
                               0: host-driven iterations. Same results either way. */
+  int32_t total_order;     /* -1: full tensor basis, M = m^dim modes; K >= 0:
+                              total-order truncation (Sec. 5.2): only modes with
+                              k_x + k_y (+ k_z) <= K (each k < m), M of them, in
+                              the full basis' flat order */
+  int32_t reserved0;       /* 0 */
 } mlmc_config;
 
 /* Per-level Welford state (Eq. (sample_variance): V = m2 / n). */
@@ -96,8 +101,8 @@ typedef struct mlmc_plan_s* mlmc_plan;
 
 /* Defaults: 2D, 3 levels, n_0 = 16, m = 4, sigma2 = 1, corr_len = 0.3,
  * domain-mean QoI, Jacobi-PCG, rtol 1e-10, FP64, seed 0, mg_omega 0.9,
- * CUDA graphs on; mixed form: inner_rtol 3e-3, inner_max_iter 60,
- * outer_max_iter 16.
+ * CUDA graphs on, full tensor KLE basis (total_order -1); mixed form:
+ * inner_rtol 3e-3, inner_max_iter 60, outer_max_iter 16.
  *
  * MLMC_MIXED (iterative refinement, the precision pattern the method admits
  * on GB300): u = 0, r = b; repeat { d = A32^-1 (r / s) by FP32 PCG with
@@ -129,7 +134,7 @@ mlmc_status mlmc_plan_create(const mlmc_config* cfg, void* stream, mlmc_plan* ou
 mlmc_status mlmc_plan_destroy(mlmc_plan plan);
 
 /* Re-target an idle plan to a configuration of the same shape (dim,
- * n_levels, coarse_cells, modes_per_dim, solver, precision): field
+ * n_levels, coarse_cells, modes_per_dim, solver, precision, total_order): field
  * parameters, seed, stream id, tolerances and QoI may change. Rebuilds the
  * KLE tables in place, drops cached graphs and resets the level states;
  * allocates nothing (no device synchronisation from cudaFree). A nonzero
@@ -235,12 +240,15 @@ mlmc_status mlmc_allocation(mlmc_plan plan, double eps, int64_t* N_out);
 
 /* ---- device-level steps (device pointers, asynchronous on the plan's stream) */
 
-/* xi[s * n_modes + k] = xi_k(level, first + s), s < count (the plan's seed
- * and stream_id; Philox4x32-10 counter (k/2, i, level, stream_id)). */
+/* xi[s * M + k] = xi_k(level, first + s), s < count (the plan's seed and
+ * stream_id; Philox4x32-10 counter (k/2, i, level, stream_id)); M = m^dim,
+ * or the number of modes kept by the total-order truncation, coefficient k
+ * belonging to the k-th kept mode in the full basis' flat order. */
 mlmc_status mlmc_draw_xi(mlmc_plan plan, int level, int64_t first, int64_t count, double* xi);
 
 /* kappa = exp(Phi xi) at the element centroids of mesh `mesh` for `count`
- * coefficient vectors xi (count x M, contiguous). Output element arrays. */
+ * coefficient vectors xi (count x M, contiguous; Phi restricted to the kept
+ * modes under total-order truncation). Output element arrays. */
 mlmc_status mlmc_kappa(mlmc_plan plan, int mesh, const double* xi, int64_t count, double* kappa);
 
 /* y = A(kappa) x on mesh `mesh` (Q1 stiffness, homogeneous Dirichlet):

@@ -76,23 +76,30 @@ def centroids_1d(n):
     return (np.arange(n, dtype=np.float64) + 0.5) / n
 
 
-def mode_indices(dim, m):
-    """Per-axis mode indices of flat mode k (k_x fastest); shape (m^dim, dim)."""
+def mode_indices(dim, m, total_order=None):
+    """Per-axis mode indices of flat mode k (k_x fastest); shape (M, dim).
+
+    total_order K (Sec. 5.2, "total-order basis"): keep only the modes with
+    k_x + k_y (+ k_z) <= K, in the same flat order; None or K < 0 keeps the
+    full tensor basis (M = m^dim)."""
     grids = np.meshgrid(*([np.arange(m)] * dim), indexing='ij')
     # grids[0] varies slowest in C order -> reverse so axis 0 is x (fastest)
     flat = [g.reshape(-1) for g in grids]
-    return np.stack(flat[::-1], axis=1)
+    kidx = np.stack(flat[::-1], axis=1)
+    if total_order is not None and total_order >= 0:
+        kidx = kidx[kidx.sum(axis=1) <= total_order]
+    return kidx
 
 
-def phi_matrix(dim, n, corr_len, sigma2, m):
+def phi_matrix(dim, n, corr_len, sigma2, m, total_order=None):
     """Dense Phi[e, k] = sqrt(sigma^2 prod_a theta_{k_a}) prod_a f_{k_a}(c_a(e)).
 
     Elements e are in lexicographic order, x fastest; c(e) is the centroid.
-    Shape (n^dim, m^dim).
+    Shape (n^dim, M) with M modes as chosen by ``mode_indices``.
     """
     omega, theta, even = eigenpairs_1d(corr_len, m)
     f = eigfun_1d(omega, even, centroids_1d(n))            # (n, m)
-    kidx = mode_indices(dim, m)                             # (M, dim)
+    kidx = mode_indices(dim, m, total_order)               # (M, dim)
     lam = sigma2 * np.prod(theta[kidx], axis=1)             # (M,)
     cells = np.stack([g.reshape(-1) for g in
                       np.meshgrid(*([np.arange(n)] * dim), indexing='ij')][::-1], axis=1)
@@ -102,13 +109,18 @@ def phi_matrix(dim, n, corr_len, sigma2, m):
     return phi * np.sqrt(lam)[None, :]
 
 
-def log_field(dim, n, corr_len, sigma2, m, xi):
+def log_field(dim, n, corr_len, sigma2, m, xi, total_order=None):
     """g = Phi xi at the element centroids; xi shape (M,) or (B, M) -> (B, n^dim)."""
-    phi = phi_matrix(dim, n, corr_len, sigma2, m)
+    phi = phi_matrix(dim, n, corr_len, sigma2, m, total_order)
     xi = np.atleast_2d(xi)
     return xi @ phi.T
 
 
-def kappa(dim, n, corr_len, sigma2, m, xi):
+def kappa(dim, n, corr_len, sigma2, m, xi, total_order=None):
     """kappa = exp(Phi xi), one value per element (x fastest)."""
-    return np.exp(log_field(dim, n, corr_len, sigma2, m, xi))
+    return np.exp(log_field(dim, n, corr_len, sigma2, m, xi, total_order))
+
+
+def n_modes(dim, m, total_order=None):
+    """M: m^dim, or the number of modes of the total-order truncation."""
+    return len(mode_indices(dim, m, total_order))

@@ -50,7 +50,7 @@ def solve_qoi(cfg, mesh, xi):
     """Q(u_mesh) for one coefficient vector xi: kappa, assemble, solve, QoI."""
     d = cfg['dim']
     n = mesh_cells(cfg, mesh)
-    kap = kle.kappa(d, n, cfg['corr_len'], cfg['sigma2'], cfg['m'], xi)[0]
+    kap = kle.kappa(d, n, cfg['corr_len'], cfg['sigma2'], cfg['m'], xi, cfg.get('total_order'))[0]
     A = fem.assemble_fast(d, n, kap)
     b = fem.load_vector(d, n)
     u = fem.solve(A, b, d)
@@ -60,7 +60,7 @@ def solve_qoi(cfg, mesh, xi):
 
 def coupled_sample(cfg, level, i):
     """(Q_l, Q_{l-1}) of sample i on level l with shared xi(l, i); Q_{-1} = 0."""
-    M = cfg['m'] ** cfg['dim']
+    M = kle.n_modes(cfg['dim'], cfg['m'], cfg.get('total_order'))
     xi = philox.draw_xi(cfg['seed'], cfg.get('stream_id', 0), level, [i], M)[0]
     qf = solve_qoi(cfg, level, xi)
     qc = solve_qoi(cfg, level - 1, xi) if level > 0 else 0.0

@@ -38,10 +38,26 @@ __global__ void k_kle_table(int n, int m, const double* __restrict__ omega,
 
 constexpr int KAP_ROWS = 4;  // element rows per thread in 2D
 
+// The sample's KLE coefficients in the full tensor layout (m^dim entries) in
+// shared memory: a copy, or under total-order truncation the kept
+// coefficients scattered to their full-basis slots and zeros elsewhere.
+__device__ __forceinline__ void load_coefs(const double* __restrict__ xs, int M_xi,
+                                           const int32_t* __restrict__ slot, int M_full,
+                                           double* s_xi, int tid, int nthreads) {
+  if (!slot) {
+    for (int k = tid; k < M_full; k += nthreads) s_xi[k] = xs[k];
+    return;
+  }
+  for (int k = tid; k < M_full; k += nthreads) s_xi[k] = 0.0;
+  __syncthreads();
+  for (int t = tid; t < M_xi; t += nthreads) s_xi[slot[t]] = xs[t];
+}
+
 // 2D: CTA covers 32 x (8 * KAP_ROWS) elements of one sample.
 __global__ void __launch_bounds__(TX2* TY2)
     k_kappa2d(int n, int m, double sqrt_sigma2, const double* __restrict__ table,
-              const double* __restrict__ xi, int64_t es, double* __restrict__ kappa, Prof prof) {
+              const double* __restrict__ xi, int M_xi, const int32_t* __restrict__ slot,
+              int64_t es, double* __restrict__ kappa, Prof prof) {
   __shared__ double s_xi[MAX_MODES_1D * MAX_MODES_1D];
   __shared__ double s_t[TX2][MAX_MODES_1D + 1];          // T[ix][k_y]
   __shared__ double s_fy[TY2 * KAP_ROWS][MAX_MODES_1D + 1];
@@ -50,9 +66,7 @@ __global__ void __launch_bounds__(TX2* TY2)
   const int nthreads = TX2 * TY2;
   const int x0 = blockIdx.x * TX2;
   const int y0 = blockIdx.y * TY2 * KAP_ROWS;
-  const int M = m * m;
-  const double* xs = xi + (int64_t)b * M;
-  for (int k = tid; k < M; k += nthreads) s_xi[k] = xs[k];
+  load_coefs(xi + (int64_t)b * M_xi, M_xi, slot, m * m, s_xi, tid, nthreads);
   for (int idx = tid; idx < TY2 * KAP_ROWS * m; idx += nthreads) {
     const int r = idx / m, k = idx - r * m;
     const int iy = y0 + r;
@@ -93,8 +107,8 @@ __global__ void __launch_bounds__(TX2* TY2)
 constexpr int K3_TY = 4;
 __global__ void __launch_bounds__(TX2* K3_TY)
     k_kappa3d(int n, int m, double sqrt_sigma2, const double* __restrict__ table,
-              const double* __restrict__ xi, int64_t es, double* __restrict__ kappa,
-              int z_chunk, Prof prof) {
+              const double* __restrict__ xi, int M_xi, const int32_t* __restrict__ slot,
+              int64_t es, double* __restrict__ kappa, int z_chunk, Prof prof) {
   extern __shared__ double smem[];
   const int M = m * m * m;
   double* s_xi = smem;                              // M
@@ -104,8 +118,7 @@ __global__ void __launch_bounds__(TX2* K3_TY)
   const int nthreads = TX2 * K3_TY;
   const int x0 = blockIdx.x * TX2;
   const int iy = blockIdx.y * K3_TY + threadIdx.y;
-  const double* xs = xi + (int64_t)b * M;
-  for (int k = tid; k < M; k += nthreads) s_xi[k] = xs[k];
+  load_coefs(xi + (int64_t)b * M_xi, M_xi, slot, M, s_xi, tid, nthreads);
   __syncthreads();
   const int mm = m * m;
   for (int idx = tid; idx < TX2 * mm; idx += nthreads) {
@@ -196,11 +209,12 @@ cudaError_t launch_kle_table(cudaStream_t s, int n, int m, const double* omega,
 }
 
 cudaError_t launch_kappa(cudaStream_t s, const Grid& g, int m, double sqrt_sigma2,
-                         const double* table, const double* xi, int64_t B, double* kappa, Prof p) {
+                         const double* table, const double* xi, int M_xi, const int32_t* slot,
+                         int64_t B, double* kappa, Prof p) {
   if (B == 0) return cudaSuccess;
   if (g.dim == 2) {
     dim3 grid((g.n + TX2 - 1) / TX2, (g.n + TY2 * KAP_ROWS - 1) / (TY2 * KAP_ROWS), (unsigned)B);
-    k_kappa2d<<<grid, dim3(TX2, TY2), 0, s>>>(g.n, m, sqrt_sigma2, table, xi, g.es, kappa, p);
+    k_kappa2d<<<grid, dim3(TX2, TY2), 0, s>>>(g.n, m, sqrt_sigma2, table, xi, M_xi, slot, g.es, kappa, p);
   } else {
     const int M = m * m * m;
     const size_t smem = sizeof(double) * ((size_t)M + (size_t)TX2 * m * m);
@@ -210,8 +224,8 @@ cudaError_t launch_kappa(cudaStream_t s, const Grid& g, int m, double sqrt_sigma
       attr_set = true;
     }
     dim3 grid((g.n + TX2 - 1) / TX2, (g.n + K3_TY - 1) / K3_TY, (unsigned)B);
-    k_kappa3d<<<grid, dim3(TX2, K3_TY), smem, s>>>(g.n, m, sqrt_sigma2, table, xi, g.es, kappa,
-                                                   g.n, p);
+    k_kappa3d<<<grid, dim3(TX2, K3_TY), smem, s>>>(g.n, m, sqrt_sigma2, table, xi, M_xi, slot, g.es,
+                                                   kappa, g.n, p);
   }
   return cudaGetLastError();
 }

@@ -126,7 +126,8 @@ cudaError_t launch_kle_table(cudaStream_t s, int n, int m, const double* omega,
                              const double* theta, const int32_t* even, double* table);
 
 cudaError_t launch_kappa(cudaStream_t s, const Grid& g, int m, double sqrt_sigma2,
-                         const double* table, const double* xi, int64_t B, double* kappa, Prof p);
+                         const double* table, const double* xi, int M_xi, const int32_t* slot,
+                         int64_t B, double* kappa, Prof p);
 
 template <class T>
 cudaError_t launch_coarsen(cudaStream_t s, const Grid& fine, const Grid& coarse,

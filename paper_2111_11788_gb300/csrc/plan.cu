@@ -226,7 +226,8 @@ using namespace mlmc;
 struct mlmc_plan_s {
   mlmc_config cfg;
   cudaStream_t stream = nullptr;
-  int M = 0;
+  int M = 0;                      // KLE coefficients per sample
+  int32_t* d_slot = nullptr;      // total-order truncation: full-basis index of each coefficient
   double sqrt_sigma2 = 1.0;
   std::vector<MeshInfo> meshes;
   double* d_omega = nullptr;
@@ -280,7 +281,32 @@ namespace {
 
 bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 
+// Number of KLE coefficients: m^dim, or the modes with k_x + k_y (+ k_z) <= K.
+int64_t coef_count(const mlmc_config* c) {
+  const int m = c->modes_per_dim;
+  if (c->total_order < 0) return ipow(m, c->dim);
+  int64_t M = 0;
+  for (int kz = 0; kz < (c->dim == 3 ? m : 1); ++kz)
+    for (int ky = 0; ky < m; ++ky)
+      for (int kx = 0; kx < m; ++kx)
+        if (kx + ky + kz <= c->total_order) ++M;
+  return M;
+}
+
+// Full-basis flat index (k_z m + k_y) m + k_x of each kept coefficient.
+std::vector<int32_t> coef_slots(const mlmc_config* c) {
+  std::vector<int32_t> slot;
+  const int m = c->modes_per_dim;
+  for (int kz = 0; kz < (c->dim == 3 ? m : 1); ++kz)
+    for (int ky = 0; ky < m; ++ky)
+      for (int kx = 0; kx < m; ++kx)
+        if (c->total_order < 0 || kx + ky + kz <= c->total_order)
+          slot.push_back((int32_t)((kz * m + ky) * m + kx));
+  return slot;
+}
+
 mlmc_status validate(const mlmc_config* c) {
+  if (c && c->total_order < -1) return MLMC_ERR_INVALID;
   if (!c) return MLMC_ERR_INVALID;
   if (c->dim != 2 && c->dim != 3) return MLMC_ERR_INVALID;
   if (c->n_levels < 1 || c->n_levels > 16) return MLMC_ERR_INVALID;
@@ -1006,8 +1032,8 @@ mlmc_status solve_mixed(mlmc_plan p, int mesh, const MeshInfo& mi, MixedWs& w, i
 mlmc_status make_kappa(mlmc_plan p, int mesh, const double* xi, int64_t B, double* kappa) {
   const MeshInfo& mi = p->meshes[mesh];
   CK(run(p, KID_KAPPA, [&] {
-    return launch_kappa(p->stream, mi.g[0], p->cfg.modes_per_dim, p->sqrt_sigma2, mi.table, xi, B,
-                        kappa, prof_for(p, KID_KAPPA, elems_of(mi.g[0]) * 8));
+    return launch_kappa(p->stream, mi.g[0], p->cfg.modes_per_dim, p->sqrt_sigma2, mi.table, xi, p->M,
+                        p->d_slot, B, kappa, prof_for(p, KID_KAPPA, elems_of(mi.g[0]) * 8));
   }));
   return MLMC_OK;
 }
@@ -1199,6 +1225,8 @@ void mlmc_config_default(mlmc_config* c) {
   c->inner_max_iter = 60;
   c->outer_max_iter = 16;
   c->use_graphs = 1;
+  c->total_order = -1;
+  c->reserved0 = 0;
 }
 
 int64_t mlmc_node_stride(int dim, int n) {
@@ -1250,7 +1278,7 @@ mlmc_status mlmc_plan_create(const mlmc_config* cfg, void* stream, mlmc_plan* ou
   p->cfg = *cfg;
   p->stream = (cudaStream_t)stream;
   const int m = cfg->modes_per_dim;
-  p->M = (int)ipow(m, cfg->dim);
+  p->M = (int)coef_count(cfg);
   p->sqrt_sigma2 = std::sqrt(cfg->sigma2);
   std::vector<double> omega, theta;
   std::vector<int32_t> even;
@@ -1269,6 +1297,16 @@ mlmc_status mlmc_plan_create(const mlmc_config* cfg, void* stream, mlmc_plan* ou
       cudaMalloc(&p->d_prof, sizeof(double) * NUM_KERNELS) != cudaSuccess) {
     cudaGetLastError();
     return fail(MLMC_ERR_OOM);
+  }
+  if (cfg->total_order >= 0) {
+    const std::vector<int32_t> slot = coef_slots(cfg);
+    if (cudaMalloc(&p->d_slot, sizeof(int32_t) * slot.size()) != cudaSuccess) {
+      p->d_slot = nullptr;
+      cudaGetLastError();
+      return fail(MLMC_ERR_OOM);
+    }
+    if (cudaMemcpy(p->d_slot, slot.data(), sizeof(int32_t) * slot.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail(MLMC_ERR_CUDA);
   }
   std::vector<double> cost(cfg->n_levels);
   for (int l = 0; l < cfg->n_levels; ++l) cost[l] = level_cost_cfg(cfg, l);
@@ -1337,7 +1375,7 @@ mlmc_status mlmc_plan_retarget(mlmc_plan p, const mlmc_config* cfg) {
   const mlmc_config& o = p->cfg;
   if (cfg->dim != o.dim || cfg->n_levels != o.n_levels || cfg->coarse_cells != o.coarse_cells ||
       cfg->modes_per_dim != o.modes_per_dim || cfg->solver != o.solver ||
-      cfg->precision != o.precision)
+      cfg->precision != o.precision || cfg->total_order != o.total_order)
     return MLMC_ERR_INVALID;
   if (!p->round_count.empty()) return MLMC_ERR_INVALID;
   CK(cudaStreamSynchronize(p->stream));
@@ -1381,7 +1419,7 @@ mlmc_status mlmc_plan_set_workspace(mlmc_plan p, void* ws, uint64_t bytes) {
 
 int64_t mlmc_round_bytes(const mlmc_config* cfg, const int64_t* count) {
   if (!cfg || !count || validate(cfg) != MLMC_OK) return -1;
-  const int M = (int)ipow(cfg->modes_per_dim, cfg->dim);
+  const int M = (int)coef_count(cfg);
   int64_t total = 0;
   for (int l = 0; l < cfg->n_levels; ++l) {
     if (count[l] <= 0) continue;
@@ -1412,6 +1450,7 @@ mlmc_status mlmc_plan_destroy(mlmc_plan p) {
   for (auto& mi : p->meshes)
     if (mi.table) cudaFree(mi.table);
   cudaFree(p->d_omega);
+  cudaFree(p->d_slot);
   cudaFree(p->d_theta);
   cudaFree(p->d_even);
   cudaFree(p->d_states);

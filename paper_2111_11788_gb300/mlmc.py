@@ -54,6 +54,8 @@ class Config(ctypes.Structure):
         ("inner_max_iter", ctypes.c_int32),
         ("outer_max_iter", ctypes.c_int32),
         ("use_graphs", ctypes.c_int32),
+        ("total_order", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32),
     ]
 
 
@@ -195,7 +197,7 @@ def config(dim=2, n_levels=3, coarse_cells=16, modes_per_dim=4, sigma2=1.0, corr
            qoi="domain", solver="jacobi", box=(0.25, 0.75), rtol=1e-10, max_iter=None,
            precision="fp64", seed=0, stream_id=0, mg_omega=None, check_every=0,
            workspace_bytes=0, inner_rtol=None, inner_max_iter=None, outer_max_iter=None,
-           use_graphs=None):
+           use_graphs=None, total_order=None):
     """Build a Config from plain values (defaults from mlmc_config_default)."""
     c = Config()
     lib().mlmc_config_default(ctypes.byref(c))
@@ -223,6 +225,8 @@ def config(dim=2, n_levels=3, coarse_cells=16, modes_per_dim=4, sigma2=1.0, corr
         c.outer_max_iter = outer_max_iter
     if use_graphs is not None:
         c.use_graphs = int(use_graphs)
+    if total_order is not None:
+        c.total_order = int(total_order)
     return c
 
 
@@ -233,7 +237,8 @@ def config_from_workload(wl, **over):
                 qoi=wl.get("qoi", "domain"), solver=wl.get("solver", "jacobi"),
                 box=tuple(wl.get("box", (0.25, 0.75))), rtol=wl["rtol"],
                 seed=wl.get("seed", 0), stream_id=wl.get("stream_id", 0),
-                precision=wl.get("precision", "fp64"))
+                precision=wl.get("precision", "fp64"),
+                total_order=-1 if wl.get("total_order") is None else wl["total_order"])
     args.update(over)
     return config(**args)
 

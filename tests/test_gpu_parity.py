@@ -336,3 +336,46 @@ def test_round_graph_run_matches_level_by_level(m, dim, precision):
             out.append((q, v, list(N), [plan.level_stats(l) for l in range(3)], plan.launch_count()))
     assert out[0][:4] == out[1][:4]
     assert out[1][4] > 0
+
+
+# ------------------------------------------------ total-order KLE truncation
+
+@pytest.mark.parametrize("dim,n0,levels,mpd,K", [(2, 8, 3, 6, 4), (2, 5, 2, 8, 7), (3, 4, 2, 5, 3),
+                                                 (3, 3, 2, 4, 0)])
+def test_kappa_parity_total_order(m, dim, n0, levels, mpd, K):
+    """xi has the kept-mode count; kappa = exp(Phi xi) over the kept modes (<= 1e-12)."""
+    cfg = m.config(dim=dim, n_levels=levels, coarse_cells=n0, modes_per_dim=mpd, corr_len=0.2,
+                   sigma2=1.4, seed=3, total_order=K)
+    M = kle.n_modes(dim, mpd, K)
+    assert M < mpd ** dim
+    count = 5
+    with m.Plan(cfg, stream()) as plan:
+        xi = dev(count * M)
+        plan.draw_xi(levels - 1, 2, count, xi.data_ptr())
+        xin = xi.cpu().numpy().reshape(count, M)
+        assert np.array_equal(xin, philox.draw_xi(3, 0, levels - 1, list(range(2, 2 + count)), M))
+        for mesh in range(levels):
+            n = n0 << mesh
+            es = m.elem_stride(dim, n)
+            kap = dev(count * es)
+            plan.kappa(mesh, xi.data_ptr(), count, kap.data_ptr())
+            got = kap.cpu().numpy().reshape(count, es)[:, :n ** dim]
+            ref = kle.kappa(dim, n, 0.2, 1.4, mpd, xin, K)
+            assert np.max(np.abs(got - ref) / ref) <= 1e-12
+
+
+@pytest.mark.parametrize("dim,precision", [(2, "fp64"), (3, "mixed")])
+def test_coupled_samples_total_order(m, dim, precision):
+    if dim == 2:
+        wl = small_case(2, n0=8, levels=2, m=6, solver="gmg", rtol=1e-11, precision=precision,
+                        total_order=3)
+    else:
+        wl = small_case(3, n0=4, levels=2, m=4, solver="gmg", qoi="box", rtol=1e-11,
+                        precision=precision, total_order=2)
+    cfg = m.config_from_workload(wl)
+    with m.Plan(cfg, stream()) as plan:
+        qf, qc, _ = plan.sample_level(1, 0, 4)
+    for s in range(4):
+        rf, rc = omlmc.coupled_sample(wl, 1, s)
+        assert abs(qf[s] - rf) <= RTOL_Q * abs(rf)
+        assert abs(qc[s] - rc) <= RTOL_Q * abs(rc)

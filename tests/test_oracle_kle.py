@@ -7,7 +7,14 @@ quadrature; eigenvalues sum to the variance x length (trace of the kernel)
 and the Mercer sum converges pointwise; a Nystrom discretisation of the
 kernel gives the same leading eigenvalues; the tensor basis reproduces the
 separable covariance and the sampled log-field has the truncated variance.
+Total-order truncation (Sec. 5.2): the kept-mode count equals the closed form
+C(K + d, d) when K < m and a brute-force count otherwise (680 modes for d =
+3, m = 16 at K = 14); the truncated field equals the full-basis field with
+the dropped coefficients set to zero; its pointwise variance is the Mercer
+sum over the kept modes.
 """
+import itertools
+import math
 import numpy as np
 import pytest
 
@@ -114,3 +121,52 @@ def test_3d_tensor_index_order():
     assert np.allclose(r[..., 1], r[:1, :1, :, 1])    # k = 1: k_x = 1, depends on x only
     assert np.allclose(r[..., 2], r[:1, :, :1, 2])    # k = 2: k_y = 1, y only
     assert np.allclose(r[..., 4], r[:, :1, :1, 4])    # k = 4: k_z = 1, z only
+
+
+# ---------------------------------------------------- total-order truncation
+
+@pytest.mark.parametrize("dim,m,K", [(2, 4, 0), (2, 4, 2), (2, 4, 3), (2, 6, 8), (3, 3, 1),
+                                     (3, 5, 4), (3, 5, 7), (3, 7, 12)])
+def test_total_order_count(dim, m, K):
+    brute = sum(1 for k in itertools.product(range(m), repeat=dim) if sum(k) <= K)
+    assert kle.n_modes(dim, m, K) == brute
+    if K < m:
+        assert brute == math.comb(K + dim, dim)
+    assert kle.n_modes(dim, m, None) == m ** dim == kle.n_modes(dim, m, -1)
+
+
+def test_total_order_680_modes():
+    # 16 eigenfunctions per axis, 3D, sum of 0-based orders <= 14
+    assert kle.n_modes(3, 16, 14) == 680
+
+
+@pytest.mark.parametrize("dim,m,K,n", [(2, 5, 3, 12), (3, 4, 2, 5)])
+def test_truncated_field_is_full_field_with_dropped_coefficients_zero(dim, m, K, n):
+    rng = np.random.default_rng(4)
+    full = kle.mode_indices(dim, m)
+    kept = kle.mode_indices(dim, m, K)
+    M = len(kept)
+    xi = rng.standard_normal((3, M))
+    # scatter into the full basis by matching per-axis indices
+    pos = {tuple(k): i for i, k in enumerate(full)}
+    xf = np.zeros((3, len(full)))
+    for t, k in enumerate(kept):
+        xf[:, pos[tuple(k)]] = xi[:, t]
+    g_t = kle.log_field(dim, n, 0.2, 1.3, m, xi, K)
+    g_f = kle.log_field(dim, n, 0.2, 1.3, m, xf)
+    assert np.max(np.abs(g_t - g_f)) <= 1e-13 * np.max(np.abs(g_f))
+    # kept modes in the full basis' flat order, sums within the bound
+    assert all(sum(k) <= K for k in kept)
+    flat = [pos[tuple(k)] for k in kept]
+    assert flat == sorted(flat)
+
+
+def test_truncated_pointwise_variance_is_kept_mercer_sum():
+    dim, m, K, n, lam, s2 = 2, 8, 5, 10, 0.15, 1.7
+    phi = kle.phi_matrix(dim, n, lam, s2, m, K)
+    omega, theta, even = kle.eigenpairs_1d(lam, m)
+    f = kle.eigfun_1d(omega, even, kle.centroids_1d(n))
+    var = np.zeros((n, n))
+    for kx, ky in kle.mode_indices(dim, m, K):
+        var += s2 * theta[kx] * theta[ky] * np.outer(f[:, ky] ** 2, f[:, kx] ** 2)
+    assert np.allclose((phi ** 2).sum(axis=1), var.reshape(-1), rtol=1e-12, atol=0)
