@@ -13,20 +13,27 @@
 //   8 corner neighbours   -h/12 * (the 1 shared kappa)
 // and no face coupling.
 //
-// Stencil kernels march along z: a CTA owns a 32 x 8 tile of node columns
-// and a chunk of zc planes. Each step stages one plane of the input vector
-// (34 x 10 with the halo) and one layer of kappa (33 x 9 elements) in shared
-// memory, double buffered, while the next plane is fetched into registers.
-// A plane p feeds three outputs of a column: p - 1 (the 8 couplings across
-// layer p - 1, after which output p - 1 is complete and goes to the
-// epilogue), p (the centre and its 4 in-plane diagonal edge neighbours) and
-// p + 1 (the 8 couplings across layer p). So a node costs one coalesced load
-// of the vector and of kappa, 13 shared-memory reads and one store, instead
-// of 27 + 8 cached global loads. Pointwise kernels run one thread per node
-// on 32 x 8 tiles of each plane. Node arrays carry the boundary nodes
-// (always 0). Partials: one per CTA (g.tiles_s per sample for the stencil
-// kernels, g.tiles_q for the QoI).
+// Stencil kernels march along z: a CTA owns a 32 x 16 tile of node columns
+// and a chunk of zc planes; a thread owns two rows of one column. Each step
+// stages one plane of the input field (with a one-node halo) and one layer
+// of kappa (with a one-element halo) in shared memory, double buffered,
+// while the next plane is fetched into registers. A plane p feeds three
+// outputs of a column: p - 1 (the 8 couplings across layer p - 1, after
+// which output p - 1 is complete and goes to the epilogue), p (the centre
+// and its 4 in-plane diagonal edge neighbours) and p + 1 (the 8 couplings
+// across layer p). So a node costs about one coalesced load of the field and
+// of kappa, a few shared-memory reads and one store, instead of 27 + 8
+// cached global loads. The field a stencil acts on is formed by a loader
+// while its plane is staged (z + beta p for A p, omega D^-1 b for the
+// multigrid residual), so those need no pointwise pre-pass. In FP32 the two
+// rows of a thread are 8 apart and stored as pairs, so the stencil runs on
+// paired FP32 instructions. The remaining pointwise kernels run one thread
+// per node on 32 x 8 tiles of each plane. Node arrays carry the boundary
+// nodes (always 0). Partials: one per CTA (g.tiles_s per sample for the
+// stencil kernels, g.tiles_q for the QoI).
 #include "mlmc_internal.cuh"
+
+#include <type_traits>
 
 namespace mlmc {
 namespace {
@@ -166,9 +173,8 @@ __device__ __forceinline__ ZTile ztile(const Grid& g) {
 // [0, 32 ceil(n/32)) x [0, 16 ceil(n/16)); when n is a multiple of the tile
 // width, the column n (boundary) is written by the thread of column n - 1
 // (epi.zero). Offsets inside one sample fit 32 bits ((n + 1)^3 < 2^31).
-template <class T, class Epi>
-__global__ void __launch_bounds__(ZTHREADS) k_zm3(Grid g, const T* __restrict__ Kap,
-                                                  const T* __restrict__ X,
+template <class T, class Ld, class Epi>
+__global__ void __launch_bounds__(ZTHREADS, 2) k_zm3(Grid g, const T* __restrict__ Kap, Ld ld,
                                                   const int32_t* __restrict__ active, Epi epi,
                                                   double* __restrict__ part, Prof prof) {
   const int64_t b = blockIdx.y;
@@ -178,8 +184,8 @@ __global__ void __launch_bounds__(ZTHREADS) k_zm3(Grid g, const T* __restrict__ 
   const ZTile t = ztile(g);
   const int n = g.n, N1 = n + 1, P = N1 * N1, KP = n * n;
   const int tid = threadIdx.y * ZTX + threadIdx.x;
-  const T* __restrict__ x = X + b * g.ns;
   const T* __restrict__ kp = Kap + b * g.es;
+  ld.bind(b);
   epi.bind(b);
   // staging slots: plane entries tid + q * ZTHREADS, with their in-plane
   // offsets and whether they lie inside (interior nodes for x, whose
@@ -203,7 +209,7 @@ __global__ void __launch_bounds__(ZTHREADS) k_zm3(Grid g, const T* __restrict__ 
     const bool pv = pp >= 1 && pp < n, pk = pp >= 0 && pp < n;
 #pragma unroll
     for (int q = 0; q < ZSLOTS; ++q) {
-      rv[q] = (pv && vok[q]) ? __ldg(x + pp * P + vo[q]) : T(0);
+      rv[q] = (pv && vok[q]) ? ld(pp * P + vo[q]) : T(0);
       rk[q] = (pk && kok[q]) ? __ldg(kp + pp * KP + ko[q]) : T(0);
     }
   };
@@ -286,6 +292,47 @@ __global__ void __launch_bounds__(ZTHREADS) k_zm3(Grid g, const T* __restrict__ 
   prof_tick3(prof);
 }
 
+// Loaders: the value the stencil acts on at an interior node, formed while
+// the plane is staged (bind(sample) offsets the arrays to the sample), so a
+// pointwise pre-pass is not needed.
+template <class T>
+struct LdX {   // x
+  const T* x;
+  int64_t ns;
+  __device__ void bind(int64_t b) { x += b * ns; }
+  __device__ T operator()(int o) const { return __ldg(x + o); }
+};
+
+template <class T>
+struct LdPupd {   // the new CG direction z + beta p (beta == 0: z)
+  const T* z;
+  const T* pold;
+  const double* beta;
+  int64_t ns;
+  T bb;
+  __device__ void bind(int64_t b) {
+    z += b * ns;
+    pold += b * ns;
+    bb = (T)beta[b];
+  }
+  __device__ T operator()(int o) const {
+    const T zv = __ldg(z + o);
+    return bb == T(0) ? zv : fma(bb, __ldg(pold + o), zv);
+  }
+};
+
+template <class T>
+struct LdWb {   // the pre-smoothed iterate from zero: omega D^-1 b
+  const T* W;
+  const T* Bv;
+  int64_t ns;
+  __device__ void bind(int64_t b) {
+    W += b * ns;
+    Bv += b * ns;
+  }
+  __device__ T operator()(int o) const { return __ldg(W + o) * __ldg(Bv + o); }
+};
+
 // Epilogues: bind(sample) offsets their arrays to the sample; load(node)
 // fetches the node's own inputs (Pre) one plane ahead; then (node offset,
 // interior?, (A x) at the node, x at the node, Pre) -> contribution to the
@@ -307,18 +354,26 @@ struct EpiApply {   // y = A x
 };
 
 template <class T>
-struct EpiAq {   // q = A p, partial of p.q
+struct EpiAq {   // q = A p, partial of p.q; p itself stored (Pn) when formed by the loader
   using Pre = NoPre;
   T* Q;
+  T* Pn;
   int64_t ns;
-  __device__ void bind(int64_t b) { Q += b * ns; }
+  __device__ void bind(int64_t b) {
+    Q += b * ns;
+    if (Pn) Pn += b * ns;
+  }
   __device__ Pre load(int) const { return Pre{}; }
   __device__ T operator()(int o, bool in, T ax, T xc, const Pre&) const {
     const T qv = in ? ax : T(0);
     Q[o] = qv;
+    if (Pn) Pn[o] = in ? xc : T(0);
     return xc * qv;
   }
-  __device__ void zero(int o) const { Q[o] = T(0); }
+  __device__ void zero(int o) const {
+    Q[o] = T(0);
+    if (Pn) Pn[o] = T(0);
+  }
 };
 
 template <class T>
@@ -327,21 +382,27 @@ struct PreB {
 };
 
 template <class T>
-struct EpiMgRes {   // residual of the pre-smoothed iterate: b - A e
+struct EpiMgRes {   // residual of the pre-smoothed iterate: b - A e; e stored (E) when formed by the loader
   using Pre = PreB<T>;
   const T* Bv;
   T* R1;
+  T* E;
   int64_t ns;
   __device__ void bind(int64_t b) {
     Bv += b * ns;
     R1 += b * ns;
+    if (E) E += b * ns;
   }
   __device__ Pre load(int o) const { return Pre{__ldg(Bv + o)}; }
-  __device__ T operator()(int o, bool in, T ax, T, const Pre& pr) const {
+  __device__ T operator()(int o, bool in, T ax, T xc, const Pre& pr) const {
     R1[o] = in ? pr.b - ax : T(0);
+    if (E) E[o] = in ? xc : T(0);
     return T(0);
   }
-  __device__ void zero(int o) const { R1[o] = T(0); }
+  __device__ void zero(int o) const {
+    R1[o] = T(0);
+    if (E) E[o] = T(0);
+  }
 };
 
 template <class T>
@@ -385,7 +446,279 @@ struct EpiResid {   // outer FP64 residual h^3 - A u, partial of its square
   __device__ void zero(int o) const { R[o] = 0.0; }
 };
 
+// ------------------------------------------------ FP32 z-march, packed pairs
+//
+// The FP32 form of k_zm3 on Blackwell's paired FP32 instructions (FFMA2 and
+// friends, __ffma2_rn / __fadd2_rn / __fmul2_rn): a thread owns rows j and
+// j + 8 of one column of the 32 x 16 tile, and shared memory holds each
+// staged plane as pairs (value at row r, value at row r + 8), so one 64-bit
+// shared load brings the same neighbour of both outputs and every stencil
+// operation serves both. Same tile, chunks, boundary rule and epilogues as
+// k_zm3.
+constexpr int ZPY = ZTY / 2 + 2, ZNVP = ZSX * ZPY;   // 34 x 10 pairs
+constexpr int ZKPY = ZTY / 2 + 1, ZNKP = ZKX * ZKPY; // 33 x 9 pairs
+static_assert(ZNVP <= 2 * ZTHREADS && ZNKP <= 2 * ZTHREADS, "two paired staging slots per thread");
+
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// across3 on pairs: K[b][a] kappa of the layer, v[dy + 1][dx + 1] the plane.
+__device__ __forceinline__ float2 across3p(const float2 K[2][2], const float2 v[3][3]) {
+  float2 e = mul2(add2(K[0][0], K[1][0]), v[1][0]);
+  e = fma2(add2(K[0][1], K[1][1]), v[1][2], e);
+  e = fma2(add2(K[0][0], K[0][1]), v[0][1], e);
+  e = fma2(add2(K[1][0], K[1][1]), v[2][1], e);
+  e = fma2(K[0][0], v[0][0], e);
+  e = fma2(K[0][1], v[0][2], e);
+  e = fma2(K[1][0], v[2][0], e);
+  return fma2(K[1][1], v[2][2], e);
+}
+
+// inplane3 on pairs: h/3 S v_c - h/12 E.
+__device__ __forceinline__ float2 inplane3p(const float2 Kb[2][2], const float2 Ka[2][2],
+                                            const float2 v[3][3], float2 c3, float2 mc12) {
+  const float2 s = add2(add2(add2(Kb[0][0], Kb[0][1]), add2(Kb[1][0], Kb[1][1])),
+                        add2(add2(Ka[0][0], Ka[0][1]), add2(Ka[1][0], Ka[1][1])));
+  float2 e = mul2(add2(Kb[0][0], Ka[0][0]), v[0][0]);
+  e = fma2(add2(Kb[0][1], Ka[0][1]), v[0][2], e);
+  e = fma2(add2(Kb[1][0], Ka[1][0]), v[2][0], e);
+  e = fma2(add2(Kb[1][1], Ka[1][1]), v[2][2], e);
+  return fma2(mc12, e, mul2(mul2(c3, s), v[1][1]));
+}
+
+// Asynchronous 4-byte global -> shared copy (zero-filled when src_bytes = 0).
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem, int src_bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+constexpr int ZSTAGES = 4;   // planes in flight: the current one and ZSTAGES - 1 ahead
+
+// Paired FP32 loaders for k_zm3f: kArrays node arrays are staged per plane
+// and combined pairwise into the field once the plane has arrived.
+struct LdXf {   // x
+  static constexpr int kArrays = 1;
+  const float* a0;
+  int64_t ns;
+  __device__ void bind(int64_t b) { a0 += b * ns; }
+  __device__ const float* src(int) const { return a0; }
+  __device__ float2 combine(float2 x, float2) const { return x; }
+};
+
+struct LdPupdf {   // z + beta p (beta == 0: z)
+  static constexpr int kArrays = 2;
+  const float* z;
+  const float* pold;
+  const double* beta;
+  int64_t ns;
+  float bb;
+  __device__ void bind(int64_t b) {
+    z += b * ns;
+    pold += b * ns;
+    bb = (float)beta[b];
+  }
+  __device__ const float* src(int k) const { return k ? pold : z; }
+  __device__ float2 combine(float2 zv, float2 pv) const {
+    return bb == 0.0f ? zv : fma2(make_float2(bb, bb), pv, zv);
+  }
+};
+
+struct LdWbf {   // omega D^-1 b
+  static constexpr int kArrays = 2;
+  const float* W;
+  const float* Bv;
+  int64_t ns;
+  __device__ void bind(int64_t b) {
+    W += b * ns;
+    Bv += b * ns;
+  }
+  __device__ const float* src(int k) const { return k ? Bv : W; }
+  __device__ float2 combine(float2 w, float2 bv) const { return mul2(w, bv); }
+};
+
+template <class Ld>
+struct LdPaired;
+template <>
+struct LdPaired<LdX<float>> {
+  using type = LdXf;
+  static LdXf make(const LdX<float>& l) { return LdXf{l.x, l.ns}; }
+};
+template <>
+struct LdPaired<LdPupd<float>> {
+  using type = LdPupdf;
+  static LdPupdf make(const LdPupd<float>& l) { return LdPupdf{l.z, l.pold, l.beta, l.ns, 0.0f}; }
+};
+template <>
+struct LdPaired<LdWb<float>> {
+  using type = LdWbf;
+  static LdWbf make(const LdWb<float>& l) { return LdWbf{l.W, l.Bv, l.ns}; }
+};
+
+template <class Ld, class Epi>
+__global__ void __launch_bounds__(ZTHREADS, 3) k_zm3f(Grid g, const float* __restrict__ Kap, Ld ld,
+                                                      const int32_t* __restrict__ active, Epi epi,
+                                                      double* __restrict__ part, Prof prof) {
+  constexpr int NA = Ld::kArrays;
+  const int64_t b = blockIdx.y;
+  if (active && !active[b]) return;
+  __shared__ __align__(16) float2 sv[ZSTAGES][NA][ZNVP];
+  __shared__ __align__(16) float2 sk[ZSTAGES][ZNKP];
+  const ZTile t = ztile(g);
+  const int n = g.n, N1 = n + 1, P = N1 * N1, KP = n * n;
+  const int tid = threadIdx.y * ZTX + threadIdx.x;
+  const float* __restrict__ kp = Kap + b * g.es;
+  ld.bind(b);
+  epi.bind(b);
+  // copy slots: pair entries tid and tid + 256; entry (xx, yy) holds rows
+  // r = ty0 - 1 + yy and r + 8 of column tx0 - 1 + xx
+  int vo[2][2], ko[2][2];
+  bool vok[2][2], kok[2][2], vin[2], kin[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int e = tid + q * ZTHREADS;
+    vin[q] = e < ZNVP;
+    kin[q] = e < ZNKP;
+    const int vx = t.tx0 - 1 + e % ZSX, vy = t.ty0 - 1 + e / ZSX;
+    const int kx = t.tx0 - 1 + e % ZKX, ky = t.ty0 - 1 + e / ZKX;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int ry = vy + 8 * h, rk = ky + 8 * h;
+      vok[q][h] = vin[q] && vx >= 1 && vx < n && ry >= 1 && ry < n;
+      vo[q][h] = vok[q][h] ? ry * N1 + vx : 0;
+      kok[q][h] = kin[q] && kx >= 0 && kx < n && rk >= 0 && rk < n;
+      ko[q][h] = kok[q][h] ? rk * n + kx : 0;
+    }
+  }
+  // stage plane pp into ring slot st (one commit group per plane; empty
+  // groups past the chunk keep the group count uniform)
+  auto issue = [&](int pp, int st) {
+    if (pp <= t.z1) {
+      const bool pv = pp >= 1 && pp < n, pk = pp >= 0 && pp < n;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int e = tid + q * ZTHREADS;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (vin[q]) {
+#pragma unroll
+            for (int a = 0; a < NA; ++a) {
+              const float* src = ld.src(a);
+              const bool ok = pv && vok[q][h];
+              cp_async4(reinterpret_cast<float*>(&sv[st][a][e]) + h, ok ? src + pp * P + vo[q][h] : src,
+                        ok ? 4 : 0);
+            }
+          }
+          if (kin[q]) {
+            const bool ok = pk && kok[q][h];
+            cp_async4(reinterpret_cast<float*>(&sk[st][e]) + h, ok ? kp + pp * KP + ko[q][h] : kp,
+                      ok ? 4 : 0);
+          }
+        }
+      }
+    }
+    cp_async_commit();
+  };
+  int p = t.z0 - 1;
+#pragma unroll
+  for (int j = 0; j < ZSTAGES - 1; ++j) issue(p + j, j);
+
+  const int i = t.tx0 + threadIdx.x;
+  const int jr[2] = {t.ty0 + (int)threadIdx.y, t.ty0 + (int)threadIdx.y + 8};
+  bool cvalid[2], cint[2], ey[2];
+  int ocol[2];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    cvalid[r] = i <= n && jr[r] <= n;
+    cint[r] = i >= 1 && i < n && jr[r] >= 1 && jr[r] < n;
+    ey[r] = jr[r] == n - 1 && n % ZTY == 0;
+    ocol[r] = jr[r] * N1 + i;
+  }
+  const bool ex = i == n - 1 && n % ZTX == 0;
+  const float c3s = (float)(g.h / 3.0), c12s = (float)(g.h / 12.0);
+  const float2 c3 = make_float2(c3s, c3s), mc12 = make_float2(-c12s, -c12s);
+  float2 a0 = make_float2(0.f, 0.f), a1 = a0, vc = a0;
+  float2 kb[2][2] = {{a0, a0}, {a0, a0}};
+  typename Epi::Pre pre[2];
+  float dot = 0.0f;
+  const int vbase = (threadIdx.y + 1) * ZSX + threadIdx.x + 1;
+  const int kbase = threadIdx.y * ZKX + threadIdx.x;
+  int st = 0;
+  for (; p <= t.z1; ++p) {
+    cp_async_wait<ZSTAGES - 2>();   // this thread's copies of plane p have landed
+    if (NA > 1) {                   // combine this thread's entries into the field
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+        if (vin[q]) {
+          const int e = tid + q * ZTHREADS;
+          sv[st][0][e] = ld.combine(sv[st][0][e], sv[st][NA - 1][e]);
+        }
+    }
+    __syncthreads();                // plane p complete; slot of plane p - 1 free
+    issue(p + ZSTAGES - 1, (st + ZSTAGES - 1) % ZSTAGES);
+    typename Epi::Pre nxt[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+      if (cint[r] && p >= t.z0 && p < t.z1 && p >= 1 && p < n) nxt[r] = epi.load(p * P + ocol[r]);
+    const float2* svb = sv[st][0];
+    const float2* skb = sk[st];
+    float2 v[3][3], ka[2][2];
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 3; ++dx) v[dy][dx] = svb[vbase + (dy - 1) * ZSX + (dx - 1)];
+#pragma unroll
+    for (int bq = 0; bq < 2; ++bq)
+#pragma unroll
+      for (int a = 0; a < 2; ++a) ka[bq][a] = skb[kbase + bq * ZKX + a];
+    // outputs of plane p - 1 are complete
+    const float2 done = fma2(mc12, across3p(kb, v), a0);
+    const int m = p - 1;
+    if (m >= t.z0) {
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        if (!cvalid[r]) continue;
+        const int o = m * P + ocol[r];
+        dot += epi(o, cint[r] && m >= 1 && m < n, r ? done.y : done.x, r ? vc.y : vc.x, pre[r]);
+        if (ex) epi.zero(o + 1);
+        if (ey[r]) epi.zero(o + N1);
+        if (ex && ey[r]) epi.zero(o + N1 + 1);
+      }
+    }
+    a0 = add2(a1, inplane3p(kb, ka, v, c3, mc12));
+    a1 = mul2(mc12, across3p(ka, v));
+#pragma unroll
+    for (int bq = 0; bq < 2; ++bq)
+#pragma unroll
+      for (int a = 0; a < 2; ++a) kb[bq][a] = ka[bq][a];
+    vc = v[1][1];
+    pre[0] = nxt[0];
+    pre[1] = nxt[1];
+    st = (st + 1) % ZSTAGES;
+  }
+  cp_async_wait<0>();
+  if (part) cta_partial3((double)dot, part, g.tiles_s);
+  prof_tick3(prof);
+}
+
 inline dim3 gridz(const Grid& g, int64_t B) { return dim3((unsigned)g.zx, (unsigned)B, 1); }
+
+// The z-march launch of an epilogue: the paired FP32 kernel for float.
+template <class T, class Ld, class Epi>
+inline void launch_zm3(cudaStream_t s, const Grid& g, int64_t B, const T* kappa, const Ld& ld,
+                       const int32_t* active, const Epi& epi, double* part, Prof p) {
+  if constexpr (std::is_same<T, float>::value) {
+    using LP = LdPaired<Ld>;
+    k_zm3f<typename LP::type, Epi><<<gridz(g, B), dim3(ZTX, ZTY / ZRY, 1), 0, s>>>(
+        g, kappa, LP::make(ld), active, epi, part, p);
+  }
+  else
+    k_zm3<T, Ld, Epi><<<gridz(g, B), dim3(ZTX, ZTY / ZRY, 1), 0, s>>>(g, kappa, ld, active, epi, part, p);
+}
 
 
 template <class T>
@@ -411,33 +744,6 @@ __global__ void __launch_bounds__(256) k_init3(Grid g, T* __restrict__ X, T* __r
   X[b * g.ns + q.idx] = T(0);
   if (R) R[b * g.ns + q.idx] = q.interior ? T(g.h * g.h * g.h) : T(0);
   prof_tick3(prof);
-}
-
-// Pointwise: p_new = z + beta p_old (beta == 0: p_new = z; p_old unread).
-template <class T>
-__global__ void __launch_bounds__(256) k_pupd3(Grid g, const T* __restrict__ Z, const T* __restrict__ Pold,
-                                               T* __restrict__ Pnew, const double* __restrict__ beta,
-                                               const int32_t* __restrict__ active) {
-  const int64_t b = blockIdx.y;
-  if (!active[b]) return;
-  const Node3 q = node3(g.n);
-  if (!q.valid) return;
-  const T bb = (T)beta[b];
-  const int64_t o = b * g.ns + q.idx;
-  const T zv = Z[o];
-  Pnew[o] = (bb == T(0)) ? zv : fma(bb, Pold[o], zv);
-}
-
-// Pointwise: out = W b (the pre-smoothing step from zero).
-template <class T>
-__global__ void __launch_bounds__(256) k_wb3(Grid g, const T* __restrict__ W, const T* __restrict__ Bv,
-                                             T* __restrict__ E, const int32_t* __restrict__ active) {
-  const int64_t b = blockIdx.y;
-  if (!active[b]) return;
-  const Node3 q = node3(g.n);
-  if (!q.valid) return;
-  const int64_t o = b * g.ns + q.idx;
-  E[o] = W[o] * Bv[o];
 }
 
 // Full weighting: bc(I) = sum_{d in {-1,0,1}^3} w(dx) w(dy) w(dz) r1(2I + d).
@@ -541,8 +847,7 @@ namespace d3 {
 
 template <class T>
 cudaError_t apply(cudaStream_t s, const Grid& g, const T* kappa, const T* x, T* y, int64_t B, Prof p) {
-  k_zm3<T, EpiApply<T>><<<gridz(g, B), block3(), 0, s>>>(g, kappa, x, nullptr, EpiApply<T>{y, g.ns},
-                                                        nullptr, p);
+  launch_zm3<T>(s, g, B, kappa, LdX<T>{x, g.ns}, nullptr, EpiApply<T>{y, g.ns}, nullptr, p);
   return cudaGetLastError();
 }
 template <class T>
@@ -558,17 +863,14 @@ cudaError_t pcg_init(cudaStream_t s, const Grid& g, T* x, T* r, int64_t B, Prof 
 template <class T>
 cudaError_t pcg_pq(cudaStream_t s, const Grid& g, const T* kappa, const T* z, const T* p_old, T* p_new,
                    T* q, const Scalars& sc, double* part, int64_t B, Prof p) {
-  k_pupd3<T><<<grid3(g, B), block3(), 0, s>>>(g, z, p_old, p_new, sc.beta, sc.active);
-  k_zm3<T, EpiAq<T>><<<gridz(g, B), block3(), 0, s>>>(g, kappa, p_new, sc.active, EpiAq<T>{q, g.ns},
-                                                     part, p);
+  launch_zm3<T>(s, g, B, kappa, LdPupd<T>{z, p_old, sc.beta, g.ns, T(0)}, sc.active,
+                EpiAq<T>{q, p_new, g.ns}, part, p);
   return cudaGetLastError();
 }
 template <class T>
 cudaError_t mg_pre(cudaStream_t s, const Grid& g, const T* kappa, const T* w, const T* b, T* e, T* r1,
                    const int32_t* active, int64_t B, Prof p) {
-  k_wb3<T><<<grid3(g, B), block3(), 0, s>>>(g, w, b, e, active);
-  k_zm3<T, EpiMgRes<T>><<<gridz(g, B), block3(), 0, s>>>(g, kappa, e, active,
-                                                        EpiMgRes<T>{b, r1, g.ns}, nullptr, p);
+  launch_zm3<T>(s, g, B, kappa, LdWb<T>{w, b, g.ns}, active, EpiMgRes<T>{b, r1, e, g.ns}, nullptr, p);
   return cudaGetLastError();
 }
 template <class T>
@@ -588,8 +890,7 @@ cudaError_t mg_post(cudaStream_t s, const Grid& g, const Grid& coarse, const T* 
                     const T* b, const T* e, const T* ec, T* out, T* tmp, const int32_t* active,
                     double* part, int64_t B, Prof p) {
   k_prolong3<T><<<grid3(g, B), block3(), 0, s>>>(g, coarse.ns, e, ec, tmp, active);
-  k_zm3<T, EpiMgPost<T>><<<gridz(g, B), block3(), 0, s>>>(g, kappa, tmp, active,
-                                                         EpiMgPost<T>{w, b, out, g.ns}, part, p);
+  launch_zm3<T>(s, g, B, kappa, LdX<T>{tmp, g.ns}, active, EpiMgPost<T>{w, b, out, g.ns}, part, p);
   return cudaGetLastError();
 }
 template <class T>
@@ -600,8 +901,8 @@ cudaError_t qoi(cudaStream_t s, const Grid& g, int box, int L, int H, double inv
 }
 cudaError_t resid64(cudaStream_t s, const Grid& g, const double* kappa, const double* u, double* r,
                     const int32_t* active, double* part, int64_t B, Prof p) {
-  k_zm3<double, EpiResid><<<gridz(g, B), block3(), 0, s>>>(g, kappa, u, active,
-                                                          EpiResid{r, g.ns, g.h * g.h * g.h}, part, p);
+  launch_zm3<double>(s, g, B, kappa, LdX<double>{u, g.ns}, active, EpiResid{r, g.ns, g.h * g.h * g.h},
+                     part, p);
   return cudaGetLastError();
 }
 
