@@ -238,6 +238,30 @@ mlmc_status mlmc_round_end(mlmc_plan plan);
  * and the cost model: N_out (host, n_levels entries). */
 mlmc_status mlmc_allocation(mlmc_plan plan, double eps, int64_t* N_out);
 
+/* ---- autotuning ------------------------------------------------------ */
+
+enum { MLMC_TUNE_INNER_RTOL = 1, MLMC_TUNE_MG_OMEGA = 2, MLMC_TUNE_Z_CHUNK = 4 };
+
+typedef struct mlmc_tune_report {
+  int32_t candidates;   /* settings timed */
+  int32_t z_chunk;      /* chosen z-planes per 3D stencil CTA (0 = built-in rule) */
+  double inner_rtol;    /* chosen inner tolerance (mixed form) */
+  double mg_omega;      /* chosen Jacobi damping of the multigrid smoother */
+  double best_ms;       /* time of one coupled batch with the chosen setting */
+  double worst_ms;      /* slowest setting */
+} mlmc_tune_report;
+
+/* Time `count` (1..4096) coupled samples of `level` under every setting of
+ * the selected knobs (flags: MLMC_TUNE_*; mixed-form inner tolerance
+ * 1e-2..3e-4, multigrid damping 0.7..0.9, 3D z-planes per stencil CTA) and
+ * keep the fastest in the plan (cached graphs are rebuilt; a setting whose
+ * solves hit the iteration cap is never chosen). Probe samples use indices
+ * just below 2^32; the level states are restored. Solves then stop at the
+ * same rtol but their iterates, hence results in the last digits, depend on
+ * the chosen setting, and the choice on the measured times. NOT_CONVERGED if
+ * no setting converged. */
+mlmc_status mlmc_autotune(mlmc_plan plan, int level, int64_t count, int flags, mlmc_tune_report* out);
+
 /* ---- device-level steps (device pointers, asynchronous on the plan's stream) */
 
 /* xi[s * M + k] = xi_k(level, first + s), s < count (the plan's seed and

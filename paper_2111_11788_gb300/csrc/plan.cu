@@ -19,7 +19,7 @@
 
 namespace mlmc {
 
-Grid make_grid(int dim, int n) {
+Grid make_grid(int dim, int n, int zc_override) {
   Grid g{};
   g.dim = dim;
   g.n = n;
@@ -37,6 +37,7 @@ Grid make_grid(int dim, int n) {
     g.sx = ((n + 1 + 31) / 32) * ((n + 1 + 7) / 8) * (n + 1);
     g.sy = 1;
     g.zc = (n + 1 <= 24) ? n + 1 : 16;
+    if (zc_override > 0) g.zc = std::min(zc_override, n + 1);
     g.zx = ((n + 31) / 32) * ((n + 15) / 16) * ((n + 1 + g.zc - 1) / g.zc);
     g.tiles_s = g.zx;
   }
@@ -241,6 +242,7 @@ struct mlmc_plan_s {
   size_t ws_bytes = 0;
   size_t ws_budget = 0;
   bool ws_borrowed = false;       // ws belongs to the caller (mlmc_plan_set_workspace)
+  int zc_override = 0;            // 3D: z-planes per stencil CTA (0 = default), set by mlmc_autotune
   double* d_fold = nullptr;       // staging of mlmc_level_fold
   int64_t fold_cap = 0;
   void* h_pin = nullptr;
@@ -1781,6 +1783,98 @@ mlmc_status mlmc_run_adaptive(mlmc_plan p, double eps, int64_t pilot, int32_t L0
     for (int l = 0; l < L1; ++l) N_out[l] = have[l];
   if (L_out) *L_out = L;
   return bad ? MLMC_ERR_NOT_CONVERGED : MLMC_OK;
+}
+
+// Rebuilds the grids of every mesh (after a change of zc_override).
+void regrid(mlmc_plan p) {
+  for (auto& mi : p->meshes)
+    for (int k = 0; k < mi.K; ++k) mi.g[k] = make_grid(p->cfg.dim, mi.g[k].n, p->zc_override);
+}
+
+mlmc_status mlmc_autotune(mlmc_plan p, int level, int64_t count, int flags, mlmc_tune_report* out) {
+  if (!p || !out || level < 0 || level >= p->cfg.n_levels || count < 1 || count > 4096 ||
+      !p->round_count.empty())
+    return MLMC_ERR_INVALID;
+  const int L1 = p->cfg.n_levels;
+  std::vector<mlmc_level_state> saved(L1);
+  CK(cudaMemcpyAsync(saved.data(), p->d_states, sizeof(mlmc_level_state) * L1, cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  const bool mixed = is_mixed(p);
+  std::vector<double> rtols = {p->cfg.inner_rtol};
+  if (mixed && (flags & MLMC_TUNE_INNER_RTOL)) rtols = {1e-2, 3e-3, 1e-3, 3e-4};
+  std::vector<double> omegas = {p->cfg.mg_omega};
+  if (p->cfg.solver == MLMC_GMG_PCG && (flags & MLMC_TUNE_MG_OMEGA)) omegas = {0.7, 0.8, 0.9};
+  std::vector<int> zcs = {p->zc_override};
+  if (p->cfg.dim == 3 && (flags & MLMC_TUNE_Z_CHUNK)) zcs = {0, 24, 32, 64};
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return MLMC_ERR_CUDA;
+  }
+  const mlmc_config base = p->cfg;
+  const int zc0 = p->zc_override;
+  mlmc_tune_report r{};
+  r.best_ms = -1.0;
+  r.worst_ms = -1.0;
+  mlmc_status st = MLMC_OK;
+  // probe samples far from the indices a run uses; the level states are
+  // restored afterwards
+  const int64_t first = (int64_t(1) << 32) - count;
+  for (double rt : rtols) {
+    for (double om : omegas) {
+      for (int zc : zcs) {
+        if (st != MLMC_OK) break;
+        p->cfg.inner_rtol = rt;
+        p->cfg.mg_omega = om;
+        p->zc_override = zc;
+        if ((st = settle_graph_launches(p)) != MLMC_OK) break;
+        clear_graphs(p);
+        regrid(p);
+        // the first call builds and caches the solve graphs; the second is timed
+        st = mlmc_sample_level(p, level, first, count, nullptr, nullptr, nullptr);
+        if (st != MLMC_OK && st != MLMC_ERR_NOT_CONVERGED) break;
+        if (cudaEventRecord(e0, p->stream) != cudaSuccess) { st = MLMC_ERR_CUDA; break; }
+        const mlmc_status st2 = mlmc_sample_level(p, level, first, count, nullptr, nullptr, nullptr);
+        if (cudaEventRecord(e1, p->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+          st = MLMC_ERR_CUDA;
+          break;
+        }
+        st = MLMC_OK;
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ++r.candidates;
+        if (st2 == MLMC_ERR_NOT_CONVERGED) continue;   // a setting that fails is never chosen
+        if (st2 != MLMC_OK) { st = st2; break; }
+        if (r.best_ms < 0.0 || ms < r.best_ms) {
+          r.best_ms = ms;
+          r.inner_rtol = rt;
+          r.mg_omega = om;
+          r.z_chunk = zc;
+        }
+        if (ms > r.worst_ms) r.worst_ms = ms;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // apply the best setting (or restore the original one on failure)
+  p->cfg = base;
+  p->zc_override = zc0;
+  if (st == MLMC_OK && r.best_ms >= 0.0) {
+    p->cfg.inner_rtol = r.inner_rtol;
+    p->cfg.mg_omega = r.mg_omega;
+    p->zc_override = r.z_chunk;
+  }
+  settle_graph_launches(p);
+  clear_graphs(p);
+  regrid(p);
+  CK(cudaMemcpyAsync(p->d_states, saved.data(), sizeof(mlmc_level_state) * L1, cudaMemcpyHostToDevice, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  if (st != MLMC_OK) return st;
+  if (r.best_ms < 0.0) return MLMC_ERR_NOT_CONVERGED;
+  *out = r;
+  return MLMC_OK;
 }
 
 mlmc_status mlmc_profile_enable(mlmc_plan p, int mask) {

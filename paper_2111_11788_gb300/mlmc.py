@@ -88,6 +88,18 @@ class RequestResult(ctypes.Structure):
                 ("N", ctypes.c_int64 * 16)]
 
 
+class TuneReport(ctypes.Structure):
+    """Mirror of ``mlmc_tune_report``."""
+    _fields_ = [("candidates", ctypes.c_int32), ("z_chunk", ctypes.c_int32),
+                ("inner_rtol", ctypes.c_double), ("mg_omega", ctypes.c_double),
+                ("best_ms", ctypes.c_double), ("worst_ms", ctypes.c_double)]
+
+
+TUNE_INNER_RTOL = 1
+TUNE_MG_OMEGA = 2
+TUNE_Z_CHUNK = 4
+
+
 class SchedResult(ctypes.Structure):
     """Mirror of ``mlmc_sched_result``."""
     _fields_ = [("makespan", ctypes.c_double), ("work_total", ctypes.c_double),
@@ -139,6 +151,7 @@ SIGNATURES = [
     ("mlmc_plan_set_workspace", _I, [_P, _P, ctypes.c_uint64]),
     ("mlmc_run_adaptive", _I, [_P, _D, _I64, ctypes.c_int32, _DP, _DP, _I64P, _I32P]),
     ("mlmc_level_fold", _I, [_P, _I, _DP, _DP, _I64]),
+    ("mlmc_autotune", _I, [_P, _I, _I64, _I, ctypes.POINTER(TuneReport)]),
     # include/mlmc_sched.h
     ("mlmc_batch_size", _I64, [_I64, _I64, _I64, _D, _D]),
     ("mlmc_schedule_greedy", _I, [_I, _I64P, _I64P, _DP, _I64, _I, _D, _D, _D,
@@ -316,6 +329,14 @@ class Plan:
                             ctypes.byref(q), ctypes.byref(v), Nout.ctypes.data_as(_I64P))
         check(st, "mlmc_run")
         return q.value, v.value, Nout
+
+    def autotune(self, level, count, flags=7):
+        """mlmc_autotune: keep the fastest setting; returns the report as a dict."""
+        r = TuneReport()
+        check(lib().mlmc_autotune(self._h, int(level), int(count), int(flags), ctypes.byref(r)),
+              "mlmc_autotune")
+        return dict(candidates=r.candidates, z_chunk=r.z_chunk, inner_rtol=r.inner_rtol,
+                    mg_omega=r.mg_omega, best_ms=r.best_ms, worst_ms=r.worst_ms)
 
     def allocation(self, eps):
         """mlmc_allocation: N_l of Eq. (mlmc_num_samples) from the device level states."""
