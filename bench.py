@@ -55,6 +55,10 @@ def parse():
     ap.add_argument("--serve-pilot", type=int, default=32)
     ap.add_argument("--serve-adapt", type=int, default=2,
                     help="requests start on levels 0..K and adapt L (0: all levels, L fixed)")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="skip the autotuner (by default inner tolerance, MG damping and the 3D "
+                         "z-chunk are tuned on the finest level before the warm-up, outside the "
+                         "timed region)")
     ap.add_argument("--no-graphs", action="store_true",
                     help="host-driven solver loops (same kernels; ncu cannot profile kernels "
                          "inside graphs with conditional nodes)")
@@ -216,6 +220,7 @@ def measure_form(m, wl, cfg, stream, args, world, barrier, with_e2e):
     sh = stream.cuda_stream
     with torch.cuda.stream(stream):
         plan = m.Plan(cfg, sh)
+        tune = plan.autotune(wl["levels"] - 1, 16, 7) if args.autotune else None
         N = None
         def one_run():
             if wl.get("N") is not None:
@@ -277,7 +282,7 @@ def measure_form(m, wl, cfg, stream, args, world, barrier, with_e2e):
                 torch.cuda.synchronize()
                 wall.append(time.perf_counter() - t0)
         plan.close()
-    return dict(ms=ms, N=[int(x) for x in N], dofs_step=dofs_step, q=q, v=v, dom=dom,
+    return dict(ms=ms, N=[int(x) for x in N], dofs_step=dofs_step, q=q, v=v, dom=dom, tune=tune,
                 dstat=dstat, shares=shares, per_kernel=per_kernel, clocks=clk, launches=launches,
                 wall=wall)
 
@@ -438,6 +443,7 @@ def bench_ours(args):
                        "time_to_eps_s": oms / args.steps / 1e3,
                        "samples_per_level": res["N"], "q_hat": res["q"], "stat_var": res["v"],
                        "gpu_launches": int(res["launches"]), "clocks": res["clocks"],
+                       "autotune": res["tune"],
                        "roofline": roofline_of(res, peaks, fp64_alu=(form == "fp64"))}
     if rank == 0:
         names = {"fp64": "plain FP64", "mixed": "mixed: FP32 inner PCG + FP64 refinement"}
@@ -454,6 +460,7 @@ def bench_ours(args):
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "roofline": roofline_of(main, peaks, fp64_alu=(args.form == "fp64")),
                 "clocks": main["clocks"], "gpu_launches": int(main["launches"]),
+                "autotune": main["tune"],
                 "e2e": {"value": e2e_value, "unit": "coupled DOF-solves/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "other_forms": {names[k]: v for k, v in other.items()}}
