@@ -267,13 +267,18 @@ def measure_form(m, wl, cfg, stream, args, world, barrier, with_e2e):
         dstat = plan.kernel_stats()[dom]
         plan.profile(0)
         wall = []
+        # the tuned settings are configuration fields: a user's plan takes them directly
+        cfg2 = m.Config.from_buffer_copy(cfg)
+        if tune is not None:
+            cfg2.inner_rtol, cfg2.mg_omega, cfg2.z_chunk = (tune["inner_rtol"], tune["mg_omega"],
+                                                            tune["z_chunk"])
         if with_e2e:
             # end to end through the public API: plan creation (host KLE roots,
             # table upload), the run, results back to host, plan destruction
             for _ in range(args.steps):
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-                p2 = m.Plan(cfg, sh)
+                p2 = m.Plan(cfg2, sh)
                 if wl.get("N") is not None:
                     p2.run(N=list(wl["N"]))
                 else:

@@ -84,7 +84,8 @@ typedef struct mlmc_config {
                               total-order truncation (Sec. 5.2): only modes with
                               k_x + k_y (+ k_z) <= K (each k < m), M of them, in
                               the full basis' flat order */
-  int32_t reserved0;       /* 0 */
+  int32_t z_chunk;         /* 3D: z-planes per stencil CTA (0 = built-in rule:
+                              all planes up to 24, else 16); set by mlmc_autotune */
 } mlmc_config;
 
 /* Per-level Welford state (Eq. (sample_variance): V = m2 / n). */
@@ -134,7 +135,8 @@ mlmc_status mlmc_plan_create(const mlmc_config* cfg, void* stream, mlmc_plan* ou
 mlmc_status mlmc_plan_destroy(mlmc_plan plan);
 
 /* Re-target an idle plan to a configuration of the same shape (dim,
- * n_levels, coarse_cells, modes_per_dim, solver, precision, total_order): field
+ * n_levels, coarse_cells, modes_per_dim, solver, precision, total_order,
+ * z_chunk): field
  * parameters, seed, stream id, tolerances and QoI may change. Rebuilds the
  * KLE tables in place, drops cached graphs and resets the level states;
  * allocates nothing (no device synchronisation from cudaFree). A nonzero
@@ -254,7 +256,8 @@ typedef struct mlmc_tune_report {
 /* Time `count` (1..4096) coupled samples of `level` under every setting of
  * the selected knobs (flags: MLMC_TUNE_*; mixed-form inner tolerance
  * 1e-2..3e-4, multigrid damping 0.7..0.9, 3D z-planes per stencil CTA) and
- * keep the fastest in the plan (cached graphs are rebuilt; a setting whose
+ * keep the fastest in the plan's configuration (inner_rtol, mg_omega,
+ * z_chunk; cached graphs are rebuilt; a setting whose
  * solves hit the iteration cap is never chosen). Probe samples use indices
  * just below 2^32; the level states are restored. Solves then stop at the
  * same rtol but their iterates, hence results in the last digits, depend on

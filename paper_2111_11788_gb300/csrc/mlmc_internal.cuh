@@ -87,7 +87,7 @@ struct Grid {
   }
 };
 
-Grid make_grid(int dim, int n, int zc_override = 0);
+Grid make_grid(int dim, int n, int z_chunk = 0);
 
 // Per-sample scalars of the batched PCG (struct of arrays, B entries each).
 struct Scalars {

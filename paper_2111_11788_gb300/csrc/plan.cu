@@ -19,7 +19,7 @@
 
 namespace mlmc {
 
-Grid make_grid(int dim, int n, int zc_override) {
+Grid make_grid(int dim, int n, int z_chunk) {
   Grid g{};
   g.dim = dim;
   g.n = n;
@@ -37,7 +37,7 @@ Grid make_grid(int dim, int n, int zc_override) {
     g.sx = ((n + 1 + 31) / 32) * ((n + 1 + 7) / 8) * (n + 1);
     g.sy = 1;
     g.zc = (n + 1 <= 24) ? n + 1 : 16;
-    if (zc_override > 0) g.zc = std::min(zc_override, n + 1);
+    if (z_chunk > 0) g.zc = std::min(z_chunk, n + 1);
     g.zx = ((n + 31) / 32) * ((n + 15) / 16) * ((n + 1 + g.zc - 1) / g.zc);
     g.tiles_s = g.zx;
   }
@@ -242,7 +242,6 @@ struct mlmc_plan_s {
   size_t ws_bytes = 0;
   size_t ws_budget = 0;
   bool ws_borrowed = false;       // ws belongs to the caller (mlmc_plan_set_workspace)
-  int zc_override = 0;            // 3D: z-planes per stencil CTA (0 = default), set by mlmc_autotune
   double* d_fold = nullptr;       // staging of mlmc_level_fold
   int64_t fold_cap = 0;
   void* h_pin = nullptr;
@@ -308,7 +307,7 @@ std::vector<int32_t> coef_slots(const mlmc_config* c) {
 }
 
 mlmc_status validate(const mlmc_config* c) {
-  if (c && c->total_order < -1) return MLMC_ERR_INVALID;
+  if (c && (c->total_order < -1 || c->z_chunk < 0)) return MLMC_ERR_INVALID;
   if (!c) return MLMC_ERR_INVALID;
   if (c->dim != 2 && c->dim != 3) return MLMC_ERR_INVALID;
   if (c->n_levels < 1 || c->n_levels > 16) return MLMC_ERR_INVALID;
@@ -1228,7 +1227,7 @@ void mlmc_config_default(mlmc_config* c) {
   c->outer_max_iter = 16;
   c->use_graphs = 1;
   c->total_order = -1;
-  c->reserved0 = 0;
+  c->z_chunk = 0;
 }
 
 int64_t mlmc_node_stride(int dim, int n) {
@@ -1324,12 +1323,12 @@ mlmc_status mlmc_plan_create(const mlmc_config* cfg, void* stream, mlmc_plan* ou
     MeshInfo& mi = p->meshes[l];
     mi.n = cfg->coarse_cells << l;
     mi.K = 1;
-    mi.g[0] = make_grid(cfg->dim, mi.n);
+    mi.g[0] = make_grid(cfg->dim, mi.n, cfg->z_chunk);
     if (cfg->solver == MLMC_GMG_PCG && mi.n > 2) {
       int n = mi.n;
       while (n > 2 && mi.K < MAX_MG) {
         n /= 2;
-        mi.g[mi.K++] = make_grid(cfg->dim, n);
+        mi.g[mi.K++] = make_grid(cfg->dim, n, cfg->z_chunk);
       }
     }
     if (cudaMalloc(&mi.table, sizeof(double) * (size_t)mi.n * m) != cudaSuccess) {
@@ -1377,7 +1376,8 @@ mlmc_status mlmc_plan_retarget(mlmc_plan p, const mlmc_config* cfg) {
   const mlmc_config& o = p->cfg;
   if (cfg->dim != o.dim || cfg->n_levels != o.n_levels || cfg->coarse_cells != o.coarse_cells ||
       cfg->modes_per_dim != o.modes_per_dim || cfg->solver != o.solver ||
-      cfg->precision != o.precision || cfg->total_order != o.total_order)
+      cfg->precision != o.precision || cfg->total_order != o.total_order ||
+      cfg->z_chunk != o.z_chunk)
     return MLMC_ERR_INVALID;
   if (!p->round_count.empty()) return MLMC_ERR_INVALID;
   CK(cudaStreamSynchronize(p->stream));
@@ -1428,12 +1428,12 @@ int64_t mlmc_round_bytes(const mlmc_config* cfg, const int64_t* count) {
     MeshInfo mi;
     mi.n = cfg->coarse_cells << l;
     mi.K = 1;
-    mi.g[0] = make_grid(cfg->dim, mi.n);
+    mi.g[0] = make_grid(cfg->dim, mi.n, cfg->z_chunk);
     if (cfg->solver == MLMC_GMG_PCG && mi.n > 2) {
       int n = mi.n;
       while (n > 2 && mi.K < MAX_MG) {
         n /= 2;
-        mi.g[mi.K++] = make_grid(cfg->dim, n);
+        mi.g[mi.K++] = make_grid(cfg->dim, n, cfg->z_chunk);
       }
     }
     total += round_up((int64_t)coupled_bytes(mi, M, count[l], cfg->precision == MLMC_MIXED), 256);
@@ -1785,10 +1785,10 @@ mlmc_status mlmc_run_adaptive(mlmc_plan p, double eps, int64_t pilot, int32_t L0
   return bad ? MLMC_ERR_NOT_CONVERGED : MLMC_OK;
 }
 
-// Rebuilds the grids of every mesh (after a change of zc_override).
+// Rebuilds the grids of every mesh (after a change of cfg.z_chunk).
 void regrid(mlmc_plan p) {
   for (auto& mi : p->meshes)
-    for (int k = 0; k < mi.K; ++k) mi.g[k] = make_grid(p->cfg.dim, mi.g[k].n, p->zc_override);
+    for (int k = 0; k < mi.K; ++k) mi.g[k] = make_grid(p->cfg.dim, mi.g[k].n, p->cfg.z_chunk);
 }
 
 mlmc_status mlmc_autotune(mlmc_plan p, int level, int64_t count, int flags, mlmc_tune_report* out) {
@@ -1804,7 +1804,7 @@ mlmc_status mlmc_autotune(mlmc_plan p, int level, int64_t count, int flags, mlmc
   if (mixed && (flags & MLMC_TUNE_INNER_RTOL)) rtols = {1e-2, 3e-3, 1e-3, 3e-4};
   std::vector<double> omegas = {p->cfg.mg_omega};
   if (p->cfg.solver == MLMC_GMG_PCG && (flags & MLMC_TUNE_MG_OMEGA)) omegas = {0.7, 0.8, 0.9};
-  std::vector<int> zcs = {p->zc_override};
+  std::vector<int> zcs = {p->cfg.z_chunk};
   if (p->cfg.dim == 3 && (flags & MLMC_TUNE_Z_CHUNK)) zcs = {0, 24, 32, 64};
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
@@ -1813,7 +1813,6 @@ mlmc_status mlmc_autotune(mlmc_plan p, int level, int64_t count, int flags, mlmc
     return MLMC_ERR_CUDA;
   }
   const mlmc_config base = p->cfg;
-  const int zc0 = p->zc_override;
   mlmc_tune_report r{};
   r.best_ms = -1.0;
   r.worst_ms = -1.0;
@@ -1827,7 +1826,7 @@ mlmc_status mlmc_autotune(mlmc_plan p, int level, int64_t count, int flags, mlmc
         if (st != MLMC_OK) break;
         p->cfg.inner_rtol = rt;
         p->cfg.mg_omega = om;
-        p->zc_override = zc;
+        p->cfg.z_chunk = zc;
         if ((st = settle_graph_launches(p)) != MLMC_OK) break;
         clear_graphs(p);
         regrid(p);
@@ -1860,11 +1859,10 @@ mlmc_status mlmc_autotune(mlmc_plan p, int level, int64_t count, int flags, mlmc
   cudaEventDestroy(e1);
   // apply the best setting (or restore the original one on failure)
   p->cfg = base;
-  p->zc_override = zc0;
   if (st == MLMC_OK && r.best_ms >= 0.0) {
     p->cfg.inner_rtol = r.inner_rtol;
     p->cfg.mg_omega = r.mg_omega;
-    p->zc_override = r.z_chunk;
+    p->cfg.z_chunk = r.z_chunk;
   }
   settle_graph_launches(p);
   clear_graphs(p);

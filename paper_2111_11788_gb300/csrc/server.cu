@@ -30,11 +30,11 @@ using Clock = std::chrono::steady_clock;
 constexpr int kMaxLevels = 16;
 
 // Plans of one shape can be re-targeted to each other's configurations.
-using ShapeKey = std::tuple<int, int, int, int, int, int, int>;
+using ShapeKey = std::tuple<int, int, int, int, int, int, int, int>;
 
 ShapeKey shape_of(const mlmc_config& c) {
   return ShapeKey(c.dim, c.n_levels, c.coarse_cells, c.modes_per_dim, c.solver, c.precision,
-                  c.total_order);
+                  c.total_order, c.z_chunk);
 }
 
 struct Slot {

@@ -55,7 +55,7 @@ class Config(ctypes.Structure):
         ("outer_max_iter", ctypes.c_int32),
         ("use_graphs", ctypes.c_int32),
         ("total_order", ctypes.c_int32),
-        ("reserved0", ctypes.c_int32),
+        ("z_chunk", ctypes.c_int32),
     ]
 
 
