@@ -790,32 +790,39 @@ __global__ void k_coarse3(Grid g, const T* __restrict__ K, const T* __restrict__
   E[b * g.ns + 13] = Bv[b * g.ns + 13] / d;
 }
 
-// Trilinear prolongation of the coarse correction at fine node (i, j, k).
-template <class T>
-__device__ __forceinline__ T prolong3(const T* __restrict__ Ec, int nc, int i, int j, int k) {
-  const int64_t N1 = nc + 1;
-  const int I = i >> 1, J = j >> 1, Kc = k >> 1;
-  const int ox = i & 1, oy = j & 1, oz = k & 1;
-  T acc = T(0);
-  for (int c = 0; c <= oz; ++c)
-    for (int bq = 0; bq <= oy; ++bq)
-      for (int a = 0; a <= ox; ++a) acc += __ldg(Ec + ((int64_t)(Kc + c) * N1 + (J + bq)) * N1 + (I + a));
-  const T scale = T(1) / T(1 << (ox + oy + oz));
-  return acc * scale;
-}
-
-// Pointwise: tmp = e + P ec (trilinear prolongation of the coarse correction).
+// Pointwise: tmp = e + P ec (trilinear prolongation of the coarse
+// correction). A thread takes the fine nodes 2I and 2I + 1 of one fine row
+// (y, z): the coarse rows under it (1, 2 or 4 by the parity of y and z) are
+// summed at coarse columns I and I + 1 once, the even node takes the first
+// sum, the odd node the mean of both, each divided by the number of rows.
+// Warps run along I with uniform parities, so the gathers do not diverge.
 template <class T>
 __global__ void __launch_bounds__(256) k_prolong3(Grid g, int64_t nsc, const T* __restrict__ E,
                                                   const T* __restrict__ Ec, T* __restrict__ Tmp,
                                                   const int32_t* __restrict__ active) {
-  const int64_t b = blockIdx.y;
+  const int64_t b = blockIdx.z;
   if (!active[b]) return;
-  const Node3 q = node3(g.n);
-  if (!q.valid) return;
-  T v = T(0);
-  if (q.interior) v = E[b * g.ns + q.idx] + prolong3(Ec + b * nsc, g.n / 2, q.i, q.j, q.k);
-  Tmp[b * g.ns + q.idx] = v;
+  const int n = g.n, nc = n / 2, N1 = n + 1, C1 = nc + 1;
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int ry = blockIdx.y * blockDim.y + threadIdx.y;   // (z, y) row index
+  const int rows_y = ((N1 + 7) / 8) * 8;
+  const int z = ry / rows_y, y = ry - z * rows_y;
+  if (I > nc || y > n || z > n) return;
+  const T* ec = Ec + b * nsc;
+  const int J = y >> 1, Kc = z >> 1, oy = y & 1, oz = z & 1;
+  T s0 = T(0), s1 = T(0);
+  for (int c = 0; c <= oz; ++c)
+    for (int bq = 0; bq <= oy; ++bq) {
+      const T* row = ec + ((Kc + c) * C1 + (J + bq)) * C1;
+      s0 += __ldg(row + I);
+      if (I < nc) s1 += __ldg(row + I + 1);
+    }
+  const T inv = T(1) / T(1 << (oy + oz));
+  const bool row_in = y >= 1 && y < n && z >= 1 && z < n;
+  const int64_t o = b * g.ns + ((int64_t)z * N1 + y) * N1 + 2 * I;
+  const int x0 = 2 * I;
+  Tmp[o] = (row_in && x0 >= 1 && x0 < n) ? E[o] + s0 * inv : T(0);
+  if (x0 + 1 <= n) Tmp[o + 1] = (row_in && x0 + 1 < n) ? E[o + 1] + T(0.5) * (s0 + s1) * inv : T(0);
 }
 
 // QoI partials: domain: w = h^3 at interior nodes; box [L, H]^3 in node
@@ -889,7 +896,11 @@ template <class T>
 cudaError_t mg_post(cudaStream_t s, const Grid& g, const Grid& coarse, const T* kappa, const T* w,
                     const T* b, const T* e, const T* ec, T* out, T* tmp, const int32_t* active,
                     double* part, int64_t B, Prof p) {
-  k_prolong3<T><<<grid3(g, B), block3(), 0, s>>>(g, coarse.ns, e, ec, tmp, active);
+  {
+    const int nc = g.n / 2, rows_y = ((g.n + 1 + 7) / 8) * 8;
+    const dim3 grid((unsigned)((nc + 1 + 31) / 32), (unsigned)(rows_y / 8 * (g.n + 1)), (unsigned)B);
+    k_prolong3<T><<<grid, dim3(32, 8, 1), 0, s>>>(g, coarse.ns, e, ec, tmp, active);
+  }
   launch_zm3<T>(s, g, B, kappa, LdX<T>{tmp, g.ns}, active, EpiMgPost<T>{w, b, out, g.ns}, part, p);
   return cudaGetLastError();
 }
