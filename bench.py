@@ -370,20 +370,54 @@ def serving_run(m, args, device=0, adapt=0):
                    "capped 8 (2D) / 7 (3D); GMG-PCG rtol 1e-10, FP32 inner + FP64 refinement"}
 
 
-def roofline_of(res, peaks, fp64_alu):
+# FP64 work per algorithmic byte of the FP64 stencil kernels, from their
+# per-node operation counts (read off the kernels) and byte models (nn ~ ne,
+# nc ~ nn / 2^d; bytes per node 42, 40, 40, 24). Per node: the 2D stencil is
+# 17 FP64 instructions (5 adds, 4 multiplies, 8 FMAs = 25 flops), the 3D one
+# 52 instructions (64 flops); mg_post adds the prolongation and the smoothing update with its dot, mg_pre
+# the W b product and the residual, pcg_pq the direction update and the dot,
+# resid64 the residual and its square.
+#   (instructions per node, flops per node, bytes per node)
+FP64_WORK = {
+    (2, "mg_post"): (22.5, 33.0, 42.0), (2, "mg_pre"): (19.0, 27.0, 40.0),
+    (2, "pcg_pq"): (19.0, 29.0, 40.0), (2, "resid64"): (19.0, 28.0, 24.0),
+    (3, "mg_post"): (57.5, 72.0, 41.0), (3, "mg_pre"): (54.0, 66.0, 40.0),
+    (3, "pcg_pq"): (54.0, 68.0, 40.0), (3, "resid64"): (54.0, 67.0, 24.0),
+}
+GB300_SMS = 152
+DFMA_PER_SM_CLK = 2
+
+
+def roofline_of(res, peaks, fp64_alu, dim=2):
     d_launches, d_ms, d_bytes = res["dstat"]
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     src = "measured" if "hbm_gbs" in peaks else "fallback"
-    achieved = (d_bytes / (d_ms / 1e3)) / 1e9 if d_ms > 0 else 0.0
-    r = {"bound": "alu" if fp64_alu else "hbm", "kernel": res["dom"],
-         "achieved": round(achieved, 1), "peak": hbm_peak, "peak_source": src, "unit": "GB/s",
-         "frac": round(achieved / hbm_peak, 4), "traffic": None, "launches": d_launches,
+    gbs = (d_bytes / (d_ms / 1e3)) / 1e9 if d_ms > 0 else 0.0
+    r = {"kernel": res["dom"], "traffic": None, "launches": d_launches,
          "avg_launch_us": round(1e3 * d_ms / max(d_launches, 1), 2),
          "time_shares": res["shares"], "per_kernel": res["per_kernel"]}
-    if fp64_alu:
-        r["note"] = ("FP64 form: the kernel is bound by the FP64 pipe (2 DFMA/SM/cycle on GB300, "
-                     "1.26 TFLOP/s at 2.07 GHz); achieved/peak/frac here are its HBM bytes "
-                     "against the measured copy bandwidth")
+    work = FP64_WORK.get((dim, res["dom"]))
+    if fp64_alu and work is not None:
+        # FP64-pipe bound: algorithmic FP64 flops/s (FMA = 2) against 2 DFMA per
+        # SM per cycle at the median SM clock of the timed region; the same as
+        # FP64 instructions/s against the pipe's 2 instructions per SM per cycle
+        ins, flops, nbytes = work
+        mhz = (res.get("clocks") or {}).get("sm_mhz") or 2070.0
+        peak = DFMA_PER_SM_CLK * 2 * GB300_SMS * mhz * 1e6 / 1e12
+        achieved = gbs * flops / nbytes / 1e3
+        ipeak = DFMA_PER_SM_CLK * GB300_SMS * mhz * 1e6 / 1e12
+        iach = gbs * ins / nbytes / 1e3
+        r.update({"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4),
+                  "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                  "peak_source": "derived: %d SMs x %d DFMA/cycle x 2 flops x %.0f MHz (median "
+                                 "under load)" % (GB300_SMS, DFMA_PER_SM_CLK, mhz),
+                  "fp64_instructions": {"achieved": round(iach, 4), "peak": round(ipeak, 4),
+                                        "unit": "T instr/s", "frac": round(iach / ipeak, 4)},
+                  "hbm": {"achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                          "frac": round(gbs / hbm_peak, 4), "peak_source": src}})
+    else:
+        r.update({"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                  "frac": round(gbs / hbm_peak, 4), "peak_source": src})
     return r
 
 
@@ -449,7 +483,7 @@ def bench_ours(args):
                        "samples_per_level": res["N"], "q_hat": res["q"], "stat_var": res["v"],
                        "gpu_launches": int(res["launches"]), "clocks": res["clocks"],
                        "autotune": res["tune"],
-                       "roofline": roofline_of(res, peaks, fp64_alu=(form == "fp64"))}
+                       "roofline": roofline_of(res, peaks, fp64_alu=(form == "fp64"), dim=wl["dim"])}
     if rank == 0:
         names = {"fp64": "plain FP64", "mixed": "mixed: FP32 inner PCG + FP64 refinement"}
         line = {"metric": "coupled DOF-solves/s", "value": value, "unit": "coupled DOF-solves/s",
@@ -463,7 +497,7 @@ def bench_ours(args):
                            "q_hat": main["q"], "stat_var": main["v"],
                            "l2": "working set of the 512^2/1024^2 levels (GBs) exceeds the 129 MB L2",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
-                "roofline": roofline_of(main, peaks, fp64_alu=(args.form == "fp64")),
+                "roofline": roofline_of(main, peaks, fp64_alu=(args.form == "fp64"), dim=wl["dim"]),
                 "clocks": main["clocks"], "gpu_launches": int(main["launches"]),
                 "autotune": main["tune"],
                 "e2e": {"value": e2e_value, "unit": "coupled DOF-solves/s",

@@ -471,7 +471,7 @@ __global__ void __launch_bounds__(FLAT_THREADS) k_init_flat(Grid g, T* __restric
     if (R) {
       T v = T(0);
       if (e < nn) {
-        const int j = (int)(e / N1), i = (int)(e - (int64_t)j * N1);
+        const int ei = (int)e, j = ei / N1, i = ei - j * N1;   // e < (n + 1)^2 < 2^31
         if (interior2(g.n, i, j)) v = h2;
       }
       R[b * g.ns + e] = v;
@@ -496,7 +496,7 @@ __global__ void __launch_bounds__(FLAT_THREADS) k_qoi_flat(Grid g, int box, int 
   const double h2 = g.h * g.h;
   double v = 0.0;
   for (int64_t e = e0 + threadIdx.x; e < e1 && e < nn; e += FLAT_THREADS) {
-    const int j = (int)(e / N1), i = (int)(e - (int64_t)j * N1);
+    const int ei = (int)e, j = ei / N1, i = ei - j * N1;   // e < (n + 1)^2 < 2^31
     if (!interior2(g.n, i, j)) continue;
     double w = h2;
     if (box) {
@@ -567,7 +567,7 @@ __global__ void __launch_bounds__(FLAT_THREADS) k_winv2(Grid g, const T* __restr
   for (int64_t e = e0 + threadIdx.x; e < e1; e += FLAT_THREADS) {
     T w = T(0);
     if (e < nn) {
-      const int j = (int)(e / N1), i = (int)(e - (int64_t)j * N1);
+      const int ei = (int)e, j = ei / N1, i = ei - j * N1;   // e < (n + 1)^2 < 2^31
       if (interior2(g.n, i, j)) {
         const T* r0 = k + (int64_t)(j - 1) * g.n + (i - 1);
         const T d = Consts<T>::c23 * ((r0[0] + r0[1]) + (r0[g.n] + r0[g.n + 1]));
@@ -597,7 +597,7 @@ __global__ void __launch_bounds__(FLAT_THREADS) k_restrict2(Grid gc, int64_t nsf
   for (int64_t e = e0 + threadIdx.x; e < e1; e += FLAT_THREADS) {
     T v = T(0);
     if (e < nn) {
-      const int J = (int)(e / N1c), I = (int)(e - (int64_t)J * N1c);
+      const int ei = (int)e, J = ei / N1c, I = ei - J * N1c;
       if (interior2(nc, I, J)) {
         const T* r = R1 + b * nsf + (int64_t)(2 * J) * N1 + 2 * I;
         const T h = T(0.5);
