@@ -42,6 +42,15 @@ WORKLOADS = {
                      qoi='box', box=(0.25, 0.75), solver='gmg', rtol=1e-10,
                      seed=0, stream_id=0, eps=None, pilot=0, N=(64, 32, 16, 8, 4),
                      precision='mixed'),
+    # The paper-shaped sample mix: 3 levels 16^3..64^3 (the grids of the
+    # paper's 3D Poisson example), N = C (1024, 64, 4) with C = 1 (Table 1),
+    # the example's field (correlation length 0.25, standard deviation 0.25,
+    # 16 eigenfunctions per axis under a total-order truncation: 680 modes
+    # with 0-based orders summing to at most 14), box-mean QoI, mixed form.
+    "3d-paper-mix": dict(dim=3, n0=16, levels=3, sigma2=0.0625, corr_len=0.25, m=16,
+                         total_order=14, qoi='box', box=(0.25, 0.75), solver='gmg',
+                         rtol=1e-10, seed=0, stream_id=0, eps=None, pilot=0,
+                         N=(1024, 64, 4), precision='mixed'),
 }
 
 

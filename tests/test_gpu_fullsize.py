@@ -50,3 +50,24 @@ def test_pilot_batch_full_size(m, precision, level, checked):
         rf, rc = oracle_sample(level, i)
         assert abs(qf[i] - rf) <= 1e-9 * abs(rf)
         assert abs(qc[i] - rc) <= 1e-9 * abs(rc)
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_mix_sample(level, i):
+    return omlmc.coupled_sample(workload("3d-paper-mix"), level, i)
+
+
+@pytest.mark.parametrize("level,count,checked", [(1, 64, (0, 41)), (0, 256, (7,))])
+def test_paper_sample_mix_full_size(m, level, count, checked):
+    """The paper-shaped 3D mix (680 total-order modes, 16^3..64^3): a level's
+    batch in one call, sampled samples against the oracle."""
+    wl = workload("3d-paper-mix")
+    cfg = m.config_from_workload(wl)
+    with m.Plan(cfg, torch.cuda.current_stream().cuda_stream) as plan:
+        qf, qc, it = plan.sample_level(level, 0, count)
+    assert np.all(it > 0)
+    for i in checked:
+        rf, rc = oracle_mix_sample(level, i)
+        assert abs(qf[i] - rf) <= 1e-9 * abs(rf)
+        if level > 0:
+            assert abs(qc[i] - rc) <= 1e-9 * abs(rc)
