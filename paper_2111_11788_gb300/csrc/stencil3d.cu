@@ -487,9 +487,9 @@ __device__ __forceinline__ float2 inplane3p(const float2 Kb[2][2], const float2 
   return fma2(mc12, e, mul2(mul2(c3, s), v[1][1]));
 }
 
-// Asynchronous 4-byte global -> shared copy (zero-filled when src_bytes = 0).
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem, int src_bytes) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+// Asynchronous 4-byte global -> shared copy to a shared-window address
+// (zero-filled when src_bytes = 0).
+__device__ __forceinline__ void cp_async4s(unsigned sa, const void* gmem, int src_bytes) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(src_bytes)
                : "memory");
 }
@@ -596,28 +596,30 @@ __global__ void __launch_bounds__(ZTHREADS, 3) k_zm3f(Grid g, const float* __res
   }
   // stage plane pp into ring slot st (one commit group per plane; empty
   // groups past the chunk keep the group count uniform)
+  // shared addresses of this thread's copy slots in ring slot 0 (slot st is
+  // st * stage bytes further); global reads of masked slots point at a plane
+  // inside the sample and copy 0 bytes
+  const unsigned sv0 = (unsigned)__cvta_generic_to_shared(&sv[0][0][0]);
+  const unsigned sk0 = (unsigned)__cvta_generic_to_shared(&sk[0][0]);
+  constexpr unsigned SV_ARR = ZNVP * 8, SV_STAGE = NA * ZNVP * 8, SK_STAGE = ZNKP * 8;
   auto issue = [&](int pp, int st) {
     if (pp <= t.z1) {
       const bool pv = pp >= 1 && pp < n, pk = pp >= 0 && pp < n;
+      const int pc = min(max(pp, 0), n - 1);
+      const unsigned svs = sv0 + st * SV_STAGE, sks = sk0 + st * SK_STAGE;
+      const float* kpl = kp + pc * KP;
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
-        const int e = tid + q * ZTHREADS;
+        const unsigned e8 = (unsigned)(tid + q * ZTHREADS) * 8u;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           if (vin[q]) {
 #pragma unroll
-            for (int a = 0; a < NA; ++a) {
-              const float* src = ld.src(a);
-              const bool ok = pv && vok[q][h];
-              cp_async4(reinterpret_cast<float*>(&sv[st][a][e]) + h, ok ? src + pp * P + vo[q][h] : src,
-                        ok ? 4 : 0);
-            }
+            for (int a = 0; a < NA; ++a)
+              cp_async4s(svs + a * SV_ARR + e8 + 4u * h, ld.src(a) + pc * P + vo[q][h],
+                         (pv && vok[q][h]) ? 4 : 0);
           }
-          if (kin[q]) {
-            const bool ok = pk && kok[q][h];
-            cp_async4(reinterpret_cast<float*>(&sk[st][e]) + h, ok ? kp + pp * KP + ko[q][h] : kp,
-                      ok ? 4 : 0);
-          }
+          if (kin[q]) cp_async4s(sks + e8 + 4u * h, kpl + ko[q][h], (pk && kok[q][h]) ? 4 : 0);
         }
       }
     }
