@@ -560,7 +560,7 @@ struct LdPaired<LdWb<float>> {
 };
 
 template <class Ld, class Epi>
-__global__ void __launch_bounds__(ZTHREADS, 3) k_zm3f(Grid g, const float* __restrict__ Kap, Ld ld,
+__global__ void __launch_bounds__(ZTHREADS, 2) k_zm3f(Grid g, const float* __restrict__ Kap, Ld ld,
                                                       const int32_t* __restrict__ active, Epi epi,
                                                       double* __restrict__ part, Prof prof) {
   constexpr int NA = Ld::kArrays;
