@@ -73,6 +73,7 @@ struct Grid {
   int64_t ns;       // node stride (values per sample)
   int64_t es;       // element stride
   double h;
+  double c3, c12;   // h / 3 and h / 12 (3D stencil coefficients), computed on the host
   int sx, sy;       // 2D: stencil CTAs per sample (strip groups x row chunks);
                     // 3D: node-tile CTAs per sample of the pointwise kernels (sx)
   int zc;           // 3D: z-planes per CTA of the z-marching stencil kernels

@@ -26,6 +26,8 @@ Grid make_grid(int dim, int n, int z_chunk) {
   g.ns = round_up(ipow(n + 1, dim), 32);
   g.es = round_up(ipow(n, dim), 32);
   g.h = 1.0 / n;
+  g.c3 = g.h / 3.0;
+  g.c12 = g.h / 12.0;
   if (dim == 2) {
     const int strips = (n + 1 + 29) / 30;
     g.sx = (strips + SWARPS - 1) / SWARPS;

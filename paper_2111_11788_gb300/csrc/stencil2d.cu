@@ -522,7 +522,10 @@ __global__ void __launch_bounds__(FLAT_THREADS) k_refine_flat(Grid g, int mode,
   const int64_t b = blockIdx.y;
   if (!active[b]) return;
   const double sc = scale[b];
-  const double inv = 1.0 / sc;
+  __shared__ double s_inv;   // one division per CTA, not per thread
+  if (threadIdx.x == 0) s_inv = 1.0 / sc;
+  __syncthreads();
+  const double inv = s_inv;
   int64_t v0, v1, t0, nn;
   flat_range<float>(g, v0, v1, t0, nn);
   double2* d = reinterpret_cast<double2*>(Dbl + b * g.ns);

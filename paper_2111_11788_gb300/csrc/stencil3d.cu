@@ -103,10 +103,10 @@ __device__ __forceinline__ void load_k8(const T* __restrict__ K, int n, const No
 }
 
 template <class T>
-__device__ __forceinline__ T diag3(const T kk[2][2][2], double h) {
+__device__ __forceinline__ T diag3(const T kk[2][2][2], double c3) {
   const T s = ((kk[0][0][0] + kk[0][0][1]) + (kk[0][1][0] + kk[0][1][1])) +
               ((kk[1][0][0] + kk[1][0][1]) + (kk[1][1][0] + kk[1][1][1]));
-  return T(h / 3.0) * s;
+  return T(c3) * s;
 }
 
 // ---------------------------------------------------------------- z-march
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(ZTHREADS, 2) k_zm3(Grid g, const T* __restrict
     ocol[r] = j * N1 + i;
   }
   const bool ex = i == n - 1 && n % ZTX == 0;
-  const T c3 = T(g.h / 3.0), c12 = T(g.h / 12.0);
+  const T c3 = T(g.c3), c12 = T(g.c12);
   T a0[ZRY], a1[ZRY], vc[ZRY];   // outputs of planes p - 1 and p so far; x at plane p - 1
   typename Epi::Pre pre[ZRY];    // epilogue inputs of plane p - 1
 #pragma unroll
@@ -641,7 +641,7 @@ __global__ void __launch_bounds__(ZTHREADS, 2) k_zm3f(Grid g, const float* __res
     ocol[r] = jr[r] * N1 + i;
   }
   const bool ex = i == n - 1 && n % ZTX == 0;
-  const float c3s = (float)(g.h / 3.0), c12s = (float)(g.h / 12.0);
+  const float c3s = (float)g.c3, c12s = (float)g.c12;
   const float2 c3 = make_float2(c3s, c3s), mc12 = make_float2(-c12s, -c12s);
   float2 a0 = make_float2(0.f, 0.f), a1 = a0, vc = a0;
   float2 kb[2][2] = {{a0, a0}, {a0, a0}};
@@ -733,7 +733,7 @@ __global__ void __launch_bounds__(256) k_winv3(Grid g, const T* __restrict__ K, 
   if (q.interior) {
     T kk[2][2][2];
     load_k8(K + b * g.es, g.n, q, kk);
-    w = T(omega) / diag3(kk, g.h);
+    w = T(omega) / diag3(kk, g.c3);
   }
   W[b * g.ns + q.idx] = w;
 }
@@ -787,7 +787,7 @@ __global__ void k_coarse3(Grid g, const T* __restrict__ K, const T* __restrict__
   const T* k = K + b * g.es;
   T s = T(0);
   for (int e = 0; e < 8; ++e) s += k[e];
-  const T d = T(g.h / 3.0) * s;
+  const T d = T(g.c3) * s;
   for (int t = 0; t < 27; ++t) E[b * g.ns + t] = T(0);
   E[b * g.ns + 13] = Bv[b * g.ns + 13] / d;
 }
@@ -819,7 +819,8 @@ __global__ void __launch_bounds__(256) k_prolong3(Grid g, int64_t nsc, const T* 
       s0 += __ldg(row + I);
       if (I < nc) s1 += __ldg(row + I + 1);
     }
-  const T inv = T(1) / T(1 << (oy + oz));
+  const int rows = oy + oz;
+  const T inv = rows == 0 ? T(1) : (rows == 1 ? T(0.5) : T(0.25));
   const bool row_in = y >= 1 && y < n && z >= 1 && z < n;
   const int64_t o = b * g.ns + ((int64_t)z * N1 + y) * N1 + 2 * I;
   const int x0 = 2 * I;
