@@ -147,9 +147,13 @@ cudaError_t winv(cudaStream_t s, const Grid& g, const T* kappa, double omega, T*
 // x = 0; if r != nullptr, r = b (b_i = h^2 at interior nodes).
 template <class T>
 cudaError_t pcg_init(cudaStream_t s, const Grid& g, T* x, T* r, int64_t B, Prof p);
+// coef (may be null): the FP64 form's precomputed operator coefficients
+// (coef()), used instead of kappa by the stencil kernels
+template <class T>
+cudaError_t coef(cudaStream_t s, const Grid& g, const T* kappa, T* coef, int64_t B);
 template <class T>
 cudaError_t pcg_pq(cudaStream_t s, const Grid& g, const T* kappa, const T* z, const T* p_old,
-                   T* p_new, T* q, const Scalars& sc, double* part, int64_t B, Prof p);
+                   T* p_new, T* q, const Scalars& sc, double* part, int64_t B, Prof p, const T* coef);
 template <class T>
 cudaError_t pcg_xr(cudaStream_t s, const Grid& g, T* x, const T* pv, T* r, const T* q,
                    const Scalars& sc, double* part, int64_t B, Prof p);
@@ -158,7 +162,7 @@ cudaError_t jacobi_z(cudaStream_t s, const Grid& g, const T* winv, const T* r, T
                      const Scalars& sc, double* part, int64_t B, Prof p);
 template <class T>
 cudaError_t mg_pre(cudaStream_t s, const Grid& g, const T* kappa, const T* w, const T* b, T* e,
-                   T* r1, const int32_t* active, int64_t B, Prof p);
+                   T* r1, const int32_t* active, int64_t B, Prof p, const T* coef);
 template <class T>
 cudaError_t restrict_(cudaStream_t s, const Grid& fine, const Grid& coarse, const T* r1, T* bc,
                       const int32_t* active, int64_t B, Prof p);
@@ -168,13 +172,14 @@ cudaError_t coarse_solve(cudaStream_t s, const Grid& g, const T* kappa, const T*
 template <class T>
 cudaError_t mg_post(cudaStream_t s, const Grid& g, const Grid& coarse, const T* kappa, const T* w,
                     const T* b, const T* e, const T* ec, T* out, const int32_t* active,
-                    double* part, int64_t B, Prof p);
+                    double* part, int64_t B, Prof p, const T* coef);
 template <class T>
 cudaError_t qoi(cudaStream_t s, const Grid& g, int box, int L, int H, double inv_vol, const T* x,
                 double* part, int64_t B, Prof p);
 // mixed form (FP64 outer refinement around the FP32 inner solve)
 cudaError_t resid64(cudaStream_t s, const Grid& g, const double* kappa, const double* u,
-                    double* r, const int32_t* active, double* part, int64_t B, Prof p);
+                    double* r, const int32_t* active, double* part, int64_t B, Prof p,
+                    const double* coef);
 cudaError_t to_rhs32(cudaStream_t s, const Grid& g, const double* r, const double* scale,
                      float* r32, const int32_t* active, int64_t B, Prof p);
 cudaError_t add_correction(cudaStream_t s, const Grid& g, double* u, const float* d32,
@@ -231,8 +236,9 @@ inline cudaError_t pcg_init(cudaStream_t s, const Grid& g, T* x, T* r, int64_t B
 }
 template <class T>
 inline cudaError_t pcg_pq(cudaStream_t s, const Grid& g, const T* kappa, const T* z, const T* p_old,
-                          T* p_new, T* q, const Scalars& sc, double* part, int64_t B, Prof p) {
-  return g.dim == 2 ? d2::pcg_pq<T>(s, g, kappa, z, p_old, p_new, q, sc, part, B, p)
+                          T* p_new, T* q, const Scalars& sc, double* part, int64_t B, Prof p,
+                          const T* coef = nullptr) {
+  return g.dim == 2 ? d2::pcg_pq<T>(s, g, kappa, z, p_old, p_new, q, sc, part, B, p, coef)
                     : d3::pcg_pq<T>(s, g, kappa, z, p_old, p_new, q, sc, part, B, p);
 }
 template <class T>
@@ -247,8 +253,8 @@ inline cudaError_t jacobi_z(cudaStream_t s, const Grid& g, const T* winv, const 
 }
 template <class T>
 inline cudaError_t mg_pre(cudaStream_t s, const Grid& g, const T* kappa, const T* w, const T* b, T* e,
-                          T* r1, const int32_t* active, int64_t B, Prof p) {
-  return g.dim == 2 ? d2::mg_pre<T>(s, g, kappa, w, b, e, r1, active, B, p)
+                          T* r1, const int32_t* active, int64_t B, Prof p, const T* coef = nullptr) {
+  return g.dim == 2 ? d2::mg_pre<T>(s, g, kappa, w, b, e, r1, active, B, p, coef)
                     : d3::mg_pre<T>(s, g, kappa, w, b, e, r1, active, B, p);
 }
 template <class T>
@@ -267,8 +273,8 @@ inline cudaError_t coarse_solve(cudaStream_t s, const Grid& g, const T* kappa, c
 template <class T>
 inline cudaError_t mg_post(cudaStream_t s, const Grid& g, const Grid& coarse, const T* kappa, const T* w,
                            const T* b, const T* e, const T* ec, T* out, T* tmp, const int32_t* active,
-                           double* part, int64_t B, Prof p) {
-  return g.dim == 2 ? d2::mg_post<T>(s, g, coarse, kappa, w, b, e, ec, out, active, part, B, p)
+                           double* part, int64_t B, Prof p, const T* coef = nullptr) {
+  return g.dim == 2 ? d2::mg_post<T>(s, g, coarse, kappa, w, b, e, ec, out, active, part, B, p, coef)
                     : d3::mg_post<T>(s, g, coarse, kappa, w, b, e, ec, out, tmp, active, part, B, p);
 }
 template <class T>
@@ -278,8 +284,9 @@ inline cudaError_t qoi(cudaStream_t s, const Grid& g, int box, int L, int H, dou
                     : d3::qoi<T>(s, g, box, L, H, inv_vol, x, part, B, p);
 }
 inline cudaError_t resid64(cudaStream_t s, const Grid& g, const double* kappa, const double* u,
-                           double* r, const int32_t* active, double* part, int64_t B, Prof p) {
-  return g.dim == 2 ? d2::resid64(s, g, kappa, u, r, active, part, B, p)
+                           double* r, const int32_t* active, double* part, int64_t B, Prof p,
+                           const double* coef = nullptr) {
+  return g.dim == 2 ? d2::resid64(s, g, kappa, u, r, active, part, B, p, coef)
                     : d3::resid64(s, g, kappa, u, r, active, part, B, p);
 }
 inline cudaError_t to_rhs32(cudaStream_t s, const Grid& g, const double* r, const double* scale,

@@ -124,13 +124,14 @@ mlmc_status na_precondition(cudaStream_t s, const Grid* g, int K, NaWs& w, int64
     return MLMC_OK;
   }
   for (int k = 0; k < K - 1; ++k) {
-    NA_CK(d2::mg_pre(s, g[k], w.kap[k], w.w[k], w.bk[k], w.e[k], w.r1[k], w.sc.active, B, off));
+    NA_CK(d2::mg_pre(s, g[k], w.kap[k], w.w[k], w.bk[k], w.e[k], w.r1[k], w.sc.active, B, off,
+                     (const double*)nullptr));
     NA_CK(d2::restrict_(s, g[k], g[k + 1], w.r1[k], w.bk[k + 1], w.sc.active, B, off));
   }
   NA_CK(d2::coarse_solve(s, g[K - 1], w.kap[K - 1], w.bk[K - 1], w.e[K - 1], w.sc.active, B));
   for (int k = K - 2; k >= 0; --k)
     NA_CK(d2::mg_post(s, g[k], g[k + 1], w.kap[k], w.w[k], w.bk[k], w.e[k], w.eo[k + 1], w.eo[k],
-                      w.sc.active, k == 0 ? w.part : nullptr, B, off));
+                      w.sc.active, k == 0 ? w.part : nullptr, B, off, (const double*)nullptr));
   *tiles = g[0].tiles_s;
   return MLMC_OK;
 }
@@ -189,7 +190,8 @@ extern "C" mlmc_status mlmc_solve_noalloc(const mlmc_config* c, int mesh, const 
   double* pnew = w.p1;
   int32_t h_count = 0;
   for (int it = 1; it <= c->max_iter; ++it) {
-    NA_CK(d2::pcg_pq(s, g[0], w.kap[0], w.z, pold, pnew, w.q, w.sc, w.part, count, off));
+    NA_CK(d2::pcg_pq(s, g[0], w.kap[0], w.z, pold, pnew, w.q, w.sc, w.part, count, off,
+                     (const double*)nullptr));
     NA_CK(launch_finalize(s, FIN_ALPHA, w.part, g[0].tiles_s, w.sc, nullptr, it, c->max_iter, count));
     NA_CK(d2::pcg_xr(s, g[0], w.x, pnew, w.r, w.q, w.sc, w.part, count, off));
     NA_CK(launch_finalize(s, FIN_CONV, w.part, g[0].tiles_f, w.sc, nullptr, it, c->max_iter, count));

@@ -85,6 +85,7 @@ template <class T>
 struct SolveWs {
   T *x, *r, *p0, *p1, *q, *z;
   T* kap[MAX_MG];
+  T* coef[MAX_MG];   // FP64 2D: precomputed operator coefficients per level (else null)
   T* w[MAX_MG];
   T *e[MAX_MG], *r1[MAX_MG], *bk[MAX_MG], *eo[MAX_MG];
   double* part;
@@ -96,6 +97,9 @@ struct SolveWs {
 
 template <class T>
 void carve_solve(Carve& c, const MeshInfo& mi, int64_t B, bool own_kappa0, SolveWs<T>& w) {
+  // the FP64 2D stencils run on precomputed coefficients (3 node + 1 element
+  // arrays per level where a stencil kernel runs)
+  const bool coef = sizeof(T) == 8 && mi.g[0].dim == 2;
   const Grid& g0 = mi.g[0];
   w.x = c.take<T>(B * g0.ns);
   w.r = c.take<T>(B * g0.ns);
@@ -106,6 +110,7 @@ void carve_solve(Carve& c, const MeshInfo& mi, int64_t B, bool own_kappa0, Solve
   for (int k = 0; k < mi.K; ++k) {
     const Grid& g = mi.g[k];
     w.kap[k] = (k == 0 && !own_kappa0) ? nullptr : c.take<T>(B * g.es);
+    w.coef[k] = (coef && (k == 0 || k < mi.K - 1)) ? c.take<T>(B * (3 * g.ns + g.es)) : nullptr;
     w.w[k] = c.take<T>(B * g.ns);
     if (mi.K > 1) {
       w.e[k] = c.take<T>(B * g.ns);
@@ -135,6 +140,7 @@ struct MixedWs {
   double* u;
   double* r;
   double* kap64;
+  double* coef64;   // 2D: coefficients of the FP64 operator for the outer residual (else null)
   Scalars outer;
   int32_t* outer_count;
   int32_t* outer_it;
@@ -147,6 +153,7 @@ void carve_mixed(Carve& c, const MeshInfo& mi, int64_t B, MixedWs& w) {
   w.u = c.take<double>(B * g0.ns);
   w.r = c.take<double>(B * g0.ns);
   w.kap64 = c.take<double>(B * g0.es);
+  w.coef64 = g0.dim == 2 ? c.take<double>(B * (3 * g0.ns + g0.es)) : nullptr;
   w.outer.gamma = w.outer.delta = w.outer.alpha = w.outer.beta = nullptr;
   w.outer.rho = c.take<double>(B);
   w.outer.tol = c.take<double>(B);
@@ -536,7 +543,7 @@ mlmc_status precondition(mlmc_plan p, const MeshInfo& mi, SolveWs<T>& w, int64_t
     const double nn = nodes_of(g), ne = elems_of(g);
     CK(run(p, KID_MG_PRE, [&] {
       return op::mg_pre<T>(s, g, w.kap[k], w.w[k], w.bk[k], w.e[k], w.r1[k], w.sc.active, B,
-                           prof_for(p, KID_MG_PRE, (4 * nn + ne) * vb));
+                           prof_for(p, KID_MG_PRE, (4 * nn + ne) * vb), w.coef[k]);
     }));
     CK(run(p, KID_RESTRICT, [&] {
       return op::restrict_<T>(s, g, mi.g[k + 1], w.r1[k], w.bk[k + 1], w.sc.active, B,
@@ -553,7 +560,7 @@ mlmc_status precondition(mlmc_plan p, const MeshInfo& mi, SolveWs<T>& w, int64_t
       // r1[k] is dead once restricted: it serves as the 3D scratch for e + P e_c
       return op::mg_post<T>(s, g, mi.g[k + 1], w.kap[k], w.w[k], w.bk[k], w.e[k], w.eo[k + 1],
                             w.eo[k], w.r1[k], w.sc.active, k == 0 ? w.part : nullptr, B,
-                            prof_for(p, KID_MG_POST, (4 * nn + ne + nc) * vb));
+                            prof_for(p, KID_MG_POST, (4 * nn + ne + nc) * vb), w.coef[k]);
     }));
   }
   *tiles = g0.tiles_s;
@@ -575,6 +582,8 @@ mlmc_status setup_levels(mlmc_plan p, const MeshInfo& mi, SolveWs<T>& w, int64_t
   const double omega = (K > 1) ? p->cfg.mg_omega : 1.0;
   for (int k = 0; k < std::max(1, K - 1); ++k)
     CK(run(p, KID_SETUP, [&] { return op::winv<T>(s, mi.g[k], w.kap[k], omega, w.w[k], B); }));
+  for (int k = 0; k < K; ++k)
+    if (w.coef[k]) CK(run(p, KID_SETUP, [&] { return d2::coef<T>(s, mi.g[k], w.kap[k], w.coef[k], B); }));
   return MLMC_OK;
 }
 
@@ -602,7 +611,7 @@ mlmc_status pcg_iteration(mlmc_plan p, const MeshInfo& mi, SolveWs<T>& w, int64_
   const int32_t* itd = h ? w.it : nullptr;
   CK(run(p, KID_PCG_PQ, [&] {
     return op::pcg_pq<T>(s, g0, w.kap[0], w.z, pold, pnew, w.q, w.sc, w.part, B,
-                         prof_for(p, KID_PCG_PQ, (4 * nn0 + ne0) * vb));
+                         prof_for(p, KID_PCG_PQ, (4 * nn0 + ne0) * vb), w.coef[0]);
   }));
   CK(run(p, KID_FINALIZE, [&] { return launch_finalize(s, FIN_ALPHA, w.part, g0.tiles_s, w.sc, nullptr, it, max_iter, B, itd); }));
   CK(run(p, KID_PCG_XR, [&] {
@@ -901,6 +910,7 @@ mlmc_status mixed_setup(mlmc_plan p, const MeshInfo& mi, MixedWs& w, int64_t B) 
   const mlmc_config& c = p->cfg;
   const Grid& g0 = mi.g[0];
   CK(run(p, KID_SETUP, [&] { return launch_cast_kappa(s, g0, w.kap64, w.in.kap[0], B); }));
+  if (w.coef64) CK(run(p, KID_SETUP, [&] { return d2::coef<double>(s, g0, w.kap64, w.coef64, B); }));
   mlmc_status st = setup_levels<float>(p, mi, w.in, B);
   if (st != MLMC_OK) return st;
   const double bn = b_norm(c, g0);
@@ -944,7 +954,7 @@ mlmc_status mixed_post_inner(mlmc_plan p, const MeshInfo& mi, MixedWs& w, int64_
   }));
   CK(run(p, KID_RESID64, [&] {
     return op::resid64(s, g0, w.kap64, w.u, w.r, w.outer.active, w.in.part, B,
-                       prof_for(p, KID_RESID64, (2 * nn0 + ne0) * 8));
+                       prof_for(p, KID_RESID64, (2 * nn0 + ne0) * 8), w.coef64);
   }));
   CK(run(p, KID_FINALIZE, [&] {
     return launch_outer_step(s, w.in.part, g0.tiles_s, w.outer, w.in.sc.iters, c.inner_max_iter,

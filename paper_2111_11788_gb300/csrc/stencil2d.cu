@@ -106,39 +106,118 @@ __device__ __forceinline__ T stencil_win(const Win<T>& w) {
   return Consts<T>::c23 * (kS + kN) * w.v0 - Consts<T>::c16 * edge - Consts<T>::c13 * corner;
 }
 
+// Node coefficients of the 2D operator, precomputed once per solve (FP64
+// form): per sample cd (diagonal), ce (coupling with the east neighbour),
+// cn (coupling with the north neighbour) at every node, and q (corner
+// coupling) per element, laid out [cd | ce | cn] in node strides, then q.
+// With them a row of the operator costs 1 multiply and 8 FMAs instead of 17
+// FP64 operations on kappa (the west and south couplings are the east and
+// north ones of the neighbours).
+template <class T>
+struct WinC {
+  T vm, v0, vp, lm, l0, lp, rm, r0, rp;   // field, as in Win
+  T qa, qb, qal, qbl;                     // corner couplings of elements (c, j-1), (c, j), (c-1, j-1), (c-1, j)
+  T cd, ce, ceW, cnN, cnS;                // diagonal, east, west, north, south couplings
+};
+
+template <class T>
+__device__ __forceinline__ T stencil_coef(const WinC<T>& w) {
+  T a = w.cd * w.v0;
+  a = fma(w.ce, w.r0, a);
+  a = fma(w.ceW, w.l0, a);
+  a = fma(w.cnN, w.vp, a);
+  a = fma(w.cnS, w.vm, a);
+  a = fma(w.qb, w.rp, a);
+  a = fma(w.qbl, w.lp, a);
+  a = fma(w.qa, w.rm, a);
+  return fma(w.qal, w.lm, a);
+}
+
 // Streams one warp strip. field(c, j) is the stencilled field at an interior
-// node; out(j, w) runs for each output row j of an output lane with the
-// window centred on (c, j). Every lane executes the loads and shuffles.
-template <class T, class FieldF, class OutF>
-__device__ __forceinline__ void stream_strip(const Strip& s, const T* __restrict__ kap,
+// node; out(j, x, ax) runs for each output row j of an output lane with the
+// field x at (c, j) and ax = (A x)(c, j) (0 at boundary nodes). C selects
+// the operator source: kappa per element (src = kappa of the sample), or the
+// precomputed coefficients (src = coefficient block of the sample, ns its
+// node stride). Every lane executes the loads and shuffles.
+template <class T, bool C, class FieldF, class OutF>
+__device__ __forceinline__ void stream_strip(const Strip& s, const T* __restrict__ src, int64_t ns,
                                              FieldF&& field, OutF&& out) {
   const int n = s.n;
   auto fld = [&](int j) -> T { return interior2(n, s.c, j) ? field(s.c, j) : T(0); };
-  Win<T> w;
-  w.v0 = fld(s.y0 - 1);
-  w.vp = fld(s.y0);
-  w.l0 = __shfl_up_sync(0xffffffffu, w.v0, 1);
-  w.r0 = __shfl_down_sync(0xffffffffu, w.v0, 1);
-  w.lp = __shfl_up_sync(0xffffffffu, w.vp, 1);
-  w.rp = __shfl_down_sync(0xffffffffu, w.vp, 1);
-  w.kb = kap_at(kap, n, s.c, s.y0 - 1);
-  w.kbl = __shfl_up_sync(0xffffffffu, w.kb, 1);
-  T vn = fld(s.y0 + 1);
-  T kn = kap_at(kap, n, s.c, s.y0);
-  for (int j = s.y0; j < s.y1; ++j) {
-    w.vm = w.v0; w.lm = w.l0; w.rm = w.r0;
-    w.v0 = w.vp; w.l0 = w.lp; w.r0 = w.rp;
-    w.vp = vn;
-    w.lp = __shfl_up_sync(0xffffffffu, vn, 1);
-    w.rp = __shfl_down_sync(0xffffffffu, vn, 1);
-    w.ka = w.kb; w.kal = w.kbl;
-    w.kb = kn;
-    w.kbl = __shfl_up_sync(0xffffffffu, kn, 1);
-    if (j + 1 < s.y1) {          // fetch the next rows before consuming this one
-      vn = fld(j + 2);
-      kn = kap_at(kap, n, s.c, j + 1);
+  if constexpr (!C) {
+    const T* __restrict__ kap = src;
+    Win<T> w;
+    w.v0 = fld(s.y0 - 1);
+    w.vp = fld(s.y0);
+    w.l0 = __shfl_up_sync(0xffffffffu, w.v0, 1);
+    w.r0 = __shfl_down_sync(0xffffffffu, w.v0, 1);
+    w.lp = __shfl_up_sync(0xffffffffu, w.vp, 1);
+    w.rp = __shfl_down_sync(0xffffffffu, w.vp, 1);
+    w.kb = kap_at(kap, n, s.c, s.y0 - 1);
+    w.kbl = __shfl_up_sync(0xffffffffu, w.kb, 1);
+    T vn = fld(s.y0 + 1);
+    T kn = kap_at(kap, n, s.c, s.y0);
+    for (int j = s.y0; j < s.y1; ++j) {
+      w.vm = w.v0; w.lm = w.l0; w.rm = w.r0;
+      w.v0 = w.vp; w.l0 = w.lp; w.r0 = w.rp;
+      w.vp = vn;
+      w.lp = __shfl_up_sync(0xffffffffu, vn, 1);
+      w.rp = __shfl_down_sync(0xffffffffu, vn, 1);
+      w.ka = w.kb; w.kal = w.kbl;
+      w.kb = kn;
+      w.kbl = __shfl_up_sync(0xffffffffu, kn, 1);
+      if (j + 1 < s.y1) {          // fetch the next rows before consuming this one
+        vn = fld(j + 2);
+        kn = kap_at(kap, n, s.c, j + 1);
+      }
+      if (s.out) out(j, w.v0, interior2(n, s.c, j) ? stencil_win(w) : T(0));
     }
-    if (s.out) out(j, w);
+  } else {
+    const T* __restrict__ cd = src;
+    const T* __restrict__ ce = src + ns;
+    const T* __restrict__ cn = src + 2 * ns;
+    const T* __restrict__ q = src + 3 * ns;
+    const int N1 = n + 1;
+    auto node = [&](const T* __restrict__ a, int j) -> T {
+      return (s.c <= n && j >= 0 && j <= n) ? __ldg(a + (int64_t)j * N1 + s.c) : T(0);
+    };
+    WinC<T> w;
+    w.v0 = fld(s.y0 - 1);
+    w.vp = fld(s.y0);
+    w.l0 = __shfl_up_sync(0xffffffffu, w.v0, 1);
+    w.r0 = __shfl_down_sync(0xffffffffu, w.v0, 1);
+    w.lp = __shfl_up_sync(0xffffffffu, w.vp, 1);
+    w.rp = __shfl_down_sync(0xffffffffu, w.vp, 1);
+    w.qb = kap_at(q, n, s.c, s.y0 - 1);
+    w.qbl = __shfl_up_sync(0xffffffffu, w.qb, 1);
+    T vn = fld(s.y0 + 1);
+    T qn = kap_at(q, n, s.c, s.y0);
+    T cn_prev = node(cn, s.y0 - 1);
+    T cdn = node(cd, s.y0), cen = node(ce, s.y0), cnn = node(cn, s.y0);
+    for (int j = s.y0; j < s.y1; ++j) {
+      w.vm = w.v0; w.lm = w.l0; w.rm = w.r0;
+      w.v0 = w.vp; w.l0 = w.lp; w.r0 = w.rp;
+      w.vp = vn;
+      w.lp = __shfl_up_sync(0xffffffffu, vn, 1);
+      w.rp = __shfl_down_sync(0xffffffffu, vn, 1);
+      w.qa = w.qb; w.qal = w.qbl;
+      w.qb = qn;
+      w.qbl = __shfl_up_sync(0xffffffffu, qn, 1);
+      w.cd = cdn;
+      w.ce = cen;
+      w.ceW = __shfl_up_sync(0xffffffffu, cen, 1);
+      w.cnN = cnn;
+      w.cnS = cn_prev;
+      cn_prev = cnn;
+      if (j + 1 < s.y1) {          // fetch the next rows before consuming this one
+        vn = fld(j + 2);
+        qn = kap_at(q, n, s.c, j + 1);
+        cdn = node(cd, j + 1);
+        cen = node(ce, j + 1);
+        cnn = node(cn, j + 1);
+      }
+      if (s.out) out(j, w.v0, interior2(n, s.c, j) ? stencil_coef(w) : T(0));
+    }
   }
 }
 
@@ -160,17 +239,16 @@ __global__ void __launch_bounds__(SBLOCK) k_apply2(Grid g, const T* __restrict__
   const int64_t b = blockIdx.z;
   const T* x = X + b * g.ns;
   T* y = Y + b * g.ns;
-  stream_strip<T>(s, K + b * g.es,
-                  [&](int c, int j) { return __ldg(x + (int64_t)j * s.N1 + c); },
-                  [&](int j, const Win<T>& w) {
-                    y[(int64_t)j * s.N1 + s.c] = interior2(s.n, s.c, j) ? stencil_win(w) : T(0);
-                  });
+  stream_strip<T, false>(s, K + b * g.es, g.ns,
+                         [&](int c, int j) { return __ldg(x + (int64_t)j * s.N1 + c); },
+                         [&](int j, T, T ax) { y[(int64_t)j * s.N1 + s.c] = ax; });
   prof_tick(prof);
 }
 
 // p_new = z + beta p_old (beta == 0: p_new = z), q = A p_new, partials of p.q
-template <class T>
-__global__ void __launch_bounds__(SBLOCK) k_pq2(Grid g, const T* __restrict__ K,
+// (K: kappa, or with C the coefficient blocks, cs doubles per sample)
+template <class T, bool C>
+__global__ void __launch_bounds__(SBLOCK) k_pq2(Grid g, const T* __restrict__ K, int64_t cs,
                                                 const T* __restrict__ Z, const T* __restrict__ Pold,
                                                 T* __restrict__ Pnew, T* __restrict__ Q,
                                                 const double* __restrict__ beta,
@@ -185,20 +263,17 @@ __global__ void __launch_bounds__(SBLOCK) k_pq2(Grid g, const T* __restrict__ K,
   T* pn = Pnew + b * g.ns;
   T* q = Q + b * g.ns;
   T dot = T(0);
-  auto out = [&](int j, const Win<T>& w) {
+  auto out = [&](int j, T pv, T ax) {
     const int64_t o = (int64_t)j * s.N1 + s.c;
-    T qv = T(0);
-    if (interior2(s.n, s.c, j)) {
-      qv = stencil_win(w);
-      dot = fma(w.v0, qv, dot);
-    }
-    pn[o] = w.v0;
-    q[o] = qv;
+    dot = fma(pv, ax, dot);
+    pn[o] = pv;
+    q[o] = ax;
   };
+  const T* src = K + b * cs;
   if (bb == T(0)) {
-    stream_strip<T>(s, K + b * g.es, [&](int c, int j) { return __ldg(z + (int64_t)j * s.N1 + c); }, out);
+    stream_strip<T, C>(s, src, g.ns, [&](int c, int j) { return __ldg(z + (int64_t)j * s.N1 + c); }, out);
   } else {
-    stream_strip<T>(s, K + b * g.es, [&](int c, int j) {
+    stream_strip<T, C>(s, src, g.ns, [&](int c, int j) {
       const int64_t o = (int64_t)j * s.N1 + c;
       return fma(bb, __ldg(po + o), __ldg(z + o));
     }, out);
@@ -208,8 +283,8 @@ __global__ void __launch_bounds__(SBLOCK) k_pq2(Grid g, const T* __restrict__ K,
 }
 
 // Pre-smoothing from zero and residual: e = W b, r1 = b - A e.
-template <class T>
-__global__ void __launch_bounds__(SBLOCK) k_mgpre2(Grid g, const T* __restrict__ K,
+template <class T, bool C>
+__global__ void __launch_bounds__(SBLOCK) k_mgpre2(Grid g, const T* __restrict__ K, int64_t cs,
                                                    const T* __restrict__ W,
                                                    const T* __restrict__ Bv, T* __restrict__ E,
                                                    T* __restrict__ R1,
@@ -221,21 +296,17 @@ __global__ void __launch_bounds__(SBLOCK) k_mgpre2(Grid g, const T* __restrict__
   const T* bv = Bv + b * g.ns;
   T* e = E + b * g.ns;
   T* r1 = R1 + b * g.ns;
-  stream_strip<T>(s, K + b * g.es,
-                  [&](int c, int j) {
-                    const int64_t o = (int64_t)j * s.N1 + c;
-                    return __ldg(w_ + o) * __ldg(bv + o);
-                  },
-                  [&](int j, const Win<T>& w) {
-                    const int64_t o = (int64_t)j * s.N1 + s.c;
-                    T ev = T(0), rv = T(0);
-                    if (interior2(s.n, s.c, j)) {
-                      ev = w.v0;
-                      rv = __ldg(bv + o) - stencil_win(w);
-                    }
-                    e[o] = ev;
-                    r1[o] = rv;
-                  });
+  stream_strip<T, C>(s, K + b * cs, g.ns,
+                     [&](int c, int j) {
+                       const int64_t o = (int64_t)j * s.N1 + c;
+                       return __ldg(w_ + o) * __ldg(bv + o);
+                     },
+                     [&](int j, T ev, T ax) {
+                       const int64_t o = (int64_t)j * s.N1 + s.c;
+                       const bool in = interior2(s.n, s.c, j);
+                       e[o] = ev;
+                       r1[o] = in ? __ldg(bv + o) - ax : T(0);
+                     });
   prof_tick(prof);
 }
 
@@ -254,8 +325,8 @@ __device__ __forceinline__ T prolong2(const T* __restrict__ Ec, int nc, int i, i
 }
 
 // out = e' + W (b - A e'), e' = e + P ec; partials of b.out when part != nullptr.
-template <class T>
-__global__ void __launch_bounds__(SBLOCK) k_mgpost2(Grid g, int64_t nsc, const T* __restrict__ K,
+template <class T, bool C>
+__global__ void __launch_bounds__(SBLOCK) k_mgpost2(Grid g, int64_t nsc, const T* __restrict__ K, int64_t cs,
                                                     const T* __restrict__ W,
                                                     const T* __restrict__ Bv,
                                                     const T* __restrict__ E,
@@ -272,26 +343,27 @@ __global__ void __launch_bounds__(SBLOCK) k_mgpost2(Grid g, int64_t nsc, const T
   const T* bv = Bv + b * g.ns;
   T* out = Out + b * g.ns;
   T dot = T(0);
-  stream_strip<T>(s, K + b * g.es,
-                  [&](int c, int j) {
-                    return __ldg(e + (int64_t)j * s.N1 + c) + prolong2(ec, nc, c, j);
-                  },
-                  [&](int j, const Win<T>& w) {
-                    const int64_t o = (int64_t)j * s.N1 + s.c;
-                    T ov = T(0);
-                    if (interior2(s.n, s.c, j)) {
-                      const T bval = __ldg(bv + o);
-                      ov = fma(__ldg(w_ + o), bval - stencil_win(w), w.v0);
-                      dot = fma(bval, ov, dot);
-                    }
-                    out[o] = ov;
-                  });
+  stream_strip<T, C>(s, K + b * cs, g.ns,
+                     [&](int c, int j) {
+                       return __ldg(e + (int64_t)j * s.N1 + c) + prolong2(ec, nc, c, j);
+                     },
+                     [&](int j, T ev, T ax) {
+                       const int64_t o = (int64_t)j * s.N1 + s.c;
+                       T ov = T(0);
+                       if (interior2(s.n, s.c, j)) {
+                         const T bval = __ldg(bv + o);
+                         ov = fma(__ldg(w_ + o), bval - ax, ev);
+                         dot = fma(bval, ov, dot);
+                       }
+                       out[o] = ov;
+                     });
   if (part) warp_partial(dot, part, s.part_idx);
   prof_tick(prof);
 }
 
 // Mixed form, outer FP64 residual: r = b - A(kappa) u (b_i = h^2), partials of r.r.
-__global__ void __launch_bounds__(SBLOCK) k_resid2(Grid g, const double* __restrict__ K,
+template <bool C>
+__global__ void __launch_bounds__(SBLOCK) k_resid2(Grid g, const double* __restrict__ K, int64_t cs,
                                                    const double* __restrict__ U,
                                                    double* __restrict__ R,
                                                    const int32_t* __restrict__ active,
@@ -303,18 +375,51 @@ __global__ void __launch_bounds__(SBLOCK) k_resid2(Grid g, const double* __restr
   const double* u = U + b * g.ns;
   double* r = R + b * g.ns;
   double dot = 0.0;
-  stream_strip<double>(s, K + b * g.es,
-                       [&](int c, int j) { return __ldg(u + (int64_t)j * s.N1 + c); },
-                       [&](int j, const Win<double>& w) {
-                         double rv = 0.0;
-                         if (interior2(s.n, s.c, j)) {
-                           rv = h2 - stencil_win(w);
-                           dot = fma(rv, rv, dot);
-                         }
-                         r[(int64_t)j * s.N1 + s.c] = rv;
-                       });
+  stream_strip<double, C>(s, K + b * cs, g.ns,
+                          [&](int c, int j) { return __ldg(u + (int64_t)j * s.N1 + c); },
+                          [&](int j, double, double ax) {
+                            double rv = 0.0;
+                            if (interior2(s.n, s.c, j)) {
+                              rv = h2 - ax;
+                              dot = fma(rv, rv, dot);
+                            }
+                            r[(int64_t)j * s.N1 + s.c] = rv;
+                          });
   warp_partial(dot, part, s.part_idx);
   prof_tick(prof);
+}
+
+// Coefficient blocks of the FP64 2D operator (see WinC): per sample
+// cd, ce, cn at every node (kappa outside the mesh counts as 0), then
+// q = -kappa/3 per element.
+template <class T>
+__global__ void __launch_bounds__(FLAT_THREADS) k_coef2(Grid g, const T* __restrict__ K,
+                                                        T* __restrict__ Cb, int64_t cs) {
+  const int64_t b = blockIdx.y;
+  const int n = g.n, N1 = n + 1;
+  const int64_t nn = (int64_t)N1 * N1, ne = (int64_t)n * n;
+  const T* k = K + b * g.es;
+  T* cd = Cb + b * cs;
+  T* ce = cd + g.ns;
+  T* cn = cd + 2 * g.ns;
+  T* q = cd + 3 * g.ns;
+  const int64_t e0 = (int64_t)blockIdx.x * FLAT_ELEMS;
+  const int64_t e1 = min(e0 + (int64_t)FLAT_ELEMS, g.ns);
+  for (int64_t e = e0 + threadIdx.x; e < e1; e += FLAT_THREADS) {
+    T d = T(0), xe = T(0), xn = T(0);
+    if (e < nn) {
+      const int ei = (int)e, j = ei / N1, i = ei - j * N1;
+      const T ksw = kap_at(k, n, i - 1, j - 1), kse = kap_at(k, n, i, j - 1);
+      const T knw = kap_at(k, n, i - 1, j), kne = kap_at(k, n, i, j);
+      if (interior2(n, i, j)) d = Consts<T>::c23 * ((ksw + kse) + (knw + kne));
+      xe = -Consts<T>::c16 * (kse + kne);
+      xn = -Consts<T>::c16 * (knw + kne);
+    }
+    cd[e] = d;
+    ce[e] = xe;
+    cn[e] = xn;
+    if (e < g.es) q[e] = e < ne ? -Consts<T>::c13 * __ldg(k + e) : T(0);
+  }
 }
 
 // ------------------------------------------------------------ flat kernels
@@ -652,10 +757,24 @@ cudaError_t pcg_init(cudaStream_t s, const Grid& g, T* x, T* r, int64_t B, Prof 
   return cudaGetLastError();
 }
 
+// The coefficient-block stride per sample (node arrays cd, ce, cn, then q).
+inline int64_t coef_stride(const Grid& g) { return 3 * g.ns + g.es; }
+
+template <class T>
+cudaError_t coef(cudaStream_t s, const Grid& g, const T* kappa, T* coef, int64_t B) {
+  k_coef2<T><<<fgrid(g, B), FLAT_THREADS, 0, s>>>(g, kappa, coef, coef_stride(g));
+  return cudaGetLastError();
+}
+
 template <class T>
 cudaError_t pcg_pq(cudaStream_t s, const Grid& g, const T* kappa, const T* z, const T* p_old,
-                   T* p_new, T* q, const Scalars& sc, double* part, int64_t B, Prof p) {
-  k_pq2<T><<<sgrid(g, B), SBLOCK, 0, s>>>(g, kappa, z, p_old, p_new, q, sc.beta, sc.active, part, p);
+                   T* p_new, T* q, const Scalars& sc, double* part, int64_t B, Prof p, const T* coef) {
+  if (coef)
+    k_pq2<T, true><<<sgrid(g, B), SBLOCK, 0, s>>>(g, coef, coef_stride(g), z, p_old, p_new, q, sc.beta,
+                                                  sc.active, part, p);
+  else
+    k_pq2<T, false><<<sgrid(g, B), SBLOCK, 0, s>>>(g, kappa, g.es, z, p_old, p_new, q, sc.beta, sc.active,
+                                                   part, p);
   return cudaGetLastError();
 }
 
@@ -675,8 +794,11 @@ cudaError_t jacobi_z(cudaStream_t s, const Grid& g, const T* winv, const T* r, T
 
 template <class T>
 cudaError_t mg_pre(cudaStream_t s, const Grid& g, const T* kappa, const T* w, const T* b, T* e,
-                   T* r1, const int32_t* active, int64_t B, Prof p) {
-  k_mgpre2<T><<<sgrid(g, B), SBLOCK, 0, s>>>(g, kappa, w, b, e, r1, active, p);
+                   T* r1, const int32_t* active, int64_t B, Prof p, const T* coef) {
+  if (coef)
+    k_mgpre2<T, true><<<sgrid(g, B), SBLOCK, 0, s>>>(g, coef, coef_stride(g), w, b, e, r1, active, p);
+  else
+    k_mgpre2<T, false><<<sgrid(g, B), SBLOCK, 0, s>>>(g, kappa, g.es, w, b, e, r1, active, p);
   return cudaGetLastError();
 }
 
@@ -697,8 +819,13 @@ cudaError_t coarse_solve(cudaStream_t s, const Grid& g, const T* kappa, const T*
 template <class T>
 cudaError_t mg_post(cudaStream_t s, const Grid& g, const Grid& coarse, const T* kappa, const T* w,
                     const T* b, const T* e, const T* ec, T* out, const int32_t* active,
-                    double* part, int64_t B, Prof p) {
-  k_mgpost2<T><<<sgrid(g, B), SBLOCK, 0, s>>>(g, coarse.ns, kappa, w, b, e, ec, out, active, part, p);
+                    double* part, int64_t B, Prof p, const T* coef) {
+  if (coef)
+    k_mgpost2<T, true><<<sgrid(g, B), SBLOCK, 0, s>>>(g, coarse.ns, coef, coef_stride(g), w, b, e, ec, out,
+                                                      active, part, p);
+  else
+    k_mgpost2<T, false><<<sgrid(g, B), SBLOCK, 0, s>>>(g, coarse.ns, kappa, g.es, w, b, e, ec, out,
+                                                       active, part, p);
   return cudaGetLastError();
 }
 
@@ -710,8 +837,12 @@ cudaError_t qoi(cudaStream_t s, const Grid& g, int box, int L, int H, double inv
 }
 
 cudaError_t resid64(cudaStream_t s, const Grid& g, const double* kappa, const double* u,
-                    double* r, const int32_t* active, double* part, int64_t B, Prof p) {
-  k_resid2<<<sgrid(g, B), SBLOCK, 0, s>>>(g, kappa, u, r, active, part, p);
+                    double* r, const int32_t* active, double* part, int64_t B, Prof p,
+                    const double* coef) {
+  if (coef)
+    k_resid2<true><<<sgrid(g, B), SBLOCK, 0, s>>>(g, coef, coef_stride(g), u, r, active, part, p);
+  else
+    k_resid2<false><<<sgrid(g, B), SBLOCK, 0, s>>>(g, kappa, g.es, u, r, active, part, p);
   return cudaGetLastError();
 }
 
@@ -734,20 +865,21 @@ cudaError_t add_correction(cudaStream_t s, const Grid& g, double* u, const float
   template cudaError_t winv<T>(cudaStream_t, const Grid&, const T*, double, T*, int64_t);          \
   template cudaError_t pcg_init<T>(cudaStream_t, const Grid&, T*, T*, int64_t, Prof);              \
   template cudaError_t pcg_pq<T>(cudaStream_t, const Grid&, const T*, const T*, const T*, T*, T*,  \
-                                 const Scalars&, double*, int64_t, Prof);                          \
+                                 const Scalars&, double*, int64_t, Prof, const T*);                \
+  template cudaError_t coef<T>(cudaStream_t, const Grid&, const T*, T*, int64_t);                  \
   template cudaError_t pcg_xr<T>(cudaStream_t, const Grid&, T*, const T*, T*, const T*,            \
                                  const Scalars&, double*, int64_t, Prof);                          \
   template cudaError_t jacobi_z<T>(cudaStream_t, const Grid&, const T*, const T*, T*,              \
                                    const Scalars&, double*, int64_t, Prof);                        \
   template cudaError_t mg_pre<T>(cudaStream_t, const Grid&, const T*, const T*, const T*, T*, T*,  \
-                                 const int32_t*, int64_t, Prof);                                   \
+                                 const int32_t*, int64_t, Prof, const T*);                         \
   template cudaError_t restrict_<T>(cudaStream_t, const Grid&, const Grid&, const T*, T*,          \
                                     const int32_t*, int64_t, Prof);                                \
   template cudaError_t coarse_solve<T>(cudaStream_t, const Grid&, const T*, const T*, T*,          \
                                        const int32_t*, int64_t);                                   \
   template cudaError_t mg_post<T>(cudaStream_t, const Grid&, const Grid&, const T*, const T*,      \
                                   const T*, const T*, const T*, T*, const int32_t*, double*,       \
-                                  int64_t, Prof);                                                  \
+                                  int64_t, Prof, const T*);                                        \
   template cudaError_t qoi<T>(cudaStream_t, const Grid&, int, int, int, double, const T*, double*, \
                               int64_t, Prof);
 
