@@ -230,13 +230,22 @@ __global__ void __launch_bounds__(ZTHREADS, 2) k_zm3(Grid g, const T* __restrict
   }
   const bool ex = i == n - 1 && n % ZTX == 0;
   const T c3 = T(g.c3), c12 = T(g.c12);
-  T a0[ZRY], a1[ZRY], vc[ZRY];   // outputs of planes p - 1 and p so far; x at plane p - 1
+  // Per output row: U = unscaled coupling sum and D = (sum of the 8 kappa) x
+  // centre of the output of plane p - 1 so far, N = the couplings of the
+  // output of plane p with plane p - 1; output = c3 D - c12 U. Pair sums of a
+  // kappa layer (X: along x per element row, Y: along y per column, S: the 4
+  // elements around an output row) are formed once per layer and reused by
+  // both rows and by the next plane; every coupling is one FMA into U.
+  T U[ZRY], D[ZRY], N[ZRY], vc[ZRY];
   typename Epi::Pre pre[ZRY];    // epilogue inputs of plane p - 1
 #pragma unroll
-  for (int r = 0; r < ZRY; ++r) a0[r] = a1[r] = vc[r] = T(0);
+  for (int r = 0; r < ZRY; ++r) U[r] = D[r] = N[r] = vc[r] = T(0);
   T kb[ZRY + 1][2];              // kappa layer p - 1, element rows j0 - 1 .. j0 + ZRY - 1
+  T Xb[ZRY + 1], Yb[ZRY][2], Sb[ZRY];
 #pragma unroll
-  for (int r = 0; r <= ZRY; ++r) kb[r][0] = kb[r][1] = T(0);
+  for (int r = 0; r <= ZRY; ++r) kb[r][0] = kb[r][1] = Xb[r] = T(0);
+#pragma unroll
+  for (int r = 0; r < ZRY; ++r) Yb[r][0] = Yb[r][1] = Sb[r] = T(0);
   T dot = T(0);
   const int vbase = (ZRY * threadIdx.y + 1) * ZSX + threadIdx.x + 1;
   const int kbase = ZRY * threadIdx.y * ZKX + threadIdx.x;
@@ -264,11 +273,32 @@ __global__ void __launch_bounds__(ZTHREADS, 2) k_zm3(Grid g, const T* __restrict
     for (int r = 0; r <= ZRY; ++r)
 #pragma unroll
       for (int a = 0; a < 2; ++a) ka[r][a] = skb[kbase + r * ZKX + a];
+    T Xa[ZRY + 1], Ya[ZRY][2], Sa[ZRY];
+#pragma unroll
+    for (int r = 0; r <= ZRY; ++r) Xa[r] = ka[r][0] + ka[r][1];
+#pragma unroll
+    for (int r = 0; r < ZRY; ++r) {
+      Ya[r][0] = ka[r][0] + ka[r + 1][0];
+      Ya[r][1] = ka[r][1] + ka[r + 1][1];
+      Sa[r] = Xa[r] + Xa[r + 1];
+    }
     const int m = p - 1;
 #pragma unroll
     for (int r = 0; r < ZRY; ++r) {
-      // output (i, j0 + r, p - 1) is complete
-      const T done = a0[r] - c12 * across3(kb[r], kb[r + 1], v[r], v[r + 1], v[r + 2]);
+      const T* v0 = v[r];
+      const T* v1 = v[r + 1];
+      const T* v2 = v[r + 2];
+      // couplings of output p - 1 with plane p across layer p - 1: complete
+      T u = U[r];
+      u = fma(Yb[r][0], v1[0], u);
+      u = fma(Yb[r][1], v1[2], u);
+      u = fma(Xb[r], v0[1], u);
+      u = fma(Xb[r + 1], v2[1], u);
+      u = fma(kb[r][0], v0[0], u);
+      u = fma(kb[r][1], v0[2], u);
+      u = fma(kb[r + 1][0], v2[0], u);
+      u = fma(kb[r + 1][1], v2[2], u);
+      const T done = fma(-c12, u, c3 * D[r]);
       if (cvalid[r] && m >= t.z0) {
         const int o = m * P + ocol[r];
         dot += epi(o, cint[r] && m >= 1 && m < n, done, vc[r], pre[r]);
@@ -276,15 +306,38 @@ __global__ void __launch_bounds__(ZTHREADS, 2) k_zm3(Grid g, const T* __restrict
         if (ey[r]) epi.zero(o + N1);
         if (ex && ey[r]) epi.zero(o + N1 + 1);
       }
-      a0[r] = a1[r] + inplane3(kb[r], kb[r + 1], ka[r], ka[r + 1], v[r], v[r + 1], v[r + 2], c3, c12);
-      a1[r] = -c12 * across3(ka[r], ka[r + 1], v[r], v[r + 1], v[r + 2]);
-      vc[r] = v[r + 1][1];
+      // output p: couplings with plane p - 1 (N) and the in-plane diagonal
+      // edges (free axis z: one kappa of each layer), and the diagonal part
+      u = N[r];
+      u = fma(kb[r][0] + ka[r][0], v0[0], u);
+      u = fma(kb[r][1] + ka[r][1], v0[2], u);
+      u = fma(kb[r + 1][0] + ka[r + 1][0], v2[0], u);
+      u = fma(kb[r + 1][1] + ka[r + 1][1], v2[2], u);
+      U[r] = u;
+      D[r] = (Sb[r] + Sa[r]) * v1[1];
+      // output p + 1: couplings with plane p across layer p
+      u = Ya[r][0] * v1[0];
+      u = fma(Ya[r][1], v1[2], u);
+      u = fma(Xa[r], v0[1], u);
+      u = fma(Xa[r + 1], v2[1], u);
+      u = fma(ka[r][0], v0[0], u);
+      u = fma(ka[r][1], v0[2], u);
+      u = fma(ka[r + 1][0], v2[0], u);
+      N[r] = fma(ka[r + 1][1], v2[2], u);
+      vc[r] = v1[1];
       pre[r] = nxt[r];
     }
 #pragma unroll
     for (int r = 0; r <= ZRY; ++r) {
       kb[r][0] = ka[r][0];
       kb[r][1] = ka[r][1];
+      Xb[r] = Xa[r];
+    }
+#pragma unroll
+    for (int r = 0; r < ZRY; ++r) {
+      Yb[r][0] = Ya[r][0];
+      Yb[r][1] = Ya[r][1];
+      Sb[r] = Sa[r];
     }
     buf ^= 1;
   }
