@@ -120,32 +120,6 @@ constexpr int ZSLOTS = ((ZNV > ZNK ? ZNV : ZNK) + ZTHREADS - 1) / ZTHREADS;
 static_assert(ZNV <= ZSLOTS * ZTHREADS && ZNK <= ZSLOTS * ZTHREADS, "staging slots per thread");
 static_assert(ZTHREADS == BX * BY, "the z-march CTA has the node-tile thread count");
 
-// Couplings of output node c with the 8 nodes of an adjacent plane across
-// the kappa layer K between them (K[b][a]: element at x-offset a - 1, y-offset
-// b - 1 from c; v[dy + 1][dx + 1]): edge neighbours (one in-plane offset
-// zero) take the two shared kappa, corners the one; the face neighbour
-// (0, 0) is not coupled. Returns the sum without the -h/12 factor.
-template <class T>
-__device__ __forceinline__ T across3(const T* K0, const T* K1, const T* v0, const T* v1, const T* v2) {
-  const T edges = ((K0[0] + K1[0]) * v1[0] + (K0[1] + K1[1]) * v1[2]) +
-                  ((K0[0] + K0[1]) * v0[1] + (K1[0] + K1[1]) * v2[1]);
-  const T corners = (K0[0] * v0[0] + K0[1] * v0[2]) + (K1[0] * v2[0] + K1[1] * v2[2]);
-  return edges + corners;
-}
-
-// In-plane part for output c from its own plane, between the layers below
-// (B0, B1: rows b = 0, 1) and above (A0, A1): the diagonal h/3 sum(8 kappa)
-// and the 4 diagonal edge neighbours (free axis z: one kappa of each layer):
-// h/3 S v_c - h/12 E.
-template <class T>
-__device__ __forceinline__ T inplane3(const T* B0, const T* B1, const T* A0, const T* A1, const T* v0,
-                                      const T* v1, const T* v2, T c3, T c12) {
-  const T s = ((B0[0] + B0[1]) + (B1[0] + B1[1])) + ((A0[0] + A0[1]) + (A1[0] + A1[1]));
-  const T e = ((B0[0] + A0[0]) * v0[0] + (B0[1] + A0[1]) * v0[2]) +
-              ((B1[0] + A1[0]) * v2[0] + (B1[1] + A1[1]) * v2[2]);
-  return c3 * s * v1[1] - c12 * e;
-}
-
 struct ZTile {
   int tx0, ty0, z0, z1;   // column origin; output planes [z0, z1)
 };
@@ -516,30 +490,6 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
-// across3 on pairs: K[b][a] kappa of the layer, v[dy + 1][dx + 1] the plane.
-__device__ __forceinline__ float2 across3p(const float2 K[2][2], const float2 v[3][3]) {
-  float2 e = mul2(add2(K[0][0], K[1][0]), v[1][0]);
-  e = fma2(add2(K[0][1], K[1][1]), v[1][2], e);
-  e = fma2(add2(K[0][0], K[0][1]), v[0][1], e);
-  e = fma2(add2(K[1][0], K[1][1]), v[2][1], e);
-  e = fma2(K[0][0], v[0][0], e);
-  e = fma2(K[0][1], v[0][2], e);
-  e = fma2(K[1][0], v[2][0], e);
-  return fma2(K[1][1], v[2][2], e);
-}
-
-// inplane3 on pairs: h/3 S v_c - h/12 E.
-__device__ __forceinline__ float2 inplane3p(const float2 Kb[2][2], const float2 Ka[2][2],
-                                            const float2 v[3][3], float2 c3, float2 mc12) {
-  const float2 s = add2(add2(add2(Kb[0][0], Kb[0][1]), add2(Kb[1][0], Kb[1][1])),
-                        add2(add2(Ka[0][0], Ka[0][1]), add2(Ka[1][0], Ka[1][1])));
-  float2 e = mul2(add2(Kb[0][0], Ka[0][0]), v[0][0]);
-  e = fma2(add2(Kb[0][1], Ka[0][1]), v[0][2], e);
-  e = fma2(add2(Kb[1][0], Ka[1][0]), v[2][0], e);
-  e = fma2(add2(Kb[1][1], Ka[1][1]), v[2][2], e);
-  return fma2(mc12, e, mul2(mul2(c3, s), v[1][1]));
-}
-
 // Asynchronous 4-byte global -> shared copy to a shared-window address
 // (zero-filled when src_bytes = 0).
 __device__ __forceinline__ void cp_async4s(unsigned sa, const void* gmem, int src_bytes) {
@@ -696,8 +646,14 @@ __global__ void __launch_bounds__(ZTHREADS, 2) k_zm3f(Grid g, const float* __res
   const bool ex = i == n - 1 && n % ZTX == 0;
   const float c3s = (float)g.c3, c12s = (float)g.c12;
   const float2 c3 = make_float2(c3s, c3s), mc12 = make_float2(-c12s, -c12s);
-  float2 a0 = make_float2(0.f, 0.f), a1 = a0, vc = a0;
-  float2 kb[2][2] = {{a0, a0}, {a0, a0}};
+  // as in k_zm3: U unscaled couplings and D diagonal part of the output of
+  // plane p - 1, N couplings of the output of plane p with plane p - 1; the
+  // kappa pair sums of a layer (X along x, Y along y, S of the 4 elements)
+  // are formed once and reused for the next plane
+  const float2 z2 = make_float2(0.f, 0.f);
+  float2 U = z2, D = z2, Nn = z2, vc = z2;
+  float2 kb[2][2] = {{z2, z2}, {z2, z2}};
+  float2 Xb[2] = {z2, z2}, Yb[2] = {z2, z2}, Sb = z2;
   typename Epi::Pre pre[2];
   float dot = 0.0f;
   const int vbase = (threadIdx.y + 1) * ZSX + threadIdx.x + 1;
@@ -730,8 +686,22 @@ __global__ void __launch_bounds__(ZTHREADS, 2) k_zm3f(Grid g, const float* __res
     for (int bq = 0; bq < 2; ++bq)
 #pragma unroll
       for (int a = 0; a < 2; ++a) ka[bq][a] = skb[kbase + bq * ZKX + a];
-    // outputs of plane p - 1 are complete
-    const float2 done = fma2(mc12, across3p(kb, v), a0);
+    float2 Xa[2], Ya[2];
+    Xa[0] = add2(ka[0][0], ka[0][1]);
+    Xa[1] = add2(ka[1][0], ka[1][1]);
+    Ya[0] = add2(ka[0][0], ka[1][0]);
+    Ya[1] = add2(ka[0][1], ka[1][1]);
+    const float2 Sa = add2(Xa[0], Xa[1]);
+    // outputs of plane p - 1 are complete: couplings with plane p across layer p - 1
+    float2 u = fma2(Yb[0], v[1][0], U);
+    u = fma2(Yb[1], v[1][2], u);
+    u = fma2(Xb[0], v[0][1], u);
+    u = fma2(Xb[1], v[2][1], u);
+    u = fma2(kb[0][0], v[0][0], u);
+    u = fma2(kb[0][1], v[0][2], u);
+    u = fma2(kb[1][0], v[2][0], u);
+    u = fma2(kb[1][1], v[2][2], u);
+    const float2 done = fma2(mc12, u, mul2(c3, D));
     const int m = p - 1;
     if (m >= t.z0) {
 #pragma unroll
@@ -744,12 +714,30 @@ __global__ void __launch_bounds__(ZTHREADS, 2) k_zm3f(Grid g, const float* __res
         if (ex && ey[r]) epi.zero(o + N1 + 1);
       }
     }
-    a0 = add2(a1, inplane3p(kb, ka, v, c3, mc12));
-    a1 = mul2(mc12, across3p(ka, v));
+    // output p: couplings with plane p - 1 and the in-plane diagonal edges
+    u = fma2(add2(kb[0][0], ka[0][0]), v[0][0], Nn);
+    u = fma2(add2(kb[0][1], ka[0][1]), v[0][2], u);
+    u = fma2(add2(kb[1][0], ka[1][0]), v[2][0], u);
+    U = fma2(add2(kb[1][1], ka[1][1]), v[2][2], u);
+    D = mul2(add2(Sb, Sa), v[1][1]);
+    // output p + 1: couplings with plane p across layer p
+    u = mul2(Ya[0], v[1][0]);
+    u = fma2(Ya[1], v[1][2], u);
+    u = fma2(Xa[0], v[0][1], u);
+    u = fma2(Xa[1], v[2][1], u);
+    u = fma2(ka[0][0], v[0][0], u);
+    u = fma2(ka[0][1], v[0][2], u);
+    u = fma2(ka[1][0], v[2][0], u);
+    Nn = fma2(ka[1][1], v[2][2], u);
 #pragma unroll
     for (int bq = 0; bq < 2; ++bq)
 #pragma unroll
       for (int a = 0; a < 2; ++a) kb[bq][a] = ka[bq][a];
+    Xb[0] = Xa[0];
+    Xb[1] = Xa[1];
+    Yb[0] = Ya[0];
+    Yb[1] = Ya[1];
+    Sb = Sa;
     vc = v[1][1];
     pre[0] = nxt[0];
     pre[1] = nxt[1];
