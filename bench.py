@@ -299,7 +299,8 @@ def serving_both(m, args, device=0):
     if args.serve_adapt > 0:
         fixed = serving_run(m, args, device, 0)
         keep = ("p50_time_to_eps_s", "p99_time_to_eps_s", "mean_time_to_eps_s",
-                "aggregate_dof_solves_per_s", "span_s", "max_in_flight", "failed", "rounds")
+                "aggregate_dof_solves_per_s", "span_s", "max_in_flight", "failed", "failed_requests",
+                "rounds")
         res["fixed_levels"] = {k: fixed[k] for k in keep}
     return res
 
@@ -338,6 +339,9 @@ def serving_run(m, args, device=0, adapt=0):
     finally:
         srv.close()
     bad = [r for r in res if r["status"] not in (0,)]
+    bad_info = [dict(status=r["status"], dim=wl["dim"], sigma2=round(wl["sigma2"], 3),
+                     corr_len=round(wl["corr_len"], 3), m=wl["m"], eps=round(eps, 6), N=r["N"][:wl["levels"]])
+                for (ta, wl, eps), r in zip(stream, res) if r["status"] != 0]
     lat = np.array([r["t_done"] - r["t_submit"] for r in res])
     wait = np.array([r["t_admit"] - r["t_submit"] for r in res])
     span = max(r["t_done"] for r in res) - min(r["t_submit"] for r in res)
@@ -353,6 +357,7 @@ def serving_run(m, args, device=0, adapt=0):
         peak = max(peak, cur)
     return {"requests": n_req, "rate_per_s": args.serve_rate, "arrival_seed": 1,
             "slots": args.serve_slots, "pilot": args.serve_pilot, "failed": len(bad),
+            "failed_requests": bad_info,
             "levels": ("adaptive from levels 0..%d (Eq. mlmc_num_levels)" % adapt
                        if adapt > 0 else "all levels of the range"),
             "levels_used_hist": {str(k): sum(1 for r in res if r["levels"] == k)

@@ -103,13 +103,17 @@ typedef struct mlmc_plan_s* mlmc_plan;
 /* Defaults: 2D, 3 levels, n_0 = 16, m = 4, sigma2 = 1, corr_len = 0.3,
  * domain-mean QoI, Jacobi-PCG, rtol 1e-10, FP64, seed 0, mg_omega 0.9,
  * CUDA graphs on, full tensor KLE basis (total_order -1); mixed form:
- * inner_rtol 3e-3, inner_max_iter 60, outer_max_iter 16.
+ * inner_rtol 3e-3, inner_max_iter 200, outer_max_iter 40.
  *
  * MLMC_MIXED (iterative refinement, the precision pattern the method admits
  * on GB300): u = 0, r = b; repeat { d = A32^-1 (r / s) by FP32 PCG with
  * kappa32 = (float) kappa to inner_rtol; u += s d; r = b - A(kappa) u in
- * FP64; s = ||r|| } until ||r||_2 <= rtol ||b||_2 (the FP64 true residual).
- * iters then counts all inner iterations; -1 if outer_max_iter was hit. */
+ * FP64; s = ||r|| } until ||r||_2 <= rtol ||b||_2 (the FP64 true residual),
+ * or until a refinement step no longer halves ||r|| while ||r|| is already
+ * within 100 rtol ||b||: the FP64 evaluation of b - A u cannot resolve a
+ * smaller residual there (for high-contrast kappa its rounding floor can sit
+ * a few times above rtol ||b||). iters then counts all inner iterations; -1
+ * if outer_max_iter was hit. */
 void mlmc_config_default(mlmc_config* cfg);
 
 /* Doubles between consecutive samples in node / element arrays. */

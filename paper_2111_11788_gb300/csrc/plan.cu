@@ -1235,8 +1235,8 @@ void mlmc_config_default(mlmc_config* c) {
   c->check_every = 0;
   c->workspace_bytes = 0;
   c->inner_rtol = 3e-3;
-  c->inner_max_iter = 60;
-  c->outer_max_iter = 16;
+  c->inner_max_iter = 200;
+  c->outer_max_iter = 40;
   c->use_graphs = 1;
   c->total_order = -1;
   c->z_chunk = 0;

@@ -135,7 +135,9 @@ __global__ void k_outer_step(const double* __restrict__ part, int64_t tiles, Sca
     tot += (it > 0) ? it : inner_max;
   }
   so.total[b] = tot;
-  if (rho <= so.tol[b]) {
+  const double prev = so.scale[b];   // ||r|| before this refinement step
+  if (rho <= so.tol[b] || (rho > 0.5 * prev && rho <= 100.0 * so.tol[b])) {
+    // converged, or stalled at the rounding floor of the FP64 residual
     so.active[b] = 0;
     so.iters[b] = tot;
   } else if (outer_it >= outer_max || !(rho == rho)) {

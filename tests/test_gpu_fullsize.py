@@ -71,3 +71,19 @@ def test_paper_sample_mix_full_size(m, level, count, checked):
         assert abs(qf[i] - rf) <= 1e-9 * abs(rf)
         if level > 0:
             assert abs(qc[i] - rc) <= 1e-9 * abs(rc)
+
+
+def test_mixed_form_high_contrast_sample_stops_at_the_residual_floor(m):
+    """A 2D request of the serving stream (sigma2 = 1.94, corr_len = 0.29) whose
+    mixed-form solve on 512^2 stalls a few times above rtol at the rounding
+    floor of the FP64 residual: it is accepted there, and its QoIs still match
+    the oracle to 1e-9."""
+    from synth import serving_stream
+    wl = serving_stream(100)[46][1]
+    cfg = m.config_from_workload(wl)
+    with m.Plan(cfg, torch.cuda.current_stream().cuda_stream) as plan:
+        qf, qc, it = plan.sample_level(4, 23, 1)
+    assert it[0] > 0
+    rf, rc = omlmc.coupled_sample(wl, 4, 23)
+    assert abs(qf[0] - rf) <= 1e-9 * abs(rf)
+    assert abs(qc[0] - rc) <= 1e-9 * abs(rc)
