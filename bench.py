@@ -375,19 +375,28 @@ def serving_run(m, args, device=0, adapt=0):
                    "capped 8 (2D) / 7 (3D); GMG-PCG rtol 1e-10, FP32 inner + FP64 refinement"}
 
 
-# FP64 work per algorithmic byte of the FP64 stencil kernels, from their
-# per-node operation counts (read off the kernels) and byte models (nn ~ ne,
-# nc ~ nn / 2^d; bytes per node 42, 40, 40, 24). Per node: the 2D stencil is
-# 17 FP64 instructions (5 adds, 4 multiplies, 8 FMAs = 25 flops), the 3D one
-# 52 instructions (64 flops); mg_post adds the prolongation and the smoothing update with its dot, mg_pre
-# the W b product and the residual, pcg_pq the direction update and the dot,
-# resid64 the residual and its square.
+# FP64 work of the FP64 stencil kernels per output node, counted off the
+# kernels as built (the halo lanes and rows a strip or tile also computes are
+# not counted: they show up as lost efficiency), with the algorithmic bytes
+# per node that the byte counters use (nn ~ ne, nc ~ nn / 2^d).
+# 2D (coefficient form): the operator is 1 multiply + 8 FMAs, or 9 FMAs when
+# a residual f - A x is accumulated from f; mg_post adds the streamed
+# prolongation (1 add on every other row for the coarse row sums, 1 add on
+# odd rows, 1 FMA), the smoothing FMA and the dot (13 instructions, 25
+# flops); mg_pre the W b multiply and the residual stencil (10, 19); pcg_pq
+# the direction FMA, the stencil and the dot (11, 21); resid64 the residual
+# stencil and its square (10, 20).
+# 3D (z-march on kappa): the operator is 32.5 instructions per node (4.5
+# adds for the pair sums of each kappa layer, 8 FMAs + 1 multiply + 1 FMA to
+# complete output p - 1, 4 adds + 4 FMAs + 1 add + 1 multiply for output p,
+# 1 multiply + 7 FMAs for output p + 1; 52.5 flops); the loaders and
+# epilogues add 2 to 3 instructions.
 #   (instructions per node, flops per node, bytes per node)
 FP64_WORK = {
-    (2, "mg_post"): (22.5, 33.0, 42.0), (2, "mg_pre"): (19.0, 27.0, 40.0),
-    (2, "pcg_pq"): (19.0, 29.0, 40.0), (2, "resid64"): (19.0, 28.0, 24.0),
-    (3, "mg_post"): (57.5, 72.0, 41.0), (3, "mg_pre"): (54.0, 66.0, 40.0),
-    (3, "pcg_pq"): (54.0, 68.0, 40.0), (3, "resid64"): (54.0, 67.0, 24.0),
+    (2, "mg_post"): (13.0, 25.0, 42.0), (2, "mg_pre"): (10.0, 19.0, 40.0),
+    (2, "pcg_pq"): (11.0, 21.0, 40.0), (2, "resid64"): (10.0, 20.0, 24.0),
+    (3, "mg_post"): (35.5, 57.5, 41.0), (3, "mg_pre"): (34.5, 54.5, 40.0),
+    (3, "pcg_pq"): (34.5, 56.5, 40.0), (3, "resid64"): (34.5, 55.5, 24.0),
 }
 GB300_SMS = 152
 DFMA_PER_SM_CLK = 2

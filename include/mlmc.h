@@ -86,6 +86,12 @@ typedef struct mlmc_config {
                               the full basis' flat order */
   int32_t z_chunk;         /* 3D: z-planes per stencil CTA (0 = built-in rule:
                               all planes up to 24, else 16); set by mlmc_autotune */
+  int32_t nested_guess;    /* 1 (default): in a coupled batch of level l > 0 the
+                              mesh l-1 solve runs first and its solution,
+                              interpolated (bi/trilinear) to mesh l, is the
+                              initial iterate of the mesh l solve; 0: both
+                              solves start from u = 0. The stopping test
+                              (||r|| <= rtol ||b||) is the same either way. */
 } mlmc_config;
 
 /* Per-level Welford state (Eq. (sample_variance): V = m2 / n). */
@@ -102,11 +108,12 @@ typedef struct mlmc_plan_s* mlmc_plan;
 
 /* Defaults: 2D, 3 levels, n_0 = 16, m = 4, sigma2 = 1, corr_len = 0.3,
  * domain-mean QoI, Jacobi-PCG, rtol 1e-10, FP64, seed 0, mg_omega 0.9,
- * CUDA graphs on, full tensor KLE basis (total_order -1); mixed form:
- * inner_rtol 3e-3, inner_max_iter 200, outer_max_iter 40.
+ * CUDA graphs on, full tensor KLE basis (total_order -1), nested initial
+ * guess on; mixed form: inner_rtol 3e-3, inner_max_iter 200,
+ * outer_max_iter 40.
  *
  * MLMC_MIXED (iterative refinement, the precision pattern the method admits
- * on GB300): u = 0, r = b; repeat { d = A32^-1 (r / s) by FP32 PCG with
+ * on GB300): u = u0 (0, or the nested guess), r = b - A u; repeat { d = A32^-1 (r / s) by FP32 PCG with
  * kappa32 = (float) kappa to inner_rtol; u += s d; r = b - A(kappa) u in
  * FP64; s = ||r|| } until ||r||_2 <= rtol ||b||_2 (the FP64 true residual),
  * or until a refinement step no longer halves ||r|| while ||r|| is already

@@ -184,6 +184,9 @@ cudaError_t to_rhs32(cudaStream_t s, const Grid& g, const double* r, const doubl
                      float* r32, const int32_t* active, int64_t B, Prof p);
 cudaError_t add_correction(cudaStream_t s, const Grid& g, double* u, const float* d32,
                            const double* scale, const int32_t* active, int64_t B, Prof p);
+// nested initial guess: x = P uc (bilinear interpolation from grid `coarse`)
+cudaError_t prolong_guess(cudaStream_t s, const Grid& g, const Grid& coarse, const double* uc,
+                          double* x, const int32_t* active, int64_t B, Prof p);
 }  // namespace d2
 
 // iter_dev (may be null) overrides iter with a device-side iteration counter.
@@ -218,6 +221,9 @@ cudaError_t qoi(cudaStream_t s, const Grid& g, int box, int L, int H, double inv
                 double* part, int64_t B, Prof p);
 cudaError_t resid64(cudaStream_t s, const Grid& g, const double* kappa, const double* u,
                     double* r, const int32_t* active, double* part, int64_t B, Prof p);
+// nested initial guess: x = P uc (trilinear interpolation from grid `coarse`)
+cudaError_t prolong_guess(cudaStream_t s, const Grid& g, const Grid& coarse, const double* uc,
+                          double* x, const int32_t* active, int64_t B, Prof p);
 }  // namespace d3
 
 // Dimension dispatch used by the plan.
@@ -296,6 +302,11 @@ inline cudaError_t to_rhs32(cudaStream_t s, const Grid& g, const double* r, cons
 inline cudaError_t add_correction(cudaStream_t s, const Grid& g, double* u, const float* d32,
                                   const double* scale, const int32_t* active, int64_t B, Prof p) {
   return d2::add_correction(s, g, u, d32, scale, active, B, p);
+}
+inline cudaError_t prolong_guess(cudaStream_t s, const Grid& g, const Grid& coarse, const double* uc,
+                                 double* x, const int32_t* active, int64_t B, Prof p) {
+  return g.dim == 2 ? d2::prolong_guess(s, g, coarse, uc, x, active, B, p)
+                    : d3::prolong_guess(s, g, coarse, uc, x, active, B, p);
 }
 }  // namespace op
 

@@ -172,33 +172,52 @@ void carve_mixed(Carve& c, const MeshInfo& mi, int64_t B, MixedWs& w) {
   carve_solve(c, mi, B, true, w.in);
 }
 
-// Workspace of one coupled batch: xi, outputs and the solve views of the
-// finer mesh (the coarse solve reuses them).
+// Workspace of one coupled batch: xi, outputs, the coarse solution that
+// seeds the fine solve (nested initial guess; guess_ns doubles per sample,
+// 0 when unused) and the solve views of the finer mesh (the coarse solve
+// reuses them).
 struct CoupledWs {
   double* xi;
   double* qf;
   double* qc;
   int32_t* itf;
   int32_t* itc;
+  double* uc;           // coarse-mesh solution (nested guess) or null
   double* kap;          // FP64 kappa of the mesh being solved
   SolveWs<double> s;    // FP64 form
   MixedWs mx;           // mixed form
 };
 
-void carve_coupled(Carve& c, const MeshInfo& mi, int M, int64_t B, bool mixed, CoupledWs& w) {
+// side: 0 for the solve on mesh `level`, 1 for mesh `level - 1`. The two
+// solves share the region after the prefix; their loop-execution counters,
+// which are read after both have run, live in the prefix.
+void carve_coupled(Carve& c, const MeshInfo& mi, int M, int64_t B, bool mixed, int64_t guess_ns,
+                   int side, CoupledWs& w) {
   w.xi = c.take<double>(B * M);
   w.qf = c.take<double>(B);
   w.qc = c.take<double>(B);
   w.itf = c.take<int32_t>(B);
   w.itc = c.take<int32_t>(B);
+  int32_t* execs = c.take<int32_t>(4);
+  w.uc = guess_ns > 0 ? c.take<double>(B * guess_ns) : nullptr;
   if (mixed) {
     carve_mixed(c, mi, B, w.mx);
     w.kap = w.mx.kap64;
+    w.mx.outer_execs = execs ? execs + 2 * side : nullptr;
+    w.mx.in.execs = execs ? execs + 2 * side + 1 : nullptr;
   } else {
     carve_solve(c, mi, B, true, w.s);
     w.kap = w.s.kap[0];
+    w.s.execs = execs ? execs + 2 * side : nullptr;
   }
 }
+
+// Nested initial guess of a fine-mesh solve: the coarse-mesh solution of
+// the same sample (uc, on grid gc), or none (uc == nullptr: x0 = 0).
+struct Guess {
+  const double* uc = nullptr;
+  Grid gc{};
+};
 
 struct PendingEvent {
   int kid;
@@ -264,8 +283,10 @@ struct mlmc_plan_s {
   double ms[NUM_KERNELS] = {0};
   int64_t kl[NUM_KERNELS] = {0};
   int64_t launches = 0;
-  // graph-captured solves, keyed by (form, mesh, batch, workspace)
-  std::map<std::tuple<int, int, int64_t, const void*, const void*, const void*, const void*>,
+  // graph-captured solves, keyed by (form, mesh, batch, workspace) and the
+  // arrays they bake in (kappa, solution, QoI, iteration counts, guess)
+  std::map<std::tuple<int, int, int64_t, const void*, const void*, const void*, const void*,
+                      const void*, const void*>,
            struct GraphRec> graphs;
   // whole allocation rounds (one branch per level), keyed by form, batch
   // counts and first sample indices
@@ -316,7 +337,8 @@ std::vector<int32_t> coef_slots(const mlmc_config* c) {
 }
 
 mlmc_status validate(const mlmc_config* c) {
-  if (c && (c->total_order < -1 || c->z_chunk < 0)) return MLMC_ERR_INVALID;
+  if (c && (c->total_order < -1 || c->z_chunk < 0 || (c->nested_guess != 0 && c->nested_guess != 1)))
+    return MLMC_ERR_INVALID;
   if (!c) return MLMC_ERR_INVALID;
   if (c->dim != 2 && c->dim != 3) return MLMC_ERR_INVALID;
   if (c->n_levels < 1 || c->n_levels > 16) return MLMC_ERR_INVALID;
@@ -487,11 +509,18 @@ mlmc_status ensure_pin(mlmc_plan p, size_t bytes) {
 
 bool is_mixed(mlmc_plan p) { return p->cfg.precision == MLMC_MIXED; }
 
-size_t coupled_bytes(const MeshInfo& mi, int M, int64_t B, bool mixed) {
+size_t coupled_bytes(const MeshInfo& mi, int M, int64_t B, bool mixed, int64_t guess_ns) {
   Carve c(nullptr);
   CoupledWs w;
-  carve_coupled(c, mi, M, B, mixed, w);
+  carve_coupled(c, mi, M, B, mixed, guess_ns, 0, w);
   return c.off + 256;
+}
+
+// Node stride of mesh level - 1 when its solution seeds the solve on mesh
+// `level` (nested initial guess), else 0.
+int64_t guess_ns_of(const mlmc_config& c, int level) {
+  if (!c.nested_guess || level <= 0) return 0;
+  return make_grid(c.dim, c.coarse_cells << (level - 1), c.z_chunk).ns;
 }
 
 size_t solve_bytes(const MeshInfo& mi, int64_t B, bool mixed) {
@@ -838,8 +867,25 @@ mlmc_status qoi_of(mlmc_plan p, const Grid& g0, const double* u, double* part, c
   return MLMC_OK;
 }
 
+// u = P uc (the coarse solution interpolated to the fine mesh) and its FP64
+// residual r = b - A u, with per-tile partials of r.r in part.
+mlmc_status init_from_guess(mlmc_plan p, const Grid& g0, const Guess& gs, const double* kappa,
+                            const double* coef, double* u, double* r, const int32_t* active,
+                            double* part, int64_t B) {
+  const double nn0 = nodes_of(g0), ne0 = elems_of(g0);
+  CK(run(p, KID_PCG_INIT, [&] {
+    return op::prolong_guess(p->stream, g0, gs.gc, gs.uc, u, active, B,
+                             prof_for(p, KID_PCG_INIT, (nn0 + nodes_of(gs.gc)) * 8));
+  }));
+  CK(run(p, KID_RESID64, [&] {
+    return op::resid64(p->stream, g0, kappa, u, r, active, part, B,
+                       prof_for(p, KID_RESID64, (2 * nn0 + ne0) * 8), coef);
+  }));
+  return MLMC_OK;
+}
+
 // FP64 form, launch sequences.
-mlmc_status fp64_setup(mlmc_plan p, const MeshInfo& mi, SolveWs<double>& w, int64_t B) {
+mlmc_status fp64_setup(mlmc_plan p, const MeshInfo& mi, SolveWs<double>& w, int64_t B, const Guess& gs) {
   cudaStream_t s = p->stream;
   const mlmc_config& c = p->cfg;
   const Grid& g0 = mi.g[0];
@@ -847,9 +893,14 @@ mlmc_status fp64_setup(mlmc_plan p, const MeshInfo& mi, SolveWs<double>& w, int6
   if (st != MLMC_OK) return st;
   CK(run(p, KID_SETUP, [&] { return launch_scalars_init(s, w.sc, c.rtol * b_norm(c, g0), 0.0, B); }));
   CK(run(p, KID_SETUP, [&] { return launch_set_int(s, w.execs, 0); }));
-  CK(run(p, KID_PCG_INIT, [&] {
-    return op::pcg_init<double>(s, g0, w.x, w.r, B, prof_for(p, KID_PCG_INIT, 2 * nodes_of(g0) * 8));
-  }));
+  if (gs.uc) {
+    st = init_from_guess(p, g0, gs, w.kap[0], w.coef[0], w.x, w.r, w.sc.active, w.part, B);
+    if (st != MLMC_OK) return st;
+  } else {
+    CK(run(p, KID_PCG_INIT, [&] {
+      return op::pcg_init<double>(s, g0, w.x, w.r, B, prof_for(p, KID_PCG_INIT, 2 * nodes_of(g0) * 8));
+    }));
+  }
   return pcg_prologue<double>(p, mi, w, B, c.max_iter);
 }
 
@@ -864,8 +915,8 @@ mlmc_status fp64_epilogue(mlmc_plan p, const MeshInfo& mi, SolveWs<double>& w, i
 // FP64 solve issued into the graph being captured: setup -> while(two PCG
 // iterations + loop control) -> QoI epilogue.
 mlmc_status issue_fp64(mlmc_plan p, const MeshInfo& mi, SolveWs<double>& w, int64_t B,
-                       double* q_dev, int32_t* iters_dev) {
-  mlmc_status st = fp64_setup(p, mi, w, B);
+                       double* q_dev, int32_t* iters_dev, const Guess& gs) {
+  mlmc_status st = fp64_setup(p, mi, w, B, gs);
   if (st != MLMC_OK) return st;
   const MeshInfo* mip = &mi;
   SolveWs<double> wc = w;   // copied into the deferred body (mutable lambda)
@@ -881,21 +932,22 @@ mlmc_status issue_fp64(mlmc_plan p, const MeshInfo& mi, SolveWs<double>& w, int6
 // Leaves u in w.x, writes q (device) and iters (device). With graphs on,
 // the whole solve is one graph: setup -> while(two PCG iterations) -> QoI.
 mlmc_status solve_fp64(mlmc_plan p, int mesh, const MeshInfo& mi, SolveWs<double>& w, int64_t B,
-                       double* q_dev, int32_t* iters_dev) {
+                       double* q_dev, int32_t* iters_dev, const Guess& gs) {
   const mlmc_config& c = p->cfg;
   if (!graphs_on(p)) {
-    mlmc_status st = fp64_setup(p, mi, w, B);
+    mlmc_status st = fp64_setup(p, mi, w, B, gs);
     if (st != MLMC_OK) return st;
     st = pcg_loop<double>(p, mi, w, B, c.max_iter);
     if (st != MLMC_OK) return st;
     return fp64_epilogue(p, mi, w, B, q_dev, iters_dev);
   }
   const auto key = std::make_tuple(0, mesh, B, (const void*)p->ws, (const void*)w.kap[0],
-                                   (const void*)q_dev, (const void*)iters_dev);
+                                   (const void*)w.x, (const void*)q_dev, (const void*)iters_dev,
+                                   (const void*)gs.uc);
   auto it = p->graphs.find(key);
   if (it == p->graphs.end()) {
     GraphRec rec;
-    mlmc_status st = build_graph(p, [&] { return issue_fp64(p, mi, w, B, q_dev, iters_dev); }, &rec);
+    mlmc_status st = build_graph(p, [&] { return issue_fp64(p, mi, w, B, q_dev, iters_dev, gs); }, &rec);
     if (st != MLMC_OK) return st;
     it = p->graphs.emplace(key, rec).first;
   }
@@ -905,7 +957,7 @@ mlmc_status solve_fp64(mlmc_plan p, int mesh, const MeshInfo& mi, SolveWs<double
 }
 
 // Mixed form, launch sequences.
-mlmc_status mixed_setup(mlmc_plan p, const MeshInfo& mi, MixedWs& w, int64_t B) {
+mlmc_status mixed_setup(mlmc_plan p, const MeshInfo& mi, MixedWs& w, int64_t B, const Guess& gs) {
   cudaStream_t s = p->stream;
   const mlmc_config& c = p->cfg;
   const Grid& g0 = mi.g[0];
@@ -918,9 +970,19 @@ mlmc_status mixed_setup(mlmc_plan p, const MeshInfo& mi, MixedWs& w, int64_t B) 
   CK(run(p, KID_SETUP, [&] { return launch_set_int(s, w.outer_it, 1); }));
   CK(run(p, KID_SETUP, [&] { return launch_set_int(s, w.outer_execs, 0); }));
   CK(run(p, KID_SETUP, [&] { return launch_set_int(s, w.in.execs, 0); }));
-  CK(run(p, KID_PCG_INIT, [&] {
-    return op::pcg_init<double>(s, g0, w.u, w.r, B, prof_for(p, KID_PCG_INIT, 2 * nodes_of(g0) * 8));
-  }));
+  if (gs.uc) {
+    st = init_from_guess(p, g0, gs, w.kap64, w.coef64, w.u, w.r, w.outer.active, w.in.part, B);
+    if (st != MLMC_OK) return st;
+    // ||r0|| becomes the scale of the first inner right-hand side
+    CK(run(p, KID_FINALIZE, [&] {
+      return launch_outer_step(s, w.in.part, g0.tiles_s, w.outer, nullptr, c.inner_max_iter, 0,
+                               c.outer_max_iter, B, nullptr);
+    }));
+  } else {
+    CK(run(p, KID_PCG_INIT, [&] {
+      return op::pcg_init<double>(s, g0, w.u, w.r, B, prof_for(p, KID_PCG_INIT, 2 * nodes_of(g0) * 8));
+    }));
+  }
   return MLMC_OK;
 }
 
@@ -974,8 +1036,8 @@ mlmc_status mixed_epilogue(mlmc_plan p, const MeshInfo& mi, MixedWs& w, int64_t 
 // Mixed solve issued into the graph being captured: setup ->
 // while_outer(pre, re-arm inner, while_inner(PCG), post, outer control) -> QoI.
 mlmc_status issue_mixed(mlmc_plan p, const MeshInfo& mi, MixedWs& w, int64_t B, double* q_dev,
-                        int32_t* iters_dev) {
-  mlmc_status st = mixed_setup(p, mi, w, B);
+                        int32_t* iters_dev, const Guess& gs) {
+  mlmc_status st = mixed_setup(p, mi, w, B, gs);
   if (st != MLMC_OK) return st;
   const MeshInfo* mip = &mi;
   MixedWs wc = w;           // copied into the deferred bodies (mutable lambdas)
@@ -1009,11 +1071,11 @@ mlmc_status issue_mixed(mlmc_plan p, const MeshInfo& mi, MixedWs& w, int64_t B, 
 // (kappa32 = rounded kappa64). w.kap64 holds kappa. Leaves u in w.u. With
 // graphs on the whole solve is one graph (issue_mixed).
 mlmc_status solve_mixed(mlmc_plan p, int mesh, const MeshInfo& mi, MixedWs& w, int64_t B,
-                        double* q_dev, int32_t* iters_dev) {
+                        double* q_dev, int32_t* iters_dev, const Guess& gs) {
   cudaStream_t s = p->stream;
   const mlmc_config& c = p->cfg;
   if (!graphs_on(p)) {
-    mlmc_status st = mixed_setup(p, mi, w, B);
+    mlmc_status st = mixed_setup(p, mi, w, B, gs);
     if (st != MLMC_OK) return st;
     if (ensure_pin(p, 64) != MLMC_OK) return MLMC_ERR_OOM;
     int32_t* h_count = (int32_t*)p->h_pin;
@@ -1029,11 +1091,12 @@ mlmc_status solve_mixed(mlmc_plan p, int mesh, const MeshInfo& mi, MixedWs& w, i
     return mixed_epilogue(p, mi, w, B, q_dev, iters_dev);
   }
   const auto key = std::make_tuple(1, mesh, B, (const void*)p->ws, (const void*)w.kap64,
-                                   (const void*)q_dev, (const void*)iters_dev);
+                                   (const void*)w.u, (const void*)q_dev, (const void*)iters_dev,
+                                   (const void*)gs.uc);
   auto it = p->graphs.find(key);
   if (it == p->graphs.end()) {
     GraphRec rec;
-    mlmc_status st = build_graph(p, [&] { return issue_mixed(p, mi, w, B, q_dev, iters_dev); }, &rec);
+    mlmc_status st = build_graph(p, [&] { return issue_mixed(p, mi, w, B, q_dev, iters_dev, gs); }, &rec);
     if (st != MLMC_OK) return st;
     it = p->graphs.emplace(key, rec).first;
   }
@@ -1053,29 +1116,51 @@ mlmc_status make_kappa(mlmc_plan p, int mesh, const double* xi, int64_t B, doubl
 
 // --- one allocation round as one graph ----------------------------------
 
+// Nested guess wiring of one side of a coupled batch: the coarse solve
+// (side 1) writes its solution into w.uc, the fine solve (side 0) starts
+// from it. No-op when the batch has no guess buffer.
+Guess guess_views(mlmc_plan p, int level, int side, bool mixed, CoupledWs& w) {
+  Guess gs;
+  if (!w.uc) return gs;
+  if (side == 1) {
+    if (mixed) w.mx.u = w.uc;
+    else w.s.x = w.uc;
+  } else {
+    gs.uc = w.uc;
+    gs.gc = p->meshes[level - 1].g[0];
+  }
+  return gs;
+}
+
 // Coupled batch of `level` issued into the graph being captured on p->stream,
 // in the workspace region at `region`: xi, kappa and solve on mesh `level`,
 // kappa and solve on mesh `level - 1`, Welford fold in sample order.
 mlmc_status issue_level(mlmc_plan p, int level, int64_t first, int64_t B, void* region) {
   const bool mixed = is_mixed(p);
   const int M = p->M;
+  const int64_t gns = guess_ns_of(p->cfg, level);
+  const int sides = level > 0 ? 2 : 1;
   mlmc_status st;
-  for (int side = 0; side < (level > 0 ? 2 : 1); ++side) {
+  for (int k = 0; k < sides; ++k) {
+    // side 0: mesh `level`, side 1: mesh `level - 1`; with the nested guess
+    // the coarse mesh goes first and its solution seeds the fine solve
+    const int side = gns > 0 ? sides - 1 - k : k;
     const int mesh = level - side;
     const MeshInfo& mi = p->meshes[mesh];
     Carve c(region);
     CoupledWs w;
-    carve_coupled(c, mi, M, B, mixed, w);
-    if (side == 0 && (st = mlmc_draw_xi(p, level, first, B, w.xi)) != MLMC_OK) return st;
+    carve_coupled(c, mi, M, B, mixed, gns, side, w);
+    if (k == 0 && (st = mlmc_draw_xi(p, level, first, B, w.xi)) != MLMC_OK) return st;
     if ((st = make_kappa(p, mesh, w.xi, B, w.kap)) != MLMC_OK) return st;
     double* qd = side == 0 ? w.qf : w.qc;
     int32_t* itd = side == 0 ? w.itf : w.itc;
-    st = mixed ? issue_mixed(p, mi, w.mx, B, qd, itd) : issue_fp64(p, mi, w.s, B, qd, itd);
+    const Guess gs = guess_views(p, level, side, mixed, w);
+    st = mixed ? issue_mixed(p, mi, w.mx, B, qd, itd, gs) : issue_fp64(p, mi, w.s, B, qd, itd, gs);
     if (st != MLMC_OK) return st;
   }
   Carve c(region);
   CoupledWs w;
-  carve_coupled(c, p->meshes[level], M, B, mixed, w);
+  carve_coupled(c, p->meshes[level], M, B, mixed, gns, 0, w);
   const double cost = level_cost_cfg(&p->cfg, level);
   CK(run(p, KID_WELFORD, [&] {
     return launch_welford(p->stream, w.qf, level > 0 ? w.qc : nullptr, B, p->d_states + level, cost);
@@ -1098,7 +1183,8 @@ mlmc_status round_launch(mlmc_plan p, const std::vector<int64_t>& first,
     if (count[l] <= 0) continue;
     if (count[l] > 65535) return MLMC_ERR_UNIMPLEMENTED;
     off[l] = total;
-    total += (size_t)round_up((int64_t)coupled_bytes(p->meshes[l], p->M, count[l], mixed), 256);
+    total += (size_t)round_up((int64_t)coupled_bytes(p->meshes[l], p->M, count[l], mixed,
+                                                     guess_ns_of(p->cfg, l)), 256);
   }
   p->round_off = off;
   p->round_count = count;
@@ -1153,7 +1239,7 @@ mlmc_status round_finish(mlmc_plan p, bool* bad) {
     if (n <= 0) continue;
     Carve c((char*)p->ws + p->round_off[l]);
     CoupledWs w;
-    carve_coupled(c, p->meshes[l], p->M, n, mixed, w);
+    carve_coupled(c, p->meshes[l], p->M, n, mixed, guess_ns_of(p->cfg, l), 0, w);
     h.resize(2 * n);
     // on the plan's stream: other plans' rounds keep running meanwhile
     CK(cudaMemcpyAsync(h.data(), w.itf, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, p->stream));
@@ -1240,6 +1326,7 @@ void mlmc_config_default(mlmc_config* c) {
   c->use_graphs = 1;
   c->total_order = -1;
   c->z_chunk = 0;
+  c->nested_guess = 1;
 }
 
 int64_t mlmc_node_stride(int dim, int n) {
@@ -1448,7 +1535,8 @@ int64_t mlmc_round_bytes(const mlmc_config* cfg, const int64_t* count) {
         mi.g[mi.K++] = make_grid(cfg->dim, n, cfg->z_chunk);
       }
     }
-    total += round_up((int64_t)coupled_bytes(mi, M, count[l], cfg->precision == MLMC_MIXED), 256);
+    total += round_up((int64_t)coupled_bytes(mi, M, count[l], cfg->precision == MLMC_MIXED,
+                                             guess_ns_of(*cfg, l)), 256);
   }
   return total;
 }
@@ -1550,14 +1638,14 @@ mlmc_status mlmc_solve(mlmc_plan p, int mesh, const double* kappa, int64_t count
       MixedWs w;
       carve_mixed(c, mi, B, w);
       CK(cudaMemcpyAsync(w.kap64, kap, sizeof(double) * B * mi.g[0].es, cudaMemcpyDeviceToDevice, p->stream));
-      st = solve_mixed(p, mesh, mi, w, B, q + off, iters ? iters + off : nullptr);
+      st = solve_mixed(p, mesh, mi, w, B, q + off, iters ? iters + off : nullptr, Guess{});
       it_dev = w.outer.iters;
       x = w.u;
     } else {
       SolveWs<double> w;
       carve_solve(c, mi, B, false, w);
       w.kap[0] = const_cast<double*>(kap);
-      st = solve_fp64(p, mesh, mi, w, B, q + off, iters ? iters + off : nullptr);
+      st = solve_fp64(p, mesh, mi, w, B, q + off, iters ? iters + off : nullptr, Guess{});
       it_dev = w.sc.iters;
       x = w.x;
     }
@@ -1582,22 +1670,26 @@ mlmc_status mlmc_sample_level(mlmc_plan p, int level, int64_t first, int64_t cou
   const MeshInfo& mf = p->meshes[level];
   const int M = p->M;
   const bool mixed = is_mixed(p);
-  const int64_t Bmax = max_batch(p, [&](int64_t B) { return coupled_bytes(mf, M, B, mixed); }, count);
+  const int64_t gns = guess_ns_of(p->cfg, level);
+  const int64_t Bmax = max_batch(p, [&](int64_t B) { return coupled_bytes(mf, M, B, mixed, gns); }, count);
   const double cost = level_cost_cfg(&p->cfg, level);
+  const int sides = level > 0 ? 2 : 1;
   bool bad = false;
   for (int64_t off = 0; off < count; off += Bmax) {
     const int64_t B = std::min<int64_t>(Bmax, count - off);
-    mlmc_status st = ensure_ws(p, coupled_bytes(mf, M, B, mixed));
+    mlmc_status st = ensure_ws(p, coupled_bytes(mf, M, B, mixed, gns));
     if (st != MLMC_OK) return st;
-    for (int side = 0; side < (level > 0 ? 2 : 1); ++side) {
+    for (int k = 0; k < sides; ++k) {
       // side 0: mesh `level` (fine), side 1: mesh `level - 1` (coarse); the
-      // carve prefix (xi, q_f, q_c, iteration counts) is identical for both.
+      // carve prefix (xi, q_f, q_c, iteration counts, guess) is identical for
+      // both. With the nested guess the coarse mesh is solved first.
+      const int side = gns > 0 ? sides - 1 - k : k;
       const int mesh = level - side;
       const MeshInfo& mi = p->meshes[mesh];
       Carve c(p->ws);
       CoupledWs w;
-      carve_coupled(c, mi, M, B, mixed, w);
-      if (side == 0) {
+      carve_coupled(c, mi, M, B, mixed, gns, side, w);
+      if (k == 0) {
         st = mlmc_draw_xi(p, level, first + off, B, w.xi);
         if (st != MLMC_OK) return st;
       }
@@ -1605,12 +1697,14 @@ mlmc_status mlmc_sample_level(mlmc_plan p, int level, int64_t first, int64_t cou
       if (st != MLMC_OK) return st;
       double* qd = side == 0 ? w.qf : w.qc;
       int32_t* itd = side == 0 ? w.itf : w.itc;
-      st = mixed ? solve_mixed(p, mesh, mi, w.mx, B, qd, itd) : solve_fp64(p, mesh, mi, w.s, B, qd, itd);
+      const Guess gs = guess_views(p, level, side, mixed, w);
+      st = mixed ? solve_mixed(p, mesh, mi, w.mx, B, qd, itd, gs)
+                 : solve_fp64(p, mesh, mi, w.s, B, qd, itd, gs);
       if (st != MLMC_OK) return st;
     }
     Carve c(p->ws);
     CoupledWs w;
-    carve_coupled(c, mf, M, B, mixed, w);
+    carve_coupled(c, mf, M, B, mixed, gns, 0, w);
     CK(run(p, KID_WELFORD, [&] {
       return launch_welford(p->stream, w.qf, level > 0 ? w.qc : nullptr, B, p->d_states + level, cost);
     }));

@@ -133,17 +133,47 @@ __device__ __forceinline__ T stencil_coef(const WinC<T>& w) {
   return fma(w.qal, w.lm, a);
 }
 
+// FP64 kernels are bound by the FP64 pipe, so they take the forms with the
+// fewest FP64 instructions (residuals accumulated from the right-hand side,
+// the streamed prolongation of the post-smoother); FP32 kernels are bound by instruction
+// issue, where the plain forms need fewer instructions in all.
+template <class T>
+constexpr bool kResidualForm = sizeof(T) == 8;
+
+// rhs - (A x) at the window's centre, accumulated from rhs with negated
+// couplings: 9 FMAs where rhs - stencil_coef costs a multiply, 8 FMAs and a
+// subtraction.
+template <class T>
+__device__ __forceinline__ T stencil_coef_res(const WinC<T>& w, T rhs) {
+  T a = fma(-w.cd, w.v0, rhs);
+  a = fma(-w.ce, w.r0, a);
+  a = fma(-w.ceW, w.l0, a);
+  a = fma(-w.cnN, w.vp, a);
+  a = fma(-w.cnS, w.vm, a);
+  a = fma(-w.qb, w.rp, a);
+  a = fma(-w.qbl, w.lp, a);
+  a = fma(-w.qa, w.rm, a);
+  return fma(-w.qal, w.lm, a);
+}
+
 // Streams one warp strip. field(c, j) is the stencilled field at an interior
-// node; out(j, x, ax) runs for each output row j of an output lane with the
-// field x at (c, j) and ax = (A x)(c, j) (0 at boundary nodes). C selects
-// the operator source: kappa per element (src = kappa of the sample), or the
-// precomputed coefficients (src = coefficient block of the sample, ns its
-// node stride). Every lane executes the loads and shuffles.
-template <class T, bool C, class FieldF, class OutF>
-__device__ __forceinline__ void stream_strip(const Strip& s, const T* __restrict__ src, int64_t ns,
-                                             FieldF&& field, OutF&& out) {
+// node, called for consecutive rows j; out(j, x, y, f) runs for each output
+// row j of an output lane with the field x at (c, j) and y = (A x)(c, j)
+// (R false) or y = f - (A x)(c, j) with f = rhs(j) (R true); y is 0 at
+// boundary nodes. rhs(j) is called for output lanes only, one row ahead of
+// its use. C selects the operator source: kappa per element (src = kappa of
+// the sample), or the precomputed coefficients (src = coefficient block of
+// the sample, ns its node stride). Every lane executes the loads and
+// shuffles.
+template <class T, bool C, bool R, class FieldF, class RhsF, class OutF>
+__device__ __forceinline__ void stream_strip_r(const Strip& s, const T* __restrict__ src, int64_t ns,
+                                               FieldF&& field, RhsF&& rhs, OutF&& out) {
   const int n = s.n;
   auto fld = [&](int j) -> T { return interior2(n, s.c, j) ? field(s.c, j) : T(0); };
+  T fn = T(0);
+  if constexpr (R) {
+    if (s.out && s.y0 < s.y1) fn = rhs(s.y0);
+  }
   if constexpr (!C) {
     const T* __restrict__ kap = src;
     Win<T> w;
@@ -166,11 +196,19 @@ __device__ __forceinline__ void stream_strip(const Strip& s, const T* __restrict
       w.ka = w.kb; w.kal = w.kbl;
       w.kb = kn;
       w.kbl = __shfl_up_sync(0xffffffffu, kn, 1);
+      const T f = fn;
       if (j + 1 < s.y1) {          // fetch the next rows before consuming this one
         vn = fld(j + 2);
         kn = kap_at(kap, n, s.c, j + 1);
+        if constexpr (R) {
+          if (s.out) fn = rhs(j + 1);
+        }
       }
-      if (s.out) out(j, w.v0, interior2(n, s.c, j) ? stencil_win(w) : T(0));
+      if (s.out) {
+        T y = T(0);
+        if (interior2(n, s.c, j)) y = R ? f - stencil_win(w) : stencil_win(w);
+        out(j, w.v0, y, f);
+      }
     }
   } else {
     const T* __restrict__ cd = src;
@@ -209,16 +247,32 @@ __device__ __forceinline__ void stream_strip(const Strip& s, const T* __restrict
       w.cnN = cnn;
       w.cnS = cn_prev;
       cn_prev = cnn;
+      const T f = fn;
       if (j + 1 < s.y1) {          // fetch the next rows before consuming this one
         vn = fld(j + 2);
         qn = kap_at(q, n, s.c, j + 1);
         cdn = node(cd, j + 1);
         cen = node(ce, j + 1);
         cnn = node(cn, j + 1);
+        if constexpr (R) {
+          if (s.out) fn = rhs(j + 1);
+        }
       }
-      if (s.out) out(j, w.v0, interior2(n, s.c, j) ? stencil_coef(w) : T(0));
+      if (s.out) {
+        T y = T(0);
+        if (interior2(n, s.c, j)) y = R ? stencil_coef_res(w, f) : stencil_coef(w);
+        out(j, w.v0, y, f);
+      }
     }
   }
+}
+
+// The operator-apply form: out(j, x, A x).
+template <class T, bool C, class FieldF, class OutF>
+__device__ __forceinline__ void stream_strip(const Strip& s, const T* __restrict__ src, int64_t ns,
+                                             FieldF&& field, OutF&& out) {
+  stream_strip_r<T, C, false>(s, src, ns, field, [](int) { return T(0); },
+                              [&](int j, T x, T ax, T) { out(j, x, ax); });
 }
 
 // This warp's partial: per-lane sums (in T) are added across the warp in FP64.
@@ -296,17 +350,25 @@ __global__ void __launch_bounds__(SBLOCK) k_mgpre2(Grid g, const T* __restrict__
   const T* bv = Bv + b * g.ns;
   T* e = E + b * g.ns;
   T* r1 = R1 + b * g.ns;
-  stream_strip<T, C>(s, K + b * cs, g.ns,
-                     [&](int c, int j) {
-                       const int64_t o = (int64_t)j * s.N1 + c;
-                       return __ldg(w_ + o) * __ldg(bv + o);
-                     },
-                     [&](int j, T ev, T ax) {
-                       const int64_t o = (int64_t)j * s.N1 + s.c;
-                       const bool in = interior2(s.n, s.c, j);
-                       e[o] = ev;
-                       r1[o] = in ? __ldg(bv + o) - ax : T(0);
-                     });
+  auto field = [&](int c, int j) {
+    const int64_t o = (int64_t)j * s.N1 + c;
+    return __ldg(w_ + o) * __ldg(bv + o);
+  };
+  if constexpr (kResidualForm<T>) {
+    stream_strip_r<T, C, true>(s, K + b * cs, g.ns, field,
+                               [&](int j) { return __ldg(bv + (int64_t)j * s.N1 + s.c); },
+                               [&](int j, T ev, T rv, T) {
+                                 const int64_t o = (int64_t)j * s.N1 + s.c;
+                                 e[o] = ev;
+                                 r1[o] = rv;
+                               });
+  } else {
+    stream_strip<T, C>(s, K + b * cs, g.ns, field, [&](int j, T ev, T ax) {
+      const int64_t o = (int64_t)j * s.N1 + s.c;
+      e[o] = ev;
+      r1[o] = interior2(s.n, s.c, j) ? __ldg(bv + o) - ax : T(0);
+    });
+  }
   prof_tick(prof);
 }
 
@@ -323,6 +385,43 @@ __device__ __forceinline__ T prolong2(const T* __restrict__ Ec, int nc, int i, i
   if (ox) v1 = T(0.5) * (v1 + __ldg(e + N1c + 1));
   return T(0.5) * (v0 + v1);
 }
+
+// Bilinear prolongation of the coarse correction, streamed down one fine
+// node column i: at fine row j with coarse row J = j / 2, let H(J) be the sum
+// of the two coarse values at columns i / 2 and (i + 1) / 2 of row J (twice
+// the value when i is even). Then (P ec)(i, j) = H(J) / 2 on even rows and
+// (H(J) + H(J + 1)) / 4 on odd rows; x + P ec is one FMA (even rows) or an
+// add and an FMA (odd rows), and each coarse row sum is formed once per
+// column. Rows must be visited in increasing order; the values equal the
+// textbook form 0.5 (0.5 (a + b) + 0.5 (c + d)) bit for bit (the scalings
+// are exact).
+template <class T>
+struct Prolong2 {
+  const T* __restrict__ ec;   // coarse correction of the sample
+  int N1c;                    // coarse nodes per row
+  int jc = -2;                // coarse row held in hc
+  bool have_next = false;     // hn holds H(jc + 1)
+  T hc = T(0), hn = T(0);
+  __device__ __forceinline__ T row_sum(int J, int i) const {
+    const T* r = ec + (int64_t)J * N1c + (i >> 1);
+    return __ldg(r) + __ldg(r + (i & 1));
+  }
+  // x + (P ec)(i, j)
+  __device__ __forceinline__ T add(T x, int i, int j) {
+    const int J = j >> 1;
+    if (J != jc) {
+      hc = (have_next && J == jc + 1) ? hn : row_sum(J, i);
+      jc = J;
+      have_next = false;
+    }
+    if (!(j & 1)) return fma(T(0.5), hc, x);
+    if (!have_next) {
+      hn = row_sum(J + 1, i);
+      have_next = true;
+    }
+    return fma(T(0.25), hc + hn, x);
+  }
+};
 
 // out = e' + W (b - A e'), e' = e + P ec; partials of b.out when part != nullptr.
 template <class T, bool C>
@@ -343,20 +442,34 @@ __global__ void __launch_bounds__(SBLOCK) k_mgpost2(Grid g, int64_t nsc, const T
   const T* bv = Bv + b * g.ns;
   T* out = Out + b * g.ns;
   T dot = T(0);
-  stream_strip<T, C>(s, K + b * cs, g.ns,
-                     [&](int c, int j) {
-                       return __ldg(e + (int64_t)j * s.N1 + c) + prolong2(ec, nc, c, j);
-                     },
-                     [&](int j, T ev, T ax) {
-                       const int64_t o = (int64_t)j * s.N1 + s.c;
-                       T ov = T(0);
-                       if (interior2(s.n, s.c, j)) {
-                         const T bval = __ldg(bv + o);
-                         ov = fma(__ldg(w_ + o), bval - ax, ev);
-                         dot = fma(bval, ov, dot);
-                       }
-                       out[o] = ov;
-                     });
+  if constexpr (kResidualForm<T>) {
+    Prolong2<T> pr{ec, nc + 1};
+    stream_strip_r<T, C, true>(s, K + b * cs, g.ns,
+                               [&](int c, int j) { return pr.add(__ldg(e + (int64_t)j * s.N1 + c), c, j); },
+                               [&](int j) { return __ldg(bv + (int64_t)j * s.N1 + s.c); },
+                               [&](int j, T ev, T rv, T bval) {
+                                 const int64_t o = (int64_t)j * s.N1 + s.c;
+                                 T ov = T(0);
+                                 if (interior2(s.n, s.c, j)) {
+                                   ov = fma(__ldg(w_ + o), rv, ev);
+                                   dot = fma(bval, ov, dot);
+                                 }
+                                 out[o] = ov;
+                               });
+  } else {
+    stream_strip<T, C>(s, K + b * cs, g.ns,
+                       [&](int c, int j) { return __ldg(e + (int64_t)j * s.N1 + c) + prolong2(ec, nc, c, j); },
+                       [&](int j, T ev, T ax) {
+                         const int64_t o = (int64_t)j * s.N1 + s.c;
+                         T ov = T(0);
+                         if (interior2(s.n, s.c, j)) {
+                           const T bval = __ldg(bv + o);
+                           ov = fma(__ldg(w_ + o), bval - ax, ev);
+                           dot = fma(bval, ov, dot);
+                         }
+                         out[o] = ov;
+                       });
+  }
   if (part) warp_partial(dot, part, s.part_idx);
   prof_tick(prof);
 }
@@ -375,16 +488,13 @@ __global__ void __launch_bounds__(SBLOCK) k_resid2(Grid g, const double* __restr
   const double* u = U + b * g.ns;
   double* r = R + b * g.ns;
   double dot = 0.0;
-  stream_strip<double, C>(s, K + b * cs, g.ns,
-                          [&](int c, int j) { return __ldg(u + (int64_t)j * s.N1 + c); },
-                          [&](int j, double, double ax) {
-                            double rv = 0.0;
-                            if (interior2(s.n, s.c, j)) {
-                              rv = h2 - ax;
-                              dot = fma(rv, rv, dot);
-                            }
-                            r[(int64_t)j * s.N1 + s.c] = rv;
-                          });
+  stream_strip_r<double, C, true>(s, K + b * cs, g.ns,
+                                  [&](int c, int j) { return __ldg(u + (int64_t)j * s.N1 + c); },
+                                  [&](int) { return h2; },
+                                  [&](int j, double, double rv, double) {
+                                    dot = fma(rv, rv, dot);
+                                    r[(int64_t)j * s.N1 + s.c] = rv;
+                                  });
   warp_partial(dot, part, s.part_idx);
   prof_tick(prof);
 }
@@ -720,6 +830,31 @@ __global__ void __launch_bounds__(FLAT_THREADS) k_restrict2(Grid gc, int64_t nsf
   if (prof.acc && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(prof.acc, prof.per_sample);
 }
 
+// Nested initial guess: x = P uc, the coarse-mesh solution interpolated
+// bilinearly to the fine mesh (0 on the boundary), one thread per node.
+__global__ void __launch_bounds__(FLAT_THREADS) k_prolong_guess2(Grid g, int64_t nsc,
+                                                                 const double* __restrict__ Uc,
+                                                                 double* __restrict__ X,
+                                                                 const int32_t* __restrict__ active,
+                                                                 Prof prof) {
+  const int64_t b = blockIdx.y;
+  if (!active[b]) return;
+  const int n = g.n, N1 = n + 1;
+  const int64_t nn = (int64_t)N1 * N1;
+  const double* uc = Uc + b * nsc;
+  const int64_t e0 = (int64_t)blockIdx.x * FLAT_ELEMS;
+  const int64_t e1 = min(e0 + (int64_t)FLAT_ELEMS, g.ns);
+  for (int64_t e = e0 + threadIdx.x; e < e1; e += FLAT_THREADS) {
+    double v = 0.0;
+    if (e < nn) {
+      const int ei = (int)e, j = ei / N1, i = ei - j * N1;
+      if (interior2(n, i, j)) v = prolong2(uc, n / 2, i, j);
+    }
+    X[b * g.ns + e] = v;
+  }
+  if (prof.acc && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(prof.acc, prof.per_sample);
+}
+
 // Coarsest grid (n = 2, one unknown): e = b / D exactly.
 template <class T>
 __global__ void k_coarse2(int64_t ns, int64_t es, const T* __restrict__ K, const T* __restrict__ Bv,
@@ -738,6 +873,12 @@ __global__ void k_coarse2(int64_t ns, int64_t es, const T* __restrict__ K, const
 // ------------------------------------------------------------- launchers
 
 namespace d2 {
+
+cudaError_t prolong_guess(cudaStream_t s, const Grid& g, const Grid& coarse, const double* uc,
+                          double* x, const int32_t* active, int64_t B, Prof p) {
+  k_prolong_guess2<<<fgrid(g, B), FLAT_THREADS, 0, s>>>(g, coarse.ns, uc, x, active, p);
+  return cudaGetLastError();
+}
 
 template <class T>
 cudaError_t apply(cudaStream_t s, const Grid& g, const T* kappa, const T* x, T* y, int64_t B, Prof p) {

@@ -834,7 +834,7 @@ __global__ void k_coarse3(Grid g, const T* __restrict__ K, const T* __restrict__
 }
 
 // Pointwise: tmp = e + P ec (trilinear prolongation of the coarse
-// correction). A thread takes the fine nodes 2I and 2I + 1 of one fine row
+// correction; E == nullptr: tmp = P ec, the nested initial guess). A thread takes the fine nodes 2I and 2I + 1 of one fine row
 // (y, z): the coarse rows under it (1, 2 or 4 by the parity of y and z) are
 // summed at coarse columns I and I + 1 once, the even node takes the first
 // sum, the odd node the mean of both, each divided by the number of rows.
@@ -842,7 +842,7 @@ __global__ void k_coarse3(Grid g, const T* __restrict__ K, const T* __restrict__
 template <class T>
 __global__ void __launch_bounds__(256) k_prolong3(Grid g, int64_t nsc, const T* __restrict__ E,
                                                   const T* __restrict__ Ec, T* __restrict__ Tmp,
-                                                  const int32_t* __restrict__ active) {
+                                                  const int32_t* __restrict__ active, Prof prof) {
   const int64_t b = blockIdx.z;
   if (!active[b]) return;
   const int n = g.n, nc = n / 2, N1 = n + 1, C1 = nc + 1;
@@ -865,8 +865,14 @@ __global__ void __launch_bounds__(256) k_prolong3(Grid g, int64_t nsc, const T* 
   const bool row_in = y >= 1 && y < n && z >= 1 && z < n;
   const int64_t o = b * g.ns + ((int64_t)z * N1 + y) * N1 + 2 * I;
   const int x0 = 2 * I;
-  Tmp[o] = (row_in && x0 >= 1 && x0 < n) ? E[o] + s0 * inv : T(0);
-  if (x0 + 1 <= n) Tmp[o + 1] = (row_in && x0 + 1 < n) ? E[o + 1] + T(0.5) * (s0 + s1) * inv : T(0);
+  if (prof.acc && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0)
+    atomicAdd(prof.acc, prof.per_sample);
+  const T e0 = E ? E[o] : T(0);
+  Tmp[o] = (row_in && x0 >= 1 && x0 < n) ? e0 + s0 * inv : T(0);
+  if (x0 + 1 <= n) {
+    const T e1 = E ? E[o + 1] : T(0);
+    Tmp[o + 1] = (row_in && x0 + 1 < n) ? e1 + T(0.5) * (s0 + s1) * inv : T(0);
+  }
 }
 
 // QoI partials: domain: w = h^3 at interior nodes; box [L, H]^3 in node
@@ -943,7 +949,7 @@ cudaError_t mg_post(cudaStream_t s, const Grid& g, const Grid& coarse, const T* 
   {
     const int nc = g.n / 2, rows_y = ((g.n + 1 + 7) / 8) * 8;
     const dim3 grid((unsigned)((nc + 1 + 31) / 32), (unsigned)(rows_y / 8 * (g.n + 1)), (unsigned)B);
-    k_prolong3<T><<<grid, dim3(32, 8, 1), 0, s>>>(g, coarse.ns, e, ec, tmp, active);
+    k_prolong3<T><<<grid, dim3(32, 8, 1), 0, s>>>(g, coarse.ns, e, ec, tmp, active, Prof{nullptr, 0.0});
   }
   launch_zm3<T>(s, g, B, kappa, LdX<T>{tmp, g.ns}, active, EpiMgPost<T>{w, b, out, g.ns}, part, p);
   return cudaGetLastError();
@@ -954,6 +960,14 @@ cudaError_t qoi(cudaStream_t s, const Grid& g, int box, int L, int H, double inv
   k_qoi3<T><<<grid3(g, B), block3(), 0, s>>>(g, box, L, H, inv_vol, x, part, p);
   return cudaGetLastError();
 }
+cudaError_t prolong_guess(cudaStream_t s, const Grid& g, const Grid& coarse, const double* uc,
+                          double* x, const int32_t* active, int64_t B, Prof p) {
+  const int nc = g.n / 2, rows_y = ((g.n + 1 + 7) / 8) * 8;
+  const dim3 grid((unsigned)((nc + 1 + 31) / 32), (unsigned)(rows_y / 8 * (g.n + 1)), (unsigned)B);
+  k_prolong3<double><<<grid, dim3(32, 8, 1), 0, s>>>(g, coarse.ns, nullptr, uc, x, active, p);
+  return cudaGetLastError();
+}
+
 cudaError_t resid64(cudaStream_t s, const Grid& g, const double* kappa, const double* u, double* r,
                     const int32_t* active, double* part, int64_t B, Prof p) {
   launch_zm3<double>(s, g, B, kappa, LdX<double>{u, g.ns}, active, EpiResid{r, g.ns, g.h * g.h * g.h},

@@ -56,6 +56,7 @@ class Config(ctypes.Structure):
         ("use_graphs", ctypes.c_int32),
         ("total_order", ctypes.c_int32),
         ("z_chunk", ctypes.c_int32),
+        ("nested_guess", ctypes.c_int32),
     ]
 
 
@@ -210,7 +211,7 @@ def config(dim=2, n_levels=3, coarse_cells=16, modes_per_dim=4, sigma2=1.0, corr
            qoi="domain", solver="jacobi", box=(0.25, 0.75), rtol=1e-10, max_iter=None,
            precision="fp64", seed=0, stream_id=0, mg_omega=None, check_every=0,
            workspace_bytes=0, inner_rtol=None, inner_max_iter=None, outer_max_iter=None,
-           use_graphs=None, total_order=None):
+           use_graphs=None, total_order=None, nested_guess=None):
     """Build a Config from plain values (defaults from mlmc_config_default)."""
     c = Config()
     lib().mlmc_config_default(ctypes.byref(c))
@@ -240,6 +241,8 @@ def config(dim=2, n_levels=3, coarse_cells=16, modes_per_dim=4, sigma2=1.0, corr
         c.use_graphs = int(use_graphs)
     if total_order is not None:
         c.total_order = int(total_order)
+    if nested_guess is not None:
+        c.nested_guess = int(nested_guess)
     return c
 
 

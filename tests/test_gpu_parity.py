@@ -379,3 +379,33 @@ def test_coupled_samples_total_order(m, dim, precision):
         rf, rc = omlmc.coupled_sample(wl, 1, s)
         assert abs(qf[s] - rf) <= RTOL_Q * abs(rf)
         assert abs(qc[s] - rc) <= RTOL_Q * abs(rc)
+
+
+# ------------------------------------------------- nested initial guess
+
+@pytest.mark.parametrize("dim,precision,solver", [(2, "fp64", "gmg"), (2, "mixed", "gmg"),
+                                                  (2, "fp64", "jacobi"), (3, "fp64", "gmg"),
+                                                  (3, "mixed", "gmg")])
+def test_nested_guess_same_answer_fewer_iterations(m, dim, precision, solver):
+    """The fine solve of a coupled sample started from the interpolated
+    coarse solution meets the same stopping test: its QoIs match the oracle
+    and the zero-start solve, and it needs fewer iterations on average."""
+    n0, levels = (16, 3) if dim == 2 else (8, 2)
+    wl = small_case(dim, n0=n0, levels=levels, corr_len=0.2, m=4, solver=solver,
+                    rtol=1e-10, precision=precision)
+    level = levels - 1
+    out = {}
+    for guess in (0, 1):
+        cfg = m.config_from_workload(wl, nested_guess=guess)
+        with m.Plan(cfg, stream()) as plan:
+            out[guess] = plan.sample_level(level, 0, 8)
+    (qf0, qc0, it0), (qf1, qc1, it1) = out[0], out[1]
+    assert np.array_equal(qc0, qc1)          # the coarse solve is the same solve
+    assert np.all(np.abs(qf1 - qf0) <= 2e-10 * np.abs(qf0))
+    if precision == "fp64":
+        assert it1.mean() < it0.mean()
+    print("iterations zero start %.2f, nested guess %.2f" % (it0.mean(), it1.mean()))
+    for i in (0, 5):
+        rf, rc = omlmc.coupled_sample(wl, level, i)
+        assert abs(qf1[i] - rf) <= RTOL_Q * abs(rf)
+        assert abs(qc1[i] - rc) <= RTOL_Q * abs(rc)
