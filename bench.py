@@ -220,7 +220,7 @@ def measure_form(m, wl, cfg, stream, args, world, barrier, with_e2e):
     sh = stream.cuda_stream
     with torch.cuda.stream(stream):
         plan = m.Plan(cfg, sh)
-        tune = plan.autotune(wl["levels"] - 1, 16, 7) if args.autotune else None
+        tune = plan.autotune(wl["levels"] - 1, 32 if wl["dim"] == 2 else 16, 7) if args.autotune else None
         N = None
         def one_run():
             if wl.get("N") is not None:
@@ -390,13 +390,14 @@ def serving_run(m, args, device=0, adapt=0):
 # adds for the pair sums of each kappa layer, 8 FMAs + 1 multiply + 1 FMA to
 # complete output p - 1, 4 adds + 4 FMAs + 1 add + 1 multiply for output p,
 # 1 multiply + 7 FMAs for output p + 1; 52.5 flops); the loaders and
-# epilogues add 2 to 3 instructions.
+# epilogues add 1 to 2 instructions (the residual epilogues fold f into the
+# last two FMAs of output p - 1, one instruction less).
 #   (instructions per node, flops per node, bytes per node)
 FP64_WORK = {
     (2, "mg_post"): (13.0, 25.0, 42.0), (2, "mg_pre"): (10.0, 19.0, 40.0),
     (2, "pcg_pq"): (11.0, 21.0, 40.0), (2, "resid64"): (10.0, 20.0, 24.0),
-    (3, "mg_post"): (35.5, 57.5, 41.0), (3, "mg_pre"): (34.5, 54.5, 40.0),
-    (3, "pcg_pq"): (34.5, 56.5, 40.0), (3, "resid64"): (34.5, 55.5, 24.0),
+    (3, "mg_post"): (34.5, 57.5, 41.0), (3, "mg_pre"): (33.5, 54.5, 40.0),
+    (3, "pcg_pq"): (34.5, 56.5, 40.0), (3, "resid64"): (33.5, 55.5, 24.0),
 }
 GB300_SMS = 152
 DFMA_PER_SM_CLK = 2
@@ -411,7 +412,9 @@ def roofline_of(res, peaks, fp64_alu, dim=2):
          "avg_launch_us": round(1e3 * d_ms / max(d_launches, 1), 2),
          "time_shares": res["shares"], "per_kernel": res["per_kernel"]}
     work = FP64_WORK.get((dim, res["dom"]))
-    if fp64_alu and work is not None:
+    # the FP64 kernels (every stencil of the FP64 form; the outer residual of
+    # the mixed form) are bound by the FP64 pipe
+    if (fp64_alu or res["dom"] == "resid64") and work is not None:
         # FP64-pipe bound: algorithmic FP64 flops/s (FMA = 2) against 2 DFMA per
         # SM per cycle at the median SM clock of the timed region; the same as
         # FP64 instructions/s against the pipe's 2 instructions per SM per cycle

@@ -268,7 +268,9 @@ typedef struct mlmc_tune_report {
  * the selected knobs (flags: MLMC_TUNE_*; mixed-form inner tolerance
  * 1e-2..3e-4, multigrid damping 0.7..0.9, 3D z-planes per stencil CTA) and
  * keep the fastest in the plan's configuration (inner_rtol, mg_omega,
- * z_chunk; cached graphs are rebuilt; a setting whose
+ * z_chunk; each setting is timed twice and the faster time counts; the
+ * plan's current setting stays unless another is more than 2% faster;
+ * cached graphs are rebuilt; a setting whose
  * solves hit the iteration cap is never chosen). Probe samples use indices
  * just below 2^32; the level states are restored. Solves then stop at the
  * same rtol but their iterates, hence results in the last digits, depend on

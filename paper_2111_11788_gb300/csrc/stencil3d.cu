@@ -272,7 +272,10 @@ __global__ void __launch_bounds__(ZTHREADS, 2) k_zm3(Grid g, const T* __restrict
       u = fma(kb[r][1], v0[2], u);
       u = fma(kb[r + 1][0], v2[0], u);
       u = fma(kb[r + 1][1], v2[2], u);
-      const T done = fma(-c12, u, c3 * D[r]);
+      // A x = c3 D - c12 U, or f - A x = f - c3 D + c12 U for a residual epilogue
+      T done;
+      if constexpr (Epi::kRes) done = fma(c12, u, fma(-c3, D[r], T(epi.rhs(pre[r]))));
+      else done = fma(-c12, u, c3 * D[r]);
       if (cvalid[r] && m >= t.z0) {
         const int o = m * P + ocol[r];
         dot += epi(o, cint[r] && m >= 1 && m < n, done, vc[r], pre[r]);
@@ -362,13 +365,19 @@ struct LdWb {   // the pre-smoothed iterate from zero: omega D^-1 b
 
 // Epilogues: bind(sample) offsets their arrays to the sample; load(node)
 // fetches the node's own inputs (Pre) one plane ahead; then (node offset,
-// interior?, (A x) at the node, x at the node, Pre) -> contribution to the
-// CTA partial; zero() writes a boundary node.
+// interior?, y, x at the node, Pre) -> contribution to the CTA partial;
+// zero() writes a boundary node. y is (A x) at the node, or, for an epilogue
+// with kRes (the FP64 residual forms, k_zm3 only), f - (A x) with f =
+// rhs(Pre): the FP64 kernel then folds f into its last two FMAs instead of a
+// multiply, an FMA and a subtraction.
 struct NoPre {};
+
 
 template <class T>
 struct EpiApply {   // y = A x
   using Pre = NoPre;
+  static constexpr bool kRes = false;
+  __device__ T rhs(const Pre&) const { return T(0); }
   T* Y;
   int64_t ns;
   __device__ void bind(int64_t b) { Y += b * ns; }
@@ -383,6 +392,8 @@ struct EpiApply {   // y = A x
 template <class T>
 struct EpiAq {   // q = A p, partial of p.q; p itself stored (Pn) when formed by the loader
   using Pre = NoPre;
+  static constexpr bool kRes = false;
+  __device__ T rhs(const Pre&) const { return T(0); }
   T* Q;
   T* Pn;
   int64_t ns;
@@ -411,6 +422,8 @@ struct PreB {
 template <class T>
 struct EpiMgRes {   // residual of the pre-smoothed iterate: b - A e; e stored (E) when formed by the loader
   using Pre = PreB<T>;
+  static constexpr bool kRes = sizeof(T) == 8;
+  __device__ T rhs(const Pre& pr) const { return pr.b; }
   const T* Bv;
   T* R1;
   T* E;
@@ -421,8 +434,8 @@ struct EpiMgRes {   // residual of the pre-smoothed iterate: b - A e; e stored (
     if (E) E += b * ns;
   }
   __device__ Pre load(int o) const { return Pre{__ldg(Bv + o)}; }
-  __device__ T operator()(int o, bool in, T ax, T xc, const Pre& pr) const {
-    R1[o] = in ? pr.b - ax : T(0);
+  __device__ T operator()(int o, bool in, T y, T xc, const Pre& pr) const {
+    R1[o] = in ? (kRes ? y : pr.b - y) : T(0);
     if (E) E[o] = in ? xc : T(0);
     return T(0);
   }
@@ -440,6 +453,8 @@ struct PreBW {
 template <class T>
 struct EpiMgPost {   // post-smoothing: e + W (b - A e), partial of b.out
   using Pre = PreBW<T>;
+  static constexpr bool kRes = sizeof(T) == 8;
+  __device__ T rhs(const Pre& pr) const { return pr.b; }
   const T* W;
   const T* Bv;
   T* Out;
@@ -450,8 +465,8 @@ struct EpiMgPost {   // post-smoothing: e + W (b - A e), partial of b.out
     Out += b * ns;
   }
   __device__ Pre load(int o) const { return Pre{__ldg(Bv + o), __ldg(W + o)}; }
-  __device__ T operator()(int o, bool in, T ax, T ec, const Pre& pr) const {
-    const T ov = in ? fma(pr.w, pr.b - ax, ec) : T(0);
+  __device__ T operator()(int o, bool in, T y, T ec, const Pre& pr) const {
+    const T ov = in ? fma(pr.w, kRes ? y : pr.b - y, ec) : T(0);
     Out[o] = ov;
     return in ? pr.b * ov : T(0);
   }
@@ -460,13 +475,15 @@ struct EpiMgPost {   // post-smoothing: e + W (b - A e), partial of b.out
 
 struct EpiResid {   // outer FP64 residual h^3 - A u, partial of its square
   using Pre = NoPre;
+  static constexpr bool kRes = true;
   double* R;
   int64_t ns;
   double h3;
+  __device__ double rhs(const Pre&) const { return h3; }
   __device__ void bind(int64_t b) { R += b * ns; }
   __device__ Pre load(int) const { return Pre{}; }
-  __device__ double operator()(int o, bool in, double ax, double, const Pre&) const {
-    const double rv = in ? h3 - ax : 0.0;
+  __device__ double operator()(int o, bool in, double rv_in, double, const Pre&) const {
+    const double rv = in ? rv_in : 0.0;
     R[o] = rv;
     return rv * rv;
   }
@@ -566,6 +583,7 @@ template <class Ld, class Epi>
 __global__ void __launch_bounds__(ZTHREADS, 2) k_zm3f(Grid g, const float* __restrict__ Kap, Ld ld,
                                                       const int32_t* __restrict__ active, Epi epi,
                                                       double* __restrict__ part, Prof prof) {
+  static_assert(!Epi::kRes, "the FP32 z-march hands A x to its epilogues");
   constexpr int NA = Ld::kArrays;
   const int64_t b = blockIdx.y;
   if (active && !active[b]) return;
