@@ -49,6 +49,7 @@ enum KernelId {
   KID_SETUP,
   KID_REFINE,
   KID_RESID64,
+  KID_MG_BOTTOM,
   NUM_KERNELS
 };
 
@@ -187,6 +188,28 @@ cudaError_t add_correction(cudaStream_t s, const Grid& g, double* u, const float
 // nested initial guess: x = P uc (bilinear interpolation from grid `coarse`)
 cudaError_t prolong_guess(cudaStream_t s, const Grid& g, const Grid& coarse, const double* uc,
                           double* x, const int32_t* active, int64_t B, Prof p);
+
+// The small multigrid levels k0 .. K-1 of a V-cycle fused into one kernel,
+// one CTA per sample in shared memory: from b at level k0 (restricted by the
+// level above) to the post-smoothed correction out at level k0. Per level:
+// the grid, kappa, W and (FP64: non-null) operator coefficients; sample
+// strides as in the unfused kernels.
+constexpr int MAX_BOTTOM = 8;
+template <class T>
+struct BottomLevels {
+  int L;                       // fused levels (the last is the coarsest, n = 2)
+  Grid g[MAX_BOTTOM];
+  const T* kap[MAX_BOTTOM];
+  const T* coef[MAX_BOTTOM];
+  const T* w[MAX_BOTTOM];
+};
+// largest grid (cells per side) whose level is fused
+constexpr int BOTTOM_MAX_N = 32;
+template <class T>
+size_t bottom_smem(const BottomLevels<T>& lv);
+template <class T>
+cudaError_t mg_bottom(cudaStream_t s, const BottomLevels<T>& lv, const T* b, T* out,
+                      const int32_t* active, int64_t B, Prof p);
 }  // namespace d2
 
 // iter_dev (may be null) overrides iter with a device-side iteration counter.

@@ -55,7 +55,7 @@ namespace {
 const char* kKernelNames[NUM_KERNELS] = {
     "draw_xi", "kle_table", "kappa", "coarsen_kappa", "apply", "pcg_init", "pcg_pq", "pcg_xr",
     "jacobi_z", "mg_pre", "restrict", "coarse_solve", "mg_post", "qoi", "finalize", "welford",
-    "estimate", "count_active", "setup", "refine", "resid64"};
+    "estimate", "count_active", "setup", "refine", "resid64", "mg_bottom"};
 
 // Bump allocator over the workspace (base == nullptr: size only).
 struct Carve {
@@ -567,7 +567,14 @@ mlmc_status precondition(mlmc_plan p, const MeshInfo& mi, SolveWs<T>& w, int64_t
     return MLMC_OK;
   }
   const int K = mi.K;
-  for (int k = 0; k < K - 1; ++k) {
+  // 2D: the levels below the finest whose grids have at most BOTTOM_MAX_N
+  // cells per side run as one fused kernel (k0 .. K-1), one CTA per sample
+  int k0 = K - 1;
+  if (g0.dim == 2)
+    while (k0 - 1 >= 1 && mi.g[k0 - 1].n <= d2::BOTTOM_MAX_N) --k0;
+  const bool fuse = k0 < K - 1 && K - k0 <= d2::MAX_BOTTOM;
+  const int kd = fuse ? k0 : K - 1;   // levels above the bottom
+  for (int k = 0; k < kd; ++k) {
     const Grid& g = mi.g[k];
     const double nn = nodes_of(g), ne = elems_of(g);
     CK(run(p, KID_MG_PRE, [&] {
@@ -579,10 +586,27 @@ mlmc_status precondition(mlmc_plan p, const MeshInfo& mi, SolveWs<T>& w, int64_t
                               prof_for(p, KID_RESTRICT, (nn + nodes_of(mi.g[k + 1])) * vb));
     }));
   }
-  CK(run(p, KID_COARSE, [&] {
-    return op::coarse_solve<T>(s, mi.g[K - 1], w.kap[K - 1], w.bk[K - 1], w.e[K - 1], w.sc.active, B);
-  }));
-  for (int k = K - 2; k >= 0; --k) {
+  if (fuse) {
+    d2::BottomLevels<T> lv{};
+    lv.L = K - k0;
+    double bytes = 2 * nodes_of(mi.g[k0]);
+    for (int l = 0; l < lv.L; ++l) {
+      lv.g[l] = mi.g[k0 + l];
+      lv.kap[l] = w.kap[k0 + l];
+      lv.coef[l] = w.coef[k0 + l];
+      lv.w[l] = w.w[k0 + l];
+      bytes += nodes_of(mi.g[k0 + l]) + elems_of(mi.g[k0 + l]);
+    }
+    CK(run(p, KID_MG_BOTTOM, [&] {
+      return d2::mg_bottom<T>(s, lv, w.bk[k0], w.eo[k0], w.sc.active, B,
+                              prof_for(p, KID_MG_BOTTOM, bytes * vb));
+    }));
+  } else {
+    CK(run(p, KID_COARSE, [&] {
+      return op::coarse_solve<T>(s, mi.g[K - 1], w.kap[K - 1], w.bk[K - 1], w.e[K - 1], w.sc.active, B);
+    }));
+  }
+  for (int k = kd - 1; k >= 0; --k) {
     const Grid& g = mi.g[k];
     const double nn = nodes_of(g), ne = elems_of(g), nc = nodes_of(mi.g[k + 1]);
     CK(run(p, KID_MG_POST, [&] {

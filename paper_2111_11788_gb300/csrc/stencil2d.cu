@@ -953,6 +953,159 @@ __global__ void k_coarse2(int64_t ns, int64_t es, const T* __restrict__ K, const
   E[off + 4] = Bv[off + 4] / d;
 }
 
+
+// --------------------------------------------- fused bottom of the V-cycle
+
+constexpr int BOTTOM_THREADS = 256;
+
+// Bilinear prolongation from a coarse array in shared memory.
+template <class T>
+__device__ __forceinline__ T prolong2_s(const T* ec, int nc, int i, int j) {
+  const int N1c = nc + 1;
+  const T* e = ec + (j >> 1) * N1c + (i >> 1);
+  const bool ox = i & 1, oy = j & 1;
+  T v0 = e[0];
+  if (ox) v0 = T(0.5) * (v0 + e[1]);
+  if (!oy) return v0;
+  T v1 = e[N1c];
+  if (ox) v1 = T(0.5) * (v1 + e[N1c + 1]);
+  return T(0.5) * (v0 + v1);
+}
+
+// Levels k0 .. K-1 of the V-cycle for one sample per CTA, in shared memory
+// (per level: b, e and a third array for r1, then the level's output): the
+// same steps and arithmetic as k_mgpre2, k_restrict2, k_coarse2 and
+// k_mgpost2 (C: FP64 coefficient form with residuals accumulated from b;
+// else kappa form), with a barrier between steps instead of a launch.
+// Operator data, W and kappa are read from global memory (cached).
+template <class T, bool C>
+__global__ void __launch_bounds__(BOTTOM_THREADS) k_bottom2(d2::BottomLevels<T> lv, const T* __restrict__ Bv,
+                                                            T* __restrict__ Out,
+                                                            const int32_t* __restrict__ active,
+                                                            Prof prof) {
+  const int64_t smp = blockIdx.x;
+  if (!active[smp]) return;
+  extern __shared__ __align__(16) unsigned char bottom_raw[];
+  T* sm = reinterpret_cast<T*>(bottom_raw);
+  const int L = lv.L;
+  const int tid = threadIdx.x;
+  // level l's arrays start at 3 x (nodes of the levels before it)
+  auto base = [&](int l) -> T* {
+    int off = 0;
+    for (int m = 0; m < l; ++m) off += 3 * (lv.g[m].n + 1) * (lv.g[m].n + 1);
+    return sm + off;
+  };
+  // f - (A e)(c, j) at an interior node of level l (e in shared memory)
+  auto resid = [&](int l, const T* e, int c, int j, T f) -> T {
+    const Grid& g = lv.g[l];
+    const int n = g.n, N1 = n + 1, o = j * N1 + c, eo = j * n + c;
+    if constexpr (C) {
+      const T* cb = lv.coef[l] + smp * (3 * g.ns + g.es);
+      const T* cd = cb;
+      const T* ce = cb + g.ns;
+      const T* cn = cb + 2 * g.ns;
+      const T* q = cb + 3 * g.ns;
+      WinC<T> w;
+      w.v0 = e[o]; w.l0 = e[o - 1]; w.r0 = e[o + 1];
+      w.vp = e[o + N1]; w.lp = e[o + N1 - 1]; w.rp = e[o + N1 + 1];
+      w.vm = e[o - N1]; w.lm = e[o - N1 - 1]; w.rm = e[o - N1 + 1];
+      w.qb = __ldg(q + eo); w.qbl = __ldg(q + eo - 1);
+      w.qa = __ldg(q + eo - n); w.qal = __ldg(q + eo - n - 1);
+      w.cd = __ldg(cd + o); w.ce = __ldg(ce + o); w.ceW = __ldg(ce + o - 1);
+      w.cnN = __ldg(cn + o); w.cnS = __ldg(cn + o - N1);
+      return stencil_coef_res(w, f);
+    } else {
+      const T* k = lv.kap[l] + smp * g.es;
+      Win<T> w;
+      w.v0 = e[o]; w.l0 = e[o - 1]; w.r0 = e[o + 1];
+      w.vp = e[o + N1]; w.lp = e[o + N1 - 1]; w.rp = e[o + N1 + 1];
+      w.vm = e[o - N1]; w.lm = e[o - N1 - 1]; w.rm = e[o - N1 + 1];
+      w.kb = __ldg(k + eo); w.kbl = __ldg(k + eo - 1);
+      w.ka = __ldg(k + eo - n); w.kal = __ldg(k + eo - n - 1);
+      return f - stencil_win(w);
+    }
+  };
+  {
+    const int N1 = lv.g[0].n + 1;
+    T* b = base(0);
+    const T* src = Bv + smp * lv.g[0].ns;
+    for (int i = tid; i < N1 * N1; i += BOTTOM_THREADS) b[i] = src[i];
+  }
+  __syncthreads();
+  // down: e = W b, r1 = b - A e, b_{l+1} = R r1
+  for (int l = 0; l < L - 1; ++l) {
+    const int n = lv.g[l].n, N1 = n + 1, nn = N1 * N1;
+    T* b = base(l);
+    T* e = b + nn;
+    T* t = e + nn;
+    const T* W = lv.w[l] + smp * lv.g[l].ns;
+    for (int i = tid; i < nn; i += BOTTOM_THREADS) e[i] = __ldg(W + i) * b[i];
+    __syncthreads();
+    for (int i = tid; i < nn; i += BOTTOM_THREADS) {
+      const int j = i / N1, c = i - j * N1;
+      t[i] = interior2(n, c, j) ? resid(l, e, c, j, b[i]) : T(0);
+    }
+    __syncthreads();
+    const int nc = lv.g[l + 1].n, N1c = nc + 1;
+    T* bc = base(l + 1);
+    for (int i = tid; i < N1c * N1c; i += BOTTOM_THREADS) {
+      const int J = i / N1c, I = i - J * N1c;
+      T v = T(0);
+      if (interior2(nc, I, J)) {
+        const T* r = t + (2 * J) * N1 + 2 * I;
+        const T h = T(0.5);
+        const T row0 = h * r[-N1 - 1] + r[-N1] + h * r[-N1 + 1];
+        const T row1 = h * r[-1] + r[0] + h * r[1];
+        const T row2 = h * r[N1 - 1] + r[N1] + h * r[N1 + 1];
+        v = h * (row0 + row2) + row1;
+      }
+      bc[i] = v;
+    }
+    __syncthreads();
+  }
+  // coarsest grid (n = 2, one unknown): e = b / D
+  {
+    T* b = base(L - 1);
+    T* e = b + 9;
+    if (tid == 0) {
+      const T* k = lv.kap[L - 1] + smp * lv.g[L - 1].es;
+      const T d = Consts<T>::c23 * ((k[0] + k[1]) + (k[2] + k[3]));
+      for (int q = 0; q < 9; ++q) e[q] = T(0);
+      e[4] = b[4] / d;
+    }
+  }
+  __syncthreads();
+  // up: e += P e_c, out = e + W (b - A e)
+  for (int l = L - 2; l >= 0; --l) {
+    const int n = lv.g[l].n, N1 = n + 1, nn = N1 * N1;
+    T* b = base(l);
+    T* e = b + nn;
+    T* t = e + nn;
+    const int ncn = (lv.g[l + 1].n + 1) * (lv.g[l + 1].n + 1);
+    const T* ec = base(l + 1) + ((l + 1 == L - 1) ? ncn : 2 * ncn);
+    for (int i = tid; i < nn; i += BOTTOM_THREADS) {
+      const int j = i / N1, c = i - j * N1;
+      if (interior2(n, c, j)) e[i] = e[i] + prolong2_s(ec, n / 2, c, j);
+    }
+    __syncthreads();
+    const T* W = lv.w[l] + smp * lv.g[l].ns;
+    for (int i = tid; i < nn; i += BOTTOM_THREADS) {
+      const int j = i / N1, c = i - j * N1;
+      T ov = T(0);
+      if (interior2(n, c, j)) ov = fma(__ldg(W + i), resid(l, e, c, j, b[i]), e[i]);
+      t[i] = ov;
+    }
+    __syncthreads();
+  }
+  {
+    const int N1 = lv.g[0].n + 1;
+    const T* t = base(0) + 2 * N1 * N1;
+    T* dst = Out + smp * lv.g[0].ns;
+    for (int i = tid; i < N1 * N1; i += BOTTOM_THREADS) dst[i] = t[i];
+  }
+  if (prof.acc && tid == 0) atomicAdd(prof.acc, prof.per_sample);
+}
+
 }  // namespace
 
 // ------------------------------------------------------------- launchers
@@ -1086,6 +1239,26 @@ cudaError_t add_correction(cudaStream_t s, const Grid& g, double* u, const float
   return cudaGetLastError();
 }
 
+template <class T>
+size_t bottom_smem(const BottomLevels<T>& lv) {
+  size_t nodes = 0;
+  for (int l = 0; l < lv.L; ++l) nodes += 3 * (size_t)(lv.g[l].n + 1) * (lv.g[l].n + 1);
+  return nodes * sizeof(T);
+}
+
+template <class T>
+cudaError_t mg_bottom(cudaStream_t s, const BottomLevels<T>& lv, const T* b, T* out,
+                      const int32_t* active, int64_t B, Prof p) {
+  if (lv.L < 2 || lv.L > MAX_BOTTOM || lv.g[lv.L - 1].n != 2 || lv.g[0].n > BOTTOM_MAX_N)
+    return cudaErrorInvalidValue;
+  const size_t smem = bottom_smem(lv);
+  if (lv.coef[0])
+    k_bottom2<T, true><<<(unsigned)B, BOTTOM_THREADS, smem, s>>>(lv, b, out, active, p);
+  else
+    k_bottom2<T, false><<<(unsigned)B, BOTTOM_THREADS, smem, s>>>(lv, b, out, active, p);
+  return cudaGetLastError();
+}
+
 #define MLMC_INST2(T)                                                                              \
   template cudaError_t apply<T>(cudaStream_t, const Grid&, const T*, const T*, T*, int64_t, Prof); \
   template cudaError_t winv<T>(cudaStream_t, const Grid&, const T*, double, T*, int64_t);          \
@@ -1107,7 +1280,10 @@ cudaError_t add_correction(cudaStream_t s, const Grid& g, double* u, const float
                                   const T*, const T*, const T*, T*, const int32_t*, double*,       \
                                   int64_t, Prof, const T*);                                        \
   template cudaError_t qoi<T>(cudaStream_t, const Grid&, int, int, int, double, const T*, double*, \
-                              int64_t, Prof);
+                              int64_t, Prof);                                                      \
+  template size_t bottom_smem<T>(const BottomLevels<T>&);                                          \
+  template cudaError_t mg_bottom<T>(cudaStream_t, const BottomLevels<T>&, const T*, T*,            \
+                                    const int32_t*, int64_t, Prof);
 
 MLMC_INST2(double)
 MLMC_INST2(float)
