@@ -204,7 +204,7 @@ struct BottomLevels {
   const T* w[MAX_BOTTOM];
 };
 // largest grid (cells per side) whose level is fused
-constexpr int BOTTOM_MAX_N = 32;
+constexpr int BOTTOM_MAX_N = 64;
 template <class T>
 size_t bottom_smem(const BottomLevels<T>& lv);
 template <class T>

@@ -956,7 +956,7 @@ __global__ void k_coarse2(int64_t ns, int64_t es, const T* __restrict__ K, const
 
 // --------------------------------------------- fused bottom of the V-cycle
 
-constexpr int BOTTOM_THREADS = 256;
+constexpr int BOTTOM_THREADS = 512;
 
 // Bilinear prolongation from a coarse array in shared memory.
 template <class T>
@@ -1252,6 +1252,15 @@ cudaError_t mg_bottom(cudaStream_t s, const BottomLevels<T>& lv, const T* b, T* 
   if (lv.L < 2 || lv.L > MAX_BOTTOM || lv.g[lv.L - 1].n != 2 || lv.g[0].n > BOTTOM_MAX_N)
     return cudaErrorInvalidValue;
   const size_t smem = bottom_smem(lv);
+  // opt in once to the shared memory of the largest fused chain (64^2 .. 2^2)
+  static const cudaError_t attr = [] {
+    size_t most = 0;
+    for (int n = BOTTOM_MAX_N; n >= 2; n /= 2) most += 3 * (size_t)(n + 1) * (n + 1) * sizeof(T);
+    cudaError_t e1 = cudaFuncSetAttribute(k_bottom2<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
+    cudaError_t e2 = cudaFuncSetAttribute(k_bottom2<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
+    return e1 != cudaSuccess ? e1 : e2;
+  }();
+  if (attr != cudaSuccess) return attr;
   if (lv.coef[0])
     k_bottom2<T, true><<<(unsigned)B, BOTTOM_THREADS, smem, s>>>(lv, b, out, active, p);
   else
