@@ -91,6 +91,24 @@ struct Grid {
 
 Grid make_grid(int dim, int n, int z_chunk = 0);
 
+// The small multigrid levels k0 .. K-1 of a V-cycle fused into one kernel,
+// one CTA per sample in shared memory: from b at level k0 (restricted by the
+// level above) to the post-smoothed correction out at level k0. Per level:
+// the grid, kappa, W and (2D FP64: non-null) operator coefficients; sample
+// strides as in the unfused kernels.
+constexpr int MAX_BOTTOM = 8;
+template <class T>
+struct BottomLevels {
+  int L;                       // fused levels (the last is the coarsest, n = 2)
+  Grid g[MAX_BOTTOM];
+  const T* kap[MAX_BOTTOM];
+  const T* coef[MAX_BOTTOM];
+  const T* w[MAX_BOTTOM];
+};
+// largest grid (cells per side) whose level is fused: 2D, 3D
+constexpr int BOTTOM_MAX_N2 = 64;
+constexpr int BOTTOM_MAX_N3 = 16;
+
 // Per-sample scalars of the batched PCG (struct of arrays, B entries each).
 struct Scalars {
   double* gamma;
@@ -189,24 +207,6 @@ cudaError_t add_correction(cudaStream_t s, const Grid& g, double* u, const float
 cudaError_t prolong_guess(cudaStream_t s, const Grid& g, const Grid& coarse, const double* uc,
                           double* x, const int32_t* active, int64_t B, Prof p);
 
-// The small multigrid levels k0 .. K-1 of a V-cycle fused into one kernel,
-// one CTA per sample in shared memory: from b at level k0 (restricted by the
-// level above) to the post-smoothed correction out at level k0. Per level:
-// the grid, kappa, W and (FP64: non-null) operator coefficients; sample
-// strides as in the unfused kernels.
-constexpr int MAX_BOTTOM = 8;
-template <class T>
-struct BottomLevels {
-  int L;                       // fused levels (the last is the coarsest, n = 2)
-  Grid g[MAX_BOTTOM];
-  const T* kap[MAX_BOTTOM];
-  const T* coef[MAX_BOTTOM];
-  const T* w[MAX_BOTTOM];
-};
-// largest grid (cells per side) whose level is fused
-constexpr int BOTTOM_MAX_N = 64;
-template <class T>
-size_t bottom_smem(const BottomLevels<T>& lv);
 template <class T>
 cudaError_t mg_bottom(cudaStream_t s, const BottomLevels<T>& lv, const T* b, T* out,
                       const int32_t* active, int64_t B, Prof p);
@@ -247,6 +247,9 @@ cudaError_t resid64(cudaStream_t s, const Grid& g, const double* kappa, const do
 // nested initial guess: x = P uc (trilinear interpolation from grid `coarse`)
 cudaError_t prolong_guess(cudaStream_t s, const Grid& g, const Grid& coarse, const double* uc,
                           double* x, const int32_t* active, int64_t B, Prof p);
+template <class T>
+cudaError_t mg_bottom(cudaStream_t s, const BottomLevels<T>& lv, const T* b, T* out,
+                      const int32_t* active, int64_t B, Prof p);
 }  // namespace d3
 
 // Dimension dispatch used by the plan.
@@ -325,6 +328,12 @@ inline cudaError_t to_rhs32(cudaStream_t s, const Grid& g, const double* r, cons
 inline cudaError_t add_correction(cudaStream_t s, const Grid& g, double* u, const float* d32,
                                   const double* scale, const int32_t* active, int64_t B, Prof p) {
   return d2::add_correction(s, g, u, d32, scale, active, B, p);
+}
+template <class T>
+inline cudaError_t mg_bottom(cudaStream_t s, const BottomLevels<T>& lv, const T* b, T* out,
+                             const int32_t* active, int64_t B, Prof p) {
+  return lv.g[0].dim == 2 ? d2::mg_bottom<T>(s, lv, b, out, active, B, p)
+                          : d3::mg_bottom<T>(s, lv, b, out, active, B, p);
 }
 inline cudaError_t prolong_guess(cudaStream_t s, const Grid& g, const Grid& coarse, const double* uc,
                                  double* x, const int32_t* active, int64_t B, Prof p) {

@@ -567,12 +567,13 @@ mlmc_status precondition(mlmc_plan p, const MeshInfo& mi, SolveWs<T>& w, int64_t
     return MLMC_OK;
   }
   const int K = mi.K;
-  // 2D: the levels below the finest whose grids have at most BOTTOM_MAX_N
-  // cells per side run as one fused kernel (k0 .. K-1), one CTA per sample
+  // the levels below the finest whose grids have at most BOTTOM_MAX_N2 (2D)
+  // or BOTTOM_MAX_N3 (3D) cells per side run as one fused kernel
+  // (k0 .. K-1), one CTA per sample
+  const int nmax = g0.dim == 2 ? BOTTOM_MAX_N2 : BOTTOM_MAX_N3;
   int k0 = K - 1;
-  if (g0.dim == 2)
-    while (k0 - 1 >= 1 && mi.g[k0 - 1].n <= d2::BOTTOM_MAX_N) --k0;
-  const bool fuse = k0 < K - 1 && K - k0 <= d2::MAX_BOTTOM;
+  while (k0 - 1 >= 1 && mi.g[k0 - 1].n <= nmax) --k0;
+  const bool fuse = k0 < K - 1 && K - k0 <= MAX_BOTTOM;
   const int kd = fuse ? k0 : K - 1;   // levels above the bottom
   for (int k = 0; k < kd; ++k) {
     const Grid& g = mi.g[k];
@@ -587,7 +588,7 @@ mlmc_status precondition(mlmc_plan p, const MeshInfo& mi, SolveWs<T>& w, int64_t
     }));
   }
   if (fuse) {
-    d2::BottomLevels<T> lv{};
+    BottomLevels<T> lv{};
     lv.L = K - k0;
     double bytes = 2 * nodes_of(mi.g[k0]);
     for (int l = 0; l < lv.L; ++l) {
@@ -598,7 +599,7 @@ mlmc_status precondition(mlmc_plan p, const MeshInfo& mi, SolveWs<T>& w, int64_t
       bytes += nodes_of(mi.g[k0 + l]) + elems_of(mi.g[k0 + l]);
     }
     CK(run(p, KID_MG_BOTTOM, [&] {
-      return d2::mg_bottom<T>(s, lv, w.bk[k0], w.eo[k0], w.sc.active, B,
+      return op::mg_bottom<T>(s, lv, w.bk[k0], w.eo[k0], w.sc.active, B,
                               prof_for(p, KID_MG_BOTTOM, bytes * vb));
     }));
   } else {

@@ -979,7 +979,7 @@ __device__ __forceinline__ T prolong2_s(const T* ec, int nc, int i, int j) {
 // else kappa form), with a barrier between steps instead of a launch.
 // Operator data, W and kappa are read from global memory (cached).
 template <class T, bool C>
-__global__ void __launch_bounds__(BOTTOM_THREADS) k_bottom2(d2::BottomLevels<T> lv, const T* __restrict__ Bv,
+__global__ void __launch_bounds__(BOTTOM_THREADS) k_bottom2(BottomLevels<T> lv, const T* __restrict__ Bv,
                                                             T* __restrict__ Out,
                                                             const int32_t* __restrict__ active,
                                                             Prof prof) {
@@ -1240,22 +1240,16 @@ cudaError_t add_correction(cudaStream_t s, const Grid& g, double* u, const float
 }
 
 template <class T>
-size_t bottom_smem(const BottomLevels<T>& lv) {
-  size_t nodes = 0;
-  for (int l = 0; l < lv.L; ++l) nodes += 3 * (size_t)(lv.g[l].n + 1) * (lv.g[l].n + 1);
-  return nodes * sizeof(T);
-}
-
-template <class T>
 cudaError_t mg_bottom(cudaStream_t s, const BottomLevels<T>& lv, const T* b, T* out,
                       const int32_t* active, int64_t B, Prof p) {
-  if (lv.L < 2 || lv.L > MAX_BOTTOM || lv.g[lv.L - 1].n != 2 || lv.g[0].n > BOTTOM_MAX_N)
+  if (lv.L < 2 || lv.L > MAX_BOTTOM || lv.g[lv.L - 1].n != 2 || lv.g[0].n > BOTTOM_MAX_N2)
     return cudaErrorInvalidValue;
-  const size_t smem = bottom_smem(lv);
+  size_t smem = 0;
+  for (int l = 0; l < lv.L; ++l) smem += 3 * (size_t)(lv.g[l].n + 1) * (lv.g[l].n + 1) * sizeof(T);
   // opt in once to the shared memory of the largest fused chain (64^2 .. 2^2)
   static const cudaError_t attr = [] {
     size_t most = 0;
-    for (int n = BOTTOM_MAX_N; n >= 2; n /= 2) most += 3 * (size_t)(n + 1) * (n + 1) * sizeof(T);
+    for (int n = BOTTOM_MAX_N2; n >= 2; n /= 2) most += 3 * (size_t)(n + 1) * (n + 1) * sizeof(T);
     cudaError_t e1 = cudaFuncSetAttribute(k_bottom2<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
     cudaError_t e2 = cudaFuncSetAttribute(k_bottom2<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
     return e1 != cudaSuccess ? e1 : e2;
@@ -1290,7 +1284,6 @@ cudaError_t mg_bottom(cudaStream_t s, const BottomLevels<T>& lv, const T* b, T* 
                                   int64_t, Prof, const T*);                                        \
   template cudaError_t qoi<T>(cudaStream_t, const Grid&, int, int, int, double, const T*, double*, \
                               int64_t, Prof);                                                      \
-  template size_t bottom_smem<T>(const BottomLevels<T>&);                                          \
   template cudaError_t mg_bottom<T>(cudaStream_t, const BottomLevels<T>&, const T*, T*,            \
                                     const int32_t*, int64_t, Prof);
 

@@ -852,8 +852,9 @@ __global__ void k_coarse3(Grid g, const T* __restrict__ K, const T* __restrict__
 }
 
 // Pointwise: tmp = e + P ec (trilinear prolongation of the coarse
-// correction; E == nullptr: tmp = P ec, the nested initial guess). A thread takes the fine nodes 2I and 2I + 1 of one fine row
-// (y, z): the coarse rows under it (1, 2 or 4 by the parity of y and z) are
+// correction; E == nullptr: tmp = P ec, the nested initial guess). A thread
+// takes the fine nodes 2I and 2I + 1 of one fine row (y, z): the coarse
+// rows under it (1, 2 or 4 by the parity of y and z) are
 // summed at coarse columns I and I + 1 once, the even node takes the first
 // sum, the odd node the mean of both, each divided by the number of rows.
 // Warps run along I with uniform parities, so the gathers do not diverge.
@@ -915,6 +916,174 @@ __global__ void __launch_bounds__(256) k_qoi3(Grid g, int box, int L, int H, dou
 
 inline dim3 grid3(const Grid& g, int64_t B) { return dim3((unsigned)g.sx, (unsigned)B, 1); }
 inline dim3 block3() { return dim3(BX, BY, 1); }
+
+
+// --------------------------------------------- fused bottom of the V-cycle
+
+constexpr int BOTTOM3_THREADS = 512;
+
+// Levels k0 .. K-1 of the 3D V-cycle for one sample per CTA, in shared
+// memory (per level: b, e and a third array for r1, then the level's
+// output): pre-smoothing from zero, residual, full weighting, the exact
+// coarsest solve, trilinear prolongation and post-smoothing, with a barrier
+// between steps instead of a launch. A thread forms the 27-point row of a
+// node from the kappa of its 8 elements (diagonal h/3 sum of the 8 kappa,
+// -h/12 times the shared kappa for the 12 edge and 8 corner neighbours, as
+// the z-march does); residuals are accumulated from b (in FP64 two FMAs
+// instead of a multiply, an FMA and a subtraction).
+template <class T>
+__global__ void __launch_bounds__(BOTTOM3_THREADS) k_bottom3(BottomLevels<T> lv, const T* __restrict__ Bv,
+                                                             T* __restrict__ Out,
+                                                             const int32_t* __restrict__ active,
+                                                             Prof prof) {
+  const int64_t smp = blockIdx.x;
+  if (!active[smp]) return;
+  extern __shared__ __align__(16) unsigned char bottom3_raw[];
+  T* sm = reinterpret_cast<T*>(bottom3_raw);
+  const int L = lv.L;
+  const int tid = threadIdx.x;
+  auto nodes = [&](int l) { const int N1 = lv.g[l].n + 1; return N1 * N1 * N1; };
+  auto base = [&](int l) -> T* {
+    int off = 0;
+    for (int m = 0; m < l; ++m) off += 3 * nodes(m);
+    return sm + off;
+  };
+  // f - (A e) at the interior node (i, j, k) of level l (e in shared memory)
+  auto resid = [&](int l, const T* e, int i, int j, int k, T f) -> T {
+    const Grid& g = lv.g[l];
+    const int n = g.n, N1 = n + 1, P = N1 * N1, o = (k * N1 + j) * N1 + i;
+    const T* K = lv.kap[l] + smp * g.es;
+    T kk[2][2][2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        const T* r = K + ((k - 1 + c) * n + (j - 1 + b)) * n + (i - 1);
+        kk[c][b][0] = __ldg(r);
+        kk[c][b][1] = __ldg(r + 1);
+      }
+    auto v = [&](int dx, int dy, int dz) { return e[o + dz * P + dy * N1 + dx]; };
+    T u = T(0);
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        u = fma(kk[0][q][p] + kk[1][q][p], v(2 * p - 1, 2 * q - 1, 0), u);   // edges in the xy-plane
+        u = fma(kk[q][0][p] + kk[q][1][p], v(2 * p - 1, 0, 2 * q - 1), u);   // edges in the xz-plane
+        u = fma(kk[q][p][0] + kk[q][p][1], v(0, 2 * p - 1, 2 * q - 1), u);   // edges in the yz-plane
+      }
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int a = 0; a < 2; ++a) u = fma(kk[c][b][a], v(2 * a - 1, 2 * b - 1, 2 * c - 1), u);
+    const T S = ((kk[0][0][0] + kk[0][0][1]) + (kk[0][1][0] + kk[0][1][1])) +
+                ((kk[1][0][0] + kk[1][0][1]) + (kk[1][1][0] + kk[1][1][1]));
+    return fma(T(g.c12), u, fma(-T(g.c3), S * v(0, 0, 0), f));
+  };
+  auto interior = [](int n, int i, int j, int k) {
+    return i > 0 && i < n && j > 0 && j < n && k > 0 && k < n;
+  };
+  {
+    T* b = base(0);
+    const T* src = Bv + smp * lv.g[0].ns;
+    for (int x = tid; x < nodes(0); x += BOTTOM3_THREADS) b[x] = src[x];
+  }
+  __syncthreads();
+  // down: e = W b, r1 = b - A e, b_{l+1} = R r1
+  for (int l = 0; l < L - 1; ++l) {
+    const int n = lv.g[l].n, N1 = n + 1, nn = nodes(l);
+    T* b = base(l);
+    T* e = b + nn;
+    T* t = e + nn;
+    const T* W = lv.w[l] + smp * lv.g[l].ns;
+    for (int x = tid; x < nn; x += BOTTOM3_THREADS) e[x] = __ldg(W + x) * b[x];
+    __syncthreads();
+    for (int x = tid; x < nn; x += BOTTOM3_THREADS) {
+      const int k = x / (N1 * N1), r = x - k * N1 * N1, j = r / N1, i = r - j * N1;
+      t[x] = interior(n, i, j, k) ? resid(l, e, i, j, k, b[x]) : T(0);
+    }
+    __syncthreads();
+    const int nc = lv.g[l + 1].n, C1 = nc + 1;
+    T* bc = base(l + 1);
+    for (int x = tid; x < C1 * C1 * C1; x += BOTTOM3_THREADS) {
+      const int K = x / (C1 * C1), r = x - K * C1 * C1, J = r / C1, I = r - J * C1;
+      T v = T(0);
+      if (interior(nc, I, J, K)) {
+        const int P = N1 * N1;
+        const T* rr0 = t + ((2 * K) * N1 + 2 * J) * N1 + 2 * I;
+        const T wt[3] = {T(0.5), T(1), T(0.5)};
+#pragma unroll
+        for (int dz = -1; dz <= 1; ++dz) {
+          T pl = T(0);
+#pragma unroll
+          for (int dy = -1; dy <= 1; ++dy) {
+            const T* rr = rr0 + dz * P + dy * N1;
+            const T row = T(0.5) * rr[-1] + rr[0] + T(0.5) * rr[1];
+            pl += wt[dy + 1] * row;
+          }
+          v += wt[dz + 1] * pl;
+        }
+      }
+      bc[x] = v;
+    }
+    __syncthreads();
+  }
+  // coarsest grid (n = 2, one unknown at (1, 1, 1)): e = b / D
+  {
+    T* b = base(L - 1);
+    T* e = b + 27;
+    if (tid == 0) {
+      const T* k = lv.kap[L - 1] + smp * lv.g[L - 1].es;
+      T s = T(0);
+      for (int q = 0; q < 8; ++q) s += k[q];
+      const T d = T(lv.g[L - 1].c3) * s;
+      for (int q = 0; q < 27; ++q) e[q] = T(0);
+      e[13] = b[13] / d;
+    }
+  }
+  __syncthreads();
+  // up: e += P e_c, out = e + W (b - A e)
+  for (int l = L - 2; l >= 0; --l) {
+    const int n = lv.g[l].n, N1 = n + 1, nn = nodes(l);
+    T* b = base(l);
+    T* e = b + nn;
+    T* t = e + nn;
+    const int C1 = lv.g[l + 1].n + 1, ncn = nodes(l + 1);
+    const T* ec = base(l + 1) + ((l + 1 == L - 1) ? ncn : 2 * ncn);
+    for (int x = tid; x < nn; x += BOTTOM3_THREADS) {
+      const int k = x / (N1 * N1), r = x - k * N1 * N1, j = r / N1, i = r - j * N1;
+      if (!interior(n, i, j, k)) continue;
+      const int I = i >> 1, J = j >> 1, Kc = k >> 1, ox = i & 1, oy = j & 1, oz = k & 1;
+      T s0 = T(0), s1 = T(0);
+      for (int c = 0; c <= oz; ++c)
+        for (int bq = 0; bq <= oy; ++bq) {
+          const T* row = ec + ((Kc + c) * C1 + (J + bq)) * C1;
+          s0 += row[I];
+          if (ox) s1 += row[I + 1];
+        }
+      const int rows = oy + oz;
+      const T inv = rows == 0 ? T(1) : (rows == 1 ? T(0.5) : T(0.25));
+      e[x] = e[x] + (ox ? T(0.5) * (s0 + s1) * inv : s0 * inv);
+    }
+    __syncthreads();
+    const T* W = lv.w[l] + smp * lv.g[l].ns;
+    for (int x = tid; x < nn; x += BOTTOM3_THREADS) {
+      const int k = x / (N1 * N1), r = x - k * N1 * N1, j = r / N1, i = r - j * N1;
+      T ov = T(0);
+      if (interior(n, i, j, k)) ov = fma(__ldg(W + x), resid(l, e, i, j, k, b[x]), e[x]);
+      t[x] = ov;
+    }
+    __syncthreads();
+  }
+  {
+    const T* t = base(0) + 2 * nodes(0);
+    T* dst = Out + smp * lv.g[0].ns;
+    for (int x = tid; x < nodes(0); x += BOTTOM3_THREADS) dst[x] = t[x];
+  }
+  if (prof.acc && tid == 0) atomicAdd(prof.acc, prof.per_sample);
+}
 
 }  // namespace
 
@@ -993,6 +1162,27 @@ cudaError_t resid64(cudaStream_t s, const Grid& g, const double* kappa, const do
   return cudaGetLastError();
 }
 
+template <class T>
+cudaError_t mg_bottom(cudaStream_t s, const BottomLevels<T>& lv, const T* b, T* out,
+                      const int32_t* active, int64_t B, Prof p) {
+  if (lv.L < 2 || lv.L > MAX_BOTTOM || lv.g[lv.L - 1].n != 2 || lv.g[0].n > BOTTOM_MAX_N3)
+    return cudaErrorInvalidValue;
+  size_t smem = 0;
+  for (int l = 0; l < lv.L; ++l) {
+    const size_t N1 = lv.g[l].n + 1;
+    smem += 3 * N1 * N1 * N1 * sizeof(T);
+  }
+  // opt in once to the shared memory of the largest fused chain (16^3 .. 2^3)
+  static const cudaError_t attr = [] {
+    size_t most = 0;
+    for (int n = BOTTOM_MAX_N3; n >= 2; n /= 2) most += 3 * (size_t)(n + 1) * (n + 1) * (n + 1) * sizeof(T);
+    return cudaFuncSetAttribute(k_bottom3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
+  }();
+  if (attr != cudaSuccess) return attr;
+  k_bottom3<T><<<(unsigned)B, BOTTOM3_THREADS, smem, s>>>(lv, b, out, active, p);
+  return cudaGetLastError();
+}
+
 #define MLMC_INST3(T)                                                                              \
   template cudaError_t apply<T>(cudaStream_t, const Grid&, const T*, const T*, T*, int64_t, Prof); \
   template cudaError_t winv<T>(cudaStream_t, const Grid&, const T*, double, T*, int64_t);          \
@@ -1009,7 +1199,9 @@ cudaError_t resid64(cudaStream_t s, const Grid& g, const double* kappa, const do
                                   const T*, const T*, const T*, T*, T*, const int32_t*, double*,   \
                                   int64_t, Prof);                                                  \
   template cudaError_t qoi<T>(cudaStream_t, const Grid&, int, int, int, double, const T*, double*, \
-                              int64_t, Prof);
+                              int64_t, Prof);                                                      \
+  template cudaError_t mg_bottom<T>(cudaStream_t, const BottomLevels<T>&, const T*, T*,            \
+                                    const int32_t*, int64_t, Prof);
 
 MLMC_INST3(double)
 MLMC_INST3(float)
