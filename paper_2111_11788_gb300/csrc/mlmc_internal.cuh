@@ -169,7 +169,8 @@ cudaError_t pcg_init(cudaStream_t s, const Grid& g, T* x, T* r, int64_t B, Prof 
 // coef (may be null): the FP64 form's precomputed operator coefficients
 // (coef()), used instead of kappa by the stencil kernels
 template <class T>
-cudaError_t coef(cudaStream_t s, const Grid& g, const T* kappa, T* coef, int64_t B);
+cudaError_t coef(cudaStream_t s, const Grid& g, const T* kappa, T* coef, int64_t B,
+                 double omega = 0.0, T* w = nullptr);
 template <class T>
 cudaError_t pcg_pq(cudaStream_t s, const Grid& g, const T* kappa, const T* z, const T* p_old,
                    T* p_new, T* q, const Scalars& sc, double* part, int64_t B, Prof p, const T* coef);

@@ -634,10 +634,15 @@ mlmc_status setup_levels(mlmc_plan p, const MeshInfo& mi, SolveWs<T>& w, int64_t
     }));
   }
   const double omega = (K > 1) ? p->cfg.mg_omega : 1.0;
-  for (int k = 0; k < std::max(1, K - 1); ++k)
-    CK(run(p, KID_SETUP, [&] { return op::winv<T>(s, mi.g[k], w.kap[k], omega, w.w[k], B); }));
+  const int kw = std::max(1, K - 1);   // levels that smooth (W = omega / D)
+  // levels with operator coefficients get W from the same kernel
   for (int k = 0; k < K; ++k)
-    if (w.coef[k]) CK(run(p, KID_SETUP, [&] { return d2::coef<T>(s, mi.g[k], w.kap[k], w.coef[k], B); }));
+    if (w.coef[k])
+      CK(run(p, KID_SETUP, [&] {
+        return d2::coef<T>(s, mi.g[k], w.kap[k], w.coef[k], B, omega, k < kw ? w.w[k] : nullptr);
+      }));
+  for (int k = 0; k < kw; ++k)
+    if (!w.coef[k]) CK(run(p, KID_SETUP, [&] { return op::winv<T>(s, mi.g[k], w.kap[k], omega, w.w[k], B); }));
   return MLMC_OK;
 }
 

@@ -586,10 +586,12 @@ __global__ void __launch_bounds__(SBLOCK) k_resid2(Grid g, const double* __restr
 
 // Coefficient blocks of the FP64 2D operator (see WinC): per sample
 // cd, ce, cn at every node (kappa outside the mesh counts as 0), then
-// q = -kappa/3 per element.
+// q = -kappa/3 per element; with W, also the smoother weights W = omega / D
+// (the same values k_winv2 computes, without a second pass over kappa).
 template <class T>
 __global__ void __launch_bounds__(FLAT_THREADS) k_coef2(Grid g, const T* __restrict__ K,
-                                                        T* __restrict__ Cb, int64_t cs) {
+                                                        T* __restrict__ Cb, int64_t cs, double omega,
+                                                        T* __restrict__ W) {
   const int64_t b = blockIdx.y;
   const int n = g.n, N1 = n + 1;
   const int64_t nn = (int64_t)N1 * N1, ne = (int64_t)n * n;
@@ -613,6 +615,7 @@ __global__ void __launch_bounds__(FLAT_THREADS) k_coef2(Grid g, const T* __restr
     cd[e] = d;
     ce[e] = xe;
     cn[e] = xn;
+    if (W) W[b * g.ns + e] = d != T(0) ? T(omega) / d : T(0);   // d = 0 exactly off the interior
     if (e < g.es) q[e] = e < ne ? -Consts<T>::c13 * __ldg(k + e) : T(0);
   }
 }
@@ -1140,8 +1143,8 @@ cudaError_t pcg_init(cudaStream_t s, const Grid& g, T* x, T* r, int64_t B, Prof 
 inline int64_t coef_stride(const Grid& g) { return 3 * g.ns + g.es; }
 
 template <class T>
-cudaError_t coef(cudaStream_t s, const Grid& g, const T* kappa, T* coef, int64_t B) {
-  k_coef2<T><<<fgrid(g, B), FLAT_THREADS, 0, s>>>(g, kappa, coef, coef_stride(g));
+cudaError_t coef(cudaStream_t s, const Grid& g, const T* kappa, T* coef, int64_t B, double omega, T* w) {
+  k_coef2<T><<<fgrid(g, B), FLAT_THREADS, 0, s>>>(g, kappa, coef, coef_stride(g), omega, w);
   return cudaGetLastError();
 }
 
@@ -1268,7 +1271,7 @@ cudaError_t mg_bottom(cudaStream_t s, const BottomLevels<T>& lv, const T* b, T* 
   template cudaError_t pcg_init<T>(cudaStream_t, const Grid&, T*, T*, int64_t, Prof);              \
   template cudaError_t pcg_pq<T>(cudaStream_t, const Grid&, const T*, const T*, const T*, T*, T*,  \
                                  const Scalars&, double*, int64_t, Prof, const T*);                \
-  template cudaError_t coef<T>(cudaStream_t, const Grid&, const T*, T*, int64_t);                  \
+  template cudaError_t coef<T>(cudaStream_t, const Grid&, const T*, T*, int64_t, double, T*);      \
   template cudaError_t pcg_xr<T>(cudaStream_t, const Grid&, T*, const T*, T*, const T*,            \
                                  const Scalars&, double*, int64_t, Prof);                          \
   template cudaError_t jacobi_z<T>(cudaStream_t, const Grid&, const T*, const T*, T*,              \
