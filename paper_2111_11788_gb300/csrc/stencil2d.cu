@@ -17,6 +17,10 @@
 // node as its row enters the window, and the next row is fetched before the
 // current one is consumed. No shared memory, no barriers.
 //
+// The multigrid levels of at most 64^2 cells below the finest run as one
+// kernel per V-cycle (k_bottom2): one CTA per sample, every level's arrays
+// in shared memory, a barrier between the steps instead of a launch.
+//
 // Pointwise kernels treat each sample's node array as a flat vector
 // (boundary entries are 0 and stay 0) with 16-byte vector accesses.
 //

@@ -30,7 +30,9 @@
 // paired FP32 instructions. The remaining pointwise kernels run one thread
 // per node on 32 x 8 tiles of each plane. Node arrays carry the boundary
 // nodes (always 0). Partials: one per CTA (g.tiles_s per sample for the
-// stencil kernels, g.tiles_q for the QoI).
+// stencil kernels, g.tiles_q for the QoI). The multigrid levels of at most
+// 16^3 cells below the finest run as one kernel per V-cycle (k_bottom3, one
+// CTA per sample in shared memory).
 #include "mlmc_internal.cuh"
 
 #include <type_traits>
