@@ -140,3 +140,27 @@ def test_round_bytes_grows_with_counts(m):
     assert zero == 0 and 0 < one < two and fine > coarse > 0
     cfg.dim = 7
     assert L.mlmc_round_bytes(ctypes.byref(cfg), arr([1, 1, 1])) == -1
+
+
+def test_round_bytes_counts_the_nested_guess_buffer(m):
+    """A coupled batch of level l > 0 keeps the coarse solution (one node
+    array of mesh l-1 per sample) while the fine mesh is solved; level 0 has
+    no coarse partner."""
+    L = m.lib()
+    arr = lambda xs: (ctypes.c_int64 * 3)(*xs)
+    for dim, n0 in ((2, 8), (3, 4)):
+        on = m.config(dim=dim, n_levels=3, coarse_cells=n0, solver="gmg", nested_guess=1)
+        off = m.config(dim=dim, n_levels=3, coarse_cells=n0, solver="gmg", nested_guess=0)
+        for level in range(3):
+            for B in (1, 7, 64):
+                counts = [0, 0, 0]
+                counts[level] = B
+                a = L.mlmc_round_bytes(ctypes.byref(on), arr(counts))
+                b = L.mlmc_round_bytes(ctypes.byref(off), arr(counts))
+                if level == 0:
+                    assert a == b
+                else:
+                    guess = B * m.node_stride(dim, n0 << (level - 1)) * 8
+                    assert guess <= a - b <= guess + 512
+    bad = m.config(nested_guess=2)
+    assert L.mlmc_round_bytes(ctypes.byref(bad), arr([1, 1, 1])) == -1
