@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstdint>
 
 #include "../../include/mlmc.h"
@@ -90,6 +91,20 @@ struct Grid {
 };
 
 Grid make_grid(int dim, int n, int z_chunk = 0);
+
+// Runs set() once per device of this process (function attributes such as
+// the shared-memory opt-in are per device); device ids below 64.
+template <class F>
+inline cudaError_t once_per_device(std::atomic<uint64_t>& done, F&& set) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const uint64_t bit = uint64_t(1) << (dev & 63);
+  if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+  e = set();
+  if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
+  return e;
+}
 
 // The small multigrid levels k0 .. K-1 of a V-cycle fused into one kernel,
 // one CTA per sample in shared memory: from b at level k0 (restricted by the

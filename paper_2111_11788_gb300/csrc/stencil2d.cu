@@ -1253,14 +1253,15 @@ cudaError_t mg_bottom(cudaStream_t s, const BottomLevels<T>& lv, const T* b, T* 
     return cudaErrorInvalidValue;
   size_t smem = 0;
   for (int l = 0; l < lv.L; ++l) smem += 3 * (size_t)(lv.g[l].n + 1) * (lv.g[l].n + 1) * sizeof(T);
-  // opt in once to the shared memory of the largest fused chain (64^2 .. 2^2)
-  static const cudaError_t attr = [] {
+  // opt in (once per device) to the shared memory of the largest fused chain (64^2 .. 2^2)
+  static std::atomic<uint64_t> opted{0};
+  const cudaError_t attr = once_per_device(opted, [] {
     size_t most = 0;
     for (int n = BOTTOM_MAX_N2; n >= 2; n /= 2) most += 3 * (size_t)(n + 1) * (n + 1) * sizeof(T);
     cudaError_t e1 = cudaFuncSetAttribute(k_bottom2<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
     cudaError_t e2 = cudaFuncSetAttribute(k_bottom2<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
     return e1 != cudaSuccess ? e1 : e2;
-  }();
+  });
   if (attr != cudaSuccess) return attr;
   if (lv.coef[0])
     k_bottom2<T, true><<<(unsigned)B, BOTTOM_THREADS, smem, s>>>(lv, b, out, active, p);

@@ -1174,12 +1174,13 @@ cudaError_t mg_bottom(cudaStream_t s, const BottomLevels<T>& lv, const T* b, T* 
     const size_t N1 = lv.g[l].n + 1;
     smem += 3 * N1 * N1 * N1 * sizeof(T);
   }
-  // opt in once to the shared memory of the largest fused chain (16^3 .. 2^3)
-  static const cudaError_t attr = [] {
+  // opt in (once per device) to the shared memory of the largest fused chain (16^3 .. 2^3)
+  static std::atomic<uint64_t> opted{0};
+  const cudaError_t attr = once_per_device(opted, [] {
     size_t most = 0;
     for (int n = BOTTOM_MAX_N3; n >= 2; n /= 2) most += 3 * (size_t)(n + 1) * (n + 1) * (n + 1) * sizeof(T);
     return cudaFuncSetAttribute(k_bottom3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
-  }();
+  });
   if (attr != cudaSuccess) return attr;
   k_bottom3<T><<<(unsigned)B, BOTTOM3_THREADS, smem, s>>>(lv, b, out, active, p);
   return cudaGetLastError();
