@@ -399,6 +399,17 @@ FP64_WORK = {
     (3, "mg_post"): (34.5, 57.5, 41.0), (3, "mg_pre"): (33.5, 54.5, 40.0),
     (3, "pcg_pq"): (34.5, 56.5, 40.0), (3, "resid64"): (33.5, 55.5, 24.0),
 }
+# DRAM bytes per output node measured by ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum of one launch whose arrays exceed L2), for the
+# dominant kernels whose capture matches the kernel as built; a launch's
+# traffic is scaled from it by the nodes the launch processes (its
+# algorithmic bytes / the per-node byte model).
+#   (dim, kernel, fp64 form?): (DRAM bytes per node, capture)
+DRAM_PER_NODE = {
+    (2, "mg_post", True): ((498.484224e6 + 59.262976e6) / (513 * 513 * 32),
+                           "ncu, k_mgpost2<double, 1>, 512^2 elements x 32 samples"),
+}
+
 GB300_SMS = 152
 DFMA_PER_SM_CLK = 2
 
@@ -412,6 +423,12 @@ def roofline_of(res, peaks, fp64_alu, dim=2):
          "avg_launch_us": round(1e3 * d_ms / max(d_launches, 1), 2),
          "time_shares": res["shares"], "per_kernel": res["per_kernel"]}
     work = FP64_WORK.get((dim, res["dom"]))
+    dram = DRAM_PER_NODE.get((dim, res["dom"], bool(fp64_alu)))
+    if dram is not None and work is not None and d_launches > 0:
+        nodes_per_launch = d_bytes / work[2] / d_launches
+        r["traffic"] = round(nodes_per_launch * dram[0])
+        r["traffic_source"] = ("%s: %.1f B/node (algorithmic %.0f), scaled to the average launch "
+                               "(%.3g nodes)" % (dram[1], dram[0], work[2], nodes_per_launch))
     # the FP64 kernels (every stencil of the FP64 form; the outer residual of
     # the mixed form) are bound by the FP64 pipe
     if (fp64_alu or res["dom"] == "resid64") and work is not None:
