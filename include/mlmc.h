@@ -173,8 +173,9 @@ mlmc_status mlmc_reset_stats(mlmc_plan plan);
 
 /* Coupled samples first..first+count-1 of `level` (Eq. (mlmc_average)):
  * one xi(level, i) per sample, solved on mesh `level` and, for level > 0,
- * on mesh level-1; Y = Q_f - Q_c is folded into the level state in sample
- * order. Optional host outputs (each `count` long, may be NULL): q_fine,
+ * on mesh level-1 (with nested_guess, mesh level-1 first, its solution
+ * seeding the mesh `level` solve); Y = Q_f - Q_c is folded into the level
+ * state in sample order. Optional host outputs (each `count` long, may be NULL): q_fine,
  * q_coarse (0 for level 0), iters (fine-mesh CG iterations, -1 if not
  * converged). Returns NOT_CONVERGED if any solve hit max_iter (its Y is
  * still folded). Samples must satisfy 0 <= i < 2^32. */
