@@ -74,16 +74,29 @@ def test_noalloc_matches_plan_solve_on_two_calls(m):
         st, q, it = _noalloc_solve(m, cfg, mesh, kap, count)
         assert st == m.MLMC_OK
         assert np.all(it_ref > 0)
-        assert np.array_equal(it, it_ref)
+        # mlmc_solve runs the FP64 2D stencils on precomputed operator
+        # coefficients and a fused V-cycle bottom; this entry point runs the
+        # kappa-form kernels and separate coarse levels. Same algorithm, so
+        # the QoIs agree to rounding; the stopping test may then trip one
+        # iteration apart.
+        assert np.all(np.abs(it - it_ref) <= 1)
         assert np.all(np.abs(q - q_ref) <= RTOL_Q * np.abs(q_ref))
 
 
 def test_noalloc_rejects_batches_beyond_the_scratch(m):
+    """A batch one sample too large is rejected before any launch. The buffers
+    passed are sized for the whole batch, so that a regression of the size
+    check shows as a failed assertion and never as an access beyond them."""
     cfg = m.config(dim=2, n_levels=5, coarse_cells=16, solver="gmg")
-    n = 16 << 4                                   # 256^2: ~6 MB of scratch per sample
-    kap = torch.zeros(m.elem_stride(2, n), dtype=torch.float64, device="cuda")
-    q = torch.zeros(1, dtype=torch.float64, device="cuda")
-    st = m.lib().mlmc_solve_noalloc(ctypes.byref(cfg), 4, ctypes.c_void_p(kap.data_ptr()), 5000,
-                                    ctypes.c_void_p(q.data_ptr()), None,
+    n = 16 << 4                                   # 256^2 cells
+    ns = m.node_stride(2, n)
+    # any PCG needs at least x, r, z, q and two directions on the finest mesh:
+    # count samples of those alone already exceed the scratch
+    count = m.NOALLOC_SCRATCH_BYTES // (6 * 8 * ns) + 1
+    kap = torch.ones(count * m.elem_stride(2, n), dtype=torch.float64, device="cuda")
+    q = torch.zeros(count, dtype=torch.float64, device="cuda")
+    it = torch.zeros(count, dtype=torch.int32, device="cuda")
+    st = m.lib().mlmc_solve_noalloc(ctypes.byref(cfg), 4, ctypes.c_void_p(kap.data_ptr()), count,
+                                    ctypes.c_void_p(q.data_ptr()), ctypes.c_void_p(it.data_ptr()),
                                     ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert st == m.MLMC_ERR_INVALID
