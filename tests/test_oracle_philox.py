@@ -19,8 +19,10 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def test_philox_matches_triton_library():
-    """Oracle Philox4x32-10 == triton.language.random.philox (CPU interpreter)."""
-    pytest.importorskip("triton")
+    """Oracle Philox4x32-10 == triton.language.random.philox (CPU interpreter).
+
+    This is the generator's only pin by an independent implementation, so a
+    missing Triton or interpreter fails the test instead of skipping it."""
     code = textwrap.dedent("""
         import numpy as np, torch, triton, triton.language as tl, sys
         from triton.language.random import philox as tphilox
@@ -50,8 +52,7 @@ def test_philox_matches_triton_library():
     env = dict(os.environ, TRITON_INTERPRET="1")
     res = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True,
                          text=True, timeout=600)
-    if res.returncode != 0 and "MATCH" not in res.stdout:
-        pytest.skip("triton interpreter unavailable: " + res.stderr[-300:])
+    assert res.returncode == 0, "triton interpreter run failed: " + res.stderr[-600:]
     assert "MATCH" in res.stdout and "MISMATCH" not in res.stdout
 
 
