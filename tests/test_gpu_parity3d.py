@@ -144,3 +144,48 @@ def test_3d_batched_full_size(m, precision, level, checked):
         rf, rc = oracle3(level, i)
         assert abs(qf[i] - rf) <= RTOL_Q * abs(rf)
         assert abs(qc[i] - rc) <= RTOL_Q * abs(rc)
+
+
+@functools.lru_cache(maxsize=None)
+def oracle4(level, i):
+    return omlmc.coupled_sample(workload("3d-mixed"), level, i)
+
+
+@pytest.mark.parametrize("level,count,checked", [(0, 32, (0, 31)), (1, 16, (0, 15)), (2, 8, (0, 7)),
+                                                 (3, 4, (0,))])
+def test_3d_mixed_workload_against_oracle(m, level, count, checked):
+    """The 3D mixed-precision workload at its own field and sizes (16^3..256^3
+    elements, corr_len 0.1, M = 343 tensor modes, box QoI, FP32 inner GMG-PCG
+    with FP64 refinement to rtol 1e-10): coupled samples of levels 0..3
+    (meshes up to 128^3) against the FP64 oracle, Q_f and Q_c each within
+    1e-9 relative."""
+    wl = workload("3d-mixed")
+    cfg = m.config_from_workload(wl)
+    assert cfg.precision == m.MIXED and cfg.modes_per_dim == 7
+    with m.Plan(cfg, stream()) as plan:
+        qf, qc, it = plan.sample_level(level, 0, count)
+        n, mean, m2, _ = plan.level_stats(level)
+    assert n == count and np.all(it > 0)
+    for i in checked:
+        rf, rc = oracle4(level, i)
+        assert abs(qf[i] - rf) <= RTOL_Q * abs(rf), (level, i, qf[i], rf)
+        if level > 0:
+            assert abs(qc[i] - rc) <= RTOL_Q * abs(rc), (level, i, qc[i], rc)
+
+
+def test_3d_mixed_workload_finest_level_against_fp64_form(m):
+    """Level 4 of the 3D mixed workload (256^3 fine, 128^3 coarse meshes, 4
+    coupled samples): the oracle cannot solve 16.6 M unknowns in test time, so
+    the mixed form is checked sample by sample against the plain FP64 form of
+    the library (Q_f and Q_c within 1e-9 relative), whose own parity with the
+    oracle is tested on every smaller mesh."""
+    wl = workload("3d-mixed")
+    got = {}
+    for precision in ("mixed", "fp64"):
+        cfg = m.config_from_workload(wl, precision=precision)
+        with m.Plan(cfg, stream()) as plan:
+            qf, qc, it = plan.sample_level(4, 0, 4)
+        assert np.all(it > 0)
+        got[precision] = (qf, qc)
+    for a, b in zip(got["mixed"], got["fp64"]):
+        assert np.all(np.abs(a - b) <= RTOL_Q * np.abs(b)), (a, b)
