@@ -266,6 +266,9 @@ cudaError_t prolong_guess(cudaStream_t s, const Grid& g, const Grid& coarse, con
 template <class T>
 cudaError_t mg_bottom(cudaStream_t s, const BottomLevels<T>& lv, const T* b, T* out,
                       const int32_t* active, int64_t B, Prof p);
+// bounded waits of the FP32 z-march that gave up (a copy never landed) since
+// the last call on this device; resets the count
+cudaError_t take_wait_timeouts(cudaStream_t s, unsigned* out);
 }  // namespace d3
 
 // Dimension dispatch used by the plan.

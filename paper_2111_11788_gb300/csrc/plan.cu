@@ -297,6 +297,8 @@ struct mlmc_plan_s {
   cudaEvent_t round_done = nullptr;                  // recorded after a launched round
   std::vector<size_t> round_off;                     // workspace regions of the launched round
   std::vector<int64_t> round_count;
+  std::vector<size_t> done_off;                      // the last finished round, while its
+  std::vector<int64_t> done_count;                   // per-sample values are still in place
   cudaStream_t cap_stream = nullptr;   // private stream the solve graphs are captured on
   // executed graphs whose kernel counts are settled at the next sync point
   std::vector<const GraphRec*> pending_graphs;
@@ -472,6 +474,7 @@ void clear_graphs(mlmc_plan p);
 mlmc_status settle_graph_launches(mlmc_plan p);
 
 mlmc_status ensure_ws(mlmc_plan p, size_t bytes) {
+  p->done_count.clear();   // the workspace is about to be reused
   if (bytes <= p->ws_bytes) return MLMC_OK;
   if (p->ws_borrowed) return MLMC_ERR_OOM;   // a borrowed workspace never grows
   if (p->ws) {
@@ -860,8 +863,15 @@ mlmc_status build_graph(mlmc_plan p, const std::function<mlmc_status()>& issue, 
   return MLMC_OK;
 }
 
-// Adds the kernels executed by graphs launched since the last sync point.
+// Adds the kernels executed by graphs launched since the last sync point;
+// for 3D mixed-form plans also checks that no bounded wait of the FP32
+// z-march gave up (MLMC_ERR_TIMEOUT).
 mlmc_status settle_graph_launches(mlmc_plan p) {
+  if (p->cfg.dim == 3 && p->cfg.precision == MLMC_MIXED) {
+    unsigned timeouts = 0;
+    CK(d3::take_wait_timeouts(p->stream, &timeouts));
+    if (timeouts) return MLMC_ERR_TIMEOUT;
+  }
   for (const GraphRec* r : p->pending_graphs) {
     p->launches += r->n_static;
     for (const auto& lp : r->loops) {
@@ -1278,6 +1288,8 @@ mlmc_status round_finish(mlmc_plan p, bool* bad) {
     for (int64_t b = 0; b < n; ++b)
       if (h[b] < 0 || (l > 0 && h[n + b] < 0)) *bad = true;
   }
+  p->done_off = p->round_off;
+  p->done_count = p->round_count;
   p->round_count.clear();
   return MLMC_OK;
 }
@@ -2090,6 +2102,26 @@ mlmc_status mlmc_round_end(mlmc_plan p) {
   mlmc_status st = round_finish(p, &bad);
   if (st != MLMC_OK) return st;
   return bad ? MLMC_ERR_NOT_CONVERGED : MLMC_OK;
+}
+
+mlmc_status mlmc_round_values(mlmc_plan p, int level, double* q_fine, double* q_coarse, int64_t count) {
+  if (!p || level < 0 || level >= p->cfg.n_levels || count < 0 || (count > 0 && !q_fine))
+    return MLMC_ERR_INVALID;
+  if (!p->round_count.empty() || level >= (int)p->done_count.size() || p->done_count[level] != count)
+    return MLMC_ERR_INVALID;
+  if (count == 0) return MLMC_OK;
+  Carve c((char*)p->ws + p->done_off[level]);
+  CoupledWs w;
+  carve_coupled(c, p->meshes[level], p->M, count, is_mixed(p), guess_ns_of(p->cfg, level), 0, w);
+  CK(cudaMemcpyAsync(q_fine, w.qf, sizeof(double) * count, cudaMemcpyDeviceToHost, p->stream));
+  if (q_coarse) {
+    if (level > 0)
+      CK(cudaMemcpyAsync(q_coarse, w.qc, sizeof(double) * count, cudaMemcpyDeviceToHost, p->stream));
+  }
+  CK(cudaStreamSynchronize(p->stream));
+  if (q_coarse && level == 0)
+    for (int64_t b = 0; b < count; ++b) q_coarse[b] = 0.0;
+  return MLMC_OK;
 }
 
 mlmc_status mlmc_allocation(mlmc_plan p, double eps, int64_t* N_out) {
