@@ -251,6 +251,19 @@ mlmc_status mlmc_round_end(mlmc_plan plan);
 /* Eq. (mlmc_num_samples) from the current level states (V_l = m2_l / n_l)
  * and the cost model: N_out (host, n_levels entries). */
 mlmc_status mlmc_allocation(mlmc_plan plan, double eps, int64_t* N_out);
+/* Per-sample values of the last finished round (after mlmc_round_end) for
+ * one level: q_fine[s] = Q_l and q_coarse[s] = Q_{l-1} (0 for level 0) of
+ * sample first[l] + s, s < count, where count must equal the round's count
+ * for the level (0: nothing to copy). Host arrays; q_coarse may be NULL.
+ * These are the Y_l = Q_l - Q_{l-1} terms of Eq. (mlmc_average) that the
+ * round folded into the level state; ranks that split a phase's samples
+ * exchange them (16 bytes per sample) and fold them in index order with
+ * mlmc_level_fold. Valid until the next call that uses the plan's workspace
+ * (a round, mlmc_sample_level, mlmc_solve, mlmc_autotune); INVALID after
+ * that, while a round is in flight or for a count that does not match.
+ * Synchronous. */
+mlmc_status mlmc_round_values(mlmc_plan plan, int level, double* q_fine, double* q_coarse,
+                              int64_t count);
 
 /* ---- autotuning ------------------------------------------------------ */
 
@@ -308,12 +321,16 @@ mlmc_status mlmc_solve(mlmc_plan plan, int mesh, const double* kappa, int64_t co
 /* Bytes of the static device scratch used by mlmc_solve_noalloc. */
 #define MLMC_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
 
-/* The batched PCG solve of mlmc_solve (same kernels, same results) for
- * callers that must not allocate device memory: code living inside another
- * framework's memory arena, latency-critical loops that cannot afford the
- * device synchronisation of cudaMalloc/cudaFree, and hosts that forbid
- * device allocation. The paper has no counterpart; it is a deployment
- * convenience of this library.
+/* The batched PCG solve of mlmc_solve (the same algorithm: Jacobi- or
+ * GMG-PCG with the same stopping test; the QoIs agree with mlmc_solve's to
+ * rounding, within 1e-9 relative, and the iteration counts can differ by
+ * one) for callers that must not allocate device memory: code living inside
+ * another framework's memory arena, latency-critical loops that cannot
+ * afford the device synchronisation of cudaMalloc/cudaFree, and hosts that
+ * forbid device allocation. It runs the kappa-form 2D kernels with separate
+ * coarse levels, where mlmc_solve's FP64 form uses precomputed operator
+ * coefficients and a fused V-cycle bottom. The paper has no counterpart; it
+ * is a deployment convenience of this library.
  *  - No plan is needed and nothing is allocated: the scratch is a static
  *    device array of MLMC_NOALLOC_SCRATCH_BYTES inside the library, held by
  *    every GPU that loads it until the process exits.
@@ -322,12 +339,14 @@ mlmc_status mlmc_solve(mlmc_plan plan, int mesh, const double* kappa, int64_t co
  *  - kappa: device element arrays (count x mlmc_elem_stride(2, n));
  *    q: device, count doubles (QoI per sample); iters: device, count int32
  *    (may be NULL; -1 = not converged). stream: borrowed cudaStream_t.
- *  - Returns MLMC_ERR_INVALID when count samples of this mesh need more
- *    scratch than MLMC_NOALLOC_SCRATCH_BYTES (e.g. about 40 GMG samples of
- *    128^2 cells, 10 of 256^2), or count > 65535; NOT_CONVERGED if a sample
- *    hit max_iter. Blocks until the results are on the device.
+ *  - Returns MLMC_ERR_INVALID, before launching anything, when count
+ *    samples of this mesh need more scratch than MLMC_NOALLOC_SCRATCH_BYTES
+ *    (e.g. about 40 GMG samples of 128^2 cells, 10 of 256^2), or
+ *    count > 65535; NOT_CONVERGED if a sample hit max_iter.
+ *  - The call blocks: it waits on `stream` between convergence checks and
+ *    returns once q and iters hold the results.
  *  - The first call on a device looks up the array's device address on
- *    that device (make it before any stream capture).
+ *    that device; make that first call before any stream capture.
  *  - Every call shares the one array, and the array keeps the last call's
  *    contents (each call writes every scratch entry it reads before reading
  *    it). Calls that overlap on the GPU (other streams, other host threads)
@@ -354,6 +373,17 @@ mlmc_status mlmc_profile_reset(mlmc_plan plan);
 mlmc_status mlmc_kernel_stats(mlmc_plan plan, int kernel_id, mlmc_kernel_stat* out);
 /* Number of kernel launches issued by this plan since creation. */
 int64_t mlmc_launch_count(mlmc_plan plan);
+
+/* ---- measurement ------------------------------------------------------ */
+
+/* Measured FP64 FMA rate of the current device, the peak that FP64-bound
+ * kernels are reported against (no passage of the paper; a measurement
+ * aid): independent FMA chains on every SM (4 CTAs of 256 threads per SM,
+ * 8 chains per thread), timed with CUDA events on `stream` (borrowed; NULL =
+ * legacy default stream), best of three launches after a warm-up; synchronous.
+ * tflops (host): FP64 TFLOP/s with an FMA counted as 2 flops; ms_out (host,
+ * may be NULL): the best launch time. Errors: INVALID (tflops NULL), CUDA. */
+mlmc_status mlmc_probe_fp64_rate(void* stream, double* tflops, double* ms_out);
 
 #ifdef __cplusplus
 }

@@ -26,6 +26,9 @@ GMG_PCG = 1
 FP64 = 0
 MIXED = 1
 
+# Bytes of the static device scratch of mlmc_solve_noalloc (include/mlmc.h).
+NOALLOC_SCRATCH_BYTES = 64 << 20
+
 
 class Config(ctypes.Structure):
     """Mirror of ``mlmc_config``."""
@@ -147,12 +150,14 @@ SIGNATURES = [
     ("mlmc_round_ready", _I, [_P]),
     ("mlmc_round_end", _I, [_P]),
     ("mlmc_allocation", _I, [_P, _D, _I64P]),
+    ("mlmc_round_values", _I, [_P, _I, _DP, _DP, _I64]),
     ("mlmc_plan_retarget", _I, [_P, ctypes.POINTER(Config)]),
     ("mlmc_round_bytes", _I64, [ctypes.POINTER(Config), _I64P]),
     ("mlmc_plan_set_workspace", _I, [_P, _P, ctypes.c_uint64]),
     ("mlmc_run_adaptive", _I, [_P, _D, _I64, ctypes.c_int32, _DP, _DP, _I64P, _I32P]),
     ("mlmc_level_fold", _I, [_P, _I, _DP, _DP, _I64]),
     ("mlmc_autotune", _I, [_P, _I, _I64, _I, ctypes.POINTER(TuneReport)]),
+    ("mlmc_probe_fp64_rate", _I, [_P, _DP, _DP]),
     # include/mlmc_sched.h
     ("mlmc_batch_size", _I64, [_I64, _I64, _I64, _D, _D]),
     ("mlmc_schedule_greedy", _I, [_I, _I64P, _I64P, _DP, _I64, _I, _D, _D, _D,
@@ -259,6 +264,14 @@ def config_from_workload(wl, **over):
     return config(**args)
 
 
+def probe_fp64_rate(stream=0):
+    """Measured FP64 FMA rate of the current device: (TFLOP/s, best launch ms)."""
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    check(lib().mlmc_probe_fp64_rate(_P(stream), ctypes.byref(tf), ctypes.byref(ms)),
+          "mlmc_probe_fp64_rate")
+    return tf.value, ms.value
+
+
 def node_stride(dim, n):
     return lib().mlmc_node_stride(dim, n)
 
@@ -347,6 +360,25 @@ class Plan:
         N = np.zeros(self.cfg.n_levels, dtype=np.int64)
         check(lib().mlmc_allocation(self._h, float(eps), N.ctypes.data_as(_I64P)), "mlmc_allocation")
         return N
+
+    def round(self, first, count):
+        """mlmc_round_begin + mlmc_round_end: samples first[l] .. first[l] + count[l] - 1
+        of every level as one graph-captured round; folded into the level states."""
+        import numpy as np
+        f = np.ascontiguousarray(first, dtype=np.int64)
+        c = np.ascontiguousarray(count, dtype=np.int64)
+        check(lib().mlmc_round_begin(self._h, f.ctypes.data_as(_I64P), c.ctypes.data_as(_I64P)),
+              "mlmc_round_begin")
+        check(lib().mlmc_round_end(self._h), "mlmc_round_end")
+
+    def round_values(self, level, count):
+        """mlmc_round_values: (Q_l, Q_{l-1}) of the last finished round's samples of `level`."""
+        import numpy as np
+        qf = np.zeros(count, dtype=np.float64)
+        qc = np.zeros(count, dtype=np.float64)
+        check(lib().mlmc_round_values(self._h, int(level), _dp(qf), _dp(qc), int(count)),
+              "mlmc_round_values")
+        return qf, qc
 
     def level_fold(self, level, qf, qc=None):
         """mlmc_level_fold: fold host sample values into the level state, in order."""
