@@ -14,6 +14,12 @@ computes the same allocation (Eq. (mlmc_num_samples)) and the same
 estimate, whatever the number of ranks or the order in which ranges were
 claimed.
 
+``run_rounds`` is the same exchange with one graph-captured round per rank
+and phase (shares fixed by Eq. (batch) with every rank claiming once), so
+the latency-bound coarse levels of a rank's share overlap its fine ones as
+in the single-GPU run; ``tensor_gather`` moves the values as one float64
+all-gather (NCCL between GPUs).
+
 The data path has one exchange per phase (the all-gather); everything
 else is local. ``run_sharded`` is transport-agnostic: the store, the
 all-gather and the per-rank sampler/fold/allocation callables are passed
@@ -119,3 +125,122 @@ def plan_callables(plan):
         plan.level_fold(level, qf, qc if level > 0 else None)
 
     return sample, fold, plan.reset_stats, plan.allocation
+
+
+def shares(missing, world):
+    """Contiguous shares of one level's missing samples, one per rank: the
+    batch of Eq. (batch) with every rank claiming once, b = ceil(missing /
+    world); rank r takes [r b, min((r + 1) b, missing)). Returns (start, size)
+    relative to the first missing sample, for every rank."""
+    b = -(-missing // world) if missing > 0 else 0
+    out = []
+    for r in range(world):
+        lo = min(r * b, missing)
+        out.append((lo, min(lo + b, missing) - lo))
+    return out
+
+
+def run_rounds(plan, rank, world, gather, eps=None, pilot=0, N_fixed=None, max_phases=64):
+    """Adaptive MLMC (Sec. 2.3, L fixed) over `world` ranks, one round per rank
+    per sampling phase.
+
+    In every phase each level's missing samples are split into contiguous
+    shares (``shares``); a rank runs its share of every level as one
+    graph-captured round (``plan.round``: a branch per level), reads the
+    round's per-sample values back (16 bytes per sample) and ``gather``s
+    them; every rank then folds all values of every level in index order
+    into its plan's level states (``plan.reset_stats``, ``plan.level_fold``),
+    so each rank holds the level states a single GPU builds for the same
+    samples, bit for bit, and computes the same allocation. ``gather(counts,
+    values)`` receives this rank's values (one float64 array per level: its
+    Q_l then its Q_{l-1}) and the counts of every rank and level
+    (counts[r][l]), and returns the arrays of every rank in rank order.
+
+    Returns (N per level, estimate, sum_l V_l / N_l) from the plan."""
+    import numpy as np
+    L1 = plan.cfg.n_levels
+    have = [0] * L1
+    target = [int(x) for x in N_fixed] if N_fixed is not None else [int(pilot)] * L1
+    hist_f = [np.zeros(0) for _ in range(L1)]
+    hist_c = [np.zeros(0) for _ in range(L1)]
+    for phase in range(max_phases):
+        part = [shares(target[l] - have[l], world) for l in range(L1)]
+        counts = [[part[l][r][1] for l in range(L1)] for r in range(world)]
+        first = [have[l] + part[l][rank][0] for l in range(L1)]
+        mine = counts[rank]
+        vals = [np.zeros(0) for _ in range(L1)]
+        in_round = False
+        if sum(mine):
+            try:
+                plan.round(first, mine)
+                in_round = True
+            except _m.MLMCError as e:
+                # the round does not fit the workspace together: level by level
+                if e.status != _m.MLMC_ERR_UNIMPLEMENTED:
+                    raise
+        for l in range(L1):
+            if not mine[l]:
+                continue
+            if in_round:
+                qf, qc = plan.round_values(l, mine[l])
+            else:
+                qf, qc, _ = plan.sample_level(l, first[l], mine[l])
+                qc = qc if l > 0 else np.zeros_like(qf)
+            vals[l] = np.concatenate([qf, qc])
+        every = gather(counts, vals)
+        for l in range(L1):
+            fs, cs = [hist_f[l]], [hist_c[l]]
+            for r in range(world):
+                c = counts[r][l]
+                fs.append(every[r][l][:c])
+                cs.append(every[r][l][c:2 * c])
+            hist_f[l] = np.concatenate(fs)
+            hist_c[l] = np.concatenate(cs)
+        plan.reset_stats()
+        for l in range(L1):
+            if hist_f[l].size:
+                plan.level_fold(l, hist_f[l], hist_c[l] if l > 0 else None)
+        have = list(target)
+        if N_fixed is not None:
+            break
+        need = plan.allocation(eps)
+        more = False
+        for l in range(L1):
+            if need[l] > target[l]:
+                target[l] = int(need[l])
+                more = True
+        if not more:
+            break
+    q, v = plan.estimate()
+    return have, q, v
+
+
+def tensor_gather(dist, device):
+    """``gather`` for run_rounds over a torch.distributed process group: the
+    values of every rank travel in one all_gather_into_tensor of float64 (NCCL
+    on GPUs, gloo on CPUs); the receiving side splits them by the counts every
+    rank already knows."""
+    import numpy as np
+    import torch
+
+    def gather(counts, vals):
+        world = len(counts)
+        sizes = [2 * sum(c) for c in counts]
+        width = max(1, max(sizes))
+        mine = np.concatenate(vals) if vals else np.zeros(0)
+        buf = torch.zeros(width, dtype=torch.float64, device=device)
+        if mine.size:
+            buf[:mine.size] = torch.from_numpy(mine).to(device)
+        out = torch.empty(world * width, dtype=torch.float64, device=device)
+        dist.all_gather_into_tensor(out, buf)
+        host = out.cpu().numpy().reshape(world, width)
+        every = []
+        for r in range(world):
+            arrs, o = [], 0
+            for c in counts[r]:
+                arrs.append(host[r, o:o + 2 * c].copy())
+                o += 2 * c
+            every.append(arrs)
+        return every
+
+    return gather

@@ -51,3 +51,28 @@ def test_sharded_run_equals_plan_run(m, dim, precision):
     assert N == [int(x) for x in N_ref]
     assert (q, v) == (q_ref, v_ref)
     assert len(claimed) > 3
+
+
+@pytest.mark.parametrize("dim,precision", [(2, "fp64"), (3, "mixed")])
+def test_round_sharded_run_equals_plan_run(m, dim, precision):
+    """run_rounds on one rank (one graph-captured round per phase, values read
+    back with mlmc_round_values and refolded in index order) equals mlmc_run
+    bit for bit; the multi-rank exchange is covered on CPU ranks."""
+    from paper_2111_11788_gb300.distributed import run_rounds
+    if dim == 2:
+        wl = small_case(2, n0=8, levels=3, m=4, solver="gmg", precision=precision)
+    else:
+        wl = small_case(3, n0=4, levels=3, m=3, solver="gmg", qoi="box", precision=precision)
+    eps, pilot = 1e-3, 10
+    cfg = m.config_from_workload(wl)
+    s = torch.cuda.current_stream().cuda_stream
+    with m.Plan(cfg, s) as plan:
+        q_ref, v_ref, N_ref = plan.run(eps=eps, pilot=pilot)
+    with m.Plan(cfg, s) as plan:
+        N, q, v = run_rounds(plan, 0, 1, lambda counts, vals: [vals], eps=eps, pilot=pilot)
+        # the values of the last round can no longer be read once the workspace is reused
+        plan.sample_level(0, 10 ** 6, 1)
+        with pytest.raises(m.MLMCError):
+            plan.round_values(0, 1)
+    assert N == [int(x) for x in N_ref]
+    assert (q, v) == (q_ref, v_ref)
