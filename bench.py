@@ -148,54 +148,130 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ CPU oracle
+#
+# The oracle runs in a pool of spawned worker processes (never forked after
+# the first CUDA call), each with single-threaded BLAS. A task is one coupled
+# sample (level, i): the worker returns (Q_l, Q_{l-1}, its own elapsed time).
 
-def oracle_sample_code(name, levels):
-    return (
-        "import sys, time, json; sys.path.insert(0, %r)\n"
-        "from synth import workload\n"
-        "from oracle import mlmc\n"
-        "wl = workload(%r)\n"
-        "t = time.perf_counter(); dofs = 0\n"
-        "for l in %r:\n"
-        "    mlmc.coupled_sample(wl, l, 0)\n"
-        "    n = wl['n0'] << l; d = (n - 1) ** wl['dim']\n"
-        "    dofs += d + ((n // 2 - 1) ** wl['dim'] if l > 0 else 0)\n"
-        "dt = time.perf_counter() - t\n"
-        "print(json.dumps({'dofs': dofs, 'seconds': dt}))\n" % (ROOT, name, list(levels)))
+_ORACLE_ENV = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1"}
 
 
-def run_oracle_sample(name, levels):
-    """One coupled sample per listed level with the oracle, single-threaded BLAS."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    res = subprocess.run([sys.executable, "-c", oracle_sample_code(name, levels)], env=env,
-                         capture_output=True, text=True, timeout=1800)
-    if res.returncode != 0:
-        raise RuntimeError("oracle sample failed: " + res.stderr[-2000:])
-    out = json.loads(res.stdout.strip().splitlines()[-1])
-    return out["dofs"], out["seconds"]
+def _oracle_task(args):
+    name, level, i = args
+    sys.path.insert(0, ROOT)
+    from oracle import mlmc as omlmc
+    from synth import workload as wlf
+    t = time.perf_counter()
+    qf, qc = omlmc.coupled_sample(wlf(name), level, i)
+    return level, i, qf, qc, time.perf_counter() - t
 
 
-def cpu_baseline(name, levels):
-    dofs, sec = run_oracle_sample(name, levels)
-    return {"value": dofs / sec, "unit": "coupled DOF-solves/s", "cores": 1, "kind": "oracle",
-            "sample": "one coupled sample (sample 0) on each of levels %s of the %s workload: "
-                      "dense KLE, assembled Q1 matrix, sparse LU solve with refinement; "
-                      "%d coupled DOFs in %.1f s" % (list(levels), name, dofs, sec)}
+class OraclePool:
+    """nproc single-threaded oracle workers (spawn start method)."""
+
+    def __init__(self, procs=None):
+        import multiprocessing as mp
+        self.procs = procs or (os.cpu_count() or 1)
+        for k, v in _ORACLE_ENV.items():
+            os.environ.setdefault(k, v)
+        self.pool = mp.get_context("spawn").Pool(self.procs)
+        self.pool.map(_noop, range(self.procs))      # workers up and importable
+
+    def run(self, tasks):
+        t = time.perf_counter()
+        out = self.pool.map(_oracle_task, tasks, chunksize=1)
+        return out, time.perf_counter() - t
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def _noop(_):
+    sys.path.insert(0, ROOT)
+    import oracle.mlmc  # noqa: F401
+    return os.getpid()
+
+
+def cpu_baseline(name, N, pool):
+    """The oracle on the host cores, reported beside the GPU number.
+
+    single thread: one coupled sample (sample 0) of every level, each in its
+    own worker at the same time (one core each), giving the per-sample time
+    t_l; all cores: nproc coupled samples of one level at once, giving the
+    speed-up S of the host over one core. Both are extrapolated to the GPU
+    run's sample counts N_l: time to eps T1 = sum N_l t_l single-threaded and
+    T1 / S on all cores. Returns (line, oracle values of sample 0 per level)."""
+    wl = workload(name)
+    L = wl["levels"]
+    res, _ = pool.run([(name, l, 0) for l in range(L)])
+    t1 = {l: dt for l, _, _, _, dt in res}
+    ref = {l: (qf, qc) for l, _, qf, qc, _ in res}
+    la = min(4, L - 1)
+    par, wall = pool.run([(name, la, 1 + k) for k in range(pool.procs)])
+    speedup = pool.procs * t1[la] / wall
+    T1 = sum(N[l] * t1[l] for l in range(L))
+    dofs = sum(N[l] * coupled_dofs(wl, l) for l in range(L))
+    line = {"value": dofs / (T1 / speedup), "unit": "coupled DOF-solves/s", "cores": pool.procs,
+            "kind": "oracle", "nproc": os.cpu_count(), "extrapolated": True,
+            "time_to_eps_s": T1 / speedup,
+            "single_thread": {"value": dofs / T1, "cores": 1, "time_to_eps_s": T1},
+            "per_sample_s": [round(t1[l], 3) for l in range(L)],
+            "all_core_speedup": round(speedup, 2),
+            "sample": ("measured: one coupled sample (sample 0) of each of levels 0..%d of the %s "
+                       "workload, single-threaded, one worker per level; %d coupled samples of "
+                       "level %d on %d workers at once (%.1f s wall); extrapolated to the GPU run's "
+                       "N = %s. Oracle: dense KLE, assembled Q1 matrix, sparse LU (or Jacobi-PCG "
+                       "to 1e-13 above its size limit)" % (L - 1, name, pool.procs, la, pool.procs,
+                                                          wall, list(N)))}
+    return line, ref
+
+
+def result_errors(m, wl, cfg, stream, ref):
+    """Per-result relative error of one GPU form against the oracle: Q_l and
+    Q_{l-1} of sample 0 of every level (a fresh plan, one coupled sample per
+    call)."""
+    import torch
+    per, worst = [], 0.0
+    with torch.cuda.stream(stream):
+        with m.Plan(cfg, stream.cuda_stream) as plan:
+            for l in sorted(ref):
+                qf, qc, _ = plan.sample_level(l, 0, 1)
+                rf, rc = ref[l]
+                ef = abs(float(qf[0]) - rf) / abs(rf)
+                per.append([l, "fine", ef])
+                worst = max(worst, ef)
+                if l > 0:
+                    ec = abs(float(qc[0]) - rc) / abs(rc)
+                    per.append([l, "coarse", ec])
+                    worst = max(worst, ec)
+    return {"max_rel": worst, "per_result": per,
+            "sample": "Q_l and Q_(l-1) of sample 0 of levels %s against the FP64 oracle"
+                      % sorted(ref)}
 
 
 def bench_reference(args):
+    """The oracle as the reference arm: each step runs nproc coupled samples
+    at once on the host cores (levels 0..min(4, L-1) in turn, one per
+    worker); value = coupled DOFs of the step / its wall time."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     wl = workload(args.workload)
     levels = list(range(min(wl["levels"], 5)))
-    for _ in range(args.warmup if args.warmup < 1 else 1):
-        run_oracle_sample(args.workload, levels[:2])
-    t_dofs, t_sec = 0, 0.0
-    for _ in range(args.steps):
-        d, s = run_oracle_sample(args.workload, levels)
-        t_dofs += d
-        t_sec += s
+    pool = OraclePool()
+    try:
+        def tasks(step):
+            return [(args.workload, levels[k % len(levels)], 1000 * step + k) for k in range(pool.procs)]
+        for w in range(min(args.warmup, 2)):
+            pool.run(tasks(10 ** 4 + w))
+        t_dofs, t_sec = 0, 0.0
+        for st in range(args.steps):
+            out, wall = pool.run(tasks(st))
+            t_dofs += sum(coupled_dofs(wl, l) for l, _, _, _, _ in out)
+            t_sec += wall
+    finally:
+        pool.close()
     value = t_dofs / t_sec
     line = {"impl": "reference", "metric": "coupled DOF-solves/s", "value": value,
             "unit": "coupled DOF-solves/s", "n_gpus": args.gpus, "steps": args.steps,
@@ -203,10 +279,13 @@ def bench_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": args.workload + ": " + workload_desc(wl),
-                       "sample": "levels %s, sample 0 each" % levels},
-            "cpu_baseline": {"value": value, "unit": "coupled DOF-solves/s", "cores": 1,
+                       "sample": "per step %d coupled samples on %d workers, levels %s in turn"
+                                 % (pool.procs, pool.procs, levels)},
+            "cpu_baseline": {"value": value, "unit": "coupled DOF-solves/s", "cores": pool.procs,
                              "kind": "oracle",
-                             "sample": "one coupled sample per level %s per step" % levels},
+                             "sample": "per step one coupled sample per host core, levels %s in "
+                                       "turn (levels above 4 are left out to bound the step)"
+                                       % levels},
             "e2e": {"value": value, "unit": "coupled DOF-solves/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -214,18 +293,50 @@ def bench_reference(args):
 
 # ------------------------------------------------------------------- GPU
 
-def measure_form(m, wl, cfg, stream, args, world, barrier, with_e2e):
+def tuned_config(m, cfg, tune):
+    """The tuned settings are configuration fields: a user's plan takes them directly."""
+    cfg2 = m.Config.from_buffer_copy(cfg)
+    if tune is not None:
+        cfg2.inner_rtol, cfg2.mg_omega, cfg2.z_chunk = (tune["inner_rtol"], tune["mg_omega"],
+                                                        tune["z_chunk"])
+    return cfg2
+
+
+def mlmc_step(plan, wl, rank, world, gather):
+    """One MLMC estimate: mlmc_run on one GPU; on several, the same estimate
+    with each phase's samples split over the ranks (distributed.run_rounds)."""
+    fixed = list(wl["N"]) if wl.get("N") is not None else None
+    if world == 1:
+        if fixed is not None:
+            return plan.run(N=fixed)
+        return plan.run(eps=wl["eps"], pilot=wl["pilot"])
+    from paper_2111_11788_gb300.distributed import run_rounds
+    N, q, v = run_rounds(plan, rank, world, gather, eps=wl.get("eps"), pilot=wl.get("pilot", 0),
+                         N_fixed=fixed)
+    return q, v, N
+
+
+def measure_form(m, wl, cfg, stream, args, world, barrier, with_e2e, rank=0, gather=None):
     """Warm up, trace one run, then time args.steps MLMC runs of one form."""
     import torch
     sh = stream.cuda_stream
     with torch.cuda.stream(stream):
+        tune = None
+        if args.autotune:
+            # tuned on rank 0 and shared, so that every rank solves with the same settings
+            if rank == 0:
+                with m.Plan(cfg, sh) as tp:
+                    tune = tp.autotune(wl["levels"] - 1, 32 if wl["dim"] == 2 else 16, 7)
+            if world > 1:
+                import torch.distributed as dist
+                box = [tune]
+                dist.broadcast_object_list(box, src=0)
+                tune = box[0]
+        cfg = tuned_config(m, cfg, tune)
         plan = m.Plan(cfg, sh)
-        tune = plan.autotune(wl["levels"] - 1, 32 if wl["dim"] == 2 else 16, 7) if args.autotune else None
         N = None
         def one_run():
-            if wl.get("N") is not None:
-                return plan.run(N=list(wl["N"]))
-            return plan.run(eps=wl["eps"], pilot=wl["pilot"])
+            return mlmc_step(plan, wl, rank, world, gather)
         for _ in range(max(args.warmup, 1)):
             q, v, N = one_run()
         dofs_step = sum(int(N[l]) * coupled_dofs(wl, l) for l in range(wl["levels"]))
@@ -267,22 +378,15 @@ def measure_form(m, wl, cfg, stream, args, world, barrier, with_e2e):
         dstat = plan.kernel_stats()[dom]
         plan.profile(0)
         wall = []
-        # the tuned settings are configuration fields: a user's plan takes them directly
-        cfg2 = m.Config.from_buffer_copy(cfg)
-        if tune is not None:
-            cfg2.inner_rtol, cfg2.mg_omega, cfg2.z_chunk = (tune["inner_rtol"], tune["mg_omega"],
-                                                            tune["z_chunk"])
         if with_e2e:
             # end to end through the public API: plan creation (host KLE roots,
             # table upload), the run, results back to host, plan destruction
             for _ in range(args.steps):
+                barrier()
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-                p2 = m.Plan(cfg2, sh)
-                if wl.get("N") is not None:
-                    p2.run(N=list(wl["N"]))
-                else:
-                    p2.run(eps=wl["eps"], pilot=wl["pilot"])
+                p2 = m.Plan(cfg, sh)
+                mlmc_step(p2, wl, rank, world, gather)
                 p2.close()
                 torch.cuda.synchronize()
                 wall.append(time.perf_counter() - t0)
@@ -414,7 +518,7 @@ GB300_SMS = 152
 DFMA_PER_SM_CLK = 2
 
 
-def roofline_of(res, peaks, fp64_alu, dim=2):
+def roofline_of(res, peaks, fp64_alu, dim=2, fp64_probe=None):
     d_launches, d_ms, d_bytes = res["dstat"]
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     src = "measured" if "hbm_gbs" in peaks else "fallback"
@@ -437,18 +541,28 @@ def roofline_of(res, peaks, fp64_alu, dim=2):
         # FP64 instructions/s against the pipe's 2 instructions per SM per cycle
         ins, flops, nbytes = work
         mhz = (res.get("clocks") or {}).get("sm_mhz") or 2070.0
-        peak = DFMA_PER_SM_CLK * 2 * GB300_SMS * mhz * 1e6 / 1e12
+        derived = DFMA_PER_SM_CLK * 2 * GB300_SMS * mhz * 1e6 / 1e12
         achieved = gbs * flops / nbytes / 1e3
         ipeak = DFMA_PER_SM_CLK * GB300_SMS * mhz * 1e6 / 1e12
         iach = gbs * ins / nbytes / 1e3
+        if fp64_probe:
+            peak = fp64_probe["tflops"]
+            psrc = ("measured: FP64 FMA-chain probe (mlmc_probe_fp64_rate, %.3f ms per launch) run "
+                    "by this bench before the timed region; derived %d SMs x %d DFMA/cycle x 2 "
+                    "flops x %.0f MHz = %.4f TFLOP/s" % (fp64_probe["ms"], GB300_SMS,
+                                                         DFMA_PER_SM_CLK, mhz, derived))
+        else:
+            peak = derived
+            psrc = ("derived: %d SMs x %d DFMA/cycle x 2 flops x %.0f MHz (median under load)"
+                    % (GB300_SMS, DFMA_PER_SM_CLK, mhz))
         r.update({"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4),
-                  "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                  "peak_source": "derived: %d SMs x %d DFMA/cycle x 2 flops x %.0f MHz (median "
-                                 "under load)" % (GB300_SMS, DFMA_PER_SM_CLK, mhz),
+                  "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "peak_source": psrc,
                   "fp64_instructions": {"achieved": round(iach, 4), "peak": round(ipeak, 4),
                                         "unit": "T instr/s", "frac": round(iach / ipeak, 4)},
+                  # the same launches against HBM, in algorithmic bytes
                   "hbm": {"achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
-                          "frac": round(gbs / hbm_peak, 4), "peak_source": src}})
+                          "frac": round(gbs / hbm_peak, 4), "peak_source": src,
+                          "bytes_per_node": nbytes}})
     else:
         r.update({"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                   "frac": round(gbs / hbm_peak, 4), "peak_source": src})
@@ -480,14 +594,22 @@ def bench_ours(args):
         return
     wl = workload(args.workload)
     stream = torch.cuda.Stream()
-    # replicas: each rank runs an independent MLMC estimate on its own Philox stream
+    # the FP64 peak of this device, measured (the FP64 form is bound by it)
+    tf, pms = m.probe_fp64_rate(stream.cuda_stream)
+    fp64_probe = {"tflops": tf, "ms": pms}
+    # several GPUs share one MLMC estimate: every phase's samples are split
+    # over the ranks and their values all-gathered (NCCL) and folded in order
+    gather = None
+    if world > 1:
+        from paper_2111_11788_gb300.distributed import tensor_gather
+        gather = tensor_gather(dist, "cuda")
     forms = {}
     for form in (args.form, "mixed" if args.form == "fp64" else "fp64"):
         if form != args.form and args.single_form:
             continue
-        cfg = m.config_from_workload(wl, stream_id=rank, precision=form)
+        cfg = m.config_from_workload(wl, precision=form)
         forms[form] = measure_form(m, wl, cfg, stream, args, world, barrier,
-                                   with_e2e=(form == args.form))
+                                   with_e2e=(form == args.form), rank=rank, gather=gather)
 
     def reduce_max(x):
         t = torch.tensor([x], device="cuda", dtype=torch.float64)
@@ -502,8 +624,9 @@ def bench_ours(args):
     main = forms[args.form]
     ms = reduce_max(main["ms"])
     e2e_s = reduce_max(sum(main["wall"]))
-    value = world * main["dofs_step"] * args.steps / (ms / 1e3)
-    e2e_value = world * main["dofs_step"] * args.steps / e2e_s
+    # one estimate per step whatever the number of GPUs (strong scaling)
+    value = main["dofs_step"] * args.steps / (ms / 1e3)
+    e2e_value = main["dofs_step"] * args.steps / e2e_s
     h2d = 8 * 2 * wl["m"] + 4 * wl["m"] + 8 * wl["levels"]
     d2h = 8 * 2 + 8 * wl["levels"]
     other = {}
@@ -511,27 +634,32 @@ def bench_ours(args):
         if form == args.form:
             continue
         oms = reduce_max(res["ms"])
-        other[form] = {"value": world * res["dofs_step"] * args.steps / (oms / 1e3),
+        other[form] = {"value": res["dofs_step"] * args.steps / (oms / 1e3),
                        "unit": "coupled DOF-solves/s", "ms_per_step": oms / args.steps,
                        "time_to_eps_s": oms / args.steps / 1e3,
                        "samples_per_level": res["N"], "q_hat": res["q"], "stat_var": res["v"],
                        "gpu_launches": int(res["launches"]), "clocks": res["clocks"],
                        "autotune": res["tune"],
-                       "roofline": roofline_of(res, peaks, fp64_alu=(form == "fp64"), dim=wl["dim"])}
+                       "roofline": roofline_of(res, peaks, fp64_alu=(form == "fp64"), dim=wl["dim"],
+                                               fp64_probe=fp64_probe)}
     if rank == 0:
         names = {"fp64": "plain FP64", "mixed": "mixed: FP32 inner PCG + FP64 refinement"}
         line = {"metric": "coupled DOF-solves/s", "value": value, "unit": "coupled DOF-solves/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": ms / args.steps, "time_to_eps_s": ms / args.steps / 1e3,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
                 "dtype": "f64" if args.form == "fp64" else "f32+f64", "data": "synthetic",
                 "config": {"workload": args.workload + ": " + workload_desc(wl),
                            "form": names[args.form],
                            "samples_per_level": main["N"],
                            "q_hat": main["q"], "stat_var": main["v"],
                            "l2": "working set of the 512^2/1024^2 levels (GBs) exceeds the 129 MB L2",
-                           "parallelism": "replicas" if world > 1 else "single GPU"},
-                "roofline": roofline_of(main, peaks, fp64_alu=(args.form == "fp64"), dim=wl["dim"]),
+                           "parallelism": ("one estimate over %d GPUs: each phase's samples "
+                                           "split by Eq. (batch), values all-gathered (NCCL) "
+                                           "and folded in index order" % world)
+                                          if world > 1 else "single GPU"},
+                "roofline": roofline_of(main, peaks, fp64_alu=(args.form == "fp64"), dim=wl["dim"],
+                                        fp64_probe=fp64_probe),
                 "clocks": main["clocks"], "gpu_launches": int(main["launches"]),
                 "autotune": main["tune"],
                 "e2e": {"value": e2e_value, "unit": "coupled DOF-solves/s",
@@ -540,7 +668,19 @@ def bench_ours(args):
         if args.serve > 0:
             line["serving"] = serving_both(m, args, local)
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(args.workload, list(range(min(wl["levels"], 5))))
+            pool = OraclePool()
+            try:
+                line["cpu_baseline"], ref = cpu_baseline(args.workload, main["N"], pool)
+            finally:
+                pool.close()
+            # error of every form against the oracle, result by result
+            for form in forms:
+                cfgf = m.config_from_workload(wl, precision=form)
+                err = result_errors(m, wl, cfgf, stream, ref)
+                if form == args.form:
+                    line["error_vs_oracle"] = err
+                else:
+                    line["other_forms"][names[form]]["error_vs_oracle"] = err
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
