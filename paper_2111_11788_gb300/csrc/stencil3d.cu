@@ -774,46 +774,37 @@ __global__ void __launch_bounds__(ZTHREADS, 2) k_zm3f(Grid g, const float* __res
   prof_tick3(prof);
 }
 
-// ---------------------------------------- FP32 z-march, bulk-copy staging
+// ------------------------------------ FP32 z-march, TMA bulk-copy staging
 //
-// k_zm3t is k_zm3f with its planes staged by the copy engine instead of by
-// per-element cp.async: each row of a staged plane is one asynchronous
-// bulk copy (cp.async.bulk, global -> shared, completing on an mbarrier), so
-// a plane of a vector costs at most 18 copy instructions for the CTA and no
-// address, predicate or register work per element. Used for meshes with
-// 4 | n (every mesh of the workloads from 8 cells per side up), where the
-// row offsets of node and element arrays have a fixed alignment pattern:
-//  - node arrays: a row of (n + 1) values has an odd pitch, so a row's first
-//    needed value (column tx0 - 1) sits sh = (offset mod 4) floats past a
-//    16-byte boundary. The copy starts at that boundary and moves 40 floats
-//    (160 bytes) to row slot yl at yl * ZT_VP + K - sh, with the row pitch
-//    ZT_VP = 1 (mod 4) = n + 1 (mod 4): then every copy destination is 16-byte
-//    aligned and the value of column x of every row lands at
-//    K + yl * ZT_VP + (x - tx0 + 1), K = the shift of row 0 (one constant per
-//    plane). Rows and planes outside 1..n-1 are never copied: their slots
-//    hold zeros. Columns 0 and n inside a copied row hold the array's
-//    boundary values; the few threads whose stencil touches them read 0.
-//  - element arrays (pitch n, 4 | n): the copy covers columns tx0 - 4 ..
-//    tx0 + 35 clipped to the row (no read before the sample or after its last
-//    element); elements outside the mesh keep the zeros of the slot.
-// The ring has ZT_S slots, ZT_S - 1 planes in flight; a slot's mbarrier is
-// armed with the plane's byte count by one lane, and its copies are issued
-// by lanes of warp 0 (one row each). Waits are bounded: a wait that gives up
-// counts a timeout in g_zt_timeouts (read by the host at its sync points),
-// drains the copies still in flight (bounded again) and ends the CTA.
-constexpr int ZT_S = 4;                      // ring slots
-constexpr int ZT_VP = 49, ZT_KP = 48;        // row pitch (floats) of vector / kappa slots
-constexpr int ZT_VROWS = ZTY + 2, ZT_KROWS = ZTY + 1;
-constexpr int ZT_VCOPY = 40;                 // floats per vector row copy
-constexpr int ZT_VBUF = 880, ZT_KBUF = 856;  // floats per slot and array
-constexpr int ZT_VWIN = ZTX + 2;             // consumed values per vector row
-constexpr int ZT_WAIT_TRIES = 1 << 22;         // bounded waits: tries and SM cycles (~2 s)
-constexpr long long ZT_WAIT_CYCLES = 1ll << 32;
-static_assert(ZT_VP % 4 == 1 && ZT_VP - 3 >= ZT_VCOPY, "vector row slots: aligned, copies never overlap");
-static_assert(ZT_VP >= ZT_VWIN + 3 + 3, "a copy never reaches the window of another row");
-static_assert((ZT_VROWS - 1) * ZT_VP + 3 + ZT_VCOPY <= ZT_VBUF && ZT_VBUF % 4 == 0, "vector slot size");
-static_assert(ZT_KP % 4 == 0 && ZT_KP >= 40, "kappa row slots: aligned, copies never overlap");
-static_assert((ZT_KROWS - 1) * ZT_KP + 40 <= ZT_KBUF && ZT_KBUF % 4 == 0, "kappa slot size");
+// k_zm3w is k_zm3f with its planes staged by the copy engine instead of by
+// per-element cp.async, for the meshes with n in {32, 64, 128, 256}: a CTA
+// covers the full width of the mesh (n threads across x, one column each)
+// and R = 512 / n node rows (two per thread), so the CTAs per sample are
+// those of the 32 x 16 tiles and the halo slab of a plane (rows
+// ty0 - 1 .. ty0 + R, every column) is one contiguous range of a node array;
+// the kappa slab (rows ty0 - 1 .. ty0 + R - 1) is one contiguous range of an
+// element array. Each plane of each array is then ONE asynchronous bulk copy
+// (cp.async.bulk, global -> shared, completing on the slot's mbarrier),
+// issued by one thread: no per-element address, predicate or register work.
+// Node rows have an odd pitch n + 1, so a slab starts sh = (offset mod 4)
+// floats past a 16-byte boundary; the copy starts at that boundary and lands
+// at a slot offset that keeps the destination 16-byte aligned, which shifts
+// the slab by OFF (0..3 floats, one value per plane) inside the slot.
+// Values that feed only boundary outputs (row -1, column -1, the kappa halo
+// and the layers -1 and n) may be stale; planes 0 and n are not copied, and
+// the boundary nodes of the field (rows, columns and planes 0 and n) are
+// read as 0 by the threads next to them, whatever the array holds there. Waits are bounded: a wait that gives up counts a
+// timeout in g_zt_timeouts (read by the host at its sync points), lets the
+// copies still in flight land (bounded again) and ends the CTA.
+constexpr int ZW_S = 4;                             // ring slots, ZW_S - 1 planes in flight
+constexpr int ZW_WAIT_TRIES = 1 << 22;              // bounded waits: tries and SM cycles (~2 s)
+constexpr long long ZW_WAIT_CYCLES = 1ll << 32;
+
+// slot sizes (floats) of a node slab and of a kappa slab for cells per side n
+__host__ __device__ constexpr int zw_rows(int n) { return 512 / n; }
+__host__ __device__ constexpr int zw_vslot(int n) { return (12 + (zw_rows(n) + 2) * (n + 1) + 3) / 4 * 4; }
+__host__ __device__ constexpr int zw_kslot(int n) { return (8 + (zw_rows(n) + 1) * n + 3) / 4 * 4; }
+inline bool zw_mesh(int n) { return n == 32 || n == 64 || n == 128 || n == 256; }
 
 __device__ unsigned int g_zt_timeouts;
 
@@ -838,9 +829,9 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned addr, unsigned parity) {
 __device__ __forceinline__ bool mbar_wait(unsigned addr, unsigned parity) {
   if (mbar_try_wait(addr, parity)) return true;
   const long long t0 = clock64();
-  for (int k = 0; k < ZT_WAIT_TRIES; ++k) {
+  for (int k = 0; k < ZW_WAIT_TRIES; ++k) {
     if (mbar_try_wait(addr, parity)) return true;
-    if (clock64() - t0 > ZT_WAIT_CYCLES) break;
+    if (clock64() - t0 > ZW_WAIT_CYCLES) break;
   }
   return false;
 }
@@ -857,141 +848,98 @@ __device__ __forceinline__ void fence_mbar_init() {
   asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
 }
 
-// Shift (mod 4) of the first staged value (column tx0 - 1, row ty0 - 1) of
-// plane pp of a node array past a 16-byte boundary: K of that plane.
-__device__ __forceinline__ int zt_shift(int pp, const ZTile& t, int N1, int P) {
-  return (pp * P + (t.ty0 - 1) * N1 + t.tx0 - 1) & 3;
-}
-
 template <class Ld, class Epi>
-__global__ void __launch_bounds__(ZTHREADS, 3) k_zm3t(Grid g, const float* __restrict__ Kap, Ld ld,
+__global__ void __launch_bounds__(ZTHREADS, 3) k_zm3w(Grid g, const float* __restrict__ Kap, Ld ld,
                                                       const int32_t* __restrict__ active, Epi epi,
                                                       double* __restrict__ part, Prof prof) {
   static_assert(!Epi::kRes, "the FP32 z-march hands A x to its epilogues");
   constexpr int NA = Ld::kArrays;
   const int64_t b = blockIdx.y;
   if (active && !active[b]) return;
-  __shared__ __align__(16) float sv[ZT_S][NA][ZT_VBUF];
-  __shared__ __align__(16) float sk[ZT_S][ZT_KBUF];
-  __shared__ __align__(8) unsigned long long sbar[ZT_S];
-  const ZTile t = ztile(g);
-  const int n = g.n, N1 = n + 1, P = N1 * N1, KP = n * n;
-  const int tid = threadIdx.y * ZTX + threadIdx.x;
-  const int lane = threadIdx.x, ty = threadIdx.y;
+  extern __shared__ __align__(16) float zw_smem[];
+  const int n = g.n, N1 = n + 1, P = N1 * N1, KPn = n * n;
+  const int R = zw_rows(n), VS = zw_vslot(n), KS = zw_kslot(n), SS = NA * VS + KS;
+  float* ring = zw_smem;                                              // ZW_S slots of SS floats
+  unsigned long long* sbar = reinterpret_cast<unsigned long long*>(zw_smem + ZW_S * SS);
+  __shared__ double s_w[ZTHREADS / 32];
+  const int tyn = n / R;
+  int t = blockIdx.x;
+  const int zq = t / tyn;
+  const int ty0 = (t - zq * tyn) * R;
+  const int z0 = zq * g.zc, z1 = min(z0 + g.zc, n + 1);
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const float* __restrict__ kp = Kap + b * g.es;
   ld.bind(b);
   epi.bind(b);
-  // zero the ring: rows, planes and elements outside the mesh are never copied
-  {
-    float4* z4 = reinterpret_cast<float4*>(&sv[0][0][0]);
-    for (int e = tid; e < ZT_S * NA * ZT_VBUF / 4; e += ZTHREADS) z4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
-    float4* k4 = reinterpret_cast<float4*>(&sk[0][0]);
-    for (int e = tid; e < ZT_S * ZT_KBUF / 4; e += ZTHREADS) k4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-  const unsigned bar0 = (unsigned)__cvta_generic_to_shared(&sbar[0]);
-  const unsigned sv0 = (unsigned)__cvta_generic_to_shared(&sv[0][0][0]);
-  const unsigned sk0 = (unsigned)__cvta_generic_to_shared(&sk[0][0]);
+  for (int e = tid; e < ZW_S * SS / 4; e += ZTHREADS)
+    reinterpret_cast<float4*>(ring)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+  const unsigned bar0 = (unsigned)__cvta_generic_to_shared(sbar);
+  const unsigned ring0 = (unsigned)__cvta_generic_to_shared(ring);
   if (tid == 0) {
 #pragma unroll
-    for (int s = 0; s < ZT_S; ++s) mbar_init(bar0 + 8u * s, 1u);
+    for (int s = 0; s < ZW_S; ++s) mbar_init(bar0 + 8u * s, 1u);
     fence_mbar_init();
   }
   fence_proxy_async_smem();
   __syncthreads();
 
-  // rows copied per plane (CTA-uniform): vector rows 1..n-1, kappa rows 0..n-1
-  const int vy_lo = max(1, t.ty0 - 1), vy_hi = min(n - 1, t.ty0 + ZTY);
-  const int ky_lo = max(0, t.ty0 - 1), ky_hi = min(n - 1, t.ty0 + ZTY - 1);
-  const int nvrows = max(0, vy_hi - vy_lo + 1), nkrows = max(0, ky_hi - ky_lo + 1);
-  // kappa span of a row, in elements from the row start: [klo, khi)
-  const int klo = t.tx0 == 0 ? 0 : t.tx0 - 4;
-  const int khi = min(t.tx0 + 36, n);
-  const int kdst = klo - (t.tx0 - 4);
-  const unsigned kbytes_row = 4u * (unsigned)(khi - klo);
-  const unsigned vbytes_plane = (unsigned)nvrows * (4u * ZT_VCOPY) * NA;
-  const unsigned kbytes_plane = (unsigned)nkrows * kbytes_row;
-
-  // stage plane pp into ring slot st: warp 0 arms the slot's barrier with
-  // the plane's bytes and issues one copy per row; planes outside the mesh
-  // arrive with no bytes (their windows were zeroed by zero_slot)
+  // slabs: node rows ylo..yhi of a plane, kappa rows kylo..ty0 + R - 1 of a layer
+  const int ylo = max(ty0 - 1, 0), yhi = min(ty0 + R, n), r0 = ylo - ty0 + 1;
+  const int kylo = max(ty0 - 1, 0), kr0 = kylo - ty0 + 1;
+  const unsigned kbytes = 4u * (unsigned)((ty0 + R - kylo) * n);
+  // shift of plane pp's slab inside its slot (the slab's 16-byte alignment)
+  auto voff = [&](int pp) {
+    const int sh = (pp * P + ylo * N1) & 3;
+    return (sh - r0 * N1) & 3;
+  };
+  // stage plane pp (field) and layer pp (kappa) into slot st: one bulk copy per array
   auto issue = [&](int pp, int st) {
-    if (ty != 0) return;
+    if (tid != 0) return;
     const bool pv = pp >= 1 && pp < n, pk = pp >= 0 && pp < n;
     const unsigned bar = bar0 + 8u * st;
-    if (lane == 0) mbar_arrive_tx(bar, (pv ? vbytes_plane : 0u) + (pk ? kbytes_plane : 0u));
-    __syncwarp();
-    if (pv && lane < ZT_VROWS) {
-      const int y = t.ty0 - 1 + lane;
-      if (y >= 1 && y <= n - 1) {
-        const int start = pp * P + y * N1 + t.tx0 - 1;
-        const int sh = start & 3;
-        const int dst = lane * ZT_VP + zt_shift(pp, t, N1, P) - sh;
+    const int G0 = pp * P + ylo * N1, G1 = pp * P + (yhi + 1) * N1;
+    const int Ga = G0 & ~3, Gb = (G1 + 3) & ~3;
+    const unsigned vbytes = 4u * (unsigned)(Gb - Ga);
+    mbar_arrive_tx(bar, (pv ? NA * vbytes : 0u) + (pk ? kbytes : 0u));
+    if (pv) {
+      const int dst = 4 + voff(pp) + r0 * N1 - (G0 - Ga);
 #pragma unroll
-        for (int a = 0; a < NA; ++a)
-          bulk_g2s(sv0 + 4u * (unsigned)((st * NA + a) * ZT_VBUF + dst), ld.src(a) + (start - sh),
-                   4u * ZT_VCOPY, bar);
-      }
+      for (int a = 0; a < NA; ++a)
+        bulk_g2s(ring0 + 4u * (unsigned)(st * SS + a * VS + dst), ld.src(a) + Ga, vbytes, bar);
     }
-    if (pk && lane < ZT_KROWS) {
-      const int ky = t.ty0 - 1 + lane;
-      if (ky >= 0 && ky <= n - 1)
-        bulk_g2s(sk0 + 4u * (unsigned)(st * ZT_KBUF + lane * ZT_KP + kdst), kp + (pp * KP + ky * n + klo),
-                 kbytes_row, bar);
-    }
-  };
-  // windows of a slot that a plane outside the mesh must show as zeros
-  auto zero_slot = [&](int pp, int st) {
-    const bool pv = pp >= 1 && pp < n, pk = pp >= 0 && pp < n;
-    if (!pv)
-      for (int e = tid; e < ZT_VROWS * 40; e += ZTHREADS) {
-        const int yl = e / 40, x = e - yl * 40;
-#pragma unroll
-        for (int a = 0; a < NA; ++a) sv[st][a][yl * ZT_VP + x] = 0.f;
-      }
-    if (!pk)
-      for (int e = tid; e < ZT_KROWS * 40; e += ZTHREADS) {
-        const int yk = e / 40, x = e - yk * 40;
-        sk[st][yk * ZT_KP + x] = 0.f;
-      }
+    if (pk)
+      bulk_g2s(ring0 + 4u * (unsigned)(st * SS + NA * VS + 4 + kr0 * n), kp + (pp * KPn + kylo * n), kbytes,
+               bar);
   };
 
-  int p = t.z0 - 1;
-  // slots 0 .. ZT_S - 2 take the first planes (all slots hold zeros now)
+  int p = z0 - 1;
   unsigned pend = 0;   // slots with copies issued and not yet waited for
 #pragma unroll
-  for (int j = 0; j < ZT_S - 1; ++j)
-    if (p + j <= t.z1) {
+  for (int j = 0; j < ZW_S - 1; ++j)
+    if (p + j <= z1) {
       issue(p + j, j);
       pend |= 1u << j;
     }
 
-  const int i = t.tx0 + lane;
-  const int jr[2] = {t.ty0 + 2 * ty, t.ty0 + 2 * ty + 1};
-  bool cvalid[2], cint[2], ey[2];
+  const int i = threadIdx.x;
+  const int jr[2] = {ty0 + 2 * (int)threadIdx.y, ty0 + 2 * (int)threadIdx.y + 1};
+  bool cint[2], ey[2];
   int ocol[2];
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
-    cvalid[r] = i <= n && jr[r] <= n;
     cint[r] = i >= 1 && i < n && jr[r] >= 1 && jr[r] < n;
-    ey[r] = jr[r] == n - 1 && n % ZTY == 0;
+    ey[r] = jr[r] == n - 1;
     ocol[r] = jr[r] * N1 + i;
   }
-  const bool ex = i == n - 1 && n % ZTX == 0;
-  // stencil columns i - 1, i, i + 1 that are boundary nodes (or beyond): read as 0
-  const bool cok0 = i - 1 >= 1 && i - 1 <= n - 1, cok1 = i >= 1 && i <= n - 1,
-             cok2 = i + 1 >= 1 && i + 1 <= n - 1;
-  const bool vedge = !(cok0 && cok1 && cok2);
-  // combine slots of this thread (loaders with two arrays): window entries
-  // e = tid + q * ZTHREADS of the 18 x 34 window, as offsets from K
-  int coff[3];
-  bool cin[3];
+  const bool ex = i == n - 1;
+  // field boundary nodes next to this thread's stencils (columns i - 1 .. i + 1,
+  // rows jr[0] - 1 .. jr[1] + 1) read as 0
+  bool cok[3], rok[4];
 #pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    const int e = tid + q * ZTHREADS;
-    cin[q] = e < ZT_VROWS * ZT_VWIN;
-    const int yl = e / ZT_VWIN;
-    coff[q] = cin[q] ? yl * ZT_VP + (e - yl * ZT_VWIN) : 0;
-  }
+  for (int dx = 0; dx < 3; ++dx) cok[dx] = i - 1 + dx >= 1 && i - 1 + dx <= n - 1;
+#pragma unroll
+  for (int r4 = 0; r4 < 4; ++r4) rok[r4] = jr[0] - 1 + r4 >= 1 && jr[0] - 1 + r4 <= n - 1;
+  const bool edge = !(cok[0] && cok[2] && rok[0] && rok[3]);
   const float c3s = (float)g.c3, c12s = (float)g.c12;
   const float2 c3 = make_float2(c3s, c3s), mc12 = make_float2(-c12s, -c12s);
   const float2 z2 = make_float2(0.f, 0.f);
@@ -1000,26 +948,20 @@ __global__ void __launch_bounds__(ZTHREADS, 3) k_zm3t(Grid g, const float* __res
   float2 Xb[2] = {z2, z2}, Yb[2] = {z2, z2}, Sb = z2;
   typename Epi::Pre pre[2];
   float dot = 0.0f;
-  const int vbase = 2 * ty * ZT_VP + lane;
-  const int kbase = 2 * ty * ZT_KP + 3 + lane;
+  const int vrow = 4 + 2 * (int)threadIdx.y * N1 + i - 1;    // + OFF: row jr[0] - 1, column i - 1
+  const int krow = 4 + 2 * (int)threadIdx.y * n + i - 1;     // row jr[0] - 1, element i - 1
   int st = 0;
-  unsigned par = 0;    // phase parity of the slots' current use, bit per slot
+  unsigned par = 0;    // phase parity of each slot's next completion
   bool timed_out = false;
-  for (; p <= t.z1; ++p) {
+  for (; p <= z1; ++p) {
     const bool landed = mbar_wait(bar0 + 8u * st, (par >> st) & 1u);
     if (landed) {
       pend &= ~(1u << st);
       par ^= 1u << st;
     }
-    const int K = zt_shift(p, t, N1, P);
-    if (NA > 1 && landed && p >= 1 && p < n) {   // combine this thread's entries into the field
-#pragma unroll
-      for (int q = 0; q < 3; ++q)
-        if (cin[q]) {
-          float* a0 = &sv[st][0][K + coff[q]];
-          const float a1 = sv[st][NA - 1][K + coff[q]];
-          *a0 = ld.combine1(*a0, a1);
-        }
+    float* slot = ring + st * SS;
+    if (NA > 1 && landed && p >= 1 && p < n) {   // combine the arrays into the field
+      for (int e = tid; e < VS; e += ZTHREADS) slot[e] = ld.combine1(slot[e], slot[VS + e]);
     }
     fence_proxy_async_smem();       // this thread's shared-memory writes before later copies
     // plane p complete; the slot of plane p - 1 is free (or a wait gave up:
@@ -1028,42 +970,43 @@ __global__ void __launch_bounds__(ZTHREADS, 3) k_zm3t(Grid g, const float* __res
       timed_out = true;
       break;
     }
-    {
-      const int pn = p + ZT_S - 1, sn = (st + ZT_S - 1) % ZT_S;
-      if (pn <= t.z1) {
-        zero_slot(pn, sn);
-        issue(pn, sn);
-        pend |= 1u << sn;
-      }
+    if (p + ZW_S - 1 <= z1) {
+      const int sn = (st + ZW_S - 1) % ZW_S;
+      issue(p + ZW_S - 1, sn);
+      pend |= 1u << sn;
     }
     typename Epi::Pre nxt[2];
 #pragma unroll
     for (int r = 0; r < 2; ++r)
-      if (cint[r] && p >= t.z0 && p < t.z1 && p >= 1 && p < n) nxt[r] = epi.load(p * P + ocol[r]);
-    const float* svb = &sv[st][0][K + vbase];
-    const float* skb = &sk[st][kbase];
-    float s[4][3], kv[3][2];
+      if (cint[r] && p >= z0 && p < z1 && p >= 1 && p < n) nxt[r] = epi.load(p * P + ocol[r]);
+    const float* svb = slot + voff(p) + vrow;
+    const float* skb = slot + NA * VS + krow;
+    float s4[4][3], kv[3][2];
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
+    for (int r4 = 0; r4 < 4; ++r4)
 #pragma unroll
-      for (int dx = 0; dx < 3; ++dx) s[r][dx] = svb[r * ZT_VP + dx];
+      for (int dx = 0; dx < 3; ++dx) s4[r4][dx] = svb[r4 * N1 + dx];
 #pragma unroll
-    for (int r = 0; r < 3; ++r)
+    for (int r3 = 0; r3 < 3; ++r3)
 #pragma unroll
-      for (int a = 0; a < 2; ++a) kv[r][a] = skb[r * ZT_KP + a];
-    if (vedge) {
+      for (int a = 0; a < 2; ++a) kv[r3][a] = skb[r3 * n + a];
+    if (p <= 0 || p >= n) {
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        if (!cok0) s[r][0] = 0.f;
-        if (!cok1) s[r][1] = 0.f;
-        if (!cok2) s[r][2] = 0.f;
-      }
+      for (int r4 = 0; r4 < 4; ++r4)
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) s4[r4][dx] = 0.f;
+    } else if (edge) {
+#pragma unroll
+      for (int r4 = 0; r4 < 4; ++r4)
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx)
+          if (!rok[r4] || !cok[dx]) s4[r4][dx] = 0.f;
     }
     float2 v[3][3], ka[2][2];
 #pragma unroll
     for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
-      for (int dx = 0; dx < 3; ++dx) v[dy][dx] = make_float2(s[dy][dx], s[dy + 1][dx]);
+      for (int dx = 0; dx < 3; ++dx) v[dy][dx] = make_float2(s4[dy][dx], s4[dy + 1][dx]);
 #pragma unroll
     for (int bq = 0; bq < 2; ++bq)
 #pragma unroll
@@ -1085,10 +1028,9 @@ __global__ void __launch_bounds__(ZTHREADS, 3) k_zm3t(Grid g, const float* __res
     u = fma2(kb[1][1], v[2][2], u);
     const float2 done = fma2(mc12, u, mul2(c3, D));
     const int m = p - 1;
-    if (m >= t.z0) {
+    if (m >= z0) {
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
-        if (!cvalid[r]) continue;
         const int o = m * P + ocol[r];
         dot += epi(o, cint[r] && m >= 1 && m < n, r ? done.y : done.x, r ? vc.y : vc.x, pre[r]);
         if (ex) epi.zero(o + 1);
@@ -1123,16 +1065,26 @@ __global__ void __launch_bounds__(ZTHREADS, 3) k_zm3t(Grid g, const float* __res
     vc = v[1][1];
     pre[0] = nxt[0];
     pre[1] = nxt[1];
-    st = (st + 1) % ZT_S;
+    st = (st + 1) % ZW_S;
   }
   if (timed_out) {
     // record the timeout, let the copies still in flight land (bounded), end the CTA
     if (tid == 0) atomicAdd(&g_zt_timeouts, 1u);
-    for (int s2 = 0; s2 < ZT_S; ++s2)
+    for (int s2 = 0; s2 < ZW_S; ++s2)
       if (pend & (1u << s2)) mbar_wait(bar0 + 8u * s2, (par >> s2) & 1u);
     return;
   }
-  if (part) cta_partial3((double)dot, part, g.tiles_s);
+  if (part) {
+    double v = warp_sum3((double)dot);
+    if ((tid & 31) == 0) s_w[tid >> 5] = v;
+    __syncthreads();
+    if (tid == 0) {
+      double r = 0.0;
+#pragma unroll
+      for (int w = 0; w < ZTHREADS / 32; ++w) r += s_w[w];
+      part[(int64_t)blockIdx.y * g.tiles_s + blockIdx.x] = r;
+    }
+  }
   prof_tick3(prof);
 }
 
@@ -1145,11 +1097,14 @@ inline void launch_zm3(cudaStream_t s, const Grid& g, int64_t B, const T* kappa,
   if constexpr (std::is_same<T, float>::value) {
     using LP = LdPaired<Ld>;
     const typename LP::type lp = LP::make(ld);
-    // bulk-copy staging: 4 | n (fixed row alignment pattern), 16-byte aligned arrays
-    if (g.n % 4 == 0 && g.n >= 8 && lp.aligned16() && ((uintptr_t)kappa & 15) == 0 && g.ns % 4 == 0 &&
-        g.es % 4 == 0)
-      k_zm3t<typename LP::type, Epi><<<gridz(g, B), dim3(ZTX, ZTY / ZRY, 1), 0, s>>>(g, kappa, lp, active,
-                                                                                   epi, part, p);
+    // bulk-copy staging: full-width tiles (n in 32..256), 16-byte aligned arrays
+    if (zw_mesh(g.n) && lp.aligned16() && ((uintptr_t)kappa & 15) == 0 && g.ns % 4 == 0 &&
+        g.es % 4 == 0 && (g.zx == (int64_t)(g.n / zw_rows(g.n)) * ((g.n + 1 + g.zc - 1) / g.zc))) {
+      constexpr int NA = LP::type::kArrays;
+      const size_t smem = sizeof(float) * ZW_S * (NA * zw_vslot(g.n) + zw_kslot(g.n)) + 8 * ZW_S;
+      k_zm3w<typename LP::type, Epi><<<gridz(g, B), dim3(g.n, ZTHREADS / g.n, 1), smem, s>>>(
+          g, kappa, lp, active, epi, part, p);
+    }
     else
       k_zm3f<typename LP::type, Epi><<<gridz(g, B), dim3(ZTX, ZTY / ZRY, 1), 0, s>>>(g, kappa, lp, active,
                                                                                    epi, part, p);
