@@ -92,6 +92,13 @@ typedef struct mlmc_config {
                               initial iterate of the mesh l solve; 0: both
                               solves start from u = 0. The stopping test
                               (||r|| <= rtol ||b||) is the same either way. */
+  int32_t kle_tensor;      /* MLMC_MIXED: 1 = the FP32 kappa of the inner solves
+                              is exp of the KLE contraction on the tensor cores
+                              (tcgen05, split BF16 with FP32 accumulation, see
+                              mlmc_kappa32); 0 (default) = the FP64 kappa rounded
+                              to FP32. The FP64 outer residual uses the FP64
+                              kappa either way, so results meet the same
+                              tolerance; iterates differ in the last digits. */
 } mlmc_config;
 
 /* Per-level Welford state (Eq. (sample_variance): V = m2 / n). */
@@ -304,6 +311,18 @@ mlmc_status mlmc_draw_xi(mlmc_plan plan, int level, int64_t first, int64_t count
  * coefficient vectors xi (count x M, contiguous; Phi restricted to the kept
  * modes under total-order truncation). Output element arrays. */
 mlmc_status mlmc_kappa(mlmc_plan plan, int mesh, const double* xi, int64_t count, double* kappa);
+
+/* The FP32 kappa of the mixed form from the tensor cores: kappa32 =
+ * exp(Phi xi) at the element centroids of mesh `mesh` (Sec. 5.2 KLE, the
+ * dense contraction of the plan's per-axis tables, full or total-order
+ * basis, with `count` coefficient vectors xi: device, count x M doubles,
+ * contiguous). Phi and xi are each split into two BF16 terms and the three
+ * leading products are accumulated in FP32 (tcgen05 MMAs, tensor-memory
+ * accumulators): about 1e-5 relative error in kappa32. kappa32: device
+ * float element arrays (count x mlmc_elem_stride(dim, n)); asynchronous on
+ * the plan's stream. Errors: INVALID, CUDA; TIMEOUT (reported at the next
+ * sync point of the plan) if a bounded wait of the kernel gave up. */
+mlmc_status mlmc_kappa32(mlmc_plan plan, int mesh, const double* xi, int64_t count, float* kappa32);
 
 /* y = A(kappa) x on mesh `mesh` (Q1 stiffness, homogeneous Dirichlet):
  * node arrays in and out, `count` samples. */

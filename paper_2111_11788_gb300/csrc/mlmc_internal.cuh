@@ -169,6 +169,11 @@ cudaError_t launch_coarsen(cudaStream_t s, const Grid& fine, const Grid& coarse,
                            const T* kf, T* kc, int64_t B, Prof p);
 
 // kappa32 = (float) kappa64, element arrays.
+// kappa32 = exp(Phi xi) on the tensor cores (split BF16, FP32 accumulation); M kept modes
+cudaError_t launch_kappa32_tc(cudaStream_t s, const Grid& g, int m, double sqrt_sigma2, const double* table,
+                              const double* xi, int M, const int32_t* slot, int64_t B, float* kappa32);
+// bounded waits of the tensor-core KLE kernel that gave up since the last call (resets the count)
+cudaError_t take_tc_timeouts(cudaStream_t s, unsigned* out);
 cudaError_t launch_cast_kappa(cudaStream_t s, const Grid& g, const double* k64, float* k32,
                               int64_t B);
 

@@ -141,6 +141,7 @@ struct MixedWs {
   double* r;
   double* kap64;
   double* coef64;   // 2D: coefficients of the FP64 operator for the outer residual (else null)
+  const double* xi_tc;  // KLE coefficients: the FP32 kappa from the tensor cores (else the cast)
   Scalars outer;
   int32_t* outer_count;
   int32_t* outer_it;
@@ -154,6 +155,7 @@ void carve_mixed(Carve& c, const MeshInfo& mi, int64_t B, MixedWs& w) {
   w.r = c.take<double>(B * g0.ns);
   w.kap64 = c.take<double>(B * g0.es);
   w.coef64 = g0.dim == 2 ? c.take<double>(B * (3 * g0.ns + g0.es)) : nullptr;
+  w.xi_tc = nullptr;
   w.outer.gamma = w.outer.delta = w.outer.alpha = w.outer.beta = nullptr;
   w.outer.rho = c.take<double>(B);
   w.outer.tol = c.take<double>(B);
@@ -203,6 +205,7 @@ void carve_coupled(Carve& c, const MeshInfo& mi, int M, int64_t B, bool mixed, i
   if (mixed) {
     carve_mixed(c, mi, B, w.mx);
     w.kap = w.mx.kap64;
+    w.mx.xi_tc = w.xi;   // used when the plan takes its FP32 kappa from the tensor cores
     w.mx.outer_execs = execs ? execs + 2 * side : nullptr;
     w.mx.in.execs = execs ? execs + 2 * side + 1 : nullptr;
   } else {
@@ -283,6 +286,7 @@ struct mlmc_plan_s {
   double ms[NUM_KERNELS] = {0};
   int64_t kl[NUM_KERNELS] = {0};
   int64_t launches = 0;
+  bool tc_used = false;           // the tensor-core KLE kernel has run on this plan
   // graph-captured solves, keyed by (form, mesh, batch, workspace) and the
   // arrays they bake in (kappa, solution, QoI, iteration counts, guess)
   std::map<std::tuple<int, int, int64_t, const void*, const void*, const void*, const void*,
@@ -339,7 +343,8 @@ std::vector<int32_t> coef_slots(const mlmc_config* c) {
 }
 
 mlmc_status validate(const mlmc_config* c) {
-  if (c && (c->total_order < -1 || c->z_chunk < 0 || (c->nested_guess != 0 && c->nested_guess != 1)))
+  if (c && (c->total_order < -1 || c->z_chunk < 0 || (c->nested_guess != 0 && c->nested_guess != 1) ||
+            (c->kle_tensor != 0 && c->kle_tensor != 1)))
     return MLMC_ERR_INVALID;
   if (!c) return MLMC_ERR_INVALID;
   if (c->dim != 2 && c->dim != 3) return MLMC_ERR_INVALID;
@@ -872,6 +877,11 @@ mlmc_status settle_graph_launches(mlmc_plan p) {
     CK(d3::take_wait_timeouts(p->stream, &timeouts));
     if (timeouts) return MLMC_ERR_TIMEOUT;
   }
+  if (p->tc_used) {
+    unsigned timeouts = 0;
+    CK(take_tc_timeouts(p->stream, &timeouts));
+    if (timeouts) return MLMC_ERR_TIMEOUT;
+  }
   for (const GraphRec* r : p->pending_graphs) {
     p->launches += r->n_static;
     for (const auto& lp : r->loops) {
@@ -1001,7 +1011,14 @@ mlmc_status mixed_setup(mlmc_plan p, const MeshInfo& mi, MixedWs& w, int64_t B, 
   cudaStream_t s = p->stream;
   const mlmc_config& c = p->cfg;
   const Grid& g0 = mi.g[0];
-  CK(run(p, KID_SETUP, [&] { return launch_cast_kappa(s, g0, w.kap64, w.in.kap[0], B); }));
+  if (w.xi_tc && c.kle_tensor) {
+    CK(run(p, KID_KAPPA, [&] {
+      return launch_kappa32_tc(s, g0, c.modes_per_dim, p->sqrt_sigma2, mi.table, w.xi_tc, p->M, p->d_slot, B,
+                               w.in.kap[0]);
+    }));
+  } else {
+    CK(run(p, KID_SETUP, [&] { return launch_cast_kappa(s, g0, w.kap64, w.in.kap[0], B); }));
+  }
   if (w.coef64) CK(run(p, KID_SETUP, [&] { return d2::coef<double>(s, g0, w.kap64, w.coef64, B); }));
   mlmc_status st = setup_levels<float>(p, mi, w.in, B);
   if (st != MLMC_OK) return st;
@@ -1369,6 +1386,7 @@ void mlmc_config_default(mlmc_config* c) {
   c->total_order = -1;
   c->z_chunk = 0;
   c->nested_guess = 1;
+  c->kle_tensor = 0;
 }
 
 int64_t mlmc_node_stride(int dim, int n) {
@@ -1419,6 +1437,7 @@ mlmc_status mlmc_plan_create(const mlmc_config* cfg, void* stream, mlmc_plan* ou
   mlmc_plan p = new mlmc_plan_s();
   p->cfg = *cfg;
   p->stream = (cudaStream_t)stream;
+  p->tc_used = cfg->kle_tensor && cfg->precision == MLMC_MIXED;
   const int m = cfg->modes_per_dim;
   p->M = (int)coef_count(cfg);
   p->sqrt_sigma2 = std::sqrt(cfg->sigma2);
@@ -1640,6 +1659,21 @@ mlmc_status mlmc_kappa(mlmc_plan p, int mesh, const double* xi, int64_t count, d
     const int64_t B = std::min<int64_t>(65535, count - off);
     mlmc_status st = make_kappa(p, mesh, xi + off * p->M, B, kappa + off * g.es);
     if (st != MLMC_OK) return st;
+  }
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_kappa32(mlmc_plan p, int mesh, const double* xi, int64_t count, float* kappa32) {
+  if (!p || mesh < 0 || mesh >= p->cfg.n_levels || count < 0 || (count > 0 && (!xi || !kappa32)))
+    return MLMC_ERR_INVALID;
+  const MeshInfo& mi = p->meshes[mesh];
+  p->tc_used = true;
+  for (int64_t off = 0; off < count; off += 65535) {
+    const int64_t B = std::min<int64_t>(65535, count - off);
+    CK(run(p, KID_KAPPA, [&] {
+      return launch_kappa32_tc(p->stream, mi.g[0], p->cfg.modes_per_dim, p->sqrt_sigma2, mi.table,
+                               xi + off * p->M, p->M, p->d_slot, B, kappa32 + off * mi.g[0].es);
+    }));
   }
   return MLMC_OK;
 }

@@ -60,6 +60,7 @@ class Config(ctypes.Structure):
         ("total_order", ctypes.c_int32),
         ("z_chunk", ctypes.c_int32),
         ("nested_guess", ctypes.c_int32),
+        ("kle_tensor", ctypes.c_int32),
     ]
 
 
@@ -137,6 +138,7 @@ SIGNATURES = [
     ("mlmc_run", _I, [_P, _D, _I64, _I64P, _DP, _DP, _I64P]),
     ("mlmc_draw_xi", _I, [_P, _I, _I64, _I64, _P]),
     ("mlmc_kappa", _I, [_P, _I, _P, _I64, _P]),
+    ("mlmc_kappa32", _I, [_P, _I, _P, _I64, _P]),
     ("mlmc_apply", _I, [_P, _I, _P, _P, _P, _I64]),
     ("mlmc_solve", _I, [_P, _I, _P, _I64, _P, _P, _P]),
     ("mlmc_kernel_count", _I, []),
@@ -216,7 +218,7 @@ def config(dim=2, n_levels=3, coarse_cells=16, modes_per_dim=4, sigma2=1.0, corr
            qoi="domain", solver="jacobi", box=(0.25, 0.75), rtol=1e-10, max_iter=None,
            precision="fp64", seed=0, stream_id=0, mg_omega=None, check_every=0,
            workspace_bytes=0, inner_rtol=None, inner_max_iter=None, outer_max_iter=None,
-           use_graphs=None, total_order=None, nested_guess=None):
+           use_graphs=None, total_order=None, nested_guess=None, kle_tensor=None):
     """Build a Config from plain values (defaults from mlmc_config_default)."""
     c = Config()
     lib().mlmc_config_default(ctypes.byref(c))
@@ -248,6 +250,8 @@ def config(dim=2, n_levels=3, coarse_cells=16, modes_per_dim=4, sigma2=1.0, corr
         c.total_order = int(total_order)
     if nested_guess is not None:
         c.nested_guess = int(nested_guess)
+    if kle_tensor is not None:
+        c.kle_tensor = int(kle_tensor)
     return c
 
 
@@ -415,6 +419,9 @@ class Plan:
 
     def kappa(self, mesh, xi_ptr, count, kappa_ptr):
         check(lib().mlmc_kappa(self._h, mesh, _P(xi_ptr), count, _P(kappa_ptr)), "mlmc_kappa")
+
+    def kappa32(self, mesh, xi_ptr, count, kappa32_ptr):
+        check(lib().mlmc_kappa32(self._h, mesh, _P(xi_ptr), count, _P(kappa32_ptr)), "mlmc_kappa32")
 
     def apply(self, mesh, kappa_ptr, x_ptr, y_ptr, count):
         check(lib().mlmc_apply(self._h, mesh, _P(kappa_ptr), _P(x_ptr), _P(y_ptr), count),

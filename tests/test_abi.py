@@ -164,3 +164,14 @@ def test_round_bytes_counts_the_nested_guess_buffer(m):
                     assert guess <= a - b <= guess + 512
     bad = m.config(nested_guess=2)
     assert L.mlmc_round_bytes(ctypes.byref(bad), arr([1, 1, 1])) == -1
+
+
+def test_kle_tensor_flag_validated_without_a_device(m):
+    L = m.lib()
+    assert m.config().kle_tensor == 0
+    counts = (ctypes.c_int64 * 3)(1, 1, 1)
+    ok = m.config(precision="mixed", kle_tensor=1)
+    assert L.mlmc_round_bytes(ctypes.byref(ok), counts) > 0
+    bad = m.config(precision="mixed", kle_tensor=2)
+    assert L.mlmc_round_bytes(ctypes.byref(bad), counts) == -1
+    assert L.mlmc_kappa32(None, 0, None, 1, None) == m.MLMC_ERR_INVALID
