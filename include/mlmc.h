@@ -137,6 +137,11 @@ int64_t mlmc_elem_stride(int dim, int n);
 /* Cells per side of mesh `mesh` (n_0 * 2^mesh), or -1 if out of range. */
 int64_t mlmc_mesh_cells(const mlmc_config* cfg, int mesh);
 
+/* KLE coefficients per sample (the length of one xi): m^dim, or the number
+ * of modes kept by the total-order truncation (Sec. 5.2); -1 for an
+ * invalid configuration. */
+int64_t mlmc_coef_count(const mlmc_config* cfg);
+
 /* Deterministic level cost C_l = interior DOFs of mesh l + of mesh l-1
  * (the paper measures CPU time per Y_l, Sec. 2.3). */
 double mlmc_level_cost(const mlmc_config* cfg, int level);
@@ -258,6 +263,39 @@ mlmc_status mlmc_round_end(mlmc_plan plan);
 /* Eq. (mlmc_num_samples) from the current level states (V_l = m2_l / n_l)
  * and the cost model: N_out (host, n_levels entries). */
 mlmc_status mlmc_allocation(mlmc_plan plan, double eps, int64_t* N_out);
+/* Cross-request batching: one allocation round over `nplans` plans whose
+ * coupled solves can share launches (same dim, levels, coarse cells, solver,
+ * precision, tolerances, iteration caps, multigrid and QoI settings,
+ * z_chunk, nested_guess, and kle_tensor 0; their fields sigma2 and
+ * corr_len, KLE modes, total order, seeds and stream ids may differ; INVALID
+ * otherwise). first and count are host arrays of nplans x n_levels entries
+ * (plan k's level l at [k * n_levels + l]): plan k contributes the coupled
+ * samples first .. first + count - 1 of level l (Eq. (mlmc_average)). For
+ * every level the samples of all plans form ONE batch: each plan draws its
+ * xi and forms kappa with its own KLE tables into its range of the batch,
+ * the solves on both meshes run once for the whole batch, and each plan's
+ * Y_l are folded into its own level state in sample order. The result of
+ * every sample, hence every plan's level states, is bit for bit what the
+ * plan's own rounds give (the solves are per sample; a converged sample is
+ * frozen while the batch finishes). The round is one CUDA graph with a
+ * branch per level, launched on plans[0]'s stream and driven by plans[0]:
+ * poll it with mlmc_round_ready(plans[0]) and end it with
+ * mlmc_round_end_group(plans[0], ...); no plan of the group may be used
+ * until then. ws: caller-owned device workspace (256-byte aligned) of at
+ * least mlmc_round_bytes_group bytes, held until the round ends.
+ * Errors: INVALID, OOM (ws too small), UNIMPLEMENTED (graphs off, tracing on,
+ * or more than 65535 samples on a level), CUDA. */
+mlmc_status mlmc_round_begin_group(mlmc_plan* plans, int nplans, const int64_t* first, const int64_t* count,
+                                   void* ws, uint64_t ws_bytes);
+/* Device workspace bytes of mlmc_round_begin_group for plans of these
+ * configurations (host array of nplans pointers) and counts (nplans x
+ * n_levels); -1 if a configuration is invalid or they cannot share a round. */
+int64_t mlmc_round_bytes_group(const mlmc_config* const* cfgs, int nplans, const int64_t* count);
+/* Waits for the group round driven by `plan`; member_bad (host, nplans
+ * entries, may be NULL) receives 1 for a plan one of whose solves hit its
+ * iteration cap. NOT_CONVERGED if any did. */
+mlmc_status mlmc_round_end_group(mlmc_plan plan, int32_t* member_bad);
+
 /* Per-sample values of the last finished round (after mlmc_round_end) for
  * one level: q_fine[s] = Q_l and q_coarse[s] = Q_{l-1} (0 for level 0) of
  * sample first[l] + s, s < count, where count must equal the round's count
@@ -398,7 +436,7 @@ int64_t mlmc_launch_count(mlmc_plan plan);
 /* Measured FP64 FMA rate of the current device, the peak that FP64-bound
  * kernels are reported against (no passage of the paper; a measurement
  * aid): independent FMA chains on every SM (4 CTAs of 256 threads per SM,
- * 8 chains per thread), timed with CUDA events on `stream` (borrowed; NULL =
+ * 16 chains per thread), timed with CUDA events on `stream` (borrowed; NULL =
  * legacy default stream), best of three launches after a warm-up; synchronous.
  * tflops (host): FP64 TFLOP/s with an FMA counted as 2 flops; ms_out (host,
  * may be NULL): the best launch time. Errors: INVALID (tflops NULL), CUDA. */

@@ -24,7 +24,10 @@
  * with a branch per level, so coupled solves of every mesh size from every
  * request overlap on the device. A finished round is followed at once by the
  * request's next one (or its allocation step); a finished request frees its
- * slot and workspace for the next queued one.
+ * slot and workspace for the next queued one. Requests that want a round at
+ * the same moment and can share solves are launched as one group round
+ * (mlmc_round_begin_group): same-size levels of different requests are then
+ * solved by the same batched launches.
  *
  * The paper has no server; its closest counterpart is the dynamic scheduler
  * of Sec. 3-4 that feeds processor groups with sample batches.
@@ -53,7 +56,14 @@ typedef struct mlmc_server_config {
   int32_t adapt_from;    /* 0: every request samples all its levels (L fixed,
                             as mlmc_run); k >= 1: requests start on levels
                             0..k and adapt L (as mlmc_run_adaptive, L0 = k) */
-  int32_t reserved;      /* 0 */
+  int32_t solo_rounds;   /* 0 (default): cross-request batching - requests
+                            whose coupled solves can share launches (same
+                            meshes, solver, precision, tolerances; see
+                            mlmc_round_begin_group) and want a round at the
+                            same moment run it as ONE group round: per level
+                            their samples form one batch, solved by one set
+                            of launches. 1: every request runs its own
+                            rounds. Results are the same either way. */
 } mlmc_server_config;
 
 typedef struct mlmc_request_result {
@@ -61,7 +71,7 @@ typedef struct mlmc_request_result {
   int32_t status;        /* mlmc_status of the request (OK, NOT_CONVERGED, ...) */
   int32_t rounds;        /* rounds of sampling launched */
   int32_t levels;        /* levels sampled: final L + 1 */
-  int32_t reserved;
+  int32_t group_rounds;  /* of those, rounds run together with other requests */
   double q_hat;          /* Eq. (mlmc_average) */
   double stat_var;       /* sum_l V_l / N_l */
   double t_submit;       /* seconds on the server clock */

@@ -303,6 +303,14 @@ struct mlmc_plan_s {
   std::vector<int64_t> round_count;
   std::vector<size_t> done_off;                      // the last finished round, while its
   std::vector<int64_t> done_count;                   // per-sample values are still in place
+  // a round over several plans driven by this one (cross-request batching):
+  // its workspace, the coefficients carved per sample and, per member plan
+  // and level, the samples it holds
+  char* round_ws = nullptr;
+  int round_M = 0;
+  std::vector<mlmc_plan> group;
+  std::vector<int64_t> group_count;                  // members x levels
+  GraphRec group_graph;
   cudaStream_t cap_stream = nullptr;   // private stream the solve graphs are captured on
   // executed graphs whose kernel counts are settled at the next sync point
   std::vector<const GraphRec*> pending_graphs;
@@ -516,6 +524,21 @@ mlmc_status ensure_pin(mlmc_plan p, size_t bytes) {
 }
 
 bool is_mixed(mlmc_plan p) { return p->cfg.precision == MLMC_MIXED; }
+
+// Grids of mesh `l` of a configuration (no tables): enough to size workspaces.
+void mesh_info_shape(const mlmc_config& c, int l, MeshInfo& mi) {
+  mi.n = c.coarse_cells << l;
+  mi.K = 1;
+  mi.table = nullptr;
+  mi.g[0] = make_grid(c.dim, mi.n, c.z_chunk);
+  if (c.solver == MLMC_GMG_PCG && mi.n > 2) {
+    int n = mi.n;
+    while (n > 2 && mi.K < MAX_MG) {
+      n /= 2;
+      mi.g[mi.K++] = make_grid(c.dim, n, c.z_chunk);
+    }
+  }
+}
 
 size_t coupled_bytes(const MeshInfo& mi, int M, int64_t B, bool mixed, int64_t guess_ns) {
   Carve c(nullptr);
@@ -1245,10 +1268,12 @@ mlmc_status round_launch(mlmc_plan p, const std::vector<int64_t>& first,
   }
   p->round_off = off;
   p->round_count = count;
+  p->round_M = p->M;
   if (total == 0) return MLMC_OK;
   if (total > p->ws_budget || (int)p->branch.size() < L1) return MLMC_ERR_UNIMPLEMENTED;
   mlmc_status st = ensure_ws(p, total);
   if (st != MLMC_OK) return st;
+  p->round_ws = (char*)p->ws;
   std::vector<int64_t> key = {mixed ? 1 : 0, (int64_t)(uintptr_t)p->ws};
   key.insert(key.end(), first.begin(), first.end());
   key.insert(key.end(), count.begin(), count.end());
@@ -1282,31 +1307,188 @@ mlmc_status round_launch(mlmc_plan p, const std::vector<int64_t>& first,
   return MLMC_OK;
 }
 
+// ---- rounds over several plans (cross-request batching) -----------------
+
+// Plans whose coupled batches can share one solve: the same meshes, solver,
+// precision, tolerances, multigrid and QoI settings (their fields, KLE modes,
+// seeds and stream ids may differ).
+bool same_solve(const mlmc_config& a, const mlmc_config& b) {
+  return a.dim == b.dim && a.n_levels == b.n_levels && a.coarse_cells == b.coarse_cells &&
+         a.solver == b.solver && a.precision == b.precision && a.rtol == b.rtol &&
+         a.max_iter == b.max_iter && a.mg_smooth == b.mg_smooth && a.mg_omega == b.mg_omega &&
+         a.mg_coarsest == b.mg_coarsest && a.check_every == b.check_every &&
+         a.inner_rtol == b.inner_rtol && a.inner_max_iter == b.inner_max_iter &&
+         a.outer_max_iter == b.outer_max_iter && a.z_chunk == b.z_chunk &&
+         a.nested_guess == b.nested_guess && a.qoi == b.qoi && a.box_lo == b.box_lo &&
+         a.box_hi == b.box_hi && a.kle_tensor == 0 && b.kle_tensor == 0;
+}
+
+// The coupled batch of `level` over the members of p's group, issued into the
+// graph being captured on p->stream: every member draws its xi (its own
+// stream of sample indices first[k] ..) and forms kappa with its own KLE
+// tables into its range of the batch; the solves on both meshes run once for
+// the whole batch (p's solver settings, which the members share); each
+// member's Y are folded into its own level state in sample order.
+mlmc_status issue_level_group(mlmc_plan p, int level, const std::vector<int64_t>& first, int64_t B,
+                              char* region) {
+  const bool mixed = is_mixed(p);
+  const int64_t gns = guess_ns_of(p->cfg, level);
+  const int sides = level > 0 ? 2 : 1;
+  const int L1 = p->cfg.n_levels;
+  const int nm = (int)p->group.size();
+  cudaStream_t S = p->stream;
+  mlmc_status st;
+  for (int k = 0; k < sides; ++k) {
+    const int side = gns > 0 ? sides - 1 - k : k;
+    const int mesh = level - side;
+    const MeshInfo& mi = p->meshes[mesh];
+    Carve c(region);
+    CoupledWs w;
+    carve_coupled(c, mi, p->round_M, B, mixed, gns, side, w);
+    int64_t o = 0, xo = 0;
+    for (int j = 0; j < nm; ++j) {
+      mlmc_plan q = p->group[j];
+      const int64_t cnt = p->group_count[(size_t)j * L1 + level];
+      if (cnt <= 0) continue;
+      cudaStream_t saved = q->stream;
+      const int64_t l0 = q->launches;
+      q->stream = S;   // the member's kernels join the graph being captured
+      if (k == 0) st = mlmc_draw_xi(q, level, first[(size_t)j * L1 + level], cnt, w.xi + xo);
+      else st = MLMC_OK;
+      if (st == MLMC_OK) st = make_kappa(q, mesh, w.xi + xo, cnt, w.kap + o * mi.g[0].es);
+      q->stream = saved;
+      if (q != p) {   // counted with the driving plan's graph
+        p->launches += q->launches - l0;
+        q->launches = l0;
+      }
+      if (st != MLMC_OK) return st;
+      o += cnt;
+      xo += cnt * q->M;
+    }
+    if (mixed) w.mx.xi_tc = nullptr;   // members' coefficients differ in number: kappa32 by the cast
+    double* qd = side == 0 ? w.qf : w.qc;
+    int32_t* itd = side == 0 ? w.itf : w.itc;
+    const Guess gs = guess_views(p, level, side, mixed, w);
+    st = mixed ? issue_mixed(p, mi, w.mx, B, qd, itd, gs) : issue_fp64(p, mi, w.s, B, qd, itd, gs);
+    if (st != MLMC_OK) return st;
+  }
+  Carve c(region);
+  CoupledWs w;
+  carve_coupled(c, p->meshes[level], p->round_M, B, mixed, gns, 0, w);
+  const double cost = level_cost_cfg(&p->cfg, level);
+  int64_t o = 0;
+  for (int j = 0; j < nm; ++j) {
+    mlmc_plan q = p->group[j];
+    const int64_t cnt = p->group_count[(size_t)j * L1 + level];
+    if (cnt <= 0) continue;
+    CK(run(p, KID_WELFORD, [&] {
+      return launch_welford(S, w.qf + o, level > 0 ? w.qc + o : nullptr, cnt, q->d_states + level, cost);
+    }));
+    o += cnt;
+  }
+  return MLMC_OK;
+}
+
+// One round over the plans of p's group in the caller's workspace `ws`: a
+// graph with a branch per level (finest first), launched on p's stream.
+mlmc_status group_launch(mlmc_plan p, const std::vector<int64_t>& first, char* ws, uint64_t ws_bytes) {
+  const int L1 = p->cfg.n_levels;
+  const bool mixed = is_mixed(p);
+  const int nm = (int)p->group.size();
+  std::vector<int64_t> B(L1, 0);
+  std::vector<size_t> off(L1, 0);
+  int Mmax = 1;
+  for (int j = 0; j < nm; ++j) Mmax = std::max(Mmax, p->group[j]->M);
+  size_t total = 0;
+  for (int l = 0; l < L1; ++l) {
+    for (int j = 0; j < nm; ++j) B[l] += p->group_count[(size_t)j * L1 + l];
+    if (B[l] <= 0) continue;
+    if (B[l] > 65535) return MLMC_ERR_UNIMPLEMENTED;
+    off[l] = total;
+    total += (size_t)round_up((int64_t)coupled_bytes(p->meshes[l], Mmax, B[l], mixed, guess_ns_of(p->cfg, l)),
+                              256);
+  }
+  if (total > ws_bytes) return MLMC_ERR_OOM;
+  p->round_off = off;
+  p->round_count = B;
+  p->round_ws = ws;
+  p->round_M = Mmax;
+  if (total == 0) return MLMC_OK;
+  GraphRec rec;
+  mlmc_status st = build_graph(p, [&]() -> mlmc_status {
+    cudaStream_t origin = p->stream;
+    CK(cudaEventRecord(p->branch_ev[0], origin));
+    int nb = 0;
+    mlmc_status s2 = MLMC_OK;
+    for (int l = L1 - 1; l >= 0 && s2 == MLMC_OK; --l) {
+      if (B[l] <= 0) continue;
+      cudaStream_t S = p->branch[nb];
+      CK(cudaStreamWaitEvent(S, p->branch_ev[0], 0));
+      p->stream = S;
+      s2 = issue_level_group(p, l, first, B[l], ws + off[l]);
+      p->stream = origin;
+      if (s2 == MLMC_OK) CK(cudaEventRecord(p->branch_ev[1 + nb], S));
+      ++nb;
+    }
+    for (int i = 0; i < nb && s2 == MLMC_OK; ++i) CK(cudaStreamWaitEvent(origin, p->branch_ev[1 + i], 0));
+    return s2;
+  }, &rec);
+  if (st != MLMC_OK) return st;
+  p->group_graph = rec;
+  CK(cudaGraphLaunch(rec.exec, p->stream));
+  CK(cudaEventRecord(p->round_done, p->stream));
+  p->pending_graphs.push_back(&p->group_graph);
+  return MLMC_OK;
+}
+
 // Waits for the launched round, settles the launch count and checks the
-// per-sample iteration counts of both meshes of every level.
-mlmc_status round_finish(mlmc_plan p, bool* bad) {
+// per-sample iteration counts of both meshes of every level. For a round over
+// several plans, member_bad[k] (may be null) tells whether a solve of member
+// k hit its iteration cap.
+mlmc_status round_finish(mlmc_plan p, bool* bad, int32_t* member_bad = nullptr) {
   CK(cudaStreamSynchronize(p->stream));
   mlmc_status st = settle_graph_launches(p);
   if (st != MLMC_OK) return st;
   const int L1 = p->cfg.n_levels;
   const bool mixed = is_mixed(p);
+  const int nm = (int)p->group.size();
+  if (member_bad)
+    for (int k = 0; k < nm; ++k) member_bad[k] = 0;
   std::vector<int32_t> h;
   for (int l = 0; l < L1 && l < (int)p->round_count.size(); ++l) {
     const int64_t n = p->round_count[l];
     if (n <= 0) continue;
-    Carve c((char*)p->ws + p->round_off[l]);
+    Carve c(p->round_ws + p->round_off[l]);
     CoupledWs w;
-    carve_coupled(c, p->meshes[l], p->M, n, mixed, guess_ns_of(p->cfg, l), 0, w);
+    carve_coupled(c, p->meshes[l], p->round_M, n, mixed, guess_ns_of(p->cfg, l), 0, w);
     h.resize(2 * n);
     // on the plan's stream: other plans' rounds keep running meanwhile
     CK(cudaMemcpyAsync(h.data(), w.itf, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, p->stream));
     CK(cudaMemcpyAsync(h.data() + n, w.itc, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, p->stream));
     CK(cudaStreamSynchronize(p->stream));
-    for (int64_t b = 0; b < n; ++b)
-      if (h[b] < 0 || (l > 0 && h[n + b] < 0)) *bad = true;
+    int k = 0;
+    int64_t end = nm ? p->group_count[l] : n;   // samples of member k end at `end`
+    for (int64_t b = 0; b < n; ++b) {
+      while (nm && b >= end && k + 1 < nm) end += p->group_count[(size_t)(++k) * L1 + l];
+      if (h[b] < 0 || (l > 0 && h[n + b] < 0)) {
+        *bad = true;
+        if (member_bad && nm) member_bad[k] = 1;
+      }
+    }
   }
-  p->done_off = p->round_off;
-  p->done_count = p->round_count;
+  if (nm) {
+    // the regions held every member's samples: no per-plan values to read back
+    if (p->group_graph.exec) cudaGraphExecDestroy(p->group_graph.exec);
+    p->group_graph = GraphRec{};
+    p->group.clear();
+    p->group_count.clear();
+    p->done_count.clear();
+  } else {
+    p->done_off = p->round_off;
+    p->done_count = p->round_count;
+  }
+  p->round_ws = (char*)p->ws;
+  p->round_M = p->M;
   p->round_count.clear();
   return MLMC_OK;
 }
@@ -1402,6 +1584,11 @@ int64_t mlmc_elem_stride(int dim, int n) {
 int64_t mlmc_mesh_cells(const mlmc_config* cfg, int mesh) {
   if (!cfg || mesh < 0 || mesh >= cfg->n_levels) return -1;
   return (int64_t)cfg->coarse_cells << mesh;
+}
+
+int64_t mlmc_coef_count(const mlmc_config* cfg) {
+  if (validate(cfg) != MLMC_OK) return -1;
+  return coef_count(cfg);
 }
 
 double mlmc_level_cost(const mlmc_config* cfg, int level) {
@@ -1586,16 +1773,7 @@ int64_t mlmc_round_bytes(const mlmc_config* cfg, const int64_t* count) {
   for (int l = 0; l < cfg->n_levels; ++l) {
     if (count[l] <= 0) continue;
     MeshInfo mi;
-    mi.n = cfg->coarse_cells << l;
-    mi.K = 1;
-    mi.g[0] = make_grid(cfg->dim, mi.n, cfg->z_chunk);
-    if (cfg->solver == MLMC_GMG_PCG && mi.n > 2) {
-      int n = mi.n;
-      while (n > 2 && mi.K < MAX_MG) {
-        n /= 2;
-        mi.g[mi.K++] = make_grid(cfg->dim, n, cfg->z_chunk);
-      }
-    }
+    mesh_info_shape(*cfg, l, mi);
     total += round_up((int64_t)coupled_bytes(mi, M, count[l], cfg->precision == MLMC_MIXED,
                                              guess_ns_of(*cfg, l)), 256);
   }
@@ -1606,6 +1784,7 @@ mlmc_status mlmc_plan_destroy(mlmc_plan p) {
   if (!p) return MLMC_ERR_INVALID;
   cudaStreamSynchronize(p->stream);
   clear_graphs(p);
+  if (p->group_graph.exec) cudaGraphExecDestroy(p->group_graph.exec);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   for (auto bs : p->branch) cudaStreamDestroy(bs);
   for (auto ev : p->branch_ev) cudaEventDestroy(ev);
@@ -2134,6 +2313,75 @@ mlmc_status mlmc_round_end(mlmc_plan p) {
   if (p->round_count.empty()) return MLMC_OK;
   bool bad = false;
   mlmc_status st = round_finish(p, &bad);
+  if (st != MLMC_OK) return st;
+  return bad ? MLMC_ERR_NOT_CONVERGED : MLMC_OK;
+}
+
+mlmc_status mlmc_round_begin_group(mlmc_plan* plans, int nplans, const int64_t* first, const int64_t* count,
+                                   void* ws, uint64_t ws_bytes) {
+  if (!plans || nplans < 1 || nplans > 256 || !first || !count || !ws || ((uintptr_t)ws & 255)) return MLMC_ERR_INVALID;
+  mlmc_plan p = plans[0];
+  if (!p) return MLMC_ERR_INVALID;
+  if (!graphs_on(p)) return MLMC_ERR_UNIMPLEMENTED;
+  const int L1 = p->cfg.n_levels;
+  for (int j = 0; j < nplans; ++j) {
+    mlmc_plan q = plans[j];
+    if (!q || !q->round_count.empty() || !q->group.empty() || !same_solve(p->cfg, q->cfg) || q->prof_on)
+      return MLMC_ERR_INVALID;
+    for (int k = 0; k < j; ++k)
+      if (plans[k] == q) return MLMC_ERR_INVALID;
+    for (int l = 0; l < L1; ++l) {
+      const int64_t f = first[(size_t)j * L1 + l], c = count[(size_t)j * L1 + l];
+      if (f < 0 || c < 0 || f + c > (int64_t(1) << 32)) return MLMC_ERR_INVALID;
+    }
+  }
+  p->group.assign(plans, plans + nplans);
+  p->group_count.assign(count, count + (size_t)nplans * L1);
+  std::vector<int64_t> f(first, first + (size_t)nplans * L1);
+  const mlmc_status st = group_launch(p, f, (char*)ws, ws_bytes);
+  if (st != MLMC_OK) {
+    if (p->group_graph.exec) cudaGraphExecDestroy(p->group_graph.exec);
+    p->group_graph = GraphRec{};
+    p->group.clear();
+    p->group_count.clear();
+    p->round_count.clear();
+    p->round_ws = (char*)p->ws;
+    p->round_M = p->M;
+  }
+  return st;
+}
+
+int64_t mlmc_round_bytes_group(const mlmc_config* const* cfgs, int nplans, const int64_t* count) {
+  if (!cfgs || nplans < 1 || !count) return -1;
+  const mlmc_config* c0 = cfgs[0];
+  if (!c0 || validate(c0) != MLMC_OK) return -1;
+  int64_t Mmax = 1;
+  for (int j = 0; j < nplans; ++j) {
+    if (!cfgs[j] || validate(cfgs[j]) != MLMC_OK || !same_solve(*c0, *cfgs[j])) return -1;
+    Mmax = std::max<int64_t>(Mmax, coef_count(cfgs[j]));
+  }
+  const int L1 = c0->n_levels;
+  const bool mixed = c0->precision == MLMC_MIXED;
+  size_t total = 0;
+  for (int l = 0; l < L1; ++l) {
+    int64_t B = 0;
+    for (int j = 0; j < nplans; ++j) {
+      if (count[(size_t)j * L1 + l] < 0) return -1;
+      B += count[(size_t)j * L1 + l];
+    }
+    if (B <= 0) continue;
+    MeshInfo mi{};
+    mesh_info_shape(*c0, l, mi);
+    total += (size_t)round_up((int64_t)coupled_bytes(mi, (int)Mmax, B, mixed, guess_ns_of(*c0, l)), 256);
+  }
+  return (int64_t)total;
+}
+
+mlmc_status mlmc_round_end_group(mlmc_plan p, int32_t* member_bad) {
+  if (!p) return MLMC_ERR_INVALID;
+  if (p->round_count.empty()) return MLMC_OK;
+  bool bad = false;
+  mlmc_status st = round_finish(p, &bad, member_bad);
   if (st != MLMC_OK) return st;
   return bad ? MLMC_ERR_NOT_CONVERGED : MLMC_OK;
 }

@@ -57,7 +57,13 @@ struct Request {
   int L = 0;        // highest active level
   bool bad = false;
   bool finished = false;
+  bool pending = false;        // its next round (inflight counts) waits for launch
+  Request* driver = nullptr;   // in a group round: the member whose plan drives it
+  std::vector<Request*> members;                // driver only: the group, driver first
+  uint64_t group_off = 0, group_bytes = 0;      // driver only: the group's arena block
 };
+
+constexpr int kMaxGroup = 32;   // requests per group round
 
 }  // namespace
 
@@ -88,6 +94,8 @@ struct mlmc_server_s {
   void run();
   bool admit();
   void advance(Request& r);
+  void launch_pending();
+  void end_group(Request& d);
   void finish(Request& r, mlmc_status st);
   uint64_t reservation(const mlmc_config& c) const;
   void chunk(const Request& r, const int64_t* want, int64_t* out) const;
@@ -268,13 +276,9 @@ void mlmc_server_s::advance(Request& r) {
       any = any || want[l] > 0;
     }
     if (any) {
+      // launched by launch_pending, together with the requests it can share solves with
       chunk(r, want, r.inflight);
-      const mlmc_status st = mlmc_round_begin(r.slot->plan, r.have, r.inflight);
-      if (st != MLMC_OK) {
-        finish(r, st);
-        return;
-      }
-      ++r.res.rounds;
+      r.pending = true;
       return;
     }
     // every level holds its target: one sampling phase is complete
@@ -306,6 +310,101 @@ void mlmc_server_s::advance(Request& r) {
       finish(r, MLMC_OK);
       return;
     }
+  }
+}
+
+// Launches the rounds that requests want now. Requests whose solves can share
+// launches (mlmc_round_bytes_group accepts them together) form groups of up to
+// kMaxGroup; a group of two or more whose round workspace fits a free block
+// of the arena runs as one group round driven by its first member's plan.
+// The others (and groups that do not fit) run their own rounds.
+void mlmc_server_s::launch_pending() {
+  std::vector<std::vector<Request*>> groups;
+  for (auto& a : active) {
+    Request& r = *a;
+    if (!r.pending || r.finished) continue;
+    bool placed = false;
+    if (!cfg.solo_rounds) {
+      for (auto& g : groups) {
+        if ((int)g.size() >= kMaxGroup || g[0]->cfg.n_levels != r.cfg.n_levels) continue;
+        const mlmc_config* pair[2] = {&g[0]->cfg, &r.cfg};
+        int64_t one[2 * kMaxLevels];
+        for (int l = 0; l < 2 * r.cfg.n_levels; ++l) one[l] = 1;
+        if (mlmc_round_bytes_group(pair, 2, one) < 0) continue;
+        g.push_back(&r);
+        placed = true;
+        break;
+      }
+    }
+    if (!placed) groups.push_back({&r});
+  }
+  for (auto& g : groups) {
+    const int n = (int)g.size();
+    if (n >= 2) {
+      const int L1 = g[0]->cfg.n_levels;
+      std::vector<const mlmc_config*> cfgs(n);
+      std::vector<mlmc_plan> plans(n);
+      std::vector<int64_t> first((size_t)n * L1), count((size_t)n * L1);
+      for (int k = 0; k < n; ++k) {
+        cfgs[k] = &g[k]->cfg;
+        plans[k] = g[k]->slot->plan;
+        for (int l = 0; l < L1; ++l) {
+          first[(size_t)k * L1 + l] = g[k]->have[l];
+          count[(size_t)k * L1 + l] = g[k]->inflight[l];
+        }
+      }
+      const int64_t bytes = mlmc_round_bytes_group(cfgs.data(), n, count.data());
+      uint64_t off = 0;
+      if (bytes > 0 && arena_alloc((uint64_t)bytes, &off)) {
+        const mlmc_status st =
+            mlmc_round_begin_group(plans.data(), n, first.data(), count.data(), arena + off, (uint64_t)bytes);
+        if (st == MLMC_OK) {
+          Request* d = g[0];
+          d->members = g;
+          d->group_off = off;
+          d->group_bytes = (uint64_t)bytes;
+          for (Request* m : g) {
+            m->driver = d;
+            m->pending = false;
+            ++m->res.rounds;
+            ++m->res.group_rounds;
+          }
+          continue;
+        }
+        arena_free(off, (uint64_t)bytes);
+      }
+    }
+    for (Request* m : g) {
+      m->pending = false;
+      const mlmc_status st = mlmc_round_begin(m->slot->plan, m->have, m->inflight);
+      if (st != MLMC_OK) {
+        finish(*m, st);
+        continue;
+      }
+      ++m->res.rounds;
+    }
+  }
+}
+
+// The group round driven by d has completed: every member takes its samples
+// and moves on (its next round, allocation step or end).
+void mlmc_server_s::end_group(Request& d) {
+  std::vector<Request*> g = d.members;
+  std::vector<int32_t> bad(g.size(), 0);
+  const mlmc_status st = mlmc_round_end_group(d.slot->plan, bad.data());
+  arena_free(d.group_off, d.group_bytes);
+  d.members.clear();
+  d.group_bytes = 0;
+  for (size_t k = 0; k < g.size(); ++k) {
+    Request& m = *g[k];
+    m.driver = nullptr;
+    if (st != MLMC_OK && st != MLMC_ERR_NOT_CONVERGED) {
+      finish(m, st);
+      continue;
+    }
+    if (bad[k]) m.bad = true;
+    for (int l = 0; l < m.cfg.n_levels; ++l) m.have[l] += m.inflight[l];
+    advance(m);
   }
 }
 
@@ -366,9 +465,24 @@ void mlmc_server_s::run() {
     bool progressed = stop ? false : admit();
     for (auto& a : active) {
       Request& r = *a;
+      if (r.finished || r.pending) continue;
+      if (r.driver && r.driver != &r) continue;   // a group member: its driver is polled
       const int ready = mlmc_round_ready(r.slot->plan);
       if (ready == 0) continue;
       progressed = true;
+      if (r.driver == &r) {
+        if (ready < 0) {
+          for (Request* m : std::vector<Request*>(r.members)) {
+            m->driver = nullptr;
+            finish(*m, MLMC_ERR_CUDA);
+          }
+          arena_free(r.group_off, r.group_bytes);
+          r.members.clear();
+          continue;
+        }
+        end_group(r);
+        continue;
+      }
       if (ready < 0) {
         finish(r, MLMC_ERR_CUDA);
         continue;
@@ -382,6 +496,7 @@ void mlmc_server_s::run() {
       for (int l = 0; l < r.cfg.n_levels; ++l) r.have[l] += r.inflight[l];
       advance(r);
     }
+    launch_pending();
     active.erase(std::remove_if(active.begin(), active.end(),
                                 [](const std::unique_ptr<Request>& a) { return a->finished; }),
                  active.end());

@@ -80,13 +80,13 @@ class ServerConfig(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_uint64), ("max_slots", ctypes.c_int32),
                 ("pilot", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("max_rounds", ctypes.c_int32), ("adapt_from", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("solo_rounds", ctypes.c_int32)]
 
 
 class RequestResult(ctypes.Structure):
     """Mirror of ``mlmc_request_result``."""
     _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int32), ("rounds", ctypes.c_int32),
-                ("levels", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("levels", ctypes.c_int32), ("group_rounds", ctypes.c_int32),
                 ("q_hat", ctypes.c_double), ("stat_var", ctypes.c_double),
                 ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
                 ("t_done", ctypes.c_double), ("dof_solves", ctypes.c_double),
@@ -127,6 +127,7 @@ SIGNATURES = [
     ("mlmc_elem_stride", _I64, [_I, _I]),
     ("mlmc_mesh_cells", _I64, [ctypes.POINTER(Config), _I]),
     ("mlmc_level_cost", _D, [ctypes.POINTER(Config), _I]),
+    ("mlmc_coef_count", _I64, [ctypes.POINTER(Config)]),
     ("mlmc_status_str", ctypes.c_char_p, [_I]),
     ("mlmc_plan_create", _I, [ctypes.POINTER(Config), _P, ctypes.POINTER(_P)]),
     ("mlmc_plan_destroy", _I, [_P]),
@@ -153,6 +154,9 @@ SIGNATURES = [
     ("mlmc_round_end", _I, [_P]),
     ("mlmc_allocation", _I, [_P, _D, _I64P]),
     ("mlmc_round_values", _I, [_P, _I, _DP, _DP, _I64]),
+    ("mlmc_round_begin_group", _I, [ctypes.POINTER(_P), _I, _I64P, _I64P, _P, ctypes.c_uint64]),
+    ("mlmc_round_bytes_group", _I64, [ctypes.POINTER(ctypes.POINTER(Config)), _I, _I64P]),
+    ("mlmc_round_end_group", _I, [_P, _I32P]),
     ("mlmc_plan_retarget", _I, [_P, ctypes.POINTER(Config)]),
     ("mlmc_round_bytes", _I64, [ctypes.POINTER(Config), _I64P]),
     ("mlmc_plan_set_workspace", _I, [_P, _P, ctypes.c_uint64]),
@@ -276,6 +280,35 @@ def probe_fp64_rate(stream=0):
     return tf.value, ms.value
 
 
+def round_bytes_group(cfgs, count):
+    """mlmc_round_bytes_group for configurations cfgs and counts (len(cfgs) x n_levels)."""
+    import numpy as np
+    arr = (ctypes.POINTER(Config) * len(cfgs))(*[ctypes.pointer(c) for c in cfgs])
+    c = np.ascontiguousarray(count, dtype=np.int64).reshape(-1)
+    return int(lib().mlmc_round_bytes_group(arr, len(cfgs), c.ctypes.data_as(_I64P)))
+
+
+def round_group(plans, first, count, ws_ptr, ws_bytes):
+    """mlmc_round_begin_group + mlmc_round_end_group on plans[0]: returns
+    (status, per-plan flags of solves that hit their iteration cap)."""
+    import numpy as np
+    hs = (_P * len(plans))(*[p._h for p in plans])
+    f = np.ascontiguousarray(first, dtype=np.int64).reshape(-1)
+    c = np.ascontiguousarray(count, dtype=np.int64).reshape(-1)
+    check(lib().mlmc_round_begin_group(hs, len(plans), f.ctypes.data_as(_I64P), c.ctypes.data_as(_I64P),
+                                       _P(ws_ptr), ctypes.c_uint64(ws_bytes)), "mlmc_round_begin_group")
+    bad = np.zeros(len(plans), dtype=np.int32)
+    st = lib().mlmc_round_end_group(plans[0]._h, bad.ctypes.data_as(_I32P))
+    if st not in (MLMC_OK, MLMC_ERR_NOT_CONVERGED):
+        check(st, "mlmc_round_end_group")
+    return st, bad
+
+
+def coef_count(cfg):
+    """mlmc_coef_count: KLE coefficients per sample of a configuration."""
+    return int(lib().mlmc_coef_count(ctypes.byref(cfg)))
+
+
 def node_stride(dim, n):
     return lib().mlmc_node_stride(dim, n)
 
@@ -375,6 +408,20 @@ class Plan:
               "mlmc_round_begin")
         check(lib().mlmc_round_end(self._h), "mlmc_round_end")
 
+    def round_begin(self, first, count):
+        """mlmc_round_begin (asynchronous); see round_ready / round_end."""
+        import numpy as np
+        f = np.ascontiguousarray(first, dtype=np.int64)
+        c = np.ascontiguousarray(count, dtype=np.int64)
+        check(lib().mlmc_round_begin(self._h, f.ctypes.data_as(_I64P), c.ctypes.data_as(_I64P)),
+              "mlmc_round_begin")
+
+    def round_ready(self):
+        return lib().mlmc_round_ready(self._h)
+
+    def round_end(self):
+        return lib().mlmc_round_end(self._h)
+
     def round_values(self, level, count):
         """mlmc_round_values: (Q_l, Q_{l-1}) of the last finished round's samples of `level`."""
         import numpy as np
@@ -467,10 +514,11 @@ class Server:
     ``poll(id)`` returns None while it runs, else a dict of its result
     (times in seconds on the server clock)."""
 
-    def __init__(self, hbm_budget=0, max_slots=8, pilot=32, device=0, max_rounds=0, adapt_from=0):
+    def __init__(self, hbm_budget=0, max_slots=8, pilot=32, device=0, max_rounds=0, adapt_from=0,
+                 solo_rounds=0):
         sc = ServerConfig(hbm_budget=int(hbm_budget), max_slots=int(max_slots), pilot=int(pilot),
                           device=int(device), max_rounds=int(max_rounds),
-                          adapt_from=int(adapt_from))
+                          adapt_from=int(adapt_from), solo_rounds=int(solo_rounds))
         self._h = _P()
         check(lib().mlmc_server_create(ctypes.byref(sc), ctypes.byref(self._h)),
               "mlmc_server_create")
@@ -489,7 +537,8 @@ class Server:
         if not done.value:
             return None
         n = [int(x) for x in r.N]
-        return dict(id=r.id, status=r.status, rounds=r.rounds, levels=r.levels, q_hat=r.q_hat,
+        return dict(id=r.id, status=r.status, rounds=r.rounds, levels=r.levels,
+                    group_rounds=r.group_rounds, q_hat=r.q_hat,
                     stat_var=r.stat_var, t_submit=r.t_submit, t_admit=r.t_admit,
                     t_done=r.t_done, dof_solves=r.dof_solves, N=n)
 

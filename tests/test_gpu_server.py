@@ -61,9 +61,9 @@ def alone(m):
     return res
 
 
-def serve(m, budget, slots, stagger):
+def serve(m, budget, slots, stagger, solo=0):
     out = {}
-    with m.Server(hbm_budget=budget, max_slots=slots, pilot=PILOT) as srv:
+    with m.Server(hbm_budget=budget, max_slots=slots, pilot=PILOT, solo_rounds=solo) as srv:
         ids = []
         for k, (wl, eps) in enumerate(mix()):
             ids.append(srv.submit(m.config_from_workload(wl), eps))
@@ -75,10 +75,16 @@ def serve(m, budget, slots, stagger):
     return out
 
 
-@pytest.mark.parametrize("budget,slots,stagger", [(0, 16, False), (48 << 20, 3, True), (4 << 20, 2, False)])
-def test_result_same_alone_and_in_mix(m, budget, slots, stagger):
+@pytest.mark.parametrize("budget,slots,stagger,solo", [(0, 16, False, 0), (48 << 20, 3, True, 0),
+                                                     (4 << 20, 2, False, 0), (0, 16, False, 1)])
+def test_result_same_alone_and_in_mix(m, budget, slots, stagger, solo):
+    """Bit for bit: alone through mlmc_run, and served in the mix, with
+    requests that can share solves batched into group rounds (solo 0) or
+    each in its own rounds (solo 1)."""
     ref = alone(m)
-    got = serve(m, budget, slots, stagger)
+    got = serve(m, budget, slots, stagger, solo)
+    if solo:
+        assert all(r["group_rounds"] == 0 for r in got.values())
     for k, (q, v, N) in enumerate(ref):
         r = got[k]
         assert r is not None and r["status"] == 0, (k, r)
@@ -128,3 +134,13 @@ def test_invalid_requests_rejected(m):
             srv.submit(cfg, 1e-3)
         with pytest.raises(m.MLMCError):
             srv.poll(12345)
+
+
+def test_requests_that_arrive_together_share_group_rounds(m):
+    """Requests admitted at the same moment whose solves can share launches
+    (same dimension, form, meshes and tolerances; different fields, modes and
+    seeds) run their rounds as group rounds: same-size levels of different
+    requests are solved by one batched set of launches."""
+    got = serve(m, 0, 16, False, 0)
+    assert sum(r["group_rounds"] for r in got.values()) >= 4
+    assert all(r["group_rounds"] <= r["rounds"] for r in got.values())
