@@ -404,7 +404,7 @@ def serving_both(m, args, device=0):
         fixed = serving_run(m, args, device, 0)
         keep = ("p50_time_to_eps_s", "p99_time_to_eps_s", "mean_time_to_eps_s",
                 "aggregate_dof_solves_per_s", "span_s", "max_in_flight", "failed", "failed_requests",
-                "rounds")
+                "rounds", "group_rounds")
         res["fixed_levels"] = {k: fixed[k] for k in keep}
     return res
 
@@ -473,6 +473,7 @@ def serving_run(m, args, device=0, adapt=0):
             "p99_admission_wait_s": float(np.percentile(wait, 99)),
             "aggregate_dof_solves_per_s": dofs / span, "span_s": span,
             "max_in_flight": peak, "rounds": int(sum(r["rounds"] for r in res)),
+            "group_rounds": int(sum(r["group_rounds"] for r in res)),
             "clocks": clk,
             "mix": "eps~U[5e-4,5e-3], dim 2|3 (p=1/2), sigma2~U[0.5,2], corr_len~U[0.05,0.3]; "
                    "2D 32^2..1024^2 domain-mean QoI, 3D 8^3..128^3 box QoI; m=ceil(1.5/corr_len) "
@@ -569,6 +570,59 @@ def roofline_of(res, peaks, fp64_alu, dim=2, fp64_probe=None):
     return r
 
 
+def kle_compare(m, wl, stream, peaks, batch=None, reps=10):
+    """The KLE contraction of one coupled batch of the finest mesh: the FP64
+    sum-factorised kernel (mlmc_kappa, the kappa of the FP64 residual) and the
+    tensor-core kernel (mlmc_kappa32, split BF16 on tcgen05, the FP32 kappa of
+    the inner solves), each timed with CUDA events on the plan's stream.
+    Tensor roofline: the dense contraction's flops 2 ne M B and the flops the
+    MMAs issue (three BF16 products on tiles padded to 128 elements x 64
+    modes x 16 samples) against the measured BF16 peak."""
+    import torch
+    L = wl["levels"] - 1
+    n = wl["n0"] << L
+    d = wl["dim"]
+    B = batch or (100 if d == 2 else 16)
+    cfg = m.config_from_workload(wl, precision="mixed")
+    M = m.coef_count(cfg)
+    ne = n ** d
+    es = m.elem_stride(d, n)
+    res = {"mesh": "%d^%d" % (n, d), "samples": B, "modes": M}
+    with torch.cuda.stream(stream):
+        with m.Plan(cfg, stream.cuda_stream) as plan:
+            xi = torch.zeros(B * M, dtype=torch.float64, device="cuda")
+            plan.draw_xi(L, 0, B, xi.data_ptr())
+            k64 = torch.empty(B * es, dtype=torch.float64, device="cuda")
+            k32 = torch.empty(B * es, dtype=torch.float32, device="cuda")
+            for name, fn in (("fp64_sum_factorised",
+                              lambda: plan.kappa(L, xi.data_ptr(), B, k64.data_ptr())),
+                             ("tensor_cores_split_bf16",
+                              lambda: plan.kappa32(L, xi.data_ptr(), B, k32.data_ptr()))):
+                fn()
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(reps):
+                    fn()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                res[name] = {"ms": e0.elapsed_time(e1) / reps}
+    dense = 2.0 * ne * M * B
+    issued = 3 * 2.0 * ((ne + 127) // 128 * 128) * ((M + 63) // 64 * 64) * ((min(B, 256) + 15) // 16 * 16) \
+        * ((B + 255) // 256)
+    t = res["tensor_cores_split_bf16"]["ms"] / 1e3
+    peak = peaks.get("bf16_tflops")
+    tens = {"bound": "tensor", "achieved": round(issued / t / 1e12, 2), "unit": "TFLOP/s",
+            "dense_contraction_tflops": round(dense / t / 1e12, 2),
+            "peak": peak, "peak_source": "measured (MEASURED_PEAKS.json bf16_tflops)" if peak else None,
+            "frac": round(issued / t / 1e12 / peak, 4) if peak else None,
+            "kappa32_write_gbs": round(4.0 * ne * B / t / 1e9, 1)}
+    res["tensor_roofline"] = tens
+    res["faster"] = min(("fp64_sum_factorised", "tensor_cores_split_bf16"), key=lambda k: res[k]["ms"])
+    return res
+
+
 def bench_ours(args):
     import torch
     import torch.distributed as dist
@@ -621,6 +675,12 @@ def bench_ours(args):
     pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pk_path):
         peaks = json.load(open(pk_path))
+    # the mixed form with its FP32 kappa from the tensor cores (kle_tensor = 1)
+    kle_tc = None
+    if not args.single_form and "mixed" in forms:
+        cfg = m.config_from_workload(wl, precision="mixed", kle_tensor=1)
+        kle_tc = measure_form(m, wl, cfg, stream, args, world, barrier, with_e2e=False, rank=rank,
+                              gather=gather)
     main = forms[args.form]
     ms = reduce_max(main["ms"])
     e2e_s = reduce_max(sum(main["wall"]))
@@ -642,8 +702,16 @@ def bench_ours(args):
                        "autotune": res["tune"],
                        "roofline": roofline_of(res, peaks, fp64_alu=(form == "fp64"), dim=wl["dim"],
                                                fp64_probe=fp64_probe)}
+    if kle_tc is not None:
+        oms = reduce_max(kle_tc["ms"])
+        other["mixed+kle_tensor"] = {
+            "value": kle_tc["dofs_step"] * args.steps / (oms / 1e3), "unit": "coupled DOF-solves/s",
+            "ms_per_step": oms / args.steps, "samples_per_level": kle_tc["N"],
+            "q_hat": kle_tc["q"], "stat_var": kle_tc["v"], "gpu_launches": int(kle_tc["launches"]),
+            "kappa_share": kle_tc["shares"].get("kappa"), "autotune": kle_tc["tune"]}
     if rank == 0:
-        names = {"fp64": "plain FP64", "mixed": "mixed: FP32 inner PCG + FP64 refinement"}
+        names = {"fp64": "plain FP64", "mixed": "mixed: FP32 inner PCG + FP64 refinement",
+                 "mixed+kle_tensor": "mixed, FP32 kappa from the tensor-core KLE"}
         line = {"metric": "coupled DOF-solves/s", "value": value, "unit": "coupled DOF-solves/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": ms / args.steps, "time_to_eps_s": ms / args.steps / 1e3,
@@ -665,6 +733,7 @@ def bench_ours(args):
                 "e2e": {"value": e2e_value, "unit": "coupled DOF-solves/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "other_forms": {names[k]: v for k, v in other.items()}}
+        line["kle"] = kle_compare(m, wl, stream, peaks)
         if args.serve > 0:
             line["serving"] = serving_both(m, args, local)
         if not args.no_cpu_baseline:

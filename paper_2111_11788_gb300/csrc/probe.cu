@@ -6,7 +6,7 @@
 namespace {
 
 constexpr int PROBE_THREADS = 256;
-constexpr int PROBE_CHAINS = 8;
+constexpr int PROBE_CHAINS = 16;
 
 __device__ double g_probe_sink;
 
@@ -15,6 +15,7 @@ __global__ void __launch_bounds__(PROBE_THREADS) k_fma64_chains(int iters, doubl
 #pragma unroll
   for (int c = 0; c < PROBE_CHAINS; ++c) a[c] = seed + 1e-3 * (threadIdx.x + c);
   const double m = 0.9999999, add = 1e-9;
+#pragma unroll 4
   for (int k = 0; k < iters; ++k) {
 #pragma unroll
     for (int c = 0; c < PROBE_CHAINS; ++c) a[c] = fma(a[c], m, add);
@@ -34,8 +35,8 @@ extern "C" mlmc_status mlmc_probe_fp64_rate(void* stream, double* tflops, double
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return MLMC_ERR_CUDA;
-  const int blocks = sms * 4;   // 32 warps per SM, 8 chains each
-  const int iters = 1 << 15;
+  const int blocks = sms * 4;   // 32 warps per SM, 16 chains each
+  const int iters = 1 << 14;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return MLMC_ERR_CUDA;
   if (cudaEventCreate(&e1) != cudaSuccess) {

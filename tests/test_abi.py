@@ -175,3 +175,11 @@ def test_kle_tensor_flag_validated_without_a_device(m):
     bad = m.config(precision="mixed", kle_tensor=2)
     assert L.mlmc_round_bytes(ctypes.byref(bad), counts) == -1
     assert L.mlmc_kappa32(None, 0, None, 1, None) == m.MLMC_ERR_INVALID
+
+
+def test_coef_count_matches_the_oracle_mode_sets(m):
+    from oracle import kle
+    for dim, mpd, order in ((2, 8, -1), (3, 7, -1), (3, 16, 14), (2, 5, 3), (3, 4, 20)):
+        cfg = m.config(dim=dim, modes_per_dim=mpd, total_order=order)
+        assert m.coef_count(cfg) == kle.n_modes(dim, mpd, None if order < 0 else order)
+    assert m.lib().mlmc_coef_count(ctypes.byref(m.config(dim=4))) == -1
