@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--profile-level", type=int, default=None,
                     help="profiling case: only run this level's coupled batch twice, then exit")
     ap.add_argument("--profile-batch", type=int, default=64)
+    ap.add_argument("--profile-kle", action="store_true",
+                    help="profiling case: the KLE contraction of the finest level's batch "
+                         "(--profile-batch samples), FP64 and tensor-core kernels, twice each")
     ap.add_argument("--form", default="fp64", choices=["fp64", "mixed"],
                     help="form of the headline line (the other form is measured alongside)")
     ap.add_argument("--single-form", action="store_true")
@@ -299,6 +302,7 @@ def tuned_config(m, cfg, tune):
     if tune is not None:
         cfg2.inner_rtol, cfg2.mg_omega, cfg2.z_chunk = (tune["inner_rtol"], tune["mg_omega"],
                                                         tune["z_chunk"])
+        cfg2.stencil_tile, cfg2.batch_split = tune["stencil_tile"], tune["batch_split"]
     return cfg2
 
 
@@ -326,7 +330,14 @@ def measure_form(m, wl, cfg, stream, args, world, barrier, with_e2e, rank=0, gat
             # tuned on rank 0 and shared, so that every rank solves with the same settings
             if rank == 0:
                 with m.Plan(cfg, sh) as tp:
-                    tune = tp.autotune(wl["levels"] - 1, 32 if wl["dim"] == 2 else 16, 7)
+                    # solver knobs on the finest level, then the tile shape and the
+                    # batch split on a round over every level (from the tuned settings)
+                    cnt = 32 if wl["dim"] == 2 else 16
+                    tune = tp.autotune(wl["levels"] - 1, cnt, 7)
+                    t2 = tp.autotune(wl["levels"] - 1, cnt, 8 | 16)
+                    tune.update(stencil_tile=t2["stencil_tile"], batch_split=t2["batch_split"],
+                                candidates=tune["candidates"] + t2["candidates"],
+                                round_best_ms=t2["best_ms"], round_worst_ms=t2["worst_ms"])
             if world > 1:
                 import torch.distributed as dist
                 box = [tune]
@@ -771,9 +782,36 @@ def profile_case(args):
     print("profile case done: level %d, batch %d" % (args.profile_level, args.profile_batch))
 
 
+def profile_kle(args):
+    """Small case for ncu: the two KLE kernels on one batch of the finest mesh."""
+    import torch
+    from paper_2111_11788_gb300.build import build_library
+    build_library()
+    import paper_2111_11788_gb300.mlmc as m
+    wl = workload(args.workload)
+    L = wl["levels"] - 1
+    n = wl["n0"] << L
+    B = args.profile_batch
+    cfg = m.config_from_workload(wl, precision="mixed")
+    M = m.coef_count(cfg)
+    es = m.elem_stride(wl["dim"], n)
+    with m.Plan(cfg, torch.cuda.current_stream().cuda_stream) as plan:
+        xi = torch.zeros(B * M, dtype=torch.float64, device="cuda")
+        plan.draw_xi(L, 0, B, xi.data_ptr())
+        k64 = torch.empty(B * es, dtype=torch.float64, device="cuda")
+        k32 = torch.empty(B * es, dtype=torch.float32, device="cuda")
+        for _ in range(2):
+            plan.kappa(L, xi.data_ptr(), B, k64.data_ptr())
+            plan.kappa32(L, xi.data_ptr(), B, k32.data_ptr())
+    torch.cuda.synchronize()
+    print("profile case done: KLE of %d samples on %d^%d" % (B, n, wl["dim"]))
+
+
 def main():
     args = parse()
-    if args.profile_level is not None:
+    if args.profile_kle:
+        profile_kle(args)
+    elif args.profile_level is not None:
         profile_case(args)
     elif args.impl == "reference":
         bench_reference(args)

@@ -99,6 +99,17 @@ typedef struct mlmc_config {
                               to FP32. The FP64 outer residual uses the FP64
                               kappa either way, so results meet the same
                               tolerance; iterates differ in the last digits. */
+  int32_t stencil_tile;    /* 3D FP32 stencils: 0 (default) = full-width tiles
+                              staged by one TMA bulk copy per plane and array
+                              where the mesh allows it (32..256 cells per side),
+                              1 = 32 x 16 column tiles staged by cp.async. Same
+                              results either way; set by mlmc_autotune */
+  int32_t batch_split;     /* rounds: each level's batch of coupled samples is
+                              split into this many near-equal batches (at most
+                              count of them), solved side by side as parallel
+                              graph branches and folded in sample order
+                              (0 or 1 = one batch per level, up to 64). Same
+                              results; set by mlmc_autotune */
 } mlmc_config;
 
 /* Per-level Welford state (Eq. (sample_variance): V = m2 / n). */
@@ -312,7 +323,8 @@ mlmc_status mlmc_round_values(mlmc_plan plan, int level, double* q_fine, double*
 
 /* ---- autotuning ------------------------------------------------------ */
 
-enum { MLMC_TUNE_INNER_RTOL = 1, MLMC_TUNE_MG_OMEGA = 2, MLMC_TUNE_Z_CHUNK = 4 };
+enum { MLMC_TUNE_INNER_RTOL = 1, MLMC_TUNE_MG_OMEGA = 2, MLMC_TUNE_Z_CHUNK = 4, MLMC_TUNE_TILE = 8,
+       MLMC_TUNE_BATCH = 16 };
 
 typedef struct mlmc_tune_report {
   int32_t candidates;   /* settings timed */
@@ -321,13 +333,18 @@ typedef struct mlmc_tune_report {
   double mg_omega;      /* chosen Jacobi damping of the multigrid smoother */
   double best_ms;       /* time of one coupled batch with the chosen setting */
   double worst_ms;      /* slowest setting */
+  int32_t stencil_tile; /* chosen 3D FP32 stencil tile shape (mlmc_config.stencil_tile) */
+  int32_t batch_split;  /* chosen batches per level in rounds (0 = one) */
 } mlmc_tune_report;
 
 /* Time `count` (1..4096) coupled samples of `level` under every setting of
  * the selected knobs (flags: MLMC_TUNE_*; mixed-form inner tolerance
- * 1e-2..3e-4, multigrid damping 0.7..0.9, 3D z-planes per stencil CTA) and
- * keep the fastest in the plan's configuration (inner_rtol, mg_omega,
- * z_chunk; each setting is timed twice and the faster time counts; the
+ * 1e-2..3e-4, multigrid damping 0.7..0.9, 3D z-planes per stencil CTA, the
+ * 3D FP32 stencil tile shape, and the batch split of rounds: 1, 2 or 4
+ * batches per level; with that knob the probe is a round of `count`
+ * samples on every level up to `level`) and keep the fastest in the plan's configuration (inner_rtol, mg_omega,
+ * z_chunk, stencil_tile, batch_split; each setting is timed twice and the
+ * faster time counts; the
  * plan's current setting stays unless another is more than 2% faster;
  * cached graphs are rebuilt; a setting whose
  * solves hit the iteration cap is never chosen). Probe samples use indices

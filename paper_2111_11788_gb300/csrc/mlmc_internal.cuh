@@ -79,6 +79,7 @@ struct Grid {
   int sx, sy;       // 2D: stencil CTAs per sample (strip groups x row chunks);
                     // 3D: node-tile CTAs per sample of the pointwise kernels (sx)
   int zc;           // 3D: z-planes per CTA of the z-marching stencil kernels
+  int zt;           // 3D FP32 z-march tiles: 0 = full width by TMA where possible, 1 = 32 x 16
   int zx;           // 3D: z-marching CTAs per sample
   int64_t tiles_s;  // partials per sample written by stencil kernels
   int fx;           // flat CTAs per sample
@@ -90,7 +91,7 @@ struct Grid {
   }
 };
 
-Grid make_grid(int dim, int n, int z_chunk = 0);
+Grid make_grid(int dim, int n, int z_chunk = 0, int stencil_tile = 0);
 
 // Runs set() once per device of this process (function attributes such as
 // the shared-memory opt-in are per device); device ids below 64.

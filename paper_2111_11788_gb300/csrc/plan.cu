@@ -19,9 +19,10 @@
 
 namespace mlmc {
 
-Grid make_grid(int dim, int n, int z_chunk) {
+Grid make_grid(int dim, int n, int z_chunk, int stencil_tile) {
   Grid g{};
   g.dim = dim;
+  g.zt = stencil_tile;
   g.n = n;
   g.ns = round_up(ipow(n + 1, dim), 32);
   g.es = round_up(ipow(n, dim), 32);
@@ -299,8 +300,13 @@ struct mlmc_plan_s {
   std::vector<cudaStream_t> branch;                  // capture streams of round branches
   std::vector<cudaEvent_t> branch_ev;
   cudaEvent_t round_done = nullptr;                  // recorded after a launched round
-  std::vector<size_t> round_off;                     // workspace regions of the launched round
-  std::vector<int64_t> round_count;
+  std::vector<int64_t> round_count;                  // samples per level (non-empty: a round in flight)
+  struct Chunk {
+    int level;
+    size_t off;          // workspace region
+    int64_t first, count;
+  };
+  std::vector<Chunk> round_chunks;                   // batched solves of the round in flight
   std::vector<size_t> done_off;                      // the last finished round, while its
   std::vector<int64_t> done_count;                   // per-sample values are still in place
   // a round over several plans driven by this one (cross-request batching):
@@ -352,7 +358,8 @@ std::vector<int32_t> coef_slots(const mlmc_config* c) {
 
 mlmc_status validate(const mlmc_config* c) {
   if (c && (c->total_order < -1 || c->z_chunk < 0 || (c->nested_guess != 0 && c->nested_guess != 1) ||
-            (c->kle_tensor != 0 && c->kle_tensor != 1)))
+            (c->kle_tensor != 0 && c->kle_tensor != 1) || (c->stencil_tile != 0 && c->stencil_tile != 1) ||
+            c->batch_split < 0 || c->batch_split > 64))
     return MLMC_ERR_INVALID;
   if (!c) return MLMC_ERR_INVALID;
   if (c->dim != 2 && c->dim != 3) return MLMC_ERR_INVALID;
@@ -530,12 +537,12 @@ void mesh_info_shape(const mlmc_config& c, int l, MeshInfo& mi) {
   mi.n = c.coarse_cells << l;
   mi.K = 1;
   mi.table = nullptr;
-  mi.g[0] = make_grid(c.dim, mi.n, c.z_chunk);
+  mi.g[0] = make_grid(c.dim, mi.n, c.z_chunk, c.stencil_tile);
   if (c.solver == MLMC_GMG_PCG && mi.n > 2) {
     int n = mi.n;
     while (n > 2 && mi.K < MAX_MG) {
       n /= 2;
-      mi.g[mi.K++] = make_grid(c.dim, n, c.z_chunk);
+      mi.g[mi.K++] = make_grid(c.dim, n, c.z_chunk, c.stencil_tile);
     }
   }
 }
@@ -1215,7 +1222,9 @@ Guess guess_views(mlmc_plan p, int level, int side, bool mixed, CoupledWs& w) {
 // Coupled batch of `level` issued into the graph being captured on p->stream,
 // in the workspace region at `region`: xi, kappa and solve on mesh `level`,
 // kappa and solve on mesh `level - 1`, Welford fold in sample order.
-mlmc_status issue_level(mlmc_plan p, int level, int64_t first, int64_t B, void* region) {
+mlmc_status fold_batch(mlmc_plan p, int level, int64_t B, void* region);
+
+mlmc_status issue_level(mlmc_plan p, int level, int64_t first, int64_t B, void* region, bool fold = true) {
   const bool mixed = is_mixed(p);
   const int M = p->M;
   const int64_t gns = guess_ns_of(p->cfg, level);
@@ -1238,14 +1247,54 @@ mlmc_status issue_level(mlmc_plan p, int level, int64_t first, int64_t B, void* 
     st = mixed ? issue_mixed(p, mi, w.mx, B, qd, itd, gs) : issue_fp64(p, mi, w.s, B, qd, itd, gs);
     if (st != MLMC_OK) return st;
   }
+  return fold ? fold_batch(p, level, B, region) : MLMC_OK;
+}
+
+// Y = Q_f - Q_c of the coupled batch in `region` folded into the level state in sample order.
+mlmc_status fold_batch(mlmc_plan p, int level, int64_t B, void* region) {
   Carve c(region);
   CoupledWs w;
-  carve_coupled(c, p->meshes[level], M, B, mixed, gns, 0, w);
+  carve_coupled(c, p->meshes[level], p->M, B, is_mixed(p), guess_ns_of(p->cfg, level), 0, w);
   const double cost = level_cost_cfg(&p->cfg, level);
   CK(run(p, KID_WELFORD, [&] {
     return launch_welford(p->stream, w.qf, level > 0 ? w.qc : nullptr, B, p->d_states + level, cost);
   }));
   return MLMC_OK;
+}
+
+// Capture streams and events for `branches` parallel branches of a round.
+mlmc_status ensure_branches(mlmc_plan p, size_t branches, size_t events) {
+  while (p->branch.size() < branches) {
+    cudaStream_t bs;
+    if (cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking) != cudaSuccess) return MLMC_ERR_CUDA;
+    p->branch.push_back(bs);
+  }
+  while (p->branch_ev.size() < events) {
+    cudaEvent_t ev;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return MLMC_ERR_CUDA;
+    p->branch_ev.push_back(ev);
+  }
+  return MLMC_OK;
+}
+
+// Batched solves of a round: per level, the samples in batch_split
+// near-equal chunks (one chunk when it is 0 or 1), each with its own
+// workspace region.
+size_t round_chunks_of(const mlmc_config& c, const MeshInfo* meshes, int M, const std::vector<int64_t>& first,
+                       const std::vector<int64_t>& count, std::vector<mlmc_plan_s::Chunk>* out) {
+  const bool mixed = c.precision == MLMC_MIXED;
+  size_t total = 0;
+  for (int l = 0; l < c.n_levels; ++l) {
+    if (count[l] <= 0) continue;
+    const int64_t k = std::max<int64_t>(1, std::min<int64_t>(c.batch_split, count[l]));
+    const int64_t w = (count[l] + k - 1) / k;
+    for (int64_t s0 = 0; s0 < count[l]; s0 += w) {
+      const int64_t cnt = std::min<int64_t>(w, count[l] - s0);
+      if (out) out->push_back({l, total, first[l] + s0, cnt});
+      total += (size_t)round_up((int64_t)coupled_bytes(meshes[l], M, cnt, mixed, guess_ns_of(c, l)), 256);
+    }
+  }
+  return total;
 }
 
 // Samples first[l] .. first[l] + count[l] - 1 of every level in one graph
@@ -1257,24 +1306,22 @@ mlmc_status round_launch(mlmc_plan p, const std::vector<int64_t>& first,
                          const std::vector<int64_t>& count) {
   const int L1 = p->cfg.n_levels;
   const bool mixed = is_mixed(p);
-  std::vector<size_t> off(L1, 0);
-  size_t total = 0;
-  for (int l = 0; l < L1; ++l) {
-    if (count[l] <= 0) continue;
+  for (int l = 0; l < L1; ++l)
     if (count[l] > 65535) return MLMC_ERR_UNIMPLEMENTED;
-    off[l] = total;
-    total += (size_t)round_up((int64_t)coupled_bytes(p->meshes[l], p->M, count[l], mixed,
-                                                     guess_ns_of(p->cfg, l)), 256);
-  }
-  p->round_off = off;
+  std::vector<mlmc_plan_s::Chunk> chunks;
+  const size_t total = round_chunks_of(p->cfg, p->meshes.data(), p->M, first, count, &chunks);
   p->round_count = count;
+  p->round_chunks = chunks;
   p->round_M = p->M;
   if (total == 0) return MLMC_OK;
-  if (total > p->ws_budget || (int)p->branch.size() < L1) return MLMC_ERR_UNIMPLEMENTED;
-  mlmc_status st = ensure_ws(p, total);
+  if (total > p->ws_budget) return MLMC_ERR_UNIMPLEMENTED;
+  // branches: one per chunk; events: the fork, one per chunk, one per level
+  mlmc_status st = ensure_branches(p, chunks.size(), 1 + chunks.size() + L1);
+  if (st != MLMC_OK) return st;
+  st = ensure_ws(p, total);
   if (st != MLMC_OK) return st;
   p->round_ws = (char*)p->ws;
-  std::vector<int64_t> key = {mixed ? 1 : 0, (int64_t)(uintptr_t)p->ws};
+  std::vector<int64_t> key = {mixed ? 1 : 0, (int64_t)(uintptr_t)p->ws, p->cfg.batch_split};
   key.insert(key.end(), first.begin(), first.end());
   key.insert(key.end(), count.begin(), count.end());
   auto it = p->round_graphs.find(key);
@@ -1282,20 +1329,41 @@ mlmc_status round_launch(mlmc_plan p, const std::vector<int64_t>& first,
     GraphRec rec;
     st = build_graph(p, [&]() -> mlmc_status {
       cudaStream_t origin = p->stream;
-      CK(cudaEventRecord(p->branch_ev[0], origin));
-      int nb = 0;
+      const size_t nc = chunks.size();
+      cudaEvent_t fork = p->branch_ev[0];
+      CK(cudaEventRecord(fork, origin));
+      // chunks finest level first, each on its own branch
+      std::vector<size_t> order(nc);
+      for (size_t i = 0; i < nc; ++i) order[i] = i;
+      std::stable_sort(order.begin(), order.end(),
+                       [&](size_t a, size_t b) { return chunks[a].level > chunks[b].level; });
       mlmc_status s2 = MLMC_OK;
-      for (int l = L1 - 1; l >= 0 && s2 == MLMC_OK; --l) {
-        if (count[l] <= 0) continue;
-        cudaStream_t S = p->branch[nb];
-        CK(cudaStreamWaitEvent(S, p->branch_ev[0], 0));
+      for (size_t i = 0; i < nc && s2 == MLMC_OK; ++i) {
+        const auto& ch = chunks[order[i]];
+        cudaStream_t S = p->branch[order[i]];
+        CK(cudaStreamWaitEvent(S, fork, 0));
         p->stream = S;
-        s2 = issue_level(p, l, first[l], count[l], (char*)p->ws + off[l]);
+        s2 = issue_level(p, ch.level, ch.first, ch.count, (char*)p->ws + ch.off, false);
         p->stream = origin;
-        if (s2 == MLMC_OK) CK(cudaEventRecord(p->branch_ev[1 + nb], S));
-        ++nb;
+        if (s2 == MLMC_OK) CK(cudaEventRecord(p->branch_ev[1 + order[i]], S));
       }
-      for (int i = 0; i < nb && s2 == MLMC_OK; ++i) CK(cudaStreamWaitEvent(origin, p->branch_ev[1 + i], 0));
+      // each level's chunks are folded in sample order on the branch of its first chunk
+      for (int l = 0; l < L1 && s2 == MLMC_OK; ++l) {
+        int head = -1;
+        for (size_t i = 0; i < nc && s2 == MLMC_OK; ++i) {
+          if (chunks[i].level != l) continue;
+          if (head < 0) head = (int)i;
+          cudaStream_t S = p->branch[head];
+          if ((int)i != head) CK(cudaStreamWaitEvent(S, p->branch_ev[1 + i], 0));
+          p->stream = S;
+          s2 = fold_batch(p, l, chunks[i].count, (char*)p->ws + chunks[i].off);
+          p->stream = origin;
+        }
+        if (head >= 0 && s2 == MLMC_OK) {
+          CK(cudaEventRecord(p->branch_ev[1 + nc + l], p->branch[head]));
+          CK(cudaStreamWaitEvent(origin, p->branch_ev[1 + nc + l], 0));
+        }
+      }
       return s2;
     }, &rec);
     if (st != MLMC_OK) return st;
@@ -1320,7 +1388,7 @@ bool same_solve(const mlmc_config& a, const mlmc_config& b) {
          a.inner_rtol == b.inner_rtol && a.inner_max_iter == b.inner_max_iter &&
          a.outer_max_iter == b.outer_max_iter && a.z_chunk == b.z_chunk &&
          a.nested_guess == b.nested_guess && a.qoi == b.qoi && a.box_lo == b.box_lo &&
-         a.box_hi == b.box_hi && a.kle_tensor == 0 && b.kle_tensor == 0;
+         a.box_hi == b.box_hi && a.stencil_tile == b.stencil_tile && a.kle_tensor == 0 && b.kle_tensor == 0;
 }
 
 // The coupled batch of `level` over the members of p's group, issued into the
@@ -1409,8 +1477,10 @@ mlmc_status group_launch(mlmc_plan p, const std::vector<int64_t>& first, char* w
                               256);
   }
   if (total > ws_bytes) return MLMC_ERR_OOM;
-  p->round_off = off;
   p->round_count = B;
+  p->round_chunks.clear();
+  for (int l = 0; l < L1; ++l)
+    if (B[l] > 0) p->round_chunks.push_back({l, off[l], 0, B[l]});
   p->round_ws = ws;
   p->round_M = Mmax;
   if (total == 0) return MLMC_OK;
@@ -1455,10 +1525,14 @@ mlmc_status round_finish(mlmc_plan p, bool* bad, int32_t* member_bad = nullptr) 
   if (member_bad)
     for (int k = 0; k < nm; ++k) member_bad[k] = 0;
   std::vector<int32_t> h;
-  for (int l = 0; l < L1 && l < (int)p->round_count.size(); ++l) {
-    const int64_t n = p->round_count[l];
+  bool one_per_level = true;
+  std::vector<int> seen(L1, 0);
+  for (const auto& ch : p->round_chunks) {
+    const int l = ch.level;
+    const int64_t n = ch.count;
     if (n <= 0) continue;
-    Carve c(p->round_ws + p->round_off[l]);
+    if (seen[l]++) one_per_level = false;
+    Carve c(p->round_ws + ch.off);
     CoupledWs w;
     carve_coupled(c, p->meshes[l], p->round_M, n, mixed, guess_ns_of(p->cfg, l), 0, w);
     h.resize(2 * n);
@@ -1483,13 +1557,20 @@ mlmc_status round_finish(mlmc_plan p, bool* bad, int32_t* member_bad = nullptr) 
     p->group.clear();
     p->group_count.clear();
     p->done_count.clear();
+  } else if (one_per_level) {
+    p->done_off.assign(L1, 0);
+    p->done_count.assign(L1, 0);
+    for (const auto& ch : p->round_chunks) {
+      p->done_off[ch.level] = ch.off;
+      p->done_count[ch.level] = ch.count;
+    }
   } else {
-    p->done_off = p->round_off;
-    p->done_count = p->round_count;
+    p->done_count.clear();   // a level in several chunks: its values are not in one place
   }
   p->round_ws = (char*)p->ws;
   p->round_M = p->M;
   p->round_count.clear();
+  p->round_chunks.clear();
   return MLMC_OK;
 }
 
@@ -1569,6 +1650,8 @@ void mlmc_config_default(mlmc_config* c) {
   c->z_chunk = 0;
   c->nested_guess = 1;
   c->kle_tensor = 0;
+  c->stencil_tile = 0;
+  c->batch_split = 0;
 }
 
 int64_t mlmc_node_stride(int dim, int n) {
@@ -1670,12 +1753,12 @@ mlmc_status mlmc_plan_create(const mlmc_config* cfg, void* stream, mlmc_plan* ou
     MeshInfo& mi = p->meshes[l];
     mi.n = cfg->coarse_cells << l;
     mi.K = 1;
-    mi.g[0] = make_grid(cfg->dim, mi.n, cfg->z_chunk);
+    mi.g[0] = make_grid(cfg->dim, mi.n, cfg->z_chunk, cfg->stencil_tile);
     if (cfg->solver == MLMC_GMG_PCG && mi.n > 2) {
       int n = mi.n;
       while (n > 2 && mi.K < MAX_MG) {
         n /= 2;
-        mi.g[mi.K++] = make_grid(cfg->dim, n, cfg->z_chunk);
+        mi.g[mi.K++] = make_grid(cfg->dim, n, cfg->z_chunk, cfg->stencil_tile);
       }
     }
     if (cudaMalloc(&mi.table, sizeof(double) * (size_t)mi.n * m) != cudaSuccess) {
@@ -1769,15 +1852,11 @@ mlmc_status mlmc_plan_set_workspace(mlmc_plan p, void* ws, uint64_t bytes) {
 int64_t mlmc_round_bytes(const mlmc_config* cfg, const int64_t* count) {
   if (!cfg || !count || validate(cfg) != MLMC_OK) return -1;
   const int M = (int)coef_count(cfg);
-  int64_t total = 0;
-  for (int l = 0; l < cfg->n_levels; ++l) {
-    if (count[l] <= 0) continue;
-    MeshInfo mi;
-    mesh_info_shape(*cfg, l, mi);
-    total += round_up((int64_t)coupled_bytes(mi, M, count[l], cfg->precision == MLMC_MIXED,
-                                             guess_ns_of(*cfg, l)), 256);
-  }
-  return total;
+  std::vector<MeshInfo> meshes(cfg->n_levels);
+  for (int l = 0; l < cfg->n_levels; ++l) mesh_info_shape(*cfg, l, meshes[l]);
+  std::vector<int64_t> f(cfg->n_levels, 0), c(count, count + cfg->n_levels);
+  for (auto& x : c) x = std::max<int64_t>(x, 0);
+  return (int64_t)round_chunks_of(*cfg, meshes.data(), M, f, c, nullptr);
 }
 
 mlmc_status mlmc_plan_destroy(mlmc_plan p) {
@@ -2149,7 +2228,7 @@ mlmc_status mlmc_run_adaptive(mlmc_plan p, double eps, int64_t pilot, int32_t L0
 // Rebuilds the grids of every mesh (after a change of cfg.z_chunk).
 void regrid(mlmc_plan p) {
   for (auto& mi : p->meshes)
-    for (int k = 0; k < mi.K; ++k) mi.g[k] = make_grid(p->cfg.dim, mi.g[k].n, p->cfg.z_chunk);
+    for (int k = 0; k < mi.K; ++k) mi.g[k] = make_grid(p->cfg.dim, mi.g[k].n, p->cfg.z_chunk, p->cfg.stencil_tile);
 }
 
 mlmc_status mlmc_autotune(mlmc_plan p, int level, int64_t count, int flags, mlmc_tune_report* out) {
@@ -2167,6 +2246,14 @@ mlmc_status mlmc_autotune(mlmc_plan p, int level, int64_t count, int flags, mlmc
   if (p->cfg.solver == MLMC_GMG_PCG && (flags & MLMC_TUNE_MG_OMEGA)) omegas = {0.7, 0.8, 0.9};
   std::vector<int> zcs = {p->cfg.z_chunk};
   if (p->cfg.dim == 3 && (flags & MLMC_TUNE_Z_CHUNK)) zcs = {0, 24, 32, 64};
+  std::vector<int> tiles = {p->cfg.stencil_tile};
+  if (p->cfg.dim == 3 && mixed && (flags & MLMC_TUNE_TILE)) tiles = {0, 1};
+  std::vector<int> widths = {p->cfg.batch_split};
+  const bool tune_split = (flags & MLMC_TUNE_BATCH) && graphs_on(p);
+  if (tune_split) {
+    widths = {0};
+    for (int k = 2; k <= 4 && count / k >= 2; k *= 2) widths.push_back(k);
+  }
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -2183,50 +2270,80 @@ mlmc_status mlmc_autotune(mlmc_plan p, int level, int64_t count, int flags, mlmc
   // the plan's own setting is kept unless another one beats it by 2%: the
   // probe is a small sample of the iteration counts, so near-ties are noise.
   const int64_t first = (int64_t(1) << 32) - count;
-  double base_ms = -1.0;
-  for (double rt : rtols) {
-    for (double om : omegas) {
-      for (int zc : zcs) {
-        if (st != MLMC_OK) break;
-        p->cfg.inner_rtol = rt;
-        p->cfg.mg_omega = om;
-        p->cfg.z_chunk = zc;
-        if ((st = settle_graph_launches(p)) != MLMC_OK) break;
-        clear_graphs(p);
-        regrid(p);
-        // the first call builds and caches the solve graphs; the next two are timed
-        st = mlmc_sample_level(p, level, first, count, nullptr, nullptr, nullptr);
-        if (st != MLMC_OK && st != MLMC_ERR_NOT_CONVERGED) break;
-        float ms = -1.0f;
-        mlmc_status st2 = MLMC_OK;
-        for (int rep = 0; rep < 2; ++rep) {
-          if (cudaEventRecord(e0, p->stream) != cudaSuccess) { st = MLMC_ERR_CUDA; break; }
-          st2 = mlmc_sample_level(p, level, first, count, nullptr, nullptr, nullptr);
-          if (cudaEventRecord(e1, p->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
-            st = MLMC_ERR_CUDA;
-            break;
-          }
-          float t = 0.0f;
-          cudaEventElapsedTime(&t, e0, e1);
-          if (ms < 0.0f || t < ms) ms = t;
-          if (st2 != MLMC_OK) break;
-        }
-        if (st == MLMC_ERR_CUDA) break;
-        st = MLMC_OK;
-        ++r.candidates;
-        if (st2 == MLMC_ERR_NOT_CONVERGED) continue;   // a setting that fails is never chosen
-        if (st2 != MLMC_OK) { st = st2; break; }
-        if (rt == base.inner_rtol && om == base.mg_omega && zc == base.z_chunk) base_ms = ms;
-        if (r.best_ms < 0.0 || ms < r.best_ms) {
-          r.best_ms = ms;
-          r.inner_rtol = rt;
-          r.mg_omega = om;
-          r.z_chunk = zc;
-        }
-        if (ms > r.worst_ms) r.worst_ms = ms;
-      }
+  // one probe: the level's samples as one round (a graph with a branch per
+  // batch; the batch width matters there) or, without graphs, one batched call
+  const bool as_round = graphs_on(p);
+  auto probe = [&]() -> mlmc_status {
+    if (!as_round) return mlmc_sample_level(p, level, first, count, nullptr, nullptr, nullptr);
+    std::vector<int64_t> f(L1, 0), c(L1, 0);
+    for (int l = tune_split ? 0 : level; l <= level; ++l) {   // the split acts on every level of a round
+      f[l] = first;
+      c[l] = count;
     }
-  }
+    mlmc_status s1 = round_launch(p, f, c);
+    if (s1 != MLMC_OK) {
+      p->round_count.clear();
+      p->round_chunks.clear();
+      return s1;
+    }
+    bool bad = false;
+    s1 = round_finish(p, &bad);
+    return s1 != MLMC_OK ? s1 : (bad ? MLMC_ERR_NOT_CONVERGED : MLMC_OK);
+  };
+  double base_ms = -1.0;
+  for (double rt : rtols)
+    for (double om : omegas)
+      for (int zc : zcs)
+        for (int tl : tiles)
+          for (int bw : widths) {
+            if (st != MLMC_OK) break;
+            p->cfg.inner_rtol = rt;
+            p->cfg.mg_omega = om;
+            p->cfg.z_chunk = zc;
+            p->cfg.stencil_tile = tl;
+            p->cfg.batch_split = bw;
+            if ((st = settle_graph_launches(p)) != MLMC_OK) break;
+            clear_graphs(p);
+            regrid(p);
+            // the first call builds and caches the graphs; the next two are timed
+            st = probe();
+            if (st == MLMC_ERR_UNIMPLEMENTED) {   // the round does not fit the budget: skip
+              st = MLMC_OK;
+              continue;
+            }
+            if (st != MLMC_OK && st != MLMC_ERR_NOT_CONVERGED) break;
+            float ms = -1.0f;
+            mlmc_status st2 = MLMC_OK;
+            for (int rep = 0; rep < 2; ++rep) {
+              if (cudaEventRecord(e0, p->stream) != cudaSuccess) { st = MLMC_ERR_CUDA; break; }
+              st2 = probe();
+              if (cudaEventRecord(e1, p->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+                st = MLMC_ERR_CUDA;
+                break;
+              }
+              float t = 0.0f;
+              cudaEventElapsedTime(&t, e0, e1);
+              if (ms < 0.0f || t < ms) ms = t;
+              if (st2 != MLMC_OK) break;
+            }
+            if (st == MLMC_ERR_CUDA) break;
+            st = MLMC_OK;
+            ++r.candidates;
+            if (st2 == MLMC_ERR_NOT_CONVERGED) continue;   // a setting that fails is never chosen
+            if (st2 != MLMC_OK) { st = st2; break; }
+            if (rt == base.inner_rtol && om == base.mg_omega && zc == base.z_chunk && tl == base.stencil_tile &&
+                bw == base.batch_split)
+              base_ms = ms;
+            if (r.best_ms < 0.0 || ms < r.best_ms) {
+              r.best_ms = ms;
+              r.inner_rtol = rt;
+              r.mg_omega = om;
+              r.z_chunk = zc;
+              r.stencil_tile = tl;
+              r.batch_split = bw;
+            }
+            if (ms > r.worst_ms) r.worst_ms = ms;
+          }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (base_ms >= 0.0 && base_ms <= 1.02 * r.best_ms) {
@@ -2234,6 +2351,8 @@ mlmc_status mlmc_autotune(mlmc_plan p, int level, int64_t count, int flags, mlmc
     r.inner_rtol = base.inner_rtol;
     r.mg_omega = base.mg_omega;
     r.z_chunk = base.z_chunk;
+    r.stencil_tile = base.stencil_tile;
+    r.batch_split = base.batch_split;
   }
   // apply the best setting (or restore the original one on failure)
   p->cfg = base;
@@ -2241,6 +2360,8 @@ mlmc_status mlmc_autotune(mlmc_plan p, int level, int64_t count, int flags, mlmc
     p->cfg.inner_rtol = r.inner_rtol;
     p->cfg.mg_omega = r.mg_omega;
     p->cfg.z_chunk = r.z_chunk;
+    p->cfg.stencil_tile = r.stencil_tile;
+    p->cfg.batch_split = r.batch_split;
   }
   settle_graph_launches(p);
   clear_graphs(p);
@@ -2294,7 +2415,10 @@ mlmc_status mlmc_round_begin(mlmc_plan p, const int64_t* first, const int64_t* c
   for (int l = 0; l < L1; ++l)
     if (f[l] < 0 || c[l] < 0 || f[l] + c[l] > (int64_t(1) << 32)) return MLMC_ERR_INVALID;
   mlmc_status st = round_launch(p, f, c);
-  if (st != MLMC_OK) p->round_count.clear();
+  if (st != MLMC_OK) {
+    p->round_count.clear();
+    p->round_chunks.clear();
+  }
   return st;
 }
 
@@ -2345,6 +2469,7 @@ mlmc_status mlmc_round_begin_group(mlmc_plan* plans, int nplans, const int64_t* 
     p->group.clear();
     p->group_count.clear();
     p->round_count.clear();
+    p->round_chunks.clear();
     p->round_ws = (char*)p->ws;
     p->round_M = p->M;
   }

@@ -1098,7 +1098,7 @@ inline void launch_zm3(cudaStream_t s, const Grid& g, int64_t B, const T* kappa,
     using LP = LdPaired<Ld>;
     const typename LP::type lp = LP::make(ld);
     // bulk-copy staging: full-width tiles (n in 32..256), 16-byte aligned arrays
-    if (zw_mesh(g.n) && lp.aligned16() && ((uintptr_t)kappa & 15) == 0 && g.ns % 4 == 0 &&
+    if (g.zt == 0 && zw_mesh(g.n) && lp.aligned16() && ((uintptr_t)kappa & 15) == 0 && g.ns % 4 == 0 &&
         g.es % 4 == 0 && (g.zx == (int64_t)(g.n / zw_rows(g.n)) * ((g.n + 1 + g.zc - 1) / g.zc))) {
       constexpr int NA = LP::type::kArrays;
       const size_t smem = sizeof(float) * ZW_S * (NA * zw_vslot(g.n) + zw_kslot(g.n)) + 8 * ZW_S;

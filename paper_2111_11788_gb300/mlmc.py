@@ -61,6 +61,8 @@ class Config(ctypes.Structure):
         ("z_chunk", ctypes.c_int32),
         ("nested_guess", ctypes.c_int32),
         ("kle_tensor", ctypes.c_int32),
+        ("stencil_tile", ctypes.c_int32),
+        ("batch_split", ctypes.c_int32),
     ]
 
 
@@ -97,12 +99,15 @@ class TuneReport(ctypes.Structure):
     """Mirror of ``mlmc_tune_report``."""
     _fields_ = [("candidates", ctypes.c_int32), ("z_chunk", ctypes.c_int32),
                 ("inner_rtol", ctypes.c_double), ("mg_omega", ctypes.c_double),
-                ("best_ms", ctypes.c_double), ("worst_ms", ctypes.c_double)]
+                ("best_ms", ctypes.c_double), ("worst_ms", ctypes.c_double),
+                ("stencil_tile", ctypes.c_int32), ("batch_split", ctypes.c_int32)]
 
 
 TUNE_INNER_RTOL = 1
 TUNE_MG_OMEGA = 2
 TUNE_Z_CHUNK = 4
+TUNE_TILE = 8
+TUNE_BATCH = 16
 
 
 class SchedResult(ctypes.Structure):
@@ -222,7 +227,8 @@ def config(dim=2, n_levels=3, coarse_cells=16, modes_per_dim=4, sigma2=1.0, corr
            qoi="domain", solver="jacobi", box=(0.25, 0.75), rtol=1e-10, max_iter=None,
            precision="fp64", seed=0, stream_id=0, mg_omega=None, check_every=0,
            workspace_bytes=0, inner_rtol=None, inner_max_iter=None, outer_max_iter=None,
-           use_graphs=None, total_order=None, nested_guess=None, kle_tensor=None):
+           use_graphs=None, total_order=None, nested_guess=None, kle_tensor=None,
+           stencil_tile=None, batch_split=None):
     """Build a Config from plain values (defaults from mlmc_config_default)."""
     c = Config()
     lib().mlmc_config_default(ctypes.byref(c))
@@ -256,6 +262,10 @@ def config(dim=2, n_levels=3, coarse_cells=16, modes_per_dim=4, sigma2=1.0, corr
         c.nested_guess = int(nested_guess)
     if kle_tensor is not None:
         c.kle_tensor = int(kle_tensor)
+    if stencil_tile is not None:
+        c.stencil_tile = int(stencil_tile)
+    if batch_split is not None:
+        c.batch_split = int(batch_split)
     return c
 
 
@@ -383,13 +393,14 @@ class Plan:
         check(st, "mlmc_run")
         return q.value, v.value, Nout
 
-    def autotune(self, level, count, flags=7):
+    def autotune(self, level, count, flags=31):
         """mlmc_autotune: keep the fastest setting; returns the report as a dict."""
         r = TuneReport()
         check(lib().mlmc_autotune(self._h, int(level), int(count), int(flags), ctypes.byref(r)),
               "mlmc_autotune")
         return dict(candidates=r.candidates, z_chunk=r.z_chunk, inner_rtol=r.inner_rtol,
-                    mg_omega=r.mg_omega, best_ms=r.best_ms, worst_ms=r.worst_ms)
+                    mg_omega=r.mg_omega, stencil_tile=r.stencil_tile, batch_split=r.batch_split,
+                    best_ms=r.best_ms, worst_ms=r.worst_ms)
 
     def allocation(self, eps):
         """mlmc_allocation: N_l of Eq. (mlmc_num_samples) from the device level states."""

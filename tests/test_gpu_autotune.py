@@ -46,3 +46,54 @@ def test_autotune_keeps_a_candidate_and_parity(m, dim, precision, flags, n_cand)
         rf, rc = omlmc.coupled_sample(wl, 2, s)
         assert abs(qf[s] - rf) <= 1e-9 * abs(rf)
         assert abs(qc[s] - rc) <= 1e-9 * abs(rc)
+
+
+def test_autotune_tile_shape_and_batch_split(m):
+    """The 3D FP32 stencil tile shape (full-width TMA tiles or 32 x 16
+    cp.async tiles) and the batch width of rounds are tuned on a round of the
+    level; the tuned plan keeps the oracle parity."""
+    wl = small_case(3, n0=8, levels=3, m=3, solver="gmg", qoi="box", rtol=1e-11, precision="mixed")
+    cfg = m.config_from_workload(wl)
+    with m.Plan(cfg, torch.cuda.current_stream().cuda_stream) as plan:
+        rep = plan.autotune(2, 16, m.TUNE_TILE | m.TUNE_BATCH)
+        assert rep["candidates"] == 6              # 2 tiles x splits (1, 2, 4)
+        assert rep["stencil_tile"] in (0, 1) and rep["batch_split"] in (0, 2, 4)
+        qf, qc, _ = plan.sample_level(2, 0, 2)
+    for s in range(2):
+        rf, rc = omlmc.coupled_sample(wl, 2, s)
+        assert abs(qf[s] - rf) <= 1e-9 * abs(rf)
+        assert abs(qc[s] - rc) <= 1e-9 * abs(rc)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_batch_split_splits_rounds_without_changing_results(m, dim):
+    """A round whose levels are each split into batch_split batches (parallel
+    graph branches, folded in sample order) gives the same estimate, variance
+    and sample counts as one batch per level, bit for bit."""
+    if dim == 2:
+        wl = small_case(2, n0=8, levels=3, m=4, solver="gmg", precision="fp64")
+    else:
+        wl = small_case(3, n0=4, levels=3, m=3, solver="gmg", qoi="box", precision="mixed")
+    s = torch.cuda.current_stream().cuda_stream
+    out = []
+    for bw in (0, 3, 7):
+        with m.Plan(m.config_from_workload(wl, batch_split=bw), s) as plan:
+            q, v, N = plan.run(eps=1e-3, pilot=10)
+        out.append((q, v, [int(x) for x in N]))
+    assert out[1] == out[0] and out[2] == out[0]
+
+
+def test_stencil_tiles_agree(m):
+    """The two 3D FP32 stencil tile shapes compute the same per-node
+    arithmetic (their per-tile partial sums differ in rounding only): the
+    mixed-form QoIs agree within the parity tolerance."""
+    wl = small_case(3, n0=8, levels=3, m=3, solver="gmg", qoi="box", rtol=1e-11, precision="mixed")
+    s = torch.cuda.current_stream().cuda_stream
+    got = []
+    for tile in (0, 1):
+        with m.Plan(m.config_from_workload(wl, stencil_tile=tile), s) as plan:
+            qf, qc, _ = plan.sample_level(2, 0, 4)
+        got.append((qf, qc))
+    import numpy as np
+    for a, b in zip(got[0], got[1]):
+        assert np.all(np.abs(a - b) <= 1e-9 * np.abs(b))
