@@ -7,13 +7,44 @@
 // tables F[i, k] = sqrt(theta_k) f_k((i + 1/2) h), the contraction Phi xi is
 // evaluated axis by axis (sum factorisation) in FP64: for each sample a
 // small x-contraction into shared memory, then m FMAs per element and one
-// exp. The kernel is bound by the write of kappa (8 B per element).
+// exp. On GB300 the FP64 exp and FMAs bound the kernel (about 20 GB/s of
+// kappa per TFLOP/s of FP64), not the write of kappa (8 B per element).
 #include <algorithm>
+#include <cmath>
 
 #include "mlmc_internal.cuh"
 
 namespace mlmc {
 namespace {
+
+// exp in FP64 by the table-driven reduction of P. T. P. Tang ("Table-driven
+// implementation of the exponential function in IEEE floating-point
+// arithmetic", ACM TOMS 15(2), 1989), written from the mathematics:
+//   x = (64 k + j) ln2 / 64 + r,  |r| <= ln2 / 128,  0 <= j < 64,
+//   exp(x) = 2^k 2^(j/64) exp(r),  exp(r) = 1 + p(r),
+//   p(r) = r + r^2 (1/2 + r (1/6 + r (1/24 + r / 120)))
+// (the next Taylor term, r^6 / 720, is below 4e-17). ln2 / 64 is split as
+// L1 + L2 with L1 carrying 32 significant bits, so N L1 is exact for the
+// |N| < 2^21 of |x| < 2^14; 2^(j/64) comes from a table of 64 doubles made on
+// the host. About 1 ulp; |x| < 700 (the log-field of the KLE stays far inside).
+__constant__ double c_exp2_tab[64];
+constexpr double kInvLn2x64 = 92.332482616893658071;   // 64 / ln 2
+// ln 2 / 64 = 0.0108304246962491454596... as L1 (32 significant bits) + L2
+constexpr double kLn2d64Hi = 0x1.62e42fee00000p-7;     // 0.01083042469326755963265895843505859375
+constexpr double kLn2d64Lo = 2.9815858269852934627254151261796896e-12;
+
+__device__ __forceinline__ double kle_exp(double x) {
+  const double t = x * kInvLn2x64;
+  const double nf = rint(t);
+  const int N = (int)nf;
+  const double r = fma(-nf, kLn2d64Lo, fma(-nf, kLn2d64Hi, x));
+  const int j = N & 63;
+  const int k = (N - j) >> 6;
+  const double q = fma(r, fma(r, fma(r, 1.0 / 120.0, 1.0 / 24.0), 1.0 / 6.0), 0.5);
+  const double p = fma(r * r, q, r);
+  const double T = c_exp2_tab[j];
+  return fma(T, p, T) * __longlong_as_double((long long)(k + 1023) << 52);
+}
 
 // F[i * m + k] = sqrt(theta_k) f_k(x_i), x_i = (i + 1/2) / n, centred t = x - 1/2:
 // even k: cos(w t) / sqrt(1/2 + sin(w) / (2w)); odd k: sin(w t) / sqrt(1/2 - sin(w) / (2w)).
@@ -36,7 +67,10 @@ __global__ void k_kle_table(int n, int m, const double* __restrict__ omega,
   table[idx] = sqrt(theta[k]) * f;
 }
 
-constexpr int KAP_ROWS = 4;  // element rows per thread in 2D
+// Element rows per thread in 2D: a CTA covers 32 columns x 8 * KAP_ROWS rows,
+// so the x-contraction of its columns (m^2 FMAs per column) is shared by 64
+// rows of elements (m FMAs and one exp each).
+constexpr int KAP_ROWS = 8;
 
 // The sample's KLE coefficients in the full tensor layout (m^dim entries) in
 // shared memory: a copy, or under total-order truncation the kept
@@ -88,14 +122,14 @@ __global__ void __launch_bounds__(TX2* TY2)
   const int ix = x0 + threadIdx.x;
   if (ix < n) {
     double* out = kappa + (int64_t)b * es;
-#pragma unroll
+#pragma unroll 4
     for (int r = 0; r < KAP_ROWS; ++r) {
       const int rl = threadIdx.y + TY2 * r;
       const int iy = y0 + rl;
       if (iy >= n) break;
       double g = 0.0;
       for (int ky = 0; ky < m; ++ky) g = fma(s_fy[rl][ky], s_t[threadIdx.x][ky], g);
-      out[(int64_t)iy * n + ix] = exp(sqrt_sigma2 * g);
+      out[(int64_t)iy * n + ix] = kle_exp(sqrt_sigma2 * g);
     }
   }
   if (prof.acc && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) atomicAdd(prof.acc, prof.per_sample);
@@ -108,7 +142,7 @@ constexpr int K3_TY = 4;
 __global__ void __launch_bounds__(TX2* K3_TY)
     k_kappa3d(int n, int m, double sqrt_sigma2, const double* __restrict__ table,
               const double* __restrict__ xi, int M_xi, const int32_t* __restrict__ slot,
-              int64_t es, double* __restrict__ kappa, int z_chunk, Prof prof) {
+              int64_t es, double* __restrict__ kappa, Prof prof) {
   extern __shared__ double smem[];
   const int M = m * m * m;
   double* s_xi = smem;                              // M
@@ -146,9 +180,8 @@ __global__ void __launch_bounds__(TX2* K3_TY)
     const double* fz = table + iz * m;
     double g = 0.0;
     for (int kz = 0; kz < m; ++kz) g = fma(fz[kz], t2[kz], g);
-    out[((int64_t)iz * n + iy) * n + ix] = exp(sqrt_sigma2 * g);
+    out[((int64_t)iz * n + iy) * n + ix] = kle_exp(sqrt_sigma2 * g);
   }
-  (void)z_chunk;
   if (prof.acc && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) atomicAdd(prof.acc, prof.per_sample);
 }
 
@@ -192,6 +225,16 @@ __global__ void k_cast_kappa(int64_t ne, int64_t es, const double* __restrict__ 
 
 }  // namespace
 
+// 2^(j/64), j < 64, for kle_exp: set once per device (not under stream capture).
+cudaError_t init_kle_exp() {
+  static std::atomic<uint64_t> done{0};
+  return once_per_device(done, [] {
+    double tab[64];
+    for (int j = 0; j < 64; ++j) tab[j] = (double)std::exp2((long double)j / 64.0L);
+    return cudaMemcpyToSymbol(c_exp2_tab, tab, sizeof(tab));
+  });
+}
+
 cudaError_t launch_cast_kappa(cudaStream_t s, const Grid& g, const double* k64, float* k32,
                               int64_t B) {
   if (B == 0) return cudaSuccess;
@@ -218,14 +261,14 @@ cudaError_t launch_kappa(cudaStream_t s, const Grid& g, int m, double sqrt_sigma
   } else {
     const int M = m * m * m;
     const size_t smem = sizeof(double) * ((size_t)M + (size_t)TX2 * m * m);
-    static bool attr_set = false;
-    if (!attr_set) {
-      cudaFuncSetAttribute(k_kappa3d, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      attr_set = true;
-    }
+    static std::atomic<uint64_t> opted{0};
+    const cudaError_t attr = once_per_device(opted, [] {
+      return cudaFuncSetAttribute(k_kappa3d, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    });
+    if (attr != cudaSuccess) return attr;
     dim3 grid((g.n + TX2 - 1) / TX2, (g.n + K3_TY - 1) / K3_TY, (unsigned)B);
     k_kappa3d<<<grid, dim3(TX2, K3_TY), smem, s>>>(g.n, m, sqrt_sigma2, table, xi, M_xi, slot, g.es,
-                                                   kappa, g.n, p);
+                                                   kappa, p);
   }
   return cudaGetLastError();
 }

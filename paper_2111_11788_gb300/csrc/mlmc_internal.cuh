@@ -170,6 +170,8 @@ cudaError_t launch_coarsen(cudaStream_t s, const Grid& fine, const Grid& coarse,
                            const T* kf, T* kc, int64_t B, Prof p);
 
 // kappa32 = (float) kappa64, element arrays.
+// the table of the FP64 exp of the kappa kernels, once per device (before any capture)
+cudaError_t init_kle_exp();
 // kappa32 = exp(Phi xi) on the tensor cores (split BF16, FP32 accumulation); M kept modes
 cudaError_t launch_kappa32_tc(cudaStream_t s, const Grid& g, int m, double sqrt_sigma2, const double* table,
                               const double* xi, int M, const int32_t* slot, int64_t B, float* kappa32);

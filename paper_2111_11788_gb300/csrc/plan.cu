@@ -1748,6 +1748,7 @@ mlmc_status mlmc_plan_create(const mlmc_config* cfg, void* stream, mlmc_plan* ou
       cudaMemsetAsync(p->d_states, 0, sizeof(mlmc_level_state) * cfg->n_levels, p->stream) != cudaSuccess ||
       cudaMemsetAsync(p->d_prof, 0, sizeof(double) * NUM_KERNELS, p->stream) != cudaSuccess)
     return fail(MLMC_ERR_CUDA);
+  if (init_kle_exp() != cudaSuccess) return fail(MLMC_ERR_CUDA);
   p->meshes.resize(cfg->n_levels);
   for (int l = 0; l < cfg->n_levels; ++l) {
     MeshInfo& mi = p->meshes[l];

@@ -173,6 +173,84 @@ __device__ __forceinline__ T stencil_coef_res(const WinC<T>& w, T rhs) {
 template <class T>
 constexpr int kStripUnroll = sizeof(T) == 8 ? 6 : 1;
 
+// FP32 strips on paired rows: a lane takes the output rows j and j + 1 per
+// step, and their two stencils run on float2 pairs (row j in .x, row j + 1
+// in .y) with the paired FP32 instructions, so the stencil arithmetic and the
+// loop overhead per node halve; loads, shuffles and outputs stay per node.
+// The next pair's field rows and kappa rows are fetched before the current
+// pair is consumed. Same contract as stream_strip_rf (kappa form, A x).
+__device__ __forceinline__ float2 pf2(float a, float b) { return make_float2(a, b); }
+
+template <class FieldF, class FormF, class OutF>
+__device__ __forceinline__ void stream_strip_pair(const Strip& s, const float* __restrict__ kap,
+                                                  FieldF&& field, FormF&& form, OutF&& out) {
+  const int n = s.n;
+  constexpr unsigned FULL = 0xffffffffu;
+  using Raw = decltype(field(0, 0));
+  auto fetch = [&](int j) -> Raw {
+    Raw r{};
+    if (interior2(n, s.c, j)) r = field(s.c, j);
+    return r;
+  };
+  auto fld = [&](int j, const Raw& r) -> float { return interior2(n, s.c, j) ? float(form(r, s.c, j)) : 0.f; };
+  // carried from the previous pair: field rows j - 1 (a) and j (b), kappa row j - 1
+  float va = fld(s.y0 - 1, fetch(s.y0 - 1));
+  float vb = fld(s.y0, fetch(s.y0));
+  float la = __shfl_up_sync(FULL, va, 1), ra = __shfl_down_sync(FULL, va, 1);
+  float lb = __shfl_up_sync(FULL, vb, 1), rb = __shfl_down_sync(FULL, vb, 1);
+  float ka = kap_at(kap, n, s.c, s.y0 - 1);
+  float kal = __shfl_up_sync(FULL, ka, 1);
+  // in flight: field rows j + 1, j + 2 and kappa rows j, j + 1
+  Raw rc = fetch(s.y0 + 1), rd = fetch(s.y0 + 2);
+  float kb = kap_at(kap, n, s.c, s.y0), kc = kap_at(kap, n, s.c, s.y0 + 1);
+  const float2 c23 = pf2(Consts<float>::c23, Consts<float>::c23);
+  const float2 mc16 = pf2(-Consts<float>::c16, -Consts<float>::c16);
+  const float2 mc13 = pf2(-Consts<float>::c13, -Consts<float>::c13);
+  for (int j = s.y0; j < s.y1; j += 2) {
+    const float vc = fld(j + 1, rc), vd = fld(j + 2, rd);
+    const float lc = __shfl_up_sync(FULL, vc, 1), rcx = __shfl_down_sync(FULL, vc, 1);
+    const float ld = __shfl_up_sync(FULL, vd, 1), rdx = __shfl_down_sync(FULL, vd, 1);
+    const float kbl = __shfl_up_sync(FULL, kb, 1), kcl = __shfl_up_sync(FULL, kc, 1);
+    const float kb_ = kb, kc_ = kc;
+    if (j + 2 < s.y1) {   // the next pair's rows before this pair is consumed
+      rc = fetch(j + 3);
+      rd = fetch(j + 4);
+      kb = kap_at(kap, n, s.c, j + 2);
+      kc = kap_at(kap, n, s.c, j + 3);
+    }
+    if (s.out) {
+      // elements around node (c, r), r = j (.x) and j + 1 (.y)
+      const float2 ksw = pf2(kal, kbl), kse = pf2(ka, kb_), knw = pf2(kbl, kcl), kne = pf2(kb_, kc_);
+      const float2 kS = __fadd2_rn(ksw, kse), kN = __fadd2_rn(knw, kne);
+      const float2 kW = __fadd2_rn(ksw, knw), kE = __fadd2_rn(kse, kne);
+      const float2 vm = pf2(va, vb), v0 = pf2(vb, vc), vp = pf2(vc, vd);
+      const float2 lm = pf2(la, lb), l0 = pf2(lb, lc), lp = pf2(lc, ld);
+      const float2 rm = pf2(ra, rb), r0 = pf2(rb, rcx), rp = pf2(rcx, rdx);
+      float2 edge = __fmul2_rn(kE, r0);
+      edge = __ffma2_rn(kW, l0, edge);
+      edge = __ffma2_rn(kN, vp, edge);
+      edge = __ffma2_rn(kS, vm, edge);
+      float2 corner = __fmul2_rn(kne, rp);
+      corner = __ffma2_rn(knw, lp, corner);
+      corner = __ffma2_rn(kse, rm, corner);
+      corner = __ffma2_rn(ksw, lm, corner);
+      float2 y = __fmul2_rn(__fmul2_rn(c23, __fadd2_rn(kS, kN)), v0);
+      y = __ffma2_rn(mc16, edge, y);
+      y = __ffma2_rn(mc13, corner, y);
+      out(j, vb, interior2(n, s.c, j) ? y.x : 0.f);
+      if (j + 1 < s.y1) out(j + 1, vc, interior2(n, s.c, j + 1) ? y.y : 0.f);
+    }
+    va = vc;
+    la = lc;
+    ra = rcx;
+    vb = vd;
+    lb = ld;
+    rb = rdx;
+    ka = kc_;
+    kal = kcl;
+  }
+}
+
 // Streams one warp strip. The stencilled field at an interior node (c, j)
 // is form(field(c, j), c, j): field issues the node's loads (called for
 // consecutive rows j, two rows ahead of use) and form combines them when
@@ -188,6 +266,10 @@ constexpr int kStripUnroll = sizeof(T) == 8 ? 6 : 1;
 template <class T, bool C, bool R, class FieldF, class FormF, class RhsF, class OutF>
 __device__ __forceinline__ void stream_strip_rf(const Strip& s, const T* __restrict__ src, int64_t ns,
                                                 FieldF&& field, FormF&& form, RhsF&& rhs, OutF&& out) {
+  if constexpr (sizeof(T) == 4 && !C && !R) {
+    stream_strip_pair(s, src, field, form, [&](int j, float x, float ax) { out(j, x, ax, 0.f); });
+    return;
+  }
   const int n = s.n;
   using Raw = decltype(field(0, 0));
   auto fetch = [&](int j) -> Raw {
