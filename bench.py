@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--profile-level", type=int, default=None,
                     help="profiling case: only run this level's coupled batch twice, then exit")
     ap.add_argument("--profile-batch", type=int, default=64)
+    ap.add_argument("--stencil-tile", type=int, default=None,
+                    help="profile case: 3D FP32 stencil tile shape (mlmc_config.stencil_tile)")
     ap.add_argument("--profile-kle", action="store_true",
                     help="profiling case: the KLE contraction of the finest level's batch "
                          "(--profile-batch samples), FP64 and tensor-core kernels, twice each")
@@ -773,7 +775,8 @@ def profile_case(args):
     build_library()
     import paper_2111_11788_gb300.mlmc as m
     wl = workload(args.workload)
-    cfg = m.config_from_workload(wl, precision=args.form, use_graphs=0 if args.no_graphs else 1)
+    cfg = m.config_from_workload(wl, precision=args.form, use_graphs=0 if args.no_graphs else 1,
+                                 stencil_tile=args.stencil_tile)
     with m.Plan(cfg, torch.cuda.current_stream().cuda_stream) as plan:
         for rep in range(2):
             plan.sample_level(args.profile_level, rep * args.profile_batch, args.profile_batch,

@@ -102,8 +102,11 @@ typedef struct mlmc_config {
   int32_t stencil_tile;    /* 3D FP32 stencils: 0 (default) = full-width tiles
                               staged by one TMA bulk copy per plane and array
                               where the mesh allows it (32..256 cells per side),
-                              1 = 32 x 16 column tiles staged by cp.async. Same
-                              results either way; set by mlmc_autotune */
+                              four node rows per thread; 2 = the same tiles with
+                              two rows per thread; 1 = 32 x 16 column tiles
+                              staged by cp.async. Same per-node arithmetic (the
+                              per-tile partial sums differ in rounding only);
+                              set by mlmc_autotune */
   int32_t batch_split;     /* rounds: each level's batch of coupled samples is
                               split into this many near-equal batches (at most
                               count of them), solved side by side as parallel

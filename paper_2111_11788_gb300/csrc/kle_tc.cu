@@ -12,15 +12,16 @@
 // 16 significant bits per product, far below the inner solve's tolerance.
 // The FP64 kappa of the outer residual is not made here.
 //
-// A CTA (4 warps) owns N_t samples (N_t a multiple of 16, <= 256) and walks
+// A CTA (16 warps) owns N_t samples (N_t a multiple of 16, <= 256) and walks
 // 128-element tiles of the mesh. Xi of its samples stays in shared memory for
-// the whole launch; Phi is generated a 64-mode chunk at a time (thread r
-// makes row r of the tile) into one of two stages while the MMAs of the other
-// stage run. Shared operands use the 128-byte swizzled K-major layout (rows of
+// the whole launch; Phi is generated a 64-mode chunk at a time (four threads
+// per tile row, 16 modes each) into one of two stages while the MMAs of the
+// other stage run. Shared operands use the 128-byte swizzled K-major layout (rows of
 // 64 BF16, 8-row atoms of 1 KB); thread 0 issues tcgen05.mma (M = 128,
 // N = N_t, K = 16) and commits each stage to an mbarrier; the epilogue reads
 // the accumulators with tcgen05.ld (warp w: lanes 32w..32w+31 = elements)
-// and stores exp(G) coalesced along the elements. Waits on mbarriers are
+// and stores exp(G) coalesced along the elements (warp w reads lanes
+// 32 (w mod 4) .. and every fourth 16-column chunk starting at w / 4). Waits on mbarriers are
 // bounded: a CTA whose wait gives up counts a timeout in g_tc_timeouts, lets
 // its MMAs land (bounded), frees its tensor memory and ends.
 #include "mlmc_internal.cuh"
@@ -30,7 +31,8 @@
 namespace mlmc {
 namespace {
 
-constexpr int TC_THREADS = 128;
+constexpr int TC_THREADS = 512;
+constexpr int TC_ROW_THREADS = TC_THREADS / 128;   // threads per tile row
 constexpr int TC_TILE = 128;                       // elements per tile (MMA M)
 constexpr int TC_KC = 64;                          // modes per chunk (one 128-byte row of BF16)
 constexpr int TC_CHUNK_BYTES = TC_TILE * TC_KC * 2;  // one BF16 operand chunk of Phi: 16 KB
@@ -164,7 +166,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_kappa32_tc(TcArgs a) {
   const int b0 = blockIdx.y * a.Nt;
   const int K = a.nch * TC_KC;
   int* modes = reinterpret_cast<int*>(sm + a.off_modes);
-  float* fac = reinterpret_cast<float*>(sm + a.off_fac);          // [dim][m][128]
+  float* fac = reinterpret_cast<float*>(sm + a.off_fac);          // [dim][m][TC_TILE]
   const uint32_t bar_stage0 = base + a.off_bar, bar_acc = base + a.off_bar + 16;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + a.off_bar + 24);
   const int m = a.m;
@@ -217,8 +219,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_kappa32_tc(TcArgs a) {
   int ntile = 0;       // tiles finished by this CTA
   bool failed = false;
   for (int64_t tile = blockIdx.x; tile < tiles && !failed; tile += gridDim.x) {
-    // this thread's element (row tid of the tile) and its per-axis factors
-    const int64_t e = tile * TC_TILE + tid;
+    // this thread's element (row tid mod 128 of the tile) and the per-axis
+    // factors of its row (the row's four threads write every fourth mode;
+    // the previous tile's reads of fac ended at its closing barrier)
+    const int row = tid & (TC_TILE - 1), quarter = tid >> 7;
+    const int64_t e = tile * TC_TILE + row;
     const bool real = e < a.ne;
     int ix = 0, iy = 0, iz = 0;
     if (real) {
@@ -227,11 +232,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_kappa32_tc(TcArgs a) {
       iy = (int)(q % a.n);
       iz = a.dim == 3 ? (int)(q / a.n) : 0;
     }
-    for (int k = 0; k < m; ++k) {
-      fac[k * TC_TILE + tid] = real ? a.sqrt_sigma2 * (float)a.table[ix * m + k] : 0.f;
-      fac[(m + k) * TC_TILE + tid] = real ? (float)a.table[iy * m + k] : 0.f;
-      if (a.dim == 3) fac[(2 * m + k) * TC_TILE + tid] = real ? (float)a.table[iz * m + k] : 0.f;
+    for (int k = quarter; k < m; k += TC_ROW_THREADS) {
+      fac[k * TC_TILE + row] = real ? a.sqrt_sigma2 * (float)a.table[ix * m + k] : 0.f;
+      fac[(m + k) * TC_TILE + row] = real ? (float)a.table[iy * m + k] : 0.f;
+      if (a.dim == 3) fac[(2 * m + k) * TC_TILE + row] = real ? (float)a.table[iz * m + k] : 0.f;
     }
+    __syncthreads();
     for (int c = 0; c < a.nch; ++c, ++gc) {
       const int s = gc & 1;
       // the stage's previous MMAs (chunk gc - 2) must have read it
@@ -240,19 +246,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_kappa32_tc(TcArgs a) {
         unsigned char* ah = sm + a.off_a + s * 2 * TC_CHUNK_BYTES;
         unsigned char* al = ah + TC_CHUNK_BYTES;
 #pragma unroll 1
-        for (int j = 0; j < TC_KC / 8; ++j) {   // 8 modes (16 bytes) at a time
+        for (int jj = 0; jj < TC_KC / 8 / TC_ROW_THREADS; ++jj) {   // 8 modes (16 bytes) at a time
+          const int j = quarter * (TC_KC / 8 / TC_ROW_THREADS) + jj;
           __align__(16) __nv_bfloat16 hv[8], lv[8];
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
             const int code = modes[c * TC_KC + j * 8 + q];
             float v = 0.f;
             if (code >= 0) {
-              v = fac[(code & 0xFF) * TC_TILE + tid] * fac[(m + ((code >> 8) & 0xFF)) * TC_TILE + tid];
-              if (a.dim == 3) v *= fac[(2 * m + (code >> 16)) * TC_TILE + tid];
+              v = fac[(code & 0xFF) * TC_TILE + row] * fac[(m + ((code >> 8) & 0xFF)) * TC_TILE + row];
+              if (a.dim == 3) v *= fac[(2 * m + (code >> 16)) * TC_TILE + row];
             }
             split_bf16(v, hv[q], lv[q]);
           }
-          const uint32_t o = sw128_off(tid, j * 8);
+          const uint32_t o = sw128_off(row, j * 8);
           *reinterpret_cast<uint4*>(ah + o) = *reinterpret_cast<const uint4*>(hv);
           *reinterpret_cast<uint4*>(al + o) = *reinterpret_cast<const uint4*>(lv);
         }
@@ -284,16 +291,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_kappa32_tc(TcArgs a) {
     const bool ok = tc_mbar_wait(bar_acc, (unsigned)(ntile & 1));
     tc_fence_after();
     if (ok) {
-      const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-      for (int c0 = 0; c0 < a.Nt; c0 += 16) {
+      // warp w: accumulator lanes (elements) 32 (w mod 4) .., column chunks w / 4, w / 4 + 4, ..
+      const int lq = warp & 3, cg = warp >> 2;
+      const int64_t ee = tile * TC_TILE + 32 * lq + (tid & 31);
+      const uint32_t lane_addr = tmem + ((uint32_t)(lq * 32) << 16);
+      for (int c0 = 16 * cg; c0 < a.Nt; c0 += 16 * TC_ROW_THREADS) {
         uint32_t r[16];
         tmem_ld16(lane_addr + (uint32_t)c0, r);
         tmem_ld_wait();
-        if (real) {
+        if (ee < a.ne) {
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int64_t bb = b0 + c0 + j;
-            if (bb < a.B) a.kappa32[bb * a.es + e] = __expf(__uint_as_float(r[j]));
+            if (bb < a.B) a.kappa32[bb * a.es + ee] = __expf(__uint_as_float(r[j]));
           }
         }
       }

@@ -358,7 +358,7 @@ std::vector<int32_t> coef_slots(const mlmc_config* c) {
 
 mlmc_status validate(const mlmc_config* c) {
   if (c && (c->total_order < -1 || c->z_chunk < 0 || (c->nested_guess != 0 && c->nested_guess != 1) ||
-            (c->kle_tensor != 0 && c->kle_tensor != 1) || (c->stencil_tile != 0 && c->stencil_tile != 1) ||
+            (c->kle_tensor != 0 && c->kle_tensor != 1) || (c->stencil_tile < 0 || c->stencil_tile > 2) ||
             c->batch_split < 0 || c->batch_split > 64))
     return MLMC_ERR_INVALID;
   if (!c) return MLMC_ERR_INVALID;
@@ -2248,7 +2248,7 @@ mlmc_status mlmc_autotune(mlmc_plan p, int level, int64_t count, int flags, mlmc
   std::vector<int> zcs = {p->cfg.z_chunk};
   if (p->cfg.dim == 3 && (flags & MLMC_TUNE_Z_CHUNK)) zcs = {0, 24, 32, 64};
   std::vector<int> tiles = {p->cfg.stencil_tile};
-  if (p->cfg.dim == 3 && mixed && (flags & MLMC_TUNE_TILE)) tiles = {0, 1};
+  if (p->cfg.dim == 3 && mixed && (flags & MLMC_TUNE_TILE)) tiles = {0, 1, 2};
   std::vector<int> widths = {p->cfg.batch_split};
   const bool tune_split = (flags & MLMC_TUNE_BATCH) && graphs_on(p);
   if (tune_split) {

@@ -177,44 +177,41 @@ constexpr int kStripUnroll = sizeof(T) == 8 ? 6 : 1;
 // step, and their two stencils run on float2 pairs (row j in .x, row j + 1
 // in .y) with the paired FP32 instructions, so the stencil arithmetic and the
 // loop overhead per node halve; loads, shuffles and outputs stay per node.
-// The next pair's field rows and kappa rows are fetched before the current
-// pair is consumed. Same contract as stream_strip_rf (kappa form, A x).
+// The field comes in row pairs (y0 - 1 + 2p, y0 + 2p): fetch2(j) issues the
+// loads of rows j and j + 1 and form2(raw, j) turns them into the two field
+// values (0 outside the interior), called once per pair in increasing j, one
+// pair after its fetch (so form2 may carry state from pair to pair). The
+// next pair's field rows and kappa rows are fetched before the current pair
+// is consumed. out(j, x, A x) as in stream_strip_rf (kappa form).
 __device__ __forceinline__ float2 pf2(float a, float b) { return make_float2(a, b); }
 
-template <class FieldF, class FormF, class OutF>
+template <class Fetch2F, class Form2F, class OutF>
 __device__ __forceinline__ void stream_strip_pair(const Strip& s, const float* __restrict__ kap,
-                                                  FieldF&& field, FormF&& form, OutF&& out) {
+                                                  Fetch2F&& fetch2, Form2F&& form2, OutF&& out) {
   const int n = s.n;
   constexpr unsigned FULL = 0xffffffffu;
-  using Raw = decltype(field(0, 0));
-  auto fetch = [&](int j) -> Raw {
-    Raw r{};
-    if (interior2(n, s.c, j)) r = field(s.c, j);
-    return r;
-  };
-  auto fld = [&](int j, const Raw& r) -> float { return interior2(n, s.c, j) ? float(form(r, s.c, j)) : 0.f; };
   // carried from the previous pair: field rows j - 1 (a) and j (b), kappa row j - 1
-  float va = fld(s.y0 - 1, fetch(s.y0 - 1));
-  float vb = fld(s.y0, fetch(s.y0));
+  const float2 vab = form2(fetch2(s.y0 - 1), s.y0 - 1);
+  float va = vab.x, vb = vab.y;
   float la = __shfl_up_sync(FULL, va, 1), ra = __shfl_down_sync(FULL, va, 1);
   float lb = __shfl_up_sync(FULL, vb, 1), rb = __shfl_down_sync(FULL, vb, 1);
   float ka = kap_at(kap, n, s.c, s.y0 - 1);
   float kal = __shfl_up_sync(FULL, ka, 1);
   // in flight: field rows j + 1, j + 2 and kappa rows j, j + 1
-  Raw rc = fetch(s.y0 + 1), rd = fetch(s.y0 + 2);
+  auto rcd = fetch2(s.y0 + 1);
   float kb = kap_at(kap, n, s.c, s.y0), kc = kap_at(kap, n, s.c, s.y0 + 1);
   const float2 c23 = pf2(Consts<float>::c23, Consts<float>::c23);
   const float2 mc16 = pf2(-Consts<float>::c16, -Consts<float>::c16);
   const float2 mc13 = pf2(-Consts<float>::c13, -Consts<float>::c13);
   for (int j = s.y0; j < s.y1; j += 2) {
-    const float vc = fld(j + 1, rc), vd = fld(j + 2, rd);
+    const float2 vcd = form2(rcd, j + 1);
+    const float vc = vcd.x, vd = vcd.y;
     const float lc = __shfl_up_sync(FULL, vc, 1), rcx = __shfl_down_sync(FULL, vc, 1);
     const float ld = __shfl_up_sync(FULL, vd, 1), rdx = __shfl_down_sync(FULL, vd, 1);
     const float kbl = __shfl_up_sync(FULL, kb, 1), kcl = __shfl_up_sync(FULL, kc, 1);
     const float kb_ = kb, kc_ = kc;
     if (j + 2 < s.y1) {   // the next pair's rows before this pair is consumed
-      rc = fetch(j + 3);
-      rd = fetch(j + 4);
+      rcd = fetch2(j + 3);
       kb = kap_at(kap, n, s.c, j + 2);
       kc = kap_at(kap, n, s.c, j + 3);
     }
@@ -251,6 +248,26 @@ __device__ __forceinline__ void stream_strip_pair(const Strip& s, const float* _
   }
 }
 
+// Per-row fields (field issues a node's loads, form combines them) on paired rows.
+template <class FieldF, class FormF, class OutF>
+__device__ __forceinline__ void stream_strip_pair_rows(const Strip& s, const float* __restrict__ kap,
+                                                       FieldF&& field, FormF&& form, OutF&& out) {
+  const int n = s.n;
+  using Raw = decltype(field(0, 0));
+  struct Raw2 {
+    Raw a, b;
+  };
+  auto fetch = [&](int j) -> Raw {
+    Raw r{};
+    if (interior2(n, s.c, j)) r = field(s.c, j);
+    return r;
+  };
+  auto fld = [&](int j, const Raw& r) -> float { return interior2(n, s.c, j) ? float(form(r, s.c, j)) : 0.f; };
+  stream_strip_pair(
+      s, kap, [&](int j) { return Raw2{fetch(j), fetch(j + 1)}; },
+      [&](const Raw2& r, int j) { return pf2(fld(j, r.a), fld(j + 1, r.b)); }, out);
+}
+
 // Streams one warp strip. The stencilled field at an interior node (c, j)
 // is form(field(c, j), c, j): field issues the node's loads (called for
 // consecutive rows j, two rows ahead of use) and form combines them when
@@ -267,7 +284,7 @@ template <class T, bool C, bool R, class FieldF, class FormF, class RhsF, class 
 __device__ __forceinline__ void stream_strip_rf(const Strip& s, const T* __restrict__ src, int64_t ns,
                                                 FieldF&& field, FormF&& form, RhsF&& rhs, OutF&& out) {
   if constexpr (sizeof(T) == 4 && !C && !R) {
-    stream_strip_pair(s, src, field, form, [&](int j, float x, float ax) { out(j, x, ax, 0.f); });
+    stream_strip_pair_rows(s, src, field, form, [&](int j, float x, float ax) { out(j, x, ax, 0.f); });
     return;
   }
   const int n = s.n;

@@ -779,11 +779,12 @@ __global__ void __launch_bounds__(ZTHREADS, 2) k_zm3f(Grid g, const float* __res
 // k_zm3w is k_zm3f with its planes staged by the copy engine instead of by
 // per-element cp.async, for the meshes with n in {32, 64, 128, 256}: a CTA
 // covers the full width of the mesh (n threads across x, one column each)
-// and R = 512 / n node rows (two per thread), so the CTAs per sample are
-// those of the 32 x 16 tiles and the halo slab of a plane (rows
-// ty0 - 1 .. ty0 + R, every column) is one contiguous range of a node array;
-// the kappa slab (rows ty0 - 1 .. ty0 + R - 1) is one contiguous range of an
-// element array. Each plane of each array is then ONE asynchronous bulk copy
+// and R = 256 RT / n node rows, RT rows per thread (RT = 2: the CTAs per
+// sample are those of the 32 x 16 tiles; RT = 4: half as many, each
+// covering two of them), so the halo slab of a plane (rows ty0 - 1 ..
+// ty0 + R, every column) is one contiguous range of a node array; the kappa
+// slab (rows ty0 - 1 .. ty0 + R - 1) is one contiguous range of an element
+// array. Each plane of each array is then ONE asynchronous bulk copy
 // (cp.async.bulk, global -> shared, completing on the slot's mbarrier),
 // issued by one thread: no per-element address, predicate or register work.
 // Node rows have an odd pitch n + 1, so a slab starts sh = (offset mod 4)
@@ -793,17 +794,22 @@ __global__ void __launch_bounds__(ZTHREADS, 2) k_zm3f(Grid g, const float* __res
 // Values that feed only boundary outputs (row -1, column -1, the kappa halo
 // and the layers -1 and n) may be stale; planes 0 and n are not copied, and
 // the boundary nodes of the field (rows, columns and planes 0 and n) are
-// read as 0 by the threads next to them, whatever the array holds there. Waits are bounded: a wait that gives up counts a
-// timeout in g_zt_timeouts (read by the host at its sync points), lets the
-// copies still in flight land (bounded again) and ends the CTA.
+// read as 0 by the threads next to them, whatever the array holds there.
+// A thread's RT rows are RT / 2 float2 pairs of consecutive rows. Waits are
+// bounded: a wait that gives up counts a timeout in g_zt_timeouts (read by
+// the host at its sync points), lets the copies still in flight land
+// (bounded again) and ends the CTA.
 constexpr int ZW_S = 4;                             // ring slots, ZW_S - 1 planes in flight
 constexpr int ZW_WAIT_TRIES = 1 << 22;              // bounded waits: tries and SM cycles (~2 s)
 constexpr long long ZW_WAIT_CYCLES = 1ll << 32;
 
-// slot sizes (floats) of a node slab and of a kappa slab for cells per side n
-__host__ __device__ constexpr int zw_rows(int n) { return 512 / n; }
-__host__ __device__ constexpr int zw_vslot(int n) { return (12 + (zw_rows(n) + 2) * (n + 1) + 3) / 4 * 4; }
-__host__ __device__ constexpr int zw_kslot(int n) { return (8 + (zw_rows(n) + 1) * n + 3) / 4 * 4; }
+// rows per CTA and slot sizes (floats) of a node slab and of a kappa slab
+// for cells per side n and rows per thread rt
+__host__ __device__ constexpr int zw_rows(int n, int rt) { return 256 * rt / n; }
+__host__ __device__ constexpr int zw_vslot(int n, int rt) {
+  return (12 + (zw_rows(n, rt) + 2) * (n + 1) + 3) / 4 * 4;
+}
+__host__ __device__ constexpr int zw_kslot(int n, int rt) { return (8 + (zw_rows(n, rt) + 1) * n + 3) / 4 * 4; }
 inline bool zw_mesh(int n) { return n == 32 || n == 64 || n == 128 || n == 256; }
 
 __device__ unsigned int g_zt_timeouts;
@@ -848,17 +854,19 @@ __device__ __forceinline__ void fence_mbar_init() {
   asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
 }
 
-template <class Ld, class Epi>
-__global__ void __launch_bounds__(ZTHREADS, 3) k_zm3w(Grid g, const float* __restrict__ Kap, Ld ld,
-                                                      const int32_t* __restrict__ active, Epi epi,
-                                                      double* __restrict__ part, Prof prof) {
+template <class Ld, class Epi, int RT>
+__global__ void __launch_bounds__(ZTHREADS, RT == 2 ? 3 : 2) k_zm3w(Grid g, const float* __restrict__ Kap, Ld ld,
+                                                                   const int32_t* __restrict__ active, Epi epi,
+                                                                   double* __restrict__ part, Prof prof) {
   static_assert(!Epi::kRes, "the FP32 z-march hands A x to its epilogues");
+  static_assert(RT == 2 || RT == 4, "two or four rows per thread");
   constexpr int NA = Ld::kArrays;
+  constexpr int NP = RT / 2;   // float2 row pairs per thread
   const int64_t b = blockIdx.y;
   if (active && !active[b]) return;
   extern __shared__ __align__(16) float zw_smem[];
   const int n = g.n, N1 = n + 1, P = N1 * N1, KPn = n * n;
-  const int R = zw_rows(n), VS = zw_vslot(n), KS = zw_kslot(n), SS = NA * VS + KS;
+  const int R = zw_rows(n, RT), VS = zw_vslot(n, RT), KS = zw_kslot(n, RT), SS = NA * VS + KS;
   float* ring = zw_smem;                                              // ZW_S slots of SS floats
   unsigned long long* sbar = reinterpret_cast<unsigned long long*>(zw_smem + ZW_S * SS);
   __shared__ double s_w[ZTHREADS / 32];
@@ -922,34 +930,42 @@ __global__ void __launch_bounds__(ZTHREADS, 3) k_zm3w(Grid g, const float* __res
     }
 
   const int i = threadIdx.x;
-  const int jr[2] = {ty0 + 2 * (int)threadIdx.y, ty0 + 2 * (int)threadIdx.y + 1};
-  bool cint[2], ey[2];
-  int ocol[2];
+  const int jr0 = ty0 + RT * (int)threadIdx.y;   // this thread's rows jr0 .. jr0 + RT - 1
+  bool cint[RT], ey[RT];
+  int ocol[RT];
 #pragma unroll
-  for (int r = 0; r < 2; ++r) {
-    cint[r] = i >= 1 && i < n && jr[r] >= 1 && jr[r] < n;
-    ey[r] = jr[r] == n - 1;
-    ocol[r] = jr[r] * N1 + i;
+  for (int r = 0; r < RT; ++r) {
+    cint[r] = i >= 1 && i < n && jr0 + r >= 1 && jr0 + r < n;
+    ey[r] = jr0 + r == n - 1;
+    ocol[r] = (jr0 + r) * N1 + i;
   }
   const bool ex = i == n - 1;
   // field boundary nodes next to this thread's stencils (columns i - 1 .. i + 1,
-  // rows jr[0] - 1 .. jr[1] + 1) read as 0
-  bool cok[3], rok[4];
+  // rows jr0 - 1 .. jr0 + RT) read as 0
+  bool cok[3], rok[RT + 2];
 #pragma unroll
   for (int dx = 0; dx < 3; ++dx) cok[dx] = i - 1 + dx >= 1 && i - 1 + dx <= n - 1;
 #pragma unroll
-  for (int r4 = 0; r4 < 4; ++r4) rok[r4] = jr[0] - 1 + r4 >= 1 && jr[0] - 1 + r4 <= n - 1;
-  const bool edge = !(cok[0] && cok[2] && rok[0] && rok[3]);
+  for (int r = 0; r < RT + 2; ++r) rok[r] = jr0 - 1 + r >= 1 && jr0 - 1 + r <= n - 1;
+  const bool edge = !(cok[0] && cok[2] && rok[0] && rok[RT + 1]);
   const float c3s = (float)g.c3, c12s = (float)g.c12;
   const float2 c3 = make_float2(c3s, c3s), mc12 = make_float2(-c12s, -c12s);
   const float2 z2 = make_float2(0.f, 0.f);
-  float2 U = z2, D = z2, Nn = z2, vc = z2;
-  float2 kb[2][2] = {{z2, z2}, {z2, z2}};
-  float2 Xb[2] = {z2, z2}, Yb[2] = {z2, z2}, Sb = z2;
-  typename Epi::Pre pre[2];
+  // per row pair q (rows jr0 + 2q, jr0 + 2q + 1), as in k_zm3f: U unscaled
+  // couplings and D diagonal part of the output of plane p - 1, N couplings
+  // of the output of plane p with plane p - 1, the kappa pair sums of the
+  // layer below (X along x, Y along y, S of the 4 elements)
+  float2 U[NP], D[NP], Nn[NP], vc[NP], kb[NP][2][2], Xb[NP][2], Yb[NP][2], Sb[NP];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    U[q] = D[q] = Nn[q] = vc[q] = Sb[q] = z2;
+    kb[q][0][0] = kb[q][0][1] = kb[q][1][0] = kb[q][1][1] = z2;
+    Xb[q][0] = Xb[q][1] = Yb[q][0] = Yb[q][1] = z2;
+  }
+  typename Epi::Pre pre[RT];
   float dot = 0.0f;
-  const int vrow = 4 + 2 * (int)threadIdx.y * N1 + i - 1;    // + OFF: row jr[0] - 1, column i - 1
-  const int krow = 4 + 2 * (int)threadIdx.y * n + i - 1;     // row jr[0] - 1, element i - 1
+  const int vrow = 4 + RT * (int)threadIdx.y * N1 + i - 1;    // + OFF: row jr0 - 1, column i - 1
+  const int krow = 4 + RT * (int)threadIdx.y * n + i - 1;     // row jr0 - 1, element i - 1
   int st = 0;
   unsigned par = 0;    // phase parity of each slot's next completion
   bool timed_out = false;
@@ -975,96 +991,100 @@ __global__ void __launch_bounds__(ZTHREADS, 3) k_zm3w(Grid g, const float* __res
       issue(p + ZW_S - 1, sn);
       pend |= 1u << sn;
     }
-    typename Epi::Pre nxt[2];
+    typename Epi::Pre nxt[RT];
 #pragma unroll
-    for (int r = 0; r < 2; ++r)
+    for (int r = 0; r < RT; ++r)
       if (cint[r] && p >= z0 && p < z1 && p >= 1 && p < n) nxt[r] = epi.load(p * P + ocol[r]);
     const float* svb = slot + voff(p) + vrow;
     const float* skb = slot + NA * VS + krow;
-    float s4[4][3], kv[3][2];
+    float sv[RT + 2][3], kv[RT + 1][2];
 #pragma unroll
-    for (int r4 = 0; r4 < 4; ++r4)
+    for (int r = 0; r < RT + 2; ++r)
 #pragma unroll
-      for (int dx = 0; dx < 3; ++dx) s4[r4][dx] = svb[r4 * N1 + dx];
+      for (int dx = 0; dx < 3; ++dx) sv[r][dx] = svb[r * N1 + dx];
 #pragma unroll
-    for (int r3 = 0; r3 < 3; ++r3)
+    for (int r = 0; r < RT + 1; ++r)
 #pragma unroll
-      for (int a = 0; a < 2; ++a) kv[r3][a] = skb[r3 * n + a];
+      for (int a = 0; a < 2; ++a) kv[r][a] = skb[r * n + a];
     if (p <= 0 || p >= n) {
 #pragma unroll
-      for (int r4 = 0; r4 < 4; ++r4)
+      for (int r = 0; r < RT + 2; ++r)
 #pragma unroll
-        for (int dx = 0; dx < 3; ++dx) s4[r4][dx] = 0.f;
+        for (int dx = 0; dx < 3; ++dx) sv[r][dx] = 0.f;
     } else if (edge) {
 #pragma unroll
-      for (int r4 = 0; r4 < 4; ++r4)
+      for (int r = 0; r < RT + 2; ++r)
 #pragma unroll
         for (int dx = 0; dx < 3; ++dx)
-          if (!rok[r4] || !cok[dx]) s4[r4][dx] = 0.f;
+          if (!rok[r] || !cok[dx]) sv[r][dx] = 0.f;
     }
-    float2 v[3][3], ka[2][2];
-#pragma unroll
-    for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-      for (int dx = 0; dx < 3; ++dx) v[dy][dx] = make_float2(s4[dy][dx], s4[dy + 1][dx]);
-#pragma unroll
-    for (int bq = 0; bq < 2; ++bq)
-#pragma unroll
-      for (int a = 0; a < 2; ++a) ka[bq][a] = make_float2(kv[bq][a], kv[bq + 1][a]);
-    float2 Xa[2], Ya[2];
-    Xa[0] = add2(ka[0][0], ka[0][1]);
-    Xa[1] = add2(ka[1][0], ka[1][1]);
-    Ya[0] = add2(ka[0][0], ka[1][0]);
-    Ya[1] = add2(ka[0][1], ka[1][1]);
-    const float2 Sa = add2(Xa[0], Xa[1]);
-    // outputs of plane p - 1 are complete: couplings with plane p across layer p - 1
-    float2 u = fma2(Yb[0], v[1][0], U);
-    u = fma2(Yb[1], v[1][2], u);
-    u = fma2(Xb[0], v[0][1], u);
-    u = fma2(Xb[1], v[2][1], u);
-    u = fma2(kb[0][0], v[0][0], u);
-    u = fma2(kb[0][1], v[0][2], u);
-    u = fma2(kb[1][0], v[2][0], u);
-    u = fma2(kb[1][1], v[2][2], u);
-    const float2 done = fma2(mc12, u, mul2(c3, D));
     const int m = p - 1;
-    if (m >= z0) {
 #pragma unroll
-      for (int r = 0; r < 2; ++r) {
-        const int o = m * P + ocol[r];
-        dot += epi(o, cint[r] && m >= 1 && m < n, r ? done.y : done.x, r ? vc.y : vc.x, pre[r]);
-        if (ex) epi.zero(o + 1);
-        if (ey[r]) epi.zero(o + N1);
-        if (ex && ey[r]) epi.zero(o + N1 + 1);
+    for (int q = 0; q < NP; ++q) {
+      float2 v[3][3], ka[2][2];
+#pragma unroll
+      for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) v[dy][dx] = make_float2(sv[2 * q + dy][dx], sv[2 * q + dy + 1][dx]);
+#pragma unroll
+      for (int bq = 0; bq < 2; ++bq)
+#pragma unroll
+        for (int a = 0; a < 2; ++a) ka[bq][a] = make_float2(kv[2 * q + bq][a], kv[2 * q + bq + 1][a]);
+      float2 Xa[2], Ya[2];
+      Xa[0] = add2(ka[0][0], ka[0][1]);
+      Xa[1] = add2(ka[1][0], ka[1][1]);
+      Ya[0] = add2(ka[0][0], ka[1][0]);
+      Ya[1] = add2(ka[0][1], ka[1][1]);
+      const float2 Sa = add2(Xa[0], Xa[1]);
+      // outputs of plane p - 1 are complete: couplings with plane p across layer p - 1
+      float2 u = fma2(Yb[q][0], v[1][0], U[q]);
+      u = fma2(Yb[q][1], v[1][2], u);
+      u = fma2(Xb[q][0], v[0][1], u);
+      u = fma2(Xb[q][1], v[2][1], u);
+      u = fma2(kb[q][0][0], v[0][0], u);
+      u = fma2(kb[q][0][1], v[0][2], u);
+      u = fma2(kb[q][1][0], v[2][0], u);
+      u = fma2(kb[q][1][1], v[2][2], u);
+      const float2 done = fma2(mc12, u, mul2(c3, D[q]));
+      if (m >= z0) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int r = 2 * q + h;
+          const int o = m * P + ocol[r];
+          dot += epi(o, cint[r] && m >= 1 && m < n, h ? done.y : done.x, h ? vc[q].y : vc[q].x, pre[r]);
+          if (ex) epi.zero(o + 1);
+          if (ey[r]) epi.zero(o + N1);
+          if (ex && ey[r]) epi.zero(o + N1 + 1);
+        }
       }
+      // output p: couplings with plane p - 1 and the in-plane diagonal edges
+      u = fma2(add2(kb[q][0][0], ka[0][0]), v[0][0], Nn[q]);
+      u = fma2(add2(kb[q][0][1], ka[0][1]), v[0][2], u);
+      u = fma2(add2(kb[q][1][0], ka[1][0]), v[2][0], u);
+      U[q] = fma2(add2(kb[q][1][1], ka[1][1]), v[2][2], u);
+      D[q] = mul2(add2(Sb[q], Sa), v[1][1]);
+      // output p + 1: couplings with plane p across layer p
+      u = mul2(Ya[0], v[1][0]);
+      u = fma2(Ya[1], v[1][2], u);
+      u = fma2(Xa[0], v[0][1], u);
+      u = fma2(Xa[1], v[2][1], u);
+      u = fma2(ka[0][0], v[0][0], u);
+      u = fma2(ka[0][1], v[0][2], u);
+      u = fma2(ka[1][0], v[2][0], u);
+      Nn[q] = fma2(ka[1][1], v[2][2], u);
+#pragma unroll
+      for (int bq = 0; bq < 2; ++bq)
+#pragma unroll
+        for (int a = 0; a < 2; ++a) kb[q][bq][a] = ka[bq][a];
+      Xb[q][0] = Xa[0];
+      Xb[q][1] = Xa[1];
+      Yb[q][0] = Ya[0];
+      Yb[q][1] = Ya[1];
+      Sb[q] = Sa;
+      vc[q] = v[1][1];
     }
-    // output p: couplings with plane p - 1 and the in-plane diagonal edges
-    u = fma2(add2(kb[0][0], ka[0][0]), v[0][0], Nn);
-    u = fma2(add2(kb[0][1], ka[0][1]), v[0][2], u);
-    u = fma2(add2(kb[1][0], ka[1][0]), v[2][0], u);
-    U = fma2(add2(kb[1][1], ka[1][1]), v[2][2], u);
-    D = mul2(add2(Sb, Sa), v[1][1]);
-    // output p + 1: couplings with plane p across layer p
-    u = mul2(Ya[0], v[1][0]);
-    u = fma2(Ya[1], v[1][2], u);
-    u = fma2(Xa[0], v[0][1], u);
-    u = fma2(Xa[1], v[2][1], u);
-    u = fma2(ka[0][0], v[0][0], u);
-    u = fma2(ka[0][1], v[0][2], u);
-    u = fma2(ka[1][0], v[2][0], u);
-    Nn = fma2(ka[1][1], v[2][2], u);
 #pragma unroll
-    for (int bq = 0; bq < 2; ++bq)
-#pragma unroll
-      for (int a = 0; a < 2; ++a) kb[bq][a] = ka[bq][a];
-    Xb[0] = Xa[0];
-    Xb[1] = Xa[1];
-    Yb[0] = Ya[0];
-    Yb[1] = Ya[1];
-    Sb = Sa;
-    vc = v[1][1];
-    pre[0] = nxt[0];
-    pre[1] = nxt[1];
+    for (int r = 0; r < RT; ++r) pre[r] = nxt[r];
     st = (st + 1) % ZW_S;
   }
   if (timed_out) {
@@ -1075,6 +1095,8 @@ __global__ void __launch_bounds__(ZTHREADS, 3) k_zm3w(Grid g, const float* __res
     return;
   }
   if (part) {
+    // the partial sits where the first 32 x 16 tile of this CTA's rows puts
+    // it; the other tiles it covers (RT = 4) get 0
     double v = warp_sum3((double)dot);
     if ((tid & 31) == 0) s_w[tid >> 5] = v;
     __syncthreads();
@@ -1082,7 +1104,11 @@ __global__ void __launch_bounds__(ZTHREADS, 3) k_zm3w(Grid g, const float* __res
       double r = 0.0;
 #pragma unroll
       for (int w = 0; w < ZTHREADS / 32; ++w) r += s_w[w];
-      part[(int64_t)blockIdx.y * g.tiles_s + blockIdx.x] = r;
+      const int R2 = zw_rows(n, 2);
+      double* pt = part + (int64_t)blockIdx.y * g.tiles_s + (int64_t)zq * (n / R2) + ty0 / R2;
+      pt[0] = r;
+#pragma unroll
+      for (int k = 1; k < NP; ++k) pt[k] = 0.0;
     }
   }
   prof_tick3(prof);
@@ -1097,13 +1123,28 @@ inline void launch_zm3(cudaStream_t s, const Grid& g, int64_t B, const T* kappa,
   if constexpr (std::is_same<T, float>::value) {
     using LP = LdPaired<Ld>;
     const typename LP::type lp = LP::make(ld);
-    // bulk-copy staging: full-width tiles (n in 32..256), 16-byte aligned arrays
-    if (g.zt == 0 && zw_mesh(g.n) && lp.aligned16() && ((uintptr_t)kappa & 15) == 0 && g.ns % 4 == 0 &&
-        g.es % 4 == 0 && (g.zx == (int64_t)(g.n / zw_rows(g.n)) * ((g.n + 1 + g.zc - 1) / g.zc))) {
+    // bulk-copy staging: full-width tiles (n in 32..256), 16-byte aligned arrays;
+    // stencil_tile 0: four rows per thread, 2: two rows per thread
+    if (g.zt != 1 && zw_mesh(g.n) && lp.aligned16() && ((uintptr_t)kappa & 15) == 0 && g.ns % 4 == 0 &&
+        g.es % 4 == 0 && (g.zx == (int64_t)(g.n / zw_rows(g.n, 2)) * ((g.n + 1 + g.zc - 1) / g.zc))) {
       constexpr int NA = LP::type::kArrays;
-      const size_t smem = sizeof(float) * ZW_S * (NA * zw_vslot(g.n) + zw_kslot(g.n)) + 8 * ZW_S;
-      k_zm3w<typename LP::type, Epi><<<gridz(g, B), dim3(g.n, ZTHREADS / g.n, 1), smem, s>>>(
-          g, kappa, lp, active, epi, part, p);
+      // four rows per thread: up to 71 KB of ring per CTA (opt-in above 48 KB)
+      static std::atomic<uint64_t> opted{0};
+      const bool four = g.zt == 0 && once_per_device(opted, [] {
+                                       return cudaFuncSetAttribute(k_zm3w<typename LP::type, Epi, 4>,
+                                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                                   96 * 1024);
+                                     }) == cudaSuccess;
+      if (four) {
+        const size_t smem = sizeof(float) * ZW_S * (NA * zw_vslot(g.n, 4) + zw_kslot(g.n, 4)) + 8 * ZW_S;
+        k_zm3w<typename LP::type, Epi, 4><<<dim3((unsigned)(g.zx / 2), (unsigned)B, 1),
+                                           dim3(g.n, ZTHREADS / g.n, 1), smem, s>>>(g, kappa, lp, active, epi,
+                                                                                   part, p);
+      } else {
+        const size_t smem = sizeof(float) * ZW_S * (NA * zw_vslot(g.n, 2) + zw_kslot(g.n, 2)) + 8 * ZW_S;
+        k_zm3w<typename LP::type, Epi, 2><<<gridz(g, B), dim3(g.n, ZTHREADS / g.n, 1), smem, s>>>(
+            g, kappa, lp, active, epi, part, p);
+      }
     }
     else
       k_zm3f<typename LP::type, Epi><<<gridz(g, B), dim3(ZTX, ZTY / ZRY, 1), 0, s>>>(g, kappa, lp, active,

@@ -177,6 +177,17 @@ def test_kle_tensor_flag_validated_without_a_device(m):
     assert L.mlmc_kappa32(None, 0, None, 1, None) == m.MLMC_ERR_INVALID
 
 
+def test_stencil_tile_validated_without_a_device(m):
+    L = m.lib()
+    counts = (ctypes.c_int64 * 3)(1, 1, 1)
+    for tile in (0, 1, 2):
+        ok = m.config(dim=3, coarse_cells=8, precision="mixed", stencil_tile=tile)
+        assert L.mlmc_round_bytes(ctypes.byref(ok), counts) > 0
+    for tile in (-1, 3):
+        bad = m.config(dim=3, coarse_cells=8, precision="mixed", stencil_tile=tile)
+        assert L.mlmc_round_bytes(ctypes.byref(bad), counts) == -1
+
+
 def test_coef_count_matches_the_oracle_mode_sets(m):
     from oracle import kle
     for dim, mpd, order in ((2, 8, -1), (3, 7, -1), (3, 16, 14), (2, 5, 3), (3, 4, 20)):

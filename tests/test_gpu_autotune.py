@@ -49,15 +49,15 @@ def test_autotune_keeps_a_candidate_and_parity(m, dim, precision, flags, n_cand)
 
 
 def test_autotune_tile_shape_and_batch_split(m):
-    """The 3D FP32 stencil tile shape (full-width TMA tiles or 32 x 16
-    cp.async tiles) and the batch width of rounds are tuned on a round of the
+    """The 3D FP32 stencil tile shape (full-width TMA tiles with four or two
+    rows per thread, or 32 x 16 cp.async tiles) and the batch width of rounds are tuned on a round of the
     level; the tuned plan keeps the oracle parity."""
     wl = small_case(3, n0=8, levels=3, m=3, solver="gmg", qoi="box", rtol=1e-11, precision="mixed")
     cfg = m.config_from_workload(wl)
     with m.Plan(cfg, torch.cuda.current_stream().cuda_stream) as plan:
         rep = plan.autotune(2, 16, m.TUNE_TILE | m.TUNE_BATCH)
-        assert rep["candidates"] == 6              # 2 tiles x splits (1, 2, 4)
-        assert rep["stencil_tile"] in (0, 1) and rep["batch_split"] in (0, 2, 4)
+        assert rep["candidates"] == 9              # 3 tiles x splits (1, 2, 4)
+        assert rep["stencil_tile"] in (0, 1, 2) and rep["batch_split"] in (0, 2, 4)
         qf, qc, _ = plan.sample_level(2, 0, 2)
     for s in range(2):
         rf, rc = omlmc.coupled_sample(wl, 2, s)
@@ -84,16 +84,17 @@ def test_batch_split_splits_rounds_without_changing_results(m, dim):
 
 
 def test_stencil_tiles_agree(m):
-    """The two 3D FP32 stencil tile shapes compute the same per-node
+    """The three 3D FP32 stencil tile shapes compute the same per-node
     arithmetic (their per-tile partial sums differ in rounding only): the
     mixed-form QoIs agree within the parity tolerance."""
     wl = small_case(3, n0=8, levels=3, m=3, solver="gmg", qoi="box", rtol=1e-11, precision="mixed")
     s = torch.cuda.current_stream().cuda_stream
     got = []
-    for tile in (0, 1):
+    for tile in (0, 1, 2):
         with m.Plan(m.config_from_workload(wl, stencil_tile=tile), s) as plan:
             qf, qc, _ = plan.sample_level(2, 0, 4)
         got.append((qf, qc))
     import numpy as np
-    for a, b in zip(got[0], got[1]):
-        assert np.all(np.abs(a - b) <= 1e-9 * np.abs(b))
+    for other in got[1:]:
+        for a, b in zip(got[0], other):
+            assert np.all(np.abs(a - b) <= 1e-9 * np.abs(b))
