@@ -969,6 +969,7 @@ __global__ void __launch_bounds__(ZTHREADS, RT == 2 ? 3 : 2) k_zm3w(Grid g, cons
   int st = 0;
   unsigned par = 0;    // phase parity of each slot's next completion
   bool timed_out = false;
+#pragma unroll 2
   for (; p <= z1; ++p) {
     const bool landed = mbar_wait(bar0 + 8u * st, (par >> st) & 1u);
     if (landed) {
