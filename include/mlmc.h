@@ -169,7 +169,16 @@ const char* mlmc_status_str(mlmc_status s);
  * the device and zeroes the level states. `stream` is borrowed for the
  * plan's lifetime. Errors: INVALID, OOM, CUDA. */
 mlmc_status mlmc_plan_create(const mlmc_config* cfg, void* stream, mlmc_plan* out);
+/* Destroys the plan after its stream's work has completed. The plan's own
+ * workspace (not one set by mlmc_plan_set_workspace) is kept by the library
+ * for the next plan on the same device that needs at most its size (up to
+ * four blocks, the oldest freed first; a failed allocation frees this
+ * device's kept blocks and retries), so creating plans in a loop does not
+ * unmap and map gigabytes each time. */
 mlmc_status mlmc_plan_destroy(mlmc_plan plan);
+/* Returns the workspaces kept from destroyed plans to the driver (call it
+ * before handing the memory to another allocator). Errors: CUDA. */
+mlmc_status mlmc_release_cached_memory(void);
 
 /* Re-target an idle plan to a configuration of the same shape (dim,
  * n_levels, coarse_cells, modes_per_dim, solver, precision, total_order,

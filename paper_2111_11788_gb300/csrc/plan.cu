@@ -12,6 +12,7 @@
 #include <cstring>
 #include <functional>
 #include <map>
+#include <mutex>
 #include <tuple>
 #include <vector>
 
@@ -490,6 +491,85 @@ double elems_of(const Grid& g) { return (double)ipow(g.n, g.dim); }
 
 // --- workspace --------------------------------------------------------
 
+// Workspaces of destroyed plans (and the smaller block a growing plan gives
+// up) are kept for the next plan on the same device instead of going back
+// to the driver: freeing a multi-GB block unmaps its pages (milliseconds per
+// plan) and the next plan would map them again. At most kWsCacheBlocks
+// blocks are kept (the oldest is freed first); an allocation that fails
+// frees this device's cached blocks and tries once more;
+// mlmc_release_cached_memory() frees them all.
+struct WsBlock {
+  int dev;
+  void* ptr;
+  size_t bytes;
+};
+constexpr size_t kWsCacheBlocks = 4;
+std::mutex g_ws_mu;
+std::vector<WsBlock> g_ws_cache;   // oldest first
+
+// A block of at least `bytes` on the current device: the smallest cached one
+// that fits, else a new allocation. Sets *got to its size.
+cudaError_t ws_acquire(size_t bytes, void** out, size_t* got) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  {
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    int best = -1;
+    for (int k = 0; k < (int)g_ws_cache.size(); ++k) {
+      const WsBlock& w = g_ws_cache[k];
+      if (w.dev == dev && w.bytes >= bytes && (best < 0 || w.bytes < g_ws_cache[best].bytes)) best = k;
+    }
+    if (best >= 0) {
+      *out = g_ws_cache[best].ptr;
+      *got = g_ws_cache[best].bytes;
+      g_ws_cache.erase(g_ws_cache.begin() + best);
+      return cudaSuccess;
+    }
+  }
+  e = cudaMalloc(out, bytes);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    std::vector<void*> mine;
+    {
+      std::lock_guard<std::mutex> lk(g_ws_mu);
+      for (auto it = g_ws_cache.begin(); it != g_ws_cache.end();) {
+        if (it->dev == dev) {
+          mine.push_back(it->ptr);
+          it = g_ws_cache.erase(it);
+        } else {
+          ++it;
+        }
+      }
+    }
+    if (mine.empty()) return e;
+    for (void* q : mine) cudaFree(q);
+    e = cudaMalloc(out, bytes);
+  }
+  if (e == cudaSuccess) *got = bytes;
+  return e;
+}
+
+// Hands a block back to the cache (the caller has synchronised its uses).
+void ws_release(void* ptr, size_t bytes) {
+  if (!ptr) return;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaFree(ptr);
+    return;
+  }
+  void* evict = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    g_ws_cache.push_back({dev, ptr, bytes});
+    if (g_ws_cache.size() > kWsCacheBlocks) {
+      evict = g_ws_cache.front().ptr;
+      g_ws_cache.erase(g_ws_cache.begin());
+    }
+  }
+  if (evict) cudaFree(evict);
+}
+
 void clear_graphs(mlmc_plan p);
 mlmc_status settle_graph_launches(mlmc_plan p);
 
@@ -501,15 +581,17 @@ mlmc_status ensure_ws(mlmc_plan p, size_t bytes) {
     cudaStreamSynchronize(p->stream);
     if (settle_graph_launches(p) != MLMC_OK) return MLMC_ERR_CUDA;
     clear_graphs(p);
-    cudaFree(p->ws);
+    ws_release(p->ws, p->ws_bytes);
     p->ws = nullptr;
     p->ws_bytes = 0;
   }
-  if (cudaMalloc(&p->ws, bytes) != cudaSuccess) {
+  size_t got = 0;
+  if (ws_acquire(bytes, &p->ws, &got) != cudaSuccess) {
     cudaGetLastError();
+    p->ws = nullptr;
     return MLMC_ERR_OOM;
   }
-  p->ws_bytes = bytes;
+  p->ws_bytes = got;
   return MLMC_OK;
 }
 
@@ -1842,7 +1924,7 @@ mlmc_status mlmc_plan_set_workspace(mlmc_plan p, void* ws, uint64_t bytes) {
   CK(cudaStreamSynchronize(p->stream));
   if (settle_graph_launches(p) != MLMC_OK) return MLMC_ERR_CUDA;
   clear_graphs(p);   // graphs bake workspace addresses
-  if (p->ws && !p->ws_borrowed) cudaFree(p->ws);
+  if (p->ws && !p->ws_borrowed) ws_release(p->ws, p->ws_bytes);
   p->ws = ws;
   p->ws_bytes = ws ? (size_t)bytes : 0;
   p->ws_borrowed = ws != nullptr;
@@ -1858,6 +1940,24 @@ int64_t mlmc_round_bytes(const mlmc_config* cfg, const int64_t* count) {
   std::vector<int64_t> f(cfg->n_levels, 0), c(count, count + cfg->n_levels);
   for (auto& x : c) x = std::max<int64_t>(x, 0);
   return (int64_t)round_chunks_of(*cfg, meshes.data(), M, f, c, nullptr);
+}
+
+mlmc_status mlmc_release_cached_memory(void) {
+  std::vector<WsBlock> all;
+  {
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    all.swap(g_ws_cache);
+  }
+  int cur = 0;
+  if (cudaGetDevice(&cur) != cudaSuccess) return MLMC_ERR_CUDA;
+  cudaError_t first = cudaSuccess;
+  for (const WsBlock& w : all) {
+    cudaError_t e = cudaSetDevice(w.dev);
+    if (e == cudaSuccess) e = cudaFree(w.ptr);
+    if (e != cudaSuccess && first == cudaSuccess) first = e;
+  }
+  if (cudaSetDevice(cur) != cudaSuccess || first != cudaSuccess) return MLMC_ERR_CUDA;
+  return MLMC_OK;
 }
 
 mlmc_status mlmc_plan_destroy(mlmc_plan p) {
@@ -1880,7 +1980,7 @@ mlmc_status mlmc_plan_destroy(mlmc_plan p) {
   cudaFree(p->d_small);
   cudaFree(p->d_N);
   cudaFree(p->d_prof);
-  if (p->ws && !p->ws_borrowed) cudaFree(p->ws);
+  if (p->ws && !p->ws_borrowed) ws_release(p->ws, p->ws_bytes);
   if (p->d_fold) cudaFree(p->d_fold);
   if (p->h_pin) cudaFreeHost(p->h_pin);
   for (auto& e : p->pending) {

@@ -136,6 +136,7 @@ SIGNATURES = [
     ("mlmc_status_str", ctypes.c_char_p, [_I]),
     ("mlmc_plan_create", _I, [ctypes.POINTER(Config), _P, ctypes.POINTER(_P)]),
     ("mlmc_plan_destroy", _I, [_P]),
+    ("mlmc_release_cached_memory", _I, []),
     ("mlmc_reset_stats", _I, [_P]),
     ("mlmc_sample_level", _I, [_P, _I, _I64, _I64, _DP, _DP, _I32P]),
     ("mlmc_level_stats", _I, [_P, _I, ctypes.POINTER(LevelState)]),
@@ -312,6 +313,11 @@ def round_group(plans, first, count, ws_ptr, ws_bytes):
     if st not in (MLMC_OK, MLMC_ERR_NOT_CONVERGED):
         check(st, "mlmc_round_end_group")
     return st, bad
+
+
+def release_cached_memory():
+    """mlmc_release_cached_memory: workspaces kept from destroyed plans back to the driver."""
+    check(lib().mlmc_release_cached_memory(), "mlmc_release_cached_memory")
 
 
 def coef_count(cfg):

@@ -409,3 +409,20 @@ def test_nested_guess_same_answer_fewer_iterations(m, dim, precision, solver):
         rf, rc = omlmc.coupled_sample(wl, level, i)
         assert abs(qf1[i] - rf) <= RTOL_Q * abs(rf)
         assert abs(qc1[i] - rc) <= RTOL_Q * abs(rc)
+
+
+def test_workspace_kept_across_plans_gives_the_same_results(m):
+    """A plan that takes the workspace a destroyed plan left behind (the
+    library keeps it for reuse) returns the same QoIs bit for bit, and the
+    kept workspaces can be released between plans."""
+    wl = small_case(2, n0=8, levels=3, m=4, solver="gmg", precision="mixed")
+    cfg = m.config_from_workload(wl)
+    s = torch.cuda.current_stream().cuda_stream
+    got = []
+    for rep in range(3):
+        if rep == 2:
+            m.release_cached_memory()
+        with m.Plan(cfg, s) as plan:
+            qf, qc, it = plan.sample_level(2, 0, 5)
+        got.append((qf.tolist(), qc.tolist()))
+    assert got[1] == got[0] and got[2] == got[0]
