@@ -396,6 +396,15 @@ mlmc_status mlmc_kappa32(mlmc_plan plan, int mesh, const double* xi, int64_t cou
 mlmc_status mlmc_apply(mlmc_plan plan, int mesh, const double* kappa, const double* x,
                        double* y, int64_t count);
 
+/* The same operator in FP32, as the mixed form's inner solve applies it
+ * (the 3D kernel is the one the plan's stencil_tile selects): y = A(kappa32)
+ * x with FP32 arithmetic (error of order 2^-24 times sum |A_ij x_j|). Node
+ * and element arrays as in mlmc_apply, in floats; asynchronous on the
+ * plan's stream. Errors: INVALID, CUDA; TIMEOUT (at the next sync point)
+ * if a bounded wait of the 3D kernel gave up. */
+mlmc_status mlmc_apply32(mlmc_plan plan, int mesh, const float* kappa32, const float* x, float* y,
+                         int64_t count);
+
 /* Solve A(kappa) u = b (b_i = h^dim) with the configured PCG for `count`
  * samples; u (node arrays, may be NULL), q (QoI, count doubles), iters
  * (count int32, may be NULL; -1 = not converged). */

@@ -289,6 +289,7 @@ struct mlmc_plan_s {
   int64_t kl[NUM_KERNELS] = {0};
   int64_t launches = 0;
   bool tc_used = false;           // the tensor-core KLE kernel has run on this plan
+  bool zw_used = false;   // mlmc_apply32 ran the 3D FP32 z-march (bounded waits to check)
   // graph-captured solves, keyed by (form, mesh, batch, workspace) and the
   // arrays they bake in (kappa, solution, QoI, iteration counts, guess)
   std::map<std::tuple<int, int, int64_t, const void*, const void*, const void*, const void*,
@@ -984,7 +985,7 @@ mlmc_status build_graph(mlmc_plan p, const std::function<mlmc_status()>& issue, 
 // for 3D mixed-form plans also checks that no bounded wait of the FP32
 // z-march gave up (MLMC_ERR_TIMEOUT).
 mlmc_status settle_graph_launches(mlmc_plan p) {
-  if (p->cfg.dim == 3 && p->cfg.precision == MLMC_MIXED) {
+  if (p->cfg.dim == 3 && (p->cfg.precision == MLMC_MIXED || p->zw_used)) {
     unsigned timeouts = 0;
     CK(d3::take_wait_timeouts(p->stream, &timeouts));
     if (timeouts) return MLMC_ERR_TIMEOUT;
@@ -2048,6 +2049,23 @@ mlmc_status mlmc_apply(mlmc_plan p, int mesh, const double* kappa, const double*
     CK(run(p, KID_APPLY, [&] {
       return op::apply(p->stream, g, kappa + off * g.es, x + off * g.ns, y + off * g.ns, B,
                        prof_for(p, KID_APPLY, (2 * nodes_of(g) + elems_of(g)) * 8));
+    }));
+  }
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_apply32(mlmc_plan p, int mesh, const float* kappa32, const float* x, float* y,
+                         int64_t count) {
+  if (!p || mesh < 0 || mesh >= p->cfg.n_levels || count < 0 ||
+      (count > 0 && (!kappa32 || !x || !y)))
+    return MLMC_ERR_INVALID;
+  const Grid& g = p->meshes[mesh].g[0];
+  if (g.dim == 3) p->zw_used = true;
+  for (int64_t off = 0; off < count; off += 65535) {
+    const int64_t B = std::min<int64_t>(65535, count - off);
+    CK(run(p, KID_APPLY, [&] {
+      return op::apply(p->stream, g, kappa32 + off * g.es, x + off * g.ns, y + off * g.ns, B,
+                       prof_for(p, KID_APPLY, (2 * nodes_of(g) + elems_of(g)) * 4));
     }));
   }
   return MLMC_OK;

@@ -147,6 +147,7 @@ SIGNATURES = [
     ("mlmc_kappa", _I, [_P, _I, _P, _I64, _P]),
     ("mlmc_kappa32", _I, [_P, _I, _P, _I64, _P]),
     ("mlmc_apply", _I, [_P, _I, _P, _P, _P, _I64]),
+    ("mlmc_apply32", _I, [_P, _I, _P, _P, _P, _I64]),
     ("mlmc_solve", _I, [_P, _I, _P, _I64, _P, _P, _P]),
     ("mlmc_kernel_count", _I, []),
     ("mlmc_kernel_name", ctypes.c_char_p, [_I]),
@@ -490,6 +491,10 @@ class Plan:
     def apply(self, mesh, kappa_ptr, x_ptr, y_ptr, count):
         check(lib().mlmc_apply(self._h, mesh, _P(kappa_ptr), _P(x_ptr), _P(y_ptr), count),
               "mlmc_apply")
+
+    def apply32(self, mesh, kappa32_ptr, x_ptr, y_ptr, count):
+        check(lib().mlmc_apply32(self._h, mesh, _P(kappa32_ptr), _P(x_ptr), _P(y_ptr), count),
+              "mlmc_apply32")
 
     def solve(self, mesh, kappa_ptr, count, u_ptr, q_ptr, iters_ptr, allow_not_converged=False):
         st = lib().mlmc_solve(self._h, mesh, _P(kappa_ptr), count, _P(u_ptr or None),
