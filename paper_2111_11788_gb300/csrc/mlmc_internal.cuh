@@ -189,6 +189,9 @@ cudaError_t winv(cudaStream_t s, const Grid& g, const T* kappa, double omega, T*
 // x = 0; if r != nullptr, r = b (b_i = h^2 at interior nodes).
 template <class T>
 cudaError_t pcg_init(cudaStream_t s, const Grid& g, T* x, T* r, int64_t B, Prof p);
+// x = 0 at every node of B samples, 2D or 3D (flat 16-byte stores).
+template <class T>
+cudaError_t zero_nodes(cudaStream_t s, const Grid& g, T* x, int64_t B, Prof p);
 // coef (may be null): the FP64 form's precomputed operator coefficients
 // (coef()), used instead of kappa by the stencil kernels
 template <class T>

@@ -47,8 +47,8 @@ Grid make_grid(int dim, int n, int z_chunk, int stencil_tile) {
   }
   g.fx = (int)((g.ns + FLAT_ELEMS - 1) / FLAT_ELEMS);
   g.tiles_f = g.fx;
-  // the 2D QoI kernel is flat, the 3D one runs on the node tiles
-  g.tiles_q = dim == 2 ? g.tiles_f : (int64_t)g.sx;
+  // the 2D QoI kernel is flat, the 3D one runs one CTA per z-plane
+  g.tiles_q = dim == 2 ? g.tiles_f : (int64_t)(n + 1);
   return g;
 }
 

@@ -781,6 +781,22 @@ __device__ __forceinline__ void flat_range(const Grid& g, int64_t& v0, int64_t& 
   tail0 = (blockIdx.x == gridDim.x - 1) ? nv * Vec<T>::L : nn;
 }
 
+// x = 0 at every node of every sample (16-byte stores; the initial iterate
+// of a solve whose residual is set elsewhere)
+template <class T>
+__global__ void __launch_bounds__(FLAT_THREADS) k_zero_flat(Grid g, T* __restrict__ X, Prof prof) {
+  using V = typename Vec<T>::V;
+  const int64_t b = blockIdx.y;
+  int64_t v0, v1, t0, nn;
+  flat_range<T>(g, v0, v1, t0, nn);
+  V* x = reinterpret_cast<V*>(X + b * g.ns);
+  V zero;
+  memset(&zero, 0, sizeof(zero));
+  for (int64_t v = v0 + threadIdx.x; v < v1; v += FLAT_THREADS) x[v] = zero;
+  for (int64_t e = t0 + threadIdx.x; e < nn; e += FLAT_THREADS) X[b * g.ns + e] = T(0);
+  if (prof.acc && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(prof.acc, prof.per_sample);
+}
+
 // x += alpha p, r -= alpha q, partials of r.r
 template <class T>
 __global__ void __launch_bounds__(FLAT_THREADS) k_xr_flat(Grid g, T* __restrict__ X,
@@ -1238,7 +1254,16 @@ cudaError_t winv(cudaStream_t s, const Grid& g, const T* kappa, double omega, T*
 
 template <class T>
 cudaError_t pcg_init(cudaStream_t s, const Grid& g, T* x, T* r, int64_t B, Prof p) {
-  k_init_flat<T><<<fgrid(g, B), FLAT_THREADS, 0, s>>>(g, x, r, p);
+  if (r)
+    k_init_flat<T><<<fgrid(g, B), FLAT_THREADS, 0, s>>>(g, x, r, p);
+  else
+    k_zero_flat<T><<<fgrid(g, B), FLAT_THREADS, 0, s>>>(g, x, p);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t zero_nodes(cudaStream_t s, const Grid& g, T* x, int64_t B, Prof p) {
+  k_zero_flat<T><<<fgrid(g, B), FLAT_THREADS, 0, s>>>(g, x, p);
   return cudaGetLastError();
 }
 
@@ -1373,6 +1398,7 @@ cudaError_t mg_bottom(cudaStream_t s, const BottomLevels<T>& lv, const T* b, T* 
   template cudaError_t apply<T>(cudaStream_t, const Grid&, const T*, const T*, T*, int64_t, Prof); \
   template cudaError_t winv<T>(cudaStream_t, const Grid&, const T*, double, T*, int64_t);          \
   template cudaError_t pcg_init<T>(cudaStream_t, const Grid&, T*, T*, int64_t, Prof);              \
+  template cudaError_t zero_nodes<T>(cudaStream_t, const Grid&, T*, int64_t, Prof);                \
   template cudaError_t pcg_pq<T>(cudaStream_t, const Grid&, const T*, const T*, const T*, T*, T*,  \
                                  const Scalars&, double*, int64_t, Prof, const T*);                \
   template cudaError_t coef<T>(cudaStream_t, const Grid&, const T*, T*, int64_t, double, T*);      \

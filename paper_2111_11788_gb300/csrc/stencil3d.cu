@@ -28,9 +28,10 @@
 // multigrid residual), so those need no pointwise pre-pass. In FP32 the two
 // rows of a thread are 8 apart and stored as pairs, so the stencil runs on
 // paired FP32 instructions. The remaining pointwise kernels run one thread
-// per node on 32 x 8 tiles of each plane. Node arrays carry the boundary
-// nodes (always 0). Partials: one per CTA (g.tiles_s per sample for the
-// stencil kernels, g.tiles_q for the QoI). The multigrid levels of at most
+// per node on 32 x 8 tiles of each plane; the initialisation and the QoI run
+// one CTA per z-plane. Node arrays carry the boundary nodes (always 0).
+// Partials: one per CTA (g.tiles_s per sample for the stencil kernels,
+// g.tiles_q = N1 for the QoI). The multigrid levels of at most
 // 16^3 cells below the finest run as one kernel per V-cycle (k_bottom3, one
 // CTA per sample in shared memory).
 #include "mlmc_internal.cuh"
@@ -1171,13 +1172,25 @@ __global__ void __launch_bounds__(256) k_winv3(Grid g, const T* __restrict__ K, 
   W[b * g.ns + q.idx] = w;
 }
 
+// x = 0 at every node, r = h^3 at interior nodes and 0 on the boundary
+// (r may be null): one CTA per z-plane, threads along x, so the stores are
+// row-contiguous and the CTA count is N1 per sample.
 template <class T>
 __global__ void __launch_bounds__(256) k_init3(Grid g, T* __restrict__ X, T* __restrict__ R, Prof prof) {
   const int64_t b = blockIdx.y;
-  const Node3 q = node3(g.n);
-  if (!q.valid) return;
-  X[b * g.ns + q.idx] = T(0);
-  if (R) R[b * g.ns + q.idx] = q.interior ? T(g.h * g.h * g.h) : T(0);
+  const int n = g.n, N1 = n + 1, k = blockIdx.x;
+  const int64_t plane = b * g.ns + (int64_t)k * N1 * N1;
+  const T h3 = T(g.h * g.h * g.h);
+  const bool kin = k > 0 && k < n;
+  for (int j = threadIdx.y; j <= n; j += blockDim.y) {
+    const bool jin = kin && j > 0 && j < n;
+    T* x = X + plane + (int64_t)j * N1;
+    T* r = R ? R + plane + (int64_t)j * N1 : nullptr;
+    for (int i = threadIdx.x; i <= n; i += blockDim.x) {
+      x[i] = T(0);
+      if (r) r[i] = (jin && i > 0 && i < n) ? h3 : T(0);
+    }
+  }
   prof_tick3(prof);
 }
 
@@ -1268,23 +1281,34 @@ __global__ void __launch_bounds__(256) k_prolong3(Grid g, int64_t nsc, const T* 
   }
 }
 
-// QoI partials: domain: w = h^3 at interior nodes; box [L, H]^3 in node
-// indices: w = h^3 chi_x chi_y chi_z / |box|, chi = 1 inside, 1/2 on a face.
+// QoI partials, one per z-plane (g.tiles_q = N1 per sample): domain: w =
+// h^3 at interior nodes; box [L, H]^3 in node indices: w = h^3 chi_x chi_y
+// chi_z / |box|, chi = 1 inside, 1/2 on a face. A CTA reads only the nodes
+// of its plane inside the region, one FP64 add per node: each row is summed
+// with its column weights (1, or 1/2 on the two face columns), each row sum
+// is added with its row weight and the plane sum is scaled once.
 template <class T>
 __global__ void __launch_bounds__(256) k_qoi3(Grid g, int box, int L, int H, double inv_vol,
                                               const T* __restrict__ X, double* __restrict__ part, Prof prof) {
   const int64_t b = blockIdx.y;
-  const Node3 q = node3(g.n);
-  double v = 0.0;
-  if (q.valid && q.interior) {
-    double w = g.h * g.h * g.h;
-    if (box) {
-      auto chi = [&](int c) { return (c > L && c < H) ? 1.0 : ((c == L || c == H) ? 0.5 : 0.0); };
-      w *= chi(q.i) * chi(q.j) * chi(q.k) * inv_vol;
+  const int n = g.n, N1 = n + 1, k = blockIdx.x;
+  const int lo = box ? L : 1, hi = box ? H : n - 1;
+  double acc = 0.0;
+  if (k >= lo && k <= hi) {
+    const T* x = X + b * g.ns + (int64_t)k * N1 * N1;
+    for (int j = lo + threadIdx.y; j <= hi; j += blockDim.y) {
+      double row = 0.0;
+      for (int i = lo + threadIdx.x; i <= hi; i += blockDim.x) {
+        const double v = (double)x[(int64_t)j * N1 + i];
+        row = (box && (i == lo || i == hi)) ? fma(0.5, v, row) : row + v;
+      }
+      acc = (box && (j == lo || j == hi)) ? fma(0.5, row, acc) : acc + row;
     }
-    v = w * (double)X[b * g.ns + q.idx];
+    double wk = g.h * g.h * g.h;
+    if (box) wk *= ((k == lo || k == hi) ? 0.5 : 1.0) * inv_vol;
+    acc *= wk;
   }
-  cta_partial3(v, part, g.tiles_q);
+  cta_partial3(acc, part, g.tiles_q);
   prof_tick3(prof);
 }
 
@@ -1475,7 +1499,8 @@ cudaError_t winv(cudaStream_t s, const Grid& g, const T* kappa, double omega, T*
 }
 template <class T>
 cudaError_t pcg_init(cudaStream_t s, const Grid& g, T* x, T* r, int64_t B, Prof p) {
-  k_init3<T><<<grid3(g, B), block3(), 0, s>>>(g, x, r, p);
+  if (!r) return d2::zero_nodes<T>(s, g, x, B, p);   // flat: node layout does not matter
+  k_init3<T><<<dim3((unsigned)(g.n + 1), (unsigned)B, 1), block3(), 0, s>>>(g, x, r, p);
   return cudaGetLastError();
 }
 template <class T>
@@ -1518,7 +1543,7 @@ cudaError_t mg_post(cudaStream_t s, const Grid& g, const Grid& coarse, const T* 
 template <class T>
 cudaError_t qoi(cudaStream_t s, const Grid& g, int box, int L, int H, double inv_vol, const T* x,
                 double* part, int64_t B, Prof p) {
-  k_qoi3<T><<<grid3(g, B), block3(), 0, s>>>(g, box, L, H, inv_vol, x, part, p);
+  k_qoi3<T><<<dim3((unsigned)(g.n + 1), (unsigned)B, 1), block3(), 0, s>>>(g, box, L, H, inv_vol, x, part, p);
   return cudaGetLastError();
 }
 cudaError_t prolong_guess(cudaStream_t s, const Grid& g, const Grid& coarse, const double* uc,
