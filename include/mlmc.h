@@ -351,7 +351,7 @@ typedef struct mlmc_tune_report {
 
 /* Time `count` (1..4096) coupled samples of `level` under every setting of
  * the selected knobs (flags: MLMC_TUNE_*; mixed-form inner tolerance
- * 1e-2..3e-4, multigrid damping 0.7..0.9, 3D z-planes per stencil CTA, the
+ * 1e-2..1e-4, multigrid damping 0.7..0.9, 3D z-planes per stencil CTA, the
  * 3D FP32 stencil tile shape, and the batch split of rounds: 1, 2 or 4
  * batches per level; with that knob the probe is a round of `count`
  * samples on every level up to `level`) and keep the fastest in the plan's configuration (inner_rtol, mg_omega,

@@ -2360,7 +2360,7 @@ mlmc_status mlmc_autotune(mlmc_plan p, int level, int64_t count, int flags, mlmc
   CK(cudaStreamSynchronize(p->stream));
   const bool mixed = is_mixed(p);
   std::vector<double> rtols = {p->cfg.inner_rtol};
-  if (mixed && (flags & MLMC_TUNE_INNER_RTOL)) rtols = {1e-2, 3e-3, 1e-3, 3e-4};
+  if (mixed && (flags & MLMC_TUNE_INNER_RTOL)) rtols = {1e-2, 3e-3, 1e-3, 3e-4, 1e-4};
   std::vector<double> omegas = {p->cfg.mg_omega};
   if (p->cfg.solver == MLMC_GMG_PCG && (flags & MLMC_TUNE_MG_OMEGA)) omegas = {0.7, 0.8, 0.9};
   std::vector<int> zcs = {p->cfg.z_chunk};

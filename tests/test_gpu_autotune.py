@@ -21,7 +21,7 @@ def m():
     return mod
 
 
-@pytest.mark.parametrize("dim,precision,flags,n_cand", [(2, "mixed", 3, 12), (3, "mixed", 7, 48),
+@pytest.mark.parametrize("dim,precision,flags,n_cand", [(2, "mixed", 3, 15), (3, "mixed", 7, 60),
                                                         (3, "fp64", 6, 12), (2, "fp64", 1, 1)])
 def test_autotune_keeps_a_candidate_and_parity(m, dim, precision, flags, n_cand):
     if dim == 2:
@@ -35,7 +35,7 @@ def test_autotune_keeps_a_candidate_and_parity(m, dim, precision, flags, n_cand)
         assert rep["candidates"] == n_cand
         assert 0 < rep["best_ms"] <= rep["worst_ms"]
         if precision == "mixed" and flags & 1:
-            assert rep["inner_rtol"] in (1e-2, 3e-3, 1e-3, 3e-4)
+            assert rep["inner_rtol"] in (1e-2, 3e-3, 1e-3, 3e-4, 1e-4)
         if flags & 2:
             assert rep["mg_omega"] in (0.7, 0.8, 0.9)
         if dim == 3 and flags & 4:
