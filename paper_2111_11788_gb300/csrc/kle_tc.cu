@@ -144,7 +144,7 @@ struct TcArgs {
   int M;                 // kept modes (columns of Phi)
   int nch;               // 64-mode chunks (K padded to nch * 64)
   int Nt;                // samples per CTA (multiple of 16, <= 256)
-  int tmem_cols;         // power of two >= max(32, Nt)
+  int tmem_cols;         // two buffers of the power of two >= max(32, Nt) columns
   int64_t ne;            // elements of the mesh
   int64_t es;            // element stride of kappa32
   int64_t B;             // samples
@@ -167,8 +167,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_kappa32_tc(TcArgs a) {
   const int K = a.nch * TC_KC;
   int* modes = reinterpret_cast<int*>(sm + a.off_modes);
   float* fac = reinterpret_cast<float*>(sm + a.off_fac);          // [dim][m][TC_TILE]
-  const uint32_t bar_stage0 = base + a.off_bar, bar_acc = base + a.off_bar + 16;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + a.off_bar + 24);
+  // mbarriers: two stages of Phi, two accumulator buffers; then the TMEM address
+  const uint32_t bar_stage0 = base + a.off_bar, bar_acc0 = base + a.off_bar + 16;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + a.off_bar + 32);
   const int m = a.m;
 
   // kept modes as packed per-axis orders (kx | ky << 8 | kz << 16), -1 for padding
@@ -200,11 +201,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_kappa32_tc(TcArgs a) {
   if (tid == 0) {
     tc_mbar_init(bar_stage0, 1);
     tc_mbar_init(bar_stage0 + 8, 1);
-    tc_mbar_init(bar_acc, 1);
+    tc_mbar_init(bar_acc0, 1);
+    tc_mbar_init(bar_acc0 + 8, 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (warp == 0) {
-    tmem_alloc(base + a.off_bar + 24, (unsigned)a.tmem_cols);
+    tmem_alloc(base + a.off_bar + 32, (unsigned)a.tmem_cols);
     tmem_relinquish();
   }
   tc_fence_proxy_async();
@@ -215,15 +217,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_kappa32_tc(TcArgs a) {
   const uint32_t idesc = bf16_idesc(TC_TILE, a.Nt);
 
   const int64_t tiles = (a.ne + TC_TILE - 1) / TC_TILE;
-  int gc = 0;          // chunks issued by this CTA (stage = gc & 1)
-  int ntile = 0;       // tiles finished by this CTA
-  bool failed = false;
-  for (int64_t tile = blockIdx.x; tile < tiles && !failed; tile += gridDim.x) {
-    // this thread's element (row tid mod 128 of the tile) and the per-axis
-    // factors of its row (the row's four threads write every fourth mode;
-    // the previous tile's reads of fac ended at its closing barrier)
-    const int row = tid & (TC_TILE - 1), quarter = tid >> 7;
-    const int64_t e = tile * TC_TILE + row;
+  const uint32_t bufcols = (uint32_t)a.tmem_cols / 2;   // two accumulator buffers
+  const int row = tid & (TC_TILE - 1), quarter = tid >> 7;
+  // per-axis factors of row `row` of tile t into fac (the row's four threads
+  // write every fourth mode)
+  auto load_fac = [&](int64_t t) {
+    const int64_t e = t * TC_TILE + row;
     const bool real = e < a.ne;
     int ix = 0, iy = 0, iz = 0;
     if (real) {
@@ -237,7 +236,43 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_kappa32_tc(TcArgs a) {
       fac[(m + k) * TC_TILE + row] = real ? (float)a.table[iy * m + k] : 0.f;
       if (a.dim == 3) fac[(2 * m + k) * TC_TILE + row] = real ? (float)a.table[iz * m + k] : 0.f;
     }
-    __syncthreads();
+  };
+  // exp of the accumulators of tile t (buffer t mod 2) into kappa32, once its MMAs have completed
+  auto epilogue = [&](int64_t t, int nt) -> bool {
+    const uint32_t b = (uint32_t)(nt & 1);
+    const bool ok = tc_mbar_wait(bar_acc0 + 8u * b, (unsigned)((nt >> 1) & 1));
+    tc_fence_after();
+    if (ok) {
+      // warp w: accumulator lanes (elements) 32 (w mod 4) .., column chunks w / 4, w / 4 + 4, ..
+      const int lq = warp & 3, cg = warp >> 2;
+      const int64_t ee = t * TC_TILE + 32 * lq + (tid & 31);
+      const uint32_t lane_addr = tmem + b * bufcols + ((uint32_t)(lq * 32) << 16);
+      for (int c0 = 16 * cg; c0 < a.Nt; c0 += 16 * TC_ROW_THREADS) {
+        uint32_t r[16];
+        tmem_ld16(lane_addr + (uint32_t)c0, r);
+        tmem_ld_wait();
+        if (ee < a.ne) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int64_t bb = b0 + c0 + j;
+            if (bb < a.B) a.kappa32[bb * a.es + ee] = __expf(__uint_as_float(r[j]));
+          }
+        }
+      }
+    }
+    return ok;
+  };
+  // Per tile t (the CTA's ntile-th): Phi of t and its MMAs into accumulator
+  // buffer ntile mod 2; then the factors of the next tile; then the epilogue
+  // of the previous tile, whose MMAs ran meanwhile.
+  int gc = 0;          // chunks issued by this CTA (stage = gc & 1)
+  int ntile = 0;       // tiles whose MMAs were issued by this CTA
+  bool failed = false;
+  if ((int64_t)blockIdx.x < tiles) load_fac(blockIdx.x);
+  __syncthreads();
+  int64_t prev = -1;
+  for (int64_t tile = blockIdx.x; tile < tiles && !failed; tile += gridDim.x) {
+    const uint32_t acc_cols = tmem + (uint32_t)(ntile & 1) * bufcols;
     for (int c = 0; c < a.nch; ++c, ++gc) {
       const int s = gc & 1;
       // the stage's previous MMAs (chunk gc - 2) must have read it
@@ -278,39 +313,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_kappa32_tc(TcArgs a) {
         for (int kk = 0; kk < TC_KC / 16; ++kk) {
           const uint32_t ko = kk * 32;
           const unsigned acc = (c > 0 || kk > 0) ? 1u : 0u;
-          umma_bf16(tmem, sw128_desc(a_hi + ko), sw128_desc(b_hi + ko), idesc, acc);
-          umma_bf16(tmem, sw128_desc(a_hi + ko), sw128_desc(b_lo + ko), idesc, 1u);
-          umma_bf16(tmem, sw128_desc(a_lo + ko), sw128_desc(b_hi + ko), idesc, 1u);
+          umma_bf16(acc_cols, sw128_desc(a_hi + ko), sw128_desc(b_hi + ko), idesc, acc);
+          umma_bf16(acc_cols, sw128_desc(a_hi + ko), sw128_desc(b_lo + ko), idesc, 1u);
+          umma_bf16(acc_cols, sw128_desc(a_lo + ko), sw128_desc(b_hi + ko), idesc, 1u);
         }
         umma_commit(bar_stage0 + 8u * s);
-        if (c == a.nch - 1) umma_commit(bar_acc);
+        if (c == a.nch - 1) umma_commit(bar_acc0 + 8u * (uint32_t)(ntile & 1));
       }
     }
     if (failed) break;
-    // epilogue: accumulators of this tile -> exp -> kappa32
-    const bool ok = tc_mbar_wait(bar_acc, (unsigned)(ntile & 1));
-    tc_fence_after();
-    if (ok) {
-      // warp w: accumulator lanes (elements) 32 (w mod 4) .., column chunks w / 4, w / 4 + 4, ..
-      const int lq = warp & 3, cg = warp >> 2;
-      const int64_t ee = tile * TC_TILE + 32 * lq + (tid & 31);
-      const uint32_t lane_addr = tmem + ((uint32_t)(lq * 32) << 16);
-      for (int c0 = 16 * cg; c0 < a.Nt; c0 += 16 * TC_ROW_THREADS) {
-        uint32_t r[16];
-        tmem_ld16(lane_addr + (uint32_t)c0, r);
-        tmem_ld_wait();
-        if (ee < a.ne) {
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int64_t bb = b0 + c0 + j;
-            if (bb < a.B) a.kappa32[bb * a.es + ee] = __expf(__uint_as_float(r[j]));
-          }
-        }
-      }
-    }
+    // the last chunk's barrier ended every read of fac for this tile
+    if (tile + gridDim.x < tiles) load_fac(tile + gridDim.x);
+    bool ok = true;
+    if (prev >= 0) ok = epilogue(prev, ntile - 1);
+    prev = tile;
     ++ntile;
     tc_fence_before();
-    if (__syncthreads_or(!ok)) failed = true;   // every thread's TMEM reads precede the next MMAs
+    // every thread's TMEM reads of the previous buffer precede its next MMAs,
+    // and the next tile's factors are complete
+    if (__syncthreads_or(!ok)) failed = true;
+  }
+  if (!failed && prev >= 0) {
+    const bool ok = epilogue(prev, ntile - 1);
+    tc_fence_before();
+    if (__syncthreads_or(!ok)) failed = true;
   }
   if (failed) {
     // record the timeout and let the MMAs in flight land (bounded) before freeing the accumulators
@@ -345,7 +371,7 @@ static size_t tc_layout(int dim, int m, int nch, int Nt, TcArgs* out) {
   a.off_b = take((size_t)nch * 2 * Nt * 128, 1024);                 // Xi hi/lo, every chunk
   a.off_modes = take(sizeof(int) * (size_t)nch * TC_KC, 16);
   a.off_fac = take(sizeof(float) * (size_t)dim * m * TC_TILE, 16);
-  a.off_bar = take(32, 16);
+  a.off_bar = take(48, 16);
   return off + 1024;   // slack for aligning the dynamic base to 1 KB
 }
 
@@ -368,6 +394,7 @@ cudaError_t launch_kappa32_tc(cudaStream_t s, const Grid& g, int m, double sqrt_
   bytes = std::max<size_t>(bytes, 116 * 1024);
   int cols = 32;
   while (cols < Nt) cols *= 2;
+  cols *= 2;   // two accumulator buffers
   a.dim = g.dim;
   a.n = g.n;
   a.m = m;
