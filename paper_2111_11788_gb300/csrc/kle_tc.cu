@@ -110,6 +110,13 @@ __device__ __forceinline__ void tmem_ld16(unsigned taddr, uint32_t (&r)[16]) {
       : "r"(taddr)
       : "memory");
 }
+// 2^x by the hardware approximation (ex2.approx.ftz.f32, relative error
+// about 2^-22): kappa32 = exp(G) = 2^(G log2 e), the log2(e) folded into Phi.
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
 
 // Shared-memory matrix descriptor: 128-byte swizzled K-major tile whose
@@ -148,7 +155,7 @@ struct TcArgs {
   int64_t ne;            // elements of the mesh
   int64_t es;            // element stride of kappa32
   int64_t B;             // samples
-  float sqrt_sigma2;
+  float scale;           // sqrt(sigma^2) log2(e): the accumulators hold G log2(e)
   const double* table;   // F[i * m + k], i < n, k < m
   const double* xi;      // Xi[b * M + k]
   const int32_t* slot;   // kept mode t -> full index (null: t itself)
@@ -165,23 +172,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_kappa32_tc(TcArgs a) {
   const int tid = threadIdx.x, warp = tid >> 5;
   const int b0 = blockIdx.y * a.Nt;
   const int K = a.nch * TC_KC;
-  int* modes = reinterpret_cast<int*>(sm + a.off_modes);
+  int4* modes = reinterpret_cast<int4*>(sm + a.off_modes);
   float* fac = reinterpret_cast<float*>(sm + a.off_fac);          // [dim][m][TC_TILE]
   // mbarriers: two stages of Phi, two accumulator buffers; then the TMEM address
   const uint32_t bar_stage0 = base + a.off_bar, bar_acc0 = base + a.off_bar + 16;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + a.off_bar + 32);
   const int m = a.m;
 
-  // kept modes as packed per-axis orders (kx | ky << 8 | kz << 16), -1 for padding
+  // kept modes as the fac offsets of their per-axis factors (x, y, z rows of
+  // fac; w = 0 for padding columns, whose Phi is 0)
   for (int t = tid; t < K; t += TC_THREADS) {
-    int code = -1;
+    int4 code = make_int4(0, 0, 0, 0);
     if (t < a.M) {
       int k = a.slot ? a.slot[t] : t;
       const int kx = k % m;
       k /= m;
       const int ky = k % m;
       const int kz = a.dim == 3 ? k / m : 0;
-      code = kx | (ky << 8) | (kz << 16);
+      code = make_int4(kx * TC_TILE, (m + ky) * TC_TILE, (2 * m + kz) * TC_TILE, 1);
     }
     modes[t] = code;
   }
@@ -232,7 +240,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_kappa32_tc(TcArgs a) {
       iz = a.dim == 3 ? (int)(q / a.n) : 0;
     }
     for (int k = quarter; k < m; k += TC_ROW_THREADS) {
-      fac[k * TC_TILE + row] = real ? a.sqrt_sigma2 * (float)a.table[ix * m + k] : 0.f;
+      fac[k * TC_TILE + row] = real ? a.scale * (float)a.table[ix * m + k] : 0.f;
       fac[(m + k) * TC_TILE + row] = real ? (float)a.table[iy * m + k] : 0.f;
       if (a.dim == 3) fac[(2 * m + k) * TC_TILE + row] = real ? (float)a.table[iz * m + k] : 0.f;
     }
@@ -252,11 +260,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_kappa32_tc(TcArgs a) {
         tmem_ld16(lane_addr + (uint32_t)c0, r);
         tmem_ld_wait();
         if (ee < a.ne) {
+          float* dst = a.kappa32 + (int64_t)(b0 + c0) * a.es + ee;
+          const int64_t left = a.B - (b0 + c0);
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int64_t bb = b0 + c0 + j;
-            if (bb < a.B) a.kappa32[bb * a.es + ee] = __expf(__uint_as_float(r[j]));
-          }
+          for (int j = 0; j < 16; ++j, dst += a.es)
+            if (j < left) *dst = ex2_approx(__uint_as_float(r[j]));
         }
       }
     }
@@ -283,16 +291,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_kappa32_tc(TcArgs a) {
 #pragma unroll 1
         for (int jj = 0; jj < TC_KC / 8 / TC_ROW_THREADS; ++jj) {   // 8 modes (16 bytes) at a time
           const int j = quarter * (TC_KC / 8 / TC_ROW_THREADS) + jj;
-          __align__(16) __nv_bfloat16 hv[8], lv[8];
+          __align__(16) __nv_bfloat162 hv[4], lv[4];
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const int code = modes[c * TC_KC + j * 8 + q];
-            float v = 0.f;
-            if (code >= 0) {
-              v = fac[(code & 0xFF) * TC_TILE + row] * fac[(m + ((code >> 8) & 0xFF)) * TC_TILE + row];
-              if (a.dim == 3) v *= fac[(2 * m + (code >> 16)) * TC_TILE + row];
+          for (int q2 = 0; q2 < 4; ++q2) {
+            float v[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int4 code = modes[c * TC_KC + j * 8 + 2 * q2 + h];
+              v[h] = 0.f;
+              if (code.w) {
+                v[h] = fac[code.x + row] * fac[code.y + row];
+                if (a.dim == 3) v[h] *= fac[code.z + row];
+              }
             }
-            split_bf16(v, hv[q], lv[q]);
+            // the two modes' hi parts in one paired conversion, then their lo parts
+            hv[q2] = __floats2bfloat162_rn(v[0], v[1]);
+            const float2 hf = __bfloat1622float2(hv[q2]);
+            lv[q2] = __floats2bfloat162_rn(v[0] - hf.x, v[1] - hf.y);
           }
           const uint32_t o = sw128_off(row, j * 8);
           *reinterpret_cast<uint4*>(ah + o) = *reinterpret_cast<const uint4*>(hv);
@@ -369,7 +384,7 @@ static size_t tc_layout(int dim, int m, int nch, int Nt, TcArgs* out) {
   TcArgs& a = *out;
   a.off_a = take(4 * (size_t)TC_CHUNK_BYTES, 1024);                 // two stages of hi + lo
   a.off_b = take((size_t)nch * 2 * Nt * 128, 1024);                 // Xi hi/lo, every chunk
-  a.off_modes = take(sizeof(int) * (size_t)nch * TC_KC, 16);
+  a.off_modes = take(sizeof(int4) * (size_t)nch * TC_KC, 16);
   a.off_fac = take(sizeof(float) * (size_t)dim * m * TC_TILE, 16);
   a.off_bar = take(48, 16);
   return off + 1024;   // slack for aligning the dynamic base to 1 KB
@@ -405,7 +420,7 @@ cudaError_t launch_kappa32_tc(cudaStream_t s, const Grid& g, int m, double sqrt_
   a.ne = ipow(g.n, g.dim);
   a.es = g.es;
   a.B = B;
-  a.sqrt_sigma2 = (float)sqrt_sigma2;
+  a.scale = (float)(sqrt_sigma2 * 1.4426950408889634074);   // log2(e)
   a.table = table;
   a.xi = xi;
   a.slot = slot;
