@@ -15,15 +15,19 @@
 // A CTA (16 warps) owns N_t samples (N_t a multiple of 16, <= 256) and walks
 // 128-element tiles of the mesh. Xi of its samples stays in shared memory for
 // the whole launch; Phi is generated a 64-mode chunk at a time (four threads
-// per tile row, 16 modes each) into one of two stages while the MMAs of the
-// other stage run. Shared operands use the 128-byte swizzled K-major layout (rows of
-// 64 BF16, 8-row atoms of 1 KB); thread 0 issues tcgen05.mma (M = 128,
-// N = N_t, K = 16) and commits each stage to an mbarrier; the epilogue reads
-// the accumulators with tcgen05.ld (warp w: lanes 32w..32w+31 = elements)
-// and stores exp(G) coalesced along the elements (warp w reads lanes
-// 32 (w mod 4) .. and every fourth 16-column chunk starting at w / 4). Waits on mbarriers are
-// bounded: a CTA whose wait gives up counts a timeout in g_tc_timeouts, lets
-// its MMAs land (bounded), frees its tensor memory and ends.
+// per tile row, 16 modes each, the per-axis factors of the tile's rows in
+// shared memory, the log2(e) of the epilogue folded into them) into one of
+// two stages while the MMAs of the other stage run. Shared operands use the
+// 128-byte swizzled K-major layout (rows of 64 BF16, 8-row atoms of 1 KB);
+// thread 0 issues tcgen05.mma (M = 128, N = N_t, K = 16) and commits each
+// stage to an mbarrier. The accumulators are double-buffered in tensor
+// memory: while the MMAs of tile t run, the CTA loads the factors of its
+// next tile and runs the epilogue of tile t - 1, which reads that buffer
+// with tcgen05.ld (warp w: lanes 32 (w mod 4) .. 32 (w mod 4) + 31, i.e.
+// elements, and every fourth 16-column chunk starting at w / 4) and stores
+// kappa32 = 2^(G log2 e) coalesced along the elements. Waits on mbarriers
+// are bounded: a CTA whose wait gives up counts a timeout in g_tc_timeouts,
+// lets its MMAs land (bounded), frees its tensor memory and ends.
 #include "mlmc_internal.cuh"
 
 #include <cuda_bf16.h>
