@@ -36,8 +36,8 @@ Grid make_grid(int dim, int n, int z_chunk, int stencil_tile) {
     g.sy = (n + 1 + SROWS - 1) / SROWS;
     g.tiles_s = (int64_t)g.sx * g.sy * SWARPS;
   } else {
-    // pointwise kernels: one CTA per 32 x 8 node tile of each z-plane;
     // stencil kernels: one CTA per 32 x 16 column tile and chunk of zc planes
+    // (sx: the 32 x 8 node tiles of all planes, kept for the tile counts)
     g.sx = ((n + 1 + 31) / 32) * ((n + 1 + 7) / 8) * (n + 1);
     g.sy = 1;
     g.zc = (n + 1 <= 24) ? n + 1 : 16;

@@ -28,7 +28,8 @@
 // multigrid residual), so those need no pointwise pre-pass. In FP32 the two
 // rows of a thread are 8 apart and stored as pairs, so the stencil runs on
 // paired FP32 instructions. The remaining pointwise kernels run one thread
-// per node on 32 x 8 tiles of each plane; the initialisation and the QoI run
+// per node column of a 32 x 8 tile over 8 z-planes (the prolongation: one
+// thread per fine x-pair over 8 planes); the initialisation and the QoI run
 // one CTA per z-plane. Node arrays carry the boundary nodes (always 0).
 // Partials: one per CTA (g.tiles_s per sample for the stencil kernels,
 // g.tiles_q = N1 for the QoI). The multigrid levels of at most
@@ -49,22 +50,33 @@ struct Node3 {
   int64_t idx;  // (k * N1 + j) * N1 + i
 };
 
-__device__ __forceinline__ Node3 node3(int n) {
-  Node3 q;
+
+// Node tiles with a z-loop: CTA (zg, tile) covers the 32 x 8 node tile in
+// planes zg * NODE_PZ .. zg * NODE_PZ + NODE_PZ - 1 (one thread per column,
+// NODE_PZ planes each), so a pointwise kernel runs few, large CTAs.
+constexpr int NODE_PZ = 8;
+struct NodeCol {
+  int i, j, k0, k1;   // column (i, j), planes [k0, k1)
+  bool valid;         // the column lies in the mesh
+};
+__device__ __forceinline__ NodeCol node_col3(int n) {
   const int N1 = n + 1;
   const int tx = (N1 + BX - 1) / BX, ty = (N1 + BY - 1) / BY;
-  int t = blockIdx.x;
-  const int kz = t / (tx * ty);
-  t -= kz * tx * ty;
+  const int tiles = tx * ty;
+  const int zg = blockIdx.x / tiles;
+  const int t = blockIdx.x - zg * tiles;
   const int ty_ = t / tx;
-  const int tx_ = t - ty_ * tx;
-  q.i = tx_ * BX + threadIdx.x;
-  q.j = ty_ * BY + threadIdx.y;
-  q.k = kz;
-  q.valid = q.i <= n && q.j <= n && q.k <= n;
-  q.interior = q.i > 0 && q.i < n && q.j > 0 && q.j < n && q.k > 0 && q.k < n;
-  q.idx = ((int64_t)q.k * N1 + q.j) * N1 + q.i;
-  return q;
+  NodeCol c;
+  c.i = (t - ty_ * tx) * BX + threadIdx.x;
+  c.j = ty_ * BY + threadIdx.y;
+  c.k0 = zg * NODE_PZ;
+  c.k1 = min(c.k0 + NODE_PZ, N1);
+  c.valid = c.i <= n && c.j <= n;
+  return c;
+}
+inline unsigned node_col3_blocks(int n) {
+  const int N1 = n + 1;
+  return (unsigned)(((N1 + BX - 1) / BX) * ((N1 + BY - 1) / BY) * ((N1 + NODE_PZ - 1) / NODE_PZ));
 }
 
 template <class T>
@@ -1161,15 +1173,25 @@ template <class T>
 __global__ void __launch_bounds__(256) k_winv3(Grid g, const T* __restrict__ K, double omega,
                                                T* __restrict__ W) {
   const int64_t b = blockIdx.y;
-  const Node3 q = node3(g.n);
-  if (!q.valid) return;
-  T w = T(0);
-  if (q.interior) {
-    T kk[2][2][2];
-    load_k8(K + b * g.es, g.n, q, kk);
-    w = T(omega) / diag3(kk, g.c3);
+  const NodeCol c = node_col3(g.n);
+  if (!c.valid) return;
+  const int n = g.n, N1 = n + 1;
+  for (int k = c.k0; k < c.k1; ++k) {
+    Node3 q;
+    q.i = c.i;
+    q.j = c.j;
+    q.k = k;
+    q.valid = true;
+    q.interior = q.i > 0 && q.i < n && q.j > 0 && q.j < n && k > 0 && k < n;
+    q.idx = ((int64_t)k * N1 + q.j) * N1 + q.i;
+    T w = T(0);
+    if (q.interior) {
+      T kk[2][2][2];
+      load_k8(K + b * g.es, g.n, q, kk);
+      w = T(omega) / diag3(kk, g.c3);
+    }
+    W[b * g.ns + q.idx] = w;
   }
-  W[b * g.ns + q.idx] = w;
 }
 
 // x = 0 at every node, r = h^3 at interior nodes and 0 on the boundary
@@ -1201,27 +1223,31 @@ __global__ void __launch_bounds__(256) k_restrict3(Grid gc, int64_t nsf, const T
                                                    Prof prof) {
   const int64_t b = blockIdx.y;
   if (!active[b]) return;
-  const Node3 q = node3(gc.n);
-  if (!q.valid) return;
-  T v = T(0);
-  if (q.interior) {
-    const int64_t N1 = 2 * gc.n + 1, P = N1 * N1;
-    const T* r = R1 + b * nsf + ((int64_t)(2 * q.k) * N1 + 2 * q.j) * N1 + 2 * q.i;
-    const T wt[3] = {T(0.5), T(1), T(0.5)};
-#pragma unroll
-    for (int dz = -1; dz <= 1; ++dz) {
-      T pl = T(0);
-#pragma unroll
-      for (int dy = -1; dy <= 1; ++dy) {
-        const T* rr = r + dz * P + dy * N1;
-        const T row = T(0.5) * __ldg(rr - 1) + __ldg(rr) + T(0.5) * __ldg(rr + 1);
-        pl += wt[dy + 1] * row;
-      }
-      v += wt[dz + 1] * pl;
-    }
-  }
-  Bc[b * gc.ns + q.idx] = v;
   prof_tick3(prof);
+  const NodeCol c = node_col3(gc.n);
+  if (!c.valid) return;
+  const int nc = gc.n, C1 = nc + 1;
+  const int64_t N1 = 2 * gc.n + 1, P = N1 * N1;
+  const T wt[3] = {T(0.5), T(1), T(0.5)};
+  const bool col_in = c.i > 0 && c.i < nc && c.j > 0 && c.j < nc;
+  for (int k = c.k0; k < c.k1; ++k) {
+    T v = T(0);
+    if (col_in && k > 0 && k < nc) {
+      const T* r = R1 + b * nsf + ((int64_t)(2 * k) * N1 + 2 * c.j) * N1 + 2 * c.i;
+#pragma unroll
+      for (int dz = -1; dz <= 1; ++dz) {
+        T pl = T(0);
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy) {
+          const T* rr = r + dz * P + dy * N1;
+          const T row = T(0.5) * __ldg(rr - 1) + __ldg(rr) + T(0.5) * __ldg(rr + 1);
+          pl += wt[dy + 1] * row;
+        }
+        v += wt[dz + 1] * pl;
+      }
+    }
+    Bc[b * gc.ns + ((int64_t)k * C1 + c.j) * C1 + c.i] = v;
+  }
 }
 
 // Coarsest grid (n = 2, one unknown at (1,1,1)): e = b / D exactly.
@@ -1240,11 +1266,15 @@ __global__ void k_coarse3(Grid g, const T* __restrict__ K, const T* __restrict__
 
 // Pointwise: tmp = e + P ec (trilinear prolongation of the coarse
 // correction; E == nullptr: tmp = P ec, the nested initial guess). A thread
-// takes the fine nodes 2I and 2I + 1 of one fine row (y, z): the coarse
-// rows under it (1, 2 or 4 by the parity of y and z) are
-// summed at coarse columns I and I + 1 once, the even node takes the first
-// sum, the odd node the mean of both, each divided by the number of rows.
-// Warps run along I with uniform parities, so the gathers do not diverge.
+// takes the fine nodes 2I and 2I + 1 of one fine row y in PROLONG_PZ
+// consecutive z-planes: per plane the coarse rows under it (1, 2 or 4 by
+// the parity of y and z) are summed at coarse columns I and I + 1 once, the
+// even node takes the first sum, the odd node the mean of both, each
+// divided by the number of rows. Warps run along I with uniform parities,
+// so the gathers do not diverge; several planes per thread keep the CTAs
+// few and large.
+constexpr int PROLONG_PZ = 8;
+
 template <class T>
 __global__ void __launch_bounds__(256) k_prolong3(Grid g, int64_t nsc, const T* __restrict__ E,
                                                   const T* __restrict__ Ec, T* __restrict__ Tmp,
@@ -1253,32 +1283,43 @@ __global__ void __launch_bounds__(256) k_prolong3(Grid g, int64_t nsc, const T* 
   if (!active[b]) return;
   const int n = g.n, nc = n / 2, N1 = n + 1, C1 = nc + 1;
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
-  const int ry = blockIdx.y * blockDim.y + threadIdx.y;   // (z, y) row index
+  const int ry = blockIdx.y * blockDim.y + threadIdx.y;   // (z-group, y) index
   const int rows_y = ((N1 + 7) / 8) * 8;
-  const int z = ry / rows_y, y = ry - z * rows_y;
-  if (I > nc || y > n || z > n) return;
-  const T* ec = Ec + b * nsc;
-  const int J = y >> 1, Kc = z >> 1, oy = y & 1, oz = z & 1;
-  T s0 = T(0), s1 = T(0);
-  for (int c = 0; c <= oz; ++c)
-    for (int bq = 0; bq <= oy; ++bq) {
-      const T* row = ec + ((Kc + c) * C1 + (J + bq)) * C1;
-      s0 += __ldg(row + I);
-      if (I < nc) s1 += __ldg(row + I + 1);
-    }
-  const int rows = oy + oz;
-  const T inv = rows == 0 ? T(1) : (rows == 1 ? T(0.5) : T(0.25));
-  const bool row_in = y >= 1 && y < n && z >= 1 && z < n;
-  const int64_t o = b * g.ns + ((int64_t)z * N1 + y) * N1 + 2 * I;
-  const int x0 = 2 * I;
+  const int zg = ry / rows_y, y = ry - zg * rows_y;
   if (prof.acc && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0)
     atomicAdd(prof.acc, prof.per_sample);
-  const T e0 = E ? E[o] : T(0);
-  Tmp[o] = (row_in && x0 >= 1 && x0 < n) ? e0 + s0 * inv : T(0);
-  if (x0 + 1 <= n) {
-    const T e1 = E ? E[o + 1] : T(0);
-    Tmp[o + 1] = (row_in && x0 + 1 < n) ? e1 + T(0.5) * (s0 + s1) * inv : T(0);
+  if (I > nc || y > n) return;
+  const T* ec = Ec + b * nsc;
+  const int J = y >> 1, oy = y & 1;
+  const int x0 = 2 * I;
+  const int z1 = min(zg * PROLONG_PZ + PROLONG_PZ, n + 1);
+  for (int z = zg * PROLONG_PZ; z < z1; ++z) {
+    const int Kc = z >> 1, oz = z & 1;
+    T s0 = T(0), s1 = T(0);
+    for (int c = 0; c <= oz; ++c)
+      for (int bq = 0; bq <= oy; ++bq) {
+        const T* row = ec + ((Kc + c) * C1 + (J + bq)) * C1;
+        s0 += __ldg(row + I);
+        if (I < nc) s1 += __ldg(row + I + 1);
+      }
+    const int rows = oy + oz;
+    const T inv = rows == 0 ? T(1) : (rows == 1 ? T(0.5) : T(0.25));
+    const bool row_in = y >= 1 && y < n && z >= 1 && z < n;
+    const int64_t o = b * g.ns + ((int64_t)z * N1 + y) * N1 + x0;
+    const T e0 = E ? E[o] : T(0);
+    Tmp[o] = (row_in && x0 >= 1 && x0 < n) ? e0 + s0 * inv : T(0);
+    if (x0 + 1 <= n) {
+      const T e1 = E ? E[o + 1] : T(0);
+      Tmp[o + 1] = (row_in && x0 + 1 < n) ? e1 + T(0.5) * (s0 + s1) * inv : T(0);
+    }
   }
+}
+
+// grid of k_prolong3 for fine mesh g and B samples
+inline dim3 prolong3_grid(const Grid& g, int64_t B) {
+  const int nc = g.n / 2, rows_y = ((g.n + 1 + 7) / 8) * 8;
+  const int zgroups = (g.n + 1 + PROLONG_PZ - 1) / PROLONG_PZ;
+  return dim3((unsigned)((nc + 1 + 31) / 32), (unsigned)(rows_y / 8 * zgroups), (unsigned)B);
 }
 
 // QoI partials, one per z-plane (g.tiles_q = N1 per sample): domain: w =
@@ -1312,7 +1353,6 @@ __global__ void __launch_bounds__(256) k_qoi3(Grid g, int box, int L, int H, dou
   prof_tick3(prof);
 }
 
-inline dim3 grid3(const Grid& g, int64_t B) { return dim3((unsigned)g.sx, (unsigned)B, 1); }
 inline dim3 block3() { return dim3(BX, BY, 1); }
 
 
@@ -1494,7 +1534,7 @@ cudaError_t apply(cudaStream_t s, const Grid& g, const T* kappa, const T* x, T* 
 }
 template <class T>
 cudaError_t winv(cudaStream_t s, const Grid& g, const T* kappa, double omega, T* w, int64_t B) {
-  k_winv3<T><<<grid3(g, B), block3(), 0, s>>>(g, kappa, omega, w);
+  k_winv3<T><<<dim3(node_col3_blocks(g.n), (unsigned)B, 1), block3(), 0, s>>>(g, kappa, omega, w);
   return cudaGetLastError();
 }
 template <class T>
@@ -1519,7 +1559,8 @@ cudaError_t mg_pre(cudaStream_t s, const Grid& g, const T* kappa, const T* w, co
 template <class T>
 cudaError_t restrict_(cudaStream_t s, const Grid& fine, const Grid& coarse, const T* r1, T* bc,
                       const int32_t* active, int64_t B, Prof p) {
-  k_restrict3<T><<<grid3(coarse, B), block3(), 0, s>>>(coarse, fine.ns, r1, bc, active, p);
+  k_restrict3<T><<<dim3(node_col3_blocks(coarse.n), (unsigned)B, 1), block3(), 0, s>>>(coarse, fine.ns, r1, bc,
+                                                                                      active, p);
   return cudaGetLastError();
 }
 template <class T>
@@ -1532,11 +1573,8 @@ template <class T>
 cudaError_t mg_post(cudaStream_t s, const Grid& g, const Grid& coarse, const T* kappa, const T* w,
                     const T* b, const T* e, const T* ec, T* out, T* tmp, const int32_t* active,
                     double* part, int64_t B, Prof p) {
-  {
-    const int nc = g.n / 2, rows_y = ((g.n + 1 + 7) / 8) * 8;
-    const dim3 grid((unsigned)((nc + 1 + 31) / 32), (unsigned)(rows_y / 8 * (g.n + 1)), (unsigned)B);
-    k_prolong3<T><<<grid, dim3(32, 8, 1), 0, s>>>(g, coarse.ns, e, ec, tmp, active, Prof{nullptr, 0.0});
-  }
+  k_prolong3<T><<<prolong3_grid(g, B), dim3(32, 8, 1), 0, s>>>(g, coarse.ns, e, ec, tmp, active,
+                                                                 Prof{nullptr, 0.0});
   launch_zm3<T>(s, g, B, kappa, LdX<T>{tmp, g.ns}, active, EpiMgPost<T>{w, b, out, g.ns}, part, p);
   return cudaGetLastError();
 }
@@ -1548,9 +1586,7 @@ cudaError_t qoi(cudaStream_t s, const Grid& g, int box, int L, int H, double inv
 }
 cudaError_t prolong_guess(cudaStream_t s, const Grid& g, const Grid& coarse, const double* uc,
                           double* x, const int32_t* active, int64_t B, Prof p) {
-  const int nc = g.n / 2, rows_y = ((g.n + 1 + 7) / 8) * 8;
-  const dim3 grid((unsigned)((nc + 1 + 31) / 32), (unsigned)(rows_y / 8 * (g.n + 1)), (unsigned)B);
-  k_prolong3<double><<<grid, dim3(32, 8, 1), 0, s>>>(g, coarse.ns, nullptr, uc, x, active, p);
+  k_prolong3<double><<<prolong3_grid(g, B), dim3(32, 8, 1), 0, s>>>(g, coarse.ns, nullptr, uc, x, active, p);
   return cudaGetLastError();
 }
 
