@@ -28,8 +28,9 @@
 // multigrid residual), so those need no pointwise pre-pass. In FP32 the two
 // rows of a thread are 8 apart and stored as pairs, so the stencil runs on
 // paired FP32 instructions. The remaining pointwise kernels run one thread
-// per node column of a 32 x 8 tile over 8 z-planes (the prolongation: one
-// thread per fine x-pair over 8 planes); the initialisation and the QoI run
+// per node column of a 32 x 8 tile over 8 z-planes on grids of 64 and more
+// cells per side, else over one (the prolongation: one thread per fine
+// x-pair over 8 planes); the initialisation and the QoI run
 // one CTA per z-plane. Node arrays carry the boundary nodes (always 0).
 // Partials: one per CTA (g.tiles_s per sample for the stencil kernels,
 // g.tiles_q = N1 for the QoI). The multigrid levels of at most
@@ -52,14 +53,17 @@ struct Node3 {
 
 
 // Node tiles with a z-loop: CTA (zg, tile) covers the 32 x 8 node tile in
-// planes zg * NODE_PZ .. zg * NODE_PZ + NODE_PZ - 1 (one thread per column,
-// NODE_PZ planes each), so a pointwise kernel runs few, large CTAs.
+// planes zg * pz .. zg * pz + pz - 1 (one thread per column, pz planes
+// each), so a pointwise kernel on a large grid runs few, large CTAs
+// (pz = NODE_PZ) and one on a small grid keeps one plane per thread
+// (node_pz).
 constexpr int NODE_PZ = 8;
+inline int node_pz(int n) { return n >= 64 ? NODE_PZ : 1; }
 struct NodeCol {
   int i, j, k0, k1;   // column (i, j), planes [k0, k1)
   bool valid;         // the column lies in the mesh
 };
-__device__ __forceinline__ NodeCol node_col3(int n) {
+__device__ __forceinline__ NodeCol node_col3(int n, int pz) {
   const int N1 = n + 1;
   const int tx = (N1 + BX - 1) / BX, ty = (N1 + BY - 1) / BY;
   const int tiles = tx * ty;
@@ -69,14 +73,14 @@ __device__ __forceinline__ NodeCol node_col3(int n) {
   NodeCol c;
   c.i = (t - ty_ * tx) * BX + threadIdx.x;
   c.j = ty_ * BY + threadIdx.y;
-  c.k0 = zg * NODE_PZ;
-  c.k1 = min(c.k0 + NODE_PZ, N1);
+  c.k0 = zg * pz;
+  c.k1 = min(c.k0 + pz, N1);
   c.valid = c.i <= n && c.j <= n;
   return c;
 }
-inline unsigned node_col3_blocks(int n) {
+inline unsigned node_col3_blocks(int n, int pz) {
   const int N1 = n + 1;
-  return (unsigned)(((N1 + BX - 1) / BX) * ((N1 + BY - 1) / BY) * ((N1 + NODE_PZ - 1) / NODE_PZ));
+  return (unsigned)(((N1 + BX - 1) / BX) * ((N1 + BY - 1) / BY) * ((N1 + pz - 1) / pz));
 }
 
 template <class T>
@@ -1171,9 +1175,9 @@ inline void launch_zm3(cudaStream_t s, const Grid& g, int64_t B, const T* kappa,
 
 template <class T>
 __global__ void __launch_bounds__(256) k_winv3(Grid g, const T* __restrict__ K, double omega,
-                                               T* __restrict__ W) {
+                                               T* __restrict__ W, int pz) {
   const int64_t b = blockIdx.y;
-  const NodeCol c = node_col3(g.n);
+  const NodeCol c = node_col3(g.n, pz);
   if (!c.valid) return;
   const int n = g.n, N1 = n + 1;
   for (int k = c.k0; k < c.k1; ++k) {
@@ -1220,11 +1224,11 @@ __global__ void __launch_bounds__(256) k_init3(Grid g, T* __restrict__ X, T* __r
 template <class T>
 __global__ void __launch_bounds__(256) k_restrict3(Grid gc, int64_t nsf, const T* __restrict__ R1,
                                                    T* __restrict__ Bc, const int32_t* __restrict__ active,
-                                                   Prof prof) {
+                                                   Prof prof, int pz) {
   const int64_t b = blockIdx.y;
   if (!active[b]) return;
   prof_tick3(prof);
-  const NodeCol c = node_col3(gc.n);
+  const NodeCol c = node_col3(gc.n, pz);
   if (!c.valid) return;
   const int nc = gc.n, C1 = nc + 1;
   const int64_t N1 = 2 * gc.n + 1, P = N1 * N1;
@@ -1534,7 +1538,8 @@ cudaError_t apply(cudaStream_t s, const Grid& g, const T* kappa, const T* x, T* 
 }
 template <class T>
 cudaError_t winv(cudaStream_t s, const Grid& g, const T* kappa, double omega, T* w, int64_t B) {
-  k_winv3<T><<<dim3(node_col3_blocks(g.n), (unsigned)B, 1), block3(), 0, s>>>(g, kappa, omega, w);
+  const int pz = node_pz(g.n);
+  k_winv3<T><<<dim3(node_col3_blocks(g.n, pz), (unsigned)B, 1), block3(), 0, s>>>(g, kappa, omega, w, pz);
   return cudaGetLastError();
 }
 template <class T>
@@ -1559,8 +1564,9 @@ cudaError_t mg_pre(cudaStream_t s, const Grid& g, const T* kappa, const T* w, co
 template <class T>
 cudaError_t restrict_(cudaStream_t s, const Grid& fine, const Grid& coarse, const T* r1, T* bc,
                       const int32_t* active, int64_t B, Prof p) {
-  k_restrict3<T><<<dim3(node_col3_blocks(coarse.n), (unsigned)B, 1), block3(), 0, s>>>(coarse, fine.ns, r1, bc,
-                                                                                      active, p);
+  const int pz = node_pz(coarse.n);
+  k_restrict3<T><<<dim3(node_col3_blocks(coarse.n, pz), (unsigned)B, 1), block3(), 0, s>>>(coarse, fine.ns, r1,
+                                                                                          bc, active, p, pz);
   return cudaGetLastError();
 }
 template <class T>
