@@ -269,8 +269,14 @@ cudaError_t mg_post(cudaStream_t s, const Grid& g, const Grid& coarse, const T* 
 template <class T>
 cudaError_t qoi(cudaStream_t s, const Grid& g, int box, int L, int H, double inv_vol, const T* x,
                 double* part, int64_t B, Prof p);
+// ks (may be null): the kappa sums of ksum(); with them the residual runs
+// the element-sum z-march (k_zm3q)
 cudaError_t resid64(cudaStream_t s, const Grid& g, const double* kappa, const double* u,
-                    double* r, const int32_t* active, double* part, int64_t B, Prof p);
+                    double* r, const int32_t* active, double* part, int64_t B, Prof p,
+                    const double* ks = nullptr);
+// Per-node kappa sums [K_n | K_x | K_y | K_z] (4 node arrays per sample,
+// sample stride 4 ns) for the FP64 element-sum z-march.
+cudaError_t ksum(cudaStream_t s, const Grid& g, const double* kappa, double* ks, int64_t B);
 // nested initial guess: x = P uc (trilinear interpolation from grid `coarse`)
 cudaError_t prolong_guess(cudaStream_t s, const Grid& g, const Grid& coarse, const double* uc,
                           double* x, const int32_t* active, int64_t B, Prof p);
@@ -349,7 +355,7 @@ inline cudaError_t resid64(cudaStream_t s, const Grid& g, const double* kappa, c
                            double* r, const int32_t* active, double* part, int64_t B, Prof p,
                            const double* coef = nullptr) {
   return g.dim == 2 ? d2::resid64(s, g, kappa, u, r, active, part, B, p, coef)
-                    : d3::resid64(s, g, kappa, u, r, active, part, B, p);
+                    : d3::resid64(s, g, kappa, u, r, active, part, B, p, coef);
 }
 inline cudaError_t to_rhs32(cudaStream_t s, const Grid& g, const double* r, const double* scale,
                             float* r32, const int32_t* active, int64_t B, Prof p) {

@@ -142,7 +142,7 @@ struct MixedWs {
   double* u;
   double* r;
   double* kap64;
-  double* coef64;   // 2D: coefficients of the FP64 operator for the outer residual (else null)
+  double* coef64;   // operator data of the outer FP64 residual: 2D coefficients, 3D kappa sums
   const double* xi_tc;  // KLE coefficients: the FP32 kappa from the tensor cores (else the cast)
   Scalars outer;
   int32_t* outer_count;
@@ -156,7 +156,7 @@ void carve_mixed(Carve& c, const MeshInfo& mi, int64_t B, MixedWs& w) {
   w.u = c.take<double>(B * g0.ns);
   w.r = c.take<double>(B * g0.ns);
   w.kap64 = c.take<double>(B * g0.es);
-  w.coef64 = g0.dim == 2 ? c.take<double>(B * (3 * g0.ns + g0.es)) : nullptr;
+  w.coef64 = g0.dim == 2 ? c.take<double>(B * (3 * g0.ns + g0.es)) : c.take<double>(B * 4 * g0.ns);
   w.xi_tc = nullptr;
   w.outer.gamma = w.outer.delta = w.outer.alpha = w.outer.beta = nullptr;
   w.outer.rho = c.take<double>(B);
@@ -1132,7 +1132,10 @@ mlmc_status mixed_setup(mlmc_plan p, const MeshInfo& mi, MixedWs& w, int64_t B, 
   } else {
     CK(run(p, KID_SETUP, [&] { return launch_cast_kappa(s, g0, w.kap64, w.in.kap[0], B); }));
   }
-  if (w.coef64) CK(run(p, KID_SETUP, [&] { return d2::coef<double>(s, g0, w.kap64, w.coef64, B); }));
+  if (w.coef64)
+    CK(run(p, KID_SETUP, [&] {
+      return g0.dim == 2 ? d2::coef<double>(s, g0, w.kap64, w.coef64, B) : d3::ksum(s, g0, w.kap64, w.coef64, B);
+    }));
   mlmc_status st = setup_levels<float>(p, mi, w.in, B);
   if (st != MLMC_OK) return st;
   const double bn = b_norm(c, g0);

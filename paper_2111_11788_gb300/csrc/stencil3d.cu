@@ -341,6 +341,222 @@ __global__ void __launch_bounds__(ZTHREADS, 2) k_zm3(Grid g, const T* __restrict
   prof_tick3(prof);
 }
 
+// FP64 z-march on precomputed kappa sums (k_zm3q). With K_n the sum of the 8
+// kappa around node n and K_{n,n+d} the sum of the 4 elements sharing the
+// edge (n, n+d), the Q1 row of node n (element stiffness h/12 (4, 0, -1,
+// -1) by the number of differing coordinates, Sec. 5.1 of the FE setting)
+// is
+//   (A u)_n = h/12 [5 u_n K_n - sum_{e ni n} kappa_e S_e + sum_{6 d} u_{n+d} K_{n,n+d}],
+// S_e the sum of u over the 8 nodes of element e. Per plane p a CTA forms,
+// for every element position of its tile (33 x 17 with the halo), the sum
+// of u over the element's 4 nodes in plane p (PXY), and Q = kappa * S for
+// the layer below plane p (S = PXY(p) + PXY(p - 1)), once per element, in
+// shared memory; a node takes the 2 x 2 sums of Q of the two layers around
+// it (B, one carried from the plane before) and its 6 face neighbours
+// weighted by the edge sums. About 19 FP64 operations per node instead of
+// the 33 of k_zm3 (the kernel is bound by the FP64 pipe; the 4 node arrays
+// of kappa sums, [K_n | K_x | K_y | K_z] per sample, are computed once per
+// solve by k_ksum3). Same tiles, chunks, loaders, epilogues and boundary
+// rule as k_zm3.
+template <class Ld, class Epi>
+__global__ void __launch_bounds__(ZTHREADS, 2) k_zm3q(Grid g, const double* __restrict__ Kap,
+                                                   const double* __restrict__ Ks, int64_t kss, Ld ld,
+                                                   const int32_t* __restrict__ active, Epi epi,
+                                                   double* __restrict__ part, Prof prof) {
+  const int64_t b = blockIdx.y;
+  if (active && !active[b]) return;
+  __shared__ double sv[3][ZNV];   // field planes with halo (p, p - 1, and the one being refilled)
+  __shared__ double sk[2][ZNK];   // kappa layers with halo
+  __shared__ double sp[2][ZNK];   // PXY of the plane, per element position
+  __shared__ double sq[ZNK];      // Q of the layer below the current plane
+  const ZTile t = ztile(g);
+  const int n = g.n, N1 = n + 1, P = N1 * N1, KP = n * n;
+  const int tid = threadIdx.y * ZTX + threadIdx.x;
+  const double* __restrict__ kp = Kap + b * g.es;
+  const double* __restrict__ Kn = Ks + b * kss;
+  const double* __restrict__ Kx = Kn + g.ns;
+  const double* __restrict__ Ky = Kn + 2 * g.ns;
+  const double* __restrict__ Kz = Kn + 3 * g.ns;
+  ld.bind(b);
+  epi.bind(b);
+  for (int e = tid; e < ZNK; e += ZTHREADS) sp[1][e] = sk[1][e] = 0.0;
+  for (int e = tid; e < ZNV; e += ZTHREADS) sv[2][e] = 0.0;
+  int vo[ZSLOTS], ko[ZSLOTS];
+  bool vok[ZSLOTS], kok[ZSLOTS], vin[ZSLOTS], kin[ZSLOTS];
+#pragma unroll
+  for (int q = 0; q < ZSLOTS; ++q) {
+    const int sidx = tid + q * ZTHREADS;
+    vin[q] = sidx < ZNV;
+    kin[q] = sidx < ZNK;
+    const int vx = t.tx0 - 1 + sidx % ZSX, vy = t.ty0 - 1 + sidx / ZSX;
+    vok[q] = vin[q] && vx >= 1 && vx < n && vy >= 1 && vy < n;
+    vo[q] = vok[q] ? vy * N1 + vx : 0;
+    const int kx = t.tx0 - 1 + sidx % ZKX, ky = t.ty0 - 1 + sidx / ZKX;
+    kok[q] = kin[q] && kx >= 0 && kx < n && ky >= 0 && ky < n;
+    ko[q] = kok[q] ? ky * n + kx : 0;
+  }
+  double rv[ZSLOTS], rk[ZSLOTS];
+  auto fetch = [&](int pp) {
+    const bool pv = pp >= 1 && pp < n, pk = pp >= 0 && pp < n;
+#pragma unroll
+    for (int q = 0; q < ZSLOTS; ++q) {
+      rv[q] = (pv && vok[q]) ? ld(pp * P + vo[q]) : 0.0;
+      rk[q] = (pk && kok[q]) ? __ldg(kp + pp * KP + ko[q]) : 0.0;
+    }
+  };
+  int p = t.z0 - 1;
+  fetch(p);
+
+  const int i = t.tx0 + threadIdx.x;
+  const int j0 = t.ty0 + ZRY * threadIdx.y;
+  bool cvalid[ZRY], cint[ZRY], ey[ZRY];
+  int ocol[ZRY];
+#pragma unroll
+  for (int r = 0; r < ZRY; ++r) {
+    const int j = j0 + r;
+    cvalid[r] = i <= n && j <= n;
+    cint[r] = i >= 1 && i < n && j >= 1 && j < n;
+    ey[r] = j == n - 1 && n % ZTY == 0;
+    ocol[r] = j * N1 + i;
+  }
+  const bool ex = i == n - 1 && n % ZTX == 0;
+  const double h12 = g.c12;   // h / 12
+  // per output row: B of the layer below the current output plane, the
+  // centre u and K_z of the plane below it, the kappa sums of the output
+  // plane (K_n, K_x(i), K_x(i - 1), K_y(j), K_y(j - 1), K_z) loaded a plane
+  // ahead, and the epilogue inputs
+  double Bprev[ZRY], ucar[ZRY], kzcar[ZRY], ks[ZRY][6];
+  typename Epi::Pre pre[ZRY];
+#pragma unroll
+  for (int r = 0; r < ZRY; ++r) {
+    Bprev[r] = ucar[r] = kzcar[r] = 0.0;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) ks[r][c] = 0.0;
+  }
+  double dot = 0.0;
+  const int vbase = (ZRY * threadIdx.y + 1) * ZSX + threadIdx.x + 1;   // node (i, j0)
+  const int kbase = ZRY * threadIdx.y * ZKX + threadIdx.x;             // element (i - 1, j0 - 1)
+  // sv: plane p in sv[cur], plane p - 1 in sv[prv]; a buffer is refilled
+  // two steps after its last read, with the barriers of a step between
+  int buf = 0, cur = 0, prv = 2;
+  for (; p <= t.z1; ++p) {
+    double* svb = sv[cur];
+    double* skb = sk[buf];
+#pragma unroll
+    for (int q = 0; q < ZSLOTS; ++q) {
+      if (vin[q]) svb[tid + q * ZTHREADS] = rv[q];
+      if (kin[q]) skb[tid + q * ZTHREADS] = rk[q];
+    }
+    __syncthreads();   // plane p and kappa layer p staged
+    if (p < t.z1) fetch(p + 1);
+    // kappa sums and epilogue inputs of plane p (an output plane at the next step)
+    typename Epi::Pre nxt[ZRY];
+    double kn[ZRY][6];
+#pragma unroll
+    for (int r = 0; r < ZRY; ++r) {
+      const bool out = cint[r] && p >= 1 && p < n;
+      if (out && p >= t.z0 && p < t.z1) nxt[r] = epi.load(p * P + ocol[r]);
+      const int o = p * P + ocol[r];
+      kn[r][0] = out ? __ldg(Kn + o) : 0.0;
+      kn[r][1] = out ? __ldg(Kx + o) : 0.0;
+      kn[r][2] = out ? __ldg(Kx + o - 1) : 0.0;
+      kn[r][3] = out ? __ldg(Ky + o) : 0.0;
+      kn[r][4] = out ? __ldg(Ky + o - N1) : 0.0;
+      kn[r][5] = (cint[r] && p >= 0 && p < n) ? __ldg(Kz + o) : 0.0;
+    }
+    // element sums of plane p and Q of layer p - 1, once per element position
+    const double* svo = sv[prv];
+    for (int e = tid; e < ZNK; e += ZTHREADS) {
+      const int ex_ = e % ZKX, ey_ = e / ZKX;
+      const double* v = svb + ey_ * ZSX + ex_;
+      const double pxy = (v[0] + v[1]) + (v[ZSX] + v[ZSX + 1]);
+      sq[e] = sk[buf ^ 1][e] * (pxy + sp[buf ^ 1][e]);
+      sp[buf][e] = pxy;
+    }
+    __syncthreads();   // Q of layer p - 1 complete
+    const int m = p - 1;
+    // Q x-pair sums of the element rows j0 - 1 .. j0 + ZRY - 1 at columns i - 1, i
+    double qx[ZRY + 1];
+#pragma unroll
+    for (int r = 0; r <= ZRY; ++r) qx[r] = sq[kbase + r * ZKX] + sq[kbase + r * ZKX + 1];
+#pragma unroll
+    for (int r = 0; r < ZRY; ++r) {
+      const double Bcur = qx[r] + qx[r + 1];
+      const double* v = svo + vbase + r * ZSX;   // node (i, j0 + r) of plane m
+      const double uc = v[0];
+      if (cvalid[r] && m >= t.z0) {
+        const int o = m * P + ocol[r];
+        const bool in = cint[r] && m >= 1 && m < n;
+        double acc = 0.0;
+        if (in) {
+          // the six face neighbours by their edge sums, then 5 u K_n - sum kappa_e S_e
+          double sx = ks[r][1] * v[1];
+          sx = fma(ks[r][2], v[-1], sx);
+          sx = fma(ks[r][3], v[ZSX], sx);
+          sx = fma(ks[r][4], v[-ZSX], sx);
+          sx = fma(ks[r][5], svb[vbase + r * ZSX], sx);
+          sx = fma(kzcar[r], ucar[r], sx);
+          sx = fma(5.0 * uc, ks[r][0], sx);
+          acc = sx - (Bprev[r] + Bcur);
+        }
+        double done;
+        if constexpr (Epi::kRes) done = fma(-h12, acc, epi.rhs(pre[r]));
+        else done = h12 * acc;
+        dot += epi(o, in, done, uc, pre[r]);
+        if (ex) epi.zero(o + 1);
+        if (ey[r]) epi.zero(o + N1);
+        if (ex && ey[r]) epi.zero(o + N1 + 1);
+      }
+      Bprev[r] = Bcur;
+      ucar[r] = uc;
+      kzcar[r] = ks[r][5];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) ks[r][c] = kn[r][c];
+      pre[r] = nxt[r];
+    }
+    buf ^= 1;
+    prv = cur;
+    cur = cur == 2 ? 0 : cur + 1;
+  }
+  if (part) cta_partial3(dot, part, g.tiles_s);
+  prof_tick3(prof);
+}
+
+// Kappa sums of every node (0 outside the mesh), per sample [K_n | K_x | K_y
+// | K_z] in node strides: K_n the 8 elements around the node, K_x the 4
+// elements sharing the edge to the +x neighbour (element column i, rows j-1
+// and j, layers k-1 and k), K_y and K_z likewise. Once per solve.
+__global__ void __launch_bounds__(256) k_ksum3(Grid g, const double* __restrict__ K, double* __restrict__ Ks,
+                                               int64_t kss, int pz) {
+  const int64_t b = blockIdx.y;
+  const NodeCol c = node_col3(g.n, pz);
+  if (!c.valid) return;
+  const int n = g.n, N1 = n + 1;
+  const double* k = K + b * g.es;
+  double* kn = Ks + b * kss;
+  auto el = [&](int z, int y, int x) -> double {
+    return (z >= 0 && z < n && y >= 0 && y < n && x >= 0 && x < n) ? __ldg(k + ((int64_t)z * n + y) * n + x) : 0.0;
+  };
+  for (int kz = c.k0; kz < c.k1; ++kz) {
+    double e[2][2][2];   // elements (kz - 1 + a, j - 1 + bq, i - 1 + cq)
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int bq = 0; bq < 2; ++bq)
+#pragma unroll
+        for (int cq = 0; cq < 2; ++cq) e[a][bq][cq] = el(kz - 1 + a, c.j - 1 + bq, c.i - 1 + cq);
+    const double sx = (e[0][0][1] + e[0][1][1]) + (e[1][0][1] + e[1][1][1]);   // column i
+    const double sy = (e[0][1][0] + e[0][1][1]) + (e[1][1][0] + e[1][1][1]);   // row j
+    const double sz = (e[1][0][0] + e[1][0][1]) + (e[1][1][0] + e[1][1][1]);   // layer kz
+    const double sn = ((e[0][0][0] + e[0][0][1]) + (e[0][1][0] + e[0][1][1])) + sz;
+    const int64_t o = ((int64_t)kz * N1 + c.j) * N1 + c.i;
+    kn[o] = sn;
+    kn[g.ns + o] = sx;
+    kn[2 * g.ns + o] = sy;
+    kn[3 * g.ns + o] = sz;
+  }
+}
+
 // Loaders: the value the stencil acts on at an interior node, formed while
 // the plane is staged (bind(sample) offsets the arrays to the sample), so a
 // pointwise pre-pass is not needed.
@@ -1597,9 +1813,19 @@ cudaError_t prolong_guess(cudaStream_t s, const Grid& g, const Grid& coarse, con
 }
 
 cudaError_t resid64(cudaStream_t s, const Grid& g, const double* kappa, const double* u, double* r,
-                    const int32_t* active, double* part, int64_t B, Prof p) {
-  launch_zm3<double>(s, g, B, kappa, LdX<double>{u, g.ns}, active, EpiResid{r, g.ns, g.h * g.h * g.h},
-                     part, p);
+                    const int32_t* active, double* part, int64_t B, Prof p, const double* ks) {
+  if (ks)
+    k_zm3q<LdX<double>, EpiResid><<<gridz(g, B), dim3(ZTX, ZTY / ZRY, 1), 0, s>>>(
+        g, kappa, ks, 4 * g.ns, LdX<double>{u, g.ns}, active, EpiResid{r, g.ns, g.h * g.h * g.h}, part, p);
+  else
+    launch_zm3<double>(s, g, B, kappa, LdX<double>{u, g.ns}, active, EpiResid{r, g.ns, g.h * g.h * g.h},
+                       part, p);
+  return cudaGetLastError();
+}
+
+cudaError_t ksum(cudaStream_t s, const Grid& g, const double* kappa, double* ks, int64_t B) {
+  const int pz = node_pz(g.n);
+  k_ksum3<<<dim3(node_col3_blocks(g.n, pz), (unsigned)B, 1), block3(), 0, s>>>(g, kappa, ks, 4 * g.ns, pz);
   return cudaGetLastError();
 }
 
