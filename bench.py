@@ -504,26 +504,23 @@ def serving_run(m, args, device=0, adapt=0):
 # flops); mg_pre the W b multiply and the residual stencil (10, 19); pcg_pq
 # the direction FMA, the stencil and the dot (11, 21); resid64 the residual
 # stencil and its square (10, 20).
-# 3D (z-march on kappa): the operator is 32.5 instructions per node (4.5
-# adds for the pair sums of each kappa layer, 8 FMAs + 1 multiply + 1 FMA to
-# complete output p - 1, 4 adds + 4 FMAs + 1 add + 1 multiply for output p,
-# 1 multiply + 7 FMAs for output p + 1; 52.5 flops); the loaders and
-# epilogues add 1 to 2 instructions (the residual epilogues fold f into the
-# last two FMAs of output p - 1, one instruction less).
-# 3D residual of the mixed form (element-sum z-march on precomputed kappa
-# sums): per element position 3 adds (plane sum of its 4 nodes), 1 add and 1
-# multiply (Q = kappa S); per node 1.5 adds (x pairs of Q, shared by the two
-# rows of a thread) + 1 add (2 x 2 sum of Q) + 1 multiply and 5 FMAs (six
-# face neighbours) + 1 multiply and 1 FMA (5 u K_n) + 2 adds (minus the two
-# layers' sums) + 1 FMA (f - h/12 t) + 1 FMA (r.r): 19.5 instructions, 27.5
-# flops (its 4 kappa-sum arrays, read per node, are precomputed once per
-# solve and, like the 2D coefficient arrays, not in the algorithmic bytes).
+# 3D (element-sum z-march on precomputed kappa sums, k_zm3q): per element
+# position 3 adds (plane sum of its 4 nodes), 1 add and 1 multiply (Q =
+# kappa S); per node 1.5 adds (x pairs of Q, shared by the two rows of a
+# thread) + 1 add (2 x 2 sum of Q) + 1 multiply and 5 FMAs (six face
+# neighbours) + 1 multiply and 1 FMA (5 u K_n) + 2 adds (minus the two
+# layers' sums): 17.5 instructions, 23.5 flops for the operator. Loaders and
+# epilogues: A p: z + beta p (1 FMA), q = h/12 t (1 multiply), p.q (1 FMA);
+# pre-smoother: W b (1 multiply), b - h/12 t (1 FMA); post-smoother: b -
+# h/12 t, e + W r and b.out (3 FMAs); residual: f - h/12 t and r.r (2 FMAs).
+# The 4 kappa-sum arrays, read per node, are precomputed once per solve and,
+# like the 2D coefficient arrays, not in the algorithmic bytes.
 #   (instructions per node, flops per node, bytes per node)
 FP64_WORK = {
     (2, "mg_post"): (13.0, 25.0, 42.0), (2, "mg_pre"): (10.0, 19.0, 40.0),
     (2, "pcg_pq"): (11.0, 21.0, 40.0), (2, "resid64"): (10.0, 20.0, 24.0),
-    (3, "mg_post"): (34.5, 57.5, 41.0), (3, "mg_pre"): (33.5, 54.5, 40.0),
-    (3, "pcg_pq"): (34.5, 56.5, 40.0), (3, "resid64"): (19.5, 27.5, 24.0),
+    (3, "mg_post"): (20.5, 29.5, 41.0), (3, "mg_pre"): (19.5, 26.5, 40.0),
+    (3, "pcg_pq"): (20.5, 28.5, 40.0), (3, "resid64"): (19.5, 27.5, 24.0),
 }
 # DRAM bytes per output node measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum of one launch whose arrays exceed L2), for the

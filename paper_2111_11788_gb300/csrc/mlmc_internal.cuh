@@ -249,12 +249,14 @@ template <class T>
 cudaError_t winv(cudaStream_t s, const Grid& g, const T* kappa, double omega, T* w, int64_t B);
 template <class T>
 cudaError_t pcg_init(cudaStream_t s, const Grid& g, T* x, T* r, int64_t B, Prof p);
+// ks (FP64 only, may be null): the kappa sums of ksum(); with them the
+// z-march runs on element sums (k_zm3q)
 template <class T>
 cudaError_t pcg_pq(cudaStream_t s, const Grid& g, const T* kappa, const T* z, const T* p_old,
-                   T* p_new, T* q, const Scalars& sc, double* part, int64_t B, Prof p);
+                   T* p_new, T* q, const Scalars& sc, double* part, int64_t B, Prof p, const T* ks);
 template <class T>
 cudaError_t mg_pre(cudaStream_t s, const Grid& g, const T* kappa, const T* w, const T* b, T* e,
-                   T* r1, const int32_t* active, int64_t B, Prof p);
+                   T* r1, const int32_t* active, int64_t B, Prof p, const T* ks);
 template <class T>
 cudaError_t restrict_(cudaStream_t s, const Grid& fine, const Grid& coarse, const T* r1, T* bc,
                       const int32_t* active, int64_t B, Prof p);
@@ -265,7 +267,7 @@ cudaError_t coarse_solve(cudaStream_t s, const Grid& g, const T* kappa, const T*
 template <class T>
 cudaError_t mg_post(cudaStream_t s, const Grid& g, const Grid& coarse, const T* kappa, const T* w,
                     const T* b, const T* e, const T* ec, T* out, T* tmp, const int32_t* active,
-                    double* part, int64_t B, Prof p);
+                    double* part, int64_t B, Prof p, const T* ks);
 template <class T>
 cudaError_t qoi(cudaStream_t s, const Grid& g, int box, int L, int H, double inv_vol, const T* x,
                 double* part, int64_t B, Prof p);
@@ -307,7 +309,7 @@ inline cudaError_t pcg_pq(cudaStream_t s, const Grid& g, const T* kappa, const T
                           T* p_new, T* q, const Scalars& sc, double* part, int64_t B, Prof p,
                           const T* coef = nullptr) {
   return g.dim == 2 ? d2::pcg_pq<T>(s, g, kappa, z, p_old, p_new, q, sc, part, B, p, coef)
-                    : d3::pcg_pq<T>(s, g, kappa, z, p_old, p_new, q, sc, part, B, p);
+                    : d3::pcg_pq<T>(s, g, kappa, z, p_old, p_new, q, sc, part, B, p, coef);
 }
 template <class T>
 inline cudaError_t pcg_xr(cudaStream_t s, const Grid& g, T* x, const T* pv, T* r, const T* q,
@@ -323,7 +325,7 @@ template <class T>
 inline cudaError_t mg_pre(cudaStream_t s, const Grid& g, const T* kappa, const T* w, const T* b, T* e,
                           T* r1, const int32_t* active, int64_t B, Prof p, const T* coef = nullptr) {
   return g.dim == 2 ? d2::mg_pre<T>(s, g, kappa, w, b, e, r1, active, B, p, coef)
-                    : d3::mg_pre<T>(s, g, kappa, w, b, e, r1, active, B, p);
+                    : d3::mg_pre<T>(s, g, kappa, w, b, e, r1, active, B, p, coef);
 }
 template <class T>
 inline cudaError_t restrict_(cudaStream_t s, const Grid& fine, const Grid& coarse, const T* r1, T* bc,
@@ -343,7 +345,7 @@ inline cudaError_t mg_post(cudaStream_t s, const Grid& g, const Grid& coarse, co
                            const T* b, const T* e, const T* ec, T* out, T* tmp, const int32_t* active,
                            double* part, int64_t B, Prof p, const T* coef = nullptr) {
   return g.dim == 2 ? d2::mg_post<T>(s, g, coarse, kappa, w, b, e, ec, out, active, part, B, p, coef)
-                    : d3::mg_post<T>(s, g, coarse, kappa, w, b, e, ec, out, tmp, active, part, B, p);
+                    : d3::mg_post<T>(s, g, coarse, kappa, w, b, e, ec, out, tmp, active, part, B, p, coef);
 }
 template <class T>
 inline cudaError_t qoi(cudaStream_t s, const Grid& g, int box, int L, int H, double inv_vol, const T* x,

@@ -14,6 +14,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <type_traits>
 #include <vector>
 
 #include "mlmc_internal.cuh"
@@ -99,9 +100,11 @@ struct SolveWs {
 
 template <class T>
 void carve_solve(Carve& c, const MeshInfo& mi, int64_t B, bool own_kappa0, SolveWs<T>& w) {
-  // the FP64 2D stencils run on precomputed coefficients (3 node + 1 element
-  // arrays per level where a stencil kernel runs)
-  const bool coef = sizeof(T) == 8 && mi.g[0].dim == 2;
+  // the FP64 stencils run on precomputed operator data where a stencil
+  // kernel runs: 2D coefficients (3 node + 1 element arrays per level), 3D
+  // kappa sums (4 node arrays per level)
+  const bool coef = sizeof(T) == 8;
+  const bool d2c = mi.g[0].dim == 2;
   const Grid& g0 = mi.g[0];
   w.x = c.take<T>(B * g0.ns);
   w.r = c.take<T>(B * g0.ns);
@@ -112,7 +115,7 @@ void carve_solve(Carve& c, const MeshInfo& mi, int64_t B, bool own_kappa0, Solve
   for (int k = 0; k < mi.K; ++k) {
     const Grid& g = mi.g[k];
     w.kap[k] = (k == 0 && !own_kappa0) ? nullptr : c.take<T>(B * g.es);
-    w.coef[k] = (coef && (k == 0 || k < mi.K - 1)) ? c.take<T>(B * (3 * g.ns + g.es)) : nullptr;
+    w.coef[k] = (coef && (k == 0 || k < mi.K - 1)) ? c.take<T>(B * (d2c ? 3 * g.ns + g.es : 4 * g.ns)) : nullptr;
     w.w[k] = c.take<T>(B * g.ns);
     if (mi.K > 1) {
       w.e[k] = c.take<T>(B * g.ns);
@@ -756,14 +759,19 @@ mlmc_status setup_levels(mlmc_plan p, const MeshInfo& mi, SolveWs<T>& w, int64_t
   }
   const double omega = (K > 1) ? p->cfg.mg_omega : 1.0;
   const int kw = std::max(1, K - 1);   // levels that smooth (W = omega / D)
-  // levels with operator coefficients get W from the same kernel
+  // 2D levels with operator coefficients get W from the same kernel; 3D
+  // levels get their kappa sums (FP64) and W separately
+  const bool d2c = mi.g[0].dim == 2;
   for (int k = 0; k < K; ++k)
     if (w.coef[k])
       CK(run(p, KID_SETUP, [&] {
-        return d2::coef<T>(s, mi.g[k], w.kap[k], w.coef[k], B, omega, k < kw ? w.w[k] : nullptr);
+        if (d2c) return d2::coef<T>(s, mi.g[k], w.kap[k], w.coef[k], B, omega, k < kw ? w.w[k] : nullptr);
+        if constexpr (std::is_same<T, double>::value) return d3::ksum(s, mi.g[k], w.kap[k], w.coef[k], B);
+        return cudaErrorInvalidValue;
       }));
   for (int k = 0; k < kw; ++k)
-    if (!w.coef[k]) CK(run(p, KID_SETUP, [&] { return op::winv<T>(s, mi.g[k], w.kap[k], omega, w.w[k], B); }));
+    if (!d2c || !w.coef[k])
+      CK(run(p, KID_SETUP, [&] { return op::winv<T>(s, mi.g[k], w.kap[k], omega, w.w[k], B); }));
   return MLMC_OK;
 }
 

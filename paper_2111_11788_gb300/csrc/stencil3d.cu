@@ -1353,7 +1353,15 @@ inline dim3 gridz(const Grid& g, int64_t B) { return dim3((unsigned)g.zx, (unsig
 // The z-march launch of an epilogue: the paired FP32 kernel for float.
 template <class T, class Ld, class Epi>
 inline void launch_zm3(cudaStream_t s, const Grid& g, int64_t B, const T* kappa, const Ld& ld,
-                       const int32_t* active, const Epi& epi, double* part, Prof p) {
+                       const int32_t* active, const Epi& epi, double* part, Prof p,
+                       const T* ks = nullptr) {
+  if constexpr (std::is_same<T, double>::value) {
+    if (ks) {   // FP64 on the element sums and the per-node kappa sums
+      k_zm3q<Ld, Epi><<<gridz(g, B), dim3(ZTX, ZTY / ZRY, 1), 0, s>>>(g, kappa, ks, 4 * g.ns, ld, active, epi,
+                                                                        part, p);
+      return;
+    }
+  }
   if constexpr (std::is_same<T, float>::value) {
     using LP = LdPaired<Ld>;
     const typename LP::type lp = LP::make(ld);
@@ -1766,15 +1774,15 @@ cudaError_t pcg_init(cudaStream_t s, const Grid& g, T* x, T* r, int64_t B, Prof 
 }
 template <class T>
 cudaError_t pcg_pq(cudaStream_t s, const Grid& g, const T* kappa, const T* z, const T* p_old, T* p_new,
-                   T* q, const Scalars& sc, double* part, int64_t B, Prof p) {
+                   T* q, const Scalars& sc, double* part, int64_t B, Prof p, const T* ks) {
   launch_zm3<T>(s, g, B, kappa, LdPupd<T>{z, p_old, sc.beta, g.ns, T(0)}, sc.active,
-                EpiAq<T>{q, p_new, g.ns}, part, p);
+                EpiAq<T>{q, p_new, g.ns}, part, p, ks);
   return cudaGetLastError();
 }
 template <class T>
 cudaError_t mg_pre(cudaStream_t s, const Grid& g, const T* kappa, const T* w, const T* b, T* e, T* r1,
-                   const int32_t* active, int64_t B, Prof p) {
-  launch_zm3<T>(s, g, B, kappa, LdWb<T>{w, b, g.ns}, active, EpiMgRes<T>{b, r1, e, g.ns}, nullptr, p);
+                   const int32_t* active, int64_t B, Prof p, const T* ks) {
+  launch_zm3<T>(s, g, B, kappa, LdWb<T>{w, b, g.ns}, active, EpiMgRes<T>{b, r1, e, g.ns}, nullptr, p, ks);
   return cudaGetLastError();
 }
 template <class T>
@@ -1794,10 +1802,10 @@ cudaError_t coarse_solve(cudaStream_t s, const Grid& g, const T* kappa, const T*
 template <class T>
 cudaError_t mg_post(cudaStream_t s, const Grid& g, const Grid& coarse, const T* kappa, const T* w,
                     const T* b, const T* e, const T* ec, T* out, T* tmp, const int32_t* active,
-                    double* part, int64_t B, Prof p) {
+                    double* part, int64_t B, Prof p, const T* ks) {
   k_prolong3<T><<<prolong3_grid(g, B), dim3(32, 8, 1), 0, s>>>(g, coarse.ns, e, ec, tmp, active,
                                                                  Prof{nullptr, 0.0});
-  launch_zm3<T>(s, g, B, kappa, LdX<T>{tmp, g.ns}, active, EpiMgPost<T>{w, b, out, g.ns}, part, p);
+  launch_zm3<T>(s, g, B, kappa, LdX<T>{tmp, g.ns}, active, EpiMgPost<T>{w, b, out, g.ns}, part, p, ks);
   return cudaGetLastError();
 }
 template <class T>
@@ -1871,16 +1879,16 @@ cudaError_t take_wait_timeouts(cudaStream_t s, unsigned* out) {
   template cudaError_t winv<T>(cudaStream_t, const Grid&, const T*, double, T*, int64_t);          \
   template cudaError_t pcg_init<T>(cudaStream_t, const Grid&, T*, T*, int64_t, Prof);              \
   template cudaError_t pcg_pq<T>(cudaStream_t, const Grid&, const T*, const T*, const T*, T*, T*,  \
-                                 const Scalars&, double*, int64_t, Prof);                          \
+                                 const Scalars&, double*, int64_t, Prof, const T*);                \
   template cudaError_t mg_pre<T>(cudaStream_t, const Grid&, const T*, const T*, const T*, T*, T*,  \
-                                 const int32_t*, int64_t, Prof);                                   \
+                                 const int32_t*, int64_t, Prof, const T*);                         \
   template cudaError_t restrict_<T>(cudaStream_t, const Grid&, const Grid&, const T*, T*,          \
                                     const int32_t*, int64_t, Prof);                                \
   template cudaError_t coarse_solve<T>(cudaStream_t, const Grid&, const T*, const T*, T*,          \
                                        const int32_t*, int64_t);                                   \
   template cudaError_t mg_post<T>(cudaStream_t, const Grid&, const Grid&, const T*, const T*,      \
                                   const T*, const T*, const T*, T*, T*, const int32_t*, double*,   \
-                                  int64_t, Prof);                                                  \
+                                  int64_t, Prof, const T*);                                        \
   template cudaError_t qoi<T>(cudaStream_t, const Grid&, int, int, int, double, const T*, double*, \
                               int64_t, Prof);                                                      \
   template cudaError_t mg_bottom<T>(cudaStream_t, const BottomLevels<T>&, const T*, T*,            \
