@@ -27,7 +27,10 @@
 // while its plane is staged (z + beta p for A p, omega D^-1 b for the
 // multigrid residual), so those need no pointwise pre-pass. In FP32 the two
 // rows of a thread are 8 apart and stored as pairs, so the stencil runs on
-// paired FP32 instructions. The remaining pointwise kernels run one thread
+// paired FP32 instructions (or, on 32..256 cells per side, on full-width
+// tiles staged by TMA bulk copies, k_zm3w). In FP64, where the plan has the
+// per-node kappa sums of the level, the same march runs on element sums
+// (k_zm3q: about 19 instead of 33 FP64 operations per node). The remaining pointwise kernels run one thread
 // per node column of a 32 x 8 tile over 8 z-planes on grids of 64 and more
 // cells per side, else over one (the prolongation: one thread per fine
 // x-pair over 8 planes); the initialisation and the QoI run
