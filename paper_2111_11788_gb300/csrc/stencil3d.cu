@@ -540,23 +540,29 @@ __global__ void __launch_bounds__(256) k_ksum3(Grid g, const double* __restrict_
   auto el = [&](int z, int y, int x) -> double {
     return (z >= 0 && z < n && y >= 0 && y < n && x >= 0 && x < n) ? __ldg(k + ((int64_t)z * n + y) * n + x) : 0.0;
   };
+  // per element layer z, around this node column: L = the 4 elements, X =
+  // the 2 elements of row j (x-pair, for K_y), Y = the 2 of column i
+  // (y-pair, for K_x); a node adds the sums of the layers below and above
+  auto layer = [&](int z, double& L, double& X, double& Y) {
+    const double a = el(z, c.j - 1, c.i - 1), bq = el(z, c.j - 1, c.i);
+    const double cq = el(z, c.j, c.i - 1), d = el(z, c.j, c.i);
+    X = cq + d;
+    Y = bq + d;
+    L = (a + bq) + X;
+  };
+  double L0, X0, Y0;
+  layer(c.k0 - 1, L0, X0, Y0);
   for (int kz = c.k0; kz < c.k1; ++kz) {
-    double e[2][2][2];   // elements (kz - 1 + a, j - 1 + bq, i - 1 + cq)
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-      for (int bq = 0; bq < 2; ++bq)
-#pragma unroll
-        for (int cq = 0; cq < 2; ++cq) e[a][bq][cq] = el(kz - 1 + a, c.j - 1 + bq, c.i - 1 + cq);
-    const double sx = (e[0][0][1] + e[0][1][1]) + (e[1][0][1] + e[1][1][1]);   // column i
-    const double sy = (e[0][1][0] + e[0][1][1]) + (e[1][1][0] + e[1][1][1]);   // row j
-    const double sz = (e[1][0][0] + e[1][0][1]) + (e[1][1][0] + e[1][1][1]);   // layer kz
-    const double sn = ((e[0][0][0] + e[0][0][1]) + (e[0][1][0] + e[0][1][1])) + sz;
+    double L1, X1, Y1;
+    layer(kz, L1, X1, Y1);
     const int64_t o = ((int64_t)kz * N1 + c.j) * N1 + c.i;
-    kn[o] = sn;
-    kn[g.ns + o] = sx;
-    kn[2 * g.ns + o] = sy;
-    kn[3 * g.ns + o] = sz;
+    kn[o] = L0 + L1;
+    kn[g.ns + o] = Y0 + Y1;
+    kn[2 * g.ns + o] = X0 + X1;
+    kn[3 * g.ns + o] = L1;
+    L0 = L1;
+    X0 = X1;
+    Y0 = Y1;
   }
 }
 
