@@ -662,6 +662,86 @@ __global__ void __launch_bounds__(SBLOCK) k_mgpost2(Grid g, int64_t nsc, const T
   prof_tick(prof);
 }
 
+// k_mgpost2 for the FP32 inner solve (kappa form), on paired rows with the
+// prolongation streamed as in Prolong2; its own kernel so that it can be
+// held to 56 registers (9 CTAs per SM) without touching the FP64 kernels.
+__global__ void __launch_bounds__(SBLOCK, 9) k_mgpost2f(Grid g, int64_t nsc, const float* __restrict__ K,
+                                                        const float* __restrict__ W,
+                                                        const float* __restrict__ Bv,
+                                                        const float* __restrict__ E,
+                                                        const float* __restrict__ Ec, float* __restrict__ Out,
+                                                        const int32_t* __restrict__ active,
+                                                        double* __restrict__ part, Prof prof) {
+  const int64_t b = blockIdx.z;
+  if (!active[b]) return;
+  const Strip s = strip_of(g);
+  const int nc = g.n / 2;
+  const float* ec = Ec + b * nsc;
+  const float* e = E + b * g.ns;
+  const float* w_ = W + b * g.ns;
+  const float* bv = Bv + b * g.ns;
+  float* out = Out + b * g.ns;
+  float dot = 0.f;
+  // FP32 on paired rows with the prolongation streamed as in Prolong2.
+  // Strips start on even rows, so a pair is (j, j + 1) = (2J + 1, 2J + 2):
+  // x(2J + 1) = e + H(J)/4 + H(J + 1)/4 and x(2J + 2) = e + H(J + 1)/2, with
+  // H(J) the sum of the coarse values at columns c / 2 and (c + 1) / 2 of
+  // coarse row J. The fetch of a pair loads coarse row J + 1; H(J) is the
+  // previous pair's (hprev). Bitwise equal to prolong2_form (the scalings
+  // are exact).
+  static_assert(SROWS % 2 == 0, "strips start on even rows");
+  const int n = s.n, c = s.c, N1c = nc + 1;
+  const bool cin = c >= 1 && c < n;
+  const float* __restrict__ ecol = ec + (cin ? (c >> 1) : 0);
+  const int dc = c & 1;
+  auto hrow = [&](int J, float& a, float& bb) {
+    a = bb = 0.f;
+    if (cin && J >= 0 && J <= nc) {
+      const float* p = ecol + J * N1c;
+      a = __ldg(p);
+      bb = __ldg(p + dc);
+    }
+  };
+  float hprev;
+  {
+    float a, bb;
+    hrow(s.y0 / 2 - 1, a, bb);
+    hprev = a + bb;
+  }
+  struct RawPE {
+    float e0, e1, a, b;
+  };
+  stream_strip_pair(
+      s, K + b * g.es,
+      [&](int j) {
+        RawPE r;
+        const float* ej = e + (j * s.N1 + c);
+        r.e0 = interior2(n, c, j) ? __ldg(ej) : 0.f;
+        r.e1 = interior2(n, c, j + 1) ? __ldg(ej + s.N1) : 0.f;
+        hrow((j + 1) >> 1, r.a, r.b);
+        return r;
+      },
+      [&](const RawPE& r, int j) {
+        const float h = r.a + r.b;
+        const float x0 = interior2(n, c, j) ? fmaf(0.25f, hprev + h, r.e0) : 0.f;
+        const float x1 = interior2(n, c, j + 1) ? fmaf(0.5f, h, r.e1) : 0.f;
+        hprev = h;
+        return make_float2(x0, x1);
+      },
+      [&](int j, float ev, float ax) {
+        const int o = j * s.N1 + c;
+        float ov = 0.f;
+        if (interior2(n, c, j)) {
+          const float bval = __ldg(bv + o);
+          ov = fmaf(__ldg(w_ + o), bval - ax, ev);
+          dot = fmaf(bval, ov, dot);
+        }
+        out[o] = ov;
+      });
+  if (part) warp_partial(dot, part, s.part_idx);
+  prof_tick(prof);
+}
+
 // Mixed form, outer FP64 residual: r = b - A(kappa) u (b_i = h^2), partials of r.r.
 template <bool C>
 __global__ void __launch_bounds__(SBLOCK) k_resid2(Grid g, const double* __restrict__ K, int64_t cs,
@@ -1333,6 +1413,8 @@ cudaError_t mg_post(cudaStream_t s, const Grid& g, const Grid& coarse, const T* 
   if (coef)
     k_mgpost2<T, true><<<sgrid(g, B), SBLOCK, 0, s>>>(g, coarse.ns, coef, coef_stride(g), w, b, e, ec, out,
                                                       active, part, p);
+  else if constexpr (sizeof(T) == 4)
+    k_mgpost2f<<<sgrid(g, B), SBLOCK, 0, s>>>(g, coarse.ns, kappa, w, b, e, ec, out, active, part, p);
   else
     k_mgpost2<T, false><<<sgrid(g, B), SBLOCK, 0, s>>>(g, coarse.ns, kappa, g.es, w, b, e, ec, out,
                                                        active, part, p);
