@@ -708,9 +708,13 @@ __global__ void __launch_bounds__(SBLOCK, 9) k_mgpost2f(Grid g, int64_t nsc, con
     hrow(s.y0 / 2 - 1, a, bb);
     hprev = a + bb;
   }
+  // The pair of field rows (j, j + 1) is formed in the step that outputs rows
+  // j - 1 and j, so its fetch also loads b and W of those two rows (bw):
+  // they get the same step of latency as the field.
   struct RawPE {
-    float e0, e1, a, b;
+    float e0, e1, a, b, b0, b1, w0, w1;
   };
+  float bw[4] = {0.f, 0.f, 0.f, 0.f};   // b, W of the even and the odd output row of the step
   stream_strip_pair(
       s, K + b * g.es,
       [&](int j) {
@@ -719,6 +723,11 @@ __global__ void __launch_bounds__(SBLOCK, 9) k_mgpost2f(Grid g, int64_t nsc, con
         r.e0 = interior2(n, c, j) ? __ldg(ej) : 0.f;
         r.e1 = interior2(n, c, j + 1) ? __ldg(ej + s.N1) : 0.f;
         hrow((j + 1) >> 1, r.a, r.b);
+        const bool o0 = s.out && interior2(n, c, j - 1), o1 = s.out && interior2(n, c, j);
+        r.b0 = o0 ? __ldg(bv + (j - 1) * s.N1 + c) : 0.f;
+        r.w0 = o0 ? __ldg(w_ + (j - 1) * s.N1 + c) : 0.f;
+        r.b1 = o1 ? __ldg(bv + j * s.N1 + c) : 0.f;
+        r.w1 = o1 ? __ldg(w_ + j * s.N1 + c) : 0.f;
         return r;
       },
       [&](const RawPE& r, int j) {
@@ -726,14 +735,20 @@ __global__ void __launch_bounds__(SBLOCK, 9) k_mgpost2f(Grid g, int64_t nsc, con
         const float x0 = interior2(n, c, j) ? fmaf(0.25f, hprev + h, r.e0) : 0.f;
         const float x1 = interior2(n, c, j + 1) ? fmaf(0.5f, h, r.e1) : 0.f;
         hprev = h;
+        bw[0] = r.b0;
+        bw[1] = r.w0;
+        bw[2] = r.b1;
+        bw[3] = r.w1;
         return make_float2(x0, x1);
       },
       [&](int j, float ev, float ax) {
+        // the step's even output row takes bw[0..1], its odd one bw[2..3]
         const int o = j * s.N1 + c;
+        const float bval = (j & 1) ? bw[2] : bw[0];
+        const float wval = (j & 1) ? bw[3] : bw[1];
         float ov = 0.f;
         if (interior2(n, c, j)) {
-          const float bval = __ldg(bv + o);
-          ov = fmaf(__ldg(w_ + o), bval - ax, ev);
+          ov = fmaf(wval, bval - ax, ev);
           dot = fmaf(bval, ov, dot);
         }
         out[o] = ov;

@@ -11,7 +11,8 @@ the previous pair carried. The first test replays that schedule (the same
 fetch and form order, lanes i = -1 .. n + 1, the pair before the first
 output row and the pairs past the last) in float32 and asks for the
 textbook value 0.5 (0.5 (a + b) + 0.5 (c + d)) bit for bit at every
-interior node and 0 elsewhere. The second pins the textbook form itself to
+interior node and 0 elsewhere, and that every output row reads b and W
+(fetched with the field pair one step ahead) of its own row. The second pins the textbook form itself to
 bilinear interpolation of the coarse grid (scipy's regular-grid
 interpolator) in float64."""
 import numpy as np
@@ -48,6 +49,7 @@ def strip_fields(n, e, ec, y0):
     i = -1 .. n + 1 and every row the strip's window sees."""
     nc, y1 = n // 2, min(y0 + SROWS, n + 1)
     formed = {}
+    outputs = strip_fields.outputs = {}
     for c in range(-1, n + 2):
         cin = 1 <= c < n
 
@@ -59,21 +61,27 @@ def strip_fields(n, e, ec, y0):
         def fetch(j):
             e0 = e[j, c] if interior(n, c, j) else f32(0.0)
             e1 = e[j + 1, c] if interior(n, c, j + 1) else f32(0.0)
-            return e0, e1, hrow((j + 1) >> 1)
+            # the rows whose b and W come with this pair
+            return e0, e1, hrow((j + 1) >> 1), (j - 1, j)
 
         hprev = hrow(y0 // 2 - 1)
+        bw = None
 
         def form(raw, j):
-            nonlocal hprev
-            e0, e1, h = raw
+            nonlocal hprev, bw
+            e0, e1, h, bw = raw
             x0 = f32(e0 + f32(0.25) * f32(hprev + h)) if interior(n, c, j) else f32(0.0)
             x1 = f32(e1 + f32(0.5) * h) if interior(n, c, j + 1) else f32(0.0)
             hprev = h
             formed[(c, j)] = x0
             formed[(c, j + 1)] = x1
 
+        def out(j):
+            # the even output row of a step takes the first of the pair's b, W rows
+            outputs[(c, j)] = bw[0] if j % 2 == 0 else bw[1]
+
         # the order of stream_strip_pair: the pair (y0 - 1, y0), then one
-        # pair fetched ahead of each pair formed
+        # pair fetched ahead of each pair formed, and the step's outputs
         form(fetch(y0 - 1), y0 - 1)
         nxt = fetch(y0 + 1)
         for j in range(y0, y1, 2):
@@ -81,6 +89,9 @@ def strip_fields(n, e, ec, y0):
             if j + 2 < y1:
                 nxt = fetch(j + 3)
             form(cur, j + 1)
+            out(j)
+            if j + 1 < y1:
+                out(j + 1)
     return formed
 
 
@@ -101,6 +112,10 @@ def test_streamed_prolongation_is_the_textbook_form_bitwise(n):
                 want = textbook(e, ec, i, j) if interior(n, i, j) else f32(0.0)
                 assert x.view(np.uint32) == want.view(np.uint32), (n, y0, i, j, x, want)
                 seen.add((i, j))
+        # each output row reads b and W of its own row
+        for (i, j), row in strip_fields.outputs.items():
+            assert row == j and y0 <= j < y1, (n, y0, i, j, row)
+        assert {j for (_, j) in strip_fields.outputs} == set(range(y0, y1))
     # every node of the grid was formed by some strip
     assert all((i, j) in seen for i in range(n + 1) for j in range(n + 1))
 
