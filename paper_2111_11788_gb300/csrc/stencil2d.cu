@@ -1132,6 +1132,79 @@ __global__ void __launch_bounds__(FLAT_THREADS) k_restrict2(Grid gc, int64_t nsf
   if (prof.acc && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(prof.acc, prof.per_sample);
 }
 
+// The same full weighting on warp strips (the FP64 form): a warp owns 32
+// coarse columns I (one per lane) and walks RSTRIP_ROWS coarse rows J. On
+// each fine row a lane loads one aligned pair of fine values, (2I, 2I + 1) on
+// even rows and (2I - 1, 2I) on odd rows (fine rows have an odd length, so on
+// odd rows the pair starting at 2I - 1 is the aligned one), and takes the
+// third value of its row sum h a + b + h c from the neighbouring lane (lanes
+// 0 and 31 load theirs); the sum over the odd fine row 2J + 1 is carried to
+// coarse row J + 1, so each fine value is read once (twice on the first row
+// of a chunk). Every node of the coarse rows is written (0 off the interior).
+constexpr int RSTRIP_ROWS = 16;
+template <class T>
+struct Vec2;
+template <>
+struct Vec2<float> {
+  using V = float2;
+};
+template <>
+struct Vec2<double> {
+  using V = double2;
+};
+
+template <class T>
+__global__ void __launch_bounds__(SBLOCK) k_restrict2s(Grid gc, int64_t nsf, const T* __restrict__ R1,
+                                                       T* __restrict__ Bc, const int32_t* __restrict__ active,
+                                                       Prof prof) {
+  using V2 = typename Vec2<T>::V;
+  constexpr unsigned FULL = 0xffffffffu;
+  const int64_t b = blockIdx.z;
+  if (!active[b]) return;
+  if (prof.acc && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) atomicAdd(prof.acc, prof.per_sample);
+  const int nc = gc.n, N1c = nc + 1, N1 = 2 * nc + 1;
+  const int lane = threadIdx.x & 31;
+  const int I0 = (blockIdx.x * SWARPS + (threadIdx.x >> 5)) * 32;
+  if (I0 > nc) return;   // the whole strip lies beyond the row
+  const int I = I0 + lane;
+  const int J0 = blockIdx.y * RSTRIP_ROWS, J1 = min(J0 + RSTRIP_ROWS, N1c);
+  const T* __restrict__ r = R1 + b * nsf;
+  T* __restrict__ bc = Bc + b * gc.ns;
+  const T h = T(0.5);
+  const bool ev_ld = I < nc;              // (2I, 2I + 1) lies in the fine row
+  const bool od_ld = I >= 1 && I <= nc;   // (2I - 1, 2I) lies in the fine row
+  // h f(2I - 1) + f(2I) + h f(2I + 1) on the even fine row fr (fr * N1 even)
+  auto even_sum = [&](int fr) -> T {
+    const T* row = r + (int64_t)fr * N1;
+    V2 p{T(0), T(0)};
+    if (ev_ld) p = __ldg(reinterpret_cast<const V2*>(row + 2 * I));
+    T left = __shfl_up_sync(FULL, p.y, 1);
+    if (lane == 0) left = I >= 1 ? __ldg(row + 2 * I - 1) : T(0);
+    return h * left + p.x + h * p.y;
+  };
+  // the same on the odd fine row fr (fr * N1 odd)
+  auto odd_sum = [&](int fr) -> T {
+    const T* row = r + (int64_t)fr * N1;
+    V2 p{T(0), T(0)};
+    if (od_ld) p = __ldg(reinterpret_cast<const V2*>(row + 2 * I - 1));
+    T right = __shfl_down_sync(FULL, p.x, 1);
+    if (lane == 31) right = I < nc ? __ldg(row + 2 * I + 1) : T(0);
+    return h * p.x + p.y + h * right;
+  };
+  T oprev = J0 >= 1 ? odd_sum(2 * J0 - 1) : T(0);
+#pragma unroll 4
+  for (int J = J0; J < J1; ++J) {
+    const bool jin = J >= 1 && J < nc;   // uniform across the warp
+    T o = T(0), ev = T(0);
+    if (J < nc) o = odd_sum(2 * J + 1);
+    if (jin) ev = even_sum(2 * J);
+    T v = T(0);
+    if (jin && I >= 1 && I < nc) v = h * (oprev + o) + ev;
+    if (I <= nc) bc[(int64_t)J * N1c + I] = v;
+    oprev = o;
+  }
+}
+
 // Nested initial guess: x = P uc, the coarse-mesh solution interpolated
 // bilinearly to the fine mesh (0 on the boundary), one thread per node.
 __global__ void __launch_bounds__(FLAT_THREADS) k_prolong_guess2(Grid g, int64_t nsc,
@@ -1410,7 +1483,18 @@ cudaError_t mg_pre(cudaStream_t s, const Grid& g, const T* kappa, const T* w, co
 template <class T>
 cudaError_t restrict_(cudaStream_t s, const Grid& fine, const Grid& coarse, const T* r1, T* bc,
                       const int32_t* active, int64_t B, Prof p) {
-  k_restrict2<T><<<fgrid(coarse, B), FLAT_THREADS, 0, s>>>(coarse, fine.ns, r1, bc, active, p);
+  // FP64: warp strips (each fine value read once; 12% less restriction time
+  // than one thread per node in the 2d-scale FP64 step). FP32: one thread per
+  // node, whose independent loads hide the latency of the mostly L2-resident
+  // FP32 arrays better (the strips took 31% longer there).
+  if constexpr (sizeof(T) == 8) {
+    const int N1c = coarse.n + 1;
+    const dim3 grid((unsigned)((N1c + 32 * SWARPS - 1) / (32 * SWARPS)),
+                    (unsigned)((N1c + RSTRIP_ROWS - 1) / RSTRIP_ROWS), (unsigned)B);
+    k_restrict2s<T><<<grid, SBLOCK, 0, s>>>(coarse, fine.ns, r1, bc, active, p);
+  } else {
+    k_restrict2<T><<<fgrid(coarse, B), FLAT_THREADS, 0, s>>>(coarse, fine.ns, r1, bc, active, p);
+  }
   return cudaGetLastError();
 }
 
